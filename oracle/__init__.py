@@ -1,0 +1,237 @@
+"""FP64 oracle for the integrated / overlapping-exposure GP log-likelihood.
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline legs of ``bench.py`` may import this package.  It shares no code with
+the CUDA path (``paper_2601_02527_gb300``) and neither imports the other.
+
+Parts:
+  * :func:`events` -- the event sequence of Section 3.2 (two events per
+    exposure, time-sorted; ties resolved end-before-start) and the slot of
+    each exposure (instrument labels, or greedy interval colouring when none
+    are given; footnote to Section 3.2.3).
+  * :func:`loglik` -- the sequential integrated Kalman filter in plain C,
+    FP64, Van Loan discretisation (``gpss_oracle.c``), with complex-step
+    gradients.
+  * :mod:`oracle.dense` -- the dense integrated-GP log-likelihood
+    (Section 2.1 with the integrated kernel of Section 3.1), used to pin the
+    filter on small N.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libgpss_oracle.so")
+_lib = None
+
+SHO = 1
+MATERN32 = 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math; FP64 throughout)."""
+    src = os.path.join(_HERE, "gpss_oracle.c")
+    hdr = os.path.join(_HERE, "oracle_body.h")
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+                           "-o", tmp, src, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.POINTER
+        lib.gpss_oracle_loglik.argtypes = [
+            P(ctypes.c_int32), ctypes.c_int64, P(ctypes.c_double), P(ctypes.c_int32),
+            P(ctypes.c_int32), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+            P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+            P(ctypes.c_double)]
+        lib.gpss_oracle_loglik.restype = ctypes.c_int
+        lib.gpss_oracle_discretize.argtypes = [
+            P(ctypes.c_int32), P(ctypes.c_double), ctypes.c_double, P(ctypes.c_double),
+            P(ctypes.c_double), P(ctypes.c_double)]
+        lib.gpss_oracle_discretize.restype = ctypes.c_int
+        lib.gpss_oracle_dim.argtypes = [P(ctypes.c_int32)]
+        lib.gpss_oracle_dim.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a, ctype):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def spec_array(terms, layout, n_slots):
+    return np.asarray([len(terms), layout, n_slots] + list(terms), dtype=np.int32)
+
+
+def dim(terms, layout, n_slots) -> int:
+    return _load().gpss_oracle_dim(_ptr(spec_array(terms, layout, n_slots), ctypes.c_int32))
+
+
+class SelfOverlapError(ValueError):
+    pass
+
+
+def events(t_start, t_end, y, yerr, instrument=None):
+    """Build the labelled event sequence of one series (Section 3.2.3).
+
+    Returns a dict with per-event arrays ``t`` (float64), ``kind`` (0 start,
+    1 end), ``slot``, ``meas``, and for end events ``y``, ``r0`` (= yerr^2)
+    and ``invd`` (= 1/delta, delta = t_end - t_start in FP64), plus
+    ``n_slots``.
+
+    Ordering: by time; at equal times every end comes before any start, so a
+    reset never wipes an integral before it is read; then by measurement.
+    Slots: the instrument label when given (each label must not overlap
+    itself: t_end[n] <= t_start[next]); otherwise greedy interval colouring in
+    start order, taking the lowest slot whose last exposure has ended.
+    """
+    t_start = np.asarray(t_start, np.float64)
+    t_end = np.asarray(t_end, np.float64)
+    n = len(t_start)
+    delta = t_end - t_start
+    if np.any(~np.isfinite(delta)) or np.any(delta <= 0):
+        raise ValueError("exposure lengths must be positive and finite")
+    if instrument is not None:
+        slot_of = np.asarray(instrument, np.int64)
+        if np.any(slot_of < 0):
+            raise ValueError("instrument labels must be >= 0")
+        n_slots = int(slot_of.max()) + 1 if n else 1
+        for s in range(n_slots):
+            idx = np.nonzero(slot_of == s)[0]
+            o = idx[np.argsort(t_start[idx], kind="stable")]
+            if np.any(t_end[o[:-1]] > t_start[o[1:]]):
+                raise SelfOverlapError(f"instrument {s} overlaps itself")
+    else:
+        slot_of = np.empty(n, np.int64)
+        last_end = []
+        for i in np.argsort(t_start, kind="stable"):
+            for s, e in enumerate(last_end):
+                if e <= t_start[i]:
+                    slot_of[i] = s
+                    last_end[s] = t_end[i]
+                    break
+            else:
+                slot_of[i] = len(last_end)
+                last_end.append(t_end[i])
+        n_slots = max(len(last_end), 1)
+    t = np.concatenate([t_start, t_end])
+    kind = np.concatenate([np.zeros(n, np.int32), np.ones(n, np.int32)])
+    meas = np.concatenate([np.arange(n), np.arange(n)])
+    # lexsort: last key is primary -> (time, kind with end=0 first, measurement)
+    order = np.lexsort((meas, 1 - kind, t))
+    t, kind, meas = t[order], kind[order], meas[order]
+    y64 = np.asarray(y, np.float64)[meas]
+    r0 = np.asarray(yerr, np.float64)[meas] ** 2
+    invd = 1.0 / delta[meas]
+    return dict(t=t, kind=kind.astype(np.int32), slot=slot_of[meas].astype(np.int32), meas=meas,
+                y=np.where(kind == 1, y64, 0.0), r0=np.where(kind == 1, r0, 0.0),
+                invd=np.where(kind == 1, invd, 0.0), n_slots=n_slots)
+
+
+def loglik_events(terms, layout, ev, theta, grad=False, n_slots=None, dump=False):
+    """Oracle log-likelihood (and complex-step gradient) from built events."""
+    lib = _load()
+    n_slots = ev["n_slots"] if n_slots is None else n_slots
+    spec = spec_array(terms, layout, n_slots)
+    theta = np.ascontiguousarray(theta, np.float64)
+    out = np.zeros(1)
+    g = np.zeros(len(theta)) if grad else None
+    D = lib.gpss_oracle_dim(_ptr(spec, ctypes.c_int32))
+    if D < 0:
+        raise ValueError("unsupported model specification")
+    n_ev = len(ev["t"])
+    dP = np.zeros((n_ev, D, D)) if dump else None
+    dS = np.zeros(int(np.sum(ev["kind"]))) if dump else None
+    arr = {k: np.ascontiguousarray(ev[k]) for k in ("t", "kind", "slot", "y", "r0", "invd")}
+    rc = lib.gpss_oracle_loglik(
+        _ptr(spec, ctypes.c_int32), n_ev, _ptr(arr["t"], ctypes.c_double),
+        _ptr(arr["kind"], ctypes.c_int32), _ptr(arr["slot"], ctypes.c_int32),
+        _ptr(arr["y"], ctypes.c_double), _ptr(arr["r0"], ctypes.c_double),
+        _ptr(arr["invd"], ctypes.c_double), _ptr(theta, ctypes.c_double),
+        _ptr(out, ctypes.c_double), _ptr(g, ctypes.c_double), _ptr(dP, ctypes.c_double),
+        _ptr(dS, ctypes.c_double))
+    if rc != 0:
+        raise RuntimeError(f"oracle filter failed with code {rc}")
+    res = {"loglik": float(out[0])}
+    if grad:
+        res["grad"] = g
+    if dump:
+        res["P"] = dP
+        res["S"] = dS
+    return res
+
+
+def loglik(terms, layout, t_start, t_end, y, yerr, theta, instrument=None, grad=False,
+           n_slots=None):
+    """Oracle log-likelihood of one series; returns float or (float, grad)."""
+    ev = events(t_start, t_end, y, yerr, instrument)
+    r = loglik_events(terms, layout, ev, theta, grad=grad, n_slots=n_slots)
+    return (r["loglik"], r["grad"]) if grad else r["loglik"]
+
+
+def discretize(terms, layout, n_slots, theta, dt):
+    """Phi~(dt), Q~(dt) and P0 of the augmented model (Van Loan + doubling)."""
+    lib = _load()
+    spec = spec_array(terms, layout, n_slots)
+    D = lib.gpss_oracle_dim(_ptr(spec, ctypes.c_int32))
+    Phi = np.zeros((D, D))
+    Q = np.zeros((D, D))
+    P0 = np.zeros((D, D))
+    th = np.ascontiguousarray(theta, np.float64)
+    rc = lib.gpss_oracle_discretize(_ptr(spec, ctypes.c_int32), _ptr(th, ctypes.c_double),
+                                    float(dt), _ptr(Phi, ctypes.c_double),
+                                    _ptr(Q, ctypes.c_double), _ptr(P0, ctypes.c_double))
+    if rc:
+        raise ValueError("unsupported model specification")
+    return Phi, Q, P0
+
+
+def _series_job(args):
+    terms, layout, ser, th, grad = args
+    ts, te, y, ye, inst = ser
+    r = loglik(terms, layout, ts, te, y, ye, th, instrument=inst, grad=grad)
+    return r
+
+
+def loglik_workload(wl, series_idx=None, set_idx=None, grad=False, processes=1):
+    """Oracle values for a ``synth.Workload``.
+
+    With ``theta_per_series`` the result is indexed by series; otherwise by
+    (set, series).  ``processes > 1`` uses a spawn-started pool.
+    """
+    if series_idx is None:
+        series_idx = range(wl.n_series)
+    jobs = []
+    if wl.theta_per_series:
+        for i in series_idx:
+            jobs.append((wl.terms, wl.layout, wl.series(i), wl.theta[i], grad))
+    else:
+        sets = range(wl.theta.shape[0]) if set_idx is None else set_idx
+        for s in sets:
+            for i in series_idx:
+                jobs.append((wl.terms, wl.layout, wl.series(i), wl.theta[s], grad))
+    if processes > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            out = pool.map(_series_job, jobs)
+    else:
+        out = [_series_job(j) for j in jobs]
+    if grad:
+        return np.array([o[0] for o in out]), np.array([o[1] for o in out])
+    return np.array(out)

@@ -1,0 +1,119 @@
+"""Dense integrated-GP log-likelihood: the plain definition the filter must equal.
+
+TEST INFRASTRUCTURE (see ``oracle/__init__.py``).
+
+Definition (Section 2.1, Eq. full GP solution; Section 3.1): for exposure
+windows [a_i, b_i] of lengths delta_i,
+
+    K_ij = 1/(delta_i delta_j) * int_{a_i}^{b_i} int_{a_j}^{b_j} k(|t - t'|) dt dt'
+    L    = -1/2 (y^T (K + R)^{-1} y + log det(K + R) + N log 2 pi),
+    R    = diag(yerr^2 + s^2).
+
+The double integral has a closed form for any lengths and any overlap: with G
+the even second antiderivative of k(|x|) normalised by G(0) = G'(0) = 0,
+
+    int_{a_i}^{b_i} int_{a_j}^{b_j} k = G(b_i - a_j) - G(a_i - a_j) - G(b_i - b_j) + G(a_i - b_j).
+
+SHO with Q > 1/2 (Eq. sho_kernel): k(x) = Re(alpha e^{-beta x}) with
+alpha = sigma^2 (1 - i/(2 eta Q)), beta = omega0/(2Q) - i eta omega0, hence
+G(x) = Re(alpha (e^{-beta x} - 1 + beta x) / beta^2).
+Matern-3/2 / critically damped SHO (Q = 1/2): k(x) = sigma^2 (1 + lam x) e^{-lam x},
+G(x) = sigma^2 [2x/lam + (2/lam + x) e^{-lam x}/lam + e^{-lam x}/lam^2 - 3/lam^2].
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+import scipy.linalg
+
+SHO = 1
+MATERN32 = 2
+
+
+def split_theta(terms, theta):
+    """Per-term (sigma, omega0, Q) and white-noise sd from natural parameters."""
+    out = []
+    j = 0
+    for k in terms:
+        if k == SHO:
+            out.append((theta[j], theta[j + 1], theta[j + 2]))
+            j += 3
+        else:
+            out.append((theta[j], math.sqrt(3.0) / theta[j + 1], 0.5))
+            j += 2
+    return out, theta[j]
+
+
+def kernel(x, sigma, w0, q):
+    """Stationary SHO kernel k(|x|) (Eq. sho_kernel), Q >= 1/2."""
+    x = np.abs(x)
+    if q == 0.5:
+        return sigma ** 2 * (1 + w0 * x) * np.exp(-w0 * x)
+    if q < 0.5:
+        raise ValueError("overdamped SHO (Q < 1/2) is not supported")
+    eta = math.sqrt(1 - 1 / (4 * q * q))
+    return sigma ** 2 * np.exp(-w0 * x / (2 * q)) * (
+        np.cos(eta * w0 * x) + np.sin(eta * w0 * x) / (2 * eta * q))
+
+
+def G(x, sigma, w0, q):
+    """Even second antiderivative of k(|x|) with G(0) = G'(0) = 0.
+
+    Evaluated in extended precision: the four-term combination below
+    cancels to O(delta^2) for short exposures."""
+    LD = np.longdouble
+    x = np.abs(np.asarray(x, LD))
+    sigma, w0, q = LD(sigma), LD(w0), LD(q)
+    if q == 0.5:
+        lam = w0
+        e = np.exp(-lam * x)
+        return sigma ** 2 * (2 * x / lam + (2 / lam + x) * e / lam + e / lam ** 2 - 3 / lam ** 2)
+    eta = np.sqrt(1 - 1 / (4 * q * q))
+    alpha = sigma ** 2 * (1 - np.clongdouble(1j) / (2 * eta * q))
+    beta = w0 / (2 * q) - np.clongdouble(1j) * eta * w0
+    return np.real(alpha * (np.exp(-beta * x) - 1 + beta * x) / beta ** 2)
+
+
+def integrated_cov(terms, theta, t_start, t_end):
+    """K_ij of exposure-averaged values for a sum of SHO / Matern-3/2 terms."""
+    a = np.asarray(t_start, np.longdouble)
+    b = np.asarray(t_end, np.longdouble)
+    d = b - a
+    pars, _ = split_theta(terms, theta)
+    K = np.zeros((len(a), len(a)), np.longdouble)
+    for sigma, w0, q in pars:
+        K += (G(b[:, None] - a[None, :], sigma, w0, q) - G(a[:, None] - a[None, :], sigma, w0, q)
+              - G(b[:, None] - b[None, :], sigma, w0, q) + G(a[:, None] - b[None, :], sigma, w0, q))
+    return (K / (d[:, None] * d[None, :])).astype(np.float64)
+
+
+def instantaneous_cov(terms, theta, t):
+    t = np.asarray(t, np.float64)
+    pars, _ = split_theta(terms, theta)
+    K = np.zeros((len(t), len(t)))
+    for sigma, w0, q in pars:
+        K += kernel(t[:, None] - t[None, :], sigma, w0, q)
+    return K
+
+
+def gaussian_loglik(K, y, noise_var):
+    """-1/2 (y^T C^{-1} y + log det C + N log 2 pi), C = K + diag(noise_var)."""
+    C = K + np.diag(noise_var)
+    c, low = scipy.linalg.cho_factor(C, lower=True)
+    alpha = scipy.linalg.cho_solve((c, low), y)
+    return -0.5 * (y @ alpha + 2 * np.sum(np.log(np.diag(c))) + len(y) * math.log(2 * math.pi))
+
+
+def loglik(terms, theta, t_start, t_end, y, yerr):
+    """Dense integrated-GP log-likelihood (N <= ~2000)."""
+    _, s = split_theta(terms, theta)
+    K = integrated_cov(terms, theta, t_start, t_end)
+    y = np.asarray(y, np.float64)
+    return gaussian_loglik(K, y, np.asarray(yerr, np.float64) ** 2 + s * s)
+
+
+def loglik_instantaneous(terms, theta, t, y, yerr):
+    """Dense log-likelihood of instantaneous measurements at times t."""
+    _, s = split_theta(terms, theta)
+    K = instantaneous_cov(terms, theta, t)
+    return gaussian_loglik(K, np.asarray(y, np.float64), np.asarray(yerr, np.float64) ** 2 + s * s)

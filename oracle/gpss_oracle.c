@@ -1,0 +1,150 @@
+/*
+ * gpss_oracle.c -- plain FP64 reference for the log-likelihood of a Gaussian
+ * process observed through integrated, possibly overlapping exposures, computed
+ * by the sequential Kalman filter over the augmented state-space model of
+ * Section 3 of the paper (arXiv 2601.02527).
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the CPU
+ * baseline of the benchmark load this library.  It shares no code with the
+ * CUDA path, and the CUDA path never calls it.
+ *
+ * What it computes, in the paper's order:
+ *   - model matrices from natural parameters (Appendix B, C.1);
+ *   - discretisation by the Van Loan matrix exponential (Eq. Q_from_vanloan)
+ *     with exact semigroup doubling for long steps;
+ *   - the integrated Kalman filter with resets (Eqs. integrated_kalman_pred,
+ *     integrated_kalman_update) and one integral state per slot (Section
+ *     3.2.3), and the prediction-error log-likelihood (Eq. loglikelihood);
+ *   - gradients by the complex-step method: the filter is compiled a second
+ *     time over double complex, theta_i is perturbed by i*h, and
+ *     d loglik / d theta_i = Im(loglik) / h, exact up to rounding.
+ * Events arrive already sorted and labelled (start/end, slot) by the Python
+ * side of the oracle.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MAXT 4
+#define TWO_PI 6.283185307179586476925286766559
+#define MAXD 12
+
+typedef struct {
+  int n_terms;
+  int kind[MAXT]; /* 1 = SHO, 2 = Matern-3/2 */
+  int layout;     /* 0: one z per slot; 1: one z per term per slot */
+  int n_slots;
+  int dim;    /* augmented state dimension */
+  int n_zper; /* integral states per slot */
+} model_t;
+
+static int zindex(const model_t *M, int slot, int t) {
+  if (M->layout == 0) return 2 * M->n_terms + slot;
+  return 2 * M->n_terms + slot * M->n_terms + t;
+}
+
+static int parse_spec(const int32_t *spec, model_t *M) {
+  M->n_terms = spec[0];
+  M->layout = spec[1];
+  M->n_slots = spec[2];
+  if (M->n_terms < 1 || M->n_terms > MAXT || M->n_slots < 1) return 1;
+  if (M->layout != 0 && M->layout != 1) return 1;
+  for (int t = 0; t < M->n_terms; ++t) {
+    M->kind[t] = spec[3 + t];
+    if (M->kind[t] != 1 && M->kind[t] != 2) return 1;
+  }
+  M->n_zper = M->layout == 0 ? 1 : M->n_terms;
+  M->dim = 2 * M->n_terms + M->n_slots * M->n_zper;
+  if (M->dim > MAXD) return 1;
+  return 0;
+}
+
+static int n_params(const model_t *M) {
+  int n = 1;
+  for (int t = 0; t < M->n_terms; ++t) n += (M->kind[t] == 1) ? 3 : 2;
+  return n;
+}
+
+/* ---- real instantiation ---- */
+#define SCALAR double
+#define SFX(name) name##_r
+#define S_SQRT sqrt
+#define S_LOG log
+#define S_ABS fabs
+#define S_RE(x) (x)
+#include "oracle_body.h"
+#undef SCALAR
+#undef SFX
+#undef S_SQRT
+#undef S_LOG
+#undef S_ABS
+#undef S_RE
+
+/* ---- complex instantiation (complex-step derivatives) ---- */
+#define SCALAR double complex
+#define SFX(name) name##_c
+#define S_SQRT csqrt
+#define S_LOG clog
+#define S_ABS cabs
+#define S_RE(x) creal(x)
+#include "oracle_body.h"
+#undef SCALAR
+#undef SFX
+#undef S_SQRT
+#undef S_LOG
+#undef S_ABS
+#undef S_RE
+
+int gpss_oracle_dim(const int32_t *spec) {
+  model_t M;
+  if (parse_spec(spec, &M)) return -1;
+  return M.dim;
+}
+
+/* Phi~, Q~ and P0 (row-major dim x dim) for one step dt of the augmented model. */
+int gpss_oracle_discretize(const int32_t *spec, const double *theta, double dt, double *Phi,
+                           double *Q, double *P0) {
+  model_t M;
+  if (parse_spec(spec, &M)) return 1;
+  double w0[MAXT], q[MAXT], var[MAXT], s2;
+  double F[MAXD * MAXD], LQL[MAXD * MAXD];
+  term_params_r(&M, theta, w0, q, var, &s2);
+  build_F_r(&M, w0, q, var, F, LQL);
+  discretize_r(&M, F, LQL, dt, Phi, Q);
+  if (P0) initial_cov_r(&M, w0, var, P0);
+  return 0;
+}
+
+/* Log-likelihood of one series (and, if grad != NULL, its gradient with
+ * respect to the natural parameters by the complex-step method).
+ * Per event k (time-sorted): t_ev, kind (0 start, 1 end), slot, and for end
+ * events y, r0 = yerr^2 and 1/delta.  dumpP (n_ev * dim * dim) receives the
+ * filtered covariance after each event and dumpS (n_end) the innovation
+ * variances; both may be NULL.  Returns 0 on success. */
+int gpss_oracle_loglik(const int32_t *spec, int64_t n_ev, const double *t_ev,
+                       const int32_t *kind, const int32_t *slot, const double *y_ev,
+                       const double *r0_ev, const double *invd_ev, const double *theta,
+                       double *loglik, double *grad, double *dumpP, double *dumpS) {
+  model_t M;
+  if (parse_spec(spec, &M)) return 1;
+  double ll;
+  int rc = filter_r(&M, theta, n_ev, t_ev, kind, slot, y_ev, r0_ev, invd_ev, &ll, dumpP, dumpS);
+  if (rc) return rc;
+  *loglik = ll;
+  if (grad) {
+    const int np = n_params(&M);
+    double complex thc[16];
+    for (int i = 0; i < np; ++i) {
+      for (int j = 0; j < np; ++j) thc[j] = theta[j];
+      double hstep = 1e-20 * (fabs(theta[i]) > 1.0 ? fabs(theta[i]) : 1.0);
+      thc[i] = theta[i] + I * hstep;
+      double complex llc;
+      rc = filter_c(&M, thc, n_ev, t_ev, kind, slot, y_ev, r0_ev, invd_ev, &llc, NULL, NULL);
+      if (rc) return rc;
+      grad[i] = cimag(llc) / hstep;
+    }
+  }
+  return 0;
+}

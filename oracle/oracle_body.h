@@ -1,0 +1,282 @@
+/*
+ * Scalar-generic body of the FP64 oracle (see gpss_oracle.c).  Included twice:
+ * once with SCALAR = double and once with SCALAR = double complex, so that the
+ * complex-step derivative runs the very same arithmetic as the plain value.
+ *
+ * TEST INFRASTRUCTURE ONLY: never linked into, or called by, the product path.
+ */
+
+/* Per-term kernel constants from natural parameters.
+ * SHO (Appendix B, Eqs. sho_kernel, sho_Qc_Pinf): (sigma, omega0, Q),
+ *   Q_c = 2 omega0^3 sigma^2 / Q, P_inf = sigma^2 diag(1, omega0^2).
+ * Matern-3/2 is the critically damped SHO: Q = 1/2, omega0 = sqrt(3)/ell
+ * (Eq. sho_kernel, Q = 1/2 case).  Last parameter: white-noise sd s. */
+static void SFX(term_params)(const model_t *M, const SCALAR *th, SCALAR *w0, SCALAR *q,
+                             SCALAR *var, SCALAR *s2) {
+  int j = 0;
+  for (int t = 0; t < M->n_terms; ++t) {
+    SCALAR sig;
+    if (M->kind[t] == 1) {
+      sig = th[j];
+      w0[t] = th[j + 1];
+      q[t] = th[j + 2];
+      j += 3;
+    } else {
+      sig = th[j];
+      w0[t] = S_SQRT(3.0) / th[j + 1];
+      q[t] = 0.5;
+      j += 2;
+    }
+    var[t] = sig * sig;
+  }
+  *s2 = th[j] * th[j];
+}
+
+/* Augmented feedback matrix F~ (Eq. augmented_sde, generalised to several
+ * integral states in Section 3.2.3) and L~ Q_c L~^T.
+ * State order: (x_t, xdot_t) for every term t, then the integral states.
+ * Layout 0: one z_j per slot j, dz_j/dt = H x = sum_t x_t (Appendix C.1).
+ * Layout 1: one z_{t,j} per term and slot, dz_{t,j}/dt = x_t. */
+static void SFX(build_F)(const model_t *M, const SCALAR *w0, const SCALAR *q, const SCALAR *var,
+                         SCALAR *F, SCALAR *LQL) {
+  const int D = M->dim;
+  for (int i = 0; i < D * D; ++i) {
+    F[i] = 0;
+    LQL[i] = 0;
+  }
+  for (int t = 0; t < M->n_terms; ++t) {
+    int i = 2 * t;
+    F[i * D + i + 1] = 1.0;
+    F[(i + 1) * D + i] = -w0[t] * w0[t];
+    F[(i + 1) * D + i + 1] = -w0[t] / q[t];
+    LQL[(i + 1) * D + i + 1] = 2.0 * w0[t] * w0[t] * w0[t] * var[t] / q[t];
+  }
+  for (int j = 0; j < M->n_slots; ++j) {
+    for (int t = 0; t < M->n_terms; ++t) {
+      int zi = zindex(M, j, t);
+      F[zi * D + 2 * t] = 1.0;
+    }
+  }
+}
+
+static void SFX(matmul)(int n, const SCALAR *A, const SCALAR *B, SCALAR *C) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      SCALAR acc = 0;
+      for (int k = 0; k < n; ++k) acc += A[i * n + k] * B[k * n + j];
+      C[i * n + j] = acc;
+    }
+}
+
+/* Matrix exponential by scaling and squaring of a truncated Taylor series:
+ * exp(A) = (exp(A / 2^r))^(2^r) with ||A / 2^r||_1 <= 1/2 and 24 Taylor terms
+ * (truncation below 1e-30).  A library-free restatement of the textbook
+ * method; adequate because every argument here has a small norm. */
+static void SFX(expm)(int n, const SCALAR *A, SCALAR *E) {
+  SCALAR X[4 * MAXD * MAXD], T[4 * MAXD * MAXD], U[4 * MAXD * MAXD];
+  double nrm = 0;
+  for (int j = 0; j < n; ++j) {
+    double c = 0;
+    for (int i = 0; i < n; ++i) c += S_ABS(A[i * n + j]);
+    if (c > nrm) nrm = c;
+  }
+  int r = 0;
+  while (nrm > 0.5 && r < 200) {
+    nrm *= 0.5;
+    ++r;
+  }
+  double sc = ldexp(1.0, -r);
+  for (int i = 0; i < n * n; ++i) X[i] = A[i] * sc;
+  for (int i = 0; i < n * n; ++i) {
+    E[i] = (i % (n + 1) == 0) ? 1.0 : 0.0;
+    T[i] = E[i];
+  }
+  for (int k = 1; k <= 24; ++k) {
+    SFX(matmul)(n, T, X, U);
+    for (int i = 0; i < n * n; ++i) {
+      T[i] = U[i] / (double)k;
+      E[i] += T[i];
+    }
+  }
+  for (int s = 0; s < r; ++s) {
+    SFX(matmul)(n, E, E, U);
+    memcpy(E, U, sizeof(SCALAR) * n * n);
+  }
+}
+
+/* Transition Phi~(dt) and process noise Q~(dt) of the augmented model.
+ * Van Loan (Eq. Q_from_vanloan): with C = [[-F~, L~QcL~^T], [0, F~^T]] dt,
+ * exp(C) = [[F2, G2], [0, F3]], Phi~ = F3^T and Q~ = F3^T G2.
+ * The exponential of C grows like exp(|F| dt), which the paper notes is
+ * unusable for long gaps (Section 2.2.2, Section 3.2).  So Van Loan is applied
+ * to h = dt / 2^s with ||F~|| h <= 1/2 and the result is doubled s times with
+ * the exact semigroup identities of Eq. sde_sol:
+ *   Phi~(2h) = Phi~(h)^2,  Q~(2h) = Phi~(h) Q~(h) Phi~(h)^T + Q~(h). */
+static void SFX(discretize)(const model_t *M, const SCALAR *F, const SCALAR *LQL, double dt,
+                            SCALAR *Phi, SCALAR *Q) {
+  const int D = M->dim, D2 = 2 * M->dim;
+  for (int i = 0; i < D * D; ++i) {
+    Phi[i] = (i % (D + 1) == 0) ? 1.0 : 0.0;
+    Q[i] = 0;
+  }
+  if (dt == 0.0) return;
+  double nrm = 0;
+  for (int j = 0; j < D; ++j) {
+    double c = 0;
+    for (int i = 0; i < D; ++i) c += S_ABS(F[i * D + j]);
+    if (c > nrm) nrm = c;
+  }
+  int s = 0;
+  double h = dt;
+  while (nrm * h > 0.5 && s < 400) {
+    h *= 0.5;
+    ++s;
+  }
+  SCALAR C[4 * MAXD * MAXD], E[4 * MAXD * MAXD], T[MAXD * MAXD], U[MAXD * MAXD];
+  for (int i = 0; i < D2 * D2; ++i) C[i] = 0;
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) {
+      C[i * D2 + j] = -F[i * D + j] * h;
+      C[i * D2 + D + j] = LQL[i * D + j] * h;
+      C[(D + i) * D2 + D + j] = F[j * D + i] * h;
+    }
+  SFX(expm)(D2, C, E);
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) Phi[i * D + j] = E[(D + j) * D2 + D + i]; /* F3^T */
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) {
+      SCALAR acc = 0;
+      for (int k = 0; k < D; ++k) acc += E[(D + k) * D2 + D + i] * E[k * D2 + D + j];
+      Q[i * D + j] = acc; /* F3^T G2 */
+    }
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < i; ++j) {
+      SCALAR a = 0.5 * (Q[i * D + j] + Q[j * D + i]);
+      Q[i * D + j] = a;
+      Q[j * D + i] = a;
+    }
+  for (int it = 0; it < s; ++it) {
+    /* Q <- Phi Q Phi^T + Q */
+    SFX(matmul)(D, Phi, Q, T);
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j <= i; ++j) {
+        SCALAR acc = 0;
+        for (int k = 0; k < D; ++k) acc += T[i * D + k] * Phi[j * D + k];
+        U[i * D + j] = acc + Q[i * D + j];
+        U[j * D + i] = U[i * D + j];
+      }
+    memcpy(Q, U, sizeof(SCALAR) * D * D);
+    SFX(matmul)(D, Phi, Phi, T);
+    memcpy(Phi, T, sizeof(SCALAR) * D * D);
+  }
+}
+
+/* Initial covariance P0 = blkdiag(P_inf, I) (Section 3.2.3, final paragraph). */
+static void SFX(initial_cov)(const model_t *M, const SCALAR *w0, const SCALAR *var, SCALAR *P) {
+  const int D = M->dim;
+  for (int i = 0; i < D * D; ++i) P[i] = 0;
+  for (int t = 0; t < M->n_terms; ++t) {
+    P[(2 * t) * D + 2 * t] = var[t];
+    P[(2 * t + 1) * D + 2 * t + 1] = var[t] * w0[t] * w0[t];
+  }
+  for (int i = 2 * M->n_terms; i < D; ++i) P[i * D + i] = 1.0;
+}
+
+/* Sequential integrated Kalman filter and log-likelihood.
+ * Predict with Phi~, Q~ (Eq. integrated_kalman_pred); at an exposure start
+ * apply the reset R_j of that exposure's slot (Eq. integrated_kalman_update,
+ * Section 3.2.3); at an exposure end update with H~ = e_z / delta
+ * (Eqs. H_aug, kalman_update) and add the term of Eq. loglikelihood.
+ * The covariance update uses the Joseph form, which is algebraically equal
+ * to P - K S K^T.  Summation is Neumaier-compensated. */
+static int SFX(filter)(const model_t *M, const SCALAR *th, int64_t n_ev, const double *t_ev,
+                       const int32_t *kind, const int32_t *slot, const double *y_ev,
+                       const double *r0_ev, const double *invd_ev, SCALAR *ll_out, double *dumpP,
+                       double *dumpS) {
+  const int D = M->dim;
+  SCALAR w0[MAXT], q[MAXT], var[MAXT], s2;
+  SCALAR F[MAXD * MAXD], LQL[MAXD * MAXD], Phi[MAXD * MAXD], Qd[MAXD * MAXD];
+  SCALAR P[MAXD * MAXD], T[MAXD * MAXD], A[MAXD * MAXD];
+  SCALAR m[MAXD], mt[MAXD], h[MAXD], u[MAXD], K[MAXD];
+  SFX(term_params)(M, th, w0, q, var, &s2);
+  SFX(build_F)(M, w0, q, var, F, LQL);
+  SFX(initial_cov)(M, w0, var, P);
+  for (int i = 0; i < D; ++i) m[i] = 0;
+  SCALAR sum = 0, comp = 0;
+  double tprev = n_ev > 0 ? t_ev[0] : 0.0;
+  int64_t n_end = 0;
+  for (int64_t k = 0; k < n_ev; ++k) {
+    double dt = t_ev[k] - tprev;
+    tprev = t_ev[k];
+    if (dt < 0) return 2;
+    SFX(discretize)(M, F, LQL, dt, Phi, Qd);
+    for (int i = 0; i < D; ++i) {
+      SCALAR acc = 0;
+      for (int j = 0; j < D; ++j) acc += Phi[i * D + j] * m[j];
+      mt[i] = acc;
+    }
+    memcpy(m, mt, sizeof(SCALAR) * D);
+    SFX(matmul)(D, Phi, P, T);
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j <= i; ++j) {
+        SCALAR acc = 0;
+        for (int kk = 0; kk < D; ++kk) acc += T[i * D + kk] * Phi[j * D + kk];
+        P[i * D + j] = acc + 0.5 * (Qd[i * D + j] + Qd[j * D + i]);
+        P[j * D + i] = P[i * D + j];
+      }
+    const int sj = slot[k];
+    if (sj < 0 || sj >= M->n_slots) return 3;
+    if (kind[k] == 0) {
+      /* exposure start: zero this slot's integral state(s) */
+      for (int t = 0; t < M->n_zper; ++t) {
+        int z = zindex(M, sj, t);
+        m[z] = 0;
+        for (int i = 0; i < D; ++i) {
+          P[z * D + i] = 0;
+          P[i * D + z] = 0;
+        }
+      }
+    } else {
+      for (int i = 0; i < D; ++i) h[i] = 0;
+      for (int t = 0; t < M->n_zper; ++t) h[zindex(M, sj, t)] = invd_ev[k];
+      SCALAR Sv = r0_ev[k] + s2, hm = 0;
+      for (int i = 0; i < D; ++i) {
+        SCALAR acc = 0;
+        for (int j = 0; j < D; ++j) acc += P[i * D + j] * h[j];
+        u[i] = acc;
+        Sv += h[i] * acc;
+        hm += h[i] * m[i];
+      }
+      SCALAR v = y_ev[k] - hm;
+      SCALAR r = r0_ev[k] + s2;
+      for (int i = 0; i < D; ++i) {
+        K[i] = u[i] / Sv;
+        m[i] += K[i] * v;
+      }
+      /* Joseph form: (I - K h^T) P (I - K h^T)^T + K r K^T */
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) A[i * D + j] = (i == j ? 1.0 : 0.0) - K[i] * h[j];
+      SFX(matmul)(D, A, P, T);
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j <= i; ++j) {
+          SCALAR acc = 0;
+          for (int kk = 0; kk < D; ++kk) acc += T[i * D + kk] * A[j * D + kk];
+          P[i * D + j] = acc + K[i] * r * K[j];
+          P[j * D + i] = P[i * D + j];
+        }
+      SCALAR term = -0.5 * (S_LOG(TWO_PI * Sv) + v * v / Sv);
+      SCALAR tt = sum + term;
+      if (S_ABS(sum) >= S_ABS(term))
+        comp += (sum - tt) + term;
+      else
+        comp += (term - tt) + sum;
+      sum = tt;
+      if (dumpS) dumpS[n_end] = S_RE(Sv);
+      ++n_end;
+    }
+    if (dumpP)
+      for (int i = 0; i < D * D; ++i) dumpP[k * D * D + i] = S_RE(P[i]);
+  }
+  *ll_out = sum + comp;
+  return 0;
+}
