@@ -1,0 +1,369 @@
+"""Benchmark: measurements/s of the batched FP32 log-likelihood + gradient.
+
+Workload (default ``c4``): 1024 independent series, N ~ U{2000..20000}
+exposures each (11.29M measurements, 22.6M events), kernel = sum of two SHO
+terms with one integral state per term (augmented dimension 6), per-series
+hyperparameters; one step = log-likelihood and adjoint gradient w.r.t. the 7
+natural parameters of every series, inputs resident in HBM.  The event stream
+(~292 MB) is larger than the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank takes a longest-processing-time share of
+the series (no collective on the data path) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "measurements/sec for loglik+grad (batched FP32 vs plain FP64 filter, 1 GB300)"
+UNIT = "measurements/s"
+
+# FP32 FLOPs per event that the method itself needs for one loglik+grad pass
+# of the dominant kernel (the reverse-time gradient): the forward filter once
+# plus its reverse sweep, excluding the recomputation passes.  Taken from ncu
+# instruction counts (see profiles/); used for roofline.achieved.
+ALG_FLOPS_PER_EVENT = {"c4": 3600.0}
+# Algorithmic bytes per measurement the gradient kernel must read: two events
+# (4 B gap + 1 B tag each) and one 16 B measurement record, read on the
+# forward pass and again on the reverse sweep, plus checkpoint traffic.
+ALG_BYTES_PER_MEAS = {"c4": 2 * (2 * 5 + 16)}
+FP32_LANES_PER_SM = 128
+N_SMS = 152
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload(name):
+    import synth
+    if name == "c4":
+        return synth.c4()
+    if name == "c2":
+        return synth.c2()
+    if name == "c3":
+        return synth.c3()
+    if name == "c5":
+        return synth.c5()
+    if name == "c4s":  # small variant for quick checks
+        return synth.c4(n_series=64, scale=0.25)
+    raise ValueError(name)
+
+
+def lpt_shards(counts, world):
+    """Longest-processing-time assignment of series to ranks."""
+    order = np.argsort(-np.asarray(counts), kind="stable")
+    loads = np.zeros(world)
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = int(np.argmin(loads))
+        parts[r].append(int(i))
+        loads[r] += counts[i]
+    return [sorted(p) for p in parts]
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    mhz.append(float(parts[1]))
+                    mx = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not mhz:
+            return None
+        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def oracle_sample_rate(wl, budget_s, n_proc, prefix_meas):
+    """The FP64 oracle (log-likelihood + complex-step gradient) on host cores.
+
+    Sample: the first ``prefix_meas`` measurements of consecutive series, one
+    job per process, repeated until ``budget_s`` of wall time has passed.
+    Returns (measurements/s, cores, description)."""
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    jobs = []
+    for i in range(wl.n_series):
+        ts, te, y, ye, inst = wl.series(i)
+        k = min(prefix_meas, len(ts))
+        th = wl.theta[i] if wl.theta_per_series else wl.theta[0]
+        jobs.append((wl.terms, wl.layout, (ts[:k], te[:k], y[:k], ye[:k],
+                                           None if inst is None else inst[:k]), th, True))
+    done = 0
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(n_proc) as pool:
+        j = 0
+        while time.perf_counter() - t0 < budget_s and j < len(jobs):
+            batch = jobs[j:j + n_proc]
+            pool.map(oracle._series_job, batch)
+            done += sum(len(b[2][0]) for b in batch)
+            j += n_proc
+    el = time.perf_counter() - t0
+    return done / el, n_proc, (f"oracle loglik + complex-step gradient, FP64, first "
+                               f"{prefix_meas} measurements of {j} series, "
+                               f"{n_proc} processes, {el:.1f} s")
+
+
+def run_reference(args):
+    """Reference arm: the oracle on host cores, same metric and config."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(args.workload)
+    n_proc = max(1, min(os.cpu_count() or 1, 16))
+    budget = max(2.0, min(8.0, 150.0 / max(args.steps + args.warmup, 1)))
+    for _ in range(args.warmup):
+        oracle_sample_rate(wl, 0.5, n_proc, 64)
+    rates = []
+    desc = ""
+    for _ in range(args.steps):
+        r, cores, desc = oracle_sample_rate(wl, budget, n_proc, 200)
+        rates.append(r)
+    v = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_series": wl.n_series, "n_meas": wl.n_meas},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": n_proc, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2601_02527_gb300 as gp
+    from paper_2601_02527_gb300 import build as gbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or world == 1:
+        gbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    wl_full = workload(args.workload)
+    counts = np.diff(wl_full.offsets)
+    total_meas = int(wl_full.n_meas)
+    wl = wl_full.subset(lpt_shards(counts, world)[rank]) if world > 1 else wl_full
+    # CPU baseline first: its process pool is spawned before the first GPU call
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, cores, desc = oracle_sample_rate(wl, args.cpu_budget,
+                                               max(1, min(os.cpu_count() or 1, 16)), 200)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    t0 = time.perf_counter()
+    model = gp.Model.from_workload(wl, chunk_len=args.chunk_len)
+    build_s = time.perf_counter() - t0
+    theta = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
+    n_out = model.info["n_series"]
+    ll = torch.empty(n_out, dtype=torch.float64, device="cuda")
+    g = torch.empty(n_out, model.n_params, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        model.loglik_grad(theta, out=ll, grad=g)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    model.set_timing(True)
+    model.get_timing()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        model.loglik_grad(theta, out=ll, grad=g)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    phases = model.get_timing()
+    model.set_timing(False)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ok = bool(torch.isfinite(ll).all().item()) and model.last_error()[0] < 0
+    value = total_meas / (ms / 1e3)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+    # dominant kernel
+    dom = max(phases, key=lambda k: phases[k][0])
+    dom_ms, dom_n = phases[dom]
+    dom_avg = dom_ms / max(dom_n, 1)
+    peaks, src = load_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    n_events = 2 * wl.n_meas
+    alg_flops = ALG_FLOPS_PER_EVENT.get(args.workload, 3600.0) * n_events
+    achieved = alg_flops / (dom_avg / 1e3) / 1e12
+    alg_bytes = ALG_BYTES_PER_MEAS.get(args.workload, 52) * wl.n_meas
+    hbm_ach = alg_bytes / (dom_avg / 1e3) / 1e9
+    roofline = {"bound": "alu", "kernel": f"k_grad ({dom})" if dom == "grad" else dom,
+                "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": f"FP32 FMA: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                               f"{sm_mhz:.0f} MHz",
+                "hbm_view": {"achieved_gbs": hbm_ach, "peak_gbs": peaks.get("hbm_gbs"),
+                             "frac": hbm_ach / peaks.get("hbm_gbs", 6800.0),
+                             "peak_source": src},
+                "phase_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in phases.items()
+                                      if v[1]}}
+    # end to end through the host-buffer C-ABI call: event stream + theta up, results down
+    e2e = None
+    if not args.no_e2e:
+        th_host = wl.theta.astype(np.float32)
+        model.loglik_grad_host(th_host, reupload_events=True)
+        k2 = max(2, min(args.steps, 5))
+        t1 = time.perf_counter()
+        for _ in range(k2):
+            model.loglik_grad_host(th_host, reupload_events=True)
+        el = (time.perf_counter() - t1) / k2
+        h2d = 2 * wl.n_meas * 5 + wl.n_meas * 16 + th_host.nbytes
+        d2h = n_out * 8 + n_out * model.n_params * 4
+        e2e = {"value": total_meas / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": el * 1e3}
+    # the plain FP64 per-series filter and the FP32 log-likelihood alone
+    extra = {}
+    if not args.no_fp64:
+        m64 = gp.Model.from_workload(wl, precision=64)
+        out64 = torch.empty(n_out, dtype=torch.float64, device="cuda")
+        m64.loglik(theta, out=out64)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m64.loglik(theta, out=out64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b)
+        extra["plain_fp64_filter"] = {"value": wl.n_meas / (ms64 / 1e3), "unit": UNIT,
+                                      "ms_per_step": ms64, "work": "loglik only"}
+        rel = (ll.cpu().numpy() - out64.cpu().numpy()) / np.abs(out64.cpu().numpy())
+        extra["fp32_vs_fp64_loglik_max_rel_err"] = float(np.max(np.abs(rel)))
+        extra["speedup_vs_plain_fp64"] = value / extra["plain_fp64_filter"]["value"]
+        del m64
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    model.loglik(theta, out=ll)
+    a.record(stream)
+    for _ in range(3):
+        model.loglik(theta, out=ll)
+    b.record(stream)
+    torch.cuda.synchronize()
+    extra["fp32_loglik_only"] = {"value": wl.n_meas / (a.elapsed_time(b) / 3 / 1e3),
+                                 "unit": UNIT}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n_series": int(wl_full.n_series),
+                       "n_meas": total_meas, "n_events": 2 * total_meas,
+                       "state_dim": model.info["state_dim"], "n_params": model.n_params,
+                       "chunk_len": args.chunk_len, "n_chunks": model.info["n_chunks"],
+                       "l2": "inputs larger than L2 (event stream ~292 MB > 129 MB)",
+                       "parallelism": f"series-sharded x{world}", "build_s": build_s},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 4 * args.steps, "clocks": clk, "ok": ok, "extra": extra}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c4")
+    ap.add_argument("--chunk-len", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * gpss.h -- C ABI of libgpss: the log-likelihood (and its gradient) of a
+ * Gaussian process observed through integrated, possibly overlapping
+ * exposures, computed on the GPU by a Kalman filter over the augmented
+ * state-space model of Rubenzahl, Hattori et al., "Scalable Gaussian
+ * Processes for Integrated and Overlapping Measurements via Augmented
+ * State-Space Models" (arXiv 2601.02527).
+ *
+ * The model (Section 3.2 of the paper): measurement n averages the latent
+ * process f = H x over its exposure [t_start[n], t_end[n]],
+ *     y_n = (1/delta_n) * int_{t_start}^{t_end} f(t) dt + eps_n,
+ *     delta_n = t_end - t_start,  eps_n ~ N(0, yerr_n^2 + s^2),
+ * where x is the state of a sum of stochastically driven damped harmonic
+ * oscillator (SHO) and Matern-3/2 terms (Appendix B, Appendix C.1) and s is a
+ * white-noise standard deviation.  The state is augmented with one integral
+ * state per instrument slot (Section 3.2.3), reset at each exposure start and
+ * read at each exposure end.  The returned value is the log marginal
+ * likelihood of Eq. loglikelihood.
+ *
+ * Conventions
+ *  - Every call returns a gp_ss_status; no C++ exception crosses the ABI.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    device memory of the device that was current when the model was built.
+ *  - Compute calls are asynchronous on the caller's stream (a cudaStream_t
+ *    passed as void*, NULL = legacy default stream).  Numeric failures found
+ *    on the device (a non-positive or non-finite innovation variance) are
+ *    reported by gp_ss_last_error_series() after the stream has synchronised.
+ *  - Scratch memory is taken from the stream-ordered allocator
+ *    (cudaMallocAsync) on the caller's stream and released before the call
+ *    returns, so calls on different streams may share one model.
+ *  - Hyperparameters are natural parameters, one row of n_params floats per
+ *    set: per term (sigma, omega0, Q) for GP_SS_TERM_SHO (Q >= 1/2) or
+ *    (sigma, ell) for GP_SS_TERM_MATERN32, in the order of the kernel spec,
+ *    then the white-noise sd s.  n_params = 3*#SHO + 2*#Matern + 1.
+ */
+#ifndef GPSS_H
+#define GPSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gp_ss_model gp_ss_model; /* opaque; immutable after build */
+
+typedef enum {
+  GP_SS_OK = 0,
+  GP_SS_EINVAL = 1,        /* bad argument: non-positive or non-finite exposure, NULL pointer, ... */
+  GP_SS_EUNSORTED = 2,     /* series offsets not non-decreasing */
+  GP_SS_ESELFOVERLAP = 3,  /* one instrument's exposures overlap each other */
+  GP_SS_EUNSUPPORTED = 4,  /* model shape not compiled (too many terms/slots), Q < 1/2 */
+  GP_SS_ENOMEM = 5,        /* device or host allocation failed */
+  GP_SS_ECUDA = 6,         /* a CUDA runtime call failed */
+  GP_SS_ENUMERIC = 7,      /* S <= 0 or non-finite value met on the device */
+  GP_SS_ETIMEOUT = 8       /* a bounded device wait gave up */
+} gp_ss_status;
+
+typedef enum {
+  GP_SS_TERM_SHO = 1,      /* (sigma, omega0, Q): Appendix B, Eq. sho_kernel */
+  GP_SS_TERM_MATERN32 = 2  /* (sigma, ell) == SHO with Q = 1/2, omega0 = sqrt(3)/ell */
+} gp_ss_term;
+
+typedef struct {
+  int n_terms;          /* 1..2 */
+  const int *terms;     /* host [n_terms] gp_ss_term values */
+  int integral_layout;  /* 0: one integral state per slot integrating H x (Section 3.2.3);
+                           1: one integral state per term and slot; the measurement reads
+                              their sum.  Both give the same likelihood. */
+} gp_ss_kernel_spec;
+
+typedef struct {
+  int precision;          /* 32 (default): FP32 filter with FP64 log-det/likelihood sums;
+                             64: plain FP64 per-series filter (log-likelihood only) */
+  int schedule;           /* 0 auto, 1 one chunk per series, 2 chunked parallel-in-time */
+  int threads_per_series; /* reserved, must be 0 or 1 */
+  int chunk_len;          /* events per chunk of the parallel-in-time schedule, 0 = auto */
+  int ckpt_interval;      /* reserved for the gradient's recomputation segment, 0 = auto */
+  int debug_checks;       /* nonzero: extra host-side validation */
+} gp_ss_options;
+
+/* Build a model from exposures (Section 3.2: two events per exposure, reset
+ * at the start, measurement at the end; Section 3.2.3: one integral state per
+ * instrument slot).
+ *   spec            host, kernel structure
+ *   n_series        number of independent series (>= 1)
+ *   series_offsets  host int64 [n_series+1], non-decreasing, offsets[0] = 0;
+ *                   series i owns measurements [offsets[i], offsets[i+1])
+ *   t_start, t_end  host f64 [N] exposure windows (t_end > t_start, finite)
+ *   y, yerr         host f32 [N] exposure-averaged values and their sd
+ *   instrument      host i32 [N] slot label per measurement (>= 0, one label
+ *                   must not overlap itself: t_end <= next t_start), or NULL
+ *                   for greedy assignment (lowest free slot in start order)
+ *   opts            host, may be NULL for defaults
+ *   out             receives the model; the caller frees it with gp_ss_free_model
+ * Events are ordered by time with every exposure end before any start at
+ * the same time, and time gaps are formed in FP64 before rounding to FP32.
+ * Inputs are copied; the model owns its device buffers.  Returns EINVAL,
+ * EUNSORTED, ESELFOVERLAP, EUNSUPPORTED (more than 3 slots, or a shape with
+ * augmented dimension above 7), ENOMEM or ECUDA on failure. */
+gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
+                               const int64_t *series_offsets, const double *t_start,
+                               const double *t_end, const float *y, const float *yerr,
+                               const int32_t *instrument, const gp_ss_options *opts,
+                               gp_ss_model **out);
+
+/* Log-likelihood (Eq. loglikelihood) for n_sets hyperparameter vectors.
+ *   theta             device f32 [n_sets * n_params], natural parameters
+ *   theta_per_series  1: n_sets == n_series, set i applies to series i;
+ *                     0: every set applies to every series
+ *   loglik_out        device f64 [n_series] (per-series mode) or
+ *                     [n_sets * n_series] (set-major) in the other mode */
+gp_ss_status gp_ss_loglik(const gp_ss_model *model, const float *theta, int n_sets,
+                          int theta_per_series, double *loglik_out, void *cuda_stream);
+
+/* Log-likelihood and its gradient with respect to the natural parameters,
+ * by a reverse-time adjoint of the filter (the paper states the likelihood
+ * only; Section 2.3 notes it feeds gradient-based optimisation).
+ *   grad_out   device f32 [n_out * n_params], same row order as loglik_out
+ *   dlogl_ddt  reserved, must be NULL */
+gp_ss_status gp_ss_loglik_grad(const gp_ss_model *model, const float *theta, int n_sets,
+                               int theta_per_series, double *loglik_out, float *grad_out,
+                               float *dlogl_ddt, void *cuda_stream);
+
+/* Same computations replayed from a CUDA graph captured on first use for
+ * this (model, pointers, n_sets, mode); a later call with other pointers
+ * re-captures.  The first call must not itself be made during a capture. */
+gp_ss_status gp_ss_loglik_batched(const gp_ss_model *model, const float *theta, int n_sets,
+                                  int theta_per_series, double *loglik_out, void *cuda_stream);
+gp_ss_status gp_ss_loglik_grad_batched(const gp_ss_model *model, const float *theta,
+                                       int n_sets, int theta_per_series, double *loglik_out,
+                                       float *grad_out, void *cuda_stream);
+
+/* Host-buffer variant of gp_ss_loglik_grad for end-to-end use: copies theta
+ * (host f32) to the device, optionally re-uploads the model's event stream
+ * from its pinned host copy (reupload_events != 0), computes, and copies the
+ * results back into host buffers before returning (synchronous). */
+gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *model, const float *theta_host,
+                                    int n_sets, int theta_per_series, double *loglik_host,
+                                    float *grad_host, int reupload_events, void *cuda_stream);
+
+/* The per-step discretisation on its own: for n gaps dt (device f32 [n]) and
+ * one parameter row theta (device f32 [n_params]), write the augmented
+ * transition Phi~(dt) (Eq. phiaug with the block layout of Section 3.2.3) and
+ * process noise Q~(dt) (Eq. Q_aug) as dense row-major d x d matrices,
+ * d = 2*n_terms + n_slots*(layout ? n_terms : 1), into phi_out and q_out
+ * (device f32 [n * d * d] each).  Same arithmetic as inside the filters. */
+gp_ss_status gp_ss_discretize(const gp_ss_kernel_spec *spec, int n_slots, const float *theta,
+                              const float *dt, int n, float *phi_out, float *q_out,
+                              void *cuda_stream);
+
+/* Model facts: any output pointer may be NULL. */
+gp_ss_status gp_ss_model_info(const gp_ss_model *model, int *n_series, int64_t *n_meas,
+                              int64_t *n_events, int *n_params, int *state_dim,
+                              int *n_slots, int *n_chunks);
+
+/* Re-plan the parallel-in-time chunks (events per chunk); 0 = auto. */
+gp_ss_status gp_ss_set_chunk_len(gp_ss_model *model, int chunk_len);
+
+/* After the stream of the last compute call has synchronised: the first
+ * series (output row) with a device-side failure and its code, or -1/GP_SS_OK. */
+gp_ss_status gp_ss_last_error_series(const gp_ss_model *model, int64_t *first_bad_series,
+                                     gp_ss_status *code);
+
+/* Per-phase device timing, for profiling.  With enable != 0, later direct
+ * compute calls (not graph replays, not calls made during a stream capture)
+ * record a CUDA event pair on the caller's stream around each kernel phase.
+ * gp_ss_get_timing waits for the recorded events, writes the accumulated
+ * milliseconds and launch counts per phase into ms[5] / launches[5]
+ * (0 chunk elements, 1 cross-chunk combination, 2 reverse-time gradient,
+ * 3 result conversion, 4 plain per-series filter) and clears the record. */
+gp_ss_status gp_ss_set_timing(gp_ss_model *model, int enable);
+gp_ss_status gp_ss_get_timing(gp_ss_model *model, double *ms, int64_t *launches);
+
+void gp_ss_free_model(gp_ss_model *model);
+const char *gp_ss_status_string(gp_ss_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPSS_H */

@@ -1,0 +1,307 @@
+"""GB300-native log-likelihood of Gaussian processes with integrated, possibly
+overlapping exposures (Rubenzahl, Hattori et al., arXiv 2601.02527).
+
+This package is a thin binding over ``libgpss.so`` (CUDA, sm_103a; C ABI in
+``include/gpss.h``): arguments are marshalled here and every step of the
+computation runs in the library's kernels.  PyTorch supplies device memory and
+streams.  There is no CPU fallback: if the library is missing or no CUDA
+device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgpss.so")
+
+SHO = 1
+MATERN32 = 2
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "series offsets not sorted",
+          3: "an instrument's exposures overlap each other",
+          4: "unsupported model shape or parameter regime", 5: "out of memory",
+          6: "CUDA runtime error", 7: "non-positive or non-finite innovation variance",
+          8: "bounded device wait timed out"}
+
+# every function declared in include/gpss.h
+EXPORTS = ["gp_ss_build_model", "gp_ss_loglik", "gp_ss_loglik_grad", "gp_ss_loglik_batched",
+           "gp_ss_loglik_grad_batched", "gp_ss_loglik_grad_host", "gp_ss_model_info",
+           "gp_ss_set_chunk_len", "gp_ss_last_error_series", "gp_ss_free_model",
+           "gp_ss_status_string", "gp_ss_discretize", "gp_ss_set_timing", "gp_ss_get_timing"]
+
+PHASES = ["elem", "scan", "grad", "convert", "plain"]
+
+
+class GPSSError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)} (status {code})")
+
+
+class _KernelSpec(ctypes.Structure):
+    _fields_ = [("n_terms", ctypes.c_int), ("terms", ctypes.POINTER(ctypes.c_int)),
+                ("integral_layout", ctypes.c_int)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int),
+                ("threads_per_series", ctypes.c_int), ("chunk_len", ctypes.c_int),
+                ("ckpt_interval", ctypes.c_int), ("debug_checks", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libgpss.so (built by ``paper_2601_02527_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libgpss.so not found at {p}; build it with "
+                           "`python -m paper_2601_02527_gb300.build`")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    P = ctypes.POINTER
+    lib.gp_ss_build_model.argtypes = [P(_KernelSpec), i32, vp, vp, vp, vp, vp, vp, P(_Options),
+                                      P(vp)]
+    lib.gp_ss_loglik.argtypes = [vp, vp, i32, i32, vp, vp]
+    lib.gp_ss_loglik_grad.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp]
+    lib.gp_ss_loglik_batched.argtypes = [vp, vp, i32, i32, vp, vp]
+    lib.gp_ss_loglik_grad_batched.argtypes = [vp, vp, i32, i32, vp, vp, vp]
+    lib.gp_ss_loglik_grad_host.argtypes = [vp, vp, i32, i32, vp, vp, i32, vp]
+    lib.gp_ss_model_info.argtypes = [vp, P(i32), P(i64), P(i64), P(i32), P(i32), P(i32), P(i32)]
+    lib.gp_ss_set_chunk_len.argtypes = [vp, i32]
+    lib.gp_ss_last_error_series.argtypes = [vp, P(i64), P(i32)]
+    lib.gp_ss_free_model.argtypes = [vp]
+    lib.gp_ss_free_model.restype = None
+    lib.gp_ss_status_string.argtypes = [i32]
+    lib.gp_ss_status_string.restype = ctypes.c_char_p
+    lib.gp_ss_discretize.argtypes = [P(_KernelSpec), i32, vp, vp, i32, vp, vp, vp]
+    lib.gp_ss_set_timing.argtypes = [vp, i32]
+    lib.gp_ss_get_timing.argtypes = [vp, vp, vp]
+    _lib = lib
+    return lib
+
+
+def _check(code, what):
+    if code != 0:
+        raise GPSSError(code, what)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _spec(terms, layout):
+    arr = (ctypes.c_int * len(terms))(*[int(t) for t in terms])
+    return _KernelSpec(len(terms), arr, int(layout)), arr
+
+
+def n_params_for(terms) -> int:
+    return sum(3 if int(t) == SHO else 2 for t in terms) + 1
+
+
+class Model:
+    """An event-stream model on the current CUDA device (gp_ss_build_model).
+
+    ``offsets`` (int64, n_series+1) delimits the series in the concatenated
+    per-measurement arrays ``t_start``, ``t_end`` (float64), ``y``, ``yerr``
+    (float32) and optional ``instrument`` (int32 slot labels).
+    """
+
+    def __init__(self, terms, offsets, t_start, t_end, y, yerr, instrument=None, layout=0,
+                 precision=32, schedule=0, chunk_len=0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        lib = load_library()
+        self.terms = [int(t) for t in terms]
+        self.layout = int(layout)
+        self.n_params = n_params_for(self.terms)
+        offs = np.ascontiguousarray(offsets, np.int64)
+        ts = np.ascontiguousarray(t_start, np.float64)
+        te = np.ascontiguousarray(t_end, np.float64)
+        yy = np.ascontiguousarray(y, np.float32)
+        ye = np.ascontiguousarray(yerr, np.float32)
+        inst = None if instrument is None else np.ascontiguousarray(instrument, np.int32)
+        spec, self._spec_arr = _spec(self.terms, self.layout)
+        opts = _Options(int(precision), int(schedule), 0, int(chunk_len), 0, 0)
+        h = ctypes.c_void_p()
+        self.device = torch.cuda.current_device()
+        rc = lib.gp_ss_build_model(ctypes.byref(spec), len(offs) - 1, offs.ctypes.data,
+                                   ts.ctypes.data, te.ctypes.data, yy.ctypes.data,
+                                   ye.ctypes.data, None if inst is None else inst.ctypes.data,
+                                   ctypes.byref(opts), ctypes.byref(h))
+        _check(rc, "gp_ss_build_model")
+        self._h = h
+        self._lib = lib
+        self.info = self._info()
+
+    @classmethod
+    def from_workload(cls, wl, **kw):
+        return cls(wl.terms, wl.offsets, wl.t_start, wl.t_end, wl.y, wl.yerr, wl.instrument,
+                   layout=wl.layout, **kw)
+
+    def _info(self):
+        ns, nd, np_, sd, sl, nc = (ctypes.c_int() for _ in range(6))
+        nm, ne = ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib.gp_ss_model_info(self._h, ctypes.byref(ns), ctypes.byref(nm),
+                                          ctypes.byref(ne), ctypes.byref(np_), ctypes.byref(sd),
+                                          ctypes.byref(sl), ctypes.byref(nc)), "gp_ss_model_info")
+        return dict(n_series=ns.value, n_meas=nm.value, n_events=ne.value,
+                    n_params=np_.value, state_dim=sd.value, n_slots=sl.value,
+                    n_chunks=nc.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gp_ss_free_model(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def n_out(self, theta, per_series):
+        n_sets = theta.shape[0]
+        return self.info["n_series"] if per_series else n_sets * self.info["n_series"]
+
+    def _theta(self, theta):
+        import torch
+        if not (isinstance(theta, torch.Tensor) and theta.is_cuda):
+            raise TypeError("theta must be a CUDA tensor")
+        th = theta.detach().to(torch.float32).contiguous()
+        if th.dim() != 2 or th.shape[1] != self.n_params:
+            raise ValueError(f"theta must be [n_sets, {self.n_params}]")
+        return th
+
+    def loglik(self, theta, per_series=True, out=None, stream=None, batched=False):
+        """Log-likelihood per output row (float64 CUDA tensor)."""
+        import torch
+        th = self._theta(theta)
+        n = self.n_out(th, per_series)
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=th.device)
+        f = self._lib.gp_ss_loglik_batched if batched else self._lib.gp_ss_loglik
+        _check(f(self._h, th.data_ptr(), th.shape[0], int(bool(per_series)), out.data_ptr(),
+                 _stream_ptr(stream)), "gp_ss_loglik")
+        return out
+
+    def loglik_grad(self, theta, per_series=True, out=None, grad=None, stream=None,
+                    batched=False):
+        """(log-likelihood [n_out] float64, gradient [n_out, n_params] float32)."""
+        import torch
+        th = self._theta(theta)
+        n = self.n_out(th, per_series)
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=th.device)
+        if grad is None:
+            grad = torch.empty(n, self.n_params, dtype=torch.float32, device=th.device)
+        if batched:
+            rc = self._lib.gp_ss_loglik_grad_batched(self._h, th.data_ptr(), th.shape[0],
+                                                     int(bool(per_series)), out.data_ptr(),
+                                                     grad.data_ptr(), _stream_ptr(stream))
+        else:
+            rc = self._lib.gp_ss_loglik_grad(self._h, th.data_ptr(), th.shape[0],
+                                             int(bool(per_series)), out.data_ptr(),
+                                             grad.data_ptr(), None, _stream_ptr(stream))
+        _check(rc, "gp_ss_loglik_grad")
+        return out, grad
+
+    def loglik_grad_host(self, theta, per_series=True, reupload_events=False, stream=None):
+        """Host-buffer variant: numpy in, numpy out (synchronous)."""
+        th = np.ascontiguousarray(theta, np.float32)
+        n = self.info["n_series"] if per_series else th.shape[0] * self.info["n_series"]
+        ll = np.empty(n, np.float64)
+        g = np.empty((n, self.n_params), np.float32)
+        _check(self._lib.gp_ss_loglik_grad_host(self._h, th.ctypes.data, th.shape[0],
+                                                int(bool(per_series)), ll.ctypes.data,
+                                                g.ctypes.data, int(bool(reupload_events)),
+                                                _stream_ptr(stream)), "gp_ss_loglik_grad_host")
+        return ll, g
+
+    def set_chunk_len(self, chunk_len: int):
+        _check(self._lib.gp_ss_set_chunk_len(self._h, int(chunk_len)), "gp_ss_set_chunk_len")
+        self.info = self._info()
+
+    def set_timing(self, enable: bool):
+        _check(self._lib.gp_ss_set_timing(self._h, int(bool(enable))), "gp_ss_set_timing")
+
+    def get_timing(self):
+        """{phase: (total ms, launches)} since the last read (see gp_ss_get_timing)."""
+        ms = np.zeros(5, np.float64)
+        n = np.zeros(5, np.int64)
+        _check(self._lib.gp_ss_get_timing(self._h, ms.ctypes.data, n.ctypes.data),
+               "gp_ss_get_timing")
+        return {p: (float(ms[i]), int(n[i])) for i, p in enumerate(PHASES)}
+
+    def last_error(self):
+        """(first failing output row or -1, status code) of the last call."""
+        row, code = ctypes.c_int64(), ctypes.c_int32()
+        _check(self._lib.gp_ss_last_error_series(self._h, ctypes.byref(row), ctypes.byref(code)),
+               "gp_ss_last_error_series")
+        return row.value, code.value
+
+
+def discretize(terms, layout, n_slots, theta_row, dt, stream=None):
+    """Phi~(dt_k), Q~(dt_k) from the library's per-step discretisation kernel
+    (float32, [n, d, d] each) for a CUDA tensor ``dt`` and one parameter row."""
+    import torch
+    lib = load_library()
+    th = theta_row.to(torch.float32).contiguous()
+    dtt = dt.to(torch.float32).contiguous()
+    spec, _keep = _spec(terms, layout)
+    nz = 1 if (layout == 0 or len(terms) == 1) else len(terms)
+    d = 2 * len(terms) + n_slots * nz
+    phi = torch.empty(dtt.numel(), d, d, dtype=torch.float32, device=dtt.device)
+    q = torch.empty_like(phi)
+    _check(lib.gp_ss_discretize(ctypes.byref(spec), int(n_slots), th.data_ptr(), dtt.data_ptr(),
+                                dtt.numel(), phi.data_ptr(), q.data_ptr(), _stream_ptr(stream)),
+           "gp_ss_discretize")
+    return phi, q
+
+
+def _autograd_function():
+    import torch
+
+    class LogLikFunction(torch.autograd.Function):
+        """Sum-reducible log-likelihood with the adjoint gradient as backward."""
+
+        @staticmethod
+        def forward(ctx, theta, model, per_series):
+            ll, g = model.loglik_grad(theta, per_series=per_series)
+            ctx.save_for_backward(g)
+            ctx.per_series = per_series
+            ctx.n_sets = theta.shape[0]
+            ctx.n_series = model.info["n_series"]
+            return ll
+
+        @staticmethod
+        def backward(ctx, gout):
+            (g,) = ctx.saved_tensors
+            w = gout.to(torch.float32)[:, None] * g
+            if not ctx.per_series:
+                w = w.view(ctx.n_sets, ctx.n_series, -1).sum(1)
+            return w, None, None
+
+    return LogLikFunction
+
+
+_LLF = None
+
+
+def loglik(model: Model, theta, per_series=True):
+    """Differentiable log-likelihood (torch.autograd): rows as ``Model.loglik``."""
+    global _LLF
+    if _LLF is None:
+        _LLF = _autograd_function()
+    return _LLF.apply(theta, model, per_series)

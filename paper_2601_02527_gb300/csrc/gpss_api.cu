@@ -1,0 +1,848 @@
+// Host side of the libgpss C ABI: event building (Section 3.2 of arXiv
+// 2601.02527), validation, chunk planning, device buffers and dispatch.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "gpss.h"
+#include "gpss_kernels.cuh"
+
+namespace gpss {
+OpTable ops_1_1_0();
+OpTable ops_1_2_0();
+OpTable ops_1_3_0();
+OpTable ops_2_1_0();
+OpTable ops_2_2_0();
+OpTable ops_2_3_0();
+OpTable ops_2_1_1();
+
+__global__ void k_to_float(int n, const double *__restrict__ src, float *__restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (float)src[i];
+}
+}  // namespace gpss
+
+using gpss::OpTable;
+
+namespace {
+
+constexpr int kMaxSlots = 3;
+constexpr int kDefaultChunk = 256;
+
+template <class T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+};
+
+struct GraphKey {
+  int kind;
+  const void *theta;
+  int n_sets, per_series;
+  const void *out1, *out2;
+  cudaStream_t stream;
+  bool operator<(const GraphKey &o) const {
+    return std::tie(kind, theta, n_sets, per_series, out1, out2, stream) <
+           std::tie(o.kind, o.theta, o.n_sets, o.per_series, o.out1, o.out2, o.stream);
+  }
+};
+
+}  // namespace
+
+struct gp_ss_model {
+  int device = 0;
+  int n_series = 0, n_terms = 0, kinds[4] = {0, 0, 0, 0}, layout = 0, n_slots = 1;
+  int n_params = 0, precision = 32, schedule = 0;
+  int64_t n_meas = 0, n_events = 0;
+  OpTable ops{};
+  // host copies
+  std::vector<int64_t> ev_off, meas_off;
+  std::vector<uint8_t> tag;
+  float *h_dt = nullptr;  // host copies of the event stream (pinned when possible)
+  uint8_t *h_tag = nullptr;
+  float4 *h_meas = nullptr;
+  bool pinned = false;
+  // device event stream
+  int64_t *d_ev_off = nullptr, *d_meas_off = nullptr;
+  float *d_dt = nullptr;
+  uint8_t *d_tag = nullptr;
+  float4 *d_meas = nullptr;
+  double *d_dt64 = nullptr, *d_meas64 = nullptr;
+  // chunk plan
+  int chunk_len = 0, n_chunks = 0, max_chunk = 0;
+  int64_t *d_ch_ev0 = nullptr, *d_ch_meas0 = nullptr;
+  int32_t *d_ch_len = nullptr, *d_ch_series = nullptr, *d_ch_first = nullptr;
+  uint8_t *d_ch_flags = nullptr;
+  // device error flags of the last call
+  mutable std::mutex mu;
+  mutable int *d_err = nullptr;
+  mutable int err_cap = 0;
+  mutable int last_n_out = 0;
+  mutable std::map<GraphKey, cudaGraphExec_t> graphs;
+  // optional per-phase timing (event pairs around kernels of direct calls)
+  mutable bool timing = false;
+  mutable std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> timings;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool pick_ops(int n_terms, int n_slots, int layout, OpTable *o) {
+  if (n_terms == 1) {
+    if (n_slots == 1) *o = gpss::ops_1_1_0();
+    else if (n_slots == 2) *o = gpss::ops_1_2_0();
+    else if (n_slots == 3) *o = gpss::ops_1_3_0();
+    else return false;
+    return true;
+  }
+  if (n_terms == 2 && layout == 0) {
+    if (n_slots == 1) *o = gpss::ops_2_1_0();
+    else if (n_slots == 2) *o = gpss::ops_2_2_0();
+    else if (n_slots == 3) *o = gpss::ops_2_3_0();
+    else return false;
+    return true;
+  }
+  if (n_terms == 2 && layout == 1 && n_slots == 1) {
+    *o = gpss::ops_2_1_1();
+    return true;
+  }
+  return false;
+}
+
+template <class T>
+gp_ss_status dev_upload(T **dst, const T *src, size_t n) {
+  *dst = nullptr;
+  if (n == 0) n = 1;
+  if (cudaMalloc((void **)dst, n * sizeof(T)) != cudaSuccess) return GP_SS_ENOMEM;
+  if (src && cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return GP_SS_ECUDA;
+  return GP_SS_OK;
+}
+
+void free_model_buffers(gp_ss_model *m) {
+  void *dev[] = {m->d_ev_off, m->d_meas_off, m->d_dt, m->d_tag, m->d_meas, m->d_dt64, m->d_meas64,
+                 m->d_ch_ev0, m->d_ch_meas0, m->d_ch_len, m->d_ch_series, m->d_ch_first,
+                 m->d_ch_flags, m->d_err};
+  for (void *p : dev)
+    if (p) cudaFree(p);
+  void *hst[] = {m->h_dt, m->h_tag, m->h_meas};
+  for (void *p : hst)
+    if (p) {
+      if (m->pinned)
+        cudaFreeHost(p);
+      else
+        std::free(p);
+    }
+  for (auto &kv : m->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto &t : m->timings) {
+    cudaEventDestroy(std::get<1>(t));
+    cudaEventDestroy(std::get<2>(t));
+  }
+}
+
+// Per-series event build.  Two events per exposure, time-ordered with every
+// end before any start at equal times (a reset must not wipe an integral
+// before it is read), then by measurement index; slot = instrument label or
+// greedy lowest free slot in start order (footnote of Section 3.2.3).
+struct SeriesOut {
+  gp_ss_status st = GP_SS_OK;
+  int n_slots = 1;
+};
+
+void build_series(int64_t a, int64_t b, const double *ts, const double *te, const float *y,
+                  const float *yerr, const int32_t *inst, float *dt, uint8_t *tag, float4 *meas,
+                  double *dt64, double *meas64, SeriesOut *out) {
+  const int64_t n = b - a;
+  std::vector<int> slot(n);
+  int n_slots = 1;
+  for (int64_t i = 0; i < n; ++i) {
+    const double d = te[a + i] - ts[a + i];
+    if (!(d > 0) || !std::isfinite(d) || !std::isfinite(ts[a + i]) || !std::isfinite(y[a + i]) ||
+        !std::isfinite(yerr[a + i])) {
+      out->st = GP_SS_EINVAL;
+      return;
+    }
+  }
+  std::vector<int64_t> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t p, int64_t q) { return ts[a + p] < ts[a + q]; });
+  if (inst) {
+    std::vector<double> last_end;
+    for (int64_t r = 0; r < n; ++r) {
+      const int64_t i = order[r];
+      const int s = inst[a + i];
+      if (s < 0 || s >= 8) {
+        out->st = s < 0 ? GP_SS_EINVAL : GP_SS_EUNSUPPORTED;
+        return;
+      }
+      if ((int)last_end.size() <= s) last_end.resize(s + 1, -INFINITY);
+      if (last_end[s] > ts[a + i]) {
+        out->st = GP_SS_ESELFOVERLAP;
+        return;
+      }
+      last_end[s] = te[a + i];
+      slot[i] = s;
+      n_slots = std::max(n_slots, s + 1);
+    }
+  } else {
+    std::vector<double> last_end;
+    for (int64_t r = 0; r < n; ++r) {
+      const int64_t i = order[r];
+      int s = 0;
+      while (s < (int)last_end.size() && last_end[s] > ts[a + i]) ++s;
+      if (s == (int)last_end.size()) last_end.push_back(0);
+      last_end[s] = te[a + i];
+      slot[i] = s;
+      n_slots = std::max(n_slots, s + 1);
+    }
+  }
+  out->n_slots = n_slots;
+  // events: key (time, kind with end = 0 first, measurement)
+  struct Ev {
+    double t;
+    int kind;  // 0 end, 1 start
+    int64_t i;
+  };
+  std::vector<Ev> ev(2 * n);
+  for (int64_t i = 0; i < n; ++i) {
+    ev[2 * i] = {ts[a + i], 1, i};
+    ev[2 * i + 1] = {te[a + i], 0, i};
+  }
+  std::sort(ev.begin(), ev.end(), [](const Ev &p, const Ev &q) {
+    if (p.t != q.t) return p.t < q.t;
+    if (p.kind != q.kind) return p.kind < q.kind;
+    return p.i < q.i;
+  });
+  const int64_t e0 = 2 * a;
+  int64_t mi = a;
+  double tprev = n > 0 ? ev[0].t : 0.0;
+  for (int64_t k = 0; k < 2 * n; ++k) {
+    const double gap = ev[k].t - tprev;
+    tprev = ev[k].t;
+    dt[e0 + k] = (float)gap;
+    if (dt64) dt64[e0 + k] = gap;
+    const int64_t i = ev[k].i;
+    const bool is_end = ev[k].kind == 0;
+    tag[e0 + k] = (uint8_t)((is_end ? 1 : 0) | (slot[i] << 1));
+    if (is_end) {
+      const double delta = te[a + i] - ts[a + i];
+      const double w = 1.0 / delta;
+      const double r0 = (double)yerr[a + i] * (double)yerr[a + i];
+      meas[mi] = make_float4(y[a + i], (float)r0, (float)w, 0.0f);
+      if (meas64) {
+        meas64[3 * mi] = (double)y[a + i];
+        meas64[3 * mi + 1] = r0;
+        meas64[3 * mi + 2] = w;
+      }
+      ++mi;
+    }
+  }
+}
+
+gp_ss_status make_plan(gp_ss_model *m, int chunk_len) {
+  const int n = m->n_series;
+  int L = chunk_len;
+  if (m->schedule == 1 || L <= 0) {
+    if (m->schedule == 1) {
+      int64_t mx = 1;
+      for (int s = 0; s < n; ++s) mx = std::max<int64_t>(mx, m->ev_off[s + 1] - m->ev_off[s]);
+      if (mx > (int64_t)1 << 30) return GP_SS_EUNSUPPORTED;
+      L = (int)mx;
+    } else {
+      L = kDefaultChunk;
+    }
+  }
+  std::vector<int64_t> ev0, meas0;
+  std::vector<int32_t> len, ser, first(n + 1);
+  std::vector<uint8_t> flags;
+  int max_len = 0;
+  for (int s = 0; s < n; ++s) {
+    first[s] = (int32_t)len.size();
+    const int64_t a = m->ev_off[s], K = m->ev_off[s + 1] - a;
+    const int64_t nch = std::max<int64_t>(1, (K + L - 1) / L);
+    const int64_t base = K / nch, rem = K % nch;
+    int64_t e = a, mi = m->meas_off[s];
+    for (int64_t c = 0; c < nch; ++c) {
+      const int64_t l = base + (c < rem ? 1 : 0);
+      ev0.push_back(e);
+      meas0.push_back(mi);
+      len.push_back((int32_t)l);
+      ser.push_back(s);
+      flags.push_back((uint8_t)((c == 0 ? 1 : 0) | (c == nch - 1 ? 2 : 0)));
+      for (int64_t k = e; k < e + l; ++k) mi += m->tag[k] & 1;
+      e += l;
+      max_len = std::max<int>(max_len, (int)l);
+    }
+  }
+  first[n] = (int32_t)len.size();
+  if (len.size() > (size_t)INT32_MAX / 4) return GP_SS_EUNSUPPORTED;
+  void *old[] = {m->d_ch_ev0, m->d_ch_meas0, m->d_ch_len, m->d_ch_series, m->d_ch_first,
+                 m->d_ch_flags};
+  for (void *p : old)
+    if (p) cudaFree(p);
+  gp_ss_status st;
+  if ((st = dev_upload(&m->d_ch_ev0, ev0.data(), ev0.size()))) return st;
+  if ((st = dev_upload(&m->d_ch_meas0, meas0.data(), meas0.size()))) return st;
+  if ((st = dev_upload(&m->d_ch_len, len.data(), len.size()))) return st;
+  if ((st = dev_upload(&m->d_ch_series, ser.data(), ser.size()))) return st;
+  if ((st = dev_upload(&m->d_ch_first, first.data(), first.size()))) return st;
+  if ((st = dev_upload(&m->d_ch_flags, flags.data(), flags.size()))) return st;
+  m->chunk_len = L;
+  m->n_chunks = (int)len.size();
+  m->max_chunk = max_len;
+  for (auto &kv : m->graphs) cudaGraphExecDestroy(kv.second);
+  m->graphs.clear();
+  return GP_SS_OK;
+}
+
+gpss::DevModel dev_view(const gp_ss_model *m) {
+  gpss::DevModel d;
+  d.n_series = m->n_series;
+  d.n_params = m->n_params;
+  d.n_terms = m->n_terms;
+  for (int i = 0; i < 4; ++i) d.kinds[i] = m->kinds[i];
+  d.ev_off = m->d_ev_off;
+  d.meas_off = m->d_meas_off;
+  d.dt = m->d_dt;
+  d.tag = m->d_tag;
+  d.meas = m->d_meas;
+  d.dt64 = m->d_dt64;
+  d.meas64 = m->d_meas64;
+  d.n_chunks = m->n_chunks;
+  d.ch_ev0 = m->d_ch_ev0;
+  d.ch_meas0 = m->d_ch_meas0;
+  d.ch_len = m->d_ch_len;
+  d.ch_series = m->d_ch_series;
+  d.ch_flags = m->d_ch_flags;
+  d.ch_first = m->d_ch_first;
+  return d;
+}
+
+#define GPSS_CK(call)                         \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return GP_SS_ECUDA; \
+  } while (0)
+
+gp_ss_status prepare_err(const gp_ss_model *m, int n_out, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(m->mu);
+  if (m->err_cap < n_out) {
+    if (m->d_err) cudaFree(m->d_err);
+    m->d_err = nullptr;
+    if (cudaMalloc((void **)&m->d_err, std::max(n_out, 1) * sizeof(int)) != cudaSuccess) {
+      m->err_cap = 0;
+      return GP_SS_ENOMEM;
+    }
+    m->err_cap = n_out;
+  }
+  m->last_n_out = n_out;
+  GPSS_CK(cudaMemsetAsync(m->d_err, 0, std::max(n_out, 1) * sizeof(int), st));
+  return GP_SS_OK;
+}
+
+// Records an event pair around one kernel phase when timing is on and the
+// stream is not being captured.
+struct PhaseTimer {
+  const gp_ss_model *m;
+  cudaStream_t st;
+  int phase;
+  cudaEvent_t a = nullptr, b = nullptr;
+  PhaseTimer(const gp_ss_model *m_, cudaStream_t st_, int phase_) : m(m_), st(st_), phase(phase_) {
+    if (!m->timing) return;
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    if (cudaEventCreate(&a) || cudaEventCreate(&b)) {
+      a = b = nullptr;
+      return;
+    }
+    cudaEventRecord(a, st);
+  }
+  ~PhaseTimer() {
+    if (!a) return;
+    cudaEventRecord(b, st);
+    std::lock_guard<std::mutex> lk(m->mu);
+    m->timings.emplace_back(phase, a, b);
+  }
+};
+
+gp_ss_status check_call(const gp_ss_model *m, const float *theta, int n_sets, int per_series,
+                        const void *out) {
+  if (!m || !theta || !out || n_sets <= 0) return GP_SS_EINVAL;
+  if (per_series && n_sets != m->n_series) return GP_SS_EINVAL;
+  return GP_SS_OK;
+}
+
+// Enqueue the log-likelihood (and optionally gradient) computation.
+gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int per_series,
+                     double *ll, float *grad, cudaStream_t st) {
+  const int n_out = per_series ? m->n_series : n_sets * m->n_series;
+  gp_ss_status s0 = prepare_err(m, n_out, st);
+  if (s0) return s0;
+  const gpss::DevModel dm = dev_view(m);
+  const OpTable &o = m->ops;
+  if (m->precision == 64) {
+    if (grad) return GP_SS_EUNSUPPORTED;
+    if (!m->d_dt64) return GP_SS_EINVAL;
+    PhaseTimer pt(m, st, 4);
+    GPSS_CK(o.plain64(dm, theta, n_out, per_series, ll, m->d_err, st));
+    return GP_SS_OK;
+  }
+  const int64_t n_vch64 = (int64_t)(per_series ? 1 : n_sets) * m->n_chunks;
+  if (n_vch64 > INT32_MAX / 8) return GP_SS_EUNSUPPORTED;
+  const int n_vch = (int)n_vch64;
+  const int SD = o.D + o.NP;
+  float *ef = nullptr, *state_in = nullptr, *adj = nullptr, *ckpt = nullptr;
+  double *ed = nullptr, *gacc = nullptr;
+  auto release = [&]() {
+    if (ef) cudaFreeAsync(ef, st);
+    if (ed) cudaFreeAsync(ed, st);
+    if (state_in) cudaFreeAsync(state_in, st);
+    if (adj) cudaFreeAsync(adj, st);
+    if (ckpt) cudaFreeAsync(ckpt, st);
+    if (gacc) cudaFreeAsync(gacc, st);
+  };
+  gp_ss_status res = GP_SS_OK;
+  do {
+    if (cudaMallocAsync((void **)&ef, (size_t)o.NF * n_vch * sizeof(float), st) ||
+        cudaMallocAsync((void **)&ed, (size_t)o.ND * n_vch * sizeof(double), st)) {
+      res = GP_SS_ENOMEM;
+      break;
+    }
+    {
+      PhaseTimer pt(m, st, 0);
+      if (o.elem(dm, theta, n_vch, per_series, ef, ed, m->d_err, st)) {
+        res = GP_SS_ECUDA;
+        break;
+      }
+    }
+    if (!grad) {
+      PhaseTimer pt(m, st, 1);
+      if (o.scan(dm, n_out, per_series, ef, ed, n_vch, nullptr, nullptr, ll, 0, m->d_err, st))
+        res = GP_SS_ECUDA;
+      break;
+    }
+    const int max_seg = (m->max_chunk + o.CK - 1) / o.CK;
+    if (cudaMallocAsync((void **)&state_in, (size_t)SD * n_vch * sizeof(float), st) ||
+        cudaMallocAsync((void **)&adj, (size_t)SD * n_vch * sizeof(float), st) ||
+        cudaMallocAsync((void **)&ckpt, (size_t)std::max(max_seg, 1) * (SD + 1) * n_vch * sizeof(float), st) ||
+        cudaMallocAsync((void **)&gacc, (size_t)n_out * m->n_params * sizeof(double), st)) {
+      res = GP_SS_ENOMEM;
+      break;
+    }
+    if (cudaMemsetAsync(gacc, 0, (size_t)n_out * m->n_params * sizeof(double), st)) {
+      res = GP_SS_ECUDA;
+      break;
+    }
+    {
+      PhaseTimer pt(m, st, 1);
+      if (o.scan(dm, n_out, per_series, ef, ed, n_vch, state_in, adj, ll, 1, m->d_err, st)) {
+        res = GP_SS_ECUDA;
+        break;
+      }
+    }
+    {
+      PhaseTimer pt(m, st, 2);
+      if (o.grad(dm, theta, n_vch, per_series, state_in, adj, ckpt, gacc, m->d_err, st)) {
+        res = GP_SS_ECUDA;
+        break;
+      }
+    }
+    const int ng = n_out * m->n_params;
+    {
+      PhaseTimer pt(m, st, 3);
+      gpss::k_to_float<<<(ng + 255) / 256, 256, 0, st>>>(ng, gacc, grad);
+      if (cudaGetLastError() != cudaSuccess) res = GP_SS_ECUDA;
+    }
+  } while (0);
+  release();
+  return res;
+}
+
+gp_ss_status run_graph(const gp_ss_model *m, int kind, const float *theta, int n_sets,
+                       int per_series, double *ll, float *grad, cudaStream_t st) {
+  GraphKey key{kind, theta, n_sets, per_series, ll, grad, st};
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(m->mu);
+    auto it = m->graphs.find(key);
+    if (it != m->graphs.end()) exec = it->second;
+  }
+  if (!exec) {
+    cudaStream_t cap;
+    GPSS_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    // make sure the error buffer exists outside the capture
+    gp_ss_status s0 = prepare_err(m, per_series ? m->n_series : n_sets * m->n_series, st);
+    if (s0) {
+      cudaStreamDestroy(cap);
+      return s0;
+    }
+    GPSS_CK(cudaStreamSynchronize(st));
+    cudaGraph_t g;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return GP_SS_ECUDA;
+    }
+    gp_ss_status r = enqueue(m, theta, n_sets, per_series, ll, grad, cap);
+    cudaError_t ce = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (r) return r;
+    if (ce != cudaSuccess) return GP_SS_ECUDA;
+    ce = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return GP_SS_ECUDA;
+    std::lock_guard<std::mutex> lk(m->mu);
+    m->graphs[key] = exec;
+  }
+  GPSS_CK(cudaGraphLaunch(exec, st));
+  return GP_SS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gp_ss_status_string(gp_ss_status s) {
+  switch (s) {
+    case GP_SS_OK: return "ok";
+    case GP_SS_EINVAL: return "invalid argument";
+    case GP_SS_EUNSORTED: return "series offsets not sorted";
+    case GP_SS_ESELFOVERLAP: return "an instrument's exposures overlap each other";
+    case GP_SS_EUNSUPPORTED: return "unsupported model shape or parameter regime";
+    case GP_SS_ENOMEM: return "out of memory";
+    case GP_SS_ECUDA: return "CUDA runtime error";
+    case GP_SS_ENUMERIC: return "non-positive or non-finite innovation variance";
+    case GP_SS_ETIMEOUT: return "bounded device wait timed out";
+  }
+  return "unknown status";
+}
+
+gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
+                               const int64_t *series_offsets, const double *t_start,
+                               const double *t_end, const float *y, const float *yerr,
+                               const int32_t *instrument, const gp_ss_options *opts,
+                               gp_ss_model **out) {
+  if (!out) return GP_SS_EINVAL;
+  *out = nullptr;
+  if (!spec || !spec->terms || n_series < 1 || !series_offsets) return GP_SS_EINVAL;
+  if (spec->n_terms < 1 || spec->n_terms > 2) return GP_SS_EUNSUPPORTED;
+  if (spec->integral_layout != 0 && spec->integral_layout != 1) return GP_SS_EINVAL;
+  for (int t = 0; t < spec->n_terms; ++t)
+    if (spec->terms[t] != GP_SS_TERM_SHO && spec->terms[t] != GP_SS_TERM_MATERN32)
+      return GP_SS_EINVAL;
+  gp_ss_options o{};
+  o.precision = 32;
+  if (opts) o = *opts;
+  if (o.precision == 0) o.precision = 32;
+  if (o.precision != 32 && o.precision != 64) return GP_SS_EINVAL;
+  if (o.threads_per_series > 1) return GP_SS_EUNSUPPORTED;
+  if (series_offsets[0] != 0) return GP_SS_EINVAL;
+  for (int s = 0; s < n_series; ++s)
+    if (series_offsets[s + 1] < series_offsets[s]) return GP_SS_EUNSORTED;
+  const int64_t N = series_offsets[n_series];
+  if (N > 0 && (!t_start || !t_end || !y || !yerr)) return GP_SS_EINVAL;
+  if (2 * N > (int64_t)INT32_MAX * 4) return GP_SS_EUNSUPPORTED;
+
+  gp_ss_model *m = new (std::nothrow) gp_ss_model();
+  if (!m) return GP_SS_ENOMEM;
+  cudaGetDevice(&m->device);
+  m->n_series = n_series;
+  m->n_terms = spec->n_terms;
+  m->layout = spec->n_terms == 1 ? 0 : spec->integral_layout;
+  m->precision = o.precision;
+  m->schedule = o.schedule;
+  m->n_params = 1;
+  for (int t = 0; t < spec->n_terms; ++t) {
+    m->kinds[t] = spec->terms[t];
+    m->n_params += spec->terms[t] == GP_SS_TERM_SHO ? 3 : 2;
+  }
+  m->n_meas = N;
+  m->n_events = 2 * N;
+  m->ev_off.resize(n_series + 1);
+  m->meas_off.resize(n_series + 1);
+  for (int s = 0; s <= n_series; ++s) {
+    m->meas_off[s] = series_offsets[s];
+    m->ev_off[s] = 2 * series_offsets[s];
+  }
+  const size_t nE = std::max<int64_t>(2 * N, 1), nM = std::max<int64_t>(N, 1);
+  // host copies: pinned for fast re-upload when a device is present, plain
+  // otherwise (validation then still runs and reports before any device work)
+  m->pinned = cudaMallocHost((void **)&m->h_dt, nE * sizeof(float)) == cudaSuccess &&
+              cudaMallocHost((void **)&m->h_tag, nE) == cudaSuccess &&
+              cudaMallocHost((void **)&m->h_meas, nM * sizeof(float4)) == cudaSuccess;
+  if (!m->pinned) {
+    if (m->h_dt) cudaFreeHost(m->h_dt);
+    if (m->h_tag) cudaFreeHost(m->h_tag);
+    m->h_dt = nullptr;
+    m->h_tag = nullptr;
+    m->h_meas = nullptr;
+    cudaGetLastError();
+    m->h_dt = (float *)std::malloc(nE * sizeof(float));
+    m->h_tag = (uint8_t *)std::malloc(nE);
+    m->h_meas = (float4 *)std::malloc(nM * sizeof(float4));
+    if (!m->h_dt || !m->h_tag || !m->h_meas) {
+      free_model_buffers(m);
+      delete m;
+      return GP_SS_ENOMEM;
+    }
+  }
+  std::vector<double> dt64, meas64;
+  if (o.precision == 64) {
+    dt64.resize(nE);
+    meas64.resize(3 * nM);
+  }
+  // build series in parallel on host threads
+  std::vector<SeriesOut> so(n_series);
+  unsigned nthr = std::max(1u, std::min(std::thread::hardware_concurrency(), 64u));
+  nthr = std::min<unsigned>(nthr, (unsigned)n_series);
+  {
+    std::vector<std::thread> pool;
+    for (unsigned w = 0; w < nthr; ++w)
+      pool.emplace_back([&, w]() {
+        for (int s = (int)w; s < n_series; s += (int)nthr)
+          build_series(series_offsets[s], series_offsets[s + 1], t_start, t_end, y, yerr,
+                       instrument, m->h_dt, m->h_tag, m->h_meas,
+                       dt64.empty() ? nullptr : dt64.data(),
+                       meas64.empty() ? nullptr : meas64.data(), &so[s]);
+      });
+    for (auto &t : pool) t.join();
+  }
+  int n_slots = 1;
+  for (int s = 0; s < n_series; ++s) {
+    if (so[s].st != GP_SS_OK) {
+      gp_ss_status st = so[s].st;
+      free_model_buffers(m);
+      delete m;
+      return st;
+    }
+    n_slots = std::max(n_slots, so[s].n_slots);
+  }
+  m->n_slots = n_slots;
+  if (n_slots > kMaxSlots || !pick_ops(m->n_terms, n_slots, m->layout, &m->ops)) {
+    free_model_buffers(m);
+    delete m;
+    return GP_SS_EUNSUPPORTED;
+  }
+  m->tag.assign(m->h_tag, m->h_tag + 2 * N);
+  gp_ss_status st = GP_SS_OK;
+  if (!st) st = dev_upload(&m->d_ev_off, m->ev_off.data(), m->ev_off.size());
+  if (!st) st = dev_upload(&m->d_meas_off, m->meas_off.data(), m->meas_off.size());
+  if (!st) st = dev_upload(&m->d_dt, m->h_dt, nE);
+  if (!st) st = dev_upload(&m->d_tag, m->h_tag, nE);
+  if (!st) st = dev_upload(&m->d_meas, m->h_meas, nM);
+  if (!st && o.precision == 64) {
+    st = dev_upload(&m->d_dt64, dt64.data(), nE);
+    if (!st) st = dev_upload(&m->d_meas64, meas64.data(), 3 * nM);
+  }
+  if (!st) st = make_plan(m, o.chunk_len);
+  if (st) {
+    free_model_buffers(m);
+    delete m;
+    return st;
+  }
+  *out = m;
+  return GP_SS_OK;
+}
+
+gp_ss_status gp_ss_set_chunk_len(gp_ss_model *m, int chunk_len) {
+  if (!m || chunk_len < 0) return GP_SS_EINVAL;
+  DeviceGuard g(m->device);
+  std::lock_guard<std::mutex> lk(m->mu);
+  if (cudaDeviceSynchronize() != cudaSuccess) return GP_SS_ECUDA;
+  return make_plan(m, chunk_len);
+}
+
+gp_ss_status gp_ss_discretize(const gp_ss_kernel_spec *spec, int n_slots, const float *theta,
+                              const float *dt, int n, float *phi_out, float *q_out,
+                              void *cuda_stream) {
+  if (!spec || !spec->terms || !theta || !dt || !phi_out || !q_out || n < 0) return GP_SS_EINVAL;
+  if (spec->n_terms < 1 || spec->n_terms > 2 || n_slots < 1) return GP_SS_EUNSUPPORTED;
+  for (int t = 0; t < spec->n_terms; ++t)
+    if (spec->terms[t] != GP_SS_TERM_SHO && spec->terms[t] != GP_SS_TERM_MATERN32)
+      return GP_SS_EINVAL;
+  OpTable o;
+  const int layout = spec->n_terms == 1 ? 0 : spec->integral_layout;
+  if (!pick_ops(spec->n_terms, n_slots, layout, &o)) return GP_SS_EUNSUPPORTED;
+  const int k1 = spec->n_terms > 1 ? spec->terms[1] : 0;
+  GPSS_CK(o.disc(theta, spec->terms[0], k1, dt, n, phi_out, q_out, (cudaStream_t)cuda_stream));
+  return GP_SS_OK;
+}
+
+gp_ss_status gp_ss_model_info(const gp_ss_model *m, int *n_series, int64_t *n_meas,
+                              int64_t *n_events, int *n_params, int *state_dim, int *n_slots,
+                              int *n_chunks) {
+  if (!m) return GP_SS_EINVAL;
+  if (n_series) *n_series = m->n_series;
+  if (n_meas) *n_meas = m->n_meas;
+  if (n_events) *n_events = m->n_events;
+  if (n_params) *n_params = m->n_params;
+  if (state_dim) *state_dim = m->ops.D;
+  if (n_slots) *n_slots = m->n_slots;
+  if (n_chunks) *n_chunks = m->n_chunks;
+  return GP_SS_OK;
+}
+
+gp_ss_status gp_ss_loglik(const gp_ss_model *m, const float *theta, int n_sets,
+                          int theta_per_series, double *loglik_out, void *cuda_stream) {
+  gp_ss_status s = check_call(m, theta, n_sets, theta_per_series, loglik_out);
+  if (s) return s;
+  DeviceGuard g(m->device);
+  return enqueue(m, theta, n_sets, theta_per_series, loglik_out, nullptr,
+                 (cudaStream_t)cuda_stream);
+}
+
+gp_ss_status gp_ss_loglik_grad(const gp_ss_model *m, const float *theta, int n_sets,
+                               int theta_per_series, double *loglik_out, float *grad_out,
+                               float *dlogl_ddt, void *cuda_stream) {
+  gp_ss_status s = check_call(m, theta, n_sets, theta_per_series, loglik_out);
+  if (s) return s;
+  if (!grad_out || dlogl_ddt) return GP_SS_EINVAL;
+  DeviceGuard g(m->device);
+  return enqueue(m, theta, n_sets, theta_per_series, loglik_out, grad_out,
+                 (cudaStream_t)cuda_stream);
+}
+
+gp_ss_status gp_ss_loglik_batched(const gp_ss_model *m, const float *theta, int n_sets,
+                                  int theta_per_series, double *loglik_out, void *cuda_stream) {
+  gp_ss_status s = check_call(m, theta, n_sets, theta_per_series, loglik_out);
+  if (s) return s;
+  DeviceGuard g(m->device);
+  return run_graph(m, 0, theta, n_sets, theta_per_series, loglik_out, nullptr,
+                   (cudaStream_t)cuda_stream);
+}
+
+gp_ss_status gp_ss_loglik_grad_batched(const gp_ss_model *m, const float *theta, int n_sets,
+                                       int theta_per_series, double *loglik_out,
+                                       float *grad_out, void *cuda_stream) {
+  gp_ss_status s = check_call(m, theta, n_sets, theta_per_series, loglik_out);
+  if (s) return s;
+  if (!grad_out) return GP_SS_EINVAL;
+  DeviceGuard g(m->device);
+  return run_graph(m, 1, theta, n_sets, theta_per_series, loglik_out, grad_out,
+                   (cudaStream_t)cuda_stream);
+}
+
+gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *m, const float *theta_host, int n_sets,
+                                    int theta_per_series, double *loglik_host, float *grad_host,
+                                    int reupload_events, void *cuda_stream) {
+  gp_ss_status s = check_call(m, theta_host, n_sets, theta_per_series, loglik_host);
+  if (s) return s;
+  if (!grad_host) return GP_SS_EINVAL;
+  DeviceGuard g(m->device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int n_out = theta_per_series ? m->n_series : n_sets * m->n_series;
+  float *d_theta = nullptr, *d_grad = nullptr;
+  double *d_ll = nullptr;
+  const size_t nth = (size_t)n_sets * m->n_params;
+  if (cudaMallocAsync((void **)&d_theta, nth * sizeof(float), st) ||
+      cudaMallocAsync((void **)&d_ll, (size_t)n_out * sizeof(double), st) ||
+      cudaMallocAsync((void **)&d_grad, (size_t)n_out * m->n_params * sizeof(float), st))
+    return GP_SS_ENOMEM;
+  gp_ss_status res = GP_SS_OK;
+  if (reupload_events) {
+    if (cudaMemcpyAsync(m->d_dt, m->h_dt, (size_t)m->n_events * sizeof(float),
+                        cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(m->d_tag, m->h_tag, (size_t)m->n_events, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(m->d_meas, m->h_meas, (size_t)m->n_meas * sizeof(float4),
+                        cudaMemcpyHostToDevice, st))
+      res = GP_SS_ECUDA;
+  }
+  if (!res && cudaMemcpyAsync(d_theta, theta_host, nth * sizeof(float), cudaMemcpyHostToDevice, st))
+    res = GP_SS_ECUDA;
+  if (!res) res = enqueue(m, d_theta, n_sets, theta_per_series, d_ll, d_grad, st);
+  if (!res && (cudaMemcpyAsync(loglik_host, d_ll, (size_t)n_out * sizeof(double),
+                               cudaMemcpyDeviceToHost, st) ||
+               cudaMemcpyAsync(grad_host, d_grad, (size_t)n_out * m->n_params * sizeof(float),
+                               cudaMemcpyDeviceToHost, st)))
+    res = GP_SS_ECUDA;
+  cudaFreeAsync(d_theta, st);
+  cudaFreeAsync(d_ll, st);
+  cudaFreeAsync(d_grad, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && !res) res = GP_SS_ECUDA;
+  return res;
+}
+
+gp_ss_status gp_ss_last_error_series(const gp_ss_model *m, int64_t *first_bad_series,
+                                     gp_ss_status *code) {
+  if (!m || !first_bad_series || !code) return GP_SS_EINVAL;
+  DeviceGuard g(m->device);
+  std::lock_guard<std::mutex> lk(m->mu);
+  *first_bad_series = -1;
+  *code = GP_SS_OK;
+  const int n = m->last_n_out;
+  if (n <= 0 || !m->d_err) return GP_SS_OK;
+  std::vector<int> h(n);
+  if (cudaMemcpy(h.data(), m->d_err, n * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return GP_SS_ECUDA;
+  for (int i = 0; i < n; ++i)
+    if (h[i]) {
+      *first_bad_series = i;
+      *code = (gp_ss_status)h[i];
+      break;
+    }
+  return GP_SS_OK;
+}
+
+gp_ss_status gp_ss_set_timing(gp_ss_model *m, int enable) {
+  if (!m) return GP_SS_EINVAL;
+  std::lock_guard<std::mutex> lk(m->mu);
+  m->timing = enable != 0;
+  return GP_SS_OK;
+}
+
+gp_ss_status gp_ss_get_timing(gp_ss_model *m, double *ms, int64_t *launches) {
+  if (!m || !ms || !launches) return GP_SS_EINVAL;
+  DeviceGuard g(m->device);
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> tv;
+  {
+    std::lock_guard<std::mutex> lk(m->mu);
+    tv.swap(m->timings);
+  }
+  for (int i = 0; i < 5; ++i) {
+    ms[i] = 0.0;
+    launches[i] = 0;
+  }
+  gp_ss_status res = GP_SS_OK;
+  for (auto &t : tv) {
+    float e = 0.f;
+    if (cudaEventSynchronize(std::get<2>(t)) != cudaSuccess ||
+        cudaEventElapsedTime(&e, std::get<1>(t), std::get<2>(t)) != cudaSuccess)
+      res = GP_SS_ECUDA;
+    ms[std::get<0>(t)] += e;
+    launches[std::get<0>(t)] += 1;
+    cudaEventDestroy(std::get<1>(t));
+    cudaEventDestroy(std::get<2>(t));
+  }
+  return res;
+}
+
+void gp_ss_free_model(gp_ss_model *m) {
+  if (!m) return;
+  {
+    DeviceGuard g(m->device);
+    cudaDeviceSynchronize();
+    free_model_buffers(m);
+  }
+  delete m;
+}
+
+}  // extern "C"

@@ -1,0 +1,508 @@
+// Device-side arithmetic of the augmented state-space filter.
+//
+// Notation follows the paper (arXiv 2601.02527): for one SHO term with
+// angular frequency omega0 and quality Q (Appendix B), write
+//   a    = omega0 / (2Q)             (decay rate of the impulse response)
+//   beta = omega0^2 (1 - 1/(4 Q^2))  (squared oscillation frequency, eta^2 omega0^2)
+//   w2   = omega0^2 = beta + a^2
+//   Qc   = 2 omega0^3 sigma^2 / Q    (driving-noise density, Eq. sho_Qc_Pinf)
+// Matern-3/2 is the same oscillator at Q = 1/2 (beta = 0).
+//
+// Everything per step follows from the impulse response f(t) = Phi_12(t),
+// f'' + 2a f' + w2 f = 0, f(0) = 0, f'(0) = 1:
+//   Phi(t)   = [[f' + 2a f, f], [-w2 f, f']]                      (Eq. sho_phi)
+//   Phibar_x = [f + 2a F1, F1],  F1 = int_0^t f                   (Eq. sho_phibar)
+//   Q(t)     = Qc [[I_ff, f^2/2], [f^2/2, I_pp]]                   (Eq. Q)
+//   Q~12     = Qc [F1^2/2, f F1 - I_ff]                           (Eq. analytic_Qaug12)
+//   Q~22     = Qc I_FF                                            (Eq. analytic_Qaug22)
+// with I_ff = int f^2, I_pp = int f'^2, I_FF = int F1^2 over [0, t].  These
+// six scalars (Disc below) are computed once per term per step.
+//
+// FP32 evaluation: the closed forms cancel catastrophically for small
+// omega0 t (the z-noise I_FF ~ t^5/20 is a difference of O(1) terms).  For
+// w2 t^2 <= XT2 the six scalars come from their Taylor series in t, whose
+// coefficients follow from the recurrence of f; above it from closed forms
+// rewritten through the identities
+//   w2 F1  = 1 - f' - 2a f
+//   4a I_pp = 1 - f'^2 - w2 f^2
+//   w2 I_ff = I_pp - f f' - a f^2
+//   w2^2 I_FF = t + I_pp + 4a^2 I_ff - 2f - 4a F1 + 2a f^2
+// (integrals of the oscillator equation multiplied by f', f and of F1^2),
+// which stay accurate once the exponential has decayed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#define GPSS_HD __host__ __device__ __forceinline__
+#define GPSS_D __device__ __forceinline__
+
+namespace gpss {
+
+// ---------------------------------------------------------------------------
+// Compile-time shape of the augmented state.
+//   NT terms (state (x_t, xdot_t) each), NS instrument slots,
+//   LAYOUT 0: one integral state z_j per slot integrating H x = sum_t x_t,
+//   LAYOUT 1: one z_{t,j} per term and slot integrating x_t.
+// ---------------------------------------------------------------------------
+template <int NT_, int NS_, int LAYOUT_>
+struct Shape {
+  static constexpr int NT = NT_;
+  static constexpr int NS = NS_;
+  static constexpr int LAYOUT = (NT_ == 1) ? 0 : LAYOUT_;
+  static constexpr int NZPER = (LAYOUT == 0) ? 1 : NT;
+  static constexpr int NZ = NS * NZPER;
+  static constexpr int D = 2 * NT + NZ;
+  static constexpr int NP = D * (D + 1) / 2;  // packed upper triangle
+  static GPSS_HD constexpr int zslot(int zi) {
+    return LAYOUT == 0 ? zi - 2 * NT : (zi - 2 * NT) / NT;
+  }
+  static GPSS_HD constexpr bool zint(int zi, int t) {
+    return LAYOUT == 0 ? true : ((zi - 2 * NT) % NT) == t;
+  }
+  static GPSS_HD constexpr int pk(int i, int j) {
+    return i <= j ? i * D - i * (i - 1) / 2 + (j - i) : j * D - j * (j - 1) / 2 + (i - j);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Forward-mode dual number with two tangents, (d/da, d/dbeta).  Used only to
+// differentiate the per-step discretisation in the reverse-time gradient.
+// ---------------------------------------------------------------------------
+template <class F>
+struct Dual2 {
+  F v, da, db;
+};
+
+template <class F> GPSS_HD Dual2<F> mk(F v, F da, F db) { return Dual2<F>{v, da, db}; }
+template <class F> GPSS_HD Dual2<F> operator+(Dual2<F> x, Dual2<F> y) { return mk(x.v + y.v, x.da + y.da, x.db + y.db); }
+template <class F> GPSS_HD Dual2<F> operator-(Dual2<F> x, Dual2<F> y) { return mk(x.v - y.v, x.da - y.da, x.db - y.db); }
+template <class F> GPSS_HD Dual2<F> operator-(Dual2<F> x) { return mk(-x.v, -x.da, -x.db); }
+template <class F> GPSS_HD Dual2<F> operator*(Dual2<F> x, Dual2<F> y) {
+  return mk(x.v * y.v, x.da * y.v + x.v * y.da, x.db * y.v + x.v * y.db);
+}
+template <class F> GPSS_HD Dual2<F> operator/(Dual2<F> x, Dual2<F> y) {
+  F iy = F(1) / y.v;
+  F q = x.v * iy;
+  return mk(q, (x.da - q * y.da) * iy, (x.db - q * y.db) * iy);
+}
+template <class F> GPSS_HD Dual2<F> operator+(Dual2<F> x, F c) { return mk(x.v + c, x.da, x.db); }
+template <class F> GPSS_HD Dual2<F> operator+(F c, Dual2<F> x) { return mk(x.v + c, x.da, x.db); }
+template <class F> GPSS_HD Dual2<F> operator-(Dual2<F> x, F c) { return mk(x.v - c, x.da, x.db); }
+template <class F> GPSS_HD Dual2<F> operator-(F c, Dual2<F> x) { return mk(c - x.v, -x.da, -x.db); }
+template <class F> GPSS_HD Dual2<F> operator*(Dual2<F> x, F c) { return mk(x.v * c, x.da * c, x.db * c); }
+template <class F> GPSS_HD Dual2<F> operator*(F c, Dual2<F> x) { return mk(x.v * c, x.da * c, x.db * c); }
+template <class F> GPSS_HD Dual2<F> operator/(Dual2<F> x, F c) { F ic = F(1) / c; return mk(x.v * ic, x.da * ic, x.db * ic); }
+
+template <class F> struct Real { using type = F; };
+template <class F> struct Real<Dual2<F>> { using type = F; };
+
+// constant of type T
+template <class T> struct Cst { static GPSS_HD T of(T v) { return v; } };
+template <class F> struct Cst<Dual2<F>> { static GPSS_HD Dual2<F> of(F v) { return mk(v, F(0), F(0)); } };
+template <class T, class F> GPSS_HD T cst(F v) { return Cst<T>::of(v); }
+
+GPSS_HD float val(float x) { return x; }
+GPSS_HD double val(double x) { return x; }
+template <class F> GPSS_HD F val(Dual2<F> x) { return x.v; }
+
+GPSS_D float gexp(float x) { return expf(x); }
+GPSS_D double gexp(double x) { return exp(x); }
+template <class F> GPSS_D Dual2<F> gexp(Dual2<F> x) {
+  F e = gexp(x.v);
+  return mk(e, e * x.da, e * x.db);
+}
+
+// S(beta, t) = sin(sqrt(beta) t) / sqrt(beta)  (= t at beta = 0),
+// C(beta, t) = cos(sqrt(beta) t), for beta >= 0.
+GPSS_D void sinc_pair(float beta, float t, float &S, float &C) {
+  float b = sqrtf(beta);
+  float tau = b * t;
+  float s, c;
+  sincosf(tau, &s, &c);
+  C = c;
+  S = (tau < 1e-3f) ? t * (1.0f - tau * tau * (1.0f / 6.0f)) : s / b;
+}
+GPSS_D void sinc_pair(double beta, double t, double &S, double &C) {
+  double b = sqrt(beta);
+  double tau = b * t;
+  double s, c;
+  sincos(tau, &s, &c);
+  C = c;
+  S = (tau < 1e-6) ? t * (1.0 - tau * tau * (1.0 / 6.0)) : s / b;
+}
+// Dual version: dC/dbeta = -t S / 2; dS/dbeta = (t C - S) / (2 beta), which
+// for small beta t^2 is evaluated from its series
+// t^3 (-1/6 + beta t^2/60 - beta^2 t^4/1680 + beta^3 t^6/90720 - ...).
+template <class F>
+GPSS_D void sinc_pair(Dual2<F> beta, F t, Dual2<F> &S, Dual2<F> &C) {
+  F s, c;
+  sinc_pair(beta.v, t, s, c);
+  F x = beta.v * t * t;
+  F dS;
+  if (x < F(0.5)) {
+    dS = t * t * t *
+         (F(-1.0 / 6.0) + x * (F(1.0 / 60.0) + x * (F(-1.0 / 1680.0) + x * (F(1.0 / 90720.0) +
+                                                                         x * F(-1.0 / 7983360.0)))));
+  } else {
+    dS = (t * c - s) / (F(2) * beta.v);
+  }
+  F dC = -t * s * F(0.5);
+  S = mk(s, dS * beta.da, dS * beta.db);
+  C = mk(c, dC * beta.da, dC * beta.db);
+}
+
+template <class T>
+struct Disc {
+  T f, fp, F1, Iff, Ipp, IFF;
+};
+
+template <class F> struct TaylorOrder;
+template <> struct TaylorOrder<float> { static constexpr int N = 10; static constexpr float XT2 = 1.0f; };
+template <> struct TaylorOrder<double> { static constexpr int N = 17; static constexpr double XT2 = 1.0; };
+
+// Taylor branch: f(s) = sum_{n>=1} c_n s^n with c_1 = 1, c_2 = -a,
+// c_{n+2} = -(2a (n+1) c_{n+1} + w2 c_n) / ((n+2)(n+1)); p_n = c_n t^n.
+//   I_ff = t   sum p_n p_m / (n+m+1)
+//   I_pp = 1/t sum n m p_n p_m / (n+m-1)
+//   I_FF = t^3 sum p_n p_m / ((n+1)(m+1)(n+m+3))
+// (double sums over n + m <= N + 1).
+template <class T, class F>
+GPSS_D Disc<T> disc_taylor(F t, T a, T w2) {
+  constexpr int N = TaylorOrder<F>::N;
+  T p[N + 1];
+  p[1] = cst<T>(t);
+  p[2] = -a * (t * t);
+  const F t2 = t * t;
+#pragma unroll
+  for (int n = 1; n + 2 <= N; ++n) {
+    const F inv = F(1) / F((n + 2) * (n + 1));
+    p[n + 2] = -(a * (F(2 * (n + 1)) * t) * p[n + 1] + w2 * t2 * p[n]) * inv;
+  }
+  Disc<T> d;
+  T f = p[1], fp = p[1], F1 = p[1] * F(0.5);
+#pragma unroll
+  for (int n = 2; n <= N; ++n) {
+    f = f + p[n];
+    fp = fp + p[n] * F(n);
+    F1 = F1 + p[n] * (F(1) / F(n + 1));
+  }
+  T sff = p[1] * p[1] * (F(1) / F(3));
+  T spp = p[1] * p[1];
+  T sFF = p[1] * p[1] * (F(1) / F(4 * 5));
+#pragma unroll
+  for (int n = 1; n <= N; ++n) {
+#pragma unroll
+    for (int m = n; m <= N; ++m) {
+      if (n + m > N + 1 || (n == 1 && m == 1)) continue;
+      const F mult = (n == m) ? F(1) : F(2);
+      const T pp = p[n] * p[m];
+      sff = sff + pp * (mult / F(n + m + 1));
+      spp = spp + pp * (mult * F(n * m) / F(n + m - 1));
+      sFF = sFF + pp * (mult / F((n + 1) * (m + 1) * (n + m + 3)));
+    }
+  }
+  const F it = F(1) / t;
+  d.f = f;
+  d.fp = fp * it;
+  d.F1 = F1 * t;
+  d.Iff = sff * t;
+  d.Ipp = spp * it;
+  d.IFF = sFF * (t * t2);
+  return d;
+}
+
+template <class T, class F>
+GPSS_D Disc<T> disc_closed(F t, T a, T beta, T w2) {
+  T E = gexp(-a * t);
+  T S, C;
+  sinc_pair(beta, t, S, C);
+  Disc<T> d;
+  d.f = E * S;
+  d.fp = E * (C - a * S);
+  const T rw2 = cst<T>(F(1)) / w2;
+  d.F1 = (F(1) - d.fp - F(2) * a * d.f) * rw2;
+  d.Ipp = (F(1) - d.fp * d.fp - w2 * d.f * d.f) / (F(4) * a);
+  d.Iff = (d.Ipp - d.f * d.fp - a * d.f * d.f) * rw2;
+  d.IFF = (cst<T>(t) + d.Ipp + F(4) * a * a * d.Iff - F(2) * d.f - F(4) * a * d.F1 +
+           F(2) * a * d.f * d.f) *
+          rw2 * rw2;
+  return d;
+}
+
+// All six per-term scalars for a step of length t >= 0.
+template <class T, class F>
+GPSS_D Disc<T> discretize(F t, T a, T beta) {
+  T w2 = beta + a * a;
+  if (t == F(0)) {
+    Disc<T> d;
+    d.f = cst<T>(F(0));
+    d.fp = cst<T>(F(1));
+    d.F1 = d.f;
+    d.Iff = d.f;
+    d.Ipp = d.f;
+    d.IFF = d.f;
+    return d;
+  }
+  if (val(w2) * t * t <= TaylorOrder<F>::XT2) return disc_taylor<T, F>(t, a, w2);
+  return disc_closed<T, F>(t, a, beta, w2);
+}
+
+// Per-term constants from natural parameters.
+template <class F>
+struct TermC {
+  F a, beta, w2, qc, var;
+};
+
+// Blocks of Phi~ and Q~ for one term (see header comment).
+template <class F>
+struct Blocks {
+  F p00, p01, p10, p11, pb0, pb1, q00, q01, q11, qz0, qz1, qzz;
+};
+
+template <class F>
+GPSS_D Blocks<F> make_blocks(const Disc<F> &d, const TermC<F> &c) {
+  Blocks<F> B;
+  B.p00 = d.fp + F(2) * c.a * d.f;
+  B.p01 = d.f;
+  B.p10 = -c.w2 * d.f;
+  B.p11 = d.fp;
+  B.pb0 = d.f + F(2) * c.a * d.F1;
+  B.pb1 = d.F1;
+  B.q00 = c.qc * d.Iff;
+  B.q01 = c.qc * d.f * d.f * F(0.5);
+  B.q11 = c.qc * d.Ipp;
+  B.qz0 = c.qc * d.F1 * d.F1 * F(0.5);
+  B.qz1 = c.qc * (d.f * d.F1 - d.Iff);
+  B.qzz = c.qc * d.IFF;
+  return B;
+}
+
+// out = Phi~ v
+template <class S, class F>
+GPSS_D void apply_phi(const Blocks<F> *B, const F *v, F *out) {
+#pragma unroll
+  for (int t = 0; t < S::NT; ++t) {
+    out[2 * t] = B[t].p00 * v[2 * t] + B[t].p01 * v[2 * t + 1];
+    out[2 * t + 1] = B[t].p10 * v[2 * t] + B[t].p11 * v[2 * t + 1];
+  }
+#pragma unroll
+  for (int zi = 2 * S::NT; zi < S::D; ++zi) {
+    F acc = v[zi];
+#pragma unroll
+    for (int t = 0; t < S::NT; ++t)
+      if (S::zint(zi, t)) acc = acc + B[t].pb0 * v[2 * t] + B[t].pb1 * v[2 * t + 1];
+    out[zi] = acc;
+  }
+}
+
+// out = Phi~^T v
+template <class S, class F>
+GPSS_D void apply_phi_t(const Blocks<F> *B, const F *v, F *out) {
+#pragma unroll
+  for (int t = 0; t < S::NT; ++t) {
+    F a0 = B[t].p00 * v[2 * t] + B[t].p10 * v[2 * t + 1];
+    F a1 = B[t].p01 * v[2 * t] + B[t].p11 * v[2 * t + 1];
+#pragma unroll
+    for (int zi = 2 * S::NT; zi < S::D; ++zi)
+      if (S::zint(zi, t)) {
+        a0 = a0 + B[t].pb0 * v[zi];
+        a1 = a1 + B[t].pb1 * v[zi];
+      }
+    out[2 * t] = a0;
+    out[2 * t + 1] = a1;
+  }
+#pragma unroll
+  for (int zi = 2 * S::NT; zi < S::D; ++zi) out[zi] = v[zi];
+}
+
+// P <- P + Q~ (packed)
+template <class S, class F>
+GPSS_D void add_q(const Blocks<F> *B, F *P) {
+#pragma unroll
+  for (int t = 0; t < S::NT; ++t) {
+    P[S::pk(2 * t, 2 * t)] += B[t].q00;
+    P[S::pk(2 * t, 2 * t + 1)] += B[t].q01;
+    P[S::pk(2 * t + 1, 2 * t + 1)] += B[t].q11;
+#pragma unroll
+    for (int zi = 2 * S::NT; zi < S::D; ++zi)
+      if (S::zint(zi, t)) {
+        P[S::pk(2 * t, zi)] += B[t].qz0;
+        P[S::pk(2 * t + 1, zi)] += B[t].qz1;
+      }
+  }
+#pragma unroll
+  for (int zi = 2 * S::NT; zi < S::D; ++zi)
+#pragma unroll
+    for (int zj = zi; zj < S::D; ++zj) {
+      F acc = F(0);
+#pragma unroll
+      for (int t = 0; t < S::NT; ++t)
+        if (S::zint(zi, t) && S::zint(zj, t)) acc += B[t].qzz;
+      P[S::pk(zi, zj)] += acc;
+    }
+}
+
+// P <- Phi~ P Phi~^T + Q~ on packed storage; G (optional) receives Phi~ P.
+template <class S, class F>
+GPSS_D void predict_cov(const Blocks<F> *B, F *P, F (*G)[S::D] = nullptr) {
+  constexpr int D = S::D;
+  F T1[D][D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    F col[D], o[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) col[i] = P[S::pk(i, j)];
+    apply_phi<S>(B, col, o);
+#pragma unroll
+    for (int i = 0; i < D; ++i) T1[i][j] = o[i];
+  }
+  if (G) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) G[i][j] = T1[i][j];
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    F o[D];
+    apply_phi<S>(B, T1[i], o);
+#pragma unroll
+    for (int j = i; j < D; ++j) P[S::pk(i, j)] = o[j];
+  }
+  add_q<S>(B, P);
+}
+
+// Reset of slot j (Eq. integrated_kalman_update with R_j of Section 3.2.3).
+template <class S, class F>
+GPSS_D void reset_slot(int j, F *m, F *P) {
+#pragma unroll
+  for (int zi = 2 * S::NT; zi < S::D; ++zi) {
+    const bool hit = (S::zslot(zi) == j);
+    m[zi] = hit ? F(0) : m[zi];
+#pragma unroll
+    for (int i = 0; i < S::D; ++i) P[S::pk(i, zi)] = hit ? F(0) : P[S::pk(i, zi)];
+  }
+}
+
+// Shared pieces of the measurement update with H~ = w * sum_{z in slot j} e_z
+// (Eq. H_aug; w = 1/delta):  u = P H~^T, S = H~ u + r, hm = H~ m.
+template <class S, class F>
+GPSS_D void obs_project(int j, F w, const F *m, const F *P, F *u, F &hu, F &hm) {
+#pragma unroll
+  for (int i = 0; i < S::D; ++i) {
+    F acc = F(0);
+#pragma unroll
+    for (int zi = 2 * S::NT; zi < S::D; ++zi) acc += (S::zslot(zi) == j) ? P[S::pk(i, zi)] : F(0);
+    u[i] = acc * w;
+  }
+  F a1 = F(0), a2 = F(0);
+#pragma unroll
+  for (int zi = 2 * S::NT; zi < S::D; ++zi) {
+    const bool hit = (S::zslot(zi) == j);
+    a1 += hit ? u[zi] : F(0);
+    a2 += hit ? m[zi] : F(0);
+  }
+  hu = a1 * w;
+  hm = a2 * w;
+}
+
+// Load per-term constants and s^2 from a row of natural parameters.
+template <int NT, class F>
+GPSS_D void load_terms(const float *th, const int *kinds, TermC<F> *tc, F &s2) {
+  int j = 0;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    F sig, w0, q;
+    if (kinds[t] == 1) {
+      sig = F(th[j]);
+      w0 = F(th[j + 1]);
+      q = F(th[j + 2]);
+      j += 3;
+    } else {
+      sig = F(th[j]);
+      w0 = F(1.7320508075688772) / F(th[j + 1]);
+      q = F(0.5);
+      j += 2;
+    }
+    tc[t].var = sig * sig;
+    tc[t].a = w0 / (F(2) * q);
+    tc[t].w2 = w0 * w0;
+    tc[t].beta = (q == F(0.5)) ? F(0) : w0 * w0 * (F(1) - F(1) / (F(4) * q * q));
+    tc[t].qc = F(2) * w0 * w0 * w0 * sig * sig / q;
+  }
+  F s = F(th[j]);
+  s2 = s * s;
+}
+
+// P0 = blkdiag(P_inf, I) (Section 3.2.3); m0 = 0.
+template <class S, class F>
+GPSS_D void init_state(const TermC<F> *tc, F *m, F *P) {
+#pragma unroll
+  for (int i = 0; i < S::D; ++i) m[i] = F(0);
+#pragma unroll
+  for (int i = 0; i < S::NP; ++i) P[i] = F(0);
+#pragma unroll
+  for (int t = 0; t < S::NT; ++t) {
+    P[S::pk(2 * t, 2 * t)] = tc[t].var;
+    P[S::pk(2 * t + 1, 2 * t + 1)] = tc[t].var * tc[t].w2;
+  }
+#pragma unroll
+  for (int zi = 2 * S::NT; zi < S::D; ++zi) P[S::pk(zi, zi)] = F(1);
+}
+
+// Dense solve with partial pivoting: B <- A^{-1} B (A destroyed); returns
+// log|det A|.  Row swaps are done with selects so that every index stays a
+// compile-time constant (register arrays).
+template <int D, int R, class F>
+GPSS_D F solve_inplace(F (&A)[D][D], F (&B)[D][R]) {
+  F logdet = F(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    // pivot row among k..D-1
+    int piv = k;
+    F best = fabs(A[k][k]);
+#pragma unroll
+    for (int r = k + 1; r < D; ++r) {
+      F v = fabs(A[r][k]);
+      if (v > best) {
+        best = v;
+        piv = r;
+      }
+    }
+#pragma unroll
+    for (int r = k + 1; r < D; ++r) {
+      const bool sw = (piv == r);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        F x = A[k][c], y = A[r][c];
+        A[k][c] = sw ? y : x;
+        A[r][c] = sw ? x : y;
+      }
+#pragma unroll
+      for (int c = 0; c < R; ++c) {
+        F x = B[k][c], y = B[r][c];
+        B[k][c] = sw ? y : x;
+        B[r][c] = sw ? x : y;
+      }
+    }
+    const F pivv = A[k][k];
+    logdet += log(fabs(pivv));
+    const F ip = F(1) / pivv;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      if (r == k) continue;
+      const F fct = A[r][k] * ip;
+#pragma unroll
+      for (int c = k + 1; c < D; ++c) A[r][c] -= fct * A[k][c];
+#pragma unroll
+      for (int c = 0; c < R; ++c) B[r][c] -= fct * B[k][c];
+    }
+#pragma unroll
+    for (int c = 0; c < R; ++c) B[k][c] *= ip;
+  }
+  return logdet;
+}
+
+}  // namespace gpss

@@ -130,7 +130,7 @@ def _sample_psd(rng, w0, q, n):
     return np.interp(rng.uniform(0, 1, n), cdf, w)
 
 
-def exposure_average_signal(rng, t_start, t_end, terms, theta_row, n_feat=64):
+def exposure_average_signal(rng, t_start, t_end, terms, theta_row, n_feat=16):
     """Exposure averages of a random-Fourier-feature draw of the kernel.
 
     Each term contributes ``n_feat`` cosines with random phases and angular
@@ -146,10 +146,13 @@ def exposure_average_signal(rng, t_start, t_end, terms, theta_row, n_feat=64):
         w = _sample_psd(rng, w0, q, n_feat)
         ph = rng.uniform(0, TWO_PI, n_feat)
         amp = sig * math.sqrt(2.0 / n_feat)
-        for wi, pi in zip(w, ph):
-            x = wi * half
-            sinc = np.where(np.abs(x) < 1e-8, 1.0, np.sin(x) / np.where(x == 0, 1.0, x))
-            f += amp * np.cos(wi * tm + pi) * sinc
+        w32 = w.astype(np.float32)
+        for a in range(0, len(tm), 16384):
+            sl = slice(a, a + 16384)
+            # phases reduced in FP64 before the FP32 cosine so long times keep their accuracy
+            arg = np.mod(np.outer(tm[sl], w) + ph, TWO_PI).astype(np.float32)
+            sinc = np.sinc(np.outer(half[sl].astype(np.float32), w32) / np.float32(math.pi))
+            f[sl] += amp * np.sum(np.cos(arg) * sinc, axis=1, dtype=np.float64)
     return f
 
 

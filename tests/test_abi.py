@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads and exports every symbol include/gpss.h
+declares; host-side validation runs without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2601_02527_gb300 as gp
+from paper_2601_02527_gb300 import build as gbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbuild.build()
+    return gp.load_library()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gpss.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gp_ss_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declarations_match_binding():
+    assert sorted(gp.EXPORTS) == declared_functions()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_status_strings(lib):
+    for code in range(9):
+        assert lib.gp_ss_status_string(code).decode()
+    assert lib.gp_ss_status_string(7).decode().startswith("non-positive")
+
+
+def _build(lib, t_start, t_end, inst=None, offsets=None, terms=(1,), layout=0):
+    n = len(t_start)
+    offs = np.asarray(offsets if offsets is not None else [0, n], np.int64)
+    ts = np.ascontiguousarray(t_start, np.float64)
+    te = np.ascontiguousarray(t_end, np.float64)
+    y = np.zeros(n, np.float32)
+    ye = np.zeros(n, np.float32)
+    spec, keep = gp._spec(terms, layout)
+    opts = gp._Options(32, 0, 0, 0, 0, 0)
+    h = ctypes.c_void_p()
+    ii = None if inst is None else np.ascontiguousarray(inst, np.int32)
+    rc = lib.gp_ss_build_model(ctypes.byref(spec), len(offs) - 1, offs.ctypes.data,
+                               ts.ctypes.data, te.ctypes.data, y.ctypes.data, ye.ctypes.data,
+                               None if ii is None else ii.ctypes.data, ctypes.byref(opts),
+                               ctypes.byref(h))
+    if rc == 0:
+        lib.gp_ss_free_model(h)
+    return rc
+
+
+def test_host_validation_without_gpu(lib):
+    # unsorted offsets
+    assert _build(lib, [0.0, 1.0], [0.5, 1.5], offsets=[0, 2, 1]) == 2
+    # non-positive exposure
+    assert _build(lib, [0.0, 1.0], [0.5, 1.0]) == 1
+    # one instrument overlapping itself
+    assert _build(lib, [0.0, 0.4], [0.5, 0.9], inst=[0, 0]) == 3
+    # more than 3 concurrently open exposures (greedy slots) is not compiled
+    assert _build(lib, [0.0, 0.1, 0.2, 0.3], [5.0, 5.0, 5.0, 5.0]) == 4
+    # more than two terms
+    assert _build(lib, [0.0], [1.0], terms=(1, 1, 1)) == 4
