@@ -49,7 +49,8 @@ class _KernelSpec(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("threads_per_series", ctypes.c_int), ("chunk_len", ctypes.c_int),
-                ("ckpt_interval", ctypes.c_int), ("debug_checks", ctypes.c_int)]
+                ("ckpt_interval", ctypes.c_int), ("debug_checks", ctypes.c_int),
+                ("chunk_combine", ctypes.c_int)]
 
 
 _lib = None
@@ -118,7 +119,7 @@ class Model:
     """
 
     def __init__(self, terms, offsets, t_start, t_end, y, yerr, instrument=None, layout=0,
-                 precision=32, schedule=0, chunk_len=0):
+                 precision=32, schedule=0, chunk_len=0, combine=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -133,7 +134,7 @@ class Model:
         ye = np.ascontiguousarray(yerr, np.float32)
         inst = None if instrument is None else np.ascontiguousarray(instrument, np.int32)
         spec, self._spec_arr = _spec(self.terms, self.layout)
-        opts = _Options(int(precision), int(schedule), 0, int(chunk_len), 0, 0)
+        opts = _Options(int(precision), int(schedule), 0, int(chunk_len), 0, 0, int(combine))
         h = ctypes.c_void_p()
         self.device = torch.cuda.current_device()
         rc = lib.gp_ss_build_model(ctypes.byref(spec), len(offs) - 1, offs.ctypes.data,

@@ -24,9 +24,29 @@ OpTable ops_2_2_0();
 OpTable ops_2_3_0();
 OpTable ops_2_1_1();
 
-__global__ void k_to_float(int n, const double *__restrict__ src, float *__restrict__ dst) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = (float)src[i];
+__global__ void k_series_sum(int n_out, int per_series, int n_series, int n_chunks,
+                             const int32_t *__restrict__ ch_first,
+                             const double *__restrict__ ll_part, int n_vch,
+                             const float *__restrict__ gpart, int n_params,
+                             double *__restrict__ ll_out, float *__restrict__ grad_out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n_out) return;
+  const int s = per_series ? v : v % n_series;
+  const int base = per_series ? 0 : (v / n_series) * n_chunks;
+  const int c0 = ch_first[s], c1 = ch_first[s + 1];
+  if (ll_part) {
+    double acc = 0.0;
+    for (int c = c0; c < c1; ++c) acc += ll_part[base + c];
+    ll_out[v] = acc;
+  }
+  if (gpart) {
+    for (int p = 0; p < n_params; ++p) {
+      double acc = 0.0;
+      const float *g = gpart + (size_t)p * n_vch + base;
+      for (int c = c0; c < c1; ++c) acc += (double)g[c];
+      grad_out[(size_t)v * n_params + p] = (float)acc;
+    }
+  }
 }
 }  // namespace gpss
 
@@ -77,7 +97,8 @@ struct gp_ss_model {
   float4 *d_meas = nullptr;
   double *d_dt64 = nullptr, *d_meas64 = nullptr;
   // chunk plan
-  int chunk_len = 0, n_chunks = 0, max_chunk = 0;
+  int chunk_len = 0, n_chunks = 0, max_chunk = 0, max_chunks_per_series = 0;
+  int combine = 0;  // cross-chunk combination: 0 auto, 1 sequential per series, 2 tree
   int64_t *d_ch_ev0 = nullptr, *d_ch_meas0 = nullptr;
   int32_t *d_ch_len = nullptr, *d_ch_series = nullptr, *d_ch_first = nullptr;
   uint8_t *d_ch_flags = nullptr;
@@ -310,6 +331,9 @@ gp_ss_status make_plan(gp_ss_model *m, int chunk_len) {
   m->chunk_len = L;
   m->n_chunks = (int)len.size();
   m->max_chunk = max_len;
+  m->max_chunks_per_series = 0;
+  for (int s = 0; s < n; ++s)
+    m->max_chunks_per_series = std::max(m->max_chunks_per_series, first[s + 1] - first[s]);
   for (auto &kv : m->graphs) cudaGraphExecDestroy(kv.second);
   m->graphs.clear();
   return GP_SS_OK;
@@ -411,20 +435,25 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
   if (n_vch64 > INT32_MAX / 8) return GP_SS_EUNSUPPORTED;
   const int n_vch = (int)n_vch64;
   const int SD = o.D + o.NP;
-  float *ef = nullptr, *state_in = nullptr, *adj = nullptr, *ckpt = nullptr;
-  double *ed = nullptr, *gacc = nullptr;
-  auto release = [&]() {
-    if (ef) cudaFreeAsync(ef, st);
-    if (ed) cudaFreeAsync(ed, st);
-    if (state_in) cudaFreeAsync(state_in, st);
-    if (adj) cudaFreeAsync(adj, st);
-    if (ckpt) cudaFreeAsync(ckpt, st);
-    if (gacc) cudaFreeAsync(gacc, st);
+  // cross-chunk combination: the sequential fold keeps one thread per series
+  // busy for its whole chunk count; long series go through the tree scan
+  bool tree = m->combine == 2 || (m->combine == 0 && m->max_chunks_per_series > 48);
+  std::vector<void *> bufs;
+  auto grab = [&](void **p, size_t bytes) -> bool {
+    if (cudaMallocAsync(p, std::max<size_t>(bytes, 16), st) != cudaSuccess) {
+      *p = nullptr;
+      return false;
+    }
+    bufs.push_back(*p);
+    return true;
   };
+  float *ef = nullptr, *state_end = nullptr, *info = nullptr, *adj = nullptr, *ckpt = nullptr,
+        *scratch = nullptr, *gpart = nullptr;
+  double *ed = nullptr, *ll_part = nullptr;
   gp_ss_status res = GP_SS_OK;
   do {
-    if (cudaMallocAsync((void **)&ef, (size_t)o.NF * n_vch * sizeof(float), st) ||
-        cudaMallocAsync((void **)&ed, (size_t)o.ND * n_vch * sizeof(double), st)) {
+    if (!grab((void **)&ef, (size_t)o.NF * n_vch * sizeof(float)) ||
+        !grab((void **)&ed, (size_t)o.ND * n_vch * sizeof(double))) {
       res = GP_SS_ENOMEM;
       break;
     }
@@ -435,46 +464,59 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
         break;
       }
     }
-    if (!grad) {
-      PhaseTimer pt(m, st, 1);
-      if (o.scan(dm, n_out, per_series, ef, ed, n_vch, nullptr, nullptr, ll, 0, m->d_err, st))
-        res = GP_SS_ECUDA;
-      break;
-    }
-    const int max_seg = (m->max_chunk + o.CK - 1) / o.CK;
-    if (cudaMallocAsync((void **)&state_in, (size_t)SD * n_vch * sizeof(float), st) ||
-        cudaMallocAsync((void **)&adj, (size_t)SD * n_vch * sizeof(float), st) ||
-        cudaMallocAsync((void **)&ckpt, (size_t)std::max(max_seg, 1) * (SD + 1) * n_vch * sizeof(float), st) ||
-        cudaMallocAsync((void **)&gacc, (size_t)n_out * m->n_params * sizeof(double), st)) {
+    if ((grad || tree) && !grab((void **)&state_end, (size_t)SD * n_vch * sizeof(float))) {
       res = GP_SS_ENOMEM;
       break;
     }
-    if (cudaMemsetAsync(gacc, 0, (size_t)n_out * m->n_params * sizeof(double), st)) {
-      res = GP_SS_ECUDA;
+    if (grad && !grab((void **)&adj, (size_t)SD * n_vch * sizeof(float))) {
+      res = GP_SS_ENOMEM;
+      break;
+    }
+    if (tree && (!grab((void **)&ll_part, (size_t)n_vch * sizeof(double)) ||
+                 !grab((void **)&scratch, o.scan_scratch(n_vch) * sizeof(float)) ||
+                 (grad && !grab((void **)&info, (size_t)SD * n_vch * sizeof(float))))) {
+      res = GP_SS_ENOMEM;
       break;
     }
     {
       PhaseTimer pt(m, st, 1);
-      if (o.scan(dm, n_out, per_series, ef, ed, n_vch, state_in, adj, ll, 1, m->d_err, st)) {
+      cudaError_t e;
+      if (!tree) {
+        e = o.scan(dm, n_out, per_series, ef, ed, n_vch, state_end, adj, ll, grad ? 1 : 0,
+                   m->d_err, st);
+      } else {
+        e = o.scan_tree(ef, n_vch, state_end, 1, 0, scratch, st);
+        if (e == cudaSuccess && grad) e = o.scan_tree(ef, n_vch, info, 2, 1, scratch, st);
+        if (e == cudaSuccess)
+          e = o.finish(dm, n_vch, per_series, ef, ed, state_end, info, adj, ll_part, m->d_err, st);
+      }
+      if (e != cudaSuccess) {
         res = GP_SS_ECUDA;
         break;
       }
     }
-    {
+    if (grad) {
+      const int max_seg = (m->max_chunk + o.CK - 1) / o.CK;
+      if (!grab((void **)&ckpt, (size_t)std::max(max_seg, 1) * (SD + 1) * n_vch * sizeof(float)) ||
+          !grab((void **)&gpart, (size_t)m->n_params * n_vch * sizeof(float))) {
+        res = GP_SS_ENOMEM;
+        break;
+      }
       PhaseTimer pt(m, st, 2);
-      if (o.grad(dm, theta, n_vch, per_series, state_in, adj, ckpt, gacc, m->d_err, st)) {
+      if (o.grad(dm, theta, n_vch, per_series, state_end, adj, ckpt, gpart, m->d_err, st)) {
         res = GP_SS_ECUDA;
         break;
       }
     }
-    const int ng = n_out * m->n_params;
-    {
+    if (tree || grad) {
       PhaseTimer pt(m, st, 3);
-      gpss::k_to_float<<<(ng + 255) / 256, 256, 0, st>>>(ng, gacc, grad);
+      gpss::k_series_sum<<<(n_out + 127) / 128, 128, 0, st>>>(
+          n_out, per_series, m->n_series, m->n_chunks, m->d_ch_first, tree ? ll_part : nullptr,
+          n_vch, grad ? gpart : nullptr, m->n_params, ll, grad);
       if (cudaGetLastError() != cudaSuccess) res = GP_SS_ECUDA;
     }
   } while (0);
-  release();
+  for (void *p : bufs) cudaFreeAsync(p, st);
   return res;
 }
 
@@ -555,6 +597,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   if (o.precision == 0) o.precision = 32;
   if (o.precision != 32 && o.precision != 64) return GP_SS_EINVAL;
   if (o.threads_per_series > 1) return GP_SS_EUNSUPPORTED;
+  if (o.chunk_combine < 0 || o.chunk_combine > 2) return GP_SS_EINVAL;
   if (series_offsets[0] != 0) return GP_SS_EINVAL;
   for (int s = 0; s < n_series; ++s)
     if (series_offsets[s + 1] < series_offsets[s]) return GP_SS_EUNSORTED;
@@ -570,6 +613,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   m->layout = spec->n_terms == 1 ? 0 : spec->integral_layout;
   m->precision = o.precision;
   m->schedule = o.schedule;
+  m->combine = o.chunk_combine;
   m->n_params = 1;
   for (int t = 0; t < spec->n_terms; ++t) {
     m->kinds[t] = spec->terms[t];

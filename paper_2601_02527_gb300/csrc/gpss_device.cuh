@@ -20,7 +20,7 @@
 //
 // FP32 evaluation: the closed forms cancel catastrophically for small
 // omega0 t (the z-noise I_FF ~ t^5/20 is a difference of O(1) terms).  For
-// w2 t^2 <= XT2 the six scalars come from their Taylor series in t, whose
+// w2 t^2 <= XT2 (omega0 t <= 1.2) the six scalars come from their Taylor series in t, whose
 // coefficients follow from the recurrence of f; above it from closed forms
 // rewritten through the identities
 //   w2 F1  = 1 - f' - 2a f
@@ -159,8 +159,12 @@ struct Disc {
 };
 
 template <class F> struct TaylorOrder;
-template <> struct TaylorOrder<float> { static constexpr int N = 10; static constexpr float XT2 = 1.0f; };
-template <> struct TaylorOrder<double> { static constexpr int N = 17; static constexpr double XT2 = 1.0; };
+// Degree and range of the Taylor branch: FP32 degree 14 for omega0 t <= 1.2
+// and FP64 degree 20 for omega0 t <= 1 keep the truncation below the
+// rounding of the closed forms that take over above (FP32: <= ~4e-6 relative
+// from omega0 t = 1.2 on; below it their cancellation grows like (omega0 t)^-4).
+template <> struct TaylorOrder<float> { static constexpr int N = 14; static constexpr float XT2 = 1.44f; };
+template <> struct TaylorOrder<double> { static constexpr int N = 20; static constexpr double XT2 = 1.0; };
 
 // Taylor branch: f(s) = sum_{n>=1} c_n s^n with c_1 = 1, c_2 = -a,
 // c_{n+2} = -(2a (n+1) c_{n+1} + w2 c_n) / ((n+2)(n+1)); p_n = c_n t^n.

@@ -28,6 +28,7 @@
 #pragma once
 
 #include "gpss_device.cuh"
+#include "gpss_scan.cuh"
 
 namespace gpss {
 
@@ -161,13 +162,7 @@ __global__ void __launch_bounds__(128) k_plain(DevModel M, const float *__restri
 // double part (stride n_vch): gamma | sum log S | n_end
 // ---------------------------------------------------------------------------
 template <class S>
-struct ElemLayout {
-  static constexpr int A = 0;
-  static constexpr int B = S::D * S::D;
-  static constexpr int C = B + S::D;
-  static constexpr int ETA = C + S::NP;
-  static constexpr int J = ETA + S::D;
-  static constexpr int NF = J + S::NP;
+struct ElemLayout : Elem<S> {
   static constexpr int ND = 3;
 };
 
@@ -318,6 +313,81 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
 // Lambda = (lambda lambda^T - (I + J P)^{-1} J) / 2.
 // State / adjoint records: (vector D | packed NP), stride n_vch.
 // ---------------------------------------------------------------------------
+// Marginal log-likelihood of a chunk's data given N(m, P) for the state
+// entering it, from the chunk's information (eta, J), gamma = sum c^2/S and
+// sum log S over its n_end measurements.
+template <class S>
+GPSS_D double chunk_loglik(const float *m, const float *P, const float *eta, const float *J,
+                           double gam, double ld, double ne) {
+  constexpr int D = S::D;
+  float X[D][D], R[D][D];
+  float u[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    float jm = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) jm += J[S::pk(i, k)] * m[k];
+    u[i] = eta[i] - jm;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float acc = (i == j) ? 1.f : 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += P[S::pk(i, k)] * J[S::pk(k, j)];
+      X[i][j] = acc;
+      R[i][j] = P[S::pk(i, j)];
+    }
+  }
+  const float logdet = solve_inplace<D, D, float>(X, R);  // R = (I + P J)^{-1} P
+  float etam = 0.f, mJm = 0.f, uWu = 0.f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    etam += eta[i] * m[i];
+    float jm = 0.f, wu = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      jm += J[S::pk(i, k)] * m[k];
+      wu += R[i][k] * u[k];
+    }
+    mJm += m[i] * jm;
+    uWu += u[i] * wu;
+  }
+  const double quad = gam + (double)(-2.f * etam + mJm - uWu);
+  return -0.5 * (ld + ne * LOG_2PI + (double)logdet + quad);
+}
+
+// Adjoint of the log-likelihood of all later data with respect to the
+// filtered state (m, P), given their information (eta, J) about it:
+// lambda = (I + J P)^{-1} (eta - J m), Lambda = (lambda lambda^T - (I + J P)^{-1} J) / 2.
+template <class S>
+GPSS_D void boundary_adjoint(const float *m, const float *P, const float *eta, const float *J,
+                             float *lam, float *Lam) {
+  constexpr int D = S::D;
+  float X[D][D], R[D][D + 1];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    float jm = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) jm += J[S::pk(i, k)] * m[k];
+    R[i][D] = eta[i] - jm;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float acc = (i == j) ? 1.f : 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += J[S::pk(i, k)] * P[S::pk(k, j)];
+      X[i][j] = acc;
+      R[i][j] = J[S::pk(i, j)];
+    }
+  }
+  solve_inplace<D, D + 1, float>(X, R);
+#pragma unroll
+  for (int i = 0; i < D; ++i) lam[i] = R[i][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j)
+      Lam[S::pk(i, j)] = 0.5f * (lam[i] * lam[j] - 0.5f * (R[i][j] + R[j][i]));
+}
+
 template <class S>
 GPSS_D void load_elem(const float *ef, int n_vch, int vc, float (&A)[S::D][S::D], float *b, float *C,
                       float *eta, float *J) {
@@ -353,11 +423,15 @@ GPSS_D void load_rec(const float *src, int n_vch, int vc, float *v, float *P) {
   for (int i = 0; i < S::NP; ++i) P[i] = src[(size_t)(S::D + i) * n_vch + vc];
 }
 
+// Sequential schedule of the cross-chunk combination: one thread per
+// (virtual) series folds its chunks in time order.  Writes the filtered state
+// at the end of every chunk (state_end), the series log-likelihood, and for
+// the gradient the adjoint of each chunk's end state (adj_end).
 template <class S>
 __global__ void __launch_bounds__(64) k_scan_seq(DevModel M, int n_out, int per_series,
                                                  const float *__restrict__ ef,
                                                  const double *__restrict__ ed, int n_vch,
-                                                 float *__restrict__ state_in,
+                                                 float *__restrict__ state_end,
                                                  float *__restrict__ adj_end,
                                                  double *__restrict__ ll_out, int want_grad,
                                                  int *__restrict__ err) {
@@ -371,7 +445,6 @@ __global__ void __launch_bounds__(64) k_scan_seq(DevModel M, int n_out, int per_
   const int base = set * M.n_chunks;
   F m[D], P[S::NP];
   double ll = 0.0;
-  bool bad = false;
   for (int c = c0; c < c1; ++c) {
     const int vc = base + c;
     F A[D][D], b[D], C[S::NP], eta[D], J[S::NP];
@@ -383,80 +456,55 @@ __global__ void __launch_bounds__(64) k_scan_seq(DevModel M, int n_out, int per_
       for (int i = 0; i < D; ++i) m[i] = b[i];
 #pragma unroll
       for (int i = 0; i < S::NP; ++i) P[i] = C[i];
-      continue;
-    }
-    if (want_grad) store_rec<S>(state_in, n_vch, vc, m, P);
-    // X = I + P J ; RHS = [P | m + P eta]
-    F X[D][D], R[D][D + 1];
-    F u[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      F pe = F(0), jm = F(0);
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        pe += P[S::pk(i, k)] * eta[k];
-        jm += J[S::pk(i, k)] * m[k];
-      }
-      u[i] = eta[i] - jm;
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        F acc = (i == j) ? F(1) : F(0);
-#pragma unroll
-        for (int k = 0; k < D; ++k) acc += P[S::pk(i, k)] * J[S::pk(k, j)];
-        X[i][j] = acc;
-        R[i][j] = P[S::pk(i, j)];
-      }
-      R[i][D] = m[i] + pe;
-    }
-    const F logdet = solve_inplace<D, D + 1, F>(X, R);
-    // quadratic form
-    F quad = F(0);
-    {
-      F etam = F(0), mJm = F(0), uWu = F(0);
+    } else {
+      ll += chunk_loglik<S>(m, P, eta, J, gam, ld, ne);
+      // outgoing state: m' = A (I + P J)^{-1} (m + P eta) + b, P' = A (I + P J)^{-1} P A^T + C
+      F X[D][D], R[D][D + 1];
 #pragma unroll
       for (int i = 0; i < D; ++i) {
-        etam += eta[i] * m[i];
-        F jm = F(0), wu = F(0);
+        F pe = F(0);
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-          jm += J[S::pk(i, k)] * m[k];
-          wu += R[i][k] * u[k];
+        for (int k = 0; k < D; ++k) pe += P[S::pk(i, k)] * eta[k];
+        R[i][D] = m[i] + pe;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          F acc = (i == j) ? F(1) : F(0);
+#pragma unroll
+          for (int k = 0; k < D; ++k) acc += P[S::pk(i, k)] * J[S::pk(k, j)];
+          X[i][j] = acc;
+          R[i][j] = P[S::pk(i, j)];
         }
-        mJm += m[i] * jm;
-        uWu += u[i] * wu;
       }
-      quad = F(gam) - F(2) * etam + mJm - uWu;
+      solve_inplace<D, D + 1, F>(X, R);
+      F T[D][D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        F acc = b[i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc += A[i][k] * R[k][D];
+        m[i] = acc;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          F a2 = F(0);
+#pragma unroll
+          for (int k = 0; k < D; ++k) a2 += A[i][k] * R[k][j];
+          T[i][j] = a2;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = i; j < D; ++j) {
+          F acc = C[S::pk(i, j)];
+#pragma unroll
+          for (int k = 0; k < D; ++k) acc += T[i][k] * A[j][k];
+          P[S::pk(i, j)] = acc;
+        }
     }
-    ll += -0.5 * (ld + ne * LOG_2PI + (double)logdet + (double)quad);
-    // outgoing state
-    F T[D][D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      F acc = b[i];
-#pragma unroll
-      for (int k = 0; k < D; ++k) acc += A[i][k] * R[k][D];
-      m[i] = acc;
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        F a2 = F(0);
-#pragma unroll
-        for (int k = 0; k < D; ++k) a2 += A[i][k] * R[k][j];
-        T[i][j] = a2;
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-      for (int j = i; j < D; ++j) {
-        F acc = C[S::pk(i, j)];
-#pragma unroll
-        for (int k = 0; k < D; ++k) acc += T[i][k] * A[j][k];
-        P[S::pk(i, j)] = acc;
-      }
+    if (want_grad) store_rec<S>(state_end, n_vch, vc, m, P);
   }
-  bad |= !isfinite(ll);
   if (ll_out) ll_out[v] = ll;
-  if (bad) flag_error(err, v, 7);
+  if (!isfinite(ll)) flag_error(err, v, 7);
   if (!want_grad) return;
   // backward information and end-of-chunk adjoints
   F ie[D], iJ[S::NP];
@@ -473,37 +521,14 @@ __global__ void __launch_bounds__(64) k_scan_seq(DevModel M, int n_out, int per_
 #pragma unroll
       for (int i = 0; i < S::NP; ++i) Lam[i] = F(0);
     } else {
-      // filtered state at the end of chunk c = incoming state of chunk c+1
       F mb[D], Pb[S::NP];
-      load_rec<S>(state_in, n_vch, vc + 1, mb, Pb);
-      F X[D][D], R[D][D + 1];
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        F jm = F(0);
-#pragma unroll
-        for (int k = 0; k < D; ++k) jm += iJ[S::pk(i, k)] * mb[k];
-        R[i][D] = ie[i] - jm;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-          F acc = (i == j) ? F(1) : F(0);
-#pragma unroll
-          for (int k = 0; k < D; ++k) acc += iJ[S::pk(i, k)] * Pb[S::pk(k, j)];
-          X[i][j] = acc;
-          R[i][j] = iJ[S::pk(i, j)];
-        }
-      }
-      solve_inplace<D, D + 1, F>(X, R);
-#pragma unroll
-      for (int i = 0; i < D; ++i) lam[i] = R[i][D];
-#pragma unroll
-      for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = i; j < D; ++j)
-          Lam[S::pk(i, j)] = F(0.5) * (lam[i] * lam[j] - F(0.5) * (R[i][j] + R[j][i]));
+      load_rec<S>(state_end, n_vch, vc, mb, Pb);
+      boundary_adjoint<S>(mb, Pb, ie, iJ, lam, Lam);
     }
     store_rec<S>(adj_end, n_vch, vc, lam, Lam);
     if (c == c0) break;
-    // fold chunk c into the backward information
+    // fold chunk c into the backward information:
+    // eta <- A^T (I + J_n C)^{-1} (eta_n - J_n b) + eta, J <- A^T (I + J_n C)^{-1} J_n A + J
     F A[D][D], b[D], C[S::NP], eta[D], J[S::NP];
     load_elem<S>(ef, n_vch, vc, A, b, C, eta, J);
     F X[D][D], R[D][D + 1];
@@ -546,6 +571,62 @@ __global__ void __launch_bounds__(64) k_scan_seq(DevModel M, int n_out, int per_
         iJ[S::pk(i, j)] = J[S::pk(i, j)] + F(0.5) * (acc + acc2);
       }
   }
+}
+
+// Tree schedule, last step: per chunk, its log-likelihood contribution
+// (closed form given the state entering it) and, for the gradient, the
+// adjoint of its end state from the information of the following chunks.
+//   state_end  (b, C) of the inclusive prefix scan   (filtered end state)
+//   info_incl  (eta, J) of the inclusive suffix scan (information about the
+//              state entering the chunk from it and all later chunks)
+template <class S>
+__global__ void __launch_bounds__(128) k_finish(DevModel M, int n_vch, int per_series,
+                                                const float *__restrict__ ef,
+                                                const double *__restrict__ ed,
+                                                const float *__restrict__ state_end,
+                                                const float *__restrict__ info_incl,
+                                                float *__restrict__ adj_end,
+                                                double *__restrict__ ll_part,
+                                                int *__restrict__ err) {
+  using F = float;
+  constexpr int D = S::D;
+  using L = ElemLayout<S>;
+  const int vc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (vc >= n_vch) return;
+  const int c = vc % M.n_chunks;
+  const int set = vc / M.n_chunks;
+  const int s = M.ch_series[c];
+  const int orow = per_series ? s : set * M.n_series + s;
+  const uint8_t flags = M.ch_flags[c];
+  const double gam = ed[vc], ld = ed[(size_t)n_vch + vc], ne = ed[(size_t)2 * n_vch + vc];
+  double ll;
+  if (flags & 1) {
+    ll = -0.5 * (ld + gam + ne * LOG_2PI);
+  } else {
+    F m[D], P[S::NP], eta[D], J[S::NP];
+    load_rec<S>(state_end, n_vch, vc - 1, m, P);
+#pragma unroll
+    for (int i = 0; i < D; ++i) eta[i] = ef[(size_t)(L::ETA + i) * n_vch + vc];
+#pragma unroll
+    for (int i = 0; i < S::NP; ++i) J[i] = ef[(size_t)(L::J + i) * n_vch + vc];
+    ll = chunk_loglik<S>(m, P, eta, J, gam, ld, ne);
+  }
+  ll_part[vc] = ll;
+  if (!isfinite(ll)) flag_error(err, orow, 7);
+  if (!adj_end) return;
+  F lam[D], Lam[S::NP];
+  if (flags & 2) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) lam[i] = F(0);
+#pragma unroll
+    for (int i = 0; i < S::NP; ++i) Lam[i] = F(0);
+  } else {
+    F mb[D], Pb[S::NP], ie[D], iJ[S::NP];
+    load_rec<S>(state_end, n_vch, vc, mb, Pb);
+    load_rec<S>(info_incl, n_vch, vc + 1, ie, iJ);
+    boundary_adjoint<S>(mb, Pb, ie, iJ, lam, Lam);
+  }
+  store_rec<S>(adj_end, n_vch, vc, lam, Lam);
 }
 
 // ---------------------------------------------------------------------------
@@ -726,9 +807,9 @@ GPSS_D void reverse_event(const DevModel &M, int64_t k, int64_t mi, const TermC<
 
 template <class S, int CK>
 __global__ void __launch_bounds__(64) k_grad(DevModel M, const float *__restrict__ theta, int n_vch,
-                                             int per_series, const float *__restrict__ state_in,
+                                             int per_series, const float *__restrict__ state_end,
                                              const float *__restrict__ adj_end,
-                                             float *__restrict__ ckpt, double *__restrict__ gacc,
+                                             float *__restrict__ ckpt, float *__restrict__ gpart,
                                              int *__restrict__ err) {
   using F = float;
   constexpr int D = S::D;
@@ -750,7 +831,7 @@ __global__ void __launch_bounds__(64) k_grad(DevModel M, const float *__restrict
   if (first)
     init_state<S>(tc, m, P);
   else
-    load_rec<S>(state_in, n_vch, vc, m, P);
+    load_rec<S>(state_end, n_vch, vc - 1, m, P);
   const int64_t e0 = M.ch_ev0[c];
   const int len = M.ch_len[c];
   const int nseg = (len + CK - 1) / CK;
@@ -820,7 +901,8 @@ __global__ void __launch_bounds__(64) k_grad(DevModel M, const float *__restrict
   }
   // chain to natural parameters
   const float *th = theta + (size_t)row * M.n_params;
-  double *g = gacc + (size_t)orow * M.n_params;
+  float *g = gpart + vc;
+  const size_t gs = (size_t)n_vch;
   int p = 0;
 #pragma unroll
   for (int t = 0; t < S::NT; ++t) {
@@ -833,9 +915,9 @@ __global__ void __launch_bounds__(64) k_grad(DevModel M, const float *__restrict
                     gr.qc[t] * F(6) * w0 * w0 * sig * sig / q;
       const F dq = -ga * w0 / (F(2) * q * q) + gb * w0 * w0 / (F(2) * q * q * q) -
                    gr.qc[t] * F(2) * w0 * w0 * w0 * sig * sig / (q * q);
-      atomicAdd(g + p, (double)dsig);
-      atomicAdd(g + p + 1, (double)dw0);
-      atomicAdd(g + p + 2, (double)dq);
+      g[p * gs] = dsig;
+      g[(p + 1) * gs] = dw0;
+      g[(p + 2) * gs] = dq;
       p += 3;
     } else {
       const F sig = th[p], ell = th[p + 1];
@@ -843,16 +925,22 @@ __global__ void __launch_bounds__(64) k_grad(DevModel M, const float *__restrict
       const F dsig = gr.qc[t] * F(8) * w0 * w0 * w0 * sig + gr.var[t] * F(2) * sig;
       // a = w0, w2 = w0^2 (through ga), qc = 4 w0^3 sig^2 ; beta = 0 along this family
       const F dw0 = gr.a[t] + F(2) * w0 * gr.w2[t] + gr.qc[t] * F(12) * w0 * w0 * sig * sig;
-      atomicAdd(g + p, (double)dsig);
-      atomicAdd(g + p + 1, (double)(dw0 * (-w0 / ell)));
+      g[p * gs] = dsig;
+      g[(p + 1) * gs] = dw0 * (-w0 / ell);
       p += 2;
     }
   }
-  atomicAdd(g + p, (double)(gr.s2 * F(2) * th[p]));
+  g[p * gs] = gr.s2 * F(2) * th[p];
   if (bad) flag_error(err, orow, 7);
 }
 
-__global__ void k_to_float(int n, const double *__restrict__ src, float *__restrict__ dst);
+// Ordered per-series sums over chunks (deterministic): log-likelihood parts
+// and gradient parts (field-major, stride n_vch), FP64 accumulation.
+__global__ void k_series_sum(int n_out, int per_series, int n_series, int n_chunks,
+                             const int32_t *__restrict__ ch_first,
+                             const double *__restrict__ ll_part, int n_vch,
+                             const float *__restrict__ gpart, int n_params,
+                             double *__restrict__ ll_out, float *__restrict__ grad_out);
 
 // Dense Phi~(dt_k), Q~(dt_k) for a list of gaps (one thread per gap).
 template <class S>
@@ -902,7 +990,11 @@ struct OpTable {
   cudaError_t (*scan)(const DevModel &, int, int, const float *, const double *, int, float *,
                       float *, double *, int, int *, cudaStream_t);
   cudaError_t (*grad)(const DevModel &, const float *, int, int, const float *, const float *,
-                      float *, double *, int *, cudaStream_t);
+                      float *, float *, int *, cudaStream_t);
+  cudaError_t (*scan_tree)(const float *, int, float *, int, int, float *, cudaStream_t);
+  size_t (*scan_scratch)(int);
+  cudaError_t (*finish)(const DevModel &, int, int, const float *, const double *, const float *,
+                        const float *, float *, double *, int *, cudaStream_t);
   cudaError_t (*disc)(const float *, int, int, const float *, int, float *, float *, cudaStream_t);
 };
 
@@ -929,18 +1021,41 @@ cudaError_t launch_elem(const DevModel &M, const float *theta, int n_vch, int pe
 
 template <class S>
 cudaError_t launch_scan(const DevModel &M, int n_out, int per_series, const float *ef,
-                        const double *ed, int n_vch, float *state_in, float *adj_end, double *ll,
+                        const double *ed, int n_vch, float *state_end, float *adj_end, double *ll,
                         int want_grad, int *err, cudaStream_t st) {
   if (n_out <= 0) return cudaSuccess;
   const int bs = 64;
-  k_scan_seq<S><<<(n_out + bs - 1) / bs, bs, 0, st>>>(M, n_out, per_series, ef, ed, n_vch, state_in,
-                                                     adj_end, ll, want_grad, err);
+  k_scan_seq<S><<<(n_out + bs - 1) / bs, bs, 0, st>>>(M, n_out, per_series, ef, ed, n_vch,
+                                                     state_end, adj_end, ll, want_grad, err);
+  return cudaGetLastError();
+}
+
+// Tree schedule: inclusive scan of the n chunk elements, mode 1 -> state
+// records in time order, mode 2 (suffix) -> information records.
+template <class S>
+cudaError_t launch_scan_tree(const float *ef, int n, float *dst, int mode, int rev,
+                             float *scratch, cudaStream_t st) {
+  return scan_elems<S>(ef, n, dst, mode, rev, rev, scratch, st);
+}
+
+template <class S>
+size_t scan_scratch_count(int n) {
+  return scan_scratch_floats<S>(n);
+}
+
+template <class S>
+cudaError_t launch_finish(const DevModel &M, int n_vch, int per_series, const float *ef,
+                          const double *ed, const float *state_end, const float *info_incl,
+                          float *adj_end, double *ll_part, int *err, cudaStream_t st) {
+  if (n_vch <= 0) return cudaSuccess;
+  k_finish<S><<<(n_vch + 127) / 128, 128, 0, st>>>(M, n_vch, per_series, ef, ed, state_end,
+                                                   info_incl, adj_end, ll_part, err);
   return cudaGetLastError();
 }
 
 template <class S>
 cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int per_series,
-                        const float *state_in, const float *adj_end, float *ckpt, double *gacc,
+                        const float *state_end, const float *adj_end, float *ckpt, float *gpart,
                         int *err, cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
   constexpr int SD = S::D + S::NP;
@@ -953,7 +1068,7 @@ cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int pe
     attr_done = true;
   }
   k_grad<S, GRAD_CK><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
-      M, theta, n_vch, per_series, state_in, adj_end, ckpt, gacc, err);
+      M, theta, n_vch, per_series, state_end, adj_end, ckpt, gpart, err);
   return cudaGetLastError();
 }
 
@@ -979,6 +1094,9 @@ OpTable make_ops() {
   o.scan = &launch_scan<S>;
   o.grad = &launch_grad<S>;
   o.disc = &launch_disc<S>;
+  o.scan_tree = &launch_scan_tree<S>;
+  o.scan_scratch = &scan_scratch_count<S>;
+  o.finish = &launch_finish<S>;
   return o;
 }
 

@@ -48,7 +48,7 @@ def _build(lib, t_start, t_end, inst=None, offsets=None, terms=(1,), layout=0):
     y = np.zeros(n, np.float32)
     ye = np.zeros(n, np.float32)
     spec, keep = gp._spec(terms, layout)
-    opts = gp._Options(32, 0, 0, 0, 0, 0)
+    opts = gp._Options(32, 0, 0, 0, 0, 0, 0)
     h = ctypes.c_void_p()
     ii = None if inst is None else np.ascontiguousarray(inst, np.int32)
     rc = lib.gp_ss_build_model(ctypes.byref(spec), len(offs) - 1, offs.ctypes.data,
