@@ -494,17 +494,20 @@ GPSS_D F solve_inplace(F (&A)[D][D], F (&B)[D][R]) {
     const F pivv = A[k][k];
     logdet += log(fabs(pivv));
     const F ip = F(1) / pivv;
+    // scale the pivot row of [A | B], then eliminate column k from every other row
+#pragma unroll
+    for (int c = k + 1; c < D; ++c) A[k][c] *= ip;
+#pragma unroll
+    for (int c = 0; c < R; ++c) B[k][c] *= ip;
 #pragma unroll
     for (int r = 0; r < D; ++r) {
       if (r == k) continue;
-      const F fct = A[r][k] * ip;
+      const F fct = A[r][k];
 #pragma unroll
       for (int c = k + 1; c < D; ++c) A[r][c] -= fct * A[k][c];
 #pragma unroll
       for (int c = 0; c < R; ++c) B[r][c] -= fct * B[k][c];
     }
-#pragma unroll
-    for (int c = 0; c < R; ++c) B[k][c] *= ip;
   }
   return logdet;
 }
