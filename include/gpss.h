@@ -53,7 +53,8 @@ typedef enum {
   GP_SS_ENOMEM = 5,        /* device or host allocation failed */
   GP_SS_ECUDA = 6,         /* a CUDA runtime call failed */
   GP_SS_ENUMERIC = 7,      /* S <= 0 or non-finite value met on the device */
-  GP_SS_ETIMEOUT = 8       /* a bounded device wait gave up */
+  GP_SS_ETIMEOUT = 8,      /* a bounded device wait gave up */
+  GP_SS_ETOOBIG = 9        /* problem exceeds the fixed scratch of gp_ss_loglik_noalloc */
 } gp_ss_status;
 
 typedef enum {
@@ -151,6 +152,35 @@ gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *model, const float *theta
 gp_ss_status gp_ss_discretize(const gp_ss_kernel_spec *spec, int n_slots, const float *theta,
                               const float *dt, int n, float *phi_out, float *q_out,
                               void *cuda_stream);
+
+/* Log-likelihood without device allocation.  (Not part of the paper's method:
+ * a deployment variant of gp_ss_loglik.)
+ * gp_ss_loglik takes scratch memory from the stream-ordered allocator on every
+ * call.  Callers that cannot allocate device memory at call time -- a host
+ * application that gives all device memory to its own pool, a latency-critical
+ * loop that must not pay for or synchronise on an allocation, a process whose
+ * allocator is disabled or capped -- can call this instead.  It computes the
+ * same log-likelihood (FP32 models only; element pass plus sequential
+ * per-series combination) with its scratch in one array of 16 MiB compiled
+ * into the library: every GPU that loads libgpss holds that array until the
+ * process exits.  It calls no allocation routine of CUDA or of any library.
+ *   - Arguments and result as gp_ss_loglik; theta and loglik_out are
+ *     caller-owned device buffers.
+ *   - Scratch needed: NF*n_chunks*4 bytes (rounded up to 256) + 24*n_chunks
+ *     bytes, NF = 2d^2 + 3d (d = augmented dimension; 90 at d = 6),
+ *     n_chunks the model's chunk count times n_sets when theta_per_series = 0.
+ *     A call that needs more than 16 MiB returns GP_SS_ETOOBIG and launches
+ *     nothing.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (every value is written before it is read, so nothing needs clearing).
+ *     Calls whose work overlaps on the GPU -- on different streams, or from
+ *     different threads without ordering -- race on the array: serialise them.
+ *   - Device-side numeric failures are not recorded for
+ *     gp_ss_last_error_series; check loglik_out for non-finite values. */
+gp_ss_status gp_ss_loglik_noalloc(const gp_ss_model *model, const float *theta, int n_sets,
+                                  int theta_per_series, double *loglik_out, void *cuda_stream);
 
 /* Model facts: any output pointer may be NULL. */
 gp_ss_status gp_ss_model_info(const gp_ss_model *model, int *n_series, int64_t *n_meas,

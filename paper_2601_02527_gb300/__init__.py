@@ -24,13 +24,15 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "series offsets not sorted",
           3: "an instrument's exposures overlap each other",
           4: "unsupported model shape or parameter regime", 5: "out of memory",
           6: "CUDA runtime error", 7: "non-positive or non-finite innovation variance",
-          8: "bounded device wait timed out"}
+          8: "bounded device wait timed out",
+          9: "problem needs more than the fixed scratch of gp_ss_loglik_noalloc"}
 
 # every function declared in include/gpss.h
 EXPORTS = ["gp_ss_build_model", "gp_ss_loglik", "gp_ss_loglik_grad", "gp_ss_loglik_batched",
            "gp_ss_loglik_grad_batched", "gp_ss_loglik_grad_host", "gp_ss_model_info",
            "gp_ss_set_chunk_len", "gp_ss_last_error_series", "gp_ss_free_model",
-           "gp_ss_status_string", "gp_ss_discretize", "gp_ss_set_timing", "gp_ss_get_timing"]
+           "gp_ss_status_string", "gp_ss_discretize", "gp_ss_set_timing", "gp_ss_get_timing",
+           "gp_ss_loglik_noalloc"]
 
 PHASES = ["elem", "scan", "grad", "convert", "plain"]
 
@@ -84,6 +86,7 @@ def load_library(path: str | None = None):
     lib.gp_ss_status_string.restype = ctypes.c_char_p
     lib.gp_ss_discretize.argtypes = [P(_KernelSpec), i32, vp, vp, i32, vp, vp, vp]
     lib.gp_ss_set_timing.argtypes = [vp, i32]
+    lib.gp_ss_loglik_noalloc.argtypes = [vp, vp, i32, i32, vp, vp]
     lib.gp_ss_get_timing.argtypes = [vp, vp, vp]
     _lib = lib
     return lib
@@ -195,6 +198,21 @@ class Model:
         f = self._lib.gp_ss_loglik_batched if batched else self._lib.gp_ss_loglik
         _check(f(self._h, th.data_ptr(), th.shape[0], int(bool(per_series)), out.data_ptr(),
                  _stream_ptr(stream)), "gp_ss_loglik")
+        return out
+
+    def loglik_noalloc(self, theta, per_series=True, out=None, stream=None):
+        """Log-likelihood through gp_ss_loglik_noalloc: the library allocates
+        nothing (its scratch is a fixed 16 MiB array per GPU).  For callers
+        that cannot allocate device memory at call time; calls that overlap on
+        the GPU share that array and must be serialised."""
+        import torch
+        th = self._theta(theta)
+        n = self.n_out(th, per_series)
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=th.device)
+        _check(self._lib.gp_ss_loglik_noalloc(self._h, th.data_ptr(), th.shape[0],
+                                              int(bool(per_series)), out.data_ptr(),
+                                              _stream_ptr(stream)), "gp_ss_loglik_noalloc")
         return out
 
     def loglik_grad(self, theta, per_series=True, out=None, grad=None, stream=None,

@@ -574,6 +574,7 @@ const char *gp_ss_status_string(gp_ss_status s) {
     case GP_SS_ECUDA: return "CUDA runtime error";
     case GP_SS_ENUMERIC: return "non-positive or non-finite innovation variance";
     case GP_SS_ETIMEOUT: return "bounded device wait timed out";
+    case GP_SS_ETOOBIG: return "problem needs more than the fixed scratch of gp_ss_loglik_noalloc";
   }
   return "unknown status";
 }
@@ -890,3 +891,76 @@ void gp_ss_free_model(gp_ss_model *m) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Log-likelihood without any device allocation.
+//
+// gp_ss_loglik takes its chunk-element scratch from the stream-ordered
+// allocator on every call.  Some callers cannot allocate device memory at
+// call time: a host application that has handed all device memory to its own
+// pool, code that must not risk the device-wide synchronisation or the
+// latency of an allocation inside a latency-critical loop, or a process whose
+// allocator is disabled or capped.  For them, gp_ss_loglik_noalloc runs the
+// same element pass and sequential per-series combination out of one fixed
+// scratch array compiled into this library.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB per GPU
+constexpr int kNoAllocMaxDevices = 64;
+
+// One copy exists on every GPU that loads the library, for the life of the
+// process.  Host code must not use this name as a pointer; it takes the
+// device address with cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the scratch array on `dev`, looked up once per device
+// with that device current.
+gp_ss_status noalloc_scratch(int dev, void **out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return GP_SS_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GP_SS_ECUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return GP_SS_OK;
+}
+
+}  // namespace
+
+extern "C" gp_ss_status gp_ss_loglik_noalloc(const gp_ss_model *m, const float *theta,
+                                             int n_sets, int theta_per_series,
+                                             double *loglik_out, void *cuda_stream) {
+  gp_ss_status s = check_call(m, theta, n_sets, theta_per_series, loglik_out);
+  if (s) return s;
+  if (m->precision != 32) return GP_SS_EUNSUPPORTED;
+  const int n_out = theta_per_series ? m->n_series : n_sets * m->n_series;
+  const int64_t n_vch64 = (int64_t)(theta_per_series ? 1 : n_sets) * m->n_chunks;
+  const OpTable &o = m->ops;
+  // element floats (field-major) then the three FP64 sums per chunk
+  const size_t f_bytes = ((size_t)o.NF * (size_t)n_vch64 * sizeof(float) + 255) & ~(size_t)255;
+  const size_t need = f_bytes + (size_t)o.ND * (size_t)n_vch64 * sizeof(double);
+  if (n_vch64 > INT32_MAX / 8 || need > kNoAllocScratchBytes) return GP_SS_ETOOBIG;
+  DeviceGuard g(m->device);
+  void *base = nullptr;
+  s = noalloc_scratch(m->device, &base);
+  if (s) return s;
+  float *ef = (float *)base;
+  double *ed = (double *)((unsigned char *)base + f_bytes);
+  const int n_vch = (int)n_vch64;
+  const gpss::DevModel dm = dev_view(m);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // every field the combination reads is written by the element pass first,
+  // so nothing in the shared array needs clearing between calls
+  if (o.elem(dm, theta, n_vch, theta_per_series, ef, ed, nullptr, st) != cudaSuccess)
+    return GP_SS_ECUDA;
+  if (o.scan(dm, n_out, theta_per_series, ef, ed, n_vch, nullptr, nullptr, loglik_out, 0,
+             nullptr, st) != cudaSuccess)
+    return GP_SS_ECUDA;
+  return GP_SS_OK;
+}
