@@ -285,10 +285,11 @@ gp_ss_status make_plan(gp_ss_model *m, int chunk_len) {
   int L = chunk_len;
   if (m->schedule == 1 || L <= 0) {
     if (m->schedule == 1) {
+      // one warp per series: 32 chunks of about K/32 events each
       int64_t mx = 1;
       for (int s = 0; s < n; ++s) mx = std::max<int64_t>(mx, m->ev_off[s + 1] - m->ev_off[s]);
-      if (mx > (int64_t)1 << 30) return GP_SS_EUNSUPPORTED;
-      L = (int)mx;
+      if (mx > (int64_t)1 << 35) return GP_SS_EUNSUPPORTED;
+      L = (int)std::max<int64_t>(1, (mx + 31) / 32);
     } else {
       L = kDefaultChunk;
     }
@@ -300,7 +301,10 @@ gp_ss_status make_plan(gp_ss_model *m, int chunk_len) {
   for (int s = 0; s < n; ++s) {
     first[s] = (int32_t)len.size();
     const int64_t a = m->ev_off[s], K = m->ev_off[s + 1] - a;
-    const int64_t nch = std::max<int64_t>(1, (K + L - 1) / L);
+    // a multiple of 32 chunks per series: every warp of the chunk kernels then
+    // works on one series (one hyperparameter row), which lets it share the
+    // row's Taylor table; chunk lengths are balanced within the series
+    const int64_t nch = 32 * std::max<int64_t>(1, (K + 32 * (int64_t)L - 1) / (32 * (int64_t)L));
     const int64_t base = K / nch, rem = K % nch;
     int64_t e = a, mi = m->meas_off[s];
     for (int64_t c = 0; c < nch; ++c) {
@@ -448,18 +452,20 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
     return true;
   };
   float *ef = nullptr, *state_end = nullptr, *info = nullptr, *adj = nullptr, *ckpt = nullptr,
-        *scratch = nullptr, *gpart = nullptr;
+        *scratch = nullptr, *gpart = nullptr, *tabs = nullptr;
   double *ed = nullptr, *ll_part = nullptr;
   gp_ss_status res = GP_SS_OK;
   do {
     if (!grab((void **)&ef, (size_t)o.NF * n_vch * sizeof(float)) ||
-        !grab((void **)&ed, (size_t)o.ND * n_vch * sizeof(double))) {
+        !grab((void **)&ed, (size_t)o.ND * n_vch * sizeof(double)) ||
+        !grab((void **)&tabs, (size_t)n_sets * o.NT * gpss::TAB_TERM * sizeof(float))) {
       res = GP_SS_ENOMEM;
       break;
     }
     {
       PhaseTimer pt(m, st, 0);
-      if (o.elem(dm, theta, n_vch, per_series, ef, ed, m->d_err, st)) {
+      if (o.tables(theta, n_sets, m->n_params, m->kinds[0], m->kinds[1], tabs, st) ||
+          o.elem(dm, theta, n_vch, per_series, ef, ed, m->d_err, tabs, st)) {
         res = GP_SS_ECUDA;
         break;
       }
@@ -503,7 +509,7 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
         break;
       }
       PhaseTimer pt(m, st, 2);
-      if (o.grad(dm, theta, n_vch, per_series, state_end, adj, ckpt, gpart, m->d_err, st)) {
+      if (o.grad(dm, theta, n_vch, per_series, state_end, adj, ckpt, gpart, m->d_err, tabs, st)) {
         res = GP_SS_ECUDA;
         break;
       }
@@ -728,8 +734,16 @@ gp_ss_status gp_ss_discretize(const gp_ss_kernel_spec *spec, int n_slots, const 
   const int layout = spec->n_terms == 1 ? 0 : spec->integral_layout;
   if (!pick_ops(spec->n_terms, n_slots, layout, &o)) return GP_SS_EUNSUPPORTED;
   const int k1 = spec->n_terms > 1 ? spec->terms[1] : 0;
-  GPSS_CK(o.disc(theta, spec->terms[0], k1, dt, n, phi_out, q_out, (cudaStream_t)cuda_stream));
-  return GP_SS_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int np = 1;
+  for (int t = 0; t < spec->n_terms; ++t) np += spec->terms[t] == GP_SS_TERM_SHO ? 3 : 2;
+  float *tabs = nullptr;
+  if (cudaMallocAsync((void **)&tabs, (size_t)o.NT * gpss::TAB_TERM * sizeof(float), st))
+    return GP_SS_ENOMEM;
+  cudaError_t e = o.tables(theta, 1, np, spec->terms[0], k1, tabs, st);
+  if (e == cudaSuccess) e = o.disc(theta, tabs, spec->terms[0], k1, dt, n, phi_out, q_out, st);
+  cudaFreeAsync(tabs, st);
+  return e == cudaSuccess ? GP_SS_OK : GP_SS_ECUDA;
 }
 
 gp_ss_status gp_ss_model_info(const gp_ss_model *m, int *n_series, int64_t *n_meas,
@@ -942,22 +956,27 @@ extern "C" gp_ss_status gp_ss_loglik_noalloc(const gp_ss_model *m, const float *
   const int n_out = theta_per_series ? m->n_series : n_sets * m->n_series;
   const int64_t n_vch64 = (int64_t)(theta_per_series ? 1 : n_sets) * m->n_chunks;
   const OpTable &o = m->ops;
-  // element floats (field-major) then the three FP64 sums per chunk
+  // Taylor tables of the hyperparameter rows, element floats (field-major),
+  // then the three FP64 sums per chunk
+  const size_t t_bytes =
+      ((size_t)n_sets * o.NT * gpss::TAB_TERM * sizeof(float) + 255) & ~(size_t)255;
   const size_t f_bytes = ((size_t)o.NF * (size_t)n_vch64 * sizeof(float) + 255) & ~(size_t)255;
-  const size_t need = f_bytes + (size_t)o.ND * (size_t)n_vch64 * sizeof(double);
+  const size_t need = t_bytes + f_bytes + (size_t)o.ND * (size_t)n_vch64 * sizeof(double);
   if (n_vch64 > INT32_MAX / 8 || need > kNoAllocScratchBytes) return GP_SS_ETOOBIG;
   DeviceGuard g(m->device);
   void *base = nullptr;
   s = noalloc_scratch(m->device, &base);
   if (s) return s;
-  float *ef = (float *)base;
-  double *ed = (double *)((unsigned char *)base + f_bytes);
+  float *tabs = (float *)base;
+  float *ef = (float *)((unsigned char *)base + t_bytes);
+  double *ed = (double *)((unsigned char *)base + t_bytes + f_bytes);
   const int n_vch = (int)n_vch64;
   const gpss::DevModel dm = dev_view(m);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   // every field the combination reads is written by the element pass first,
   // so nothing in the shared array needs clearing between calls
-  if (o.elem(dm, theta, n_vch, theta_per_series, ef, ed, nullptr, st) != cudaSuccess)
+  if (o.tables(theta, n_sets, m->n_params, m->kinds[0], m->kinds[1], tabs, st) != cudaSuccess ||
+      o.elem(dm, theta, n_vch, theta_per_series, ef, ed, nullptr, tabs, st) != cudaSuccess)
     return GP_SS_ECUDA;
   if (o.scan(dm, n_out, theta_per_series, ef, ed, n_vch, nullptr, nullptr, loglik_out, 0,
              nullptr, st) != cudaSuccess)

@@ -253,6 +253,140 @@ GPSS_D Disc<T> discretize(F t, T a, T beta) {
   return disc_closed<T, F>(t, a, beta, w2);
 }
 
+// ---------------------------------------------------------------------------
+// Taylor tables.  The Taylor coefficients of the six per-term scalars depend
+// only on (a, beta), so they are computed once per hyperparameter row and
+// evaluated per step by Horner's rule.  Each scalar is t^p0 * sum_k g_k t^k,
+// p0 = 1, 0, 2, 3, 1, 5 for f, f', F1, I_ff, I_pp, I_FF, with
+//   g^f_k   = c_{k+1},                  g^f'_k  = (k+1) c_{k+1},
+//   g^F1_k  = c_{k+1} / (k+2),
+//   g^Iff_k = sum_{n+m=k+2} c_n c_m / (k+3),
+//   g^Ipp_k = sum_{n+m=k+2} n m c_n c_m / (k+1),
+//   g^IFF_k = sum_{n+m=k+2} c_n c_m / ((n+1)(m+1)) / (k+5),
+// where f(s) = sum_{n>=1} c_n s^n (c_1 = 1, c_2 = -a,
+// c_{n+2} = -(2a (n+1) c_{n+1} + w2 c_n) / ((n+2)(n+1))).  Sixteen
+// coefficients keep the truncation below 1e-7 for omega0 t <= 1.2.
+//
+// Table layout per (row, term): for k = 0..NC-1 one record of TAB_W floats:
+// [6 values, 2 pad, 6 d/da, 2 pad, 6 d/dbeta, 2 pad].
+// ---------------------------------------------------------------------------
+constexpr int TAB_NC = 16;
+constexpr int TAB_W = 24;
+constexpr int TAB_TERM = TAB_NC * TAB_W;
+
+template <class T>
+GPSS_HD void taylor_coeffs(T a, T beta, T (&g)[6][TAB_NC]) {
+  constexpr int NCF = TAB_NC + 2;
+  T c[NCF + 1];
+  const T w2 = beta + a * a;
+  c[0] = a * 0.0;
+  c[1] = c[0] + 1.0;
+  c[2] = -a;
+  for (int n = 1; n + 2 <= NCF; ++n)
+    c[n + 2] = -(a * (2.0 * (n + 1)) * c[n + 1] + w2 * c[n]) / (double)((n + 2) * (n + 1));
+  for (int k = 0; k < TAB_NC; ++k) {
+    g[0][k] = c[k + 1];
+    g[1][k] = c[k + 1] * (double)(k + 1);
+    g[2][k] = c[k + 1] / (double)(k + 2);
+    T s1 = c[0], s2 = c[0], s3 = c[0];
+    for (int n = 1; n <= k + 1; ++n) {
+      const int m = k + 2 - n;
+      const T pp = c[n] * c[m];
+      s1 = s1 + pp;
+      s2 = s2 + pp * (double)(n * m);
+      s3 = s3 + pp / (double)((n + 1) * (m + 1));
+    }
+    g[3][k] = s1 / (double)(k + 3);
+    g[4][k] = s2 / (double)(k + 1);
+    g[5][k] = s3 / (double)(k + 5);
+  }
+}
+
+// Six Taylor-branch scalars from a table in shared memory (broadcast reads).
+GPSS_D Disc<float> disc_tab(float t, const float4 *__restrict__ tab) {
+  float acc[6];
+  {
+    const float4 q0 = tab[(TAB_NC - 1) * (TAB_W / 4)], q1 = tab[(TAB_NC - 1) * (TAB_W / 4) + 1];
+    acc[0] = q0.x; acc[1] = q0.y; acc[2] = q0.z; acc[3] = q0.w; acc[4] = q1.x; acc[5] = q1.y;
+  }
+#pragma unroll 3
+  for (int k = TAB_NC - 2; k >= 0; --k) {
+    const float4 q0 = tab[k * (TAB_W / 4)], q1 = tab[k * (TAB_W / 4) + 1];
+    acc[0] = fmaf(acc[0], t, q0.x);
+    acc[1] = fmaf(acc[1], t, q0.y);
+    acc[2] = fmaf(acc[2], t, q0.z);
+    acc[3] = fmaf(acc[3], t, q0.w);
+    acc[4] = fmaf(acc[4], t, q1.x);
+    acc[5] = fmaf(acc[5], t, q1.y);
+  }
+  const float t2 = t * t, t3 = t2 * t;
+  Disc<float> d;
+  d.f = acc[0] * t;
+  d.fp = acc[1];
+  d.F1 = acc[2] * t2;
+  d.Iff = acc[3] * t3;
+  d.Ipp = acc[4] * t;
+  d.IFF = acc[5] * (t3 * t2);
+  return d;
+}
+
+GPSS_D Disc<Dual2<float>> disc_tab_dual(float t, const float4 *__restrict__ tab) {
+  float v[6], da[6], db[6];
+  {
+    const float4 *r = tab + (TAB_NC - 1) * (TAB_W / 4);
+    const float4 q0 = r[0], q1 = r[1], q2 = r[2], q3 = r[3], q4 = r[4], q5 = r[5];
+    v[0] = q0.x; v[1] = q0.y; v[2] = q0.z; v[3] = q0.w; v[4] = q1.x; v[5] = q1.y;
+    da[0] = q2.x; da[1] = q2.y; da[2] = q2.z; da[3] = q2.w; da[4] = q3.x; da[5] = q3.y;
+    db[0] = q4.x; db[1] = q4.y; db[2] = q4.z; db[3] = q4.w; db[4] = q5.x; db[5] = q5.y;
+  }
+#pragma unroll 2
+  for (int k = TAB_NC - 2; k >= 0; --k) {
+    const float4 *r = tab + k * (TAB_W / 4);
+    const float4 q0 = r[0], q1 = r[1], q2 = r[2], q3 = r[3], q4 = r[4], q5 = r[5];
+    v[0] = fmaf(v[0], t, q0.x); v[1] = fmaf(v[1], t, q0.y); v[2] = fmaf(v[2], t, q0.z);
+    v[3] = fmaf(v[3], t, q0.w); v[4] = fmaf(v[4], t, q1.x); v[5] = fmaf(v[5], t, q1.y);
+    da[0] = fmaf(da[0], t, q2.x); da[1] = fmaf(da[1], t, q2.y); da[2] = fmaf(da[2], t, q2.z);
+    da[3] = fmaf(da[3], t, q2.w); da[4] = fmaf(da[4], t, q3.x); da[5] = fmaf(da[5], t, q3.y);
+    db[0] = fmaf(db[0], t, q4.x); db[1] = fmaf(db[1], t, q4.y); db[2] = fmaf(db[2], t, q4.z);
+    db[3] = fmaf(db[3], t, q4.w); db[4] = fmaf(db[4], t, q5.x); db[5] = fmaf(db[5], t, q5.y);
+  }
+  const float t2 = t * t, t3 = t2 * t;
+  const float sc[6] = {t, 1.f, t2, t3, t, t3 * t2};
+  Disc<Dual2<float>> d;
+  Dual2<float> *o[6] = {&d.f, &d.fp, &d.F1, &d.Iff, &d.Ipp, &d.IFF};
+#pragma unroll
+  for (int i = 0; i < 6; ++i) *o[i] = mk(v[i] * sc[i], da[i] * sc[i], db[i] * sc[i]);
+  return d;
+}
+
+// Discretisation with the Taylor branch read from a table.
+GPSS_D Disc<float> discretize_tab(float t, float a, float beta, const float4 *tab) {
+  const float w2 = beta + a * a;
+  if (t == 0.f) {
+    Disc<float> d;
+    d.f = 0.f;
+    d.fp = 1.f;
+    d.F1 = d.Iff = d.Ipp = d.IFF = 0.f;
+    return d;
+  }
+  if (w2 * t * t <= TaylorOrder<float>::XT2) return disc_tab(t, tab);
+  return disc_closed<float, float>(t, a, beta, w2);
+}
+
+GPSS_D Disc<Dual2<float>> discretize_tab_dual(float t, float a, float beta, const float4 *tab) {
+  const float w2 = beta + a * a;
+  if (t == 0.f) {
+    Disc<Dual2<float>> d;
+    d.f = mk(0.f, 0.f, 0.f);
+    d.fp = mk(1.f, 0.f, 0.f);
+    d.F1 = d.Iff = d.Ipp = d.IFF = d.f;
+    return d;
+  }
+  if (w2 * t * t <= TaylorOrder<float>::XT2) return disc_tab_dual(t, tab);
+  return disc_closed<Dual2<float>, float>(t, mk(a, 1.f, 0.f), mk(beta, 0.f, 1.f),
+                                          mk(w2, 2.f * a, 1.f));
+}
+
 // Per-term constants from natural parameters.
 template <class F>
 struct TermC {

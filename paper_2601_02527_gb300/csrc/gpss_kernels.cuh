@@ -79,14 +79,27 @@ template <> GPSS_D void load_meas<double>(const DevModel &M, int64_t i, double &
 
 // One event of the sequential filter on (m, P); returns true for an end
 // event, with S and v of its innovation.
+// Per-step scalars of term t: from the warp's Taylor table when one is given
+// (FP32 chunk kernels), else from the on-the-fly series (per-series kernels).
+template <class F>
+GPSS_D Disc<F> disc_step(F dt, const TermC<F> &c, const float4 *tab) {
+  return discretize<F, F>(dt, c.a, c.beta);
+}
+template <>
+GPSS_D Disc<float> disc_step<float>(float dt, const TermC<float> &c, const float4 *tab) {
+  if (tab) return discretize_tab(dt, c.a, c.beta, tab);
+  return discretize<float, float>(dt, c.a, c.beta);
+}
+
 template <class S, class F>
 GPSS_D bool filter_event(const DevModel &M, int64_t k, int64_t &mi, const TermC<F> *tc, F s2, F *m,
-                         F *P, F &Sv, F &v) {
+                         F *P, F &Sv, F &v, const float4 *tab = nullptr) {
   const F dt = load_dt<F>(M, k);
   const uint8_t tag = __ldg(M.tag + k);
   Blocks<F> B[S::NT];
 #pragma unroll
-  for (int t = 0; t < S::NT; ++t) B[t] = make_blocks(discretize<F, F>(dt, tc[t].a, tc[t].beta), tc[t]);
+  for (int t = 0; t < S::NT; ++t)
+    B[t] = make_blocks(disc_step<F>(dt, tc[t], tab ? tab + t * (TAB_TERM / 4) : nullptr), tc[t]);
   F mt[S::D];
   apply_phi<S>(B, m, mt);
 #pragma unroll
@@ -117,6 +130,45 @@ GPSS_D bool filter_event(const DevModel &M, int64_t k, int64_t &mi, const TermC<
 
 GPSS_D void flag_error(int *err, int row, int code) {
   if (err) atomicMax(err + row, code);
+}
+
+// ---------------------------------------------------------------------------
+// Taylor tables, one thread per (hyperparameter row, term), FP64 arithmetic.
+// ---------------------------------------------------------------------------
+template <int NT>
+__global__ void k_tables(const float *__restrict__ theta, int n_rows, int n_params, int kind0,
+                         int kind1, float *__restrict__ tab) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_rows * NT) return;
+  const int row = idx / NT, t = idx % NT;
+  const int kinds[4] = {kind0, kind1, 0, 0};
+  TermC<double> tc[NT];
+  double s2;
+  load_terms<NT, double>(theta + (size_t)row * n_params, kinds, tc, s2);
+  Dual2<double> g[6][TAB_NC];
+  taylor_coeffs<Dual2<double>>(mk(tc[t].a, 1.0, 0.0), mk(tc[t].beta, 0.0, 1.0), g);
+  float *o = tab + (size_t)idx * TAB_TERM;
+  for (int k = 0; k < TAB_NC; ++k) {
+    float *r = o + k * TAB_W;
+    for (int j = 0; j < TAB_W; ++j) r[j] = 0.f;
+    for (int j = 0; j < 6; ++j) {
+      r[j] = (float)g[j][k].v;
+      r[8 + j] = (float)g[j][k].da;
+      r[16 + j] = (float)g[j][k].db;
+    }
+  }
+}
+
+// Copy the table of hyperparameter row `row` (all NT terms) into this warp's
+// shared-memory slot.  Every lane of a warp works on the same row (the chunk
+// plan gives each series a multiple of 32 chunks).
+template <int NT>
+GPSS_D const float4 *stage_table(const float *__restrict__ tab, int row, float4 *slot) {
+  const float4 *src = reinterpret_cast<const float4 *>(tab + (size_t)row * NT * TAB_TERM);
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < NT * TAB_TERM / 4; i += 32) slot[i] = __ldg(src + i);
+  __syncwarp();
+  return slot;
 }
 
 // ---------------------------------------------------------------------------
@@ -169,9 +221,11 @@ struct ElemLayout : Elem<S> {
 template <class S>
 __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restrict__ theta, int n_vch,
                                               int per_series, float *__restrict__ ef,
-                                              double *__restrict__ ed, int *__restrict__ err) {
+                                              double *__restrict__ ed, int *__restrict__ err,
+                                              const float *__restrict__ tabs) {
   using F = float;
   constexpr int D = S::D;
+  extern __shared__ float4 smem_tab[];
   const int vc = blockIdx.x * blockDim.x + threadIdx.x;
   if (vc >= n_vch) return;
   const int c = vc % M.n_chunks;
@@ -182,6 +236,8 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
   TermC<F> tc[S::NT];
   F s2;
   load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tc, s2);
+  const float4 *tab =
+      stage_table<S::NT>(tabs, row, smem_tab + (threadIdx.x >> 5) * (S::NT * TAB_TERM / 4));
   const bool first = M.ch_flags[c] & 1;
   F A[D][D], b[D], C[S::NP], eta[D], J[S::NP];
   if (first) {
@@ -212,7 +268,8 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
     const uint8_t tag = __ldg(M.tag + k);
     Blocks<F> B[S::NT];
 #pragma unroll
-    for (int t = 0; t < S::NT; ++t) B[t] = make_blocks(discretize<F, F>(dt, tc[t].a, tc[t].beta), tc[t]);
+    for (int t = 0; t < S::NT; ++t)
+      B[t] = make_blocks(discretize_tab(dt, tc[t].a, tc[t].beta, tab + t * (TAB_TERM / 4)), tc[t]);
     // A <- Phi~ A (column by column), b <- Phi~ b, C <- Phi~ C Phi~^T + Q~
 #pragma unroll
     for (int col = 0; col < D; ++col) {
@@ -644,7 +701,7 @@ struct TermGrad {
 template <class S>
 GPSS_D void reverse_event(const DevModel &M, int64_t k, int64_t mi, const TermC<float> *tc,
                           float s2, const float *m, const float *P, float *lam, float *Lam,
-                          TermGrad<S::NT> &gr) {
+                          TermGrad<S::NT> &gr, const float4 *tab) {
   using F = float;
   using DF = Dual2<float>;
   constexpr int D = S::D;
@@ -655,7 +712,7 @@ GPSS_D void reverse_event(const DevModel &M, int64_t k, int64_t mi, const TermC<
   Blocks<F> B[S::NT];
 #pragma unroll
   for (int t = 0; t < S::NT; ++t) {
-    dd[t] = discretize<DF, F>(dt, mk(tc[t].a, F(1), F(0)), mk(tc[t].beta, F(0), F(1)));
+    dd[t] = discretize_tab_dual(dt, tc[t].a, tc[t].beta, tab + t * (TAB_TERM / 4));
     Disc<F> d{dd[t].f.v, dd[t].fp.v, dd[t].F1.v, dd[t].Iff.v, dd[t].Ipp.v, dd[t].IFF.v};
     B[t] = make_blocks(d, tc[t]);
   }
@@ -810,7 +867,8 @@ __global__ void __launch_bounds__(64) k_grad(DevModel M, const float *__restrict
                                              int per_series, const float *__restrict__ state_end,
                                              const float *__restrict__ adj_end,
                                              float *__restrict__ ckpt, float *__restrict__ gpart,
-                                             int *__restrict__ err) {
+                                             int *__restrict__ err,
+                                             const float *__restrict__ tabs) {
   using F = float;
   constexpr int D = S::D;
   constexpr int SD = D + S::NP;
@@ -825,6 +883,10 @@ __global__ void __launch_bounds__(64) k_grad(DevModel M, const float *__restrict
   TermC<F> tc[S::NT];
   F s2;
   load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tc, s2);
+  const int bs = blockDim.x;
+  // shared memory: [segment states CK*SD*bs | measurement indices CK*bs | tables]
+  float4 *tab_slots = reinterpret_cast<float4 *>(sm + (size_t)CK * (SD + 1) * bs);
+  const float4 *tab = stage_table<S::NT>(tabs, row, tab_slots + (threadIdx.x >> 5) * (S::NT * TAB_TERM / 4));
   const uint8_t flags = M.ch_flags[c];
   const bool first = flags & 1, last = flags & 2;
   F m[D], P[S::NP];
@@ -835,21 +897,6 @@ __global__ void __launch_bounds__(64) k_grad(DevModel M, const float *__restrict
   const int64_t e0 = M.ch_ev0[c];
   const int len = M.ch_len[c];
   const int nseg = (len + CK - 1) / CK;
-  // pass 1: forward from the incoming state, checkpoint (m, P, measurement
-  // index) at the start of every segment of CK events
-  bool bad = false;
-  int64_t mi = M.ch_meas0[c];
-  for (int kk = 0; kk < len; ++kk) {
-    if (kk % CK == 0) {
-      float *dst = ckpt + (size_t)(kk / CK) * (SD + 1) * n_vch;
-      store_rec<S>(dst, n_vch, vc, m, P);
-      dst[(size_t)SD * n_vch + vc] = __int_as_float((int)(mi - M.ch_meas0[c]));
-    }
-    F Sv, vv;
-    if (filter_event<S, F>(M, e0 + kk, mi, tc, s2, m, P, Sv, vv)) bad |= !(Sv > F(0));
-  }
-  // pass 2: reverse sweep, segment by segment; each segment is replayed from
-  // its checkpoint into shared memory and then walked backwards
   F lam[D], Lam[S::NP];
   if (last) {
 #pragma unroll
@@ -863,33 +910,58 @@ __global__ void __launch_bounds__(64) k_grad(DevModel M, const float *__restrict
 #pragma unroll
   for (int t = 0; t < S::NT; ++t) gr.a[t] = gr.beta[t] = gr.w2[t] = gr.qc[t] = gr.var[t] = F(0);
   gr.s2 = F(0);
-  const int bs = blockDim.x;
   float *my = sm + threadIdx.x;
   int *mys = reinterpret_cast<int *>(sm + (size_t)CK * SD * bs) + threadIdx.x;
-  for (int seg = nseg - 1; seg >= 0; --seg) {
+  bool bad = false;
+  // One forward loop serves both the checkpointing pass over the whole chunk
+  // (replay = false) and the replay of one segment into shared memory
+  // (replay = true); after each replay the segment is walked backwards.
+  bool replay = false;
+  int seg = nseg - 1;
+  int kk = 0, kend = len;
+  int64_t mi = M.ch_meas0[c];
+  for (;;) {
+    if (kk < kend) {
+      if (!replay) {
+        if (kk % CK == 0) {
+          float *dst = ckpt + (size_t)(kk / CK) * (SD + 1) * n_vch;
+          store_rec<S>(dst, n_vch, vc, m, P);
+          dst[(size_t)SD * n_vch + vc] = __int_as_float((int)(mi - M.ch_meas0[c]));
+        }
+      } else {
+        const int slot = kk - seg * CK;
+#pragma unroll
+        for (int i = 0; i < D; ++i) my[(slot * SD + i) * bs] = m[i];
+#pragma unroll
+        for (int i = 0; i < S::NP; ++i) my[(slot * SD + D + i) * bs] = P[i];
+        mys[slot * bs] = (int)(mi - M.ch_meas0[c]);
+      }
+      F Sv, vv;
+      if (filter_event<S, F>(M, e0 + kk, mi, tc, s2, m, P, Sv, vv, tab)) bad |= !(Sv > F(0));
+      ++kk;
+      continue;
+    }
+    if (replay) {
+      // backward walk over the replayed segment
+      for (int k2 = kend - 1; k2 >= seg * CK; --k2) {
+        const int slot = k2 - seg * CK;
+#pragma unroll
+        for (int i = 0; i < D; ++i) m[i] = my[(slot * SD + i) * bs];
+#pragma unroll
+        for (int i = 0; i < S::NP; ++i) P[i] = my[(slot * SD + D + i) * bs];
+        reverse_event<S>(M, e0 + k2, M.ch_meas0[c] + mys[slot * bs], tc, s2, m, P, lam, Lam, gr,
+                         tab);
+      }
+      --seg;
+    }
+    if (seg < 0) break;
+    // start (or continue) replaying segment `seg` from its checkpoint
+    replay = true;
     const float *src = ckpt + (size_t)seg * (SD + 1) * n_vch;
     load_rec<S>(src, n_vch, vc, m, P);
-    int64_t mcur = M.ch_meas0[c] + __float_as_int(src[(size_t)SD * n_vch + vc]);
-    const int kb = seg * CK;
-    const int ke = min(kb + CK, len);
-    for (int kk = kb; kk < ke; ++kk) {
-      const int slot = kk - kb;
-#pragma unroll
-      for (int i = 0; i < D; ++i) my[(slot * SD + i) * bs] = m[i];
-#pragma unroll
-      for (int i = 0; i < S::NP; ++i) my[(slot * SD + D + i) * bs] = P[i];
-      mys[slot * bs] = (int)(mcur - M.ch_meas0[c]);
-      F Sv, vv;
-      filter_event<S, F>(M, e0 + kk, mcur, tc, s2, m, P, Sv, vv);
-    }
-    for (int kk = ke - 1; kk >= kb; --kk) {
-      const int slot = kk - kb;
-#pragma unroll
-      for (int i = 0; i < D; ++i) m[i] = my[(slot * SD + i) * bs];
-#pragma unroll
-      for (int i = 0; i < S::NP; ++i) P[i] = my[(slot * SD + D + i) * bs];
-      reverse_event<S>(M, e0 + kk, M.ch_meas0[c] + mys[slot * bs], tc, s2, m, P, lam, Lam, gr);
-    }
+    mi = M.ch_meas0[c] + __float_as_int(src[(size_t)SD * n_vch + vc]);
+    kk = seg * CK;
+    kend = min(kk + CK, len);
   }
   if (first) {
     // P0 = blkdiag(var diag(1, w2), I)
@@ -944,21 +1016,21 @@ __global__ void k_series_sum(int n_out, int per_series, int n_series, int n_chun
 
 // Dense Phi~(dt_k), Q~(dt_k) for a list of gaps (one thread per gap).
 template <class S>
-__global__ void k_disc(const float *__restrict__ theta, const int *kinds, int kinds0, int kinds1,
-                       const float *__restrict__ dt, int n, float *__restrict__ phi,
+__global__ void k_disc(const float *__restrict__ theta, const float *__restrict__ tabs, int kinds0,
+                       int kinds1, const float *__restrict__ dt, int n, float *__restrict__ phi,
                        float *__restrict__ q) {
   constexpr int D = S::D;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   int kk[4] = {kinds0, kinds1, 0, 0};
-  (void)kinds;
   TermC<float> tc[S::NT];
   float s2;
   load_terms<S::NT, float>(theta, kk, tc, s2);
+  const float4 *tab = reinterpret_cast<const float4 *>(tabs);
   Blocks<float> B[S::NT];
 #pragma unroll
   for (int t = 0; t < S::NT; ++t)
-    B[t] = make_blocks(discretize<float, float>(dt[k], tc[t].a, tc[t].beta), tc[t]);
+    B[t] = make_blocks(discretize_tab(dt[k], tc[t].a, tc[t].beta, tab + t * (TAB_TERM / 4)), tc[t]);
   float P[S::NP];
 #pragma unroll
   for (int i = 0; i < S::NP; ++i) P[i] = 0.f;
@@ -986,16 +1058,19 @@ struct OpTable {
   cudaError_t (*plain32)(const DevModel &, const float *, int, int, double *, int *, cudaStream_t);
   cudaError_t (*plain64)(const DevModel &, const float *, int, int, double *, int *, cudaStream_t);
   cudaError_t (*elem)(const DevModel &, const float *, int, int, float *, double *, int *,
-                      cudaStream_t);
+                      const float *, cudaStream_t);
   cudaError_t (*scan)(const DevModel &, int, int, const float *, const double *, int, float *,
                       float *, double *, int, int *, cudaStream_t);
   cudaError_t (*grad)(const DevModel &, const float *, int, int, const float *, const float *,
-                      float *, float *, int *, cudaStream_t);
+                      float *, float *, int *, const float *, cudaStream_t);
+  cudaError_t (*tables)(const float *, int, int, int, int, float *, cudaStream_t);
+  int NT;
   cudaError_t (*scan_tree)(const float *, int, float *, int, int, float *, cudaStream_t);
   size_t (*scan_scratch)(int);
   cudaError_t (*finish)(const DevModel &, int, int, const float *, const double *, const float *,
                         const float *, float *, double *, int *, cudaStream_t);
-  cudaError_t (*disc)(const float *, int, int, const float *, int, float *, float *, cudaStream_t);
+  cudaError_t (*disc)(const float *, const float *, int, int, const float *, int, float *, float *,
+                      cudaStream_t);
 };
 
 constexpr int GRAD_CK = 8;
@@ -1012,10 +1087,21 @@ cudaError_t launch_plain(const DevModel &M, const float *theta, int n_out, int p
 
 template <class S>
 cudaError_t launch_elem(const DevModel &M, const float *theta, int n_vch, int per_series,
-                        float *ef, double *ed, int *err, cudaStream_t st) {
+                        float *ef, double *ed, int *err, const float *tabs, cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
   const int bs = 128;
-  k_elem<S><<<(n_vch + bs - 1) / bs, bs, 0, st>>>(M, theta, n_vch, per_series, ef, ed, err);
+  const size_t smem = (size_t)(bs / 32) * S::NT * TAB_TERM * sizeof(float);
+  k_elem<S><<<(n_vch + bs - 1) / bs, bs, smem, st>>>(M, theta, n_vch, per_series, ef, ed, err,
+                                                    tabs);
+  return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_tables(const float *theta, int n_rows, int n_params, int k0, int k1,
+                          float *tab, cudaStream_t st) {
+  const int n = n_rows * S::NT;
+  if (n <= 0) return cudaSuccess;
+  k_tables<S::NT><<<(n + 63) / 64, 64, 0, st>>>(theta, n_rows, n_params, k0, k1, tab);
   return cudaGetLastError();
 }
 
@@ -1056,10 +1142,11 @@ cudaError_t launch_finish(const DevModel &M, int n_vch, int per_series, const fl
 template <class S>
 cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int per_series,
                         const float *state_end, const float *adj_end, float *ckpt, float *gpart,
-                        int *err, cudaStream_t st) {
+                        int *err, const float *tabs, cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
   constexpr int SD = S::D + S::NP;
-  const size_t smem = (size_t)GRAD_CK * (SD + 1) * GRAD_BS * sizeof(float);
+  const size_t smem = (size_t)GRAD_CK * (SD + 1) * GRAD_BS * sizeof(float) +
+                      (size_t)(GRAD_BS / 32) * S::NT * TAB_TERM * sizeof(float);
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(k_grad<S, GRAD_CK>,
@@ -1068,15 +1155,15 @@ cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int pe
     attr_done = true;
   }
   k_grad<S, GRAD_CK><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
-      M, theta, n_vch, per_series, state_end, adj_end, ckpt, gpart, err);
+      M, theta, n_vch, per_series, state_end, adj_end, ckpt, gpart, err, tabs);
   return cudaGetLastError();
 }
 
 template <class S>
-cudaError_t launch_disc(const float *theta, int k0, int k1, const float *dt, int n, float *phi,
-                        float *q, cudaStream_t st) {
+cudaError_t launch_disc(const float *theta, const float *tabs, int k0, int k1, const float *dt,
+                        int n, float *phi, float *q, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_disc<S><<<(n + 127) / 128, 128, 0, st>>>(theta, nullptr, k0, k1, dt, n, phi, q);
+  k_disc<S><<<(n + 127) / 128, 128, 0, st>>>(theta, tabs, k0, k1, dt, n, phi, q);
   return cudaGetLastError();
 }
 
@@ -1097,6 +1184,8 @@ OpTable make_ops() {
   o.scan_tree = &launch_scan_tree<S>;
   o.scan_scratch = &scan_scratch_count<S>;
   o.finish = &launch_finish<S>;
+  o.tables = &launch_tables<S>;
+  o.NT = S::NT;
   return o;
 }
 
