@@ -107,16 +107,16 @@ GPSS_HD float val(float x) { return x; }
 GPSS_HD double val(double x) { return x; }
 template <class F> GPSS_HD F val(Dual2<F> x) { return x.v; }
 
-GPSS_D float gexp(float x) { return expf(x); }
-GPSS_D double gexp(double x) { return exp(x); }
-template <class F> GPSS_D Dual2<F> gexp(Dual2<F> x) {
+GPSS_HD float gexp(float x) { return expf(x); }
+GPSS_HD double gexp(double x) { return exp(x); }
+template <class F> GPSS_HD Dual2<F> gexp(Dual2<F> x) {
   F e = gexp(x.v);
   return mk(e, e * x.da, e * x.db);
 }
 
 // S(beta, t) = sin(sqrt(beta) t) / sqrt(beta)  (= t at beta = 0),
 // C(beta, t) = cos(sqrt(beta) t), for beta >= 0.
-GPSS_D void sinc_pair(float beta, float t, float &S, float &C) {
+GPSS_HD void sinc_pair(float beta, float t, float &S, float &C) {
   float b = sqrtf(beta);
   float tau = b * t;
   float s, c;
@@ -124,7 +124,7 @@ GPSS_D void sinc_pair(float beta, float t, float &S, float &C) {
   C = c;
   S = (tau < 1e-3f) ? t * (1.0f - tau * tau * (1.0f / 6.0f)) : s / b;
 }
-GPSS_D void sinc_pair(double beta, double t, double &S, double &C) {
+GPSS_HD void sinc_pair(double beta, double t, double &S, double &C) {
   double b = sqrt(beta);
   double tau = b * t;
   double s, c;
@@ -136,7 +136,7 @@ GPSS_D void sinc_pair(double beta, double t, double &S, double &C) {
 // for small beta t^2 is evaluated from its series
 // t^3 (-1/6 + beta t^2/60 - beta^2 t^4/1680 + beta^3 t^6/90720 - ...).
 template <class F>
-GPSS_D void sinc_pair(Dual2<F> beta, F t, Dual2<F> &S, Dual2<F> &C) {
+GPSS_HD void sinc_pair(Dual2<F> beta, F t, Dual2<F> &S, Dual2<F> &C) {
   F s, c;
   sinc_pair(beta.v, t, s, c);
   F x = beta.v * t * t;
@@ -159,11 +159,11 @@ struct Disc {
 };
 
 template <class F> struct TaylorOrder;
-// Degree and range of the Taylor branch: FP32 degree 14 for omega0 t <= 1.2
+// Degree and range of the Taylor branch: FP32 degree 16 for omega0 t <= 1.2
 // and FP64 degree 20 for omega0 t <= 1 keep the truncation below the
 // rounding of the closed forms that take over above (FP32: <= ~4e-6 relative
 // from omega0 t = 1.2 on; below it their cancellation grows like (omega0 t)^-4).
-template <> struct TaylorOrder<float> { static constexpr int N = 14; static constexpr float XT2 = 1.44f; };
+template <> struct TaylorOrder<float> { static constexpr int N = 16; static constexpr float XT2 = 1.44f; };
 template <> struct TaylorOrder<double> { static constexpr int N = 20; static constexpr double XT2 = 1.0; };
 
 // Taylor branch: f(s) = sum_{n>=1} c_n s^n with c_1 = 1, c_2 = -a,
@@ -173,7 +173,7 @@ template <> struct TaylorOrder<double> { static constexpr int N = 20; static con
 //   I_FF = t^3 sum p_n p_m / ((n+1)(m+1)(n+m+3))
 // (double sums over n + m <= N + 1).
 template <class T, class F>
-GPSS_D Disc<T> disc_taylor(F t, T a, T w2) {
+GPSS_HD Disc<T> disc_taylor(F t, T a, T w2) {
   constexpr int N = TaylorOrder<F>::N;
   T p[N + 1];
   p[1] = cst<T>(t);
@@ -218,7 +218,7 @@ GPSS_D Disc<T> disc_taylor(F t, T a, T w2) {
 }
 
 template <class T, class F>
-GPSS_D Disc<T> disc_closed(F t, T a, T beta, T w2) {
+GPSS_HD Disc<T> disc_closed(F t, T a, T beta, T w2) {
   T E = gexp(-a * t);
   T S, C;
   sinc_pair(beta, t, S, C);
@@ -237,7 +237,7 @@ GPSS_D Disc<T> disc_closed(F t, T a, T beta, T w2) {
 
 // All six per-term scalars for a step of length t >= 0.
 template <class T, class F>
-GPSS_D Disc<T> discretize(F t, T a, T beta) {
+GPSS_HD Disc<T> discretize(F t, T a, T beta) {
   T w2 = beta + a * a;
   if (t == F(0)) {
     Disc<T> d;
@@ -303,7 +303,7 @@ GPSS_HD void taylor_coeffs(T a, T beta, T (&g)[6][TAB_NC]) {
 }
 
 // Six Taylor-branch scalars from a table in shared memory (broadcast reads).
-GPSS_D Disc<float> disc_tab(float t, const float4 *__restrict__ tab) {
+GPSS_HD Disc<float> disc_tab(float t, const float4 *__restrict__ tab) {
   float acc[6];
   {
     const float4 q0 = tab[(TAB_NC - 1) * (TAB_W / 4)], q1 = tab[(TAB_NC - 1) * (TAB_W / 4) + 1];
@@ -330,7 +330,7 @@ GPSS_D Disc<float> disc_tab(float t, const float4 *__restrict__ tab) {
   return d;
 }
 
-GPSS_D Disc<Dual2<float>> disc_tab_dual(float t, const float4 *__restrict__ tab) {
+GPSS_HD Disc<Dual2<float>> disc_tab_dual(float t, const float4 *__restrict__ tab) {
   float v[6], da[6], db[6];
   {
     const float4 *r = tab + (TAB_NC - 1) * (TAB_W / 4);
@@ -360,7 +360,7 @@ GPSS_D Disc<Dual2<float>> disc_tab_dual(float t, const float4 *__restrict__ tab)
 }
 
 // Discretisation with the Taylor branch read from a table.
-GPSS_D Disc<float> discretize_tab(float t, float a, float beta, const float4 *tab) {
+GPSS_HD Disc<float> discretize_tab(float t, float a, float beta, const float4 *tab) {
   const float w2 = beta + a * a;
   if (t == 0.f) {
     Disc<float> d;
@@ -373,7 +373,7 @@ GPSS_D Disc<float> discretize_tab(float t, float a, float beta, const float4 *ta
   return disc_closed<float, float>(t, a, beta, w2);
 }
 
-GPSS_D Disc<Dual2<float>> discretize_tab_dual(float t, float a, float beta, const float4 *tab) {
+GPSS_HD Disc<Dual2<float>> discretize_tab_dual(float t, float a, float beta, const float4 *tab) {
   const float w2 = beta + a * a;
   if (t == 0.f) {
     Disc<Dual2<float>> d;
@@ -400,7 +400,7 @@ struct Blocks {
 };
 
 template <class F>
-GPSS_D Blocks<F> make_blocks(const Disc<F> &d, const TermC<F> &c) {
+GPSS_HD Blocks<F> make_blocks(const Disc<F> &d, const TermC<F> &c) {
   Blocks<F> B;
   B.p00 = d.fp + F(2) * c.a * d.f;
   B.p01 = d.f;
@@ -419,7 +419,7 @@ GPSS_D Blocks<F> make_blocks(const Disc<F> &d, const TermC<F> &c) {
 
 // out = Phi~ v
 template <class S, class F>
-GPSS_D void apply_phi(const Blocks<F> *B, const F *v, F *out) {
+GPSS_HD void apply_phi(const Blocks<F> *B, const F *v, F *out) {
 #pragma unroll
   for (int t = 0; t < S::NT; ++t) {
     out[2 * t] = B[t].p00 * v[2 * t] + B[t].p01 * v[2 * t + 1];
@@ -437,7 +437,7 @@ GPSS_D void apply_phi(const Blocks<F> *B, const F *v, F *out) {
 
 // out = Phi~^T v
 template <class S, class F>
-GPSS_D void apply_phi_t(const Blocks<F> *B, const F *v, F *out) {
+GPSS_HD void apply_phi_t(const Blocks<F> *B, const F *v, F *out) {
 #pragma unroll
   for (int t = 0; t < S::NT; ++t) {
     F a0 = B[t].p00 * v[2 * t] + B[t].p10 * v[2 * t + 1];
@@ -457,7 +457,7 @@ GPSS_D void apply_phi_t(const Blocks<F> *B, const F *v, F *out) {
 
 // P <- P + Q~ (packed)
 template <class S, class F>
-GPSS_D void add_q(const Blocks<F> *B, F *P) {
+GPSS_HD void add_q(const Blocks<F> *B, F *P) {
 #pragma unroll
   for (int t = 0; t < S::NT; ++t) {
     P[S::pk(2 * t, 2 * t)] += B[t].q00;
@@ -484,7 +484,7 @@ GPSS_D void add_q(const Blocks<F> *B, F *P) {
 
 // P <- Phi~ P Phi~^T + Q~ on packed storage; G (optional) receives Phi~ P.
 template <class S, class F>
-GPSS_D void predict_cov(const Blocks<F> *B, F *P, F (*G)[S::D] = nullptr) {
+GPSS_HD void predict_cov(const Blocks<F> *B, F *P, F (*G)[S::D] = nullptr) {
   constexpr int D = S::D;
   F T1[D][D];
 #pragma unroll
@@ -514,7 +514,7 @@ GPSS_D void predict_cov(const Blocks<F> *B, F *P, F (*G)[S::D] = nullptr) {
 
 // Reset of slot j (Eq. integrated_kalman_update with R_j of Section 3.2.3).
 template <class S, class F>
-GPSS_D void reset_slot(int j, F *m, F *P) {
+GPSS_HD void reset_slot(int j, F *m, F *P) {
 #pragma unroll
   for (int zi = 2 * S::NT; zi < S::D; ++zi) {
     const bool hit = (S::zslot(zi) == j);
@@ -527,7 +527,7 @@ GPSS_D void reset_slot(int j, F *m, F *P) {
 // Shared pieces of the measurement update with H~ = w * sum_{z in slot j} e_z
 // (Eq. H_aug; w = 1/delta):  u = P H~^T, S = H~ u + r, hm = H~ m.
 template <class S, class F>
-GPSS_D void obs_project(int j, F w, const F *m, const F *P, F *u, F &hu, F &hm) {
+GPSS_HD void obs_project(int j, F w, const F *m, const F *P, F *u, F &hu, F &hm) {
 #pragma unroll
   for (int i = 0; i < S::D; ++i) {
     F acc = F(0);
@@ -548,7 +548,7 @@ GPSS_D void obs_project(int j, F w, const F *m, const F *P, F *u, F &hu, F &hm) 
 
 // Load per-term constants and s^2 from a row of natural parameters.
 template <int NT, class F>
-GPSS_D void load_terms(const float *th, const int *kinds, TermC<F> *tc, F &s2) {
+GPSS_HD void load_terms(const float *th, const int *kinds, TermC<F> *tc, F &s2) {
   int j = 0;
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
@@ -576,7 +576,7 @@ GPSS_D void load_terms(const float *th, const int *kinds, TermC<F> *tc, F &s2) {
 
 // P0 = blkdiag(P_inf, I) (Section 3.2.3); m0 = 0.
 template <class S, class F>
-GPSS_D void init_state(const TermC<F> *tc, F *m, F *P) {
+GPSS_HD void init_state(const TermC<F> *tc, F *m, F *P) {
 #pragma unroll
   for (int i = 0; i < S::D; ++i) m[i] = F(0);
 #pragma unroll
@@ -594,7 +594,7 @@ GPSS_D void init_state(const TermC<F> *tc, F *m, F *P) {
 // log|det A|.  Row swaps are done with selects so that every index stays a
 // compile-time constant (register arrays).
 template <int D, int R, class F>
-GPSS_D F solve_inplace(F (&A)[D][D], F (&B)[D][R]) {
+GPSS_HD F solve_inplace(F (&A)[D][D], F (&B)[D][R]) {
   F logdet = F(0);
 #pragma unroll
   for (int k = 0; k < D; ++k) {

@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
 // entering it, from the chunk's information (eta, J), gamma = sum c^2/S and
 // sum log S over its n_end measurements.
 template <class S>
-GPSS_D double chunk_loglik(const float *m, const float *P, const float *eta, const float *J,
+GPSS_HD double chunk_loglik(const float *m, const float *P, const float *eta, const float *J,
                            double gam, double ld, double ne) {
   constexpr int D = S::D;
   float X[D][D], R[D][D];
@@ -416,7 +416,7 @@ GPSS_D double chunk_loglik(const float *m, const float *P, const float *eta, con
 // filtered state (m, P), given their information (eta, J) about it:
 // lambda = (I + J P)^{-1} (eta - J m), Lambda = (lambda lambda^T - (I + J P)^{-1} J) / 2.
 template <class S>
-GPSS_D void boundary_adjoint(const float *m, const float *P, const float *eta, const float *J,
+GPSS_HD void boundary_adjoint(const float *m, const float *P, const float *eta, const float *J,
                              float *lam, float *Lam) {
   constexpr int D = S::D;
   float X[D][D], R[D][D + 1];

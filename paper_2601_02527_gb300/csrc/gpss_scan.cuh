@@ -43,11 +43,11 @@ struct Elem {
 struct EView {
   float *p;
   int stride;
-  GPSS_D float &operator[](int f) const { return p[(size_t)f * stride]; }
+  GPSS_HD float &operator[](int f) const { return p[(size_t)f * stride]; }
 };
 
 template <class S>
-GPSS_D void set_identity(EView e) {
+GPSS_HD void set_identity(EView e) {
   using L = Elem<S>;
 #pragma unroll
   for (int f = 0; f < L::NF; ++f) e[f] = 0.f;
@@ -56,7 +56,7 @@ GPSS_D void set_identity(EView e) {
 }
 
 template <class S>
-GPSS_D void copy_elem(EView dst, EView src) {
+GPSS_HD void copy_elem(EView dst, EView src) {
 #pragma unroll 8
   for (int f = 0; f < Elem<S>::NF; ++f) dst[f] = src[f];
 }
@@ -64,7 +64,7 @@ GPSS_D void copy_elem(EView dst, EView src) {
 // out <- Ei o Ej (Ei earlier).  out may alias Ej (the operands are read into
 // registers field by field before out is written, see ordering below).
 template <class S>
-GPSS_D void combine(EView Ei, EView Ej, EView out) {
+GPSS_HD void combine(EView Ei, EView Ej, EView out) {
   using L = Elem<S>;
   constexpr int D = S::D;
   // X = I + C_i J_j ; right-hand sides [A_i | C_i | b_i + C_i eta_j]
@@ -180,12 +180,12 @@ GPSS_D void combine(EView Ei, EView Ej, EView out) {
 }
 
 // Logical index i of a scan of n items -> physical position.
-GPSS_D int phys(int i, int n, int rev) { return rev ? n - 1 - i : i; }
+GPSS_HD int phys(int i, int n, int rev) { return rev ? n - 1 - i : i; }
 
 // Combine in time order: with rev_op = 0 the logical order is time order;
 // with rev_op = 1 the logical predecessor is later in time.
 template <class S>
-GPSS_D void combine_logical(EView left, EView right, EView out, int rev_op) {
+GPSS_HD void combine_logical(EView left, EView right, EView out, int rev_op) {
   if (rev_op)
     combine<S>(right, left, out);
   else

@@ -1,0 +1,132 @@
+// Host build of the CUDA path's device arithmetic, for CPU tests: the same
+// header functions the kernels inline, called from ordinary host code.
+// Compiled by tests/test_host_math.py with nvcc into a shared library.
+#include <cstring>
+
+#include "gpss_kernels.cuh"
+
+using namespace gpss;
+
+namespace {
+
+void build_table(float a, float beta, float *tab) {
+  Dual2<double> g[6][TAB_NC];
+  taylor_coeffs<Dual2<double>>(mk((double)a, 1.0, 0.0), mk((double)beta, 0.0, 1.0), g);
+  for (int k = 0; k < TAB_NC; ++k) {
+    float *r = tab + k * TAB_W;
+    for (int j = 0; j < TAB_W; ++j) r[j] = 0.f;
+    for (int j = 0; j < 6; ++j) {
+      r[j] = (float)g[j][k].v;
+      r[8 + j] = (float)g[j][k].da;
+      r[16 + j] = (float)g[j][k].db;
+    }
+  }
+}
+
+template <class S>
+void combine_s(const float *Ei, const float *Ej, float *out) {
+  constexpr int NF = Elem<S>::NF;
+  float a[NF], b[NF], o[NF];
+  std::memcpy(a, Ei, sizeof a);
+  std::memcpy(b, Ej, sizeof b);
+  combine<S>(EView{a, 1}, EView{b, 1}, EView{o, 1});
+  std::memcpy(out, o, sizeof o);
+}
+
+template <class S>
+double chunk_ll_s(const float *m, const float *P, const float *eta, const float *J, double gam,
+                  double ld, double ne) {
+  return chunk_loglik<S>(m, P, eta, J, gam, ld, ne);
+}
+
+template <class S>
+void adj_s(const float *m, const float *P, const float *eta, const float *J, float *lam,
+           float *Lam) {
+  boundary_adjoint<S>(m, P, eta, J, lam, Lam);
+}
+
+template <int D>
+float solve_d(const float *A, const float *B, float *X, int R) {
+  float a[D][D], b[D][8];
+  for (int i = 0; i < D; ++i) {
+    for (int j = 0; j < D; ++j) a[i][j] = A[i * D + j];
+    for (int j = 0; j < 8; ++j) b[i][j] = j < R ? B[i * R + j] : 0.f;
+  }
+  const float ld = solve_inplace<D, 8, float>(a, b);
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < R; ++j) X[i * R + j] = b[i][j];
+  return ld;
+}
+
+}  // namespace
+
+extern "C" {
+
+// out6 = (f, f', F1, I_ff, I_pp, I_FF); mode 0: table path (FP32),
+// 1: on-the-fly series / closed forms (FP32), 2: same in FP64.
+void hh_discretize(int mode, double t, double a, double beta, double *out6) {
+  if (mode == 2) {
+    Disc<double> d = discretize<double, double>(t, a, beta);
+    double v[6] = {d.f, d.fp, d.F1, d.Iff, d.Ipp, d.IFF};
+    std::memcpy(out6, v, sizeof v);
+    return;
+  }
+  Disc<float> d;
+  if (mode == 0) {
+    float tab[TAB_TERM];
+    build_table((float)a, (float)beta, tab);
+    d = discretize_tab((float)t, (float)a, (float)beta, reinterpret_cast<const float4 *>(tab));
+  } else {
+    d = discretize<float, float>((float)t, (float)a, (float)beta);
+  }
+  const float v[6] = {d.f, d.fp, d.F1, d.Iff, d.Ipp, d.IFF};
+  for (int i = 0; i < 6; ++i) out6[i] = v[i];
+}
+
+// out18 = values, d/da, d/dbeta of the six scalars (table path, FP32 duals)
+void hh_discretize_dual(double t, double a, double beta, double *out18) {
+  float tab[TAB_TERM];
+  build_table((float)a, (float)beta, tab);
+  Disc<Dual2<float>> d = discretize_tab_dual((float)t, (float)a, (float)beta,
+                                             reinterpret_cast<const float4 *>(tab));
+  const Dual2<float> v[6] = {d.f, d.fp, d.F1, d.Iff, d.Ipp, d.IFF};
+  for (int i = 0; i < 6; ++i) {
+    out18[i] = v[i].v;
+    out18[6 + i] = v[i].da;
+    out18[12 + i] = v[i].db;
+  }
+}
+
+float hh_solve(int D, const float *A, const float *B, float *X, int R) {
+  switch (D) {
+    case 3: return solve_d<3>(A, B, X, R);
+    case 5: return solve_d<5>(A, B, X, R);
+    case 6: return solve_d<6>(A, B, X, R);
+    case 7: return solve_d<7>(A, B, X, R);
+  }
+  return 0.f;
+}
+
+// shape ids: 0 = (1 term, 1 slot), 1 = (2 terms, 1 slot, layout 1), 2 = (2 terms, 3 slots)
+int hh_dim(int shape) {
+  return shape == 0 ? Shape<1, 1, 0>::D : shape == 1 ? Shape<2, 1, 1>::D : Shape<2, 3, 0>::D;
+}
+void hh_combine(int shape, const float *Ei, const float *Ej, float *out) {
+  if (shape == 0) combine_s<Shape<1, 1, 0>>(Ei, Ej, out);
+  else if (shape == 1) combine_s<Shape<2, 1, 1>>(Ei, Ej, out);
+  else combine_s<Shape<2, 3, 0>>(Ei, Ej, out);
+}
+double hh_chunk_loglik(int shape, const float *m, const float *P, const float *eta,
+                       const float *J, double gam, double ld, double ne) {
+  if (shape == 0) return chunk_ll_s<Shape<1, 1, 0>>(m, P, eta, J, gam, ld, ne);
+  if (shape == 1) return chunk_ll_s<Shape<2, 1, 1>>(m, P, eta, J, gam, ld, ne);
+  return chunk_ll_s<Shape<2, 3, 0>>(m, P, eta, J, gam, ld, ne);
+}
+void hh_boundary_adjoint(int shape, const float *m, const float *P, const float *eta,
+                         const float *J, float *lam, float *Lam) {
+  if (shape == 0) adj_s<Shape<1, 1, 0>>(m, P, eta, J, lam, Lam);
+  else if (shape == 1) adj_s<Shape<2, 1, 1>>(m, P, eta, J, lam, Lam);
+  else adj_s<Shape<2, 3, 0>>(m, P, eta, J, lam, Lam);
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+"""The CUDA path's device arithmetic, built for the host and checked on the CPU.
+
+tests/hostmath/gpss_host_harness.cu compiles the same header functions the
+kernels inline (nvcc, host code only).  Checked here:
+  * the per-step scalars (f, f', F1, I_ff, I_pp, I_FF) of the table/Horner
+    path, the on-the-fly FP32 path and the FP64 path against the oracle's Van
+    Loan discretisation over seven decades of step length;
+  * their forward-mode derivatives in (a, beta) against central differences
+    of the oracle;
+  * the pivoted dense solver, the element combination, the closed-form chunk
+    log-likelihood and the boundary adjoint against numpy.
+"""
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(HERE, "hostmath", "gpss_host_harness.cu")
+OUT = os.path.join(HERE, "hostmath", "_build", "libgpss_hostmath.so")
+
+
+@pytest.fixture(scope="module")
+def hh():
+    os.makedirs(os.path.dirname(OUT), exist_ok=True)
+    deps = [SRC] + [os.path.join(ROOT, "paper_2601_02527_gb300", "csrc", f)
+                    for f in ("gpss_device.cuh", "gpss_kernels.cuh", "gpss_scan.cuh")]
+    if not os.path.exists(OUT) or os.path.getmtime(OUT) < max(map(os.path.getmtime, deps)):
+        nvcc = "/usr/local/cuda/bin/nvcc"
+        subprocess.check_call([nvcc, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                               "-I", os.path.join(ROOT, "include"),
+                               "-I", os.path.join(ROOT, "paper_2601_02527_gb300", "csrc"),
+                               SRC, "-o", OUT + ".tmp"])
+        os.replace(OUT + ".tmp", OUT)
+    lib = ctypes.CDLL(OUT)
+    P = ctypes.POINTER
+    d, f = ctypes.c_double, ctypes.c_float
+    lib.hh_discretize.argtypes = [ctypes.c_int, d, d, d, P(d)]
+    lib.hh_discretize_dual.argtypes = [d, d, d, P(d)]
+    lib.hh_solve.argtypes = [ctypes.c_int, P(f), P(f), P(f), ctypes.c_int]
+    lib.hh_solve.restype = f
+    lib.hh_dim.argtypes = [ctypes.c_int]
+    lib.hh_combine.argtypes = [ctypes.c_int, P(f), P(f), P(f)]
+    lib.hh_chunk_loglik.argtypes = [ctypes.c_int, P(f), P(f), P(f), P(f), d, d, d]
+    lib.hh_chunk_loglik.restype = d
+    lib.hh_boundary_adjoint.argtypes = [ctypes.c_int, P(f), P(f), P(f), P(f), P(f), P(f)]
+    return lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def oracle_scalars(w0, q, t):
+    """(f, f', F1, I_ff, I_pp, I_FF) from the oracle's Phi~, Q~ (sigma = 1)."""
+    Phi, Q, _ = oracle.discretize([1], 0, 1, [1.0, w0, q, 0.1], t)
+    qc = 2 * w0 ** 3 / q
+    return np.array([Phi[0, 1], Phi[1, 1], Phi[2, 1], Q[0, 0] / qc, Q[1, 1] / qc, Q[2, 2] / qc])
+
+
+CASES = [(2 * math.pi / 10, 3.0), (math.sqrt(3) / 5, 0.5), (2.0, 0.55), (1.0, 9.5), (8.0, 1.0)]
+
+
+def ab(w0, q):
+    return w0 / (2 * q), (w0 * w0 * (1 - 1 / (4 * q * q)) if q != 0.5 else 0.0)
+
+
+@pytest.mark.parametrize("w0,q", CASES)
+def test_step_scalars_match_oracle(oracle_lib, hh, w0, q):
+    a, beta = ab(w0, q)
+    ts = np.logspace(-5, math.log10(40.0), 120) / w0
+    refs = np.array([oracle_scalars(w0, q, t) for t in ts])
+    floor = np.max(np.abs(refs), axis=0)
+    out = np.zeros(6)
+    for mode, rtol, ntol in ((0, 6e-6, 3e-7), (1, 6e-6, 3e-7), (2, 1e-11, 1e-13)):
+        for t, ref in zip(ts, refs):
+            hh.hh_discretize(mode, t, a, beta, _p(out, ctypes.c_double))
+            bad = np.abs(out - ref) > rtol * np.abs(ref) + ntol * floor
+            assert not bad.any(), (mode, t, w0 * t, out, ref)
+
+
+@pytest.mark.parametrize("w0,q", [(2 * math.pi / 10, 3.0), (2.0, 0.55), (1.0, 9.5)])
+def test_step_scalar_derivatives(oracle_lib, hh, w0, q):
+    a, beta = ab(w0, q)
+    out = np.zeros(18)
+    for x in (0.01, 0.3, 0.9, 1.1, 1.3, 2.5, 8.0):
+        t = x / w0
+        hh.hh_discretize_dual(t, a, beta, _p(out, ctypes.c_double))
+        da, db = out[6:12], out[12:18]
+        # chain (a, beta) -> (omega0, Q) and compare with oracle central differences
+        g_w0 = da / (2 * q) + db * 2 * w0 * (1 - 1 / (4 * q * q))
+        g_q = -da * w0 / (2 * q * q) + db * w0 * w0 / (2 * q ** 3)
+        h1, h2 = 1e-6 * w0, 1e-6 * q
+        fd_w0 = (oracle_scalars(w0 + h1, q, t) - oracle_scalars(w0 - h1, q, t)) / (2 * h1)
+        fd_q = (oracle_scalars(w0, q + h2, t) - oracle_scalars(w0, q - h2, t)) / (2 * h2)
+        for got, ref in ((g_w0, fd_w0), (g_q, fd_q)):
+            assert np.all(np.abs(got - ref) <= 1e-4 * np.abs(ref) + 1e-5 * np.max(np.abs(ref))), (x, got, ref)
+
+
+@pytest.mark.parametrize("D", [3, 5, 6, 7])
+def test_pivoted_solver(hh, D):
+    rng = np.random.default_rng(D)
+    for trial in range(20):
+        A = rng.normal(size=(D, D)).astype(np.float32) + 2 * np.eye(D, dtype=np.float32)
+        if trial % 3 == 0:
+            A[0, 0] = 0.0  # needs a row exchange
+        B = rng.normal(size=(D, 3)).astype(np.float32)
+        X = np.zeros((D, 3), np.float32)
+        ld = hh.hh_solve(D, _p(A, ctypes.c_float), _p(B, ctypes.c_float), _p(X, ctypes.c_float), 3)
+        ref = np.linalg.solve(A.astype(float), B.astype(float))
+        assert np.allclose(X, ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+        assert abs(ld - np.linalg.slogdet(A.astype(float))[1]) < 1e-4 * max(1, abs(ld))
+
+
+def _pk(D, i, j):
+    i, j = min(i, j), max(i, j)
+    return i * D - i * (i - 1) // 2 + (j - i)
+
+
+def _pack(S):
+    D = S.shape[0]
+    return np.array([S[i, j] for i in range(D) for j in range(i, D)], np.float32)
+
+
+def _unpack(v, D):
+    S = np.zeros((D, D))
+    for i in range(D):
+        for j in range(i, D):
+            S[i, j] = S[j, i] = v[_pk(D, i, j)]
+    return S
+
+
+def _rand_elem(rng, D):
+    A = rng.normal(size=(D, D)) * 0.5
+    b = rng.normal(size=D)
+    G = rng.normal(size=(D, D)) * 0.5
+    C = G @ G.T
+    H = rng.normal(size=(D, D)) * 0.5
+    J = H @ H.T
+    eta = rng.normal(size=D)
+    return A, b, C, eta, J
+
+
+def _flat(e):
+    A, b, C, eta, J = e
+    return np.concatenate([A.ravel(), b, _pack(C), eta, _pack(J)]).astype(np.float32)
+
+
+def _sg21(ei, ej):
+    Ai, bi, Ci, ei_, Ji = ei
+    Aj, bj, Cj, ej_, Jj = ej
+    D = len(bi)
+    Mj = Aj @ np.linalg.inv(np.eye(D) + Ci @ Jj)
+    Nj = Ai.T @ np.linalg.inv(np.eye(D) + Jj @ Ci)
+    return (Mj @ Ai, Mj @ (bi + Ci @ ej_) + bj, Mj @ Ci @ Aj.T + Cj,
+            Nj @ (ej_ - Jj @ bi) + ei_, Nj @ Jj @ Ai + Ji)
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+def test_element_combination(hh, shape):
+    D = hh.hh_dim(shape)
+    rng = np.random.default_rng(10 + shape)
+    for _ in range(10):
+        ei, ej = _rand_elem(rng, D), _rand_elem(rng, D)
+        out = np.zeros(2 * D * D + 3 * D, np.float32)
+        hh.hh_combine(shape, _p(_flat(ei), ctypes.c_float), _p(_flat(ej), ctypes.c_float),
+                      _p(out, ctypes.c_float))
+        ref = _flat(_sg21(ei, ej))
+        assert np.allclose(out, ref, rtol=2e-4, atol=2e-4 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+def test_chunk_loglik_and_adjoint(hh, shape):
+    D = hh.hh_dim(shape)
+    rng = np.random.default_rng(20 + shape)
+    for _ in range(10):
+        _, _, P, eta, J = _rand_elem(rng, D)
+        m = rng.normal(size=D)
+        gam, ld, ne = 3.7, -5.2, 11.0
+        f32 = lambda a: np.ascontiguousarray(a, np.float32)
+        got = hh.hh_chunk_loglik(shape, _p(f32(m), ctypes.c_float), _p(_pack(P), ctypes.c_float),
+                                 _p(f32(eta), ctypes.c_float), _p(_pack(J), ctypes.c_float),
+                                 gam, ld, ne)
+        u = eta - J @ m
+        X = np.eye(D) + P @ J
+        quad = gam - 2 * eta @ m + m @ J @ m - u @ np.linalg.solve(X, P) @ u
+        ref = -0.5 * (ld + ne * math.log(2 * math.pi) + np.linalg.slogdet(X)[1] + quad)
+        assert abs(got - ref) <= 1e-4 * max(1.0, abs(ref))
+        lam = np.zeros(D, np.float32)
+        Lam = np.zeros(D * (D + 1) // 2, np.float32)
+        hh.hh_boundary_adjoint(shape, _p(f32(m), ctypes.c_float), _p(_pack(P), ctypes.c_float),
+                               _p(f32(eta), ctypes.c_float), _p(_pack(J), ctypes.c_float),
+                               _p(lam, ctypes.c_float), _p(Lam, ctypes.c_float))
+        Y = np.eye(D) + J @ P
+        lref = np.linalg.solve(Y, eta - J @ m)
+        Lref = 0.5 * (np.outer(lref, lref) - np.linalg.solve(Y, J))
+        assert np.allclose(lam, lref, rtol=1e-4, atol=1e-4 * np.abs(lref).max())
+        assert np.allclose(_unpack(Lam, D), Lref, rtol=1e-3, atol=1e-4 * np.abs(Lref).max())
