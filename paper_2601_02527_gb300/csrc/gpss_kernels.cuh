@@ -91,11 +91,12 @@ GPSS_D Disc<float> disc_step<float>(float dt, const TermC<float> &c, const float
   return discretize<float, float>(dt, c.a, c.beta);
 }
 
+// One event of the sequential filter on (m, P) given its gap, tag and (for an
+// exposure end) its measurement record; returns true for an end event, with
+// S and v of its innovation.
 template <class S, class F>
-GPSS_D bool filter_event(const DevModel &M, int64_t k, int64_t &mi, const TermC<F> *tc, F s2, F *m,
-                         F *P, F &Sv, F &v, const float4 *tab = nullptr) {
-  const F dt = load_dt<F>(M, k);
-  const uint8_t tag = __ldg(M.tag + k);
+GPSS_D bool filter_step(F dt, uint8_t tag, F y, F r0, F w, const TermC<F> *tc, F s2, F *m, F *P,
+                        F &Sv, F &v, const float4 *tab) {
   Blocks<F> B[S::NT];
 #pragma unroll
   for (int t = 0; t < S::NT; ++t)
@@ -110,9 +111,6 @@ GPSS_D bool filter_event(const DevModel &M, int64_t k, int64_t &mi, const TermC<
     reset_slot<S>(j, m, P);
     return false;
   }
-  F y, r0, w;
-  load_meas<F>(M, mi, y, r0, w);
-  ++mi;
   F u[S::D], hu, hm;
   obs_project<S>(j, w, m, P, u, hu, hm);
   Sv = hu + r0 + s2;
@@ -127,6 +125,61 @@ GPSS_D bool filter_event(const DevModel &M, int64_t k, int64_t &mi, const TermC<
     for (int jj = i; jj < S::D; ++jj) P[S::pk(i, jj)] -= u[i] * u[jj] * iS;
   return true;
 }
+
+// Same, loading the event's data itself (per-series kernels).
+template <class S, class F>
+GPSS_D bool filter_event(const DevModel &M, int64_t k, int64_t &mi, const TermC<F> *tc, F s2, F *m,
+                         F *P, F &Sv, F &v, const float4 *tab = nullptr) {
+  const F dt = load_dt<F>(M, k);
+  const uint8_t tag = __ldg(M.tag + k);
+  F y = F(0), r0 = F(0), w = F(0);
+  if (tag & 1) {
+    load_meas<F>(M, mi, y, r0, w);
+    ++mi;
+  }
+  return filter_step<S, F>(dt, tag, y, r0, w, tc, s2, m, P, Sv, v, tab);
+}
+
+// Event reader for the FP32 chunk kernels: the gap and tag of the next event
+// and the next measurement record are loaded one step ahead of their use, so
+// their latency overlaps the arithmetic of the current event.
+struct EventReader {
+  const float *dt;
+  const uint8_t *tag;
+  const float4 *meas;
+  int64_t k, kend, mi;
+  float dt_n;
+  uint8_t tag_n;
+  float4 q_n;
+  GPSS_D void start(const DevModel &M, int64_t k0, int64_t k1, int64_t m0) {
+    dt = M.dt;
+    tag = M.tag;
+    meas = M.meas;
+    k = k0;
+    kend = k1;
+    mi = m0;
+    if (k < kend) {
+      dt_n = __ldg(dt + k);
+      tag_n = __ldg(tag + k);
+    }
+    q_n = __ldg(meas + mi);
+  }
+  // current event's data; prefetches the following one
+  GPSS_D void next(float &d, uint8_t &t, float4 &q) {
+    d = dt_n;
+    t = tag_n;
+    q = q_n;
+    ++k;
+    if (k < kend) {
+      dt_n = __ldg(dt + k);
+      tag_n = __ldg(tag + k);
+    }
+    if (t & 1) {
+      ++mi;
+      q_n = __ldg(meas + mi);
+    }
+  }
+};
 
 GPSS_D void flag_error(int *err, int row, int code) {
   if (err) atomicMax(err + row, code);
@@ -259,13 +312,15 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
   double gam = 0.0, ld = 0.0;
   int n_end = 0;
   bool bad = false;
-  int64_t mi = M.ch_meas0[c];
   const int64_t e0 = M.ch_ev0[c];
   const int len = M.ch_len[c];
+  EventReader rd;
+  rd.start(M, e0, e0 + len, M.ch_meas0[c]);
   for (int kk = 0; kk < len; ++kk) {
-    const int64_t k = e0 + kk;
-    const F dt = load_dt<F>(M, k);
-    const uint8_t tag = __ldg(M.tag + k);
+    F dt;
+    uint8_t tag;
+    float4 q;
+    rd.next(dt, tag, q);
     Blocks<F> B[S::NT];
 #pragma unroll
     for (int t = 0; t < S::NT; ++t)
@@ -297,9 +352,7 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
         for (int col = 0; col < D; ++col) A[zi][col] = hit ? F(0) : A[zi][col];
       }
     } else {
-      F y, r0, w;
-      load_meas<F>(M, mi, y, r0, w);
-      ++mi;
+      const F y = q.x, r0 = q.y, w = q.z;
       F u[D], hu, hb;
       obs_project<S>(j, w, b, C, u, hu, hb);
       const F Sv = hu + r0 + s2;
@@ -699,14 +752,12 @@ struct TermGrad {
 // (lam, Lam): adjoint of the filtered state after the event (full-matrix
 // gradient convention, stored packed); on return, adjoint of (m, P).
 template <class S>
-GPSS_D void reverse_event(const DevModel &M, int64_t k, int64_t mi, const TermC<float> *tc,
-                          float s2, const float *m, const float *P, float *lam, float *Lam,
+GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *tc, float s2,
+                          const float *m, const float *P, float *lam, float *Lam,
                           TermGrad<S::NT> &gr, const float4 *tab) {
   using F = float;
   using DF = Dual2<float>;
   constexpr int D = S::D;
-  const F dt = load_dt<F>(M, k);
-  const uint8_t tag = __ldg(M.tag + k);
   const int j = (tag >> 1) & 7;
   Disc<DF> dd[S::NT];
   Blocks<F> B[S::NT];
@@ -723,8 +774,7 @@ GPSS_D void reverse_event(const DevModel &M, int64_t k, int64_t mi, const TermC<
   for (int i = 0; i < S::NP; ++i) Pp[i] = P[i];
   predict_cov<S>(B, Pp, G);
   if (tag & 1) {
-    F y, r0, w;
-    load_meas<F>(M, mi, y, r0, w);
+    const F y = q.x, r0 = q.y, w = q.z;
     F u[D], hu, hm;
     obs_project<S>(j, w, mp, Pp, u, hu, hm);
     const F Sv = hu + r0 + s2;
@@ -863,7 +913,7 @@ GPSS_D void reverse_event(const DevModel &M, int64_t k, int64_t mi, const TermC<
 }
 
 template <class S, int CK>
-__global__ void __launch_bounds__(64) k_grad(DevModel M, const float *__restrict__ theta, int n_vch,
+__global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restrict__ theta, int n_vch,
                                              int per_series, const float *__restrict__ state_end,
                                              const float *__restrict__ adj_end,
                                              float *__restrict__ ckpt, float *__restrict__ gpart,
@@ -919,14 +969,16 @@ __global__ void __launch_bounds__(64) k_grad(DevModel M, const float *__restrict
   bool replay = false;
   int seg = nseg - 1;
   int kk = 0, kend = len;
-  int64_t mi = M.ch_meas0[c];
+  EventReader rd;
+  rd.start(M, e0, e0 + len, M.ch_meas0[c]);
   for (;;) {
     if (kk < kend) {
+      const int mrel = (int)(rd.mi - M.ch_meas0[c]);
       if (!replay) {
         if (kk % CK == 0) {
           float *dst = ckpt + (size_t)(kk / CK) * (SD + 1) * n_vch;
           store_rec<S>(dst, n_vch, vc, m, P);
-          dst[(size_t)SD * n_vch + vc] = __int_as_float((int)(mi - M.ch_meas0[c]));
+          dst[(size_t)SD * n_vch + vc] = __int_as_float(mrel);
         }
       } else {
         const int slot = kk - seg * CK;
@@ -934,34 +986,50 @@ __global__ void __launch_bounds__(64) k_grad(DevModel M, const float *__restrict
         for (int i = 0; i < D; ++i) my[(slot * SD + i) * bs] = m[i];
 #pragma unroll
         for (int i = 0; i < S::NP; ++i) my[(slot * SD + D + i) * bs] = P[i];
-        mys[slot * bs] = (int)(mi - M.ch_meas0[c]);
+        mys[slot * bs] = mrel;
       }
-      F Sv, vv;
-      if (filter_event<S, F>(M, e0 + kk, mi, tc, s2, m, P, Sv, vv, tab)) bad |= !(Sv > F(0));
+      F dt, Sv, vv;
+      uint8_t tag;
+      float4 q;
+      rd.next(dt, tag, q);
+      if (filter_step<S, F>(dt, tag, q.x, q.y, q.z, tc, s2, m, P, Sv, vv, tab))
+        bad |= !(Sv > F(0));
       ++kk;
       continue;
     }
     if (replay) {
-      // backward walk over the replayed segment
-      for (int k2 = kend - 1; k2 >= seg * CK; --k2) {
+      // backward walk over the replayed segment; the next (earlier) event's
+      // data are loaded while the current one is processed
+      int k2 = kend - 1;
+      F dt_n = __ldg(M.dt + e0 + k2);
+      uint8_t tag_n = __ldg(M.tag + e0 + k2);
+      float4 q_n = __ldg(M.meas + M.ch_meas0[c] + mys[(k2 - seg * CK) * bs]);
+      for (; k2 >= seg * CK; --k2) {
         const int slot = k2 - seg * CK;
+        const F dt = dt_n;
+        const uint8_t tag = tag_n;
+        const float4 q = q_n;
+        if (k2 > seg * CK) {
+          dt_n = __ldg(M.dt + e0 + k2 - 1);
+          tag_n = __ldg(M.tag + e0 + k2 - 1);
+          q_n = __ldg(M.meas + M.ch_meas0[c] + mys[(slot - 1) * bs]);
+        }
 #pragma unroll
         for (int i = 0; i < D; ++i) m[i] = my[(slot * SD + i) * bs];
 #pragma unroll
         for (int i = 0; i < S::NP; ++i) P[i] = my[(slot * SD + D + i) * bs];
-        reverse_event<S>(M, e0 + k2, M.ch_meas0[c] + mys[slot * bs], tc, s2, m, P, lam, Lam, gr,
-                         tab);
+        reverse_event<S>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab);
       }
       --seg;
     }
     if (seg < 0) break;
-    // start (or continue) replaying segment `seg` from its checkpoint
+    // start replaying segment `seg` from its checkpoint
     replay = true;
     const float *src = ckpt + (size_t)seg * (SD + 1) * n_vch;
     load_rec<S>(src, n_vch, vc, m, P);
-    mi = M.ch_meas0[c] + __float_as_int(src[(size_t)SD * n_vch + vc]);
     kk = seg * CK;
     kend = min(kk + CK, len);
+    rd.start(M, e0 + kk, e0 + kend, M.ch_meas0[c] + __float_as_int(src[(size_t)SD * n_vch + vc]));
   }
   if (first) {
     // P0 = blkdiag(var diag(1, w2), I)
@@ -1073,7 +1141,7 @@ struct OpTable {
                       cudaStream_t);
 };
 
-constexpr int GRAD_CK = 8;
+constexpr int GRAD_CK = 4;
 constexpr int GRAD_BS = 64;
 
 template <class S, class F>
