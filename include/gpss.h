@@ -78,9 +78,10 @@ typedef struct {
   int chunk_len;          /* events per chunk of the parallel-in-time schedule, 0 = auto */
   int ckpt_interval;      /* reserved for the gradient's recomputation segment, 0 = auto */
   int debug_checks;       /* nonzero: extra host-side validation */
-  int chunk_combine;      /* combination of chunk elements across a series: 0 auto,
+  int chunk_combine;      /* combination of chunk elements across a series: 0 auto (= 2),
                              1 sequential fold per series (one thread per series),
-                             2 parallel tree scan over all chunks (Section 3.2.5) */
+                             2 parallel scan (Section 3.2.5): each warp's 32 chunks in
+                               shared memory, then a tree scan of the warp totals */
 } gp_ss_options;
 
 /* Build a model from exposures (Section 3.2: two events per exposure, reset

@@ -439,9 +439,9 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
   if (n_vch64 > INT32_MAX / 8) return GP_SS_EUNSUPPORTED;
   const int n_vch = (int)n_vch64;
   const int SD = o.D + o.NP;
-  // cross-chunk combination: the sequential fold keeps one thread per series
-  // busy for its whole chunk count; long series go through the tree scan
-  bool tree = m->combine == 2 || (m->combine == 0 && m->max_chunks_per_series > 48);
+  // cross-chunk combination: warp-level scans plus a scan of warp totals
+  // (default), or the sequential fold with one thread per series
+  bool tree = m->combine != 1;
   std::vector<void *> bufs;
   auto grab = [&](void **p, size_t bytes) -> bool {
     if (cudaMallocAsync(p, std::max<size_t>(bytes, 16), st) != cudaSuccess) {
@@ -478,9 +478,18 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       res = GP_SS_ENOMEM;
       break;
     }
+    // warp-level combination buffers
+    float *pre_local = nullptr, *suf_local = nullptr, *wtot = nullptr, *wpre = nullptr,
+          *wsuf = nullptr;
+    const int n_w = n_vch / 32;
     if (tree && (!grab((void **)&ll_part, (size_t)n_vch * sizeof(double)) ||
-                 !grab((void **)&scratch, o.scan_scratch(n_vch) * sizeof(float)) ||
-                 (grad && !grab((void **)&info, (size_t)SD * n_vch * sizeof(float))))) {
+                 !grab((void **)&pre_local, (size_t)o.NF * n_vch * sizeof(float)) ||
+                 !grab((void **)&wtot, (size_t)o.NF * n_w * sizeof(float)) ||
+                 !grab((void **)&wpre, (size_t)o.NF * n_w * sizeof(float)) ||
+                 !grab((void **)&scratch, o.warp_scratch(n_vch) * sizeof(float)) ||
+                 (grad && (!grab((void **)&info, (size_t)SD * n_vch * sizeof(float)) ||
+                           !grab((void **)&suf_local, (size_t)o.NF * n_vch * sizeof(float)) ||
+                           !grab((void **)&wsuf, (size_t)o.NF * n_w * sizeof(float)))))) {
       res = GP_SS_ENOMEM;
       break;
     }
@@ -491,8 +500,8 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
         e = o.scan(dm, n_out, per_series, ef, ed, n_vch, state_end, adj, ll, grad ? 1 : 0,
                    m->d_err, st);
       } else {
-        e = o.scan_tree(ef, n_vch, state_end, 1, 0, scratch, st);
-        if (e == cudaSuccess && grad) e = o.scan_tree(ef, n_vch, info, 2, 1, scratch, st);
+        e = o.warp_combine(dm, ef, n_vch, pre_local, suf_local, wtot, wpre, wsuf, scratch,
+                           state_end, info, grad ? 1 : 0, st);
         if (e == cudaSuccess)
           e = o.finish(dm, n_vch, per_series, ef, ed, state_end, info, adj, ll_part, m->d_err, st);
       }

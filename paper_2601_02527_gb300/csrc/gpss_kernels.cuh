@@ -1132,6 +1132,9 @@ struct OpTable {
   cudaError_t (*grad)(const DevModel &, const float *, int, int, const float *, const float *,
                       float *, float *, int *, const float *, cudaStream_t);
   cudaError_t (*tables)(const float *, int, int, int, int, float *, cudaStream_t);
+  cudaError_t (*warp_combine)(const DevModel &, const float *, int, float *, float *, float *,
+                              float *, float *, float *, float *, float *, int, cudaStream_t);
+  size_t (*warp_scratch)(int);
   int NT;
   cudaError_t (*scan_tree)(const float *, int, float *, int, int, float *, cudaStream_t);
   size_t (*scan_scratch)(int);
@@ -1197,6 +1200,45 @@ size_t scan_scratch_count(int n) {
   return scan_scratch_floats<S>(n);
 }
 
+// Warp-level combination (k_warp_scan, scan of warp totals, k_join): writes
+// state_end (and info_incl when want_info).  Buffers: pre_local, suf_local
+// [NF * n_vch]; wtot, wpre, wsuf [NF * n_vch/32]; scratch [warp_scratch].
+template <class S>
+cudaError_t launch_warp_combine(const DevModel &M, const float *ef, int n_vch, float *pre_local,
+                                float *suf_local, float *wtot, float *wpre, float *wsuf,
+                                float *scratch, float *state_end, float *info_incl, int want_info,
+                                cudaStream_t st) {
+  if (n_vch <= 0) return cudaSuccess;
+  const int n_w = n_vch / 32;
+  const size_t smem = warp_scan_smem_bytes<S>(2);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_warp_scan<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_warp_scan<S><<<(n_vch + 63) / 64, 64, smem, st>>>(ef, n_vch, pre_local, suf_local, wtot,
+                                                      want_info);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = scan_elems<S>(wtot, n_w, wpre, 0, 0, 0, scratch, st);
+  if (e != cudaSuccess) return e;
+  if (want_info) {
+    e = scan_elems<S>(wtot, n_w, wsuf, 3, 1, 1, scratch, st);
+    if (e != cudaSuccess) return e;
+  }
+  k_join<S><<<(n_vch + 127) / 128, 128, 0, st>>>(n_vch, M.n_chunks, M.ch_flags, pre_local,
+                                                 suf_local, wpre, wsuf, state_end,
+                                                 want_info ? info_incl : nullptr);
+  return cudaGetLastError();
+}
+
+template <class S>
+size_t warp_scratch_count(int n_vch) {
+  return scan_scratch_floats<S>(n_vch / 32);
+}
+
 template <class S>
 cudaError_t launch_finish(const DevModel &M, int n_vch, int per_series, const float *ef,
                           const double *ed, const float *state_end, const float *info_incl,
@@ -1253,6 +1295,8 @@ OpTable make_ops() {
   o.scan_scratch = &scan_scratch_count<S>;
   o.finish = &launch_finish<S>;
   o.tables = &launch_tables<S>;
+  o.warp_combine = &launch_warp_combine<S>;
+  o.warp_scratch = &warp_scratch_count<S>;
   o.NT = S::NT;
   return o;
 }

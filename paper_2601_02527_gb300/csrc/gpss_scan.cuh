@@ -230,8 +230,9 @@ __global__ void __launch_bounds__(T) k_tile_reduce(const float *__restrict__ src
 // Inclusive scan of one tile (logical order) preceded by the inclusive scan
 // of earlier tiles, pre[tile - 1] (full elements, logical order, stride
 // n_pre; may be null).  Output mode 0: full elements to dst (logical order,
-// stride n); mode 1: (b, C) as state records at the physical position
-// (stride n); mode 2: (eta, J) as information records.
+// stride n); mode 3: full elements at the physical position; mode 1: (b, C)
+// as state records at the physical position (stride n); mode 2: (eta, J) as
+// information records.
 template <class S, int T>
 __global__ void __launch_bounds__(T) k_tile_scan(const float *__restrict__ src, int n,
                                                  const float *__restrict__ pre, int n_pre,
@@ -289,6 +290,9 @@ __global__ void __launch_bounds__(T) k_tile_scan(const float *__restrict__ src, 
   const int i = i0 + tid;
   if (mode == 0) {
     EView out{dst + i, n};
+    copy_elem<S>(out, own);
+  } else if (mode == 3) {
+    EView out{dst + phys(i, n, rev_index), n};
     copy_elem<S>(out, own);
   } else if (mode == 1) {
     const int p = phys(i, n, rev_index);
@@ -349,6 +353,226 @@ cudaError_t scan_elems(const float *src, int n, float *dst, int mode, int rev_in
   if (e != cudaSuccess) return e;
   k_tile_scan<S, T><<<nt, T, smem, st>>>(src, n, aggscan, nt, dst, mode, rev_index, rev_op);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Warp-level combination.  The chunk plan gives every series a multiple of 32
+// chunks, so each warp holds 32 consecutive chunks of one series.  Each warp
+// scans its 32 elements in shared memory (Kogge-Stone, five steps, warp
+// synchronous): inclusive prefixes (forward) and, for the gradient, inclusive
+// suffixes (backward), plus the warp's total.  The warp totals -- 32x fewer
+// than chunks -- are then scanned by scan_elems, and k_join combines the
+// two levels per chunk.
+// ---------------------------------------------------------------------------
+template <class S>
+constexpr size_t warp_scan_smem_bytes(int warps) {
+  return (size_t)warps * 2 * 32 * Elem<S>::NF * sizeof(float);
+}
+
+template <class S>
+__global__ void __launch_bounds__(64) k_warp_scan(const float *__restrict__ ef, int n_vch,
+                                                  float *__restrict__ pre_local,
+                                                  float *__restrict__ suf_local,
+                                                  float *__restrict__ wtot, int want_suffix) {
+  using L = Elem<S>;
+  extern __shared__ float sm[];
+  const int lane = threadIdx.x & 31;
+  const int vc = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n_w = n_vch >> 5;
+  const int w = vc >> 5;
+  if (w >= n_w) return;  // whole warps only (n_vch is a multiple of 32)
+  float *bufA = sm + (size_t)(threadIdx.x >> 5) * 2 * 32 * L::NF;
+  float *bufB = bufA + 32 * L::NF;
+  for (int dir = 0; dir < (want_suffix ? 2 : 1); ++dir) {
+    for (int f = 0; f < L::NF; ++f) bufA[f * 32 + lane] = ef[(size_t)f * n_vch + vc];
+    __syncwarp();
+    float *src = bufA, *dst = bufB;
+    for (int s = 1; s < 32; s <<= 1) {
+      const bool act = dir == 0 ? lane >= s : lane + s < 32;
+      if (act) {
+        if (dir == 0)
+          combine<S>(EView{src + lane - s, 32}, EView{src + lane, 32}, EView{dst + lane, 32});
+        else
+          combine<S>(EView{src + lane, 32}, EView{src + lane + s, 32}, EView{dst + lane, 32});
+      } else {
+        copy_elem<S>(EView{dst + lane, 32}, EView{src + lane, 32});
+      }
+      __syncwarp();
+      float *t = src;
+      src = dst;
+      dst = t;
+    }
+    float *out = dir == 0 ? pre_local : suf_local;
+    for (int f = 0; f < L::NF; ++f) out[(size_t)f * n_vch + vc] = src[f * 32 + lane];
+    if (dir == 0 && lane == 31)
+      for (int f = 0; f < L::NF; ++f) wtot[(size_t)f * n_w + w] = src[f * 32 + 31];
+    __syncwarp();
+  }
+}
+
+// Per chunk: filtered end state = (state entering the warp) o (warp-local
+// inclusive prefix); information about the state entering the chunk from it
+// and all later chunks of its series = (warp-local inclusive suffix) folded
+// with the information from later warps.  wpre / wsuf: inclusive scans of
+// the warp totals forward / backward (full elements, stride n_w).
+template <class S>
+__global__ void __launch_bounds__(128) k_join(int n_vch, int n_chunks,
+                                              const uint8_t *__restrict__ ch_flags,
+                                              const float *__restrict__ pre_local,
+                                              const float *__restrict__ suf_local,
+                                              const float *__restrict__ wpre,
+                                              const float *__restrict__ wsuf,
+                                              float *__restrict__ state_end,
+                                              float *__restrict__ info_incl) {
+  using L = Elem<S>;
+  constexpr int D = S::D;
+  const int vc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (vc >= n_vch) return;
+  const int n_w = n_vch >> 5;
+  const int w = vc >> 5, lane = vc & 31;
+  const int c0 = (vc - lane) % n_chunks;  // first chunk of this warp
+  const bool first_warp = ch_flags[c0] & 1;
+  // element of the warp-local prefix
+  float A[D][D], b[D], C[S::NP], eta[D], J[S::NP];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) A[i][j] = pre_local[(size_t)(L::A + i * D + j) * n_vch + vc];
+    b[i] = pre_local[(size_t)(L::B + i) * n_vch + vc];
+    eta[i] = pre_local[(size_t)(L::ETA + i) * n_vch + vc];
+  }
+#pragma unroll
+  for (int i = 0; i < S::NP; ++i) {
+    C[i] = pre_local[(size_t)(L::C + i) * n_vch + vc];
+    J[i] = pre_local[(size_t)(L::J + i) * n_vch + vc];
+  }
+  float m[D], P[S::NP];
+  if (first_warp) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) m[i] = b[i];
+#pragma unroll
+    for (int i = 0; i < S::NP; ++i) P[i] = C[i];
+  } else {
+    // state entering the warp: (b, C) of the inclusive warp prefix of w - 1
+    float mi[D], Pi[S::NP];
+#pragma unroll
+    for (int i = 0; i < D; ++i) mi[i] = wpre[(size_t)(L::B + i) * n_w + w - 1];
+#pragma unroll
+    for (int i = 0; i < S::NP; ++i) Pi[i] = wpre[(size_t)(L::C + i) * n_w + w - 1];
+    // m = A (I + Pi J)^{-1} (mi + Pi eta) + b ; P = A (I + Pi J)^{-1} Pi A^T + C
+    float X[D][D], R[D][D + 1];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      float pe = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) pe += Pi[S::pk(i, k)] * eta[k];
+      R[i][D] = mi[i] + pe;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float acc = (i == j) ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc += Pi[S::pk(i, k)] * J[S::pk(k, j)];
+        X[i][j] = acc;
+        R[i][j] = Pi[S::pk(i, j)];
+      }
+    }
+    solve_inplace<D, D + 1, float>(X, R);
+    float T[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      float acc = b[i];
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += A[i][k] * R[k][D];
+      m[i] = acc;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float a2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) a2 += A[i][k] * R[k][j];
+        T[i][j] = a2;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = i; j < D; ++j) {
+        float acc = C[S::pk(i, j)];
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc += T[i][k] * A[j][k];
+        P[S::pk(i, j)] = acc;
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) state_end[(size_t)i * n_vch + vc] = m[i];
+#pragma unroll
+  for (int i = 0; i < S::NP; ++i) state_end[(size_t)(D + i) * n_vch + vc] = P[i];
+  if (!info_incl) return;
+  // backward: warp-local inclusive suffix folded with the information from
+  // later warps (zero past the end of the series)
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) A[i][j] = suf_local[(size_t)(L::A + i * D + j) * n_vch + vc];
+    b[i] = suf_local[(size_t)(L::B + i) * n_vch + vc];
+    eta[i] = suf_local[(size_t)(L::ETA + i) * n_vch + vc];
+  }
+#pragma unroll
+  for (int i = 0; i < S::NP; ++i) {
+    C[i] = suf_local[(size_t)(L::C + i) * n_vch + vc];
+    J[i] = suf_local[(size_t)(L::J + i) * n_vch + vc];
+  }
+  float ie[D], iJ[S::NP];
+  if (w + 1 < n_w) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) ie[i] = wsuf[(size_t)(L::ETA + i) * n_w + w + 1];
+#pragma unroll
+    for (int i = 0; i < S::NP; ++i) iJ[i] = wsuf[(size_t)(L::J + i) * n_w + w + 1];
+  } else {
+#pragma unroll
+    for (int i = 0; i < D; ++i) ie[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < S::NP; ++i) iJ[i] = 0.f;
+  }
+  // eta' = A^T (I + iJ C)^{-1} (ie - iJ b) + eta ; J' = A^T (I + iJ C)^{-1} iJ A + J
+  float X[D][D], R[D][D + 1];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    float jb = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) jb += iJ[S::pk(i, k)] * b[k];
+    R[i][D] = ie[i] - jb;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float acc = (i == j) ? 1.f : 0.f, ja = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        acc += iJ[S::pk(i, k)] * C[S::pk(k, j)];
+        ja += iJ[S::pk(i, k)] * A[k][j];
+      }
+      X[i][j] = acc;
+      R[i][j] = ja;
+    }
+  }
+  solve_inplace<D, D + 1, float>(X, R);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    float acc = eta[i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc += A[k][i] * R[k][D];
+    info_incl[(size_t)i * n_vch + vc] = acc;
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      float a1 = 0.f, a2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        a1 += A[k][i] * R[k][j];
+        a2 += A[k][j] * R[k][i];
+      }
+      info_incl[(size_t)(D + S::pk(i, j)) * n_vch + vc] = J[S::pk(i, j)] + 0.5f * (a1 + a2);
+    }
 }
 
 }  // namespace gpss

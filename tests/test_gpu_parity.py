@@ -119,10 +119,10 @@ def test_fp32_plain_per_series_kernel_matches(gp):
     check_ll(b, ref, counts_of(wl))
 
 
-@pytest.mark.parametrize("chunk", [48, 256])
-def test_fp32_grad_layout1(gp, chunk):
+@pytest.mark.parametrize("chunk,combine", [(8, 2), (8, 1), (48, 0), (256, 0)])
+def test_fp32_grad_layout1(gp, chunk, combine):
     wl = f32_theta(synth.c4(n_series=6, scale=0.05))
-    m = gp.Model.from_workload(wl, chunk_len=chunk)
+    m = gp.Model.from_workload(wl, chunk_len=chunk, combine=combine)
     ll, g = m.loglik_grad(theta_dev(wl))
     ref_ll, ref_g = oracle_ll(wl, grad=True)
     check_ll(ll.cpu().numpy(), ref_ll, counts_of(wl))
@@ -132,7 +132,7 @@ def test_fp32_grad_layout1(gp, chunk):
     np.testing.assert_allclose(ll.cpu().numpy(), ll2, rtol=1e-12)
 
 
-@pytest.mark.parametrize("chunk", [40, 300])
+@pytest.mark.parametrize("chunk", [8, 40, 300])
 def test_overlapping_three_slots(gp, chunk):
     rng = np.random.default_rng(77)
     ts, te, slot = synth.capped_overlap_exposures(rng, 1500, 0.5, 0.5, 3.0, cap=3)
@@ -148,10 +148,11 @@ def test_overlapping_three_slots(gp, chunk):
     check_grad(g.cpu().numpy(), ref_g)
 
 
-def test_theta_sets_shared_series(gp):
+@pytest.mark.parametrize("chunk", [16, 128])
+def test_theta_sets_shared_series(gp, chunk):
     wl = synth.c5(n=1200, n_sets=5)
     wl = f32_theta(wl)
-    m = gp.Model.from_workload(wl, chunk_len=128)
+    m = gp.Model.from_workload(wl, chunk_len=chunk)
     assert m.info["state_dim"] == 7
     th = theta_dev(wl)
     ll, g = m.loglik_grad(th, per_series=False)
