@@ -305,10 +305,13 @@ gp_ss_status make_plan(gp_ss_model *m, int chunk_len) {
     // works on one series (one hyperparameter row), which lets it share the
     // row's Taylor table; chunk lengths are balanced within the series
     const int64_t nch = 32 * std::max<int64_t>(1, (K + 32 * (int64_t)L - 1) / (32 * (int64_t)L));
-    const int64_t base = K / nch, rem = K % nch;
+    // boundaries at even event offsets: in a series whose events alternate
+    // start / end, every lane of a warp then meets the same kind of event at
+    // the same step (no divergence between the reset and update paths)
     int64_t e = a, mi = m->meas_off[s];
     for (int64_t c = 0; c < nch; ++c) {
-      const int64_t l = base + (c < rem ? 1 : 0);
+      const int64_t hi = (c == nch - 1) ? K : std::min<int64_t>(K, 2 * (((c + 1) * K) / (2 * nch)));
+      const int64_t l = std::max<int64_t>(0, a + hi - e);
       ev0.push_back(e);
       meas0.push_back(mi);
       len.push_back((int32_t)l);

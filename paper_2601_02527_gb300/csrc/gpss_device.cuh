@@ -253,6 +253,49 @@ GPSS_HD Disc<T> discretize(F t, T a, T beta) {
   return disc_closed<T, F>(t, a, beta, w2);
 }
 
+// Per-term constants from natural parameters, with the reciprocals and the
+// oscillation frequency the closed-form branch needs precomputed:
+// b = sqrt(beta), rb = 1/b (0 when b = 0), rw2 = 1/w2, r4a = 1/(4a).
+template <class F>
+struct TermC {
+  F a, beta, w2, qc, var;
+  F b, rb, rw2, r4a;
+};
+
+template <class F>
+GPSS_HD void finish_termc(TermC<F> &c) {
+  c.b = sqrt(c.beta);
+  c.rb = c.b > F(0) ? F(1) / c.b : F(0);
+  c.rw2 = F(1) / c.w2;
+  c.r4a = F(1) / (F(4) * c.a);
+}
+
+// Closed-form branch with the per-term constants precomputed (no division,
+// no square root per step).  S = sin(b t)/b, C = cos(b t) as in sinc_pair.
+template <class T, class F>
+GPSS_HD Disc<T> disc_closed_k(F t, T a, T w2, T rw2, T r4a, T S, T C) {
+  T E = gexp(-a * t);
+  Disc<T> d;
+  d.f = E * S;
+  d.fp = E * (C - a * S);
+  const T a2 = a * F(2);
+  d.F1 = (F(1) - d.fp - a2 * d.f) * rw2;
+  const T ff = d.f * d.f;
+  d.Ipp = (F(1) - d.fp * d.fp - w2 * ff) * r4a;
+  d.Iff = (d.Ipp - d.f * d.fp - a * ff) * rw2;
+  d.IFF = (cst<T>(t) + d.Ipp + a2 * a2 * d.Iff - F(2) * d.f - a2 * F(2) * d.F1 + a2 * ff) *
+          (rw2 * rw2);
+  return d;
+}
+
+GPSS_HD void sinc_pair_k(float t, float b, float rb, float &S, float &C) {
+  const float tau = b * t;
+  float s, c;
+  sincosf(tau, &s, &c);
+  C = c;
+  S = (tau < 1e-3f) ? t * (1.0f - tau * tau * (1.0f / 6.0f)) : s * rb;
+}
+
 // ---------------------------------------------------------------------------
 // Taylor tables.  The Taylor coefficients of the six per-term scalars depend
 // only on (a, beta), so they are computed once per hyperparameter row and
@@ -360,8 +403,7 @@ GPSS_HD Disc<Dual2<float>> disc_tab_dual(float t, const float4 *__restrict__ tab
 }
 
 // Discretisation with the Taylor branch read from a table.
-GPSS_HD Disc<float> discretize_tab(float t, float a, float beta, const float4 *tab) {
-  const float w2 = beta + a * a;
+GPSS_HD Disc<float> discretize_tab(float t, const TermC<float> &c, const float4 *tab) {
   if (t == 0.f) {
     Disc<float> d;
     d.f = 0.f;
@@ -369,12 +411,14 @@ GPSS_HD Disc<float> discretize_tab(float t, float a, float beta, const float4 *t
     d.F1 = d.Iff = d.Ipp = d.IFF = 0.f;
     return d;
   }
-  if (w2 * t * t <= TaylorOrder<float>::XT2) return disc_tab(t, tab);
-  return disc_closed<float, float>(t, a, beta, w2);
+  if (c.w2 * t * t <= TaylorOrder<float>::XT2) return disc_tab(t, tab);
+  float S, C;
+  sinc_pair_k(t, c.b, c.rb, S, C);
+  return disc_closed_k<float, float>(t, c.a, c.w2, c.rw2, c.r4a, S, C);
 }
 
-GPSS_HD Disc<Dual2<float>> discretize_tab_dual(float t, float a, float beta, const float4 *tab) {
-  const float w2 = beta + a * a;
+// Same with forward-mode derivatives in (a, beta).
+GPSS_HD Disc<Dual2<float>> discretize_tab_dual(float t, const TermC<float> &c, const float4 *tab) {
   if (t == 0.f) {
     Disc<Dual2<float>> d;
     d.f = mk(0.f, 0.f, 0.f);
@@ -382,16 +426,26 @@ GPSS_HD Disc<Dual2<float>> discretize_tab_dual(float t, float a, float beta, con
     d.F1 = d.Iff = d.Ipp = d.IFF = d.f;
     return d;
   }
-  if (w2 * t * t <= TaylorOrder<float>::XT2) return disc_tab_dual(t, tab);
-  return disc_closed<Dual2<float>, float>(t, mk(a, 1.f, 0.f), mk(beta, 0.f, 1.f),
-                                          mk(w2, 2.f * a, 1.f));
+  if (c.w2 * t * t <= TaylorOrder<float>::XT2) return disc_tab_dual(t, tab);
+  float s, co;
+  sinc_pair_k(t, c.b, c.rb, s, co);
+  // dS/dbeta = (t C - S) / (2 beta) (series for small beta t^2); dC/dbeta = -t S / 2
+  const float x = c.beta * t * t;
+  float dS;
+  if (x < 0.5f)
+    dS = t * t * t *
+         (-1.f / 6.f + x * (1.f / 60.f + x * (-1.f / 1680.f + x * (1.f / 90720.f + x * (-1.f / 7983360.f)))));
+  else
+    dS = (t * co - s) * (0.5f * c.rb * c.rb);
+  const float dC = -0.5f * t * s;
+  // w2 = beta + a^2 ; rw2 = 1/w2 ; r4a = 1/(4a)
+  const Dual2<float> a = mk(c.a, 1.f, 0.f);
+  const Dual2<float> w2 = mk(c.w2, 2.f * c.a, 1.f);
+  const Dual2<float> rw2 = mk(c.rw2, -2.f * c.a * c.rw2 * c.rw2, -c.rw2 * c.rw2);
+  const Dual2<float> r4a = mk(c.r4a, -4.f * c.r4a * c.r4a, 0.f);
+  return disc_closed_k<Dual2<float>, float>(t, a, w2, rw2, r4a, mk(s, 0.f, dS), mk(co, 0.f, dC));
 }
 
-// Per-term constants from natural parameters.
-template <class F>
-struct TermC {
-  F a, beta, w2, qc, var;
-};
 
 // Blocks of Phi~ and Q~ for one term (see header comment).
 template <class F>
@@ -569,6 +623,7 @@ GPSS_HD void load_terms(const float *th, const int *kinds, TermC<F> *tc, F &s2) 
     tc[t].w2 = w0 * w0;
     tc[t].beta = (q == F(0.5)) ? F(0) : w0 * w0 * (F(1) - F(1) / (F(4) * q * q));
     tc[t].qc = F(2) * w0 * w0 * w0 * sig * sig / q;
+    finish_termc(tc[t]);
   }
   F s = F(th[j]);
   s2 = s * s;

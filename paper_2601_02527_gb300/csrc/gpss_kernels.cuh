@@ -87,7 +87,7 @@ GPSS_D Disc<F> disc_step(F dt, const TermC<F> &c, const float4 *tab) {
 }
 template <>
 GPSS_D Disc<float> disc_step<float>(float dt, const TermC<float> &c, const float4 *tab) {
-  if (tab) return discretize_tab(dt, c.a, c.beta, tab);
+  if (tab) return discretize_tab(dt, c, tab);
   return discretize<float, float>(dt, c.a, c.beta);
 }
 
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
     Blocks<F> B[S::NT];
 #pragma unroll
     for (int t = 0; t < S::NT; ++t)
-      B[t] = make_blocks(discretize_tab(dt, tc[t].a, tc[t].beta, tab + t * (TAB_TERM / 4)), tc[t]);
+      B[t] = make_blocks(discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4)), tc[t]);
     // A <- Phi~ A (column by column), b <- Phi~ b, C <- Phi~ C Phi~^T + Q~
 #pragma unroll
     for (int col = 0; col < D; ++col) {
@@ -763,7 +763,7 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
   Blocks<F> B[S::NT];
 #pragma unroll
   for (int t = 0; t < S::NT; ++t) {
-    dd[t] = discretize_tab_dual(dt, tc[t].a, tc[t].beta, tab + t * (TAB_TERM / 4));
+    dd[t] = discretize_tab_dual(dt, tc[t], tab + t * (TAB_TERM / 4));
     Disc<F> d{dd[t].f.v, dd[t].fp.v, dd[t].F1.v, dd[t].Iff.v, dd[t].Ipp.v, dd[t].IFF.v};
     B[t] = make_blocks(d, tc[t]);
   }
@@ -1098,7 +1098,7 @@ __global__ void k_disc(const float *__restrict__ theta, const float *__restrict_
   Blocks<float> B[S::NT];
 #pragma unroll
   for (int t = 0; t < S::NT; ++t)
-    B[t] = make_blocks(discretize_tab(dt[k], tc[t].a, tc[t].beta, tab + t * (TAB_TERM / 4)), tc[t]);
+    B[t] = make_blocks(discretize_tab(dt[k], tc[t], tab + t * (TAB_TERM / 4)), tc[t]);
   float P[S::NP];
 #pragma unroll
   for (int i = 0; i < S::NP; ++i) P[i] = 0.f;

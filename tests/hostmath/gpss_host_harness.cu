@@ -23,6 +23,17 @@ void build_table(float a, float beta, float *tab) {
   }
 }
 
+TermC<float> termc(float a, float beta) {
+  TermC<float> c;
+  c.a = a;
+  c.beta = beta;
+  c.w2 = beta + a * a;
+  c.qc = 1.f;
+  c.var = 1.f;
+  finish_termc(c);
+  return c;
+}
+
 template <class S>
 void combine_s(const float *Ei, const float *Ej, float *out) {
   constexpr int NF = Elem<S>::NF;
@@ -75,7 +86,7 @@ void hh_discretize(int mode, double t, double a, double beta, double *out6) {
   if (mode == 0) {
     float tab[TAB_TERM];
     build_table((float)a, (float)beta, tab);
-    d = discretize_tab((float)t, (float)a, (float)beta, reinterpret_cast<const float4 *>(tab));
+    d = discretize_tab((float)t, termc((float)a, (float)beta), reinterpret_cast<const float4 *>(tab));
   } else {
     d = discretize<float, float>((float)t, (float)a, (float)beta);
   }
@@ -87,7 +98,7 @@ void hh_discretize(int mode, double t, double a, double beta, double *out6) {
 void hh_discretize_dual(double t, double a, double beta, double *out18) {
   float tab[TAB_TERM];
   build_table((float)a, (float)beta, tab);
-  Disc<Dual2<float>> d = discretize_tab_dual((float)t, (float)a, (float)beta,
+  Disc<Dual2<float>> d = discretize_tab_dual((float)t, termc((float)a, (float)beta),
                                              reinterpret_cast<const float4 *>(tab));
   const Dual2<float> v[6] = {d.f, d.fp, d.F1, d.Iff, d.Ipp, d.IFF};
   for (int i = 0; i < 6; ++i) {
