@@ -29,22 +29,27 @@ __global__ void k_series_sum(int n_out, int per_series, int n_series, int n_chun
                              const double *__restrict__ ll_part, int n_vch,
                              const float *__restrict__ gpart, int n_params,
                              double *__restrict__ ll_out, float *__restrict__ grad_out) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per output row; lanes stride over the row's chunks and a fixed
+  // shuffle tree combines them (the same order on every call)
+  const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (v >= n_out) return;
   const int s = per_series ? v : v % n_series;
   const int base = per_series ? 0 : (v / n_series) * n_chunks;
   const int c0 = ch_first[s], c1 = ch_first[s + 1];
   if (ll_part) {
     double acc = 0.0;
-    for (int c = c0; c < c1; ++c) acc += ll_part[base + c];
-    ll_out[v] = acc;
+    for (int c = c0 + lane; c < c1; c += 32) acc += ll_part[base + c];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) ll_out[v] = acc;
   }
   if (gpart) {
     for (int p = 0; p < n_params; ++p) {
       double acc = 0.0;
       const float *g = gpart + (size_t)p * n_vch + base;
-      for (int c = c0; c < c1; ++c) acc += (double)g[c];
-      grad_out[(size_t)v * n_params + p] = (float)acc;
+      for (int c = c0 + lane; c < c1; c += 32) acc += (double)g[c];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) grad_out[(size_t)v * n_params + p] = (float)acc;
     }
   }
 }
@@ -503,8 +508,10 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
         e = o.scan(dm, n_out, per_series, ef, ed, n_vch, state_end, adj, ll, grad ? 1 : 0,
                    m->d_err, st);
       } else {
+        // few warps per series: fold warp totals sequentially; else scan them
+        const int fold = m->max_chunks_per_series <= 16 * 32 ? 1 : 0;
         e = o.warp_combine(dm, ef, n_vch, pre_local, suf_local, wtot, wpre, wsuf, scratch,
-                           state_end, info, grad ? 1 : 0, st);
+                           state_end, info, grad ? 1 : 0, fold, n_out, per_series, st);
         if (e == cudaSuccess)
           e = o.finish(dm, n_vch, per_series, ef, ed, state_end, info, adj, ll_part, m->d_err, st);
       }
@@ -528,7 +535,7 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
     }
     if (tree || grad) {
       PhaseTimer pt(m, st, 3);
-      gpss::k_series_sum<<<(n_out + 127) / 128, 128, 0, st>>>(
+      gpss::k_series_sum<<<(n_out * 32 + 127) / 128, 128, 0, st>>>(
           n_out, per_series, m->n_series, m->n_chunks, m->d_ch_first, tree ? ll_part : nullptr,
           n_vch, grad ? gpart : nullptr, m->n_params, ll, grad);
       if (cudaGetLastError() != cudaSuccess) res = GP_SS_ECUDA;

@@ -345,6 +345,33 @@ GPSS_HD void taylor_coeffs(T a, T beta, T (&g)[6][TAB_NC]) {
   }
 }
 
+// Coefficient k of all six series (same definitions as taylor_coeffs).
+template <class T>
+GPSS_HD void taylor_coeff_k(T a, T beta, int k, T (&g)[6]) {
+  constexpr int NCF = TAB_NC + 2;
+  T c[NCF + 1];
+  const T w2 = beta + a * a;
+  c[0] = a * 0.0;
+  c[1] = c[0] + 1.0;
+  c[2] = -a;
+  for (int n = 1; n + 2 <= k + 2 && n + 2 <= NCF; ++n)
+    c[n + 2] = -(a * (2.0 * (n + 1)) * c[n + 1] + w2 * c[n]) / (double)((n + 2) * (n + 1));
+  g[0] = c[k + 1];
+  g[1] = c[k + 1] * (double)(k + 1);
+  g[2] = c[k + 1] / (double)(k + 2);
+  T s1 = c[0], s2 = c[0], s3 = c[0];
+  for (int n = 1; n <= k + 1; ++n) {
+    const int m = k + 2 - n;
+    const T pp = c[n] * c[m];
+    s1 = s1 + pp;
+    s2 = s2 + pp * (double)(n * m);
+    s3 = s3 + pp / (double)((n + 1) * (m + 1));
+  }
+  g[3] = s1 / (double)(k + 3);
+  g[4] = s2 / (double)(k + 1);
+  g[5] = s3 / (double)(k + 5);
+}
+
 // Six Taylor-branch scalars from a table in shared memory (broadcast reads).
 GPSS_HD Disc<float> disc_tab(float t, const float4 *__restrict__ tab) {
   float acc[6];

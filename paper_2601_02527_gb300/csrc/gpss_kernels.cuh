@@ -192,23 +192,21 @@ template <int NT>
 __global__ void k_tables(const float *__restrict__ theta, int n_rows, int n_params, int kind0,
                          int kind1, float *__restrict__ tab) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n_rows * NT) return;
-  const int row = idx / NT, t = idx % NT;
+  if (idx >= n_rows * NT * TAB_NC) return;
+  const int k = idx % TAB_NC, rt = idx / TAB_NC;
+  const int row = rt / NT, t = rt % NT;
   const int kinds[4] = {kind0, kind1, 0, 0};
   TermC<double> tc[NT];
   double s2;
   load_terms<NT, double>(theta + (size_t)row * n_params, kinds, tc, s2);
-  Dual2<double> g[6][TAB_NC];
-  taylor_coeffs<Dual2<double>>(mk(tc[t].a, 1.0, 0.0), mk(tc[t].beta, 0.0, 1.0), g);
-  float *o = tab + (size_t)idx * TAB_TERM;
-  for (int k = 0; k < TAB_NC; ++k) {
-    float *r = o + k * TAB_W;
-    for (int j = 0; j < TAB_W; ++j) r[j] = 0.f;
-    for (int j = 0; j < 6; ++j) {
-      r[j] = (float)g[j][k].v;
-      r[8 + j] = (float)g[j][k].da;
-      r[16 + j] = (float)g[j][k].db;
-    }
+  Dual2<double> g[6];
+  taylor_coeff_k<Dual2<double>>(mk(tc[t].a, 1.0, 0.0), mk(tc[t].beta, 0.0, 1.0), k, g);
+  float *r = tab + ((size_t)rt * TAB_NC + k) * TAB_W;
+  for (int j = 0; j < TAB_W; ++j) r[j] = 0.f;
+  for (int j = 0; j < 6; ++j) {
+    r[j] = (float)g[j].v;
+    r[8 + j] = (float)g[j].da;
+    r[16 + j] = (float)g[j].db;
   }
 }
 
@@ -1133,7 +1131,8 @@ struct OpTable {
                       float *, float *, int *, const float *, cudaStream_t);
   cudaError_t (*tables)(const float *, int, int, int, int, float *, cudaStream_t);
   cudaError_t (*warp_combine)(const DevModel &, const float *, int, float *, float *, float *,
-                              float *, float *, float *, float *, float *, int, cudaStream_t);
+                              float *, float *, float *, float *, float *, int, int, int, int,
+                              cudaStream_t);
   size_t (*warp_scratch)(int);
   int NT;
   cudaError_t (*scan_tree)(const float *, int, float *, int, int, float *, cudaStream_t);
@@ -1170,9 +1169,9 @@ cudaError_t launch_elem(const DevModel &M, const float *theta, int n_vch, int pe
 template <class S>
 cudaError_t launch_tables(const float *theta, int n_rows, int n_params, int k0, int k1,
                           float *tab, cudaStream_t st) {
-  const int n = n_rows * S::NT;
+  const int n = n_rows * S::NT * TAB_NC;
   if (n <= 0) return cudaSuccess;
-  k_tables<S::NT><<<(n + 63) / 64, 64, 0, st>>>(theta, n_rows, n_params, k0, k1, tab);
+  k_tables<S::NT><<<(n + 127) / 128, 128, 0, st>>>(theta, n_rows, n_params, k0, k1, tab);
   return cudaGetLastError();
 }
 
@@ -1207,7 +1206,7 @@ template <class S>
 cudaError_t launch_warp_combine(const DevModel &M, const float *ef, int n_vch, float *pre_local,
                                 float *suf_local, float *wtot, float *wpre, float *wsuf,
                                 float *scratch, float *state_end, float *info_incl, int want_info,
-                                cudaStream_t st) {
+                                int fold, int n_out, int per_series, cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
   const int n_w = n_vch / 32;
   const size_t smem = warp_scan_smem_bytes<S>(2);
@@ -1222,11 +1221,20 @@ cudaError_t launch_warp_combine(const DevModel &M, const float *ef, int n_vch, f
                                                       want_info);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = scan_elems<S>(wtot, n_w, wpre, 0, 0, 0, scratch, st);
-  if (e != cudaSuccess) return e;
-  if (want_info) {
-    e = scan_elems<S>(wtot, n_w, wsuf, 3, 1, 1, scratch, st);
+  if (fold) {
+    // few warps per series: sequential fold of the warp totals per series
+    k_warp_fold<S><<<(n_out + 63) / 64, 64, 0, st>>>(n_out, per_series, M.n_series, M.n_chunks,
+                                                     M.ch_first, wtot, n_w, wpre, wsuf,
+                                                     want_info);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+  } else {
+    e = scan_elems<S>(wtot, n_w, wpre, 0, 0, 0, scratch, st);
+    if (e != cudaSuccess) return e;
+    if (want_info) {
+      e = scan_elems<S>(wtot, n_w, wsuf, 3, 1, 1, scratch, st);
+      if (e != cudaSuccess) return e;
+    }
   }
   k_join<S><<<(n_vch + 127) / 128, 128, 0, st>>>(n_vch, M.n_chunks, M.ch_flags, pre_local,
                                                  suf_local, wpre, wsuf, state_end,

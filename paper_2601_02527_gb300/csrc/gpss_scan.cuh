@@ -575,4 +575,165 @@ __global__ void __launch_bounds__(128) k_join(int n_vch, int n_chunks,
     }
 }
 
+// Sequential alternative to the scan of warp totals when every series spans
+// only a few warps: one thread per (virtual) series folds its warp totals in
+// time order.  Writes, in the field positions k_join reads, the filtered
+// state at the end of each warp ((b, C) of wpre) and the information about
+// the state entering each warp from it and all later warps of the series
+// ((eta, J) of wsuf).
+template <class S>
+__global__ void __launch_bounds__(64) k_warp_fold(int n_out, int per_series, int n_series,
+                                                  int n_chunks,
+                                                  const int32_t *__restrict__ ch_first,
+                                                  const float *__restrict__ wtot, int n_w,
+                                                  float *__restrict__ wpre,
+                                                  float *__restrict__ wsuf, int want_info) {
+  using L = Elem<S>;
+  constexpr int D = S::D;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n_out) return;
+  const int s = per_series ? v : v % n_series;
+  const int base = per_series ? 0 : (v / n_series) * n_chunks;
+  const int w0 = (base + ch_first[s]) >> 5, w1 = (base + ch_first[s + 1]) >> 5;
+  float m[D], P[S::NP];
+  for (int w = w0; w < w1; ++w) {
+    float A[D][D], b[D], C[S::NP], eta[D], J[S::NP];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) A[i][j] = wtot[(size_t)(L::A + i * D + j) * n_w + w];
+      b[i] = wtot[(size_t)(L::B + i) * n_w + w];
+      eta[i] = wtot[(size_t)(L::ETA + i) * n_w + w];
+    }
+#pragma unroll
+    for (int i = 0; i < S::NP; ++i) {
+      C[i] = wtot[(size_t)(L::C + i) * n_w + w];
+      J[i] = wtot[(size_t)(L::J + i) * n_w + w];
+    }
+    if (w == w0) {
+#pragma unroll
+      for (int i = 0; i < D; ++i) m[i] = b[i];
+#pragma unroll
+      for (int i = 0; i < S::NP; ++i) P[i] = C[i];
+    } else {
+      float X[D][D], R[D][D + 1];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        float pe = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) pe += P[S::pk(i, k)] * eta[k];
+        R[i][D] = m[i] + pe;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          float acc = (i == j) ? 1.f : 0.f;
+#pragma unroll
+          for (int k = 0; k < D; ++k) acc += P[S::pk(i, k)] * J[S::pk(k, j)];
+          X[i][j] = acc;
+          R[i][j] = P[S::pk(i, j)];
+        }
+      }
+      solve_inplace<D, D + 1, float>(X, R);
+      float T[D][D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        float acc = b[i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc += A[i][k] * R[k][D];
+        m[i] = acc;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          float a2 = 0.f;
+#pragma unroll
+          for (int k = 0; k < D; ++k) a2 += A[i][k] * R[k][j];
+          T[i][j] = a2;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = i; j < D; ++j) {
+          float acc = C[S::pk(i, j)];
+#pragma unroll
+          for (int k = 0; k < D; ++k) acc += T[i][k] * A[j][k];
+          P[S::pk(i, j)] = acc;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) wpre[(size_t)(L::B + i) * n_w + w] = m[i];
+#pragma unroll
+    for (int i = 0; i < S::NP; ++i) wpre[(size_t)(L::C + i) * n_w + w] = P[i];
+  }
+  if (!want_info) return;
+  float ie[D], iJ[S::NP];
+#pragma unroll
+  for (int i = 0; i < D; ++i) ie[i] = 0.f;
+#pragma unroll
+  for (int i = 0; i < S::NP; ++i) iJ[i] = 0.f;
+  for (int w = w1 - 1; w >= w0; --w) {
+    float A[D][D], b[D], C[S::NP], eta[D], J[S::NP];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) A[i][j] = wtot[(size_t)(L::A + i * D + j) * n_w + w];
+      b[i] = wtot[(size_t)(L::B + i) * n_w + w];
+      eta[i] = wtot[(size_t)(L::ETA + i) * n_w + w];
+    }
+#pragma unroll
+    for (int i = 0; i < S::NP; ++i) {
+      C[i] = wtot[(size_t)(L::C + i) * n_w + w];
+      J[i] = wtot[(size_t)(L::J + i) * n_w + w];
+    }
+    float X[D][D], R[D][D + 1];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      float jb = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) jb += iJ[S::pk(i, k)] * b[k];
+      R[i][D] = ie[i] - jb;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float acc = (i == j) ? 1.f : 0.f, ja = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          acc += iJ[S::pk(i, k)] * C[S::pk(k, j)];
+          ja += iJ[S::pk(i, k)] * A[k][j];
+        }
+        X[i][j] = acc;
+        R[i][j] = ja;
+      }
+    }
+    solve_inplace<D, D + 1, float>(X, R);
+    float ne[D], nJ[S::NP];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      float acc = eta[i];
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += A[k][i] * R[k][D];
+      ne[i] = acc;
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = i; j < D; ++j) {
+        float a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          a1 += A[k][i] * R[k][j];
+          a2 += A[k][j] * R[k][i];
+        }
+        nJ[S::pk(i, j)] = J[S::pk(i, j)] + 0.5f * (a1 + a2);
+      }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      ie[i] = ne[i];
+      wsuf[(size_t)(L::ETA + i) * n_w + w] = ne[i];
+    }
+#pragma unroll
+    for (int i = 0; i < S::NP; ++i) {
+      iJ[i] = nJ[i];
+      wsuf[(size_t)(L::J + i) * n_w + w] = nJ[i];
+    }
+  }
+}
+
 }  // namespace gpss

@@ -1,6 +1,7 @@
 // Host build of the CUDA path's device arithmetic, for CPU tests: the same
 // header functions the kernels inline, called from ordinary host code.
 // Compiled by tests/test_host_math.py with nvcc into a shared library.
+#include <cmath>
 #include <cstring>
 
 #include "gpss_kernels.cuh"
@@ -106,6 +107,26 @@ void hh_discretize_dual(double t, double a, double beta, double *out18) {
     out18[6 + i] = v[i].da;
     out18[12 + i] = v[i].db;
   }
+}
+
+// coefficient k of the six series, one-index generator vs the full table
+double hh_table_check(double a, double beta) {
+  Dual2<double> g[6][TAB_NC];
+  taylor_coeffs<Dual2<double>>(mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), g);
+  double worst = 0.0;
+  for (int k = 0; k < TAB_NC; ++k) {
+    Dual2<double> h[6];
+    taylor_coeff_k<Dual2<double>>(mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), k, h);
+    for (int j = 0; j < 6; ++j) {
+      const double d[3] = {h[j].v - g[j][k].v, h[j].da - g[j][k].da, h[j].db - g[j][k].db};
+      const double r[3] = {g[j][k].v, g[j][k].da, g[j][k].db};
+      for (int q = 0; q < 3; ++q) {
+        const double e = std::fabs(d[q]) / (std::fabs(r[q]) + 1e-300);
+        if (d[q] != 0.0 && e > worst) worst = e;
+      }
+    }
+  }
+  return worst;
 }
 
 float hh_solve(int D, const float *A, const float *B, float *X, int R) {

@@ -132,7 +132,7 @@ def test_fp32_grad_layout1(gp, chunk, combine):
     np.testing.assert_allclose(ll.cpu().numpy(), ll2, rtol=1e-12)
 
 
-@pytest.mark.parametrize("chunk", [8, 40, 300])
+@pytest.mark.parametrize("chunk", [4, 8, 40, 300])
 def test_overlapping_three_slots(gp, chunk):
     rng = np.random.default_rng(77)
     ts, te, slot = synth.capped_overlap_exposures(rng, 1500, 0.5, 0.5, 3.0, cap=3)
@@ -148,7 +148,7 @@ def test_overlapping_three_slots(gp, chunk):
     check_grad(g.cpu().numpy(), ref_g)
 
 
-@pytest.mark.parametrize("chunk", [16, 128])
+@pytest.mark.parametrize("chunk", [4, 16, 128])
 def test_theta_sets_shared_series(gp, chunk):
     wl = synth.c5(n=1200, n_sets=5)
     wl = f32_theta(wl)

@@ -46,6 +46,8 @@ def hh():
     lib.hh_solve.argtypes = [ctypes.c_int, P(f), P(f), P(f), ctypes.c_int]
     lib.hh_solve.restype = f
     lib.hh_dim.argtypes = [ctypes.c_int]
+    lib.hh_table_check.argtypes = [d, d]
+    lib.hh_table_check.restype = d
     lib.hh_combine.argtypes = [ctypes.c_int, P(f), P(f), P(f)]
     lib.hh_chunk_loglik.argtypes = [ctypes.c_int, P(f), P(f), P(f), P(f), d, d, d]
     lib.hh_chunk_loglik.restype = d
@@ -101,6 +103,12 @@ def test_step_scalar_derivatives(oracle_lib, hh, w0, q):
         fd_q = (oracle_scalars(w0, q + h2, t) - oracle_scalars(w0, q - h2, t)) / (2 * h2)
         for got, ref in ((g_w0, fd_w0), (g_q, fd_q)):
             assert np.all(np.abs(got - ref) <= 1e-4 * np.abs(ref) + 1e-5 * np.max(np.abs(ref))), (x, got, ref)
+
+
+@pytest.mark.parametrize("w0,q", CASES)
+def test_table_generators_agree(hh, w0, q):
+    a, beta = ab(w0, q)
+    assert hh.hh_table_check(a, beta) <= 1e-13
 
 
 @pytest.mark.parametrize("D", [3, 5, 6, 7])
