@@ -122,7 +122,7 @@ class Model:
     """
 
     def __init__(self, terms, offsets, t_start, t_end, y, yerr, instrument=None, layout=0,
-                 precision=32, schedule=0, chunk_len=0, combine=0):
+                 precision=32, schedule=0, chunk_len=0, combine=0, ckpt_interval=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -137,7 +137,8 @@ class Model:
         ye = np.ascontiguousarray(yerr, np.float32)
         inst = None if instrument is None else np.ascontiguousarray(instrument, np.int32)
         spec, self._spec_arr = _spec(self.terms, self.layout)
-        opts = _Options(int(precision), int(schedule), 0, int(chunk_len), 0, 0, int(combine))
+        opts = _Options(int(precision), int(schedule), 0, int(chunk_len), int(ckpt_interval), 0,
+                        int(combine))
         h = ctypes.c_void_p()
         self.device = torch.cuda.current_device()
         rc = lib.gp_ss_build_model(ctypes.byref(spec), len(offs) - 1, offs.ctypes.data,

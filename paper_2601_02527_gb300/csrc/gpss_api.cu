@@ -104,6 +104,7 @@ struct gp_ss_model {
   // chunk plan
   int chunk_len = 0, n_chunks = 0, max_chunk = 0, max_chunks_per_series = 0;
   int combine = 0;  // cross-chunk combination: 0 auto, 1 sequential per series, 2 tree
+  int ckpt_interval = 16;  // events per recomputation segment of the gradient
   int64_t *d_ch_ev0 = nullptr, *d_ch_meas0 = nullptr;
   int32_t *d_ch_len = nullptr, *d_ch_series = nullptr, *d_ch_first = nullptr;
   uint8_t *d_ch_flags = nullptr;
@@ -521,14 +522,18 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       }
     }
     if (grad) {
-      const int max_seg = (m->max_chunk + o.CK - 1) / o.CK;
+      const int ck = m->ckpt_interval;
+      const int max_seg = (m->max_chunk + ck - 1) / ck;
+      float *rbuf = nullptr;
       if (!grab((void **)&ckpt, (size_t)std::max(max_seg, 1) * (SD + 1) * n_vch * sizeof(float)) ||
+          !grab((void **)&rbuf, (size_t)ck * (SD + 1) * n_vch * sizeof(float)) ||
           !grab((void **)&gpart, (size_t)m->n_params * n_vch * sizeof(float))) {
         res = GP_SS_ENOMEM;
         break;
       }
       PhaseTimer pt(m, st, 2);
-      if (o.grad(dm, theta, n_vch, per_series, state_end, adj, ckpt, gpart, m->d_err, tabs, st)) {
+      if (o.grad(dm, theta, n_vch, per_series, state_end, adj, ckpt, gpart, m->d_err, tabs, rbuf,
+                 ck, st)) {
         res = GP_SS_ECUDA;
         break;
       }
@@ -624,6 +629,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   if (o.precision != 32 && o.precision != 64) return GP_SS_EINVAL;
   if (o.threads_per_series > 1) return GP_SS_EUNSUPPORTED;
   if (o.chunk_combine < 0 || o.chunk_combine > 2) return GP_SS_EINVAL;
+  if (o.ckpt_interval != 0 && o.ckpt_interval != 8 && o.ckpt_interval != 16) return GP_SS_EINVAL;
   if (series_offsets[0] != 0) return GP_SS_EINVAL;
   for (int s = 0; s < n_series; ++s)
     if (series_offsets[s + 1] < series_offsets[s]) return GP_SS_EUNSORTED;
@@ -640,6 +646,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   m->precision = o.precision;
   m->schedule = o.schedule;
   m->combine = o.chunk_combine;
+  m->ckpt_interval = o.ckpt_interval == 8 ? 8 : 16;
   m->n_params = 1;
   for (int t = 0; t < spec->n_terms; ++t) {
     m->kinds[t] = spec->terms[t];

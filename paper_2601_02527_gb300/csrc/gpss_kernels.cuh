@@ -916,7 +916,8 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
                                              const float *__restrict__ adj_end,
                                              float *__restrict__ ckpt, float *__restrict__ gpart,
                                              int *__restrict__ err,
-                                             const float *__restrict__ tabs) {
+                                             const float *__restrict__ tabs,
+                                             float *__restrict__ rbuf) {
   using F = float;
   constexpr int D = S::D;
   constexpr int SD = D + S::NP;
@@ -932,8 +933,10 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   F s2;
   load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tc, s2);
   const int bs = blockDim.x;
-  // shared memory: [segment states CK*SD*bs | measurement indices CK*bs | tables]
-  float4 *tab_slots = reinterpret_cast<float4 *>(sm + (size_t)CK * (SD + 1) * bs);
+  // shared memory holds the warps' Taylor tables; the replayed states of a
+  // segment go to this thread's column of rbuf (global, coalesced across the
+  // warp; written and read back within one segment, so it stays in L2)
+  float4 *tab_slots = reinterpret_cast<float4 *>(sm);
   const float4 *tab = stage_table<S::NT>(tabs, row, tab_slots + (threadIdx.x >> 5) * (S::NT * TAB_TERM / 4));
   const uint8_t flags = M.ch_flags[c];
   const bool first = flags & 1, last = flags & 2;
@@ -958,8 +961,9 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
 #pragma unroll
   for (int t = 0; t < S::NT; ++t) gr.a[t] = gr.beta[t] = gr.w2[t] = gr.qc[t] = gr.var[t] = F(0);
   gr.s2 = F(0);
-  float *my = sm + threadIdx.x;
-  int *mys = reinterpret_cast<int *>(sm + (size_t)CK * SD * bs) + threadIdx.x;
+  const int64_t m0 = M.ch_meas0[c];
+  float *my = rbuf + vc;
+  const size_t rs = (size_t)n_vch;
   bool bad = false;
   // One forward loop serves both the checkpointing pass over the whole chunk
   // (replay = false) and the replay of one segment into shared memory
@@ -971,7 +975,7 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   rd.start(M, e0, e0 + len, M.ch_meas0[c]);
   for (;;) {
     if (kk < kend) {
-      const int mrel = (int)(rd.mi - M.ch_meas0[c]);
+      const int mrel = (int)(rd.mi - m0);
       if (!replay) {
         if (kk % CK == 0) {
           float *dst = ckpt + (size_t)(kk / CK) * (SD + 1) * n_vch;
@@ -981,10 +985,10 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       } else {
         const int slot = kk - seg * CK;
 #pragma unroll
-        for (int i = 0; i < D; ++i) my[(slot * SD + i) * bs] = m[i];
+        for (int i = 0; i < D; ++i) my[(slot * (SD + 1) + i) * rs] = m[i];
 #pragma unroll
-        for (int i = 0; i < S::NP; ++i) my[(slot * SD + D + i) * bs] = P[i];
-        mys[slot * bs] = mrel;
+        for (int i = 0; i < S::NP; ++i) my[(slot * (SD + 1) + D + i) * rs] = P[i];
+        my[(slot * (SD + 1) + SD) * rs] = __int_as_float(mrel);
       }
       F dt, Sv, vv;
       uint8_t tag;
@@ -1001,7 +1005,7 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       int k2 = kend - 1;
       F dt_n = __ldg(M.dt + e0 + k2);
       uint8_t tag_n = __ldg(M.tag + e0 + k2);
-      float4 q_n = __ldg(M.meas + M.ch_meas0[c] + mys[(k2 - seg * CK) * bs]);
+      float4 q_n = __ldg(M.meas + m0 + __float_as_int(my[((k2 - seg * CK) * (SD + 1) + SD) * rs]));
       for (; k2 >= seg * CK; --k2) {
         const int slot = k2 - seg * CK;
         const F dt = dt_n;
@@ -1010,12 +1014,12 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
         if (k2 > seg * CK) {
           dt_n = __ldg(M.dt + e0 + k2 - 1);
           tag_n = __ldg(M.tag + e0 + k2 - 1);
-          q_n = __ldg(M.meas + M.ch_meas0[c] + mys[(slot - 1) * bs]);
+          q_n = __ldg(M.meas + m0 + __float_as_int(my[((slot - 1) * (SD + 1) + SD) * rs]));
         }
 #pragma unroll
-        for (int i = 0; i < D; ++i) m[i] = my[(slot * SD + i) * bs];
+        for (int i = 0; i < D; ++i) m[i] = my[(slot * (SD + 1) + i) * rs];
 #pragma unroll
-        for (int i = 0; i < S::NP; ++i) P[i] = my[(slot * SD + D + i) * bs];
+        for (int i = 0; i < S::NP; ++i) P[i] = my[(slot * (SD + 1) + D + i) * rs];
         reverse_event<S>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab);
       }
       --seg;
@@ -1027,7 +1031,7 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
     load_rec<S>(src, n_vch, vc, m, P);
     kk = seg * CK;
     kend = min(kk + CK, len);
-    rd.start(M, e0 + kk, e0 + kend, M.ch_meas0[c] + __float_as_int(src[(size_t)SD * n_vch + vc]));
+    rd.start(M, e0 + kk, e0 + kend, m0 + __float_as_int(src[(size_t)SD * n_vch + vc]));
   }
   if (first) {
     // P0 = blkdiag(var diag(1, w2), I)
@@ -1128,7 +1132,7 @@ struct OpTable {
   cudaError_t (*scan)(const DevModel &, int, int, const float *, const double *, int, float *,
                       float *, double *, int, int *, cudaStream_t);
   cudaError_t (*grad)(const DevModel &, const float *, int, int, const float *, const float *,
-                      float *, float *, int *, const float *, cudaStream_t);
+                      float *, float *, int *, const float *, float *, int, cudaStream_t);
   cudaError_t (*tables)(const float *, int, int, int, int, float *, cudaStream_t);
   cudaError_t (*warp_combine)(const DevModel &, const float *, int, float *, float *, float *,
                               float *, float *, float *, float *, float *, int, int, int, int,
@@ -1143,7 +1147,7 @@ struct OpTable {
                       cudaStream_t);
 };
 
-constexpr int GRAD_CK = 4;
+constexpr int GRAD_CK = 16;
 constexpr int GRAD_BS = 64;
 
 template <class S, class F>
@@ -1257,24 +1261,28 @@ cudaError_t launch_finish(const DevModel &M, int n_vch, int per_series, const fl
   return cudaGetLastError();
 }
 
+template <class S, int CK>
+cudaError_t launch_grad_ck(const DevModel &M, const float *theta, int n_vch, int per_series,
+                           const float *state_end, const float *adj_end, float *ckpt, float *gpart,
+                           int *err, const float *tabs, float *rbuf, cudaStream_t st) {
+  const size_t smem = (size_t)(GRAD_BS / 32) * S::NT * TAB_TERM * sizeof(float);
+  k_grad<S, CK><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
+      M, theta, n_vch, per_series, state_end, adj_end, ckpt, gpart, err, tabs, rbuf);
+  return cudaGetLastError();
+}
+
+// ck: events per recomputation segment (8 or 16).  Scratch: ckpt
+// [ceil(max_len/ck) * (SD+1) * n_vch], rbuf [ck * (SD+1) * n_vch] floats.
 template <class S>
 cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int per_series,
                         const float *state_end, const float *adj_end, float *ckpt, float *gpart,
-                        int *err, const float *tabs, cudaStream_t st) {
+                        int *err, const float *tabs, float *rbuf, int ck, cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
-  constexpr int SD = S::D + S::NP;
-  const size_t smem = (size_t)GRAD_CK * (SD + 1) * GRAD_BS * sizeof(float) +
-                      (size_t)(GRAD_BS / 32) * S::NT * TAB_TERM * sizeof(float);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_grad<S, GRAD_CK>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
-  k_grad<S, GRAD_CK><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
-      M, theta, n_vch, per_series, state_end, adj_end, ckpt, gpart, err, tabs);
-  return cudaGetLastError();
+  if (ck == 8)
+    return launch_grad_ck<S, 8>(M, theta, n_vch, per_series, state_end, adj_end, ckpt, gpart, err,
+                                tabs, rbuf, st);
+  return launch_grad_ck<S, 16>(M, theta, n_vch, per_series, state_end, adj_end, ckpt, gpart, err,
+                               tabs, rbuf, st);
 }
 
 template <class S>
