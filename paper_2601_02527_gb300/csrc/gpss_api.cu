@@ -465,16 +465,22 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
   double *ed = nullptr, *ll_part = nullptr;
   gp_ss_status res = GP_SS_OK;
   do {
+    // for the gradient, k_elem also saves the partial element at the start of
+    // every recomputation segment but a chunk's first
+    const int ck = m->ckpt_interval;
+    const int n_pck = std::max((m->max_chunk - 1) / ck, 1);
     if (!grab((void **)&ef, (size_t)o.NF * n_vch * sizeof(float)) ||
         !grab((void **)&ed, (size_t)o.ND * n_vch * sizeof(double)) ||
-        !grab((void **)&tabs, (size_t)n_sets * o.NT * gpss::TAB_TERM * sizeof(float))) {
+        !grab((void **)&tabs, (size_t)n_sets * o.NT * gpss::TAB_TERM * sizeof(float)) ||
+        (grad && !grab((void **)&ckpt, (size_t)n_pck * (o.NF + 1) * n_vch * sizeof(float)))) {
       res = GP_SS_ENOMEM;
       break;
     }
     {
       PhaseTimer pt(m, st, 0);
       if (o.tables(theta, n_sets, m->n_params, m->kinds[0], m->kinds[1], tabs, st) ||
-          o.elem(dm, theta, n_vch, per_series, ef, ed, m->d_err, tabs, st)) {
+          o.elem(dm, theta, n_vch, per_series, ef, ed, m->d_err, tabs, grad ? ckpt : nullptr, ck,
+                 st)) {
         res = GP_SS_ECUDA;
         break;
       }
@@ -522,11 +528,8 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       }
     }
     if (grad) {
-      const int ck = m->ckpt_interval;
-      const int max_seg = (m->max_chunk + ck - 1) / ck;
       float *rbuf = nullptr;
-      if (!grab((void **)&ckpt, (size_t)std::max(max_seg, 1) * (SD + 1) * n_vch * sizeof(float)) ||
-          !grab((void **)&rbuf, (size_t)ck * (SD + 1) * n_vch * sizeof(float)) ||
+      if (!grab((void **)&rbuf, (size_t)ck * (SD + 1) * n_vch * sizeof(float)) ||
           !grab((void **)&gpart, (size_t)m->n_params * n_vch * sizeof(float))) {
         res = GP_SS_ENOMEM;
         break;
@@ -660,7 +663,9 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
     m->meas_off[s] = series_offsets[s];
     m->ev_off[s] = 2 * series_offsets[s];
   }
-  const size_t nE = std::max<int64_t>(2 * N, 1), nM = std::max<int64_t>(N, 1);
+  // one record past the last measurement: the chunk kernels prefetch the
+  // next measurement record before they know whether another one follows
+  const size_t nE = std::max<int64_t>(2 * N, 1), nM = (size_t)N + 1;
   // host copies: pinned for fast re-upload when a device is present, plain
   // otherwise (validation then still runs and reports before any device work)
   m->pinned = cudaMallocHost((void **)&m->h_dt, nE * sizeof(float)) == cudaSuccess &&
@@ -682,6 +687,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
       return GP_SS_ENOMEM;
     }
   }
+  m->h_meas[N] = make_float4(0.f, 0.f, 0.f, 0.f);
   std::vector<double> dt64, meas64;
   if (o.precision == 64) {
     dt64.resize(nE);
@@ -1002,7 +1008,8 @@ extern "C" gp_ss_status gp_ss_loglik_noalloc(const gp_ss_model *m, const float *
   // every field the combination reads is written by the element pass first,
   // so nothing in the shared array needs clearing between calls
   if (o.tables(theta, n_sets, m->n_params, m->kinds[0], m->kinds[1], tabs, st) != cudaSuccess ||
-      o.elem(dm, theta, n_vch, theta_per_series, ef, ed, nullptr, tabs, st) != cudaSuccess)
+      o.elem(dm, theta, n_vch, theta_per_series, ef, ed, nullptr, tabs, nullptr, 0, st) !=
+          cudaSuccess)
     return GP_SS_ECUDA;
   if (o.scan(dm, n_out, theta_per_series, ef, ed, n_vch, nullptr, nullptr, loglik_out, 0,
              nullptr, st) != cudaSuccess)

@@ -21,7 +21,8 @@
 // FP32 evaluation: the closed forms cancel catastrophically for small
 // omega0 t (the z-noise I_FF ~ t^5/20 is a difference of O(1) terms).  For
 // w2 t^2 <= XT2 (omega0 t <= 1.2) the six scalars come from their Taylor series in t, whose
-// coefficients follow from the recurrence of f; above it from closed forms
+// coefficients follow from the recurrence of f (the chunk kernels read an
+// economised form of them from per-row tables); above it from closed forms
 // rewritten through the identities
 //   w2 F1  = 1 - f' - 2a f
 //   4a I_pp = 1 - f'^2 - w2 f^2
@@ -297,29 +298,44 @@ GPSS_HD void sinc_pair_k(float t, float b, float rb, float &S, float &C) {
 }
 
 // ---------------------------------------------------------------------------
-// Taylor tables.  The Taylor coefficients of the six per-term scalars depend
-// only on (a, beta), so they are computed once per hyperparameter row and
-// evaluated per step by Horner's rule.  Each scalar is t^p0 * sum_k g_k t^k,
-// p0 = 1, 0, 2, 3, 1, 5 for f, f', F1, I_ff, I_pp, I_FF, with
+// Step-scalar tables.  The Taylor coefficients of the six per-term scalars
+// depend only on (a, beta), so the polynomials are built once per
+// hyperparameter row and evaluated per step by Horner's rule.  Each scalar is
+// t^p0 * g(t), p0 = 1, 0, 2, 3, 1, 5 for f, f', F1, I_ff, I_pp, I_FF, with
+// Taylor coefficients
 //   g^f_k   = c_{k+1},                  g^f'_k  = (k+1) c_{k+1},
 //   g^F1_k  = c_{k+1} / (k+2),
 //   g^Iff_k = sum_{n+m=k+2} c_n c_m / (k+3),
 //   g^Ipp_k = sum_{n+m=k+2} n m c_n c_m / (k+1),
 //   g^IFF_k = sum_{n+m=k+2} c_n c_m / ((n+1)(m+1)) / (k+5),
 // where f(s) = sum_{n>=1} c_n s^n (c_1 = 1, c_2 = -a,
-// c_{n+2} = -(2a (n+1) c_{n+1} + w2 c_n) / ((n+2)(n+1))).  Sixteen
-// coefficients keep the truncation below 1e-7 for omega0 t <= 1.2.
+// c_{n+2} = -(2a (n+1) c_{n+1} + w2 c_n) / ((n+2)(n+1))).
+//
+// The table holds the Chebyshev economisation of these series on the range
+// the table serves, [0, T] with w2 T^2 = XT2 (1% margin): TAB_NTAY Taylor
+// terms (truncation ~1e-13 there), then each power u^n (u = t/T) from the
+// top down to TAB_NC is traded for the lower powers of the shifted Chebyshev
+// polynomial T*_n(u) = T_n(2u - 1), whose leading coefficient is 2^(2n-1)
+// and whose size on [0, 1] is 1.  Each step adds at most |d_n| / 2^(2n-1)
+// to the maximum error, d_n the current coefficient of u^n.  With ten
+// coefficients the error stays below 1e-8 of each value series' size and
+// below 1e-6 of each (a, beta) tangent's (those enter only the gradient) for
+// omega0 t <= 1.2 at every damping the SHO and Matern-3/2 terms allow; the
+// worst case is critical damping.  The map is linear with T held fixed, so
+// the tangent series are economised like the values.
 //
 // Table layout per (row, term): for k = 0..NC-1 one record of TAB_W floats:
 // [6 values, 2 pad, 6 d/da, 2 pad, 6 d/dbeta, 2 pad].
 // ---------------------------------------------------------------------------
-constexpr int TAB_NC = 16;
+constexpr int TAB_NC = 10;
+constexpr int TAB_NTAY = 22;
 constexpr int TAB_W = 24;
 constexpr int TAB_TERM = TAB_NC * TAB_W;
 
+// Taylor coefficients g[j][k], k < TAB_NTAY, of the six series.
 template <class T>
-GPSS_HD void taylor_coeffs(T a, T beta, T (&g)[6][TAB_NC]) {
-  constexpr int NCF = TAB_NC + 2;
+GPSS_HD void taylor_coeffs(T a, T beta, T (&g)[6][TAB_NTAY]) {
+  constexpr int NCF = TAB_NTAY + 2;
   T c[NCF + 1];
   const T w2 = beta + a * a;
   c[0] = a * 0.0;
@@ -327,7 +343,7 @@ GPSS_HD void taylor_coeffs(T a, T beta, T (&g)[6][TAB_NC]) {
   c[2] = -a;
   for (int n = 1; n + 2 <= NCF; ++n)
     c[n + 2] = -(a * (2.0 * (n + 1)) * c[n + 1] + w2 * c[n]) / (double)((n + 2) * (n + 1));
-  for (int k = 0; k < TAB_NC; ++k) {
+  for (int k = 0; k < TAB_NTAY; ++k) {
     g[0][k] = c[k + 1];
     g[1][k] = c[k + 1] * (double)(k + 1);
     g[2][k] = c[k + 1] / (double)(k + 2);
@@ -345,10 +361,11 @@ GPSS_HD void taylor_coeffs(T a, T beta, T (&g)[6][TAB_NC]) {
   }
 }
 
-// Coefficient k of all six series (same definitions as taylor_coeffs).
+// Coefficient k < TAB_NTAY of the six Taylor series (same definitions as
+// taylor_coeffs; one table-building lane per coefficient).
 template <class T>
 GPSS_HD void taylor_coeff_k(T a, T beta, int k, T (&g)[6]) {
-  constexpr int NCF = TAB_NC + 2;
+  constexpr int NCF = TAB_NTAY + 2;
   T c[NCF + 1];
   const T w2 = beta + a * a;
   c[0] = a * 0.0;
@@ -370,6 +387,61 @@ GPSS_HD void taylor_coeff_k(T a, T beta, int k, T (&g)[6]) {
   g[3] = s1 / (double)(k + 3);
   g[4] = s2 / (double)(k + 1);
   g[5] = s3 / (double)(k + 5);
+}
+
+// Range of the table: t in [0, T], T = 1.01 sqrt(XT2 / w2).
+GPSS_HD double table_range(double w2) {
+  return 1.01 * sqrt((double)TaylorOrder<float>::XT2 / w2);
+}
+
+// The economisation as a fixed linear map in u = t / T: coefficient k < NC of
+// the economised polynomial is sum_n m[k][n] d_n, d_n the Taylor
+// coefficients of u^n.  Built by applying the reductions (top power first)
+// to the unit vectors.  Monomial coefficients of T*_n: s_{n,0} = (-1)^n and
+// s_{n,j+1} = -4 (n+j)(n-j) / ((2j+1)(2j+2)) s_{n,j} (integers).
+struct EconMap {
+  double m[TAB_NC][TAB_NTAY];
+};
+
+GPSS_HD void econ_map(EconMap &E) {
+  for (int col = 0; col < TAB_NTAY; ++col) {
+    double d[TAB_NTAY];
+    for (int k = 0; k < TAB_NTAY; ++k) d[k] = (k == col) ? 1.0 : 0.0;
+    for (int n = TAB_NTAY - 1; n >= TAB_NC; --n) {
+      if (d[n] == 0.0) continue;
+      const double lead = ldexp(1.0, 2 * n - 1);
+      double sn = (n & 1) ? -1.0 : 1.0;
+      for (int k = 0; k < n; ++k) {
+        d[k] -= d[n] * (sn / lead);
+        sn *= -4.0 * (double)(n + k) * (double)(n - k) / ((double)(2 * k + 1) * (double)(2 * k + 2));
+      }
+      d[n] = 0.0;
+    }
+    for (int k = 0; k < TAB_NC; ++k) E.m[k][col] = d[k];
+  }
+}
+
+// Table coefficient k (in t) from the Taylor coefficients g[j][n] (all n):
+// e_k = sum_n m[k][n] T^(n-k) g_n.
+template <class T>
+GPSS_HD T econ_apply(const EconMap &E, int k, double rng, const T *g, int stride) {
+  T acc = g[0] * 0.0;
+  double p = 1.0;  // T^(n-k)
+  for (int n = k; n < TAB_NTAY; ++n) {
+    acc = acc + g[(size_t)n * stride] * (E.m[k][n] * p);
+    p *= rng;
+  }
+  return acc;
+}
+
+// Economised table coefficients e[j][k], k < TAB_NC, on [0, T] (FP64).
+template <class T>
+GPSS_HD void table_coeffs(const EconMap &E, T a, T beta, T (&e)[6][TAB_NC]) {
+  T g[6][TAB_NTAY];
+  taylor_coeffs<T>(a, beta, g);
+  const double rng = table_range(val(beta + a * a));
+  for (int j = 0; j < 6; ++j)
+    for (int k = 0; k < TAB_NC; ++k) e[j][k] = econ_apply<T>(E, k, rng, g[j], 1);
 }
 
 // Six Taylor-branch scalars from a table in shared memory (broadcast reads).
@@ -409,7 +481,7 @@ GPSS_HD Disc<Dual2<float>> disc_tab_dual(float t, const float4 *__restrict__ tab
     da[0] = q2.x; da[1] = q2.y; da[2] = q2.z; da[3] = q2.w; da[4] = q3.x; da[5] = q3.y;
     db[0] = q4.x; db[1] = q4.y; db[2] = q4.z; db[3] = q4.w; db[4] = q5.x; db[5] = q5.y;
   }
-#pragma unroll 2
+#pragma unroll 3
   for (int k = TAB_NC - 2; k >= 0; --k) {
     const float4 *r = tab + k * (TAB_W / 4);
     const float4 q0 = r[0], q1 = r[1], q2 = r[2], q3 = r[3], q4 = r[4], q5 = r[5];

@@ -22,9 +22,11 @@
 //                 log-likelihood in closed form, and for the gradient the
 //                 information about each chunk's end state from all later
 //                 data, turned into the adjoint of that state.
-//      k_grad     one thread per chunk: recompute the chunk from its incoming
-//                 state with checkpoints every CK events, then sweep back in
-//                 time, accumulating d loglik / d theta.
+//      k_grad     one thread per chunk, segments of CK events from last to
+//                 first: the segment's starting state from the partial
+//                 element k_elem saved there and the chunk's incoming state,
+//                 a forward replay of the segment, then a sweep back in time
+//                 accumulating d loglik / d theta.
 #pragma once
 
 #include "gpss_device.cuh"
@@ -186,27 +188,42 @@ GPSS_D void flag_error(int *err, int row, int code) {
 }
 
 // ---------------------------------------------------------------------------
-// Taylor tables, one thread per (hyperparameter row, term), FP64 arithmetic.
+// Step-scalar tables, one warp per (hyperparameter row, term), FP64: lane k
+// builds Taylor coefficient k of the six series and their (a, beta)
+// tangents, then lanes k < TAB_NC apply row k of the economisation map.
 // ---------------------------------------------------------------------------
+constexpr int TABLE_WARPS = 4;
+
 template <int NT>
-__global__ void k_tables(const float *__restrict__ theta, int n_rows, int n_params, int kind0,
-                         int kind1, float *__restrict__ tab) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n_rows * NT * TAB_NC) return;
-  const int k = idx % TAB_NC, rt = idx / TAB_NC;
+__global__ void __launch_bounds__(32 * TABLE_WARPS) k_tables(const float *__restrict__ theta,
+                                                            int n_rows, int n_params, int kind0,
+                                                            int kind1, float *__restrict__ tab,
+                                                            EconMap E) {
+  __shared__ Dual2<double> sg[TABLE_WARPS][TAB_NTAY][6];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rt = blockIdx.x * TABLE_WARPS + w;
+  if (rt >= n_rows * NT) return;  // whole warps leave together
   const int row = rt / NT, t = rt % NT;
   const int kinds[4] = {kind0, kind1, 0, 0};
   TermC<double> tc[NT];
   double s2;
   load_terms<NT, double>(theta + (size_t)row * n_params, kinds, tc, s2);
-  Dual2<double> g[6];
-  taylor_coeff_k<Dual2<double>>(mk(tc[t].a, 1.0, 0.0), mk(tc[t].beta, 0.0, 1.0), k, g);
-  float *r = tab + ((size_t)rt * TAB_NC + k) * TAB_W;
+  const Dual2<double> a = mk(tc[t].a, 1.0, 0.0), beta = mk(tc[t].beta, 0.0, 1.0);
+  if (lane < TAB_NTAY) {
+    Dual2<double> g[6];
+    taylor_coeff_k<Dual2<double>>(a, beta, lane, g);
+    for (int j = 0; j < 6; ++j) sg[w][lane][j] = g[j];
+  }
+  __syncwarp();
+  if (lane >= TAB_NC) return;
+  const double rng = table_range(tc[t].w2);
+  float *r = tab + ((size_t)rt * TAB_NC + lane) * TAB_W;
   for (int j = 0; j < TAB_W; ++j) r[j] = 0.f;
   for (int j = 0; j < 6; ++j) {
-    r[j] = (float)g[j].v;
-    r[8 + j] = (float)g[j].da;
-    r[16 + j] = (float)g[j].db;
+    const Dual2<double> e = econ_apply<Dual2<double>>(E, lane, rng, &sg[w][0][j], 6);
+    r[j] = (float)e.v;
+    r[8 + j] = (float)e.da;
+    r[16 + j] = (float)e.db;
   }
 }
 
@@ -270,12 +287,37 @@ struct ElemLayout : Elem<S> {
 };
 
 template <class S>
+GPSS_D void store_elem(float *dst, int n_vch, int vc, const float (&A)[S::D][S::D], const float *b,
+                       const float *C, const float *eta, const float *J) {
+  using L = ElemLayout<S>;
+  constexpr int D = S::D;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) dst[(size_t)(L::A + i * D + j) * n_vch + vc] = A[i][j];
+    dst[(size_t)(L::B + i) * n_vch + vc] = b[i];
+    dst[(size_t)(L::ETA + i) * n_vch + vc] = eta[i];
+  }
+#pragma unroll
+  for (int i = 0; i < S::NP; ++i) {
+    dst[(size_t)(L::C + i) * n_vch + vc] = C[i];
+    dst[(size_t)(L::J + i) * n_vch + vc] = J[i];
+  }
+}
+
+// With pck set, the partial element of the chunk's first events is also saved
+// at the start of every gradient segment but the first (segments of ck
+// events, aligned to the chunk's end): record j at pck + j (NF + 1) n_vch,
+// fields as above plus the number of measurements before that point.
+template <class S>
 __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restrict__ theta, int n_vch,
                                               int per_series, float *__restrict__ ef,
                                               double *__restrict__ ed, int *__restrict__ err,
-                                              const float *__restrict__ tabs) {
+                                              const float *__restrict__ tabs,
+                                              float *__restrict__ pck, int ck) {
   using F = float;
   constexpr int D = S::D;
+  using L = ElemLayout<S>;
   extern __shared__ float4 smem_tab[];
   const int vc = blockIdx.x * blockDim.x + threadIdx.x;
   if (vc >= n_vch) return;
@@ -314,7 +356,17 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
   const int len = M.ch_len[c];
   EventReader rd;
   rd.start(M, e0, e0 + len, M.ch_meas0[c]);
+  // gradient segments end at len - j ck (the first one is the short one);
+  // at each later segment's start the partial element is saved
+  const int f0 = len - ((len - 1) / ck) * ck;
+  int next_ck = pck ? f0 : len;
   for (int kk = 0; kk < len; ++kk) {
+    if (kk == next_ck) {
+      float *dst = pck + (size_t)((kk - f0) / ck) * (L::NF + 1) * n_vch;
+      store_elem<S>(dst, n_vch, vc, A, b, C, eta, J);
+      dst[(size_t)L::NF * n_vch + vc] = __int_as_float(n_end);
+      next_ck += ck;
+    }
     F dt;
     uint8_t tag;
     float4 q;
@@ -386,19 +438,7 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
       }
     }
   }
-  using L = ElemLayout<S>;
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-#pragma unroll
-    for (int j = 0; j < D; ++j) ef[(size_t)(L::A + i * D + j) * n_vch + vc] = A[i][j];
-    ef[(size_t)(L::B + i) * n_vch + vc] = b[i];
-    ef[(size_t)(L::ETA + i) * n_vch + vc] = eta[i];
-  }
-#pragma unroll
-  for (int i = 0; i < S::NP; ++i) {
-    ef[(size_t)(L::C + i) * n_vch + vc] = C[i];
-    ef[(size_t)(L::J + i) * n_vch + vc] = J[i];
-  }
+  store_elem<S>(ef, n_vch, vc, A, b, C, eta, J);
   ed[vc] = gam;
   ed[(size_t)n_vch + vc] = ld;
   ed[(size_t)2 * n_vch + vc] = (double)n_end;
@@ -910,17 +950,75 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
   }
 }
 
+// Filtered state after the first events of a chunk, from the state entering
+// the chunk, N(m_in, P_in), and the partial element (A, b, C, eta, J) of
+// those events (the same combination as between chunks):
+//   X = I + P_in J,  m = A X^{-1} (m_in + P_in eta) + b,  P = A X^{-1} P_in A^T + C.
+template <class S>
+GPSS_HD void apply_partial(const float *src, int n_vch, int vc, const float *m_in,
+                           const float *P_in, float *m, float *P) {
+  using L = ElemLayout<S>;
+  constexpr int D = S::D;
+  float J[S::NP], X[D][D], R[D][D + 1];
+#pragma unroll
+  for (int i = 0; i < S::NP; ++i) J[i] = src[(size_t)(L::J + i) * n_vch + vc];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    float pe = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) pe += P_in[S::pk(i, k)] * src[(size_t)(L::ETA + k) * n_vch + vc];
+    R[i][D] = m_in[i] + pe;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float acc = (i == j) ? 1.f : 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += P_in[S::pk(i, k)] * J[S::pk(k, j)];
+      X[i][j] = acc;
+      R[i][j] = P_in[S::pk(i, j)];
+    }
+  }
+  solve_inplace<D, D + 1, float>(X, R);  // R = X^{-1} [P_in | m_in + P_in eta]
+  float T[D][D + 1];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j <= D; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += src[(size_t)(L::A + i * D + k) * n_vch + vc] * R[k][j];
+      T[i][j] = acc;
+    }
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    m[i] = T[i][D] + src[(size_t)(L::B + i) * n_vch + vc];
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      float acc = src[(size_t)(L::C + S::pk(i, j)) * n_vch + vc];
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += T[i][k] * src[(size_t)(L::A + j * D + k) * n_vch + vc];
+      P[S::pk(i, j)] = acc;
+    }
+  }
+}
+
+// Segments of CK events aligned to the chunk's end (the first may be
+// shorter).  Walking the segments from last to first: the filtered state at
+// the segment's start comes from the partial element saved there by k_elem,
+// the segment is replayed forward into this thread's column of rbuf (global,
+// coalesced across the warp, written and read back within one segment so it
+// stays in L2), then walked backwards in time.
 template <class S, int CK>
 __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restrict__ theta, int n_vch,
                                              int per_series, const float *__restrict__ state_end,
                                              const float *__restrict__ adj_end,
-                                             float *__restrict__ ckpt, float *__restrict__ gpart,
+                                             const float *__restrict__ pck, float *__restrict__ gpart,
                                              int *__restrict__ err,
                                              const float *__restrict__ tabs,
                                              float *__restrict__ rbuf) {
   using F = float;
   constexpr int D = S::D;
   constexpr int SD = D + S::NP;
+  constexpr int NF = ElemLayout<S>::NF;
   extern __shared__ float sm[];
   const int vc = blockIdx.x * blockDim.x + threadIdx.x;
   if (vc >= n_vch) return;
@@ -932,22 +1030,16 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   TermC<F> tc[S::NT];
   F s2;
   load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tc, s2);
-  const int bs = blockDim.x;
-  // shared memory holds the warps' Taylor tables; the replayed states of a
-  // segment go to this thread's column of rbuf (global, coalesced across the
-  // warp; written and read back within one segment, so it stays in L2)
+  // shared memory holds the warps' Taylor tables
   float4 *tab_slots = reinterpret_cast<float4 *>(sm);
   const float4 *tab = stage_table<S::NT>(tabs, row, tab_slots + (threadIdx.x >> 5) * (S::NT * TAB_TERM / 4));
   const uint8_t flags = M.ch_flags[c];
   const bool first = flags & 1, last = flags & 2;
   F m[D], P[S::NP];
-  if (first)
-    init_state<S>(tc, m, P);
-  else
-    load_rec<S>(state_end, n_vch, vc - 1, m, P);
   const int64_t e0 = M.ch_ev0[c];
   const int len = M.ch_len[c];
   const int nseg = (len + CK - 1) / CK;
+  const int f0 = len - (nseg - 1) * CK;
   F lam[D], Lam[S::NP];
   if (last) {
 #pragma unroll
@@ -965,73 +1057,69 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   float *my = rbuf + vc;
   const size_t rs = (size_t)n_vch;
   bool bad = false;
-  // One forward loop serves both the checkpointing pass over the whole chunk
-  // (replay = false) and the replay of one segment into shared memory
-  // (replay = true); after each replay the segment is walked backwards.
-  bool replay = false;
-  int seg = nseg - 1;
-  int kk = 0, kend = len;
-  EventReader rd;
-  rd.start(M, e0, e0 + len, M.ch_meas0[c]);
-  for (;;) {
-    if (kk < kend) {
-      const int mrel = (int)(rd.mi - m0);
-      if (!replay) {
-        if (kk % CK == 0) {
-          float *dst = ckpt + (size_t)(kk / CK) * (SD + 1) * n_vch;
-          store_rec<S>(dst, n_vch, vc, m, P);
-          dst[(size_t)SD * n_vch + vc] = __int_as_float(mrel);
-        }
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int k0 = seg == 0 ? 0 : f0 + (seg - 1) * CK;
+    const int k1 = seg == 0 ? f0 : k0 + CK;
+    int mrel = 0;
+    if (seg == 0) {
+      if (first)
+        init_state<S>(tc, m, P);
+      else
+        load_rec<S>(state_end, n_vch, vc - 1, m, P);
+    } else {
+      F mi[D], Pi[S::NP];
+      if (first) {
+        // the first chunk's element already starts from the prior (A = 0)
+#pragma unroll
+        for (int i = 0; i < D; ++i) mi[i] = F(0);
+#pragma unroll
+        for (int i = 0; i < S::NP; ++i) Pi[i] = F(0);
       } else {
-        const int slot = kk - seg * CK;
-#pragma unroll
-        for (int i = 0; i < D; ++i) my[(slot * (SD + 1) + i) * rs] = m[i];
-#pragma unroll
-        for (int i = 0; i < S::NP; ++i) my[(slot * (SD + 1) + D + i) * rs] = P[i];
-        my[(slot * (SD + 1) + SD) * rs] = __int_as_float(mrel);
+        load_rec<S>(state_end, n_vch, vc - 1, mi, Pi);
       }
+      const float *src = pck + (size_t)(seg - 1) * (NF + 1) * n_vch;
+      apply_partial<S>(src, n_vch, vc, mi, Pi, m, P);
+      mrel = __float_as_int(src[(size_t)NF * n_vch + vc]);
+    }
+    // forward replay of the segment
+    EventReader rd;
+    rd.start(M, e0 + k0, e0 + k1, m0 + mrel);
+    for (int kk = k0; kk < k1; ++kk) {
+      const int slot = kk - k0;
+#pragma unroll
+      for (int i = 0; i < D; ++i) my[(slot * (SD + 1) + i) * rs] = m[i];
+#pragma unroll
+      for (int i = 0; i < S::NP; ++i) my[(slot * (SD + 1) + D + i) * rs] = P[i];
+      my[(slot * (SD + 1) + SD) * rs] = __int_as_float((int)(rd.mi - m0));
       F dt, Sv, vv;
       uint8_t tag;
       float4 q;
       rd.next(dt, tag, q);
       if (filter_step<S, F>(dt, tag, q.x, q.y, q.z, tc, s2, m, P, Sv, vv, tab))
         bad |= !(Sv > F(0));
-      ++kk;
-      continue;
     }
-    if (replay) {
-      // backward walk over the replayed segment; the next (earlier) event's
-      // data are loaded while the current one is processed
-      int k2 = kend - 1;
-      F dt_n = __ldg(M.dt + e0 + k2);
-      uint8_t tag_n = __ldg(M.tag + e0 + k2);
-      float4 q_n = __ldg(M.meas + m0 + __float_as_int(my[((k2 - seg * CK) * (SD + 1) + SD) * rs]));
-      for (; k2 >= seg * CK; --k2) {
-        const int slot = k2 - seg * CK;
-        const F dt = dt_n;
-        const uint8_t tag = tag_n;
-        const float4 q = q_n;
-        if (k2 > seg * CK) {
-          dt_n = __ldg(M.dt + e0 + k2 - 1);
-          tag_n = __ldg(M.tag + e0 + k2 - 1);
-          q_n = __ldg(M.meas + m0 + __float_as_int(my[((slot - 1) * (SD + 1) + SD) * rs]));
-        }
-#pragma unroll
-        for (int i = 0; i < D; ++i) m[i] = my[(slot * (SD + 1) + i) * rs];
-#pragma unroll
-        for (int i = 0; i < S::NP; ++i) P[i] = my[(slot * (SD + 1) + D + i) * rs];
-        reverse_event<S>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab);
+    // backward walk; the next (earlier) event's data are loaded while the
+    // current one is processed
+    int k2 = k1 - 1;
+    F dt_n = __ldg(M.dt + e0 + k2);
+    uint8_t tag_n = __ldg(M.tag + e0 + k2);
+    float4 q_n = __ldg(M.meas + m0 + __float_as_int(my[((k2 - k0) * (SD + 1) + SD) * rs]));
+    for (; k2 >= k0; --k2) {
+      const int slot = k2 - k0;
+      const F dt = dt_n;
+      const uint8_t tag = tag_n;
+      const float4 q = q_n;
+      if (k2 > k0) {
+        dt_n = __ldg(M.dt + e0 + k2 - 1);
+        tag_n = __ldg(M.tag + e0 + k2 - 1);
+        q_n = __ldg(M.meas + m0 + __float_as_int(my[((slot - 1) * (SD + 1) + SD) * rs]));
       }
-      --seg;
+#pragma unroll
+      for (int i = 0; i < D; ++i) m[i] = my[(slot * (SD + 1) + i) * rs];
+#pragma unroll
+      for (int i = 0; i < S::NP; ++i) P[i] = my[(slot * (SD + 1) + D + i) * rs];
+      reverse_event<S>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab);
     }
-    if (seg < 0) break;
-    // start replaying segment `seg` from its checkpoint
-    replay = true;
-    const float *src = ckpt + (size_t)seg * (SD + 1) * n_vch;
-    load_rec<S>(src, n_vch, vc, m, P);
-    kk = seg * CK;
-    kend = min(kk + CK, len);
-    rd.start(M, e0 + kk, e0 + kend, m0 + __float_as_int(src[(size_t)SD * n_vch + vc]));
   }
   if (first) {
     // P0 = blkdiag(var diag(1, w2), I)
@@ -1128,11 +1216,11 @@ struct OpTable {
   cudaError_t (*plain32)(const DevModel &, const float *, int, int, double *, int *, cudaStream_t);
   cudaError_t (*plain64)(const DevModel &, const float *, int, int, double *, int *, cudaStream_t);
   cudaError_t (*elem)(const DevModel &, const float *, int, int, float *, double *, int *,
-                      const float *, cudaStream_t);
+                      const float *, float *, int, cudaStream_t);
   cudaError_t (*scan)(const DevModel &, int, int, const float *, const double *, int, float *,
                       float *, double *, int, int *, cudaStream_t);
   cudaError_t (*grad)(const DevModel &, const float *, int, int, const float *, const float *,
-                      float *, float *, int *, const float *, float *, int, cudaStream_t);
+                      const float *, float *, int *, const float *, float *, int, cudaStream_t);
   cudaError_t (*tables)(const float *, int, int, int, int, float *, cudaStream_t);
   cudaError_t (*warp_combine)(const DevModel &, const float *, int, float *, float *, float *,
                               float *, float *, float *, float *, float *, int, int, int, int,
@@ -1161,21 +1249,29 @@ cudaError_t launch_plain(const DevModel &M, const float *theta, int n_out, int p
 
 template <class S>
 cudaError_t launch_elem(const DevModel &M, const float *theta, int n_vch, int per_series,
-                        float *ef, double *ed, int *err, const float *tabs, cudaStream_t st) {
+                        float *ef, double *ed, int *err, const float *tabs, float *pck, int ck,
+                        cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
+  if (pck && (ck != 8 && ck != 16)) return cudaErrorInvalidValue;
   const int bs = 128;
   const size_t smem = (size_t)(bs / 32) * S::NT * TAB_TERM * sizeof(float);
   k_elem<S><<<(n_vch + bs - 1) / bs, bs, smem, st>>>(M, theta, n_vch, per_series, ef, ed, err,
-                                                    tabs);
+                                                    tabs, pck, pck ? ck : 1);
   return cudaGetLastError();
 }
 
 template <class S>
 cudaError_t launch_tables(const float *theta, int n_rows, int n_params, int k0, int k1,
                           float *tab, cudaStream_t st) {
-  const int n = n_rows * S::NT * TAB_NC;
+  const int n = n_rows * S::NT;
   if (n <= 0) return cudaSuccess;
-  k_tables<S::NT><<<(n + 127) / 128, 128, 0, st>>>(theta, n_rows, n_params, k0, k1, tab);
+  static const EconMap E = [] {
+    EconMap e;
+    econ_map(e);
+    return e;
+  }();
+  k_tables<S::NT><<<(n + TABLE_WARPS - 1) / TABLE_WARPS, 32 * TABLE_WARPS, 0, st>>>(
+      theta, n_rows, n_params, k0, k1, tab, E);
   return cudaGetLastError();
 }
 
@@ -1263,26 +1359,30 @@ cudaError_t launch_finish(const DevModel &M, int n_vch, int per_series, const fl
 
 template <class S, int CK>
 cudaError_t launch_grad_ck(const DevModel &M, const float *theta, int n_vch, int per_series,
-                           const float *state_end, const float *adj_end, float *ckpt, float *gpart,
-                           int *err, const float *tabs, float *rbuf, cudaStream_t st) {
+                           const float *state_end, const float *adj_end, const float *pck,
+                           float *gpart, int *err, const float *tabs, float *rbuf, cudaStream_t st) {
   const size_t smem = (size_t)(GRAD_BS / 32) * S::NT * TAB_TERM * sizeof(float);
   k_grad<S, CK><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
-      M, theta, n_vch, per_series, state_end, adj_end, ckpt, gpart, err, tabs, rbuf);
+      M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err, tabs, rbuf);
   return cudaGetLastError();
 }
 
-// ck: events per recomputation segment (8 or 16).  Scratch: ckpt
-// [ceil(max_len/ck) * (SD+1) * n_vch], rbuf [ck * (SD+1) * n_vch] floats.
+// ck: events per recomputation segment (8 or 16), the value k_elem saved the
+// partial elements pck with ([(max_len-1)/ck] * (NF+1) * n_vch floats).
+// Scratch: rbuf [ck * (SD+1) * n_vch] floats.
 template <class S>
 cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int per_series,
-                        const float *state_end, const float *adj_end, float *ckpt, float *gpart,
-                        int *err, const float *tabs, float *rbuf, int ck, cudaStream_t st) {
+                        const float *state_end, const float *adj_end, const float *pck,
+                        float *gpart, int *err, const float *tabs, float *rbuf, int ck,
+                        cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
   if (ck == 8)
-    return launch_grad_ck<S, 8>(M, theta, n_vch, per_series, state_end, adj_end, ckpt, gpart, err,
+    return launch_grad_ck<S, 8>(M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err,
                                 tabs, rbuf, st);
-  return launch_grad_ck<S, 16>(M, theta, n_vch, per_series, state_end, adj_end, ckpt, gpart, err,
-                               tabs, rbuf, st);
+  if (ck == 16)
+    return launch_grad_ck<S, 16>(M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err,
+                                 tabs, rbuf, st);
+  return cudaErrorInvalidValue;
 }
 
 template <class S>

@@ -11,8 +11,10 @@ using namespace gpss;
 namespace {
 
 void build_table(float a, float beta, float *tab) {
+  EconMap E;
+  econ_map(E);
   Dual2<double> g[6][TAB_NC];
-  taylor_coeffs<Dual2<double>>(mk((double)a, 1.0, 0.0), mk((double)beta, 0.0, 1.0), g);
+  table_coeffs<Dual2<double>>(E, mk((double)a, 1.0, 0.0), mk((double)beta, 0.0, 1.0), g);
   for (int k = 0; k < TAB_NC; ++k) {
     float *r = tab + k * TAB_W;
     for (int j = 0; j < TAB_W; ++j) r[j] = 0.f;
@@ -109,23 +111,33 @@ void hh_discretize_dual(double t, double a, double beta, double *out18) {
   }
 }
 
-// coefficient k of the six series, one-index generator vs the full table
-double hh_table_check(double a, double beta) {
-  Dual2<double> g[6][TAB_NC];
+// Economised table polynomials (FP64) against the TAB_NTAY-term Taylor
+// series they replace, on 401 points of the table's range [0, T]: the worst
+// error of any of the 18 series (6 values, d/da, d/dbeta) relative to that
+// series' largest magnitude on the range; which = 0: the six values,
+// 1: the twelve (a, beta) tangents.
+double hh_table_check(double a, double beta, int which) {
+  EconMap E;
+  econ_map(E);
+  Dual2<double> g[6][TAB_NTAY], e[6][TAB_NC];
   taylor_coeffs<Dual2<double>>(mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), g);
+  table_coeffs<Dual2<double>>(E, mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), e);
+  const double T = table_range(beta + a * a);
   double worst = 0.0;
-  for (int k = 0; k < TAB_NC; ++k) {
-    Dual2<double> h[6];
-    taylor_coeff_k<Dual2<double>>(mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), k, h);
-    for (int j = 0; j < 6; ++j) {
-      const double d[3] = {h[j].v - g[j][k].v, h[j].da - g[j][k].da, h[j].db - g[j][k].db};
-      const double r[3] = {g[j][k].v, g[j][k].da, g[j][k].db};
-      for (int q = 0; q < 3; ++q) {
-        const double e = std::fabs(d[q]) / (std::fabs(r[q]) + 1e-300);
-        if (d[q] != 0.0 && e > worst) worst = e;
+  for (int j = 0; j < 6; ++j)
+    for (int q = which ? 1 : 0; q < (which ? 3 : 1); ++q) {
+      auto comp = [q](const Dual2<double> &x) { return q == 0 ? x.v : (q == 1 ? x.da : x.db); };
+      double mx = 0.0, err = 0.0;
+      for (int i = 0; i <= 400; ++i) {
+        const double t = T * i / 400.0;
+        double r = 0.0, h = 0.0;
+        for (int k = TAB_NTAY - 1; k >= 0; --k) r = r * t + comp(g[j][k]);
+        for (int k = TAB_NC - 1; k >= 0; --k) h = h * t + comp(e[j][k]);
+        mx = std::fmax(mx, std::fabs(r));
+        err = std::fmax(err, std::fabs(h - r));
       }
+      if (mx > 0.0) worst = std::fmax(worst, err / mx);
     }
-  }
   return worst;
 }
 
@@ -159,6 +171,27 @@ void hh_boundary_adjoint(int shape, const float *m, const float *P, const float 
   if (shape == 0) adj_s<Shape<1, 1, 0>>(m, P, eta, J, lam, Lam);
   else if (shape == 1) adj_s<Shape<2, 1, 1>>(m, P, eta, J, lam, Lam);
   else adj_s<Shape<2, 3, 0>>(m, P, eta, J, lam, Lam);
+}
+
+// coefficient k of the six Taylor series: one-index generator (the one the
+// table kernel's lanes run) vs the full generator
+double hh_taylor_k_check(double a, double beta) {
+  Dual2<double> g[6][TAB_NTAY];
+  taylor_coeffs<Dual2<double>>(mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), g);
+  double worst = 0.0;
+  for (int k = 0; k < TAB_NTAY; ++k) {
+    Dual2<double> h[6];
+    taylor_coeff_k<Dual2<double>>(mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), k, h);
+    for (int j = 0; j < 6; ++j) {
+      const double d[3] = {h[j].v - g[j][k].v, h[j].da - g[j][k].da, h[j].db - g[j][k].db};
+      const double r[3] = {g[j][k].v, g[j][k].da, g[j][k].db};
+      for (int q = 0; q < 3; ++q) {
+        const double e = std::fabs(d[q]) / (std::fabs(r[q]) + 1e-300);
+        if (d[q] != 0.0 && e > worst) worst = e;
+      }
+    }
+  }
+  return worst;
 }
 
 }  // extern "C"

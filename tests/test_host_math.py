@@ -7,6 +7,7 @@ kernels inline (nvcc, host code only).  Checked here:
     Loan discretisation over seven decades of step length;
   * their forward-mode derivatives in (a, beta) against central differences
     of the oracle;
+  * the economised step-scalar tables against the Taylor series they replace;
   * the pivoted dense solver, the element combination, the closed-form chunk
     log-likelihood and the boundary adjoint against numpy.
 """
@@ -46,8 +47,10 @@ def hh():
     lib.hh_solve.argtypes = [ctypes.c_int, P(f), P(f), P(f), ctypes.c_int]
     lib.hh_solve.restype = f
     lib.hh_dim.argtypes = [ctypes.c_int]
-    lib.hh_table_check.argtypes = [d, d]
+    lib.hh_table_check.argtypes = [d, d, ctypes.c_int]
     lib.hh_table_check.restype = d
+    lib.hh_taylor_k_check.argtypes = [d, d]
+    lib.hh_taylor_k_check.restype = d
     lib.hh_combine.argtypes = [ctypes.c_int, P(f), P(f), P(f)]
     lib.hh_chunk_loglik.argtypes = [ctypes.c_int, P(f), P(f), P(f), P(f), d, d, d]
     lib.hh_chunk_loglik.restype = d
@@ -105,10 +108,21 @@ def test_step_scalar_derivatives(oracle_lib, hh, w0, q):
             assert np.all(np.abs(got - ref) <= 1e-4 * np.abs(ref) + 1e-5 * np.max(np.abs(ref))), (x, got, ref)
 
 
-@pytest.mark.parametrize("w0,q", CASES)
-def test_table_generators_agree(hh, w0, q):
+@pytest.mark.parametrize("w0,q", CASES + [(0.2, 0.55), (9.9, 10.0), (0.05, 30.0), (30.0, 0.5)])
+def test_economised_tables_match_taylor(hh, w0, q):
+    # the ten economised coefficients reproduce the 22-term Taylor series on
+    # the table's range: the six values to 1e-8 of each series' size (FP32
+    # rounding is 6e-8), the twelve (a, beta) tangents, which enter only the
+    # gradient, to 1e-6 (worst at critical damping, Q = 1/2: 7e-7)
     a, beta = ab(w0, q)
-    assert hh.hh_table_check(a, beta) <= 1e-13
+    assert hh.hh_table_check(a, beta, 0) <= 1e-8
+    assert hh.hh_table_check(a, beta, 1) <= 1e-6
+
+
+@pytest.mark.parametrize("w0,q", CASES)
+def test_taylor_generators_agree(hh, w0, q):
+    a, beta = ab(w0, q)
+    assert hh.hh_taylor_k_check(a, beta) <= 1e-13
 
 
 @pytest.mark.parametrize("D", [3, 5, 6, 7])

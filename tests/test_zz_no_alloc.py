@@ -58,7 +58,7 @@ def test_noalloc_rejects_too_large(gp):
     m = gp.Model.from_workload(wl, chunk_len=12)
     d = m.info["state_dim"]
     need = ((2 * d * d + 3 * d) * 4 * m.info["n_chunks"] + 255) // 256 * 256 + 24 * m.info["n_chunks"]
-    need += (1536 * 2 * wl.n_series + 255) // 256 * 256
+    need += (960 * 2 * wl.n_series + 255) // 256 * 256
     assert need > 16 << 20
     th = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
     with pytest.raises(gp.GPSSError) as e:
