@@ -84,6 +84,11 @@ typedef struct {
                              1 sequential fold per series (one thread per series),
                              2 parallel scan (Section 3.2.5): each warp's 32 chunks in
                                shared memory, then a tree scan of the warp totals */
+  int step_cache;         /* gradient calls: 0 auto -- the element pass keeps every step's
+                             per-term scalars (f, f', F1, I_ff, I_pp, I_FF) in device
+                             memory for the reverse sweep while they take at most 8 GiB
+                             (24 bytes per event and term per theta set), else the sweep
+                             recomputes them; 1 always recompute */
 } gp_ss_options;
 
 /* Build a model from exposures (Section 3.2: two events per exposure, reset

@@ -52,7 +52,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("threads_per_series", ctypes.c_int), ("chunk_len", ctypes.c_int),
                 ("ckpt_interval", ctypes.c_int), ("debug_checks", ctypes.c_int),
-                ("chunk_combine", ctypes.c_int)]
+                ("chunk_combine", ctypes.c_int), ("step_cache", ctypes.c_int)]
 
 
 _lib = None
@@ -122,7 +122,8 @@ class Model:
     """
 
     def __init__(self, terms, offsets, t_start, t_end, y, yerr, instrument=None, layout=0,
-                 precision=32, schedule=0, chunk_len=0, combine=0, ckpt_interval=0):
+                 precision=32, schedule=0, chunk_len=0, combine=0, ckpt_interval=0,
+                 step_cache=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -138,7 +139,7 @@ class Model:
         inst = None if instrument is None else np.ascontiguousarray(instrument, np.int32)
         spec, self._spec_arr = _spec(self.terms, self.layout)
         opts = _Options(int(precision), int(schedule), 0, int(chunk_len), int(ckpt_interval), 0,
-                        int(combine))
+                        int(combine), int(step_cache))
         h = ctypes.c_void_p()
         self.device = torch.cuda.current_device()
         rc = lib.gp_ss_build_model(ctypes.byref(spec), len(offs) - 1, offs.ctypes.data,

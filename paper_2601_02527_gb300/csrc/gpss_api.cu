@@ -61,6 +61,8 @@ namespace {
 
 constexpr int kMaxSlots = 3;
 constexpr int kDefaultChunk = 256;
+// largest step-scalar cache a gradient call allocates (bytes)
+constexpr size_t kDcacheMax = (size_t)8 << 30;
 
 template <class T>
 struct DevBuf {
@@ -105,9 +107,14 @@ struct gp_ss_model {
   int chunk_len = 0, n_chunks = 0, max_chunk = 0, max_chunks_per_series = 0;
   int combine = 0;  // cross-chunk combination: 0 auto, 1 sequential per series, 2 tree
   int ckpt_interval = 16;  // events per recomputation segment of the gradient
+  int step_cache = 0;      // 0 auto, 1 never keep the gradient's step scalars
   int64_t *d_ch_ev0 = nullptr, *d_ch_meas0 = nullptr;
   int32_t *d_ch_len = nullptr, *d_ch_series = nullptr, *d_ch_first = nullptr;
   uint8_t *d_ch_flags = nullptr;
+  // step-scalar cache of the gradient: per warp of chunks, 32 x (its longest
+  // chunk) lane-steps; d_w_doff[w] = lane-steps before warp w, [n_w] = total
+  int64_t *d_w_doff = nullptr;
+  int64_t dcache_steps = 0;
   // device error flags of the last call
   mutable std::mutex mu;
   mutable int *d_err = nullptr;
@@ -168,7 +175,7 @@ gp_ss_status dev_upload(T **dst, const T *src, size_t n) {
 void free_model_buffers(gp_ss_model *m) {
   void *dev[] = {m->d_ev_off, m->d_meas_off, m->d_dt, m->d_tag, m->d_meas, m->d_dt64, m->d_meas64,
                  m->d_ch_ev0, m->d_ch_meas0, m->d_ch_len, m->d_ch_series, m->d_ch_first,
-                 m->d_ch_flags, m->d_err};
+                 m->d_ch_flags, m->d_w_doff, m->d_err};
   for (void *p : dev)
     if (p) cudaFree(p);
   void *hst[] = {m->h_dt, m->h_tag, m->h_meas};
@@ -330,8 +337,16 @@ gp_ss_status make_plan(gp_ss_model *m, int chunk_len) {
   }
   first[n] = (int32_t)len.size();
   if (len.size() > (size_t)INT32_MAX / 4) return GP_SS_EUNSUPPORTED;
+  // every warp of 32 chunks lies in one series (32 | chunks per series)
+  const size_t n_w = len.size() / 32;
+  std::vector<int64_t> doff(n_w + 1, 0);
+  for (size_t w = 0; w < n_w; ++w) {
+    int ml = 0;
+    for (int l = 0; l < 32; ++l) ml = std::max(ml, len[w * 32 + l]);
+    doff[w + 1] = doff[w] + 32 * (int64_t)ml;
+  }
   void *old[] = {m->d_ch_ev0, m->d_ch_meas0, m->d_ch_len, m->d_ch_series, m->d_ch_first,
-                 m->d_ch_flags};
+                 m->d_ch_flags, m->d_w_doff};
   for (void *p : old)
     if (p) cudaFree(p);
   gp_ss_status st;
@@ -341,6 +356,8 @@ gp_ss_status make_plan(gp_ss_model *m, int chunk_len) {
   if ((st = dev_upload(&m->d_ch_series, ser.data(), ser.size()))) return st;
   if ((st = dev_upload(&m->d_ch_first, first.data(), first.size()))) return st;
   if ((st = dev_upload(&m->d_ch_flags, flags.data(), flags.size()))) return st;
+  if ((st = dev_upload(&m->d_w_doff, doff.data(), doff.size()))) return st;
+  m->dcache_steps = doff[n_w];
   m->chunk_len = L;
   m->n_chunks = (int)len.size();
   m->max_chunk = max_len;
@@ -372,6 +389,8 @@ gpss::DevModel dev_view(const gp_ss_model *m) {
   d.ch_series = m->d_ch_series;
   d.ch_flags = m->d_ch_flags;
   d.ch_first = m->d_ch_first;
+  d.w_doff = m->d_w_doff;
+  d.dcache_steps = m->dcache_steps;
   return d;
 }
 
@@ -476,11 +495,22 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       res = GP_SS_ENOMEM;
       break;
     }
+    // the element pass keeps every step's scalars for the gradient's replay
+    // while that takes at most kDcacheMax bytes (else the replay recomputes them)
+    float *dcache = nullptr;
+    if (grad) {
+      const size_t dbytes = (size_t)(n_vch / m->n_chunks) * (size_t)m->dcache_steps * 6 * o.NT *
+                            sizeof(float);
+      if (m->step_cache == 0 && dbytes <= kDcacheMax && !grab((void **)&dcache, dbytes)) {
+        res = GP_SS_ENOMEM;
+        break;
+      }
+    }
     {
       PhaseTimer pt(m, st, 0);
       if (o.tables(theta, n_sets, m->n_params, m->kinds[0], m->kinds[1], tabs, st) ||
           o.elem(dm, theta, n_vch, per_series, ef, ed, m->d_err, tabs, grad ? ckpt : nullptr, ck,
-                 st)) {
+                 dcache, st)) {
         res = GP_SS_ECUDA;
         break;
       }
@@ -536,7 +566,7 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       }
       PhaseTimer pt(m, st, 2);
       if (o.grad(dm, theta, n_vch, per_series, state_end, adj, ckpt, gpart, m->d_err, tabs, rbuf,
-                 ck, st)) {
+                 dcache, ck, st)) {
         res = GP_SS_ECUDA;
         break;
       }
@@ -633,6 +663,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   if (o.threads_per_series > 1) return GP_SS_EUNSUPPORTED;
   if (o.chunk_combine < 0 || o.chunk_combine > 2) return GP_SS_EINVAL;
   if (o.ckpt_interval != 0 && o.ckpt_interval != 8 && o.ckpt_interval != 16) return GP_SS_EINVAL;
+  if (o.step_cache != 0 && o.step_cache != 1) return GP_SS_EINVAL;
   if (series_offsets[0] != 0) return GP_SS_EINVAL;
   for (int s = 0; s < n_series; ++s)
     if (series_offsets[s + 1] < series_offsets[s]) return GP_SS_EUNSORTED;
@@ -650,6 +681,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   m->schedule = o.schedule;
   m->combine = o.chunk_combine;
   m->ckpt_interval = o.ckpt_interval == 8 ? 8 : 16;
+  m->step_cache = o.step_cache;
   m->n_params = 1;
   for (int t = 0; t < spec->n_terms; ++t) {
     m->kinds[t] = spec->terms[t];
@@ -1008,7 +1040,7 @@ extern "C" gp_ss_status gp_ss_loglik_noalloc(const gp_ss_model *m, const float *
   // every field the combination reads is written by the element pass first,
   // so nothing in the shared array needs clearing between calls
   if (o.tables(theta, n_sets, m->n_params, m->kinds[0], m->kinds[1], tabs, st) != cudaSuccess ||
-      o.elem(dm, theta, n_vch, theta_per_series, ef, ed, nullptr, tabs, nullptr, 0, st) !=
+      o.elem(dm, theta, n_vch, theta_per_series, ef, ed, nullptr, tabs, nullptr, 0, nullptr, st) !=
           cudaSuccess)
     return GP_SS_ECUDA;
   if (o.scan(dm, n_out, theta_per_series, ef, ed, n_vch, nullptr, nullptr, loglik_out, 0,

@@ -546,6 +546,89 @@ GPSS_HD Disc<Dual2<float>> discretize_tab_dual(float t, const TermC<float> &c, c
 }
 
 
+// (a, beta) tangents of the six scalars given their values d (FP32).
+// Order of da, db: f, f', F1, I_ff, I_pp, I_FF.
+//
+// Table branch: Horner on the tangent columns of the table.
+GPSS_HD void disc_tab_tangents(float t, const float4 *__restrict__ tab, float (&da)[6],
+                               float (&db)[6]) {
+  {
+    const float4 *r = tab + (TAB_NC - 1) * (TAB_W / 4);
+    const float4 q2 = r[2], q3 = r[3], q4 = r[4], q5 = r[5];
+    da[0] = q2.x; da[1] = q2.y; da[2] = q2.z; da[3] = q2.w; da[4] = q3.x; da[5] = q3.y;
+    db[0] = q4.x; db[1] = q4.y; db[2] = q4.z; db[3] = q4.w; db[4] = q5.x; db[5] = q5.y;
+  }
+#pragma unroll 3
+  for (int k = TAB_NC - 2; k >= 0; --k) {
+    const float4 *r = tab + k * (TAB_W / 4);
+    const float4 q2 = r[2], q3 = r[3], q4 = r[4], q5 = r[5];
+    da[0] = fmaf(da[0], t, q2.x); da[1] = fmaf(da[1], t, q2.y); da[2] = fmaf(da[2], t, q2.z);
+    da[3] = fmaf(da[3], t, q2.w); da[4] = fmaf(da[4], t, q3.x); da[5] = fmaf(da[5], t, q3.y);
+    db[0] = fmaf(db[0], t, q4.x); db[1] = fmaf(db[1], t, q4.y); db[2] = fmaf(db[2], t, q4.z);
+    db[3] = fmaf(db[3], t, q4.w); db[4] = fmaf(db[4], t, q5.x); db[5] = fmaf(db[5], t, q5.y);
+  }
+  const float t2 = t * t, t3 = t2 * t;
+  const float sc[6] = {t, 1.f, t2, t3, t, t3 * t2};
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    da[i] *= sc[i];
+    db[i] *= sc[i];
+  }
+}
+
+// Closed-form branch: the derivatives of the closed forms written through
+// the values themselves.  With E = exp(-a t), S = sin(b t)/b, C = cos(b t):
+// E S = f and E C = f' + a f, so df/da = -t f, df'/da = -t f' - f,
+// G := df/dbeta = E dS/dbeta = (t (f' + a f) - f) / (2 beta) (series in
+// beta t^2 below 1/2, where that difference cancels), df'/dbeta = -t f/2 - a G,
+// and F1, I_pp, I_ff, I_FF follow by differentiating their identities
+// (w2 = beta + a^2, dw2/da = 2a, dw2/dbeta = 1).
+GPSS_HD void disc_closed_tangents(float t, const TermC<float> &c, const Disc<float> &d,
+                                  float (&da)[6], float (&db)[6]) {
+  const float a = c.a, w2 = c.w2, rw2 = c.rw2, r4a = c.r4a;
+  const float f = d.f, fp = d.fp, F1 = d.F1, Iff = d.Iff, Ipp = d.Ipp, IFF = d.IFF;
+  const float tf = t * f, ff = f * f;
+  // d/da
+  const float fa = -tf;
+  const float fpa = -t * fp - f;
+  const float F1a = (t * (fp + 2.f * a * f) - f - 2.f * a * F1) * rw2;
+  const float Ippa = r4a * (2.f * fp * (t * fp + f) - 2.f * a * ff + 2.f * w2 * t * ff) - 4.f * r4a * Ipp;
+  const float Iffa = (Ippa + 2.f * tf * fp + 2.f * a * t * ff - 2.f * a * Iff) * rw2;
+  const float IFFa = (Ippa + 8.f * a * Iff + 4.f * a * a * Iffa + 2.f * tf - 4.f * F1 - 4.f * a * F1a +
+                      2.f * ff - 4.f * a * t * ff) * (rw2 * rw2) - 4.f * a * IFF * rw2;
+  // d/dbeta
+  const float x = c.beta * t * t;
+  float G;
+  if (x < 0.5f)
+    G = gexp(-a * t) * t * t * t *
+        (-1.f / 6.f + x * (1.f / 60.f + x * (-1.f / 1680.f + x * (1.f / 90720.f + x * (-1.f / 7983360.f)))));
+  else
+    G = (t * (fp + a * f) - f) * (0.5f * c.rb * c.rb);
+  const float fpb = -0.5f * tf - a * G;
+  const float F1b = (0.5f * tf - a * G - F1) * rw2;
+  const float Ippb = r4a * (-2.f * fp * fpb - ff - 2.f * w2 * f * G);
+  const float Iffb = (Ippb - G * fp - f * fpb - 2.f * a * f * G - Iff) * rw2;
+  const float IFFb = (Ippb + 4.f * a * a * Iffb - 2.f * G - 4.f * a * F1b + 4.f * a * f * G) *
+                         (rw2 * rw2) - 2.f * IFF * rw2;
+  da[0] = fa; da[1] = fpa; da[2] = F1a; da[3] = Iffa; da[4] = Ippa; da[5] = IFFa;
+  db[0] = G; db[1] = fpb; db[2] = F1b; db[3] = Iffb; db[4] = Ippb; db[5] = IFFb;
+}
+
+// Tangents for a step of length t, either branch (same branch rule as
+// discretize_tab).
+GPSS_HD void disc_tangents(float t, const TermC<float> &c, const float4 *tab, const Disc<float> &d,
+                           float (&da)[6], float (&db)[6]) {
+  if (t == 0.f) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) da[i] = db[i] = 0.f;
+    return;
+  }
+  if (c.w2 * t * t <= TaylorOrder<float>::XT2)
+    disc_tab_tangents(t, tab, da, db);
+  else
+    disc_closed_tangents(t, c, d, da, db);
+}
+
 // Blocks of Phi~ and Q~ for one term (see header comment).
 template <class F>
 struct Blocks {

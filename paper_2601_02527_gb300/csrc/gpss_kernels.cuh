@@ -56,7 +56,21 @@ struct DevModel {
   const int32_t *ch_series;  // series of chunk
   const uint8_t *ch_flags;   // bit0 first chunk of its series, bit1 last
   const int32_t *ch_first;   // [n_series+1] first chunk of each series
+  // step-scalar cache layout: warp w of chunks (32 consecutive chunks, one
+  // series) owns lane-steps [w_doff[w], w_doff[w+1]) of each theta set's
+  // dcache_steps; the record of step k is 6 NT fields x 32 lanes
+  const int64_t *w_doff;
+  int64_t dcache_steps;
 };
+
+// This chunk's column of the step-scalar cache (null when there is none):
+// field j of step k at [k * 32 * 6 NT + 32 j].
+template <int NT>
+GPSS_D float *dcache_col(const DevModel &M, float *dcache, int vc) {
+  if (!dcache) return nullptr;
+  const int c = vc % M.n_chunks, set = vc / M.n_chunks;
+  return dcache + ((size_t)set * M.dcache_steps + M.w_doff[c >> 5]) * (6 * NT) + (c & 31);
+}
 
 // log of an innovation variance: computed at the filter's precision, summed in FP64
 GPSS_D double glog(float x) { return (double)logf(x); }
@@ -97,12 +111,23 @@ GPSS_D Disc<float> disc_step<float>(float dt, const TermC<float> &c, const float
 // exposure end) its measurement record; returns true for an end event, with
 // S and v of its innovation.
 template <class S, class F>
+GPSS_D bool filter_blocks(const Blocks<F> *B, uint8_t tag, F y, F r0, F w, F s2, F *m, F *P,
+                          F &Sv, F &v);
+
+template <class S, class F>
 GPSS_D bool filter_step(F dt, uint8_t tag, F y, F r0, F w, const TermC<F> *tc, F s2, F *m, F *P,
                         F &Sv, F &v, const float4 *tab) {
   Blocks<F> B[S::NT];
 #pragma unroll
   for (int t = 0; t < S::NT; ++t)
     B[t] = make_blocks(disc_step<F>(dt, tc[t], tab ? tab + t * (TAB_TERM / 4) : nullptr), tc[t]);
+  return filter_blocks<S, F>(B, tag, y, r0, w, s2, m, P, Sv, v);
+}
+
+// The filter step given the step's blocks.
+template <class S, class F>
+GPSS_D bool filter_blocks(const Blocks<F> *B, uint8_t tag, F y, F r0, F w, F s2, F *m, F *P,
+                          F &Sv, F &v) {
   F mt[S::D];
   apply_phi<S>(B, m, mt);
 #pragma unroll
@@ -308,13 +333,16 @@ GPSS_D void store_elem(float *dst, int n_vch, int vc, const float (&A)[S::D][S::
 // With pck set, the partial element of the chunk's first events is also saved
 // at the start of every gradient segment but the first (segments of ck
 // events, aligned to the chunk's end): record j at pck + j (NF + 1) n_vch,
-// fields as above plus the number of measurements before that point.
+// fields as above plus the number of measurements before that point.  With
+// dcache set, every step's six scalars per term go to the step-scalar cache
+// (for the gradient's forward replay).
 template <class S>
 __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restrict__ theta, int n_vch,
                                               int per_series, float *__restrict__ ef,
                                               double *__restrict__ ed, int *__restrict__ err,
                                               const float *__restrict__ tabs,
-                                              float *__restrict__ pck, int ck) {
+                                              float *__restrict__ pck, int ck,
+                                              float *__restrict__ dcache) {
   using F = float;
   constexpr int D = S::D;
   using L = ElemLayout<S>;
@@ -354,6 +382,7 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
   bool bad = false;
   const int64_t e0 = M.ch_ev0[c];
   const int len = M.ch_len[c];
+  float *dc = dcache_col<S::NT>(M, dcache, vc);
   EventReader rd;
   rd.start(M, e0, e0 + len, M.ch_meas0[c]);
   // gradient segments end at len - j ck (the first one is the short one);
@@ -373,8 +402,19 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
     rd.next(dt, tag, q);
     Blocks<F> B[S::NT];
 #pragma unroll
-    for (int t = 0; t < S::NT; ++t)
-      B[t] = make_blocks(discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4)), tc[t]);
+    for (int t = 0; t < S::NT; ++t) {
+      const Disc<F> d = discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4));
+      if (dc) {
+        float *r = dc + (size_t)kk * (32 * 6 * S::NT) + 32 * 6 * t;
+        r[0] = d.f;
+        r[32] = d.fp;
+        r[64] = d.F1;
+        r[96] = d.Iff;
+        r[128] = d.Ipp;
+        r[160] = d.IFF;
+      }
+      B[t] = make_blocks(d, tc[t]);
+    }
     // A <- Phi~ A (column by column), b <- Phi~ b, C <- Phi~ C Phi~^T + Q~
 #pragma unroll
     for (int col = 0; col < D; ++col) {
@@ -786,25 +826,20 @@ struct TermGrad {
   float s2;
 };
 
-// Reverse of one event.  (m, P): filtered state before the event.
-// (lam, Lam): adjoint of the filtered state after the event (full-matrix
-// gradient convention, stored packed); on return, adjoint of (m, P).
+// Reverse of one event.  (m, P): filtered state before the event; dv: the
+// step's six scalars per term.  (lam, Lam): adjoint of the filtered state
+// after the event (full-matrix gradient convention, stored packed); on
+// return, adjoint of (m, P).
 template <class S>
 GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *tc, float s2,
                           const float *m, const float *P, float *lam, float *Lam,
-                          TermGrad<S::NT> &gr, const float4 *tab) {
+                          TermGrad<S::NT> &gr, const float4 *tab, const Disc<float> *dv) {
   using F = float;
-  using DF = Dual2<float>;
   constexpr int D = S::D;
   const int j = (tag >> 1) & 7;
-  Disc<DF> dd[S::NT];
   Blocks<F> B[S::NT];
 #pragma unroll
-  for (int t = 0; t < S::NT; ++t) {
-    dd[t] = discretize_tab_dual(dt, tc[t], tab + t * (TAB_TERM / 4));
-    Disc<F> d{dd[t].f.v, dd[t].fp.v, dd[t].F1.v, dd[t].Iff.v, dd[t].Ipp.v, dd[t].IFF.v};
-    B[t] = make_blocks(d, tc[t]);
-  }
+  for (int t = 0; t < S::NT; ++t) B[t] = make_blocks(dv[t], tc[t]);
   // recompute the prediction
   F mp[D], Pp[S::NP], G[D][D];
   apply_phi<S>(B, m, mp);
@@ -894,8 +929,8 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
     const F q00 = Lam[S::pk(i0, i0)], q01 = F(2) * Lam[S::pk(i0, i1)], q11 = Lam[S::pk(i1, i1)];
     // blocks -> (f, f', F1, I_ff, I_pp, I_FF) adjoints and explicit (a, w2, Qc)
     const TermC<F> &c = tc[t];
-    const F f = dd[t].f.v, fp = dd[t].fp.v, F1 = dd[t].F1.v, Iff = dd[t].Iff.v, Ipp = dd[t].Ipp.v,
-            IFF = dd[t].IFF.v;
+    const F f = dv[t].f, fp = dv[t].fp, F1 = dv[t].F1, Iff = dv[t].Iff, Ipp = dv[t].Ipp,
+            IFF = dv[t].IFF;
     F bf = F(0), bfp = F(0), bF1 = F(0), bIff = F(0), bIpp = F(0), bIFF = F(0);
     // p00 = fp + 2a f ; p01 = f ; p10 = -w2 f ; p11 = fp
     bfp += LG[0][0] + LG[1][1];
@@ -914,11 +949,11 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
     bIFF += c.qc * q_zz;
     gr.qc[t] += Iff * q00 + F(0.5) * f * f * q01 + Ipp * q11 + F(0.5) * F1 * F1 * q_z0 +
                 (f * F1 - Iff) * q_z1 + IFF * q_zz;
-    // through the discretisation (d/da, d/dbeta by the dual tangents)
-    gr.a[t] += bf * dd[t].f.da + bfp * dd[t].fp.da + bF1 * dd[t].F1.da + bIff * dd[t].Iff.da +
-               bIpp * dd[t].Ipp.da + bIFF * dd[t].IFF.da;
-    gr.beta[t] += bf * dd[t].f.db + bfp * dd[t].fp.db + bF1 * dd[t].F1.db + bIff * dd[t].Iff.db +
-                  bIpp * dd[t].Ipp.db + bIFF * dd[t].IFF.db;
+    // through the discretisation: (a, beta) tangents of the six scalars
+    F da[6], db[6];
+    disc_tangents(dt, c, tab + t * (TAB_TERM / 4), dv[t], da, db);
+    gr.a[t] += bf * da[0] + bfp * da[1] + bF1 * da[2] + bIff * da[3] + bIpp * da[4] + bIFF * da[5];
+    gr.beta[t] += bf * db[0] + bfp * db[1] + bF1 * db[2] + bIff * db[3] + bIpp * db[4] + bIFF * db[5];
   }
   (void)zl;
   (void)zL;
@@ -1014,11 +1049,13 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
                                              const float *__restrict__ pck, float *__restrict__ gpart,
                                              int *__restrict__ err,
                                              const float *__restrict__ tabs,
-                                             float *__restrict__ rbuf) {
+                                             float *__restrict__ rbuf,
+                                             const float *__restrict__ dcache) {
   using F = float;
   constexpr int D = S::D;
   constexpr int SD = D + S::NP;
   constexpr int NF = ElemLayout<S>::NF;
+  constexpr int NDC = 6 * S::NT;  // cached scalars per step
   extern __shared__ float sm[];
   const int vc = blockIdx.x * blockDim.x + threadIdx.x;
   if (vc >= n_vch) return;
@@ -1056,6 +1093,7 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   const int64_t m0 = M.ch_meas0[c];
   float *my = rbuf + vc;
   const size_t rs = (size_t)n_vch;
+  const float *dc = dcache_col<S::NT>(M, const_cast<float *>(dcache), vc);
   bool bad = false;
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int k0 = seg == 0 ? 0 : f0 + (seg - 1) * CK;
@@ -1081,9 +1119,16 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       apply_partial<S>(src, n_vch, vc, mi, Pi, m, P);
       mrel = __float_as_int(src[(size_t)NF * n_vch + vc]);
     }
-    // forward replay of the segment
+    // forward replay of the segment (step scalars from the cache, the next
+    // step's loaded one ahead, or recomputed)
     EventReader rd;
     rd.start(M, e0 + k0, e0 + k1, m0 + mrel);
+    const float *dcr = dc ? dc + (size_t)k0 * (32 * NDC) : nullptr;
+    float nx[NDC];
+    if (dcr) {
+#pragma unroll
+      for (int j = 0; j < NDC; ++j) nx[j] = __ldg(dcr + 32 * j);
+    }
     for (int kk = k0; kk < k1; ++kk) {
       const int slot = kk - k0;
 #pragma unroll
@@ -1095,30 +1140,67 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       uint8_t tag;
       float4 q;
       rd.next(dt, tag, q);
-      if (filter_step<S, F>(dt, tag, q.x, q.y, q.z, tc, s2, m, P, Sv, vv, tab))
-        bad |= !(Sv > F(0));
+      Blocks<F> B[S::NT];
+      if (dcr) {
+#pragma unroll
+        for (int t = 0; t < S::NT; ++t) {
+          const Disc<F> d{nx[6 * t], nx[6 * t + 1], nx[6 * t + 2],
+                          nx[6 * t + 3], nx[6 * t + 4], nx[6 * t + 5]};
+          B[t] = make_blocks(d, tc[t]);
+        }
+        dcr += 32 * NDC;
+        if (kk + 1 < k1) {
+#pragma unroll
+          for (int j = 0; j < NDC; ++j) nx[j] = __ldg(dcr + 32 * j);
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < S::NT; ++t)
+          B[t] = make_blocks(discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4)), tc[t]);
+      }
+      if (filter_blocks<S, F>(B, tag, q.x, q.y, q.z, s2, m, P, Sv, vv)) bad |= !(Sv > F(0));
     }
-    // backward walk; the next (earlier) event's data are loaded while the
-    // current one is processed
+    // backward walk; the next (earlier) event's data (and cached scalars)
+    // are loaded while the current one is processed
     int k2 = k1 - 1;
     F dt_n = __ldg(M.dt + e0 + k2);
     uint8_t tag_n = __ldg(M.tag + e0 + k2);
     float4 q_n = __ldg(M.meas + m0 + __float_as_int(my[((k2 - k0) * (SD + 1) + SD) * rs]));
+    const float *dcb = dc ? dc + (size_t)k2 * (32 * NDC) : nullptr;
+    if (dcb) {
+#pragma unroll
+      for (int j = 0; j < NDC; ++j) nx[j] = __ldg(dcb + 32 * j);
+    }
     for (; k2 >= k0; --k2) {
       const int slot = k2 - k0;
       const F dt = dt_n;
       const uint8_t tag = tag_n;
       const float4 q = q_n;
+      Disc<F> dv[S::NT];
+      if (dcb) {
+#pragma unroll
+        for (int t = 0; t < S::NT; ++t)
+          dv[t] = Disc<F>{nx[6 * t], nx[6 * t + 1], nx[6 * t + 2], nx[6 * t + 3], nx[6 * t + 4],
+                          nx[6 * t + 5]};
+      } else {
+#pragma unroll
+        for (int t = 0; t < S::NT; ++t) dv[t] = discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4));
+      }
       if (k2 > k0) {
         dt_n = __ldg(M.dt + e0 + k2 - 1);
         tag_n = __ldg(M.tag + e0 + k2 - 1);
         q_n = __ldg(M.meas + m0 + __float_as_int(my[((slot - 1) * (SD + 1) + SD) * rs]));
+        if (dcb) {
+          dcb -= 32 * NDC;
+#pragma unroll
+          for (int j = 0; j < NDC; ++j) nx[j] = __ldg(dcb + 32 * j);
+        }
       }
 #pragma unroll
       for (int i = 0; i < D; ++i) m[i] = my[(slot * (SD + 1) + i) * rs];
 #pragma unroll
       for (int i = 0; i < S::NP; ++i) P[i] = my[(slot * (SD + 1) + D + i) * rs];
-      reverse_event<S>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab);
+      reverse_event<S>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab, dv);
     }
   }
   if (first) {
@@ -1216,11 +1298,12 @@ struct OpTable {
   cudaError_t (*plain32)(const DevModel &, const float *, int, int, double *, int *, cudaStream_t);
   cudaError_t (*plain64)(const DevModel &, const float *, int, int, double *, int *, cudaStream_t);
   cudaError_t (*elem)(const DevModel &, const float *, int, int, float *, double *, int *,
-                      const float *, float *, int, cudaStream_t);
+                      const float *, float *, int, float *, cudaStream_t);
   cudaError_t (*scan)(const DevModel &, int, int, const float *, const double *, int, float *,
                       float *, double *, int, int *, cudaStream_t);
   cudaError_t (*grad)(const DevModel &, const float *, int, int, const float *, const float *,
-                      const float *, float *, int *, const float *, float *, int, cudaStream_t);
+                      const float *, float *, int *, const float *, float *, const float *, int,
+                      cudaStream_t);
   cudaError_t (*tables)(const float *, int, int, int, int, float *, cudaStream_t);
   cudaError_t (*warp_combine)(const DevModel &, const float *, int, float *, float *, float *,
                               float *, float *, float *, float *, float *, int, int, int, int,
@@ -1250,13 +1333,13 @@ cudaError_t launch_plain(const DevModel &M, const float *theta, int n_out, int p
 template <class S>
 cudaError_t launch_elem(const DevModel &M, const float *theta, int n_vch, int per_series,
                         float *ef, double *ed, int *err, const float *tabs, float *pck, int ck,
-                        cudaStream_t st) {
+                        float *dcache, cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
   if (pck && (ck != 8 && ck != 16)) return cudaErrorInvalidValue;
   const int bs = 128;
   const size_t smem = (size_t)(bs / 32) * S::NT * TAB_TERM * sizeof(float);
   k_elem<S><<<(n_vch + bs - 1) / bs, bs, smem, st>>>(M, theta, n_vch, per_series, ef, ed, err,
-                                                    tabs, pck, pck ? ck : 1);
+                                                    tabs, pck, pck ? ck : 1, dcache);
   return cudaGetLastError();
 }
 
@@ -1360,28 +1443,30 @@ cudaError_t launch_finish(const DevModel &M, int n_vch, int per_series, const fl
 template <class S, int CK>
 cudaError_t launch_grad_ck(const DevModel &M, const float *theta, int n_vch, int per_series,
                            const float *state_end, const float *adj_end, const float *pck,
-                           float *gpart, int *err, const float *tabs, float *rbuf, cudaStream_t st) {
+                           float *gpart, int *err, const float *tabs, float *rbuf,
+                           const float *dcache, cudaStream_t st) {
   const size_t smem = (size_t)(GRAD_BS / 32) * S::NT * TAB_TERM * sizeof(float);
   k_grad<S, CK><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
-      M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err, tabs, rbuf);
+      M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err, tabs, rbuf, dcache);
   return cudaGetLastError();
 }
 
 // ck: events per recomputation segment (8 or 16), the value k_elem saved the
 // partial elements pck with ([(max_len-1)/ck] * (NF+1) * n_vch floats).
-// Scratch: rbuf [ck * (SD+1) * n_vch] floats.
+// Scratch: rbuf [ck * (SD+1) * n_vch] floats.  dcache: the step-scalar cache
+// k_elem filled, or null (the replay then recomputes the scalars).
 template <class S>
 cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int per_series,
                         const float *state_end, const float *adj_end, const float *pck,
-                        float *gpart, int *err, const float *tabs, float *rbuf, int ck,
-                        cudaStream_t st) {
+                        float *gpart, int *err, const float *tabs, float *rbuf,
+                        const float *dcache, int ck, cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
   if (ck == 8)
     return launch_grad_ck<S, 8>(M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err,
-                                tabs, rbuf, st);
+                                tabs, rbuf, dcache, st);
   if (ck == 16)
     return launch_grad_ck<S, 16>(M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err,
-                                 tabs, rbuf, st);
+                                 tabs, rbuf, dcache, st);
   return cudaErrorInvalidValue;
 }
 

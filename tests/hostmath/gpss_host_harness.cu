@@ -111,6 +111,24 @@ void hh_discretize_dual(double t, double a, double beta, double *out18) {
   }
 }
 
+// out18 = values (table path, FP32) and their (a, beta) tangents from the
+// values (disc_tangents: table columns or the closed-form identities)
+void hh_discretize_tangents(double t, double a, double beta, double *out18) {
+  float tab[TAB_TERM];
+  build_table((float)a, (float)beta, tab);
+  const TermC<float> c = termc((float)a, (float)beta);
+  const float4 *tb = reinterpret_cast<const float4 *>(tab);
+  const Disc<float> d = discretize_tab((float)t, c, tb);
+  float da[6], db[6];
+  disc_tangents((float)t, c, tb, d, da, db);
+  const float v[6] = {d.f, d.fp, d.F1, d.Iff, d.Ipp, d.IFF};
+  for (int i = 0; i < 6; ++i) {
+    out18[i] = v[i];
+    out18[6 + i] = da[i];
+    out18[12 + i] = db[i];
+  }
+}
+
 // Economised table polynomials (FP64) against the TAB_NTAY-term Taylor
 // series they replace, on 401 points of the table's range [0, T]: the worst
 // error of any of the 18 series (6 values, d/da, d/dbeta) relative to that

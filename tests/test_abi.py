@@ -40,7 +40,7 @@ def test_status_strings(lib):
     assert lib.gp_ss_status_string(7).decode().startswith("non-positive")
 
 
-def _build(lib, t_start, t_end, inst=None, offsets=None, terms=(1,), layout=0):
+def _build(lib, t_start, t_end, inst=None, offsets=None, terms=(1,), layout=0, opts=None):
     n = len(t_start)
     offs = np.asarray(offsets if offsets is not None else [0, n], np.int64)
     ts = np.ascontiguousarray(t_start, np.float64)
@@ -48,7 +48,7 @@ def _build(lib, t_start, t_end, inst=None, offsets=None, terms=(1,), layout=0):
     y = np.zeros(n, np.float32)
     ye = np.zeros(n, np.float32)
     spec, keep = gp._spec(terms, layout)
-    opts = gp._Options(32, 0, 0, 0, 0, 0, 0)
+    opts = opts if opts is not None else gp._Options(32, 0, 0, 0, 0, 0, 0, 0)
     h = ctypes.c_void_p()
     ii = None if inst is None else np.ascontiguousarray(inst, np.int32)
     rc = lib.gp_ss_build_model(ctypes.byref(spec), len(offs) - 1, offs.ctypes.data,
@@ -71,3 +71,7 @@ def test_host_validation_without_gpu(lib):
     assert _build(lib, [0.0, 0.1, 0.2, 0.3], [5.0, 5.0, 5.0, 5.0]) == 4
     # more than two terms
     assert _build(lib, [0.0], [1.0], terms=(1, 1, 1)) == 4
+    # option values outside their ranges
+    for bad in (gp._Options(32, 0, 0, 0, 12, 0, 0, 0), gp._Options(32, 0, 0, 0, 0, 0, 0, 2),
+                gp._Options(16, 0, 0, 0, 0, 0, 0, 0)):
+        assert _build(lib, [0.0], [1.0], opts=bad) == 1

@@ -132,6 +132,23 @@ def test_fp32_grad_layout1(gp, chunk, combine):
     np.testing.assert_allclose(ll.cpu().numpy(), ll2, rtol=1e-12)
 
 
+@pytest.mark.parametrize("ck", [8, 16])
+def test_step_cache_off_matches(gp, ck):
+    # the reverse sweep recomputing the step scalars gives the gradient of
+    # the cached path (same FP32 arithmetic up to contraction) and the oracle's
+    wl = f32_theta(synth.c4(n_series=6, scale=0.05))
+    th = theta_dev(wl)
+    on = gp.Model.from_workload(wl, chunk_len=48, ckpt_interval=ck)
+    off = gp.Model.from_workload(wl, chunk_len=48, ckpt_interval=ck, step_cache=1)
+    ll_a, g_a = on.loglik_grad(th)
+    ll_b, g_b = off.loglik_grad(th)
+    np.testing.assert_array_equal(ll_a.cpu().numpy(), ll_b.cpu().numpy())
+    g_a, g_b = g_a.cpu().numpy(), g_b.cpu().numpy()
+    assert np.all(np.abs(g_a - g_b) <= 1e-5 * np.abs(g_a) + 1e-6 * np.abs(g_a).max())
+    _, ref_g = oracle_ll(wl, grad=True)
+    check_grad(g_b, ref_g)
+
+
 @pytest.mark.parametrize("chunk", [4, 8, 40, 300])
 def test_overlapping_three_slots(gp, chunk):
     rng = np.random.default_rng(77)

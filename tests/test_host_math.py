@@ -44,6 +44,7 @@ def hh():
     d, f = ctypes.c_double, ctypes.c_float
     lib.hh_discretize.argtypes = [ctypes.c_int, d, d, d, P(d)]
     lib.hh_discretize_dual.argtypes = [d, d, d, P(d)]
+    lib.hh_discretize_tangents.argtypes = [d, d, d, P(d)]
     lib.hh_solve.argtypes = [ctypes.c_int, P(f), P(f), P(f), ctypes.c_int]
     lib.hh_solve.restype = f
     lib.hh_dim.argtypes = [ctypes.c_int]
@@ -90,13 +91,16 @@ def test_step_scalars_match_oracle(oracle_lib, hh, w0, q):
             assert not bad.any(), (mode, t, w0 * t, out, ref)
 
 
-@pytest.mark.parametrize("w0,q", [(2 * math.pi / 10, 3.0), (2.0, 0.55), (1.0, 9.5)])
-def test_step_scalar_derivatives(oracle_lib, hh, w0, q):
+@pytest.mark.parametrize("path", ["dual", "tangents"])
+@pytest.mark.parametrize("w0,q", [(2 * math.pi / 10, 3.0), (2.0, 0.55), (1.0, 9.5),
+                                  (0.7, 0.52), (5.0, 30.0)])
+def test_step_scalar_derivatives(oracle_lib, hh, w0, q, path):
     a, beta = ab(w0, q)
     out = np.zeros(18)
-    for x in (0.01, 0.3, 0.9, 1.1, 1.3, 2.5, 8.0):
+    fn = hh.hh_discretize_dual if path == "dual" else hh.hh_discretize_tangents
+    for x in (0.01, 0.3, 0.9, 1.1, 1.3, 2.5, 8.0, 30.0):
         t = x / w0
-        hh.hh_discretize_dual(t, a, beta, _p(out, ctypes.c_double))
+        fn(t, a, beta, _p(out, ctypes.c_double))
         da, db = out[6:12], out[12:18]
         # chain (a, beta) -> (omega0, Q) and compare with oracle central differences
         g_w0 = da / (2 * q) + db * 2 * w0 * (1 - 1 / (4 * q * q))
