@@ -214,6 +214,13 @@ gp_ss_status gp_ss_last_error_series(const gp_ss_model *model, int64_t *first_ba
 gp_ss_status gp_ss_set_timing(gp_ss_model *model, int enable);
 gp_ss_status gp_ss_get_timing(gp_ss_model *model, double *ms, int64_t *launches);
 
+/* Kernels this library has launched in the calling process, all models and
+ * devices together (no counterpart in the paper; an accounting aid).  Counted
+ * on the host at every launch, so kernels replayed from a captured CUDA graph
+ * (the _batched calls after their first capture) are not included.
+ *   out  host int64, written.  GP_SS_EINVAL if NULL. */
+gp_ss_status gp_ss_launch_count(int64_t *out);
+
 void gp_ss_free_model(gp_ss_model *model);
 const char *gp_ss_status_string(gp_ss_status status);
 

@@ -32,7 +32,7 @@ EXPORTS = ["gp_ss_build_model", "gp_ss_loglik", "gp_ss_loglik_grad", "gp_ss_logl
            "gp_ss_loglik_grad_batched", "gp_ss_loglik_grad_host", "gp_ss_model_info",
            "gp_ss_set_chunk_len", "gp_ss_last_error_series", "gp_ss_free_model",
            "gp_ss_status_string", "gp_ss_discretize", "gp_ss_set_timing", "gp_ss_get_timing",
-           "gp_ss_loglik_noalloc"]
+           "gp_ss_loglik_noalloc", "gp_ss_launch_count"]
 
 PHASES = ["elem", "scan", "grad", "convert", "plain"]
 
@@ -82,6 +82,7 @@ def load_library(path: str | None = None):
     lib.gp_ss_last_error_series.argtypes = [vp, P(i64), P(i32)]
     lib.gp_ss_free_model.argtypes = [vp]
     lib.gp_ss_free_model.restype = None
+    lib.gp_ss_launch_count.argtypes = [P(i64)]
     lib.gp_ss_status_string.argtypes = [i32]
     lib.gp_ss_status_string.restype = ctypes.c_char_p
     lib.gp_ss_discretize.argtypes = [P(_KernelSpec), i32, vp, vp, i32, vp, vp, vp]
@@ -271,6 +272,15 @@ class Model:
         _check(self._lib.gp_ss_last_error_series(self._h, ctypes.byref(row), ctypes.byref(code)),
                "gp_ss_last_error_series")
         return row.value, code.value
+
+
+def launch_count() -> int:
+    """Kernels the library has launched in this process (host-side count;
+    graph replays excluded)."""
+    lib = load_library()
+    out = ctypes.c_int64()
+    _check(lib.gp_ss_launch_count(ctypes.byref(out)), "gp_ss_launch_count")
+    return int(out.value)
 
 
 def discretize(terms, layout, n_slots, theta_row, dt, stream=None):

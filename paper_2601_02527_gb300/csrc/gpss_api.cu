@@ -499,8 +499,8 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
     // while that takes at most kDcacheMax bytes (else the replay recomputes them)
     float *dcache = nullptr;
     if (grad) {
-      const size_t dbytes = (size_t)(n_vch / m->n_chunks) * (size_t)m->dcache_steps * 6 * o.NT *
-                            sizeof(float);
+      const size_t dbytes = (size_t)(n_vch / m->n_chunks) * (size_t)m->dcache_steps *
+                            (4 * ((6 * o.NT + 3) / 4)) * sizeof(float);
       if (m->step_cache == 0 && dbytes <= kDcacheMax && !grab((void **)&dcache, dbytes)) {
         res = GP_SS_ENOMEM;
         break;
@@ -559,7 +559,7 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
     }
     if (grad) {
       float *rbuf = nullptr;
-      if (!grab((void **)&rbuf, (size_t)ck * (SD + 1) * n_vch * sizeof(float)) ||
+      if (!grab((void **)&rbuf, (size_t)ck * (4 * ((SD + 3) / 4)) * n_vch * sizeof(float)) ||
           !grab((void **)&gpart, (size_t)m->n_params * n_vch * sizeof(float))) {
         res = GP_SS_ENOMEM;
         break;
@@ -576,6 +576,7 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       gpss::k_series_sum<<<(n_out * 32 + 127) / 128, 128, 0, st>>>(
           n_out, per_series, m->n_series, m->n_chunks, m->d_ch_first, tree ? ll_part : nullptr,
           n_vch, grad ? gpart : nullptr, m->n_params, ll, grad);
+      GPSS_COUNT_LAUNCH();
       if (cudaGetLastError() != cudaSuccess) res = GP_SS_ECUDA;
     }
   } while (0);
@@ -922,6 +923,12 @@ gp_ss_status gp_ss_last_error_series(const gp_ss_model *m, int64_t *first_bad_se
       *code = (gp_ss_status)h[i];
       break;
     }
+  return GP_SS_OK;
+}
+
+gp_ss_status gp_ss_launch_count(int64_t *out) {
+  if (!out) return GP_SS_EINVAL;
+  *out = (int64_t)gpss::g_launches.load(std::memory_order_relaxed);
   return GP_SS_OK;
 }
 

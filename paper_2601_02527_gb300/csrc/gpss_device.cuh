@@ -34,12 +34,19 @@
 
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <atomic>
 #include <stdint.h>
 
 #define GPSS_HD __host__ __device__ __forceinline__
 #define GPSS_D __device__ __forceinline__
 
 namespace gpss {
+
+// Kernels launched by this library in the process (counted on the host at
+// each launch; launches replayed from a captured CUDA graph are not counted).
+inline std::atomic<long long> g_launches{0};
+#define GPSS_COUNT_LAUNCH() (::gpss::g_launches.fetch_add(1, std::memory_order_relaxed))
 
 // ---------------------------------------------------------------------------
 // Compile-time shape of the augmented state.

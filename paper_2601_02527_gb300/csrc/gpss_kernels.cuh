@@ -58,18 +58,45 @@ struct DevModel {
   const int32_t *ch_first;   // [n_series+1] first chunk of each series
   // step-scalar cache layout: warp w of chunks (32 consecutive chunks, one
   // series) owns lane-steps [w_doff[w], w_doff[w+1]) of each theta set's
-  // dcache_steps; the record of step k is 6 NT fields x 32 lanes
+  // dcache_steps; the record of step k is DcW<NT>::G float4 groups x 32 lanes
   const int64_t *w_doff;
   int64_t dcache_steps;
 };
 
-// This chunk's column of the step-scalar cache (null when there is none):
-// field j of step k at [k * 32 * 6 NT + 32 j].
+// Step-scalar cache record: the 6 NT scalars of a step (term-major, in Disc
+// order) padded to whole float4 groups, one float4 per lane per group.
 template <int NT>
-GPSS_D float *dcache_col(const DevModel &M, float *dcache, int vc) {
+struct DcW {
+  static constexpr int G = (6 * NT + 3) / 4;
+  static constexpr int W = 4 * G;
+};
+
+// This chunk's column of the step-scalar cache (null when there is none):
+// group v of step k at [k * 32 G + 32 v] (float4 units).
+template <int NT>
+GPSS_D float4 *dcache_col(const DevModel &M, float *dcache, int vc) {
   if (!dcache) return nullptr;
   const int c = vc % M.n_chunks, set = vc / M.n_chunks;
-  return dcache + ((size_t)set * M.dcache_steps + M.w_doff[c >> 5]) * (6 * NT) + (c & 31);
+  return reinterpret_cast<float4 *>(dcache) +
+         ((size_t)set * M.dcache_steps + M.w_doff[c >> 5]) * DcW<NT>::G + (c & 31);
+}
+
+// Load / store one step's cached scalars (W floats) for this lane.
+template <int NT>
+GPSS_D void dcache_load(const float4 *rec, float (&x)[DcW<NT>::W]) {
+#pragma unroll
+  for (int v = 0; v < DcW<NT>::G; ++v) {
+    const float4 q = __ldg(rec + 32 * v);
+    x[4 * v] = q.x;
+    x[4 * v + 1] = q.y;
+    x[4 * v + 2] = q.z;
+    x[4 * v + 3] = q.w;
+  }
+}
+
+template <int NT>
+GPSS_D Disc<float> dcache_term(const float (&x)[DcW<NT>::W], int t) {
+  return Disc<float>{x[6 * t], x[6 * t + 1], x[6 * t + 2], x[6 * t + 3], x[6 * t + 4], x[6 * t + 5]};
 }
 
 // log of an innovation variance: computed at the filter's precision, summed in FP64
@@ -382,7 +409,7 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
   bool bad = false;
   const int64_t e0 = M.ch_ev0[c];
   const int len = M.ch_len[c];
-  float *dc = dcache_col<S::NT>(M, dcache, vc);
+  float4 *dc = dcache_col<S::NT>(M, dcache, vc);
   EventReader rd;
   rd.start(M, e0, e0 + len, M.ch_meas0[c]);
   // gradient segments end at len - j ck (the first one is the short one);
@@ -401,19 +428,28 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
     float4 q;
     rd.next(dt, tag, q);
     Blocks<F> B[S::NT];
+    {
+      constexpr int W = DcW<S::NT>::W;
+      float x[W];
 #pragma unroll
-    for (int t = 0; t < S::NT; ++t) {
-      const Disc<F> d = discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4));
-      if (dc) {
-        float *r = dc + (size_t)kk * (32 * 6 * S::NT) + 32 * 6 * t;
-        r[0] = d.f;
-        r[32] = d.fp;
-        r[64] = d.F1;
-        r[96] = d.Iff;
-        r[128] = d.Ipp;
-        r[160] = d.IFF;
+      for (int t = 0; t < S::NT; ++t) {
+        const Disc<F> d = discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4));
+        x[6 * t] = d.f;
+        x[6 * t + 1] = d.fp;
+        x[6 * t + 2] = d.F1;
+        x[6 * t + 3] = d.Iff;
+        x[6 * t + 4] = d.Ipp;
+        x[6 * t + 5] = d.IFF;
+        B[t] = make_blocks(d, tc[t]);
       }
-      B[t] = make_blocks(d, tc[t]);
+#pragma unroll
+      for (int i = 6 * S::NT; i < W; ++i) x[i] = 0.f;
+      if (dc) {
+        float4 *r = dc + (size_t)kk * (32 * DcW<S::NT>::G);
+#pragma unroll
+        for (int v = 0; v < DcW<S::NT>::G; ++v)
+          r[32 * v] = make_float4(x[4 * v], x[4 * v + 1], x[4 * v + 2], x[4 * v + 3]);
+      }
     }
     // A <- Phi~ A (column by column), b <- Phi~ b, C <- Phi~ C Phi~^T + Q~
 #pragma unroll
@@ -1040,8 +1076,8 @@ GPSS_HD void apply_partial(const float *src, int n_vch, int vc, const float *m_i
 // shorter).  Walking the segments from last to first: the filtered state at
 // the segment's start comes from the partial element saved there by k_elem,
 // the segment is replayed forward into this thread's column of rbuf (global,
-// coalesced across the warp, written and read back within one segment so it
-// stays in L2), then walked backwards in time.
+// coalesced across the warp; slot k holds (m, P) before the segment's k-th
+// event), then walked backwards in time.
 template <class S, int CK>
 __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restrict__ theta, int n_vch,
                                              int per_series, const float *__restrict__ state_end,
@@ -1055,7 +1091,9 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   constexpr int D = S::D;
   constexpr int SD = D + S::NP;
   constexpr int NF = ElemLayout<S>::NF;
-  constexpr int NDC = 6 * S::NT;  // cached scalars per step
+  constexpr int NDC = DcW<S::NT>::W;  // cached scalars per step (padded)
+  constexpr int NDG = DcW<S::NT>::G;  // ... in float4 groups
+  constexpr int SG = (SD + 3) / 4;    // replay slot: (m, P) in float4 groups
   extern __shared__ float sm[];
   const int vc = blockIdx.x * blockDim.x + threadIdx.x;
   if (vc >= n_vch) return;
@@ -1067,7 +1105,7 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   TermC<F> tc[S::NT];
   F s2;
   load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tc, s2);
-  // shared memory holds the warps' Taylor tables
+  // shared memory holds the warps' tables
   float4 *tab_slots = reinterpret_cast<float4 *>(sm);
   const float4 *tab = stage_table<S::NT>(tabs, row, tab_slots + (threadIdx.x >> 5) * (S::NT * TAB_TERM / 4));
   const uint8_t flags = M.ch_flags[c];
@@ -1091,9 +1129,9 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   for (int t = 0; t < S::NT; ++t) gr.a[t] = gr.beta[t] = gr.w2[t] = gr.qc[t] = gr.var[t] = F(0);
   gr.s2 = F(0);
   const int64_t m0 = M.ch_meas0[c];
-  float *my = rbuf + vc;
+  float4 *my = reinterpret_cast<float4 *>(rbuf) + vc;  // group v of slot k at (k SG + v) n_vch
   const size_t rs = (size_t)n_vch;
-  const float *dc = dcache_col<S::NT>(M, const_cast<float *>(dcache), vc);
+  const float4 *dc = dcache_col<S::NT>(M, const_cast<float *>(dcache), vc);
   bool bad = false;
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int k0 = seg == 0 ? 0 : f0 + (seg - 1) * CK;
@@ -1123,19 +1161,23 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
     // step's loaded one ahead, or recomputed)
     EventReader rd;
     rd.start(M, e0 + k0, e0 + k1, m0 + mrel);
-    const float *dcr = dc ? dc + (size_t)k0 * (32 * NDC) : nullptr;
+    const float4 *dcr = dc ? dc + (size_t)k0 * (32 * NDG) : nullptr;
     float nx[NDC];
-    if (dcr) {
-#pragma unroll
-      for (int j = 0; j < NDC; ++j) nx[j] = __ldg(dcr + 32 * j);
-    }
+    if (dcr) dcache_load<S::NT>(dcr, nx);
     for (int kk = k0; kk < k1; ++kk) {
       const int slot = kk - k0;
+      {
+        float r[4 * SG];
 #pragma unroll
-      for (int i = 0; i < D; ++i) my[(slot * (SD + 1) + i) * rs] = m[i];
+        for (int i = 0; i < D; ++i) r[i] = m[i];
 #pragma unroll
-      for (int i = 0; i < S::NP; ++i) my[(slot * (SD + 1) + D + i) * rs] = P[i];
-      my[(slot * (SD + 1) + SD) * rs] = __int_as_float((int)(rd.mi - m0));
+        for (int i = 0; i < S::NP; ++i) r[D + i] = P[i];
+#pragma unroll
+        for (int i = SD; i < 4 * SG; ++i) r[i] = 0.f;
+#pragma unroll
+        for (int v = 0; v < SG; ++v)
+          my[(size_t)(slot * SG + v) * rs] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+      }
       F dt, Sv, vv;
       uint8_t tag;
       float4 q;
@@ -1143,16 +1185,9 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       Blocks<F> B[S::NT];
       if (dcr) {
 #pragma unroll
-        for (int t = 0; t < S::NT; ++t) {
-          const Disc<F> d{nx[6 * t], nx[6 * t + 1], nx[6 * t + 2],
-                          nx[6 * t + 3], nx[6 * t + 4], nx[6 * t + 5]};
-          B[t] = make_blocks(d, tc[t]);
-        }
-        dcr += 32 * NDC;
-        if (kk + 1 < k1) {
-#pragma unroll
-          for (int j = 0; j < NDC; ++j) nx[j] = __ldg(dcr + 32 * j);
-        }
+        for (int t = 0; t < S::NT; ++t) B[t] = make_blocks(dcache_term<S::NT>(nx, t), tc[t]);
+        dcr += 32 * NDG;
+        if (kk + 1 < k1) dcache_load<S::NT>(dcr, nx);
       } else {
 #pragma unroll
         for (int t = 0; t < S::NT; ++t)
@@ -1160,17 +1195,17 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       }
       if (filter_blocks<S, F>(B, tag, q.x, q.y, q.z, s2, m, P, Sv, vv)) bad |= !(Sv > F(0));
     }
-    // backward walk; the next (earlier) event's data (and cached scalars)
-    // are loaded while the current one is processed
+    // backward walk; the earlier step's gap, tag, measurement record and
+    // cached scalars are loaded while the current step is processed.  The
+    // measurement index of event k (relative to m0) is the count of end
+    // events before k, tracked downwards from the replay's end.
     int k2 = k1 - 1;
     F dt_n = __ldg(M.dt + e0 + k2);
     uint8_t tag_n = __ldg(M.tag + e0 + k2);
-    float4 q_n = __ldg(M.meas + m0 + __float_as_int(my[((k2 - k0) * (SD + 1) + SD) * rs]));
-    const float *dcb = dc ? dc + (size_t)k2 * (32 * NDC) : nullptr;
-    if (dcb) {
-#pragma unroll
-      for (int j = 0; j < NDC; ++j) nx[j] = __ldg(dcb + 32 * j);
-    }
+    int mr = (int)(rd.mi - m0) - (tag_n & 1);
+    float4 q_n = __ldg(M.meas + m0 + mr);
+    const float4 *dcb = dc ? dc + (size_t)k2 * (32 * NDG) : nullptr;
+    if (dcb) dcache_load<S::NT>(dcb, nx);
     for (; k2 >= k0; --k2) {
       const int slot = k2 - k0;
       const F dt = dt_n;
@@ -1179,9 +1214,7 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       Disc<F> dv[S::NT];
       if (dcb) {
 #pragma unroll
-        for (int t = 0; t < S::NT; ++t)
-          dv[t] = Disc<F>{nx[6 * t], nx[6 * t + 1], nx[6 * t + 2], nx[6 * t + 3], nx[6 * t + 4],
-                          nx[6 * t + 5]};
+        for (int t = 0; t < S::NT; ++t) dv[t] = dcache_term<S::NT>(nx, t);
       } else {
 #pragma unroll
         for (int t = 0; t < S::NT; ++t) dv[t] = discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4));
@@ -1189,17 +1222,28 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       if (k2 > k0) {
         dt_n = __ldg(M.dt + e0 + k2 - 1);
         tag_n = __ldg(M.tag + e0 + k2 - 1);
-        q_n = __ldg(M.meas + m0 + __float_as_int(my[((slot - 1) * (SD + 1) + SD) * rs]));
+        mr -= tag_n & 1;
+        q_n = __ldg(M.meas + m0 + mr);
         if (dcb) {
-          dcb -= 32 * NDC;
-#pragma unroll
-          for (int j = 0; j < NDC; ++j) nx[j] = __ldg(dcb + 32 * j);
+          dcb -= 32 * NDG;
+          dcache_load<S::NT>(dcb, nx);
         }
       }
+      {
+        float r[4 * SG];
 #pragma unroll
-      for (int i = 0; i < D; ++i) m[i] = my[(slot * (SD + 1) + i) * rs];
+        for (int v = 0; v < SG; ++v) {
+          const float4 g4 = my[(size_t)(slot * SG + v) * rs];
+          r[4 * v] = g4.x;
+          r[4 * v + 1] = g4.y;
+          r[4 * v + 2] = g4.z;
+          r[4 * v + 3] = g4.w;
+        }
 #pragma unroll
-      for (int i = 0; i < S::NP; ++i) P[i] = my[(slot * (SD + 1) + D + i) * rs];
+        for (int i = 0; i < D; ++i) m[i] = r[i];
+#pragma unroll
+        for (int i = 0; i < S::NP; ++i) P[i] = r[D + i];
+      }
       reverse_event<S>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab, dv);
     }
   }
@@ -1327,6 +1371,7 @@ cudaError_t launch_plain(const DevModel &M, const float *theta, int n_out, int p
   if (n_out <= 0) return cudaSuccess;
   const int bs = 128;
   k_plain<S, F><<<(n_out + bs - 1) / bs, bs, 0, st>>>(M, theta, n_out, per_series, ll, err);
+  GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -1340,6 +1385,7 @@ cudaError_t launch_elem(const DevModel &M, const float *theta, int n_vch, int pe
   const size_t smem = (size_t)(bs / 32) * S::NT * TAB_TERM * sizeof(float);
   k_elem<S><<<(n_vch + bs - 1) / bs, bs, smem, st>>>(M, theta, n_vch, per_series, ef, ed, err,
                                                     tabs, pck, pck ? ck : 1, dcache);
+  GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -1355,6 +1401,7 @@ cudaError_t launch_tables(const float *theta, int n_rows, int n_params, int k0, 
   }();
   k_tables<S::NT><<<(n + TABLE_WARPS - 1) / TABLE_WARPS, 32 * TABLE_WARPS, 0, st>>>(
       theta, n_rows, n_params, k0, k1, tab, E);
+  GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -1366,6 +1413,7 @@ cudaError_t launch_scan(const DevModel &M, int n_out, int per_series, const floa
   const int bs = 64;
   k_scan_seq<S><<<(n_out + bs - 1) / bs, bs, 0, st>>>(M, n_out, per_series, ef, ed, n_vch,
                                                      state_end, adj_end, ll, want_grad, err);
+  GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -1402,6 +1450,7 @@ cudaError_t launch_warp_combine(const DevModel &M, const float *ef, int n_vch, f
   }
   k_warp_scan<S><<<(n_vch + 63) / 64, 64, smem, st>>>(ef, n_vch, pre_local, suf_local, wtot,
                                                       want_info);
+  GPSS_COUNT_LAUNCH();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (fold) {
@@ -1409,6 +1458,7 @@ cudaError_t launch_warp_combine(const DevModel &M, const float *ef, int n_vch, f
     k_warp_fold<S><<<(n_out + 63) / 64, 64, 0, st>>>(n_out, per_series, M.n_series, M.n_chunks,
                                                      M.ch_first, wtot, n_w, wpre, wsuf,
                                                      want_info);
+    GPSS_COUNT_LAUNCH();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   } else {
@@ -1422,6 +1472,7 @@ cudaError_t launch_warp_combine(const DevModel &M, const float *ef, int n_vch, f
   k_join<S><<<(n_vch + 127) / 128, 128, 0, st>>>(n_vch, M.n_chunks, M.ch_flags, pre_local,
                                                  suf_local, wpre, wsuf, state_end,
                                                  want_info ? info_incl : nullptr);
+  GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -1437,6 +1488,7 @@ cudaError_t launch_finish(const DevModel &M, int n_vch, int per_series, const fl
   if (n_vch <= 0) return cudaSuccess;
   k_finish<S><<<(n_vch + 127) / 128, 128, 0, st>>>(M, n_vch, per_series, ef, ed, state_end,
                                                    info_incl, adj_end, ll_part, err);
+  GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -1448,12 +1500,13 @@ cudaError_t launch_grad_ck(const DevModel &M, const float *theta, int n_vch, int
   const size_t smem = (size_t)(GRAD_BS / 32) * S::NT * TAB_TERM * sizeof(float);
   k_grad<S, CK><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
       M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err, tabs, rbuf, dcache);
+  GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
 // ck: events per recomputation segment (8 or 16), the value k_elem saved the
 // partial elements pck with ([(max_len-1)/ck] * (NF+1) * n_vch floats).
-// Scratch: rbuf [ck * (SD+1) * n_vch] floats.  dcache: the step-scalar cache
+// Scratch: rbuf [ck * 4 ceil(SD/4) * n_vch] floats.  dcache: the step-scalar cache
 // k_elem filled, or null (the replay then recomputes the scalars).
 template <class S>
 cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int per_series,
@@ -1475,6 +1528,7 @@ cudaError_t launch_disc(const float *theta, const float *tabs, int k0, int k1, c
                         int n, float *phi, float *q, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_disc<S><<<(n + 127) / 128, 128, 0, st>>>(theta, tabs, k0, k1, dt, n, phi, q);
+  GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 

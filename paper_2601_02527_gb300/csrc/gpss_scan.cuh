@@ -342,16 +342,19 @@ cudaError_t scan_elems(const float *src, int n, float *dst, int mode, int rev_in
   if (n <= 0) return cudaSuccess;
   if (n <= T) {
     k_tile_scan<S, T><<<1, T, smem, st>>>(src, n, nullptr, 0, dst, mode, rev_index, rev_op);
+    GPSS_COUNT_LAUNCH();
     return cudaGetLastError();
   }
   const int nt = (n + T - 1) / T;
   float *agg = scratch, *aggscan = scratch + (size_t)Elem<S>::NF * nt;
   k_tile_reduce<S, T><<<nt, T, smem, st>>>(src, n, agg, nt, rev_index, rev_op);
+  GPSS_COUNT_LAUNCH();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = scan_elems<S>(agg, nt, aggscan, 0, 0, rev_op, aggscan + (size_t)Elem<S>::NF * nt, st);
   if (e != cudaSuccess) return e;
   k_tile_scan<S, T><<<nt, T, smem, st>>>(src, n, aggscan, nt, dst, mode, rev_index, rev_op);
+  GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 

@@ -229,7 +229,10 @@ def test_graph_and_host_paths_agree(gp):
     wl = f32_theta(synth.c4(n_series=5, scale=0.03))
     m = gp.Model.from_workload(wl, chunk_len=96)
     th = theta_dev(wl)
+    n0 = gp.launch_count()
     ll, g = m.loglik_grad(th)
+    # tables, elements, combination (>= 3), finish, gradient, per-series sums
+    assert gp.launch_count() - n0 >= 8
     for _ in range(2):
         ll_b, g_b = m.loglik_grad(th, batched=True)
         torch.cuda.synchronize()
