@@ -76,9 +76,9 @@ typedef struct {
   int schedule;           /* 0 auto, 1 one chunk per series, 2 chunked parallel-in-time */
   int threads_per_series; /* reserved, must be 0 or 1 */
   int chunk_len;          /* events per chunk of the parallel-in-time schedule, 0 = auto */
-  int ckpt_interval;      /* events per recomputation segment of the gradient: 8 or 16
-                             (0 = 16); the reverse sweep replays each segment from its
-                             checkpoint before walking it backwards */
+  int ckpt_interval;      /* events per recomputation segment of the gradient: 8, 16, 32
+                             or 64 (0 = 32); the reverse sweep replays each segment from
+                             its starting state before walking it backwards */
   int debug_checks;       /* nonzero: extra host-side validation */
   int chunk_combine;      /* combination of chunk elements across a series: 0 auto (= 2),
                              1 sequential fold per series (one thread per series),

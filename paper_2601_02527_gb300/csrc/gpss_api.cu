@@ -106,7 +106,7 @@ struct gp_ss_model {
   // chunk plan
   int chunk_len = 0, n_chunks = 0, max_chunk = 0, max_chunks_per_series = 0;
   int combine = 0;  // cross-chunk combination: 0 auto, 1 sequential per series, 2 tree
-  int ckpt_interval = 16;  // events per recomputation segment of the gradient
+  int ckpt_interval = 32;  // events per recomputation segment of the gradient
   int step_cache = 0;      // 0 auto, 1 never keep the gradient's step scalars
   int64_t *d_ch_ev0 = nullptr, *d_ch_meas0 = nullptr;
   int32_t *d_ch_len = nullptr, *d_ch_series = nullptr, *d_ch_first = nullptr;
@@ -663,7 +663,9 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   if (o.precision != 32 && o.precision != 64) return GP_SS_EINVAL;
   if (o.threads_per_series > 1) return GP_SS_EUNSUPPORTED;
   if (o.chunk_combine < 0 || o.chunk_combine > 2) return GP_SS_EINVAL;
-  if (o.ckpt_interval != 0 && o.ckpt_interval != 8 && o.ckpt_interval != 16) return GP_SS_EINVAL;
+  if (o.ckpt_interval != 0 && o.ckpt_interval != 8 && o.ckpt_interval != 16 &&
+      o.ckpt_interval != 32 && o.ckpt_interval != 64)
+    return GP_SS_EINVAL;
   if (o.step_cache != 0 && o.step_cache != 1) return GP_SS_EINVAL;
   if (series_offsets[0] != 0) return GP_SS_EINVAL;
   for (int s = 0; s < n_series; ++s)
@@ -681,7 +683,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   m->precision = o.precision;
   m->schedule = o.schedule;
   m->combine = o.chunk_combine;
-  m->ckpt_interval = o.ckpt_interval == 8 ? 8 : 16;
+  m->ckpt_interval = o.ckpt_interval == 0 ? 32 : o.ckpt_interval;
   m->step_cache = o.step_cache;
   m->n_params = 1;
   for (int t = 0; t < spec->n_terms; ++t) {

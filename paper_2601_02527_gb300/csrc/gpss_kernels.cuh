@@ -22,7 +22,7 @@
 //                 log-likelihood in closed form, and for the gradient the
 //                 information about each chunk's end state from all later
 //                 data, turned into the adjoint of that state.
-//      k_grad     one thread per chunk, segments of CK events from last to
+//      k_grad     one thread per chunk, segments of ck events from last to
 //                 first: the segment's starting state from the partial
 //                 element k_elem saved there and the chunk's incoming state,
 //                 a forward replay of the segment, then a sweep back in time
@@ -1072,13 +1072,13 @@ GPSS_HD void apply_partial(const float *src, int n_vch, int vc, const float *m_i
   }
 }
 
-// Segments of CK events aligned to the chunk's end (the first may be
+// Segments of ck events aligned to the chunk's end (the first may be
 // shorter).  Walking the segments from last to first: the filtered state at
 // the segment's start comes from the partial element saved there by k_elem,
 // the segment is replayed forward into this thread's column of rbuf (global,
 // coalesced across the warp; slot k holds (m, P) before the segment's k-th
 // event), then walked backwards in time.
-template <class S, int CK>
+template <class S>
 __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restrict__ theta, int n_vch,
                                              int per_series, const float *__restrict__ state_end,
                                              const float *__restrict__ adj_end,
@@ -1086,7 +1086,7 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
                                              int *__restrict__ err,
                                              const float *__restrict__ tabs,
                                              float *__restrict__ rbuf,
-                                             const float *__restrict__ dcache) {
+                                             const float *__restrict__ dcache, int ck) {
   using F = float;
   constexpr int D = S::D;
   constexpr int SD = D + S::NP;
@@ -1113,8 +1113,8 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   F m[D], P[S::NP];
   const int64_t e0 = M.ch_ev0[c];
   const int len = M.ch_len[c];
-  const int nseg = (len + CK - 1) / CK;
-  const int f0 = len - (nseg - 1) * CK;
+  const int nseg = (len + ck - 1) / ck;
+  const int f0 = len - (nseg - 1) * ck;
   F lam[D], Lam[S::NP];
   if (last) {
 #pragma unroll
@@ -1134,8 +1134,8 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   const float4 *dc = dcache_col<S::NT>(M, const_cast<float *>(dcache), vc);
   bool bad = false;
   for (int seg = nseg - 1; seg >= 0; --seg) {
-    const int k0 = seg == 0 ? 0 : f0 + (seg - 1) * CK;
-    const int k1 = seg == 0 ? f0 : k0 + CK;
+    const int k0 = seg == 0 ? 0 : f0 + (seg - 1) * ck;
+    const int k1 = seg == 0 ? f0 : k0 + ck;
     int mrel = 0;
     if (seg == 0) {
       if (first)
@@ -1338,7 +1338,7 @@ __global__ void k_disc(const float *__restrict__ theta, const float *__restrict_
 // Host launchers, one table per compiled shape.
 // ---------------------------------------------------------------------------
 struct OpTable {
-  int D, NP, NF, ND, CK;
+  int D, NP, NF, ND;
   cudaError_t (*plain32)(const DevModel &, const float *, int, int, double *, int *, cudaStream_t);
   cudaError_t (*plain64)(const DevModel &, const float *, int, int, double *, int *, cudaStream_t);
   cudaError_t (*elem)(const DevModel &, const float *, int, int, float *, double *, int *,
@@ -1362,7 +1362,6 @@ struct OpTable {
                       cudaStream_t);
 };
 
-constexpr int GRAD_CK = 16;
 constexpr int GRAD_BS = 64;
 
 template <class S, class F>
@@ -1380,7 +1379,7 @@ cudaError_t launch_elem(const DevModel &M, const float *theta, int n_vch, int pe
                         float *ef, double *ed, int *err, const float *tabs, float *pck, int ck,
                         float *dcache, cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
-  if (pck && (ck != 8 && ck != 16)) return cudaErrorInvalidValue;
+  if (pck && (ck < 2 || ck > 64 || (ck & 1))) return cudaErrorInvalidValue;
   const int bs = 128;
   const size_t smem = (size_t)(bs / 32) * S::NT * TAB_TERM * sizeof(float);
   k_elem<S><<<(n_vch + bs - 1) / bs, bs, smem, st>>>(M, theta, n_vch, per_series, ef, ed, err,
@@ -1492,35 +1491,22 @@ cudaError_t launch_finish(const DevModel &M, int n_vch, int per_series, const fl
   return cudaGetLastError();
 }
 
-template <class S, int CK>
-cudaError_t launch_grad_ck(const DevModel &M, const float *theta, int n_vch, int per_series,
-                           const float *state_end, const float *adj_end, const float *pck,
-                           float *gpart, int *err, const float *tabs, float *rbuf,
-                           const float *dcache, cudaStream_t st) {
-  const size_t smem = (size_t)(GRAD_BS / 32) * S::NT * TAB_TERM * sizeof(float);
-  k_grad<S, CK><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
-      M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err, tabs, rbuf, dcache);
-  GPSS_COUNT_LAUNCH();
-  return cudaGetLastError();
-}
-
-// ck: events per recomputation segment (8 or 16), the value k_elem saved the
-// partial elements pck with ([(max_len-1)/ck] * (NF+1) * n_vch floats).
-// Scratch: rbuf [ck * 4 ceil(SD/4) * n_vch] floats.  dcache: the step-scalar cache
-// k_elem filled, or null (the replay then recomputes the scalars).
+// ck: events per recomputation segment (even, 2..64), the value k_elem saved
+// the partial elements pck with ([(max_len-1)/ck] * (NF+1) * n_vch floats).
+// Scratch: rbuf [ck * 4 ceil(SD/4) * n_vch] floats.  dcache: the step-scalar
+// cache k_elem filled, or null (the replay then recomputes the scalars).
 template <class S>
 cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int per_series,
                         const float *state_end, const float *adj_end, const float *pck,
                         float *gpart, int *err, const float *tabs, float *rbuf,
                         const float *dcache, int ck, cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
-  if (ck == 8)
-    return launch_grad_ck<S, 8>(M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err,
-                                tabs, rbuf, dcache, st);
-  if (ck == 16)
-    return launch_grad_ck<S, 16>(M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err,
-                                 tabs, rbuf, dcache, st);
-  return cudaErrorInvalidValue;
+  if (ck < 2 || ck > 64 || (ck & 1)) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)(GRAD_BS / 32) * S::NT * TAB_TERM * sizeof(float);
+  k_grad<S><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
+      M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err, tabs, rbuf, dcache, ck);
+  GPSS_COUNT_LAUNCH();
+  return cudaGetLastError();
 }
 
 template <class S>
@@ -1539,7 +1525,6 @@ OpTable make_ops() {
   o.NP = S::NP;
   o.NF = ElemLayout<S>::NF;
   o.ND = ElemLayout<S>::ND;
-  o.CK = GRAD_CK;
   o.plain32 = &launch_plain<S, float>;
   o.plain64 = &launch_plain<S, double>;
   o.elem = &launch_elem<S>;

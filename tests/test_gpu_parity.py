@@ -132,7 +132,7 @@ def test_fp32_grad_layout1(gp, chunk, combine):
     np.testing.assert_allclose(ll.cpu().numpy(), ll2, rtol=1e-12)
 
 
-@pytest.mark.parametrize("ck", [8, 16])
+@pytest.mark.parametrize("ck", [8, 16, 32, 64])
 def test_step_cache_off_matches(gp, ck):
     # the reverse sweep recomputing the step scalars gives the gradient of
     # the cached path (same FP32 arithmetic up to contraction) and the oracle's
