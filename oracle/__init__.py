@@ -59,6 +59,12 @@ def _load():
             P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
             P(ctypes.c_double)]
         lib.gpss_oracle_loglik.restype = ctypes.c_int
+        lib.gpss_oracle_exposure_grad.argtypes = [
+            P(ctypes.c_int32), ctypes.c_int64, P(ctypes.c_double), P(ctypes.c_int32),
+            P(ctypes.c_int32), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+            P(ctypes.c_double), ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_int64),
+            P(ctypes.c_double), P(ctypes.c_double)]
+        lib.gpss_oracle_exposure_grad.restype = ctypes.c_int
         lib.gpss_oracle_discretize.argtypes = [
             P(ctypes.c_int32), P(ctypes.c_double), ctypes.c_double, P(ctypes.c_double),
             P(ctypes.c_double), P(ctypes.c_double)]
@@ -175,6 +181,41 @@ def loglik_events(terms, layout, ev, theta, grad=False, n_slots=None, dump=False
         res["P"] = dP
         res["S"] = dS
     return res
+
+
+def exposure_grad_events(terms, layout, ev, theta, n_slots=None):
+    """Complex-step d loglik / d t_start and d t_end per measurement (in the
+    measurement order of the series) from built events."""
+    lib = _load()
+    n_slots = ev["n_slots"] if n_slots is None else n_slots
+    spec = spec_array(terms, layout, n_slots)
+    theta = np.ascontiguousarray(theta, np.float64)
+    n_ev = len(ev["t"])
+    n = n_ev // 2
+    ks = np.zeros(n, np.int64)
+    ke = np.zeros(n, np.int64)
+    idx = np.arange(n_ev, dtype=np.int64)
+    ks[ev["meas"][ev["kind"] == 0]] = idx[ev["kind"] == 0]
+    ke[ev["meas"][ev["kind"] == 1]] = idx[ev["kind"] == 1]
+    d_ts = np.zeros(n)
+    d_te = np.zeros(n)
+    arr = {k: np.ascontiguousarray(ev[k]) for k in ("t", "kind", "slot", "y", "r0", "invd")}
+    rc = lib.gpss_oracle_exposure_grad(
+        _ptr(spec, ctypes.c_int32), n_ev, _ptr(arr["t"], ctypes.c_double),
+        _ptr(arr["kind"], ctypes.c_int32), _ptr(arr["slot"], ctypes.c_int32),
+        _ptr(arr["y"], ctypes.c_double), _ptr(arr["r0"], ctypes.c_double),
+        _ptr(arr["invd"], ctypes.c_double), _ptr(theta, ctypes.c_double), n,
+        _ptr(ks, ctypes.c_int64), _ptr(ke, ctypes.c_int64), _ptr(d_ts, ctypes.c_double),
+        _ptr(d_te, ctypes.c_double))
+    if rc != 0:
+        raise RuntimeError(f"oracle filter failed with code {rc}")
+    return d_ts, d_te
+
+
+def exposure_grad(terms, layout, t_start, t_end, y, yerr, theta, instrument=None, n_slots=None):
+    """Oracle (d loglik / d t_start, d loglik / d t_end) of one series."""
+    ev = events(t_start, t_end, y, yerr, instrument)
+    return exposure_grad_events(terms, layout, ev, theta, n_slots=n_slots)
 
 
 def loglik(terms, layout, t_start, t_end, y, yerr, theta, instrument=None, grad=False,

@@ -136,15 +136,76 @@ int gpss_oracle_loglik(const int32_t *spec, int64_t n_ev, const double *t_ev,
   if (grad) {
     const int np = n_params(&M);
     double complex thc[16];
-    for (int i = 0; i < np; ++i) {
+    double complex *tc = malloc(sizeof(double complex) * (size_t)(n_ev > 0 ? n_ev : 1));
+    double complex *ic = malloc(sizeof(double complex) * (size_t)(n_ev > 0 ? n_ev : 1));
+    if (!tc || !ic) {
+      free(tc);
+      free(ic);
+      return 4;
+    }
+    for (int64_t k = 0; k < n_ev; ++k) {
+      tc[k] = t_ev[k];
+      ic[k] = invd_ev[k];
+    }
+    for (int i = 0; i < np && !rc; ++i) {
       for (int j = 0; j < np; ++j) thc[j] = theta[j];
       double hstep = 1e-20 * (fabs(theta[i]) > 1.0 ? fabs(theta[i]) : 1.0);
       thc[i] = theta[i] + I * hstep;
       double complex llc;
-      rc = filter_c(&M, thc, n_ev, t_ev, kind, slot, y_ev, r0_ev, invd_ev, &llc, NULL, NULL);
-      if (rc) return rc;
-      grad[i] = cimag(llc) / hstep;
+      rc = filter_c(&M, thc, n_ev, tc, kind, slot, y_ev, r0_ev, ic, &llc, NULL, NULL);
+      if (!rc) grad[i] = cimag(llc) / hstep;
+    }
+    free(tc);
+    free(ic);
+  }
+  return rc;
+}
+
+/* Gradient of one series' log-likelihood with respect to its exposure
+ * windows, by the complex-step method on the event times: for measurement
+ * n (events ev_start[n], ev_end[n] of the sorted sequence), t_start or t_end
+ * is moved by i*h, which moves that event's time (and so the gaps on both
+ * sides of it; the event order is kept) and 1/delta of the measurement's end
+ * event, 1/(t_end - t_start).  The first event's time is the initial time
+ * (the prior is stationary), so it moves with it.  d_ts[n], d_te[n] =
+ * Im(loglik) / h.  One complex filter pass per window edge: O(N^2) work, for
+ * test-sized series. */
+int gpss_oracle_exposure_grad(const int32_t *spec, int64_t n_ev, const double *t_ev,
+                              const int32_t *kind, const int32_t *slot, const double *y_ev,
+                              const double *r0_ev, const double *invd_ev, const double *theta,
+                              int64_t n_meas, const int64_t *ev_start, const int64_t *ev_end,
+                              double *d_ts, double *d_te) {
+  model_t M;
+  if (parse_spec(spec, &M)) return 1;
+  const int np = n_params(&M);
+  double complex thc[16];
+  for (int j = 0; j < np; ++j) thc[j] = theta[j];
+  double complex *tc = malloc(sizeof(double complex) * (size_t)(n_ev > 0 ? n_ev : 1));
+  double complex *ic = malloc(sizeof(double complex) * (size_t)(n_ev > 0 ? n_ev : 1));
+  if (!tc || !ic) {
+    free(tc);
+    free(ic);
+    return 4;
+  }
+  int rc = 0;
+  for (int64_t n = 0; n < n_meas && !rc; ++n) {
+    const int64_t ks = ev_start[n], ke = ev_end[n];
+    const double delta = 1.0 / invd_ev[ke];
+    for (int edge = 0; edge < 2 && !rc; ++edge) {
+      for (int64_t k = 0; k < n_ev; ++k) {
+        tc[k] = t_ev[k];
+        ic[k] = invd_ev[k];
+      }
+      const int64_t ke_or_ks = edge ? ke : ks;
+      const double hstep = 1e-20 * (fabs(t_ev[ke_or_ks]) > 1.0 ? fabs(t_ev[ke_or_ks]) : 1.0);
+      tc[ke_or_ks] += I * hstep;
+      ic[ke] = 1.0 / (delta + (edge ? 1.0 : -1.0) * I * hstep);
+      double complex llc;
+      rc = filter_c(&M, thc, n_ev, tc, kind, slot, y_ev, r0_ev, ic, &llc, NULL, NULL);
+      if (!rc) (edge ? d_te : d_ts)[n] = cimag(llc) / hstep;
     }
   }
-  return 0;
+  free(tc);
+  free(ic);
+  return rc;
 }

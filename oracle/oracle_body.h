@@ -112,7 +112,7 @@ static void SFX(expm)(int n, const SCALAR *A, SCALAR *E) {
  * to h = dt / 2^s with ||F~|| h <= 1/2 and the result is doubled s times with
  * the exact semigroup identities of Eq. sde_sol:
  *   Phi~(2h) = Phi~(h)^2,  Q~(2h) = Phi~(h) Q~(h) Phi~(h)^T + Q~(h). */
-static void SFX(discretize)(const model_t *M, const SCALAR *F, const SCALAR *LQL, double dt,
+static void SFX(discretize)(const model_t *M, const SCALAR *F, const SCALAR *LQL, SCALAR dt,
                             SCALAR *Phi, SCALAR *Q) {
   const int D = M->dim, D2 = 2 * M->dim;
   for (int i = 0; i < D * D; ++i) {
@@ -127,8 +127,8 @@ static void SFX(discretize)(const model_t *M, const SCALAR *F, const SCALAR *LQL
     if (c > nrm) nrm = c;
   }
   int s = 0;
-  double h = dt;
-  while (nrm * h > 0.5 && s < 400) {
+  SCALAR h = dt;
+  while (nrm * S_ABS(h) > 0.5 && s < 400) {
     h *= 0.5;
     ++s;
   }
@@ -189,9 +189,9 @@ static void SFX(initial_cov)(const model_t *M, const SCALAR *w0, const SCALAR *v
  * (Eqs. H_aug, kalman_update) and add the term of Eq. loglikelihood.
  * The covariance update uses the Joseph form, which is algebraically equal
  * to P - K S K^T.  Summation is Neumaier-compensated. */
-static int SFX(filter)(const model_t *M, const SCALAR *th, int64_t n_ev, const double *t_ev,
+static int SFX(filter)(const model_t *M, const SCALAR *th, int64_t n_ev, const SCALAR *t_ev,
                        const int32_t *kind, const int32_t *slot, const double *y_ev,
-                       const double *r0_ev, const double *invd_ev, SCALAR *ll_out, double *dumpP,
+                       const double *r0_ev, const SCALAR *invd_ev, SCALAR *ll_out, double *dumpP,
                        double *dumpS) {
   const int D = M->dim;
   SCALAR w0[MAXT], q[MAXT], var[MAXT], s2;
@@ -203,12 +203,12 @@ static int SFX(filter)(const model_t *M, const SCALAR *th, int64_t n_ev, const d
   SFX(initial_cov)(M, w0, var, P);
   for (int i = 0; i < D; ++i) m[i] = 0;
   SCALAR sum = 0, comp = 0;
-  double tprev = n_ev > 0 ? t_ev[0] : 0.0;
+  SCALAR tprev = n_ev > 0 ? t_ev[0] : 0.0;
   int64_t n_end = 0;
   for (int64_t k = 0; k < n_ev; ++k) {
-    double dt = t_ev[k] - tprev;
+    SCALAR dt = t_ev[k] - tprev;
     tprev = t_ev[k];
-    if (dt < 0) return 2;
+    if (S_RE(dt) < 0) return 2;
     SFX(discretize)(M, F, LQL, dt, Phi, Qd);
     for (int i = 0; i < D; ++i) {
       SCALAR acc = 0;
