@@ -129,10 +129,15 @@ gp_ss_status gp_ss_loglik(const gp_ss_model *model, const float *theta, int n_se
  * by a reverse-time adjoint of the filter (the paper states the likelihood
  * only; Section 2.3 notes it feeds gradient-based optimisation).
  *   grad_out   device f32 [n_out * n_params], same row order as loglik_out
- *   dlogl_ddt  reserved, must be NULL */
+ *   dlogl_dexposure  NULL, or device f32 [rows * N * 2]: the gradient with respect
+ *              to every exposure window, (d/d t_start, d/d t_end) of measurement n (in
+ *              the build's measurement order) at [(row * N + n) * 2 + {0, 1}];
+ *              rows = 1 when theta_per_series (each series' own theta), else n_sets.
+ *              The event order is held fixed (windows that touch stay ordered end
+ *              before start).  FP32 models only (GP_SS_EUNSUPPORTED otherwise). */
 gp_ss_status gp_ss_loglik_grad(const gp_ss_model *model, const float *theta, int n_sets,
                                int theta_per_series, double *loglik_out, float *grad_out,
-                               float *dlogl_ddt, void *cuda_stream);
+                               float *dlogl_dexposure, void *cuda_stream);
 
 /* Same computations replayed from a CUDA graph captured on first use for
  * this (model, pointers, n_sets, mode); a later call with other pointers

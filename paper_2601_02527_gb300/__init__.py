@@ -219,8 +219,11 @@ class Model:
         return out
 
     def loglik_grad(self, theta, per_series=True, out=None, grad=None, stream=None,
-                    batched=False):
-        """(log-likelihood [n_out] float64, gradient [n_out, n_params] float32)."""
+                    batched=False, exposure=False, dexp=None):
+        """(log-likelihood [n_out] float64, gradient [n_out, n_params] float32),
+        plus, with ``exposure``, the exposure-window gradient [rows, N, 2] float32
+        ((d/d t_start, d/d t_end) per measurement; rows = 1 per series mode, else
+        the number of theta sets)."""
         import torch
         th = self._theta(theta)
         n = self.n_out(th, per_series)
@@ -228,6 +231,12 @@ class Model:
             out = torch.empty(n, dtype=torch.float64, device=th.device)
         if grad is None:
             grad = torch.empty(n, self.n_params, dtype=torch.float32, device=th.device)
+        if exposure and batched:
+            raise ValueError("the exposure gradient is computed by the direct call only")
+        if exposure and dexp is None:
+            rows = 1 if per_series else th.shape[0]
+            dexp = torch.empty(rows, self.info["n_meas"], 2, dtype=torch.float32,
+                               device=th.device)
         if batched:
             rc = self._lib.gp_ss_loglik_grad_batched(self._h, th.data_ptr(), th.shape[0],
                                                      int(bool(per_series)), out.data_ptr(),
@@ -235,9 +244,11 @@ class Model:
         else:
             rc = self._lib.gp_ss_loglik_grad(self._h, th.data_ptr(), th.shape[0],
                                              int(bool(per_series)), out.data_ptr(),
-                                             grad.data_ptr(), None, _stream_ptr(stream))
+                                             grad.data_ptr(),
+                                             dexp.data_ptr() if exposure else None,
+                                             _stream_ptr(stream))
         _check(rc, "gp_ss_loglik_grad")
-        return out, grad
+        return (out, grad, dexp) if exposure else (out, grad)
 
     def loglik_grad_host(self, theta, per_series=True, reupload_events=False, stream=None):
         """Host-buffer variant: numpy in, numpy out (synchronous)."""

@@ -53,6 +53,35 @@ __global__ void k_series_sum(int n_out, int per_series, int n_series, int n_chun
     }
   }
 }
+
+__global__ void k_exposure_grad(int n_rows, int n_series, const int64_t *__restrict__ ev_off,
+                                const int64_t *__restrict__ meas_off,
+                                const int2 *__restrict__ mev, int64_t n_meas, int64_t n_events,
+                                const float *__restrict__ gdt, const float *__restrict__ gwe,
+                                float *__restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n_rows * n_meas) return;
+  const int64_t row = idx / n_meas, n = idx % n_meas;
+  // series of measurement n: last s with meas_off[s] <= n
+  int lo = 0, hi = n_series - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (meas_off[mid] <= n)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const int64_t kb = ev_off[lo], kend = ev_off[lo + 1];
+  const float *g = gdt + row * n_events;
+  const int2 p = mev[n];
+  const int64_t ks = kb + p.x, ke = kb + p.y;
+  auto gt = [&](int64_t k) {
+    return (k == kb ? 0.f : g[k]) - (k + 1 < kend ? g[k + 1] : 0.f);
+  };
+  const float wpart = gwe[row * n_events + ke];
+  out[2 * idx] = gt(ks) + wpart;
+  out[2 * idx + 1] = gt(ke) - wpart;
+}
 }  // namespace gpss
 
 using gpss::OpTable;
@@ -103,6 +132,7 @@ struct gp_ss_model {
   uint8_t *d_tag = nullptr;
   float4 *d_meas = nullptr;
   double *d_dt64 = nullptr, *d_meas64 = nullptr;
+  int2 *d_mev = nullptr;  // per measurement (input order): its start and end event in the series
   // chunk plan
   int chunk_len = 0, n_chunks = 0, max_chunk = 0, max_chunks_per_series = 0;
   int combine = 0;  // cross-chunk combination: 0 auto, 1 sequential per series, 2 tree
@@ -174,6 +204,7 @@ gp_ss_status dev_upload(T **dst, const T *src, size_t n) {
 
 void free_model_buffers(gp_ss_model *m) {
   void *dev[] = {m->d_ev_off, m->d_meas_off, m->d_dt, m->d_tag, m->d_meas, m->d_dt64, m->d_meas64,
+                 m->d_mev,
                  m->d_ch_ev0, m->d_ch_meas0, m->d_ch_len, m->d_ch_series, m->d_ch_first,
                  m->d_ch_flags, m->d_w_doff, m->d_err};
   for (void *p : dev)
@@ -204,7 +235,7 @@ struct SeriesOut {
 
 void build_series(int64_t a, int64_t b, const double *ts, const double *te, const float *y,
                   const float *yerr, const int32_t *inst, float *dt, uint8_t *tag, float4 *meas,
-                  double *dt64, double *meas64, SeriesOut *out) {
+                  double *dt64, double *meas64, int2 *mev, SeriesOut *out) {
   const int64_t n = b - a;
   std::vector<int> slot(n);
   int n_slots = 1;
@@ -278,6 +309,11 @@ void build_series(int64_t a, int64_t b, const double *ts, const double *te, cons
     const int64_t i = ev[k].i;
     const bool is_end = ev[k].kind == 0;
     tag[e0 + k] = (uint8_t)((is_end ? 1 : 0) | (slot[i] << 1));
+    // where this measurement's window edges sit in the series' events
+    if (is_end)
+      mev[a + i].y = (int)k;
+    else
+      mev[a + i].x = (int)k;
     if (is_end) {
       const double delta = te[a + i] - ts[a + i];
       const double w = 1.0 / delta;
@@ -389,6 +425,7 @@ gpss::DevModel dev_view(const gp_ss_model *m) {
   d.ch_series = m->d_ch_series;
   d.ch_flags = m->d_ch_flags;
   d.ch_first = m->d_ch_first;
+  d.n_events = m->n_events;
   d.w_doff = m->d_w_doff;
   d.dcache_steps = m->dcache_steps;
   return d;
@@ -450,7 +487,7 @@ gp_ss_status check_call(const gp_ss_model *m, const float *theta, int n_sets, in
 
 // Enqueue the log-likelihood (and optionally gradient) computation.
 gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int per_series,
-                     double *ll, float *grad, cudaStream_t st) {
+                     double *ll, float *grad, cudaStream_t st, float *dexp = nullptr) {
   const int n_out = per_series ? m->n_series : n_sets * m->n_series;
   gp_ss_status s0 = prepare_err(m, n_out, st);
   if (s0) return s0;
@@ -558,7 +595,13 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       }
     }
     if (grad) {
-      float *rbuf = nullptr;
+      float *rbuf = nullptr, *gdt = nullptr, *gwe = nullptr;
+      const int exp_rows = per_series ? 1 : n_sets;
+      if (dexp && (!grab((void **)&gdt, (size_t)exp_rows * m->n_events * sizeof(float)) ||
+                   !grab((void **)&gwe, (size_t)exp_rows * m->n_events * sizeof(float)))) {
+        res = GP_SS_ENOMEM;
+        break;
+      }
       if (!grab((void **)&rbuf, (size_t)ck * (4 * ((SD + 3) / 4)) * n_vch * sizeof(float)) ||
           !grab((void **)&gpart, (size_t)m->n_params * n_vch * sizeof(float))) {
         res = GP_SS_ENOMEM;
@@ -566,9 +609,20 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       }
       PhaseTimer pt(m, st, 2);
       if (o.grad(dm, theta, n_vch, per_series, state_end, adj, ckpt, gpart, m->d_err, tabs, rbuf,
-                 dcache, ck, st)) {
+                 dcache, ck, gdt, gwe, st)) {
         res = GP_SS_ECUDA;
         break;
+      }
+      if (dexp && m->n_meas > 0) {
+        const int64_t nt = (int64_t)exp_rows * m->n_meas;
+        gpss::k_exposure_grad<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(
+            exp_rows, m->n_series, m->d_ev_off, m->d_meas_off, m->d_mev, m->n_meas, m->n_events,
+            gdt, gwe, dexp);
+        GPSS_COUNT_LAUNCH();
+        if (cudaGetLastError() != cudaSuccess) {
+          res = GP_SS_ECUDA;
+          break;
+        }
       }
     }
     if (tree || grad) {
@@ -723,6 +777,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
     }
   }
   m->h_meas[N] = make_float4(0.f, 0.f, 0.f, 0.f);
+  std::vector<int2> mev(std::max<int64_t>(N, 1));
   std::vector<double> dt64, meas64;
   if (o.precision == 64) {
     dt64.resize(nE);
@@ -740,7 +795,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
           build_series(series_offsets[s], series_offsets[s + 1], t_start, t_end, y, yerr,
                        instrument, m->h_dt, m->h_tag, m->h_meas,
                        dt64.empty() ? nullptr : dt64.data(),
-                       meas64.empty() ? nullptr : meas64.data(), &so[s]);
+                       meas64.empty() ? nullptr : meas64.data(), mev.data(), &so[s]);
       });
     for (auto &t : pool) t.join();
   }
@@ -767,6 +822,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   if (!st) st = dev_upload(&m->d_dt, m->h_dt, nE);
   if (!st) st = dev_upload(&m->d_tag, m->h_tag, nE);
   if (!st) st = dev_upload(&m->d_meas, m->h_meas, nM);
+  if (!st) st = dev_upload(&m->d_mev, mev.data(), mev.size());
   if (!st && o.precision == 64) {
     st = dev_upload(&m->d_dt64, dt64.data(), nE);
     if (!st) st = dev_upload(&m->d_meas64, meas64.data(), 3 * nM);
@@ -838,13 +894,14 @@ gp_ss_status gp_ss_loglik(const gp_ss_model *m, const float *theta, int n_sets,
 
 gp_ss_status gp_ss_loglik_grad(const gp_ss_model *m, const float *theta, int n_sets,
                                int theta_per_series, double *loglik_out, float *grad_out,
-                               float *dlogl_ddt, void *cuda_stream) {
+                               float *dlogl_dexposure, void *cuda_stream) {
   gp_ss_status s = check_call(m, theta, n_sets, theta_per_series, loglik_out);
   if (s) return s;
-  if (!grad_out || dlogl_ddt) return GP_SS_EINVAL;
+  if (!grad_out) return GP_SS_EINVAL;
+  if (dlogl_dexposure && m->precision == 64) return GP_SS_EUNSUPPORTED;
   DeviceGuard g(m->device);
   return enqueue(m, theta, n_sets, theta_per_series, loglik_out, grad_out,
-                 (cudaStream_t)cuda_stream);
+                 (cudaStream_t)cuda_stream, dlogl_dexposure);
 }
 
 gp_ss_status gp_ss_loglik_batched(const gp_ss_model *m, const float *theta, int n_sets,

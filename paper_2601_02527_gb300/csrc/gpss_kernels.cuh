@@ -43,6 +43,7 @@ struct DevModel {
   int kinds[4];
   const int64_t *ev_off;    // [n_series+1]
   const int64_t *meas_off;  // [n_series+1]
+  int64_t n_events;         // all series
   const float *dt;          // [n_events]
   const uint8_t *tag;       // [n_events]
   const float4 *meas;       // [n_meas] (y, yerr^2, 1/delta, 0)
@@ -866,13 +867,18 @@ struct TermGrad {
 // step's six scalars per term.  (lam, Lam): adjoint of the filtered state
 // after the event (full-matrix gradient convention, stored packed); on
 // return, adjoint of (m, P).
+// With want_exp, also g_dt = d loglik / d (this step's gap) and, at an end
+// event, g_w = d loglik / d (1/delta of its measurement).
 template <class S>
 GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *tc, float s2,
                           const float *m, const float *P, float *lam, float *Lam,
-                          TermGrad<S::NT> &gr, const float4 *tab, const Disc<float> *dv) {
+                          TermGrad<S::NT> &gr, const float4 *tab, const Disc<float> *dv,
+                          bool want_exp, float &g_dt, float &g_w) {
   using F = float;
   constexpr int D = S::D;
   const int j = (tag >> 1) & 7;
+  g_dt = F(0);
+  g_w = F(0);
   Blocks<F> B[S::NT];
 #pragma unroll
   for (int t = 0; t < S::NT; ++t) B[t] = make_blocks(dv[t], tc[t]);
@@ -908,6 +914,19 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
     F h[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) h[i] = (i >= 2 * S::NT && S::zslot(i) == j) ? w : F(0);
+    if (want_exp) {
+      // h = w e (e selects the slot's integral states): d/dh = Pp ub + 2 Sb u - vb mp
+      F gw = F(0);
+#pragma unroll
+      for (int i = 2 * S::NT; i < D; ++i) {
+        if (S::zslot(i) != j) continue;
+        F acc = F(2) * Sb * u[i] - vb * mp[i];
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) acc += Pp[S::pk(i, kk)] * ub[kk];
+        gw += acc;
+      }
+      g_w = gw;
+    }
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       lam[i] -= h[i] * vb;
@@ -990,6 +1009,11 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
     disc_tangents(dt, c, tab + t * (TAB_TERM / 4), dv[t], da, db);
     gr.a[t] += bf * da[0] + bfp * da[1] + bF1 * da[2] + bIff * da[3] + bIpp * da[4] + bIFF * da[5];
     gr.beta[t] += bf * db[0] + bfp * db[1] + bF1 * db[2] + bIff * db[3] + bIpp * db[4] + bIFF * db[5];
+    if (want_exp) {
+      // d/dt of the six scalars: f', f'' = -2a f' - w2 f, f, f^2, f'^2, F1^2
+      g_dt += bf * fp + bfp * (F(-2) * c.a * fp - c.w2 * f) + bF1 * f + bIff * f * f +
+              bIpp * fp * fp + bIFF * F1 * F1;
+    }
   }
   (void)zl;
   (void)zL;
@@ -1077,7 +1101,10 @@ GPSS_HD void apply_partial(const float *src, int n_vch, int vc, const float *m_i
 // the segment's start comes from the partial element saved there by k_elem,
 // the segment is replayed forward into this thread's column of rbuf (global,
 // coalesced across the warp; slot k holds (m, P) before the segment's k-th
-// event), then walked backwards in time.
+// event), then walked backwards in time.  With gdt set, the walk also
+// writes, per event k of theta set r, gdt[r n_events + k] = d loglik / d
+// (gap before k) and, at an end event, gwe[...] = w^2 d loglik / d w
+// (w = 1/delta of its measurement; dw/dt_start = w^2 = -dw/dt_end).
 template <class S>
 __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restrict__ theta, int n_vch,
                                              int per_series, const float *__restrict__ state_end,
@@ -1086,7 +1113,8 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
                                              int *__restrict__ err,
                                              const float *__restrict__ tabs,
                                              float *__restrict__ rbuf,
-                                             const float *__restrict__ dcache, int ck) {
+                                             const float *__restrict__ dcache, int ck,
+                                             float *__restrict__ gdt, float *__restrict__ gwe) {
   using F = float;
   constexpr int D = S::D;
   constexpr int SD = D + S::NP;
@@ -1129,6 +1157,8 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   for (int t = 0; t < S::NT; ++t) gr.a[t] = gr.beta[t] = gr.w2[t] = gr.qc[t] = gr.var[t] = F(0);
   gr.s2 = F(0);
   const int64_t m0 = M.ch_meas0[c];
+  // per-event exposure adjoints of this chunk (theta set `set`)
+  const int64_t eo = (int64_t)set * M.n_events + e0;
   float4 *my = reinterpret_cast<float4 *>(rbuf) + vc;  // group v of slot k at (k SG + v) n_vch
   const size_t rs = (size_t)n_vch;
   const float4 *dc = dcache_col<S::NT>(M, const_cast<float *>(dcache), vc);
@@ -1244,7 +1274,12 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
 #pragma unroll
         for (int i = 0; i < S::NP; ++i) P[i] = r[D + i];
       }
-      reverse_event<S>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab, dv);
+      F g_dt, g_w;
+      reverse_event<S>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab, dv, gdt != nullptr, g_dt, g_w);
+      if (gdt) {
+        gdt[eo + k2] = g_dt;
+        if (tag & 1) gwe[eo + k2] = q.z * q.z * g_w;
+      }
     }
   }
   if (first) {
@@ -1298,6 +1333,17 @@ __global__ void k_series_sum(int n_out, int per_series, int n_series, int n_chun
                              const float *__restrict__ gpart, int n_params,
                              double *__restrict__ ll_out, float *__restrict__ grad_out);
 
+// Exposure-window gradient per measurement (input order) from the per-event
+// adjoints of k_grad: d/dt_start = gt(start) + gwe(end), d/dt_end = gt(end) -
+// gwe(end), where gt(k) = gdt(k) - gdt(k+1) (the event's time ends the gap
+// before it and starts the one after it; a series' first event sets the
+// initial time, so its own gap is always zero).  out[(row N + n) 2 + {0,1}].
+__global__ void k_exposure_grad(int n_rows, int n_series, const int64_t *__restrict__ ev_off,
+                                const int64_t *__restrict__ meas_off,
+                                const int2 *__restrict__ mev, int64_t n_meas, int64_t n_events,
+                                const float *__restrict__ gdt, const float *__restrict__ gwe,
+                                float *__restrict__ out);
+
 // Dense Phi~(dt_k), Q~(dt_k) for a list of gaps (one thread per gap).
 template <class S>
 __global__ void k_disc(const float *__restrict__ theta, const float *__restrict__ tabs, int kinds0,
@@ -1347,7 +1393,7 @@ struct OpTable {
                       float *, double *, int, int *, cudaStream_t);
   cudaError_t (*grad)(const DevModel &, const float *, int, int, const float *, const float *,
                       const float *, float *, int *, const float *, float *, const float *, int,
-                      cudaStream_t);
+                      float *, float *, cudaStream_t);
   cudaError_t (*tables)(const float *, int, int, int, int, float *, cudaStream_t);
   cudaError_t (*warp_combine)(const DevModel &, const float *, int, float *, float *, float *,
                               float *, float *, float *, float *, float *, int, int, int, int,
@@ -1495,16 +1541,19 @@ cudaError_t launch_finish(const DevModel &M, int n_vch, int per_series, const fl
 // the partial elements pck with ([(max_len-1)/ck] * (NF+1) * n_vch floats).
 // Scratch: rbuf [ck * 4 ceil(SD/4) * n_vch] floats.  dcache: the step-scalar
 // cache k_elem filled, or null (the replay then recomputes the scalars).
+// gdt, gwe: per-event exposure adjoints [rows * n_events] (see k_grad), or
+// null when the exposure gradient is not wanted.
 template <class S>
 cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int per_series,
                         const float *state_end, const float *adj_end, const float *pck,
                         float *gpart, int *err, const float *tabs, float *rbuf,
-                        const float *dcache, int ck, cudaStream_t st) {
+                        const float *dcache, int ck, float *gdt, float *gwe, cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
   if (ck < 2 || ck > 64 || (ck & 1)) return cudaErrorInvalidValue;
   const size_t smem = (size_t)(GRAD_BS / 32) * S::NT * TAB_TERM * sizeof(float);
   k_grad<S><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
-      M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err, tabs, rbuf, dcache, ck);
+      M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err, tabs, rbuf, dcache, ck,
+      gdt, gwe);
   GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
