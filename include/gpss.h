@@ -73,7 +73,11 @@ typedef struct {
 typedef struct {
   int precision;          /* 32 (default): FP32 filter with FP64 log-det/likelihood sums;
                              64: plain FP64 per-series filter (log-likelihood only) */
-  int schedule;           /* 0 auto, 1 one chunk per series, 2 chunked parallel-in-time */
+  int schedule;           /* 0 auto (chunked, default chunk length);
+                             1 one warp per series: 32 chunks per series;
+                             2 chunked parallel-in-time with chunk_len events per chunk;
+                             3 one thread per series running the whole filter (the
+                               log-likelihood; gradient calls use one warp per series) */
   int threads_per_series; /* reserved, must be 0 or 1 */
   int chunk_len;          /* events per chunk of the parallel-in-time schedule, 0 = auto */
   int ckpt_interval;      /* events per recomputation segment of the gradient: 8, 16, 32
@@ -218,6 +222,31 @@ gp_ss_status gp_ss_last_error_series(const gp_ss_model *model, int64_t *first_ba
  * 3 result conversion, 4 plain per-series filter) and clears the record. */
 gp_ss_status gp_ss_set_timing(gp_ss_model *model, int enable);
 gp_ss_status gp_ss_get_timing(gp_ss_model *model, double *ms, int64_t *launches);
+
+/* Autotuner (no counterpart in the paper): times candidate schedules on this
+ * model with the caller's theta and keeps the fastest.  Candidates: one
+ * thread per series (log-likelihood only), one warp per series, and chunked
+ * parallel-in-time with chunk lengths 64..1024 (which sets the threads per
+ * series), each with the warp-level or the sequential cross-chunk
+ * combination, and for gradient calls segment lengths 16, 32 and 64.  Each
+ * candidate runs once to warm up, then reps times (1..100) timed with CUDA
+ * events on the stream; the median decides.
+ *   The model's plan changes: no other call may use the model meanwhile; the
+ *   call synchronises the device.  theta as gp_ss_loglik; want_grad selects
+ *   loglik+grad (1) or loglik (0) timing; best (host) receives the choice. */
+typedef struct {
+  int schedule;           /* 1, 2 or 3 as gp_ss_options.schedule */
+  int chunk_len;          /* events per chunk of the chosen plan */
+  int chunk_combine;      /* 1 sequential, 2 warp-level + scan of warp totals */
+  int ckpt_interval;      /* gradient segment length */
+  int threads_per_series; /* chunks (threads) given to the longest series */
+  int n_tried;            /* candidates timed */
+  double ms;              /* median time per call of the choice */
+} gp_ss_tuning;
+
+gp_ss_status gp_ss_autotune(gp_ss_model *model, const float *theta, int n_sets,
+                            int theta_per_series, int want_grad, int reps, gp_ss_tuning *best,
+                            void *cuda_stream);
 
 /* Kernels this library has launched in the calling process, all models and
  * devices together (no counterpart in the paper; an accounting aid).  Counted

@@ -32,7 +32,7 @@ EXPORTS = ["gp_ss_build_model", "gp_ss_loglik", "gp_ss_loglik_grad", "gp_ss_logl
            "gp_ss_loglik_grad_batched", "gp_ss_loglik_grad_host", "gp_ss_model_info",
            "gp_ss_set_chunk_len", "gp_ss_last_error_series", "gp_ss_free_model",
            "gp_ss_status_string", "gp_ss_discretize", "gp_ss_set_timing", "gp_ss_get_timing",
-           "gp_ss_loglik_noalloc", "gp_ss_launch_count"]
+           "gp_ss_loglik_noalloc", "gp_ss_launch_count", "gp_ss_autotune"]
 
 PHASES = ["elem", "scan", "grad", "convert", "plain"]
 
@@ -46,6 +46,13 @@ class GPSSError(RuntimeError):
 class _KernelSpec(ctypes.Structure):
     _fields_ = [("n_terms", ctypes.c_int), ("terms", ctypes.POINTER(ctypes.c_int)),
                 ("integral_layout", ctypes.c_int)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int), ("chunk_len", ctypes.c_int),
+                ("chunk_combine", ctypes.c_int), ("ckpt_interval", ctypes.c_int),
+                ("threads_per_series", ctypes.c_int), ("n_tried", ctypes.c_int),
+                ("ms", ctypes.c_double)]
 
 
 class _Options(ctypes.Structure):
@@ -83,6 +90,7 @@ def load_library(path: str | None = None):
     lib.gp_ss_free_model.argtypes = [vp]
     lib.gp_ss_free_model.restype = None
     lib.gp_ss_launch_count.argtypes = [P(i64)]
+    lib.gp_ss_autotune.argtypes = [vp, vp, i32, i32, i32, i32, P(_Tuning), vp]
     lib.gp_ss_status_string.argtypes = [i32]
     lib.gp_ss_status_string.restype = ctypes.c_char_p
     lib.gp_ss_discretize.argtypes = [P(_KernelSpec), i32, vp, vp, i32, vp, vp, vp]
@@ -133,6 +141,8 @@ class Model:
         self.layout = int(layout)
         self.n_params = n_params_for(self.terms)
         offs = np.ascontiguousarray(offsets, np.int64)
+        self.offsets = offs.copy()
+        self._meas_series = None
         ts = np.ascontiguousarray(t_start, np.float64)
         te = np.ascontiguousarray(t_end, np.float64)
         yy = np.ascontiguousarray(y, np.float32)
@@ -203,6 +213,15 @@ class Model:
                  _stream_ptr(stream)), "gp_ss_loglik")
         return out
 
+    def measurement_series(self, device):
+        """Series index of every measurement (int64 tensor [N] on ``device``)."""
+        import torch
+        if self._meas_series is None or self._meas_series.device != torch.device(device):
+            counts = torch.as_tensor(np.diff(self.offsets), device=device)
+            self._meas_series = torch.repeat_interleave(
+                torch.arange(len(counts), device=device), counts)
+        return self._meas_series
+
     def loglik_noalloc(self, theta, per_series=True, out=None, stream=None):
         """Log-likelihood through gp_ss_loglik_noalloc: the library allocates
         nothing (its scratch is a fixed 16 MiB array per GPU).  For callers
@@ -262,6 +281,17 @@ class Model:
                                                 _stream_ptr(stream)), "gp_ss_loglik_grad_host")
         return ll, g
 
+    def autotune(self, theta, per_series=True, grad=True, reps=3, stream=None):
+        """Time the candidate schedules on this model (gp_ss_autotune), keep the
+        fastest and return it as a dict."""
+        th = self._theta(theta)
+        t = _Tuning()
+        _check(self._lib.gp_ss_autotune(self._h, th.data_ptr(), th.shape[0], int(bool(per_series)),
+                                        int(bool(grad)), int(reps), ctypes.byref(t),
+                                        _stream_ptr(stream)), "gp_ss_autotune")
+        self.info = self._info()
+        return {f: getattr(t, f) for f, _ in _Tuning._fields_}
+
     def set_chunk_len(self, chunk_len: int):
         _check(self._lib.gp_ss_set_chunk_len(self._h, int(chunk_len)), "gp_ss_set_chunk_len")
         self.info = self._info()
@@ -316,24 +346,44 @@ def _autograd_function():
     import torch
 
     class LogLikFunction(torch.autograd.Function):
-        """Sum-reducible log-likelihood with the adjoint gradient as backward."""
+        """Log-likelihood rows with the adjoint gradient as backward, for the
+        hyperparameters and (when ``windows`` needs a gradient) the exposure
+        windows."""
 
         @staticmethod
-        def forward(ctx, theta, model, per_series):
-            ll, g = model.loglik_grad(theta, per_series=per_series)
-            ctx.save_for_backward(g)
+        def forward(ctx, theta, windows, model, per_series):
+            want_exp = windows is not None and ctx.needs_input_grad[1]
+            if want_exp:
+                ll, g, dexp = model.loglik_grad(theta, per_series=per_series, exposure=True)
+            else:
+                ll, g = model.loglik_grad(theta, per_series=per_series)
+                dexp = g.new_empty(0)
+            ctx.save_for_backward(g, dexp)
+            ctx.want_exp = want_exp
+            ctx.model = model
             ctx.per_series = per_series
             ctx.n_sets = theta.shape[0]
             ctx.n_series = model.info["n_series"]
+            ctx.wdtype = windows.dtype if windows is not None else None
             return ll
 
         @staticmethod
         def backward(ctx, gout):
-            (g,) = ctx.saved_tensors
+            g, dexp = ctx.saved_tensors
             w = gout.to(torch.float32)[:, None] * g
             if not ctx.per_series:
                 w = w.view(ctx.n_sets, ctx.n_series, -1).sum(1)
-            return w, None, None
+            gw = None
+            if ctx.want_exp:
+                sidx = ctx.model.measurement_series(gout.device)
+                go = gout.to(torch.float32)
+                if ctx.per_series:
+                    gw = go[sidx][:, None] * dexp[0]
+                else:
+                    coef = go.view(ctx.n_sets, ctx.n_series)[:, sidx]
+                    gw = (coef[:, :, None] * dexp).sum(0)
+                gw = gw.to(ctx.wdtype)
+            return w, gw, None, None
 
     return LogLikFunction
 
@@ -341,9 +391,13 @@ def _autograd_function():
 _LLF = None
 
 
-def loglik(model: Model, theta, per_series=True):
-    """Differentiable log-likelihood (torch.autograd): rows as ``Model.loglik``."""
+def loglik(model: Model, theta, per_series=True, windows=None):
+    """Differentiable log-likelihood (torch.autograd): rows as ``Model.loglik``.
+
+    ``windows``: optional CUDA tensor [N, 2] of the model's exposure windows
+    (t_start, t_end) in measurement order -- the values the model was built
+    from; when it requires grad, backward also returns d/d windows."""
     global _LLF
     if _LLF is None:
         _LLF = _autograd_function()
-    return _LLF.apply(theta, model, per_series)
+    return _LLF.apply(theta, windows, model, per_series)

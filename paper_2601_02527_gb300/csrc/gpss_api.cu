@@ -332,8 +332,8 @@ void build_series(int64_t a, int64_t b, const double *ts, const double *te, cons
 gp_ss_status make_plan(gp_ss_model *m, int chunk_len) {
   const int n = m->n_series;
   int L = chunk_len;
-  if (m->schedule == 1 || L <= 0) {
-    if (m->schedule == 1) {
+  if (m->schedule == 1 || m->schedule == 3 || L <= 0) {
+    if (m->schedule == 1 || m->schedule == 3) {
       // one warp per series: 32 chunks of about K/32 events each
       int64_t mx = 1;
       for (int s = 0; s < n; ++s) mx = std::max<int64_t>(mx, m->ev_off[s + 1] - m->ev_off[s]);
@@ -498,6 +498,12 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
     if (!m->d_dt64) return GP_SS_EINVAL;
     PhaseTimer pt(m, st, 4);
     GPSS_CK(o.plain64(dm, theta, n_out, per_series, ll, m->d_err, st));
+    return GP_SS_OK;
+  }
+  if (m->schedule == 3 && !grad) {
+    // one thread per series, the whole sequential filter in registers
+    PhaseTimer pt(m, st, 4);
+    GPSS_CK(o.plain32(dm, theta, n_out, per_series, ll, m->d_err, st));
     return GP_SS_OK;
   }
   const int64_t n_vch64 = (int64_t)(per_series ? 1 : n_sets) * m->n_chunks;
@@ -721,6 +727,8 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
       o.ckpt_interval != 32 && o.ckpt_interval != 64)
     return GP_SS_EINVAL;
   if (o.step_cache != 0 && o.step_cache != 1) return GP_SS_EINVAL;
+  if (o.schedule < 0 || o.schedule > 3 || o.chunk_combine < 0 || o.chunk_combine > 2)
+    return GP_SS_EINVAL;
   if (series_offsets[0] != 0) return GP_SS_EINVAL;
   for (int s = 0; s < n_series; ++s)
     if (series_offsets[s + 1] < series_offsets[s]) return GP_SS_EUNSORTED;
@@ -989,6 +997,99 @@ gp_ss_status gp_ss_launch_count(int64_t *out) {
   if (!out) return GP_SS_EINVAL;
   *out = (int64_t)gpss::g_launches.load(std::memory_order_relaxed);
   return GP_SS_OK;
+}
+
+gp_ss_status gp_ss_autotune(gp_ss_model *m, const float *theta, int n_sets,
+                            int theta_per_series, int want_grad, int reps, gp_ss_tuning *best,
+                            void *cuda_stream) {
+  gp_ss_status s = check_call(m, theta, n_sets, theta_per_series, best);
+  if (s) return s;
+  if (m->precision != 32 || reps < 1 || reps > 100) return GP_SS_EINVAL;
+  DeviceGuard g(m->device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (cudaDeviceSynchronize() != cudaSuccess) return GP_SS_ECUDA;
+  const int n_out = theta_per_series ? m->n_series : n_sets * m->n_series;
+  double *ll = nullptr;
+  float *gr = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaMalloc((void **)&ll, (size_t)n_out * sizeof(double)) ||
+      (want_grad && cudaMalloc((void **)&gr, (size_t)n_out * m->n_params * sizeof(float))) ||
+      cudaEventCreate(&e0) || cudaEventCreate(&e1)) {
+    if (ll) cudaFree(ll);
+    if (gr) cudaFree(gr);
+    if (e0) cudaEventDestroy(e0);
+    return GP_SS_ENOMEM;
+  }
+  // candidates: (schedule, chunk length, combination, segment length)
+  struct Cand {
+    int schedule, L, combine, ck;
+  };
+  std::vector<Cand> cands;
+  const int Ls[] = {64, 128, 192, 256, 384, 512, 1024};
+  if (want_grad) {
+    for (int ck : {16, 32, 64}) {
+      cands.push_back({1, 0, 2, ck});
+      for (int L : Ls)
+        if (L >= 128 && L <= 512) cands.push_back({2, L, 2, ck});
+    }
+    cands.push_back({2, 256, 1, 32});
+  } else {
+    cands.push_back({3, 0, 2, 32});
+    for (int cb : {2, 1}) {
+      cands.push_back({1, 0, cb, 32});
+      for (int L : Ls) cands.push_back({2, L, cb, 32});
+    }
+  }
+  const Cand saved{m->schedule, m->chunk_len, m->combine, m->ckpt_interval};
+  Cand win = saved;
+  double win_ms = 1e300;
+  int tried = 0;
+  gp_ss_status res = GP_SS_OK;
+  for (const Cand &c : cands) {
+    m->schedule = c.schedule;
+    m->combine = c.combine;
+    m->ckpt_interval = c.ck;
+    if ((res = make_plan(m, c.schedule == 2 ? c.L : 0))) break;
+    std::vector<float> t;
+    for (int r = 0; r <= reps && !res; ++r) {
+      cudaEventRecord(e0, st);
+      res = enqueue(m, theta, n_sets, theta_per_series, ll, gr, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) res = GP_SS_ECUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) t.push_back(ms);  // the first run warms up
+    }
+    if (res) break;
+    std::sort(t.begin(), t.end());
+    const double med = t[t.size() / 2];
+    ++tried;
+    if (med < win_ms) {
+      win_ms = med;
+      win = c;
+    }
+  }
+  // apply the winner (or restore the old settings on failure)
+  const Cand &use = res ? saved : win;
+  m->schedule = use.schedule;
+  m->combine = use.combine;
+  m->ckpt_interval = use.ck;
+  gp_ss_status r2 = make_plan(m, use.schedule == 2 ? use.L : (res ? saved.L : 0));
+  if (!res) res = r2;
+  if (!res && best) {
+    best->schedule = win.schedule;
+    best->chunk_len = m->chunk_len;
+    best->chunk_combine = win.combine;
+    best->ckpt_interval = win.ck;
+    best->threads_per_series = m->max_chunks_per_series;
+    best->ms = win_ms;
+    best->n_tried = tried;
+  }
+  cudaFree(ll);
+  if (gr) cudaFree(gr);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return res;
 }
 
 gp_ss_status gp_ss_set_timing(gp_ss_model *m, int enable) {

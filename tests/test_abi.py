@@ -73,5 +73,6 @@ def test_host_validation_without_gpu(lib):
     assert _build(lib, [0.0], [1.0], terms=(1, 1, 1)) == 4
     # option values outside their ranges
     for bad in (gp._Options(32, 0, 0, 0, 12, 0, 0, 0), gp._Options(32, 0, 0, 0, 0, 0, 0, 2),
-                gp._Options(16, 0, 0, 0, 0, 0, 0, 0)):
+                gp._Options(16, 0, 0, 0, 0, 0, 0, 0), gp._Options(32, 4, 0, 0, 0, 0, 0, 0),
+                gp._Options(32, 0, 0, 0, 0, 0, 3, 0)):
         assert _build(lib, [0.0], [1.0], opts=bad) == 1

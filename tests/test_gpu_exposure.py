@@ -96,3 +96,33 @@ def test_time_shift_invariance_on_gpu(gp):
         a, b = wl.offsets[s], wl.offsets[s + 1]
         tot = d[a:b].sum()
         assert abs(tot) <= 1e-4 * np.abs(d[a:b]).sum(), (s, tot)
+
+
+@pytest.mark.parametrize("per_series", [True, False])
+def test_autograd_windows(gp, per_series):
+    if per_series:
+        wl = _f32(synth.c4(n_series=3, scale=0.02))
+        th = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
+    else:
+        wl = _f32(synth.c5(n=300, n_sets=4))
+        th = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
+    m = gp.Model.from_workload(wl, chunk_len=32)
+    win = torch.tensor(np.stack([wl.t_start, wl.t_end], axis=1), device="cuda",
+                       dtype=torch.float64, requires_grad=True)
+    thv = th.clone().requires_grad_(True)
+    ll = gp.loglik(m, thv, per_series=per_series, windows=win)
+    wts = torch.linspace(0.5, 1.5, ll.numel(), dtype=torch.float64, device="cuda")
+    (ll * wts).sum().backward()
+    _, g, dexp = m.loglik_grad(th, per_series=per_series, exposure=True)
+    w32 = wts.float()
+    if per_series:
+        sidx = m.measurement_series("cuda")
+        ref = w32[sidx][:, None] * dexp[0]
+        gref = w32[:, None] * g
+    else:
+        sidx = m.measurement_series("cuda")
+        coef = w32.view(th.shape[0], wl.n_series)[:, sidx]
+        ref = (coef[:, :, None] * dexp).sum(0)
+        gref = (w32[:, None] * g).view(th.shape[0], wl.n_series, -1).sum(1)
+    np.testing.assert_allclose(win.grad.cpu().numpy(), ref.double().cpu().numpy(), rtol=1e-6)
+    np.testing.assert_allclose(thv.grad.cpu().numpy(), gref.cpu().numpy(), rtol=1e-6)

@@ -98,7 +98,7 @@ def test_plain_fp64_matches_oracle_c1(gp):
     assert abs(ll[0] - ref[0]) <= 1e-9 * abs(ref[0]), (ll, ref)
 
 
-@pytest.mark.parametrize("schedule,chunk", [(1, 0), (2, 64), (2, 200), (0, 0)])
+@pytest.mark.parametrize("schedule,chunk", [(1, 0), (2, 64), (2, 200), (0, 0), (3, 0)])
 def test_fp32_batch_loglik(gp, schedule, chunk):
     wl = f32_theta(synth.c2(n_series=12, scale=0.08))
     m = gp.Model.from_workload(wl, schedule=schedule, chunk_len=chunk)
@@ -268,3 +268,29 @@ def test_numeric_failure_is_reported(gp):
     m.loglik(theta_dev(wl))
     torch.cuda.synchronize()
     assert m.last_error() == (-1, 0)
+
+
+def test_autotune_gradient(gp):
+    wl = f32_theta(synth.c4(n_series=6, scale=0.05))
+    m = gp.Model.from_workload(wl)
+    th = theta_dev(wl)
+    best = m.autotune(th, grad=True, reps=1)
+    assert best["schedule"] in (1, 2) and best["ckpt_interval"] in (16, 32, 64)
+    assert best["n_tried"] >= 10 and best["ms"] > 0
+    assert m.info["n_chunks"] >= 32 * wl.n_series
+    ll, g = m.loglik_grad(th)
+    ref_ll, ref_g = oracle_ll(wl, grad=True)
+    check_ll(ll.cpu().numpy(), ref_ll, counts_of(wl))
+    check_grad(g.cpu().numpy(), ref_g)
+
+
+def test_autotune_loglik(gp):
+    wl = f32_theta(synth.c2(n_series=12, scale=0.08))
+    m = gp.Model.from_workload(wl)
+    th = theta_dev(wl)
+    best = m.autotune(th, grad=False, reps=1)
+    assert best["schedule"] in (1, 2, 3)
+    check_ll(m.loglik(th).cpu().numpy(), oracle_ll(wl), counts_of(wl))
+    # a gradient call after a log-likelihood tuning still works
+    _, g = m.loglik_grad(th)
+    assert np.isfinite(g.cpu().numpy()).all()
