@@ -69,7 +69,10 @@ def workload(name):
 
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples every 50 ms, started before the warm-up (its own
+    start-up takes a while); ``stop`` keeps the samples whose timestamps fall
+    inside the timed window marked by ``mark``."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -77,6 +80,10 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.path = None
+        self.window = None
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def start(self):
         try:
@@ -97,28 +104,40 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        mhz, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         try:
+            import datetime
             for line in open(self.path):
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
+                if len(parts) < 10:
                     continue
                 try:
-                    mhz.append(float(parts[1]))
-                    mx = float(parts[2])
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((ts, float(parts[2]), float(parts[3]),
+                                 {nm for nm, v in zip(names, parts[6:10])
+                                  if v.lower() == "active"}))
                 except ValueError:
                     continue
-                for nm, v in zip(names, parts[5:9]):
-                    if v.lower() == "active":
-                        reasons.add(nm)
             os.unlink(self.path)
         except Exception:
             pass
-        if not mhz:
+        if not rows:
             return None
-        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(mhz)}
+        sel = rows
+        where = "all samples"
+        if self.window is not None:
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 - 0.02 <= r[0] <= t1 + 0.02]
+            if inside:
+                sel, where = inside, "timed window"
+            else:
+                # window shorter than the sampling period: the samples next to it
+                sel = sorted(rows, key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))[:2]
+                where = "nearest to the timed window"
+        reasons = set().union(*[r[3] for r in sel])
+        return {"sm_mhz": float(np.median([r[1] for r in sel])), "sm_max_mhz": sel[-1][2],
+                "reasons": sorted(reasons), "samples": len(sel), "samples_from": where}
 
 
 def oracle_sample_rate(wl, budget_s, n_proc, prefix_meas):
@@ -214,15 +233,22 @@ def run_ours(args):
     model = gp.Model.from_workload(wl, chunk_len=args.chunk_len)
     build_s = time.perf_counter() - t0
     theta = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
+    # the autotuner picks schedule, chunk length (threads per series) and the
+    # gradient's segment length on this workload (before the timed region)
+    tuned = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        tuned = model.autotune(theta, grad=True, reps=3)
+        tuned["tune_s"] = time.perf_counter() - t0
     n_out = model.info["n_series"]
     ll = torch.empty(n_out, dtype=torch.float64, device="cuda")
     g = torch.empty(n_out, model.n_params, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(max(args.warmup, 3)):
         model.loglik_grad(theta, out=ll, grad=g)
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
     model.set_timing(True)
     model.get_timing()
     if world > 1:
@@ -231,12 +257,14 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     n_launch0 = gp.launch_count()
+    w0 = time.time()
     e0.record(stream)
     for _ in range(args.steps):
         model.loglik_grad(theta, out=ll, grad=g)
     e1.record(stream)
     n_launches = gp.launch_count() - n_launch0
     torch.cuda.synchronize()
+    clocks.mark(w0, time.time())
     if world > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1) / args.steps
@@ -329,7 +357,8 @@ def run_ours(args):
             "config": {"workload": args.workload, "n_series": int(wl_full.n_series),
                        "n_meas": total_meas, "n_events": 2 * total_meas,
                        "state_dim": model.info["state_dim"], "n_params": model.n_params,
-                       "chunk_len": args.chunk_len, "n_chunks": model.info["n_chunks"],
+                       "chunk_len": (tuned or {}).get("chunk_len", args.chunk_len), "n_chunks": model.info["n_chunks"],
+                       "autotuned": tuned,
                        "l2": "inputs larger than L2 (event stream ~292 MB > 129 MB)",
                        "parallelism": f"series-sharded x{world}", "build_s": build_s},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
@@ -343,7 +372,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c4")
@@ -352,6 +381,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -240,6 +240,30 @@ GPSS_D void flag_error(int *err, int row, int code) {
   if (err) atomicMax(err + row, code);
 }
 
+// Asynchronous 16-byte global -> shared copy through L2 (cp.async.cg,
+// sm_80 and later), committed as groups; wait_group<N> returns once at most
+// N of this thread's groups are still in flight, and the thread then sees
+// its own copies.  Both addresses 16-byte aligned.
+GPSS_D void cp_async16(float4 *sdst, const float4 *gsrc) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 800
+  const unsigned a = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gsrc) : "memory");
+#else
+  *sdst = *gsrc;
+#endif
+}
+GPSS_D void cp_async_commit() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 800
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+#endif
+}
+template <int N>
+GPSS_D void cp_async_wait() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 800
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // Step-scalar tables, one warp per (hyperparameter row, term), FP64: lane k
 // builds Taylor coefficient k of the six series and their (a, beta)
@@ -1133,8 +1157,11 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   TermC<F> tc[S::NT];
   F s2;
   load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tc, s2);
-  // shared memory holds the warps' tables
+  // shared memory: the warps' tables, then two staging buffers per thread
+  // for the backward walk, stg[(buf (SG + NDG) + group) bs + thread] (float4)
   float4 *tab_slots = reinterpret_cast<float4 *>(sm);
+  const int bs = blockDim.x;
+  float4 *stg = tab_slots + (bs / 32) * (S::NT * TAB_TERM / 4) + threadIdx.x;
   const float4 *tab = stage_table<S::NT>(tabs, row, tab_slots + (threadIdx.x >> 5) * (S::NT * TAB_TERM / 4));
   const uint8_t flags = M.ch_flags[c];
   const bool first = flags & 1, last = flags & 2;
@@ -1225,45 +1252,49 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       }
       if (filter_blocks<S, F>(B, tag, q.x, q.y, q.z, s2, m, P, Sv, vv)) bad |= !(Sv > F(0));
     }
-    // backward walk; the earlier step's gap, tag, measurement record and
-    // cached scalars are loaded while the current step is processed.  The
-    // measurement index of event k (relative to m0) is the count of end
+    // backward walk.  The earlier step's replayed state and cached scalars
+    // are staged into shared memory by cp.async while the current step is
+    // processed; its gap, tag and measurement record are loaded one ahead.
+    // The measurement index of event k (relative to m0) is the count of end
     // events before k, tracked downwards from the replay's end.
+    auto stage = [&](int buf, int slot, int kk) {
+      float4 *dst = stg + (size_t)buf * (SG + NDG) * bs;
+#pragma unroll
+      for (int v = 0; v < SG; ++v) cp_async16(dst + v * bs, my + (size_t)(slot * SG + v) * rs);
+      if (dc) {
+        const float4 *src = dc + (size_t)kk * (32 * NDG);
+#pragma unroll
+        for (int v = 0; v < NDG; ++v) cp_async16(dst + (SG + v) * bs, src + 32 * v);
+      }
+      cp_async_commit();
+    };
     int k2 = k1 - 1;
     F dt_n = __ldg(M.dt + e0 + k2);
     uint8_t tag_n = __ldg(M.tag + e0 + k2);
     int mr = (int)(rd.mi - m0) - (tag_n & 1);
     float4 q_n = __ldg(M.meas + m0 + mr);
-    const float4 *dcb = dc ? dc + (size_t)k2 * (32 * NDG) : nullptr;
-    if (dcb) dcache_load<S::NT>(dcb, nx);
+    stage(0, k2 - k0, k2);
     for (; k2 >= k0; --k2) {
-      const int slot = k2 - k0;
+      const int slot = k2 - k0, buf = (k1 - 1 - k2) & 1;
       const F dt = dt_n;
       const uint8_t tag = tag_n;
       const float4 q = q_n;
-      Disc<F> dv[S::NT];
-      if (dcb) {
-#pragma unroll
-        for (int t = 0; t < S::NT; ++t) dv[t] = dcache_term<S::NT>(nx, t);
-      } else {
-#pragma unroll
-        for (int t = 0; t < S::NT; ++t) dv[t] = discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4));
-      }
       if (k2 > k0) {
         dt_n = __ldg(M.dt + e0 + k2 - 1);
         tag_n = __ldg(M.tag + e0 + k2 - 1);
         mr -= tag_n & 1;
         q_n = __ldg(M.meas + m0 + mr);
-        if (dcb) {
-          dcb -= 32 * NDG;
-          dcache_load<S::NT>(dcb, nx);
-        }
+        stage(buf ^ 1, slot - 1, k2 - 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
       }
+      const float4 *sb = stg + (size_t)buf * (SG + NDG) * bs;
       {
         float r[4 * SG];
 #pragma unroll
         for (int v = 0; v < SG; ++v) {
-          const float4 g4 = my[(size_t)(slot * SG + v) * rs];
+          const float4 g4 = sb[v * bs];
           r[4 * v] = g4.x;
           r[4 * v + 1] = g4.y;
           r[4 * v + 2] = g4.z;
@@ -1273,6 +1304,22 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
         for (int i = 0; i < D; ++i) m[i] = r[i];
 #pragma unroll
         for (int i = 0; i < S::NP; ++i) P[i] = r[D + i];
+      }
+      Disc<F> dv[S::NT];
+      if (dc) {
+#pragma unroll
+        for (int v = 0; v < NDG; ++v) {
+          const float4 g4 = sb[(SG + v) * bs];
+          nx[4 * v] = g4.x;
+          nx[4 * v + 1] = g4.y;
+          nx[4 * v + 2] = g4.z;
+          nx[4 * v + 3] = g4.w;
+        }
+#pragma unroll
+        for (int t = 0; t < S::NT; ++t) dv[t] = dcache_term<S::NT>(nx, t);
+      } else {
+#pragma unroll
+        for (int t = 0; t < S::NT; ++t) dv[t] = discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4));
       }
       F g_dt, g_w;
       reverse_event<S>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab, dv, gdt != nullptr, g_dt, g_w);
@@ -1550,7 +1597,9 @@ cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int pe
                         const float *dcache, int ck, float *gdt, float *gwe, cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
   if (ck < 2 || ck > 64 || (ck & 1)) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)(GRAD_BS / 32) * S::NT * TAB_TERM * sizeof(float);
+  const int SG = (S::D + S::NP + 3) / 4, NDG = DcW<S::NT>::G;
+  const size_t smem = (size_t)(GRAD_BS / 32) * S::NT * TAB_TERM * sizeof(float) +
+                      (size_t)2 * (SG + NDG) * GRAD_BS * sizeof(float4);
   k_grad<S><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
       M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err, tabs, rbuf, dcache, ck,
       gdt, gwe);
