@@ -230,7 +230,7 @@ def run_ours(args):
                                                max(1, min(os.cpu_count() or 1, 16)), 200)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     t0 = time.perf_counter()
-    model = gp.Model.from_workload(wl, chunk_len=args.chunk_len)
+    model = gp.Model.from_workload(wl, chunk_len=args.chunk_len, ckpt_interval=args.ckpt_interval)
     build_s = time.perf_counter() - t0
     theta = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
     # the autotuner picks schedule, chunk length (threads per series) and the
@@ -377,6 +377,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c4")
     ap.add_argument("--chunk-len", type=int, default=0)
+    ap.add_argument("--ckpt-interval", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

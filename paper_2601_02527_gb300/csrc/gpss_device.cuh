@@ -368,32 +368,38 @@ GPSS_HD void taylor_coeffs(T a, T beta, T (&g)[6][TAB_NTAY]) {
   }
 }
 
-// Coefficient k < TAB_NTAY of the six Taylor series (same definitions as
-// taylor_coeffs; one table-building lane per coefficient).
+// The division-free form the table kernel uses.  c[0..NCF] (NCF = TAB_NTAY
+// + 2) receives f's Taylor coefficients by the recurrence, with rcp[i] = 1/i;
+// then coefficient k of the six series follows from c, e_n = c_n / (n+1)
+// and p_n = n c_n (same definitions as taylor_coeffs).
+constexpr int TAB_NCF = TAB_NTAY + 2;
+
 template <class T>
-GPSS_HD void taylor_coeff_k(T a, T beta, int k, T (&g)[6]) {
-  constexpr int NCF = TAB_NTAY + 2;
-  T c[NCF + 1];
+GPSS_HD void taylor_c(T a, T beta, const double *rcp, T *c) {
   const T w2 = beta + a * a;
   c[0] = a * 0.0;
   c[1] = c[0] + 1.0;
   c[2] = -a;
-  for (int n = 1; n + 2 <= k + 2 && n + 2 <= NCF; ++n)
-    c[n + 2] = -(a * (2.0 * (n + 1)) * c[n + 1] + w2 * c[n]) / (double)((n + 2) * (n + 1));
-  g[0] = c[k + 1];
-  g[1] = c[k + 1] * (double)(k + 1);
-  g[2] = c[k + 1] / (double)(k + 2);
+  for (int n = 1; n + 2 <= TAB_NCF; ++n)
+    c[n + 2] = -(a * (2.0 * (n + 1)) * c[n + 1] + w2 * c[n]) * (rcp[n + 2] * rcp[n + 1]);
+}
+
+template <class T>
+GPSS_HD void taylor_coeff_pre(const T *c, const T *e, const T *p, const double *rcp, int k,
+                              T (&g)[6]) {
   T s1 = c[0], s2 = c[0], s3 = c[0];
   for (int n = 1; n <= k + 1; ++n) {
     const int m = k + 2 - n;
-    const T pp = c[n] * c[m];
-    s1 = s1 + pp;
-    s2 = s2 + pp * (double)(n * m);
-    s3 = s3 + pp / (double)((n + 1) * (m + 1));
+    s1 = s1 + c[n] * c[m];
+    s2 = s2 + p[n] * p[m];
+    s3 = s3 + e[n] * e[m];
   }
-  g[3] = s1 / (double)(k + 3);
-  g[4] = s2 / (double)(k + 1);
-  g[5] = s3 / (double)(k + 5);
+  g[0] = c[k + 1];
+  g[1] = c[k + 1] * (double)(k + 1);
+  g[2] = c[k + 1] * rcp[k + 2];
+  g[3] = s1 * rcp[k + 3];
+  g[4] = s2 * rcp[k + 1];
+  g[5] = s3 * rcp[k + 5];
 }
 
 // Range of the table: t in [0, T], T = 1.01 sqrt(XT2 / w2).
@@ -408,9 +414,12 @@ GPSS_HD double table_range(double w2) {
 // s_{n,j+1} = -4 (n+j)(n-j) / ((2j+1)(2j+2)) s_{n,j} (integers).
 struct EconMap {
   double m[TAB_NC][TAB_NTAY];
+  double rcp[2 * TAB_NTAY + 8];  // 1/i (rcp[0] unused)
 };
 
 GPSS_HD void econ_map(EconMap &E) {
+  E.rcp[0] = 0.0;
+  for (int i = 1; i < 2 * TAB_NTAY + 8; ++i) E.rcp[i] = 1.0 / (double)i;
   for (int col = 0; col < TAB_NTAY; ++col) {
     double d[TAB_NTAY];
     for (int k = 0; k < TAB_NTAY; ++k) d[k] = (k == col) ? 1.0 : 0.0;

@@ -265,9 +265,12 @@ GPSS_D void cp_async_wait() {
 }
 
 // ---------------------------------------------------------------------------
-// Step-scalar tables, one warp per (hyperparameter row, term), FP64: lane k
-// builds Taylor coefficient k of the six series and their (a, beta)
-// tangents, then lanes k < TAB_NC apply row k of the economisation map.
+// Step-scalar tables, one warp per (hyperparameter row, term), FP64 with
+// (a, beta) tangents.  Lane 0 runs the recurrence of f's Taylor coefficients
+// c_n; lanes form the pre-scaled c_n/(n+1) and n c_n; lane k sums the
+// products giving Taylor coefficient k of the six series (definitions as in
+// taylor_coeffs); all lanes then share the outputs of the economisation map.
+// Divisions by integers use the reciprocal table of E (FP64 division is slow).
 // ---------------------------------------------------------------------------
 constexpr int TABLE_WARPS = 4;
 
@@ -276,7 +279,10 @@ __global__ void __launch_bounds__(32 * TABLE_WARPS) k_tables(const float *__rest
                                                             int n_rows, int n_params, int kind0,
                                                             int kind1, float *__restrict__ tab,
                                                             EconMap E) {
-  __shared__ Dual2<double> sg[TABLE_WARPS][TAB_NTAY][6];
+  using DD = Dual2<double>;
+  constexpr int NCF = TAB_NCF;  // c_0 .. c_NCF
+  __shared__ DD sc[TABLE_WARPS][NCF + 1], se[TABLE_WARPS][NCF + 1], sf[TABLE_WARPS][NCF + 1];
+  __shared__ DD sg[TABLE_WARPS][6][TAB_NTAY];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rt = blockIdx.x * TABLE_WARPS + w;
   if (rt >= n_rows * NT) return;  // whole warps leave together
@@ -285,22 +291,38 @@ __global__ void __launch_bounds__(32 * TABLE_WARPS) k_tables(const float *__rest
   TermC<double> tc[NT];
   double s2;
   load_terms<NT, double>(theta + (size_t)row * n_params, kinds, tc, s2);
-  const Dual2<double> a = mk(tc[t].a, 1.0, 0.0), beta = mk(tc[t].beta, 0.0, 1.0);
-  if (lane < TAB_NTAY) {
-    Dual2<double> g[6];
-    taylor_coeff_k<Dual2<double>>(a, beta, lane, g);
-    for (int j = 0; j < 6; ++j) sg[w][lane][j] = g[j];
+  const DD a = mk(tc[t].a, 1.0, 0.0), beta = mk(tc[t].beta, 0.0, 1.0);
+  if (lane == 0) taylor_c<DD>(a, beta, E.rcp, &sc[w][0]);
+  __syncwarp();
+  for (int n = lane; n <= NCF; n += 32) {
+    const DD c = sc[w][n];
+    se[w][n] = c * E.rcp[n + 1];
+    sf[w][n] = c * (double)n;
   }
   __syncwarp();
-  if (lane >= TAB_NC) return;
+  if (lane < TAB_NTAY) {
+    DD g[6];
+    taylor_coeff_pre<DD>(&sc[w][0], &se[w][0], &sf[w][0], E.rcp, lane, g);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) sg[w][j][lane] = g[j];
+  }
+  __syncwarp();
   const double rng = table_range(tc[t].w2);
-  float *r = tab + ((size_t)rt * TAB_NC + lane) * TAB_W;
-  for (int j = 0; j < TAB_W; ++j) r[j] = 0.f;
-  for (int j = 0; j < 6; ++j) {
-    const Dual2<double> e = econ_apply<Dual2<double>>(E, lane, rng, &sg[w][0][j], 6);
+  float *base = tab + (size_t)rt * TAB_NC * TAB_W;
+  for (int o = lane; o < 6 * TAB_NC; o += 32) {
+    const int j = o / TAB_NC, k = o % TAB_NC;
+    const DD e = econ_apply<DD>(E, k, rng, &sg[w][j][0], 1);
+    float *r = base + (size_t)k * TAB_W;
     r[j] = (float)e.v;
     r[8 + j] = (float)e.da;
     r[16 + j] = (float)e.db;
+  }
+  for (int o = lane; o < TAB_NC * 6; o += 32) {
+    const int k = o / 6, p = o % 6;  // the pads: columns 6, 7 of each block of 8
+    float *r = base + (size_t)k * TAB_W;
+    if (p < 2) r[6 + p] = 0.f;
+    else if (p < 4) r[14 + p - 2] = 0.f;
+    else r[22 + p - 4] = 0.f;
   }
 }
 

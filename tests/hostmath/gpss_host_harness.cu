@@ -191,22 +191,36 @@ void hh_boundary_adjoint(int shape, const float *m, const float *P, const float 
   else adj_s<Shape<2, 3, 0>>(m, P, eta, J, lam, Lam);
 }
 
-// coefficient k of the six Taylor series: one-index generator (the one the
-// table kernel's lanes run) vs the full generator
+// coefficient k of the six Taylor series: the division-free per-lane form
+// the table kernel runs vs the full generator
 double hh_taylor_k_check(double a, double beta) {
-  Dual2<double> g[6][TAB_NTAY];
-  taylor_coeffs<Dual2<double>>(mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), g);
-  double worst = 0.0;
+  using DD = Dual2<double>;
+  DD g[6][TAB_NTAY];
+  taylor_coeffs<DD>(mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), g);
+  EconMap E;
+  econ_map(E);
+  DD c[TAB_NCF + 1], e[TAB_NCF + 1], p[TAB_NCF + 1];
+  taylor_c<DD>(mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), E.rcp, c);
+  for (int n = 0; n <= TAB_NCF; ++n) {
+    e[n] = c[n] * E.rcp[n + 1];
+    p[n] = c[n] * (double)n;
+  }
+  // error of every coefficient relative to the largest coefficient of the
+  // same series and component (cancelling sums can leave exact zeros)
+  double worst = 0.0, mx[6][3] = {};
+  for (int k = 0; k < TAB_NTAY; ++k)
+    for (int j = 0; j < 6; ++j) {
+      mx[j][0] = std::fmax(mx[j][0], std::fabs(g[j][k].v));
+      mx[j][1] = std::fmax(mx[j][1], std::fabs(g[j][k].da));
+      mx[j][2] = std::fmax(mx[j][2], std::fabs(g[j][k].db));
+    }
   for (int k = 0; k < TAB_NTAY; ++k) {
-    Dual2<double> h[6];
-    taylor_coeff_k<Dual2<double>>(mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), k, h);
+    DD h[6];
+    taylor_coeff_pre<DD>(c, e, p, E.rcp, k, h);
     for (int j = 0; j < 6; ++j) {
       const double d[3] = {h[j].v - g[j][k].v, h[j].da - g[j][k].da, h[j].db - g[j][k].db};
-      const double r[3] = {g[j][k].v, g[j][k].da, g[j][k].db};
-      for (int q = 0; q < 3; ++q) {
-        const double e = std::fabs(d[q]) / (std::fabs(r[q]) + 1e-300);
-        if (d[q] != 0.0 && e > worst) worst = e;
-      }
+      for (int q = 0; q < 3; ++q)
+        if (mx[j][q] > 0.0) worst = std::fmax(worst, std::fabs(d[q]) / mx[j][q]);
     }
   }
   return worst;

@@ -126,7 +126,7 @@ def test_economised_tables_match_taylor(hh, w0, q):
 @pytest.mark.parametrize("w0,q", CASES)
 def test_taylor_generators_agree(hh, w0, q):
     a, beta = ab(w0, q)
-    assert hh.hh_taylor_k_check(a, beta) <= 1e-13
+    assert hh.hh_taylor_k_check(a, beta) <= 1e-14
 
 
 @pytest.mark.parametrize("D", [3, 5, 6, 7])
