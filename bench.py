@@ -31,17 +31,26 @@ sys.path.insert(0, ROOT)
 METRIC = "measurements/sec for loglik+grad (batched FP32 vs plain FP64 filter, 1 GB300)"
 UNIT = "measurements/s"
 
-# FP32 FLOPs per event that the method itself needs for one loglik+grad pass
-# of the dominant kernel (the reverse-time gradient): the forward filter once
-# plus its reverse sweep, excluding the recomputation passes.  Taken from ncu
-# instruction counts (see profiles/); used for roofline.achieved.
-ALG_FLOPS_PER_EVENT = {"c4": 3600.0}
-# Algorithmic bytes per measurement the gradient kernel must read: two events
-# (4 B gap + 1 B tag each) and one 16 B measurement record, read on the
-# forward pass and again on the reverse sweep, plus checkpoint traffic.
-ALG_BYTES_PER_MEAS = {"c4": 2 * (2 * 5 + 16)}
+# Dominant kernel (k_grad, the reverse-time gradient): FP32 FLOPs per event it
+# executes (fadd + fmul + 2 ffma, thread-level, predicated-on; the segment
+# replay included), counted by ncu on the c4 shape -- 512 of the 1024 series,
+# chunk length 256, segments of 64 (workload c4h; profiles/k_grad_c4_ncu.md).
+ALG_FLOPS_PER_EVENT = {"c4": 1576.0}
+# DRAM bytes (read + write) per event of that k_grad launch, same capture;
+# the traffic grows with the events (replay records, cached step scalars,
+# partial elements, event stream), so a full launch is this x its events.
+# Valid for the captured configuration only (chunk length 256, segments of 64).
+TRAFFIC_PER_EVENT = {"c4": (346.8, 256, 64)}
 FP32_LANES_PER_SM = 128
 N_SMS = 152
+
+
+def alg_bytes_per_meas(ck):
+    """Algorithmic HBM bytes per measurement of one loglik+grad pass: two gaps
+    (8 B), two tags (2 B) and y, yerr^2, 1/delta (12 B) read by the forward
+    pass and again by the reverse sweep, plus a filter state (m and packed P,
+    27 floats at state dimension 6) written and read back every ck events."""
+    return 2 * 22 + 2 * 4 * 27 * 2 / ck
 
 
 def load_peaks():
@@ -63,6 +72,8 @@ def workload(name):
         return synth.c3()
     if name == "c5":
         return synth.c5()
+    if name == "c4h":  # 512 series of the c4 recipe (profiling captures)
+        return synth.c4(n_series=512)
     if name == "c4s":  # small variant for quick checks
         return synth.c4(n_series=64, scale=0.25)
     raise ValueError(name)
@@ -290,17 +301,26 @@ def run_ours(args):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
     n_events = 2 * wl.n_meas
-    alg_flops = ALG_FLOPS_PER_EVENT.get(args.workload, 3600.0) * n_events
-    achieved = alg_flops / (dom_avg / 1e3) / 1e12
-    alg_bytes = ALG_BYTES_PER_MEAS.get(args.workload, 52) * wl.n_meas
-    hbm_ach = alg_bytes / (dom_avg / 1e3) / 1e9
-    roofline = {"bound": "alu", "kernel": f"k_grad ({dom})" if dom == "grad" else dom,
+    # the gradient phase is k_grad alone; its per-launch time from the
+    # phase events recorded on the launching stream inside the timed region
+    fpe = ALG_FLOPS_PER_EVENT.get(args.workload)
+    achieved = fpe * n_events / (dom_avg / 1e3) / 1e12 if fpe and dom == "grad" else None
+    ck_used = (tuned or {}).get("ckpt_interval", args.ckpt_interval or 32)
+    L_used = (tuned or {}).get("chunk_len", args.chunk_len or 256)
+    tr = TRAFFIC_PER_EVENT.get(args.workload)
+    traffic = tr[0] * n_events if tr and (L_used, ck_used) == (tr[1], tr[2]) else None
+    step_bytes = alg_bytes_per_meas(ck_used) * total_meas
+    roofline = {"bound": "alu", "kernel": "k_grad" if dom == "grad" else dom,
                 "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None,
+                "frac": achieved / alu_peak if achieved else None, "traffic": traffic,
                 "peak_source": f"FP32 FMA: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                               f"{sm_mhz:.0f} MHz",
-                "hbm_view": {"achieved_gbs": hbm_ach, "peak_gbs": peaks.get("hbm_gbs"),
-                             "frac": hbm_ach / peaks.get("hbm_gbs", 6800.0),
+                               f"{sm_mhz:.0f} MHz (nominal max clock; no measured FP32 peak)",
+                "kernel_ms_per_launch": dom_avg,
+                "hbm_view": {"whole_step_gbs": step_bytes / (ms / 1e3) / 1e9,
+                             "bytes_per_meas": alg_bytes_per_meas(ck_used),
+                             "peak_gbs": peaks.get("hbm_gbs"),
+                             "frac": step_bytes / (ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                             "k_grad_dram_gbs": traffic / (dom_avg / 1e3) / 1e9 if traffic else None,
                              "peak_source": src},
                 "phase_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in phases.items()
                                       if v[1]}}
