@@ -64,6 +64,8 @@ def load_peaks():
 
 def workload(name):
     import synth
+    if name == "c1":
+        return synth.c1()
     if name == "c4":
         return synth.c4()
     if name == "c2":
@@ -389,6 +391,60 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_accuracy(args):
+    """FP32 error against FP64 for every workload configuration (one JSON line
+    each): log-likelihood relative error of the FP32 path (autotuned) against
+    the plain FP64 GPU filter on every output row (c1: the FP64 path against
+    the oracle), and the FP32 gradient against the oracle's complex-step
+    gradient on sampled series (c2 has no gradient in its configuration;
+    c3's one series and c5's 256 sets are too long for the oracle's gradient:
+    c5 is checked against central differences of the FP64 filter in the
+    tests).  Slow: the FP64 filter runs one thread per series."""
+    import torch
+
+    import oracle
+    import paper_2601_02527_gb300 as gp
+    from paper_2601_02527_gb300 import build as gbuild
+    gbuild.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+    names = args.accuracy_workloads.split(",")
+    for name in names:
+        wl = workload(name)
+        wl.theta = wl.theta.astype(np.float32).astype(np.float64)
+        per = bool(wl.theta_per_series)
+        th = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
+        counts = np.diff(wl.offsets)
+        out = {"workload": name, "n_series": int(wl.n_series), "n_meas": int(wl.n_meas),
+               "n_sets": int(wl.theta.shape[0])}
+        m64 = gp.Model.from_workload(wl, precision=64)
+        l64 = m64.loglik(th, per_series=per).cpu().numpy()
+        if name == "c1":
+            ref = oracle.loglik_workload(wl)
+            out["fp64_vs_oracle_max_rel"] = float(np.max(np.abs(l64 - ref) / np.abs(ref)))
+        else:
+            m = gp.Model.from_workload(wl)
+            grad = name in ("c4", "c5")
+            tuned = m.autotune(th, per_series=per, grad=grad, reps=1)
+            out["autotuned"] = {k: tuned[k] for k in ("schedule", "chunk_len", "ckpt_interval")}
+            l32 = (m.loglik_grad(th, per_series=per)[0] if grad else
+                   m.loglik(th, per_series=per)).cpu().numpy()
+            nrow = np.tile(counts, len(l32) // len(counts))
+            rel = np.abs(l32 - l64) / np.abs(l64)
+            out["fp32_vs_fp64_loglik_max_rel"] = float(rel.max())
+            out["fp32_vs_fp64_loglik_max_abs_per_meas"] = float(np.max(np.abs(l32 - l64) / nrow))
+            if name == "c4":
+                order = np.argsort(counts)
+                idx = np.unique(order[np.linspace(0, len(order) - 1, 8).astype(int)])
+                _, g = m.loglik_grad(th)
+                g = g.cpu().numpy()[idx]
+                _, rg = oracle.loglik_workload(wl, series_idx=idx, grad=True, processes=8)
+                out["fp32_grad_vs_oracle_max_rel_of_max"] = float(
+                    np.max(np.abs(g - rg) / np.abs(rg).max(axis=1, keepdims=True)))
+                out["grad_sampled_series"] = [int(i) for i in idx]
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -403,7 +459,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="print FP32-vs-FP64 errors per workload instead of timing")
+    ap.add_argument("--accuracy-workloads", default="c1,c2,c3,c4,c5")
     args = ap.parse_args()
+    if args.accuracy:
+        run_accuracy(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

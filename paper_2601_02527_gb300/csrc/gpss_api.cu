@@ -145,6 +145,9 @@ struct gp_ss_model {
   // chunk) lane-steps; d_w_doff[w] = lane-steps before warp w, [n_w] = total
   int64_t *d_w_doff = nullptr;
   int64_t dcache_steps = 0;
+  // per-call scratch comes from this model's stream-ordered pool, which keeps
+  // freed memory reserved (no unmapping and re-mapping at every synchronise)
+  cudaMemPool_t pool = nullptr;
   // device error flags of the last call
   mutable std::mutex mu;
   mutable int *d_err = nullptr;
@@ -209,6 +212,10 @@ void free_model_buffers(gp_ss_model *m) {
                  m->d_ch_flags, m->d_w_doff, m->d_err};
   for (void *p : dev)
     if (p) cudaFree(p);
+  if (m->pool) {
+    cudaMemPoolDestroy(m->pool);
+    m->pool = nullptr;
+  }
   void *hst[] = {m->h_dt, m->h_tag, m->h_meas};
   for (void *p : hst)
     if (p) {
@@ -478,6 +485,17 @@ struct PhaseTimer {
   }
 };
 
+// Scratch from the model's pool; the default pool while the stream is
+// being captured into a graph (graph allocations have their own pool) or
+// when the model has no pool.
+cudaError_t scratch_alloc(const gp_ss_model *m, void **p, size_t bytes, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (m->pool && cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
+      cs == cudaStreamCaptureStatusNone)
+    return cudaMallocFromPoolAsync(p, bytes, m->pool, st);
+  return cudaMallocAsync(p, bytes, st);
+}
+
 gp_ss_status check_call(const gp_ss_model *m, const float *theta, int n_sets, int per_series,
                         const void *out) {
   if (!m || !theta || !out || n_sets <= 0) return GP_SS_EINVAL;
@@ -515,7 +533,7 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
   bool tree = m->combine != 1;
   std::vector<void *> bufs;
   auto grab = [&](void **p, size_t bytes) -> bool {
-    if (cudaMallocAsync(p, std::max<size_t>(bytes, 16), st) != cudaSuccess) {
+    if (scratch_alloc(m, p, std::max<size_t>(bytes, 16), st) != cudaSuccess) {
       *p = nullptr;
       return false;
     }
@@ -836,6 +854,20 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
     if (!st) st = dev_upload(&m->d_meas64, meas64.data(), 3 * nM);
   }
   if (!st) st = make_plan(m, o.chunk_len);
+  if (!st) {
+    cudaMemPoolProps pp = {};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.handleTypes = cudaMemHandleTypeNone;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = m->device;
+    if (cudaMemPoolCreate(&m->pool, &pp) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(m->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      m->pool = nullptr;
+      cudaGetLastError();
+    }
+  }
   if (st) {
     free_model_buffers(m);
     delete m;
@@ -944,9 +976,9 @@ gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *m, const float *theta_hos
   float *d_theta = nullptr, *d_grad = nullptr;
   double *d_ll = nullptr;
   const size_t nth = (size_t)n_sets * m->n_params;
-  if (cudaMallocAsync((void **)&d_theta, nth * sizeof(float), st) ||
-      cudaMallocAsync((void **)&d_ll, (size_t)n_out * sizeof(double), st) ||
-      cudaMallocAsync((void **)&d_grad, (size_t)n_out * m->n_params * sizeof(float), st))
+  if (scratch_alloc(m, (void **)&d_theta, nth * sizeof(float), st) ||
+      scratch_alloc(m, (void **)&d_ll, (size_t)n_out * sizeof(double), st) ||
+      scratch_alloc(m, (void **)&d_grad, (size_t)n_out * m->n_params * sizeof(float), st))
     return GP_SS_ENOMEM;
   gp_ss_status res = GP_SS_OK;
   if (reupload_events) {
