@@ -65,6 +65,11 @@ def _load():
             P(ctypes.c_double), ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_int64),
             P(ctypes.c_double), P(ctypes.c_double)]
         lib.gpss_oracle_exposure_grad.restype = ctypes.c_int
+        lib.gpss_oracle_condition.argtypes = [
+            P(ctypes.c_int32), ctypes.c_int64, P(ctypes.c_double), P(ctypes.c_int32),
+            P(ctypes.c_int32), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+            P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double)]
+        lib.gpss_oracle_condition.restype = ctypes.c_int
         lib.gpss_oracle_discretize.argtypes = [
             P(ctypes.c_int32), P(ctypes.c_double), ctypes.c_double, P(ctypes.c_double),
             P(ctypes.c_double), P(ctypes.c_double)]
@@ -210,6 +215,42 @@ def exposure_grad_events(terms, layout, ev, theta, n_slots=None):
     if rc != 0:
         raise RuntimeError(f"oracle filter failed with code {rc}")
     return d_ts, d_te
+
+
+def condition_events(terms, layout, ev, theta, n_slots=None):
+    """Integrated RTS smoother (Eqs. rts, integrated_rts): conditioned mean
+    and variance of every measurement's exposure average, in the series'
+    measurement order."""
+    lib = _load()
+    n_slots = ev["n_slots"] if n_slots is None else n_slots
+    spec = spec_array(terms, layout, n_slots)
+    theta = np.ascontiguousarray(theta, np.float64)
+    n_ev = len(ev["t"])
+    me = np.zeros(n_ev)
+    ve = np.zeros(n_ev)
+    arr = {k: np.ascontiguousarray(ev[k]) for k in ("t", "kind", "slot", "y", "r0", "invd")}
+    rc = lib.gpss_oracle_condition(
+        _ptr(spec, ctypes.c_int32), n_ev, _ptr(arr["t"], ctypes.c_double),
+        _ptr(arr["kind"], ctypes.c_int32), _ptr(arr["slot"], ctypes.c_int32),
+        _ptr(arr["y"], ctypes.c_double), _ptr(arr["r0"], ctypes.c_double),
+        _ptr(arr["invd"], ctypes.c_double), _ptr(theta, ctypes.c_double),
+        _ptr(me, ctypes.c_double), _ptr(ve, ctypes.c_double))
+    if rc != 0:
+        raise RuntimeError(f"oracle smoother failed with code {rc}")
+    n = n_ev // 2
+    mean = np.zeros(n)
+    var = np.zeros(n)
+    end = ev["kind"] == 1
+    mean[ev["meas"][end]] = me[end]
+    var[ev["meas"][end]] = ve[end]
+    return mean, var
+
+
+def condition(terms, layout, t_start, t_end, y, yerr, theta, instrument=None, n_slots=None):
+    """Oracle conditioned (mean, variance) of each measurement's exposure
+    average given all the series' data."""
+    ev = events(t_start, t_end, y, yerr, instrument)
+    return condition_events(terms, layout, ev, theta, n_slots=n_slots)
 
 
 def exposure_grad(terms, layout, t_start, t_end, y, yerr, theta, instrument=None, n_slots=None):

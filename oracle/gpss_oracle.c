@@ -209,3 +209,216 @@ int gpss_oracle_exposure_grad(const int32_t *spec, int64_t n_ev, const double *t
   free(ic);
   return rc;
 }
+
+/* ---- integrated RTS smoother (real arithmetic only) ---- */
+
+/* Solve A X = B for X (n x n, row-major), A n x n, by Gauss-Jordan with
+ * partial pivoting; A and B are overwritten (B becomes X).  Returns 0, or 1
+ * if A is singular to working precision. */
+static int solve_nn(int n, double *A, double *B) {
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(A[r * n + c]) > fabs(A[p * n + c])) p = r;
+    if (A[p * n + c] == 0.0) return 1;
+    if (p != c)
+      for (int j = 0; j < n; ++j) {
+        double t = A[c * n + j];
+        A[c * n + j] = A[p * n + j];
+        A[p * n + j] = t;
+        t = B[c * n + j];
+        B[c * n + j] = B[p * n + j];
+        B[p * n + j] = t;
+      }
+    const double inv = 1.0 / A[c * n + c];
+    for (int j = 0; j < n; ++j) {
+      A[c * n + j] *= inv;
+      B[c * n + j] *= inv;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c || A[r * n + c] == 0.0) continue;
+      const double f = A[r * n + c];
+      for (int j = 0; j < n; ++j) {
+        A[r * n + j] -= f * A[c * n + j];
+        B[r * n + j] -= f * B[c * n + j];
+      }
+    }
+  }
+  return 0;
+}
+
+/* Conditioned mean and variance of every measurement's exposure average
+ * given all the series' data: the filter of gpss_oracle_loglik keeping the
+ * predicted (m-, P-) and filtered (m, P) state of every event, then the RTS
+ * recursion backwards from the last event (smoothed = filtered there):
+ *   end state k:   G = P_k A_k^T (P-_{k+1})^-1, smoothed m^_k, P^_k from the
+ *                  filtered (m_k, P_k)                        (Eq. rts);
+ *   start state k: G = P-_k (A_k R_k)^T (P-_{k+1})^-1, from the pre-reset
+ *                  (m-_k, P-_k)                    (Eq. integrated_rts);
+ *   m^_k = base + G (m^_{k+1} - m-_{k+1}),
+ *   P^_k = base + G (P^_{k+1} - P-_{k+1}) G^T,
+ * with A_k the transition from event k to k+1.  At each end event (output
+ * in event order) mean = H m^, var = H P^ H^T, H = e_z / delta.  Returns 0,
+ * or 5 if some P-_{k+1} is singular. */
+int gpss_oracle_condition(const int32_t *spec, int64_t n_ev, const double *t_ev,
+                          const int32_t *kind, const int32_t *slot, const double *y_ev,
+                          const double *r0_ev, const double *invd_ev, const double *theta,
+                          double *mean_ev, double *var_ev) {
+  model_t M;
+  if (parse_spec(spec, &M)) return 1;
+  const int D = M.dim, DD = D * D;
+  double w0[MAXT], q[MAXT], var[MAXT], s2;
+  double F[MAXD * MAXD], LQL[MAXD * MAXD], Phi[MAXD * MAXD], Qd[MAXD * MAXD];
+  term_params_r(&M, theta, w0, q, var, &s2);
+  build_F_r(&M, w0, q, var, F, LQL);
+  const size_t n = (size_t)(n_ev > 0 ? n_ev : 1);
+  double *mp = malloc(sizeof(double) * n * D), *Pp = malloc(sizeof(double) * n * DD);
+  double *mf = malloc(sizeof(double) * n * D), *Pf = malloc(sizeof(double) * n * DD);
+  if (!mp || !Pp || !mf || !Pf) {
+    free(mp);
+    free(Pp);
+    free(mf);
+    free(Pf);
+    return 4;
+  }
+  int rc = 0;
+  /* forward: predicted and filtered states (Joseph-form update as in the filter) */
+  double m[MAXD], P[MAXD * MAXD], T[MAXD * MAXD], A[MAXD * MAXD], h[MAXD], u[MAXD], K[MAXD];
+  initial_cov_r(&M, w0, var, P);
+  for (int i = 0; i < D; ++i) m[i] = 0;
+  double tprev = n_ev > 0 ? t_ev[0] : 0.0;
+  for (int64_t k = 0; k < n_ev && !rc; ++k) {
+    const double dt = t_ev[k] - tprev;
+    tprev = t_ev[k];
+    if (dt < 0) {
+      rc = 2;
+      break;
+    }
+    discretize_r(&M, F, LQL, dt, Phi, Qd);
+    double mt[MAXD];
+    for (int i = 0; i < D; ++i) {
+      double acc = 0;
+      for (int j = 0; j < D; ++j) acc += Phi[i * D + j] * m[j];
+      mt[i] = acc;
+    }
+    memcpy(m, mt, sizeof(double) * D);
+    matmul_r(D, Phi, P, T);
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j <= i; ++j) {
+        double acc = 0;
+        for (int kk = 0; kk < D; ++kk) acc += T[i * D + kk] * Phi[j * D + kk];
+        P[i * D + j] = acc + 0.5 * (Qd[i * D + j] + Qd[j * D + i]);
+        P[j * D + i] = P[i * D + j];
+      }
+    memcpy(mp + k * D, m, sizeof(double) * D);
+    memcpy(Pp + k * DD, P, sizeof(double) * DD);
+    const int sj = slot[k];
+    if (kind[k] == 0) {
+      for (int t = 0; t < M.n_zper; ++t) {
+        const int z = zindex(&M, sj, t);
+        m[z] = 0;
+        for (int i = 0; i < D; ++i) P[z * D + i] = P[i * D + z] = 0;
+      }
+    } else {
+      for (int i = 0; i < D; ++i) h[i] = 0;
+      for (int t = 0; t < M.n_zper; ++t) h[zindex(&M, sj, t)] = invd_ev[k];
+      const double r = r0_ev[k] + s2;
+      double Sv = r, hm = 0;
+      for (int i = 0; i < D; ++i) {
+        double acc = 0;
+        for (int j = 0; j < D; ++j) acc += P[i * D + j] * h[j];
+        u[i] = acc;
+        Sv += h[i] * acc;
+        hm += h[i] * m[i];
+      }
+      const double v = y_ev[k] - hm;
+      for (int i = 0; i < D; ++i) {
+        K[i] = u[i] / Sv;
+        m[i] += K[i] * v;
+      }
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) A[i * D + j] = (i == j ? 1.0 : 0.0) - K[i] * h[j];
+      matmul_r(D, A, P, T);
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j <= i; ++j) {
+          double acc = 0;
+          for (int kk = 0; kk < D; ++kk) acc += T[i * D + kk] * A[j * D + kk];
+          P[i * D + j] = acc + K[i] * r * K[j];
+          P[j * D + i] = P[i * D + j];
+        }
+    }
+    memcpy(mf + k * D, m, sizeof(double) * D);
+    memcpy(Pf + k * DD, P, sizeof(double) * DD);
+  }
+  /* backward: smoothed (m^, P^), starting from the last (end) event */
+  double ms[MAXD], Ps[MAXD * MAXD];
+  if (!rc && n_ev > 0) {
+    memcpy(ms, mf + (n_ev - 1) * D, sizeof(double) * D);
+    memcpy(Ps, Pf + (n_ev - 1) * DD, sizeof(double) * DD);
+  }
+  for (int64_t k = n_ev - 1; k >= 0 && !rc; --k) {
+    if (k < n_ev - 1) {
+      /* transition from event k to k+1 (with the reset at a start state) */
+      discretize_r(&M, F, LQL, t_ev[k + 1] - t_ev[k], Phi, Qd);
+      const double *bm, *bP;
+      double AR[MAXD * MAXD];
+      memcpy(AR, Phi, sizeof(double) * DD);
+      if (kind[k] == 0) {
+        for (int t = 0; t < M.n_zper; ++t) {
+          const int z = zindex(&M, slot[k], t);
+          for (int i = 0; i < D; ++i) AR[i * D + z] = 0; /* Phi R: column z zeroed */
+        }
+        bm = mp + k * D;
+        bP = Pp + k * DD;
+      } else {
+        bm = mf + k * D;
+        bP = Pf + k * DD;
+      }
+      /* G = bP AR^T (P-_{k+1})^-1  <=>  P-_{k+1} G^T = AR bP */
+      double S[MAXD * MAXD], X[MAXD * MAXD];
+      memcpy(S, Pp + (k + 1) * DD, sizeof(double) * DD);
+      matmul_r(D, AR, bP, X);
+      if (solve_nn(D, S, X)) {
+        rc = 5;
+        break;
+      }
+      double G[MAXD * MAXD], dm[MAXD], dP[MAXD * MAXD], GT[MAXD * MAXD];
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) G[i * D + j] = X[j * D + i];
+      for (int i = 0; i < D; ++i) dm[i] = ms[i] - mp[(k + 1) * D + i];
+      for (int i = 0; i < DD; ++i) dP[i] = Ps[i] - Pp[(k + 1) * DD + i];
+      double nm[MAXD];
+      for (int i = 0; i < D; ++i) {
+        double acc = bm[i];
+        for (int j = 0; j < D; ++j) acc += G[i * D + j] * dm[j];
+        nm[i] = acc;
+      }
+      matmul_r(D, G, dP, T);
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) GT[i * D + j] = G[j * D + i];
+      matmul_r(D, T, GT, X);
+      for (int i = 0; i < DD; ++i) Ps[i] = bP[i] + X[i];
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < i; ++j) Ps[i * D + j] = Ps[j * D + i] = 0.5 * (Ps[i * D + j] + Ps[j * D + i]);
+      memcpy(ms, nm, sizeof(double) * D);
+    }
+    if (kind[k] == 1) {
+      for (int i = 0; i < D; ++i) h[i] = 0;
+      for (int t = 0; t < M.n_zper; ++t) h[zindex(&M, slot[k], t)] = invd_ev[k];
+      double mu = 0, va = 0;
+      for (int i = 0; i < D; ++i) {
+        mu += h[i] * ms[i];
+        for (int j = 0; j < D; ++j) va += h[i] * Ps[i * D + j] * h[j];
+      }
+      mean_ev[k] = mu;
+      var_ev[k] = va;
+    } else {
+      mean_ev[k] = var_ev[k] = 0.0;
+    }
+  }
+  free(mp);
+  free(Pp);
+  free(mf);
+  free(Pf);
+  return rc;
+}
