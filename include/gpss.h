@@ -143,6 +143,22 @@ gp_ss_status gp_ss_loglik_grad(const gp_ss_model *model, const float *theta, int
                                int theta_per_series, double *loglik_out, float *grad_out,
                                float *dlogl_dexposure, void *cuda_stream);
 
+/* Conditioned mean and variance of every measurement's exposure average
+ * given all of its series' data (the integrated RTS smoother of Section
+ * 3.2, Eqs. rts and integrated_rts: the smoothed state at each exposure end
+ * projected through H~ = e_z / delta), with the log-likelihood.  Computed by
+ * the gradient pipeline: the smoothed state is the filtered state corrected
+ * by the adjoint of the log-likelihood of all later data.
+ *   loglik_out  as gp_ss_loglik
+ *   cond_out    device f32 [rows * N * 2]: (mean, variance) of measurement n
+ *               (build order) at [(row * N + n) * 2 + {0, 1}]; rows = 1 when
+ *               theta_per_series, else n_sets.  The variance is that of the
+ *               noise-free exposure average (white noise and yerr excluded).
+ *   FP32 models only (GP_SS_EUNSUPPORTED otherwise). */
+gp_ss_status gp_ss_condition(const gp_ss_model *model, const float *theta, int n_sets,
+                             int theta_per_series, double *loglik_out, float *cond_out,
+                             void *cuda_stream);
+
 /* Same computations replayed from a CUDA graph captured on first use for
  * this (model, pointers, n_sets, mode); a later call with other pointers
  * re-captures.  The first call must not itself be made during a capture. */

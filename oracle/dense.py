@@ -117,3 +117,15 @@ def loglik_instantaneous(terms, theta, t, y, yerr):
     _, s = split_theta(terms, theta)
     K = instantaneous_cov(terms, theta, t)
     return gaussian_loglik(K, np.asarray(y, np.float64), np.asarray(yerr, np.float64) ** 2 + s * s)
+
+
+def posterior(terms, theta, t_start, t_end, y, yerr):
+    """Conditioned mean and variance of every exposure average given all the
+    data: K (K + R)^-1 y and diag(K - K (K + R)^-1 K), with K the integrated
+    kernel of the exposure averages and R = diag(yerr^2 + s^2) (the full GP
+    solution of Section 2 with the integrated kernel of Section 3.1)."""
+    _, s = split_theta(terms, theta)
+    K = integrated_cov(terms, theta, t_start, t_end)
+    A = K + np.diag(np.asarray(yerr, np.float64) ** 2 + s * s)
+    y = np.asarray(y, np.float64)
+    return K @ np.linalg.solve(A, y), np.diag(K - K @ np.linalg.solve(A, K))

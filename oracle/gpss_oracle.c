@@ -212,38 +212,52 @@ int gpss_oracle_exposure_grad(const int32_t *spec, int64_t n_ev, const double *t
 
 /* ---- integrated RTS smoother (real arithmetic only) ---- */
 
-/* Solve A X = B for X (n x n, row-major), A n x n, by Gauss-Jordan with
- * partial pivoting; A and B are overwritten (B becomes X).  Returns 0, or 1
- * if A is singular to working precision. */
-static int solve_nn(int n, double *A, double *B) {
-  for (int c = 0; c < n; ++c) {
+/* Solve S G^T = X for the smoother gain (S symmetric positive semidefinite,
+ * n x n; X n x n; both row-major, overwritten; G^T returned in X).  A reset
+ * followed by a zero gap leaves an exactly zero row and column in S (that
+ * integral state is known to be zero); those indices are left out and the
+ * rest is solved exactly by Gauss-Jordan with partial pivoting, which is the
+ * Moore-Penrose solution for this structure.  Returns 0, or 1 if the
+ * remaining matrix is singular. */
+static int gain_solve(int n, double *S, double *X) {
+  int keep[MAXD], nk = 0;
+  for (int i = 0; i < n; ++i)
+    if (S[i * n + i] > 0.0) keep[nk++] = i;
+  double A[MAXD * MAXD], B[MAXD * MAXD];
+  for (int r = 0; r < nk; ++r)
+    for (int c = 0; c < nk; ++c) A[r * nk + c] = S[keep[r] * n + keep[c]];
+  for (int r = 0; r < nk; ++r)
+    for (int j = 0; j < n; ++j) B[r * n + j] = X[keep[r] * n + j];
+  for (int c = 0; c < nk; ++c) {
     int p = c;
-    for (int r = c + 1; r < n; ++r)
-      if (fabs(A[r * n + c]) > fabs(A[p * n + c])) p = r;
-    if (A[p * n + c] == 0.0) return 1;
-    if (p != c)
+    for (int r = c + 1; r < nk; ++r)
+      if (fabs(A[r * nk + c]) > fabs(A[p * nk + c])) p = r;
+    if (A[p * nk + c] == 0.0) return 1;
+    if (p != c) {
+      for (int j = 0; j < nk; ++j) {
+        const double t = A[c * nk + j];
+        A[c * nk + j] = A[p * nk + j];
+        A[p * nk + j] = t;
+      }
       for (int j = 0; j < n; ++j) {
-        double t = A[c * n + j];
-        A[c * n + j] = A[p * n + j];
-        A[p * n + j] = t;
-        t = B[c * n + j];
+        const double t = B[c * n + j];
         B[c * n + j] = B[p * n + j];
         B[p * n + j] = t;
       }
-    const double inv = 1.0 / A[c * n + c];
-    for (int j = 0; j < n; ++j) {
-      A[c * n + j] *= inv;
-      B[c * n + j] *= inv;
     }
-    for (int r = 0; r < n; ++r) {
-      if (r == c || A[r * n + c] == 0.0) continue;
-      const double f = A[r * n + c];
-      for (int j = 0; j < n; ++j) {
-        A[r * n + j] -= f * A[c * n + j];
-        B[r * n + j] -= f * B[c * n + j];
-      }
+    const double inv = 1.0 / A[c * nk + c];
+    for (int j = 0; j < nk; ++j) A[c * nk + j] *= inv;
+    for (int j = 0; j < n; ++j) B[c * n + j] *= inv;
+    for (int r = 0; r < nk; ++r) {
+      if (r == c || A[r * nk + c] == 0.0) continue;
+      const double f = A[r * nk + c];
+      for (int j = 0; j < nk; ++j) A[r * nk + j] -= f * A[c * nk + j];
+      for (int j = 0; j < n; ++j) B[r * n + j] -= f * B[c * n + j];
     }
   }
+  for (int i = 0; i < n * n; ++i) X[i] = 0.0;
+  for (int r = 0; r < nk; ++r)
+    for (int j = 0; j < n; ++j) X[keep[r] * n + j] = B[r * n + j];
   return 0;
 }
 
@@ -258,8 +272,9 @@ static int solve_nn(int n, double *A, double *B) {
  *   m^_k = base + G (m^_{k+1} - m-_{k+1}),
  *   P^_k = base + G (P^_{k+1} - P-_{k+1}) G^T,
  * with A_k the transition from event k to k+1.  At each end event (output
- * in event order) mean = H m^, var = H P^ H^T, H = e_z / delta.  Returns 0,
- * or 5 if some P-_{k+1} is singular. */
+ * in event order) mean = H m^, var = H P^ H^T, H = e_z / delta.  P-_{k+1}
+ * is inverted as in gain_solve.  Returns 0, or 5 if it is singular beyond
+ * zeroed integral states. */
 int gpss_oracle_condition(const int32_t *spec, int64_t n_ev, const double *t_ev,
                           const int32_t *kind, const int32_t *slot, const double *y_ev,
                           const double *r0_ev, const double *invd_ev, const double *theta,
@@ -378,7 +393,7 @@ int gpss_oracle_condition(const int32_t *spec, int64_t n_ev, const double *t_ev,
       double S[MAXD * MAXD], X[MAXD * MAXD];
       memcpy(S, Pp + (k + 1) * DD, sizeof(double) * DD);
       matmul_r(D, AR, bP, X);
-      if (solve_nn(D, S, X)) {
+      if (gain_solve(D, S, X)) {
         rc = 5;
         break;
       }

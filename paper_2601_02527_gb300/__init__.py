@@ -32,7 +32,7 @@ EXPORTS = ["gp_ss_build_model", "gp_ss_loglik", "gp_ss_loglik_grad", "gp_ss_logl
            "gp_ss_loglik_grad_batched", "gp_ss_loglik_grad_host", "gp_ss_model_info",
            "gp_ss_set_chunk_len", "gp_ss_last_error_series", "gp_ss_free_model",
            "gp_ss_status_string", "gp_ss_discretize", "gp_ss_set_timing", "gp_ss_get_timing",
-           "gp_ss_loglik_noalloc", "gp_ss_launch_count", "gp_ss_autotune"]
+           "gp_ss_loglik_noalloc", "gp_ss_launch_count", "gp_ss_autotune", "gp_ss_condition"]
 
 PHASES = ["elem", "scan", "grad", "convert", "plain"]
 
@@ -90,6 +90,7 @@ def load_library(path: str | None = None):
     lib.gp_ss_free_model.argtypes = [vp]
     lib.gp_ss_free_model.restype = None
     lib.gp_ss_launch_count.argtypes = [P(i64)]
+    lib.gp_ss_condition.argtypes = [vp, vp, i32, i32, vp, vp, vp]
     lib.gp_ss_autotune.argtypes = [vp, vp, i32, i32, i32, i32, P(_Tuning), vp]
     lib.gp_ss_status_string.argtypes = [i32]
     lib.gp_ss_status_string.restype = ctypes.c_char_p
@@ -268,6 +269,20 @@ class Model:
                                              _stream_ptr(stream))
         _check(rc, "gp_ss_loglik_grad")
         return (out, grad, dexp) if exposure else (out, grad)
+
+    def condition(self, theta, per_series=True, stream=None):
+        """(log-likelihood [n_out] float64, conditioned [rows, N, 2] float32):
+        the mean and variance of every measurement's exposure average given
+        all of its series' data (integrated RTS smoother)."""
+        import torch
+        th = self._theta(theta)
+        out = torch.empty(self.n_out(th, per_series), dtype=torch.float64, device=th.device)
+        rows = 1 if per_series else th.shape[0]
+        cond = torch.empty(rows, self.info["n_meas"], 2, dtype=torch.float32, device=th.device)
+        _check(self._lib.gp_ss_condition(self._h, th.data_ptr(), th.shape[0], int(bool(per_series)),
+                                         out.data_ptr(), cond.data_ptr(), _stream_ptr(stream)),
+               "gp_ss_condition")
+        return out, cond
 
     def loglik_grad_host(self, theta, per_series=True, reupload_events=False, stream=None):
         """Host-buffer variant: numpy in, numpy out (synchronous)."""

@@ -82,6 +82,26 @@ __global__ void k_exposure_grad(int n_rows, int n_series, const int64_t *__restr
   out[2 * idx] = gt(ks) + wpart;
   out[2 * idx + 1] = gt(ke) - wpart;
 }
+
+__global__ void k_gather_cond(int n_rows, int n_series, const int64_t *__restrict__ ev_off,
+                              const int64_t *__restrict__ meas_off, const int2 *__restrict__ mev,
+                              int64_t n_meas, int64_t n_events, const float2 *__restrict__ cond,
+                              float *__restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n_rows * n_meas) return;
+  const int64_t row = idx / n_meas, n = idx % n_meas;
+  int lo = 0, hi = n_series - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (meas_off[mid] <= n)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const float2 v = cond[row * n_events + ev_off[lo] + mev[n].y];
+  out[2 * idx] = v.x;
+  out[2 * idx + 1] = v.y;
+}
 }  // namespace gpss
 
 using gpss::OpTable;
@@ -505,7 +525,8 @@ gp_ss_status check_call(const gp_ss_model *m, const float *theta, int n_sets, in
 
 // Enqueue the log-likelihood (and optionally gradient) computation.
 gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int per_series,
-                     double *ll, float *grad, cudaStream_t st, float *dexp = nullptr) {
+                     double *ll, float *grad, cudaStream_t st, float *dexp = nullptr,
+                     float *cond_out = nullptr) {
   const int n_out = per_series ? m->n_series : n_sets * m->n_series;
   gp_ss_status s0 = prepare_err(m, n_out, st);
   if (s0) return s0;
@@ -620,9 +641,11 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
     }
     if (grad) {
       float *rbuf = nullptr, *gdt = nullptr, *gwe = nullptr;
+      float2 *cond = nullptr;
       const int exp_rows = per_series ? 1 : n_sets;
-      if (dexp && (!grab((void **)&gdt, (size_t)exp_rows * m->n_events * sizeof(float)) ||
-                   !grab((void **)&gwe, (size_t)exp_rows * m->n_events * sizeof(float)))) {
+      if ((dexp && (!grab((void **)&gdt, (size_t)exp_rows * m->n_events * sizeof(float)) ||
+                    !grab((void **)&gwe, (size_t)exp_rows * m->n_events * sizeof(float)))) ||
+          (cond_out && !grab((void **)&cond, (size_t)exp_rows * m->n_events * sizeof(float2)))) {
         res = GP_SS_ENOMEM;
         break;
       }
@@ -633,9 +656,20 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       }
       PhaseTimer pt(m, st, 2);
       if (o.grad(dm, theta, n_vch, per_series, state_end, adj, ckpt, gpart, m->d_err, tabs, rbuf,
-                 dcache, ck, gdt, gwe, st)) {
+                 dcache, ck, gdt, gwe, cond, st)) {
         res = GP_SS_ECUDA;
         break;
+      }
+      if (cond_out && m->n_meas > 0) {
+        const int64_t nt = (int64_t)exp_rows * m->n_meas;
+        gpss::k_gather_cond<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(
+            exp_rows, m->n_series, m->d_ev_off, m->d_meas_off, m->d_mev, m->n_meas, m->n_events,
+            cond, cond_out);
+        GPSS_COUNT_LAUNCH();
+        if (cudaGetLastError() != cudaSuccess) {
+          res = GP_SS_ECUDA;
+          break;
+        }
       }
       if (dexp && m->n_meas > 0) {
         const int64_t nt = (int64_t)exp_rows * m->n_meas;
@@ -942,6 +976,24 @@ gp_ss_status gp_ss_loglik_grad(const gp_ss_model *m, const float *theta, int n_s
   DeviceGuard g(m->device);
   return enqueue(m, theta, n_sets, theta_per_series, loglik_out, grad_out,
                  (cudaStream_t)cuda_stream, dlogl_dexposure);
+}
+
+gp_ss_status gp_ss_condition(const gp_ss_model *m, const float *theta, int n_sets,
+                             int theta_per_series, double *loglik_out, float *cond_out,
+                             void *cuda_stream) {
+  gp_ss_status s = check_call(m, theta, n_sets, theta_per_series, loglik_out);
+  if (s) return s;
+  if (!cond_out) return GP_SS_EINVAL;
+  if (m->precision == 64) return GP_SS_EUNSUPPORTED;
+  DeviceGuard g(m->device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int n_out = theta_per_series ? m->n_series : n_sets * m->n_series;
+  float *grad = nullptr;
+  if (scratch_alloc(m, (void **)&grad, (size_t)n_out * m->n_params * sizeof(float), st))
+    return GP_SS_ENOMEM;
+  s = enqueue(m, theta, n_sets, theta_per_series, loglik_out, grad, st, nullptr, cond_out);
+  cudaFreeAsync(grad, st);
+  return s;
 }
 
 gp_ss_status gp_ss_loglik_batched(const gp_ss_model *m, const float *theta, int n_sets,

@@ -909,6 +909,40 @@ struct TermGrad {
   float s2;
 };
 
+// Conditioned mean and variance of an exposure average from the filtered
+// state (m, P) just after its end event (slot j, w = 1/delta) and the
+// adjoint (lam, Lam) of the log-likelihood of all later data with respect
+// to that state: the smoothed state is m + P lam and P - P (lam lam^T -
+// 2 Lam) P (the Gaussian conditioning identities behind the RTS smoother),
+// so with h = w e_j and u = P h:  mean = h.m + u.lam,
+// var = h.u + u^T (2 Lam) u - (u.lam)^2.
+template <class S>
+GPSS_HD float2 conditioned(int j, float w, const float *m, const float *P, const float *lam,
+                           const float *Lam) {
+  constexpr int D = S::D;
+  float u[D], hm = 0.f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    float acc = 0.f;
+#pragma unroll
+    for (int z = 2 * S::NT; z < D; ++z)
+      if (S::zslot(z) == j) acc += P[S::pk(i, z)];
+    u[i] = w * acc;
+    if (i >= 2 * S::NT && S::zslot(i) == j) hm += m[i];
+  }
+  float ul = 0.f, hu = 0.f, uLu = 0.f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    ul += u[i] * lam[i];
+    if (i >= 2 * S::NT && S::zslot(i) == j) hu += u[i];
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc += Lam[S::pk(i, k)] * u[k];
+    uLu += u[i] * acc;
+  }
+  return make_float2(w * hm + ul, w * hu + 2.f * uLu - ul * ul);
+}
+
 // Reverse of one event.  (m, P): filtered state before the event; dv: the
 // step's six scalars per term.  (lam, Lam): adjoint of the filtered state
 // after the event (full-matrix gradient convention, stored packed); on
@@ -1160,7 +1194,8 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
                                              const float *__restrict__ tabs,
                                              float *__restrict__ rbuf,
                                              const float *__restrict__ dcache, int ck,
-                                             float *__restrict__ gdt, float *__restrict__ gwe) {
+                                             float *__restrict__ gdt, float *__restrict__ gwe,
+                                             float2 *__restrict__ cond) {
   using F = float;
   constexpr int D = S::D;
   constexpr int SD = D + S::NP;
@@ -1274,6 +1309,15 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       }
       if (filter_blocks<S, F>(B, tag, q.x, q.y, q.z, s2, m, P, Sv, vv)) bad |= !(Sv > F(0));
     }
+    // conditioned mean and variance of the chunk's last event, if it ends an
+    // exposure: the chunk's end state and its boundary adjoint
+    if (cond && seg == nseg - 1 && (__ldg(M.tag + e0 + k1 - 1) & 1)) {
+      const uint8_t tl = __ldg(M.tag + e0 + k1 - 1);
+      const float4 ql = __ldg(M.meas + rd.mi - 1);
+      F mb[D], Pb[S::NP];
+      load_rec<S>(state_end, n_vch, vc, mb, Pb);
+      cond[eo + k1 - 1] = conditioned<S>((tl >> 1) & 7, ql.z, mb, Pb, lam, Lam);
+    }
     // backward walk.  The earlier step's replayed state and cached scalars
     // are staged into shared memory by cp.async while the current step is
     // processed; its gap, tag and measurement record are loaded one ahead.
@@ -1349,6 +1393,15 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
         gdt[eo + k2] = g_dt;
         if (tag & 1) gwe[eo + k2] = q.z * q.z * g_w;
       }
+      // (m, P) is the filtered state after event k2 - 1 and (lam, Lam) now its
+      // adjoint: the conditioned values of that event's measurement
+      if (cond && k2 > 0) {
+        const uint8_t tp = k2 > k0 ? tag_n : __ldg(M.tag + e0 + k2 - 1);
+        if (tp & 1) {
+          const float4 qp = k2 > k0 ? q_n : __ldg(M.meas + m0 + mr - 1);
+          cond[eo + k2 - 1] = conditioned<S>((tp >> 1) & 7, qp.z, m, P, lam, Lam);
+        }
+      }
     }
   }
   if (first) {
@@ -1413,6 +1466,13 @@ __global__ void k_exposure_grad(int n_rows, int n_series, const int64_t *__restr
                                 const float *__restrict__ gdt, const float *__restrict__ gwe,
                                 float *__restrict__ out);
 
+// Per measurement (input order): the conditioned (mean, variance) k_grad
+// wrote at its end event.  out[(row N + n) 2 + {0,1}].
+__global__ void k_gather_cond(int n_rows, int n_series, const int64_t *__restrict__ ev_off,
+                              const int64_t *__restrict__ meas_off, const int2 *__restrict__ mev,
+                              int64_t n_meas, int64_t n_events, const float2 *__restrict__ cond,
+                              float *__restrict__ out);
+
 // Dense Phi~(dt_k), Q~(dt_k) for a list of gaps (one thread per gap).
 template <class S>
 __global__ void k_disc(const float *__restrict__ theta, const float *__restrict__ tabs, int kinds0,
@@ -1462,7 +1522,7 @@ struct OpTable {
                       float *, double *, int, int *, cudaStream_t);
   cudaError_t (*grad)(const DevModel &, const float *, int, int, const float *, const float *,
                       const float *, float *, int *, const float *, float *, const float *, int,
-                      float *, float *, cudaStream_t);
+                      float *, float *, float2 *, cudaStream_t);
   cudaError_t (*tables)(const float *, int, int, int, int, float *, cudaStream_t);
   cudaError_t (*warp_combine)(const DevModel &, const float *, int, float *, float *, float *,
                               float *, float *, float *, float *, float *, int, int, int, int,
@@ -1611,12 +1671,14 @@ cudaError_t launch_finish(const DevModel &M, int n_vch, int per_series, const fl
 // Scratch: rbuf [ck * 4 ceil(SD/4) * n_vch] floats.  dcache: the step-scalar
 // cache k_elem filled, or null (the replay then recomputes the scalars).
 // gdt, gwe: per-event exposure adjoints [rows * n_events] (see k_grad), or
-// null when the exposure gradient is not wanted.
+// null when the exposure gradient is not wanted; cond: per-event conditioned
+// (mean, variance) of end events [rows * n_events], or null.
 template <class S>
 cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int per_series,
                         const float *state_end, const float *adj_end, const float *pck,
                         float *gpart, int *err, const float *tabs, float *rbuf,
-                        const float *dcache, int ck, float *gdt, float *gwe, cudaStream_t st) {
+                        const float *dcache, int ck, float *gdt, float *gwe, float2 *cond,
+                        cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
   if (ck < 2 || ck > 64 || (ck & 1)) return cudaErrorInvalidValue;
   const int SG = (S::D + S::NP + 3) / 4, NDG = DcW<S::NT>::G;
@@ -1624,7 +1686,7 @@ cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int pe
                       (size_t)2 * (SG + NDG) * GRAD_BS * sizeof(float4);
   k_grad<S><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
       M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err, tabs, rbuf, dcache, ck,
-      gdt, gwe);
+      gdt, gwe, cond);
   GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }

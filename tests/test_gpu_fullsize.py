@@ -75,6 +75,15 @@ def test_c4_full_autotuned(gp):
     _check_grad(g[idx], ref_g)
     # the gradient call's log-likelihood is the log-likelihood call's
     np.testing.assert_allclose(m.loglik(th).cpu().numpy(), ll, rtol=1e-12)
+    # conditioned mean and variance of the sampled series (integrated RTS)
+    _, cond = m.condition(th)
+    cond = cond.cpu().numpy()[0].astype(np.float64)
+    for i in idx[:4]:
+        a, b = wl.offsets[i], wl.offsets[i + 1]
+        ts, te, y, ye, inst = wl.series(i)
+        mu, va = oracle.condition(wl.terms, wl.layout, ts, te, y, ye, wl.theta[i])
+        assert np.all(np.abs(cond[a:b, 0] - mu) <= 1e-3 * np.abs(mu).max() + 1e-5 * np.abs(mu))
+        assert np.all(np.abs(cond[a:b, 1] - va) <= 2e-3 * va + 1e-5 * va.max())
     # time-shift invariance of the exposure gradient, every series
     for s in range(wl.n_series):
         a, b = wl.offsets[s], wl.offsets[s + 1]

@@ -90,3 +90,11 @@ def test_uninformative_point(oracle_lib):
     mu0, va0 = oracle.condition([SHO], 0, ts[keep], te[keep], y[keep], ye[keep], th)
     assert np.max(np.abs(mu[keep] - mu0)) <= 1e-9 * np.max(np.abs(mu0))
     assert np.max(np.abs(va[keep] - va0) / va0) <= 1e-8
+
+
+def test_touching_windows(oracle_lib):
+    # each exposure ends exactly where the next starts (end before start)
+    rng = np.random.default_rng(26)
+    ts = np.arange(70) * 0.5
+    _check([SHO], 0, ts, ts + 0.5, rng.normal(size=70), np.full(70, 0.05),
+           np.array([1.0, 2 * math.pi / 10, 3.0, 0.1]))
