@@ -373,6 +373,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     extra["fp32_loglik_only"] = {"value": wl.n_meas / (a.elapsed_time(b) / 3 / 1e3),
                                  "unit": UNIT}
+    # conditioned mean and variance of every measurement (integrated RTS
+    # smoother through the gradient walk), with the log-likelihood
+    model.condition(theta)
+    a.record(stream)
+    for _ in range(3):
+        model.condition(theta)
+    b.record(stream)
+    torch.cuda.synchronize()
+    extra["fp32_condition"] = {"value": wl.n_meas / (a.elapsed_time(b) / 3 / 1e3), "unit": UNIT,
+                               "work": "loglik + conditioned mean/variance per measurement"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
