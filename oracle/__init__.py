@@ -70,6 +70,12 @@ def _load():
             P(ctypes.c_int32), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
             P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double)]
         lib.gpss_oracle_condition.restype = ctypes.c_int
+        lib.gpss_oracle_predict.argtypes = [
+            P(ctypes.c_int32), ctypes.c_int64, P(ctypes.c_double), P(ctypes.c_int32),
+            P(ctypes.c_int32), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+            P(ctypes.c_double), ctypes.c_int64, P(ctypes.c_double), P(ctypes.c_double),
+            P(ctypes.c_double)]
+        lib.gpss_oracle_predict.restype = ctypes.c_int
         lib.gpss_oracle_discretize.argtypes = [
             P(ctypes.c_int32), P(ctypes.c_double), ctypes.c_double, P(ctypes.c_double),
             P(ctypes.c_double), P(ctypes.c_double)]
@@ -186,6 +192,30 @@ def loglik_events(terms, layout, ev, theta, grad=False, n_slots=None, dump=False
         res["P"] = dP
         res["S"] = dS
     return res
+
+
+def predict(terms, layout, t_start, t_end, y, yerr, theta, t_star, instrument=None,
+            n_slots=None):
+    """Oracle prediction of the latent f(t*) (mean, variance) given all of the
+    series' data, at the test times t_star (Algorithm 1)."""
+    ev = events(t_start, t_end, y, yerr, instrument)
+    lib = _load()
+    n_slots = ev["n_slots"] if n_slots is None else n_slots
+    spec = spec_array(terms, layout, n_slots)
+    theta = np.ascontiguousarray(theta, np.float64)
+    ts = np.ascontiguousarray(t_star, np.float64)
+    mean = np.zeros(len(ts))
+    var = np.zeros(len(ts))
+    arr = {k: np.ascontiguousarray(ev[k]) for k in ("t", "kind", "slot", "y", "r0", "invd")}
+    rc = lib.gpss_oracle_predict(
+        _ptr(spec, ctypes.c_int32), len(ev["t"]), _ptr(arr["t"], ctypes.c_double),
+        _ptr(arr["kind"], ctypes.c_int32), _ptr(arr["slot"], ctypes.c_int32),
+        _ptr(arr["y"], ctypes.c_double), _ptr(arr["r0"], ctypes.c_double),
+        _ptr(arr["invd"], ctypes.c_double), _ptr(theta, ctypes.c_double), len(ts),
+        _ptr(ts, ctypes.c_double), _ptr(mean, ctypes.c_double), _ptr(var, ctypes.c_double))
+    if rc != 0:
+        raise RuntimeError(f"oracle prediction failed with code {rc}")
+    return mean, var
 
 
 def exposure_grad_events(terms, layout, ev, theta, n_slots=None):

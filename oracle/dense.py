@@ -129,3 +129,40 @@ def posterior(terms, theta, t_start, t_end, y, yerr):
     A = K + np.diag(np.asarray(yerr, np.float64) ** 2 + s * s)
     y = np.asarray(y, np.float64)
     return K @ np.linalg.solve(A, y), np.diag(K - K @ np.linalg.solve(A, K))
+
+
+def F1(x, sigma, w0, q):
+    """Odd first antiderivative of k(|x|), F1(0) = 0 (the derivative of G)."""
+    x = np.asarray(x, np.float64)
+    a = np.abs(x)
+    if q == 0.5:
+        lam = w0
+        v = sigma ** 2 * (2 / lam - np.exp(-lam * a) * (2 / lam + a))
+    else:
+        eta = math.sqrt(1 - 1 / (4 * q * q))
+        alpha = sigma ** 2 * (1 - 1j / (2 * eta * q))
+        beta = w0 / (2 * q) - 1j * eta * w0
+        v = np.real(alpha * (1 - np.exp(-beta * a)) / beta)
+    return np.sign(x) * v
+
+
+def predict(terms, theta, t_start, t_end, y, yerr, t_star):
+    """Mean and variance of the latent f(t*) given exposure-averaged data:
+    k*^T (K + R)^-1 y and k(0) - k*^T (K + R)^-1 k*, with
+    k*_n = cov(f(t*), average over exposure n) = (F1(t* - ts_n) - F1(t* - te_n)) / delta_n."""
+    pars, s = split_theta(terms, theta)
+    ts_, te_ = np.asarray(t_start, np.float64), np.asarray(t_end, np.float64)
+    d = te_ - ts_
+    K = integrated_cov(terms, theta, ts_, te_)
+    A = K + np.diag(np.asarray(yerr, np.float64) ** 2 + s * s)
+    t_star = np.asarray(t_star, np.float64)
+    ks = np.zeros((len(t_star), len(ts_)))
+    k0 = 0.0
+    for sig, w0, q in pars:
+        ks += (F1(t_star[:, None] - ts_[None, :], sig, w0, q) -
+               F1(t_star[:, None] - te_[None, :], sig, w0, q)) / d[None, :]
+        k0 += sig ** 2
+    sol = np.linalg.solve(A, np.c_[np.asarray(y, np.float64), ks.T])
+    mean = ks @ sol[:, 0]
+    var = k0 - np.einsum("ij,ji->i", ks, sol[:, 1:])
+    return mean, var

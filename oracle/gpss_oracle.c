@@ -275,27 +275,17 @@ static int gain_solve(int n, double *S, double *X) {
  * in event order) mean = H m^, var = H P^ H^T, H = e_z / delta.  P-_{k+1}
  * is inverted as in gain_solve.  Returns 0, or 5 if it is singular beyond
  * zeroed integral states. */
-int gpss_oracle_condition(const int32_t *spec, int64_t n_ev, const double *t_ev,
-                          const int32_t *kind, const int32_t *slot, const double *y_ev,
-                          const double *r0_ev, const double *invd_ev, const double *theta,
-                          double *mean_ev, double *var_ev) {
-  model_t M;
-  if (parse_spec(spec, &M)) return 1;
+static int smooth_all(const model_t *Mp, int64_t n_ev, const double *t_ev, const int32_t *kind,
+                      const int32_t *slot, const double *y_ev, const double *r0_ev,
+                      const double *invd_ev, const double *theta, double *mp, double *Pp,
+                      double *mf, double *Pf, double *msa, double *Psa, double *mean_ev,
+                      double *var_ev) {
+  const model_t M = *Mp;
   const int D = M.dim, DD = D * D;
   double w0[MAXT], q[MAXT], var[MAXT], s2;
   double F[MAXD * MAXD], LQL[MAXD * MAXD], Phi[MAXD * MAXD], Qd[MAXD * MAXD];
   term_params_r(&M, theta, w0, q, var, &s2);
   build_F_r(&M, w0, q, var, F, LQL);
-  const size_t n = (size_t)(n_ev > 0 ? n_ev : 1);
-  double *mp = malloc(sizeof(double) * n * D), *Pp = malloc(sizeof(double) * n * DD);
-  double *mf = malloc(sizeof(double) * n * D), *Pf = malloc(sizeof(double) * n * DD);
-  if (!mp || !Pp || !mf || !Pf) {
-    free(mp);
-    free(Pp);
-    free(mf);
-    free(Pf);
-    return 4;
-  }
   int rc = 0;
   /* forward: predicted and filtered states (Joseph-form update as in the filter) */
   double m[MAXD], P[MAXD * MAXD], T[MAXD * MAXD], A[MAXD * MAXD], h[MAXD], u[MAXD], K[MAXD];
@@ -417,6 +407,9 @@ int gpss_oracle_condition(const int32_t *spec, int64_t n_ev, const double *t_ev,
         for (int j = 0; j < i; ++j) Ps[i * D + j] = Ps[j * D + i] = 0.5 * (Ps[i * D + j] + Ps[j * D + i]);
       memcpy(ms, nm, sizeof(double) * D);
     }
+    memcpy(msa + k * D, ms, sizeof(double) * D);
+    memcpy(Psa + k * DD, Ps, sizeof(double) * DD);
+    if (!mean_ev) continue;
     if (kind[k] == 1) {
       for (int i = 0; i < D; ++i) h[i] = 0;
       for (int t = 0; t < M.n_zper; ++t) h[zindex(&M, slot[k], t)] = invd_ev[k];
@@ -431,9 +424,221 @@ int gpss_oracle_condition(const int32_t *spec, int64_t n_ev, const double *t_ev,
       mean_ev[k] = var_ev[k] = 0.0;
     }
   }
-  free(mp);
-  free(Pp);
-  free(mf);
-  free(Pf);
+  return rc;
+}
+
+/* Per-event state arrays of the smoother: predicted, filtered, smoothed
+ * (at start states the smoothed state is the pre-reset one). */
+typedef struct {
+  double *mp, *Pp, *mf, *Pf, *ms, *Ps;
+} states_t;
+
+static int states_alloc(states_t *S, int64_t n_ev, int D) {
+  const size_t n = (size_t)(n_ev > 0 ? n_ev : 1);
+  S->mp = malloc(sizeof(double) * n * D);
+  S->mf = malloc(sizeof(double) * n * D);
+  S->ms = malloc(sizeof(double) * n * D);
+  S->Pp = malloc(sizeof(double) * n * D * D);
+  S->Pf = malloc(sizeof(double) * n * D * D);
+  S->Ps = malloc(sizeof(double) * n * D * D);
+  return (S->mp && S->mf && S->ms && S->Pp && S->Pf && S->Ps) ? 0 : 4;
+}
+
+static void states_free(states_t *S) {
+  free(S->mp);
+  free(S->mf);
+  free(S->ms);
+  free(S->Pp);
+  free(S->Pf);
+  free(S->Ps);
+}
+
+int gpss_oracle_condition(const int32_t *spec, int64_t n_ev, const double *t_ev,
+                          const int32_t *kind, const int32_t *slot, const double *y_ev,
+                          const double *r0_ev, const double *invd_ev, const double *theta,
+                          double *mean_ev, double *var_ev) {
+  model_t M;
+  if (parse_spec(spec, &M)) return 1;
+  states_t S;
+  int rc = states_alloc(&S, n_ev, M.dim);
+  if (!rc)
+    rc = smooth_all(&M, n_ev, t_ev, kind, slot, y_ev, r0_ev, invd_ev, theta, S.mp, S.Pp, S.mf,
+                    S.Pf, S.ms, S.Ps, mean_ev, var_ev);
+  states_free(&S);
+  return rc;
+}
+
+/* Prediction of the latent f(t*) = sum_t x_t(t*) (mean and variance, given
+ * all of the series' data) at test times t_star[0..n_star) by Algorithm 1,
+ * on the augmented model:
+ *   retrodiction (t* <= first event time): the stationary latent block,
+ *     x* ~ N(0, Pinf); G = Pinf Phi^T Pinf^-1 with Phi = Phi(t_1 - t*) (the
+ *     latent prior is stationary, so the predicted covariance at t_1 is
+ *     Pinf), smoothed from the first event's pre-reset smoothed latent state;
+ *   interpolation (t_{k-1} < t* <= t_k): predict from the filtered state
+ *     after event k-1 over t* - t_{k-1}, then one RTS step from event k's
+ *     smoothed state, G = P* A^T (P-_k)^-1 with A = Phi~(t_k - t*) and
+ *     P-_k = A P* A^T + Q~(t_k - t*);
+ *   extrapolation (t* > last event time): predict from the last filtered
+ *     (= smoothed) state.
+ * Smoothed covariances carry G (.) G^T.  Returns 0, 5 as the smoother. */
+int gpss_oracle_predict(const int32_t *spec, int64_t n_ev, const double *t_ev, const int32_t *kind,
+                        const int32_t *slot, const double *y_ev, const double *r0_ev,
+                        const double *invd_ev, const double *theta, int64_t n_star,
+                        const double *t_star, double *mean_out, double *var_out) {
+  model_t M;
+  if (parse_spec(spec, &M)) return 1;
+  const int D = M.dim, DD = D * D, NX = 2 * M.n_terms;
+  states_t S;
+  int rc = states_alloc(&S, n_ev, D);
+  if (!rc)
+    rc = smooth_all(&M, n_ev, t_ev, kind, slot, y_ev, r0_ev, invd_ev, theta, S.mp, S.Pp, S.mf,
+                    S.Pf, S.ms, S.Ps, NULL, NULL);
+  double w0[MAXT], q[MAXT], var[MAXT], s2;
+  double F[MAXD * MAXD], LQL[MAXD * MAXD], A[MAXD * MAXD], Qd[MAXD * MAXD], P0[MAXD * MAXD];
+  term_params_r(&M, theta, w0, q, var, &s2);
+  build_F_r(&M, w0, q, var, F, LQL);
+  initial_cov_r(&M, w0, var, P0);
+  for (int64_t j = 0; j < n_star && !rc; ++j) {
+    const double ts = t_star[j];
+    double mh[MAXD], Ph[MAXD * MAXD];
+    /* first event with t_k >= t* */
+    int64_t lo = 0, hi = n_ev;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (t_ev[mid] < ts)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const int64_t k = lo;
+    if (k == n_ev) {
+      /* extrapolation */
+      discretize_r(&M, F, LQL, ts - t_ev[n_ev - 1], A, Qd);
+      const double *m = S.mf + (n_ev - 1) * D, *P = S.Pf + (n_ev - 1) * DD;
+      double T[MAXD * MAXD];
+      for (int i = 0; i < D; ++i) {
+        double acc = 0;
+        for (int c = 0; c < D; ++c) acc += A[i * D + c] * m[c];
+        mh[i] = acc;
+      }
+      matmul_r(D, A, P, T);
+      for (int i = 0; i < D; ++i)
+        for (int c = 0; c < D; ++c) {
+          double acc = Qd[i * D + c];
+          for (int e = 0; e < D; ++e) acc += T[i * D + e] * A[c * D + e];
+          Ph[i * D + c] = acc;
+        }
+    } else if (k == 0) {
+      /* retrodiction on the latent block (indices < NX) */
+      discretize_r(&M, F, LQL, t_ev[0] - ts, A, Qd);
+      double Ax[MAXD * MAXD], X[MAXD * MAXD], Sx[MAXD * MAXD], G[MAXD * MAXD];
+      for (int i = 0; i < NX; ++i)
+        for (int c = 0; c < NX; ++c) {
+          Ax[i * NX + c] = A[i * D + c];
+          Sx[i * NX + c] = P0[i * D + c];
+        }
+      /* G = P0 Ax^T P0^-1  <=>  P0 G^T = Ax P0 */
+      for (int i = 0; i < NX; ++i)
+        for (int c = 0; c < NX; ++c) {
+          double acc = 0;
+          for (int e = 0; e < NX; ++e) acc += Ax[i * NX + e] * P0[e * D + c];
+          X[i * NX + c] = acc;
+        }
+      if (gain_solve(NX, Sx, X)) {
+        rc = 5;
+        break;
+      }
+      for (int i = 0; i < NX; ++i)
+        for (int c = 0; c < NX; ++c) G[i * NX + c] = X[c * NX + i];
+      const double *m1 = S.ms, *P1 = S.Ps;
+      for (int i = 0; i < D; ++i) mh[i] = 0;
+      for (int i = 0; i < DD; ++i) Ph[i] = 0;
+      for (int i = 0; i < NX; ++i) {
+        double acc = 0;
+        for (int c = 0; c < NX; ++c) acc += G[i * NX + c] * m1[c];
+        mh[i] = acc;
+      }
+      for (int i = 0; i < NX; ++i)
+        for (int c = 0; c < NX; ++c) {
+          double acc = P0[i * D + c];
+          for (int e = 0; e < NX; ++e)
+            for (int f = 0; f < NX; ++f)
+              acc += G[i * NX + e] * (P1[e * D + f] - P0[e * D + f]) * G[c * NX + f];
+          Ph[i * D + c] = acc;
+        }
+    } else {
+      /* interpolation: filtered after k-1, predicted to t*, smoothed from k */
+      double ms_[MAXD], Ps_[MAXD * MAXD], T[MAXD * MAXD], B[MAXD * MAXD], Qb[MAXD * MAXD];
+      discretize_r(&M, F, LQL, ts - t_ev[k - 1], A, Qd);
+      const double *m = S.mf + (k - 1) * D, *P = S.Pf + (k - 1) * DD;
+      for (int i = 0; i < D; ++i) {
+        double acc = 0;
+        for (int c = 0; c < D; ++c) acc += A[i * D + c] * m[c];
+        ms_[i] = acc;
+      }
+      matmul_r(D, A, P, T);
+      for (int i = 0; i < D; ++i)
+        for (int c = 0; c < D; ++c) {
+          double acc = Qd[i * D + c];
+          for (int e = 0; e < D; ++e) acc += T[i * D + e] * A[c * D + e];
+          Ps_[i * D + c] = acc;
+        }
+      discretize_r(&M, F, LQL, t_ev[k] - ts, B, Qb);
+      double Pn[MAXD * MAXD], mn[MAXD], X[MAXD * MAXD], G[MAXD * MAXD];
+      matmul_r(D, B, Ps_, T);
+      for (int i = 0; i < D; ++i) {
+        double acc = 0;
+        for (int c = 0; c < D; ++c) acc += B[i * D + c] * ms_[c];
+        mn[i] = acc;
+        for (int c = 0; c < D; ++c) {
+          double a2 = Qb[i * D + c];
+          for (int e = 0; e < D; ++e) a2 += T[i * D + e] * B[c * D + e];
+          Pn[i * D + c] = a2;
+        }
+      }
+      memcpy(X, T, sizeof(double) * DD); /* B P* = (P* B^T)^T */
+      if (gain_solve(D, Pn, X)) {
+        rc = 5;
+        break;
+      }
+      for (int i = 0; i < D; ++i)
+        for (int c = 0; c < D; ++c) G[i * D + c] = X[c * D + i];
+      const double *m1 = S.ms + k * D, *P1 = S.Ps + k * DD;
+      double mp1[MAXD], Pp1[MAXD * MAXD];
+      memcpy(mp1, mn, sizeof(mn));
+      /* P-_k recomputed from t* (equal to the filter's by the semigroup) */
+      for (int i = 0; i < DD; ++i) Pp1[i] = Pn[i];
+      /* restore Pn: gain_solve overwrote it */
+      matmul_r(D, B, Ps_, T);
+      for (int i = 0; i < D; ++i)
+        for (int c = 0; c < D; ++c) {
+          double a2 = Qb[i * D + c];
+          for (int e = 0; e < D; ++e) a2 += T[i * D + e] * B[c * D + e];
+          Pp1[i * D + c] = a2;
+        }
+      for (int i = 0; i < D; ++i) {
+        double acc = ms_[i];
+        for (int c = 0; c < D; ++c) acc += G[i * D + c] * (m1[c] - mp1[c]);
+        mh[i] = acc;
+      }
+      for (int i = 0; i < D; ++i)
+        for (int c = 0; c < D; ++c) {
+          double acc = Ps_[i * D + c];
+          for (int e = 0; e < D; ++e)
+            for (int f = 0; f < D; ++f)
+              acc += G[i * D + e] * (P1[e * D + f] - Pp1[e * D + f]) * G[c * D + f];
+          Ph[i * D + c] = acc;
+        }
+    }
+    double mu = 0, va = 0;
+    for (int t = 0; t < M.n_terms; ++t) {
+      mu += mh[2 * t];
+      for (int u = 0; u < M.n_terms; ++u) va += Ph[2 * t * D + 2 * u];
+    }
+    mean_out[j] = mu;
+    var_out[j] = va;
+  }
+  states_free(&S);
   return rc;
 }
