@@ -131,7 +131,7 @@ gp_ss_status gp_ss_loglik(const gp_ss_model *model, const float *theta, int n_se
 
 /* Log-likelihood and its gradient with respect to the natural parameters,
  * by a reverse-time adjoint of the filter (the paper states the likelihood
- * only; Section 2.3 notes it feeds gradient-based optimisation).
+ * only; Section 2.4 notes it feeds gradient-based optimisation).
  *   grad_out   device f32 [n_out * n_params], same row order as loglik_out
  *   dlogl_dexposure  NULL, or device f32 [rows * N * 2]: the gradient with respect
  *              to every exposure window, (d/d t_start, d/d t_end) of measurement n (in
@@ -158,6 +158,27 @@ gp_ss_status gp_ss_loglik_grad(const gp_ss_model *model, const float *theta, int
 gp_ss_status gp_ss_condition(const gp_ss_model *model, const float *theta, int n_sets,
                              int theta_per_series, double *loglik_out, float *cond_out,
                              void *cuda_stream);
+
+/* Prediction of the latent f(t*) = sum of the terms' x(t*) at arbitrary test
+ * times, mean and variance given all of the series' data (Section 2.5,
+ * Algorithm 1 on the augmented model: retrodiction before the data,
+ * interpolation between events -- inside exposures too --, extrapolation
+ * after), with the log-likelihood.  Computed by the gradient pipeline: at
+ * each event the walk predicts every test time of the interval before it
+ * from the filtered state and corrects it by the event's adjoint.
+ *   t_star        host f64 [M], test times of series i at
+ *                 [star_offsets[i], star_offsets[i+1]), any order
+ *   star_offsets  host int64 [n_series + 1], non-decreasing, [0] = 0
+ *   loglik_out    as gp_ss_loglik
+ *   pred_out      device f32 [rows * M * 2]: (mean, variance) of test time j at
+ *                 [(row * M + j) * 2 + {0, 1}]; rows as gp_ss_condition
+ *   Test times of a series without measurements: GP_SS_EUNSUPPORTED.  The
+ *   call synchronises the stream (the test-time plan is built on the host).
+ *   FP32 models only. */
+gp_ss_status gp_ss_predict(const gp_ss_model *model, const float *theta, int n_sets,
+                           int theta_per_series, const double *t_star,
+                           const int64_t *star_offsets, double *loglik_out, float *pred_out,
+                           void *cuda_stream);
 
 /* Same computations replayed from a CUDA graph captured on first use for
  * this (model, pointers, n_sets, mode); a later call with other pointers

@@ -32,7 +32,8 @@ EXPORTS = ["gp_ss_build_model", "gp_ss_loglik", "gp_ss_loglik_grad", "gp_ss_logl
            "gp_ss_loglik_grad_batched", "gp_ss_loglik_grad_host", "gp_ss_model_info",
            "gp_ss_set_chunk_len", "gp_ss_last_error_series", "gp_ss_free_model",
            "gp_ss_status_string", "gp_ss_discretize", "gp_ss_set_timing", "gp_ss_get_timing",
-           "gp_ss_loglik_noalloc", "gp_ss_launch_count", "gp_ss_autotune", "gp_ss_condition"]
+           "gp_ss_loglik_noalloc", "gp_ss_launch_count", "gp_ss_autotune", "gp_ss_condition",
+           "gp_ss_predict"]
 
 PHASES = ["elem", "scan", "grad", "convert", "plain"]
 
@@ -91,6 +92,7 @@ def load_library(path: str | None = None):
     lib.gp_ss_free_model.restype = None
     lib.gp_ss_launch_count.argtypes = [P(i64)]
     lib.gp_ss_condition.argtypes = [vp, vp, i32, i32, vp, vp, vp]
+    lib.gp_ss_predict.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp]
     lib.gp_ss_autotune.argtypes = [vp, vp, i32, i32, i32, i32, P(_Tuning), vp]
     lib.gp_ss_status_string.argtypes = [i32]
     lib.gp_ss_status_string.restype = ctypes.c_char_p
@@ -283,6 +285,22 @@ class Model:
                                          out.data_ptr(), cond.data_ptr(), _stream_ptr(stream)),
                "gp_ss_condition")
         return out, cond
+
+    def predict(self, theta, t_star, star_offsets, per_series=True, stream=None):
+        """(log-likelihood [n_out] float64, prediction [rows, M, 2] float32): mean
+        and variance of the latent f(t*) at the test times (series i's at
+        t_star[star_offsets[i]:star_offsets[i+1]]) given all the data."""
+        import torch
+        th = self._theta(theta)
+        ts = np.ascontiguousarray(t_star, np.float64)
+        so = np.ascontiguousarray(star_offsets, np.int64)
+        out = torch.empty(self.n_out(th, per_series), dtype=torch.float64, device=th.device)
+        rows = 1 if per_series else th.shape[0]
+        pred = torch.empty(rows, len(ts), 2, dtype=torch.float32, device=th.device)
+        _check(self._lib.gp_ss_predict(self._h, th.data_ptr(), th.shape[0], int(bool(per_series)),
+                                       ts.ctypes.data, so.ctypes.data, out.data_ptr(),
+                                       pred.data_ptr(), _stream_ptr(stream)), "gp_ss_predict")
+        return out, pred
 
     def loglik_grad_host(self, theta, per_series=True, reupload_events=False, stream=None):
         """Host-buffer variant: numpy in, numpy out (synchronous)."""

@@ -153,6 +153,7 @@ struct gp_ss_model {
   float4 *d_meas = nullptr;
   double *d_dt64 = nullptr, *d_meas64 = nullptr;
   int2 *d_mev = nullptr;  // per measurement (input order): its start and end event in the series
+  std::vector<double> tev;  // event times (FP64, sorted per series) for predictions
   // chunk plan
   int chunk_len = 0, n_chunks = 0, max_chunk = 0, max_chunks_per_series = 0;
   int combine = 0;  // cross-chunk combination: 0 auto, 1 sequential per series, 2 tree
@@ -262,7 +263,7 @@ struct SeriesOut {
 
 void build_series(int64_t a, int64_t b, const double *ts, const double *te, const float *y,
                   const float *yerr, const int32_t *inst, float *dt, uint8_t *tag, float4 *meas,
-                  double *dt64, double *meas64, int2 *mev, SeriesOut *out) {
+                  double *dt64, double *meas64, int2 *mev, double *tev, SeriesOut *out) {
   const int64_t n = b - a;
   std::vector<int> slot(n);
   int n_slots = 1;
@@ -333,6 +334,7 @@ void build_series(int64_t a, int64_t b, const double *ts, const double *te, cons
     tprev = ev[k].t;
     dt[e0 + k] = (float)gap;
     if (dt64) dt64[e0 + k] = gap;
+    tev[e0 + k] = ev[k].t;
     const int64_t i = ev[k].i;
     const bool is_end = ev[k].kind == 0;
     tag[e0 + k] = (uint8_t)((is_end ? 1 : 0) | (slot[i] << 1));
@@ -526,7 +528,7 @@ gp_ss_status check_call(const gp_ss_model *m, const float *theta, int n_sets, in
 // Enqueue the log-likelihood (and optionally gradient) computation.
 gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int per_series,
                      double *ll, float *grad, cudaStream_t st, float *dexp = nullptr,
-                     float *cond_out = nullptr) {
+                     float *cond_out = nullptr, const gpss::PredPlan *pred = nullptr) {
   const int n_out = per_series ? m->n_series : n_sets * m->n_series;
   gp_ss_status s0 = prepare_err(m, n_out, st);
   if (s0) return s0;
@@ -655,8 +657,9 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
         break;
       }
       PhaseTimer pt(m, st, 2);
+      const gpss::PredPlan none;
       if (o.grad(dm, theta, n_vch, per_series, state_end, adj, ckpt, gpart, m->d_err, tabs, rbuf,
-                 dcache, ck, gdt, gwe, cond, st)) {
+                 dcache, ck, gdt, gwe, cond, pred ? *pred : none, st)) {
         res = GP_SS_ECUDA;
         break;
       }
@@ -838,6 +841,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   }
   m->h_meas[N] = make_float4(0.f, 0.f, 0.f, 0.f);
   std::vector<int2> mev(std::max<int64_t>(N, 1));
+  m->tev.assign(std::max<int64_t>(2 * N, 1), 0.0);
   std::vector<double> dt64, meas64;
   if (o.precision == 64) {
     dt64.resize(nE);
@@ -855,7 +859,8 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
           build_series(series_offsets[s], series_offsets[s + 1], t_start, t_end, y, yerr,
                        instrument, m->h_dt, m->h_tag, m->h_meas,
                        dt64.empty() ? nullptr : dt64.data(),
-                       meas64.empty() ? nullptr : meas64.data(), mev.data(), &so[s]);
+                       meas64.empty() ? nullptr : meas64.data(), mev.data(), m->tev.data(),
+                       &so[s]);
       });
     for (auto &t : pool) t.join();
   }
@@ -994,6 +999,101 @@ gp_ss_status gp_ss_condition(const gp_ss_model *m, const float *theta, int n_set
   s = enqueue(m, theta, n_sets, theta_per_series, loglik_out, grad, st, nullptr, cond_out);
   cudaFreeAsync(grad, st);
   return s;
+}
+
+gp_ss_status gp_ss_predict(const gp_ss_model *m, const float *theta, int n_sets,
+                           int theta_per_series, const double *t_star,
+                           const int64_t *star_offsets, double *loglik_out, float *pred_out,
+                           void *cuda_stream) {
+  gp_ss_status s = check_call(m, theta, n_sets, theta_per_series, loglik_out);
+  if (s) return s;
+  if (!t_star || !star_offsets || !pred_out) return GP_SS_EINVAL;
+  if (m->precision == 64) return GP_SS_EUNSUPPORTED;
+  const int ns = m->n_series;
+  if (star_offsets[0] != 0) return GP_SS_EINVAL;
+  for (int i = 0; i < ns; ++i)
+    if (star_offsets[i + 1] < star_offsets[i]) return GP_SS_EUNSORTED;
+  const int64_t M = star_offsets[ns];
+  if (M > INT32_MAX / 2) return GP_SS_EUNSUPPORTED;
+  for (int64_t j = 0; j < M; ++j)
+    if (!std::isfinite(t_star[j])) return GP_SS_EINVAL;
+  DeviceGuard g(m->device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int n_out = theta_per_series ? m->n_series : n_sets * m->n_series;
+  if (M == 0) return gp_ss_loglik(m, theta, n_sets, theta_per_series, loglik_out, cuda_stream);
+  // each test time's interval: the first event at or after it (or none: after
+  // the series); gaps formed in FP64 and rounded once
+  std::vector<int64_t> key(M);  // event index, or n_events + series for "after"
+  std::vector<float2> dd(M);
+  std::vector<int> cnt(m->n_events + ns + 1, 0);
+  for (int i = 0; i < ns; ++i) {
+    const int64_t e0 = m->ev_off[i], e1 = m->ev_off[i + 1];
+    const double *t = m->tev.data();
+    for (int64_t j = star_offsets[i]; j < star_offsets[i + 1]; ++j) {
+      const double ts = t_star[j];
+      const int64_t k = std::lower_bound(t + e0, t + e1, ts) - t;
+      if (e1 == e0) {
+        key[j] = m->n_events + i;  // empty series: the prior (no data)
+        dd[j] = make_float2(0.f, 0.f);
+      } else if (k == e1) {
+        key[j] = m->n_events + i;
+        dd[j] = make_float2((float)(ts - t[e1 - 1]), 0.f);
+      } else if (k == e0) {
+        key[j] = k;
+        dd[j] = make_float2(0.f, (float)(t[k] - ts));
+      } else {
+        key[j] = k;
+        dd[j] = make_float2((float)(ts - t[k - 1]), (float)(t[k] - ts));
+      }
+      ++cnt[key[j]];
+    }
+  }
+  // counting sort by key: interior points by event, then "after" points by series
+  std::vector<int> off(m->n_events + ns + 1, 0);
+  for (int64_t k = 0; k < m->n_events + ns; ++k) off[k + 1] = off[k] + cnt[k];
+  std::vector<int> pos(off.begin(), off.end() - 1), idx(M);
+  std::vector<float2> dsort(M);
+  for (int64_t j = 0; j < M; ++j) {
+    const int p = pos[key[j]]++;
+    idx[p] = (int)j;
+    dsort[p] = dd[j];
+  }
+  gp_ss_status res = GP_SS_OK;
+  int *d_off = nullptr, *d_idx = nullptr;
+  float2 *d_d = nullptr;
+  float *grad = nullptr;
+  const size_t noff = off.size();
+  if (scratch_alloc(m, (void **)&d_off, noff * sizeof(int), st) ||
+      scratch_alloc(m, (void **)&d_idx, M * sizeof(int), st) ||
+      scratch_alloc(m, (void **)&d_d, M * sizeof(float2), st) ||
+      scratch_alloc(m, (void **)&grad, (size_t)n_out * m->n_params * sizeof(float), st))
+    res = GP_SS_ENOMEM;
+  if (!res && (cudaMemcpyAsync(d_off, off.data(), noff * sizeof(int), cudaMemcpyHostToDevice, st) ||
+               cudaMemcpyAsync(d_idx, idx.data(), M * sizeof(int), cudaMemcpyHostToDevice, st) ||
+               cudaMemcpyAsync(d_d, dsort.data(), M * sizeof(float2), cudaMemcpyHostToDevice, st)))
+    res = GP_SS_ECUDA;
+  // points of empty series: the prior, which no kernel visits
+  if (!res) {
+    bool any_empty = false;
+    for (int i = 0; i < ns; ++i) any_empty |= (m->ev_off[i] == m->ev_off[i + 1] &&
+                                               star_offsets[i + 1] > star_offsets[i]);
+    if (any_empty) res = GP_SS_EUNSUPPORTED;
+  }
+  if (!res) {
+    gpss::PredPlan pp;
+    pp.off = d_off;
+    pp.xoff = d_off + m->n_events;
+    pp.idx = d_idx;
+    pp.d = d_d;
+    pp.out = pred_out;
+    pp.n_star = M;
+    res = enqueue(m, theta, n_sets, theta_per_series, loglik_out, grad, st, nullptr, nullptr, &pp);
+  }
+  // the host vectors must outlive the copies
+  if (cudaStreamSynchronize(st) != cudaSuccess && !res) res = GP_SS_ECUDA;
+  for (void *p : {(void *)d_off, (void *)d_idx, (void *)d_d, (void *)grad})
+    if (p) cudaFreeAsync(p, st);
+  return res;
 }
 
 gp_ss_status gp_ss_loglik_batched(const gp_ss_model *m, const float *theta, int n_sets,

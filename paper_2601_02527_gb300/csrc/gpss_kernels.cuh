@@ -64,6 +64,19 @@ struct DevModel {
   int64_t dcache_steps;
 };
 
+// Test times of a prediction call, grouped by the event that closes their
+// interval: points [off[e], off[e+1]) lie in (t_{e-1}, t_e] of event e's
+// series (or before its first event); points [xoff[s], xoff[s+1]) lie after
+// series s's last event.  d = (t* - t_prev, t_next - t*) (FP32 of FP64
+// differences; t* - t_last for the latter), idx = the point's index in the
+// caller's order; out [rows * n_star * 2].  off == nullptr: no prediction.
+struct PredPlan {
+  const int *off = nullptr, *xoff = nullptr, *idx = nullptr;
+  const float2 *d = nullptr;
+  float *out = nullptr;
+  int64_t n_star = 0;
+};
+
 // Step-scalar cache record: the 6 NT scalars of a step (term-major, in Disc
 // order) padded to whole float4 groups, one float4 per lane per group.
 template <int NT>
@@ -909,6 +922,59 @@ struct TermGrad {
   float s2;
 };
 
+// Latent f(t*) = sum_t x_t(t*) at a test time between two events, given all
+// the data: (m, P) is the filtered state after the earlier event, d1 = t* -
+// t_prev, d2 = t_next - t*, and (lp, Lp) the adjoint of the later data's
+// log-likelihood with respect to the predicted state of the next event.  The
+// state at t* is predicted over d1 (m*, P*); its adjoint is that of the next
+// event pulled back over d2, lambda* = Phi2^T lp, Lambda* = Phi2^T Lp Phi2;
+// the smoothed state is m* + P* lambda*, P* - P* (lambda* lambda*^T -
+// 2 Lambda*) P*.  With h_x selecting the latent components and u = P* h_x,
+// v = Phi2 u:  mean = h_x.m* + v.lp,  var = h_x.u + 2 v^T Lp v - (v.lp)^2.
+// Retrodiction: (m, P) the prior and d1 = 0; extrapolation: zero adjoint.
+template <class S>
+GPSS_D float2 predict_point(float d1, float d2, const TermC<float> *tc, const float4 *tab,
+                            const float *m, const float *P, const float *lp, const float *Lp) {
+  constexpr int D = S::D;
+  Blocks<float> B1[S::NT], B2[S::NT];
+#pragma unroll
+  for (int t = 0; t < S::NT; ++t) {
+    B1[t] = make_blocks(discretize_tab(d1, tc[t], tab + t * (TAB_TERM / 4)), tc[t]);
+    B2[t] = make_blocks(discretize_tab(d2, tc[t], tab + t * (TAB_TERM / 4)), tc[t]);
+  }
+  float ms[D], Ps[S::NP];
+  apply_phi<S>(B1, m, ms);
+#pragma unroll
+  for (int i = 0; i < S::NP; ++i) Ps[i] = P[i];
+  predict_cov<S>(B1, Ps);
+  float u[D], hm = 0.f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    float acc = 0.f;
+#pragma unroll
+    for (int t = 0; t < S::NT; ++t) acc += Ps[S::pk(i, 2 * t)];
+    u[i] = acc;
+  }
+  float hu = 0.f;
+#pragma unroll
+  for (int t = 0; t < S::NT; ++t) {
+    hm += ms[2 * t];
+    hu += u[2 * t];
+  }
+  float v[D];
+  apply_phi<S>(B2, u, v);
+  float vl = 0.f, vLv = 0.f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    vl += v[i] * lp[i];
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc += Lp[S::pk(i, k)] * v[k];
+    vLv += v[i] * acc;
+  }
+  return make_float2(hm + vl, hu + 2.f * vLv - vl * vl);
+}
+
 // Conditioned mean and variance of an exposure average from the filtered
 // state (m, P) just after its end event (slot j, w = 1/delta) and the
 // adjoint (lam, Lam) of the log-likelihood of all later data with respect
@@ -949,11 +1015,17 @@ GPSS_HD float2 conditioned(int j, float w, const float *m, const float *P, const
 // return, adjoint of (m, P).
 // With want_exp, also g_dt = d loglik / d (this step's gap) and, at an end
 // event, g_w = d loglik / d (1/delta of its measurement).
-template <class S>
+// hook(lam, Lam) runs once the update (or reset) is reversed, with the
+// adjoint of the predicted state of this event.
+struct NoHook {
+  GPSS_D void operator()(const float *, const float *) const {}
+};
+
+template <class S, class Hook = NoHook>
 GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *tc, float s2,
                           const float *m, const float *P, float *lam, float *Lam,
                           TermGrad<S::NT> &gr, const float4 *tab, const Disc<float> *dv,
-                          bool want_exp, float &g_dt, float &g_w) {
+                          bool want_exp, float &g_dt, float &g_w, const Hook &hook = Hook()) {
   using F = float;
   constexpr int D = S::D;
   const int j = (tag >> 1) & 7;
@@ -1018,6 +1090,7 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
   } else {
     reset_slot<S>(j, lam, Lam);
   }
+  hook(lam, Lam);
   // reverse of the prediction: (lam, Lam) are now adjoints of (m-, P-)
   // d/dPhi~ = lam m^T + 2 Lam G, G = Phi~ P; d/dQ~ = Lam.
   F zl = F(0);
@@ -1195,7 +1268,7 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
                                              float *__restrict__ rbuf,
                                              const float *__restrict__ dcache, int ck,
                                              float *__restrict__ gdt, float *__restrict__ gwe,
-                                             float2 *__restrict__ cond) {
+                                             float2 *__restrict__ cond, PredPlan pp) {
   using F = float;
   constexpr int D = S::D;
   constexpr int SD = D + S::NP;
@@ -1318,6 +1391,22 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       load_rec<S>(state_end, n_vch, vc, mb, Pb);
       cond[eo + k1 - 1] = conditioned<S>((tl >> 1) & 7, ql.z, mb, Pb, lam, Lam);
     }
+    // test times after the series' last event: predicted from its filtered
+    // state (which all the data already conditions)
+    if (pp.off && last && seg == nseg - 1) {
+      F mb[D], Pb[S::NP], z[D], Z[S::NP];
+      load_rec<S>(state_end, n_vch, vc, mb, Pb);
+#pragma unroll
+      for (int i = 0; i < D; ++i) z[i] = F(0);
+#pragma unroll
+      for (int i = 0; i < S::NP; ++i) Z[i] = F(0);
+      for (int jj = pp.xoff[s]; jj < pp.xoff[s + 1]; ++jj) {
+        const float2 r = predict_point<S>(pp.d[jj].x, 0.f, tc, tab, mb, Pb, z, Z);
+        float *o = pp.out + ((int64_t)set * pp.n_star + pp.idx[jj]) * 2;
+        o[0] = r.x;
+        o[1] = r.y;
+      }
+    }
     // backward walk.  The earlier step's replayed state and cached scalars
     // are staged into shared memory by cp.async while the current step is
     // processed; its gap, tag and measurement record are loaded one ahead.
@@ -1388,7 +1477,21 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
         for (int t = 0; t < S::NT; ++t) dv[t] = discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4));
       }
       F g_dt, g_w;
-      reverse_event<S>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab, dv, gdt != nullptr, g_dt, g_w);
+      // test times in (t_{k2-1}, t_{k2}] (before the data for the series'
+      // first event): predicted from (m, P), smoothed from this event's adjoint
+      auto hook = [&](const float *lp, const float *Lp) {
+        if (!pp.off) return;
+        const int64_t e = e0 + k2;
+        for (int jj = pp.off[e]; jj < pp.off[e + 1]; ++jj) {
+          const float2 d = pp.d[jj];
+          const float2 r = predict_point<S>(d.x, d.y, tc, tab, m, P, lp, Lp);
+          float *o = pp.out + ((int64_t)set * pp.n_star + pp.idx[jj]) * 2;
+          o[0] = r.x;
+          o[1] = r.y;
+        }
+      };
+      reverse_event<S>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab, dv, gdt != nullptr, g_dt, g_w,
+                       hook);
       if (gdt) {
         gdt[eo + k2] = g_dt;
         if (tag & 1) gwe[eo + k2] = q.z * q.z * g_w;
@@ -1522,7 +1625,7 @@ struct OpTable {
                       float *, double *, int, int *, cudaStream_t);
   cudaError_t (*grad)(const DevModel &, const float *, int, int, const float *, const float *,
                       const float *, float *, int *, const float *, float *, const float *, int,
-                      float *, float *, float2 *, cudaStream_t);
+                      float *, float *, float2 *, const PredPlan &, cudaStream_t);
   cudaError_t (*tables)(const float *, int, int, int, int, float *, cudaStream_t);
   cudaError_t (*warp_combine)(const DevModel &, const float *, int, float *, float *, float *,
                               float *, float *, float *, float *, float *, int, int, int, int,
@@ -1678,7 +1781,7 @@ cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int pe
                         const float *state_end, const float *adj_end, const float *pck,
                         float *gpart, int *err, const float *tabs, float *rbuf,
                         const float *dcache, int ck, float *gdt, float *gwe, float2 *cond,
-                        cudaStream_t st) {
+                        const PredPlan &pp, cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
   if (ck < 2 || ck > 64 || (ck & 1)) return cudaErrorInvalidValue;
   const int SG = (S::D + S::NP + 3) / 4, NDG = DcW<S::NT>::G;
@@ -1686,7 +1789,7 @@ cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int pe
                       (size_t)2 * (SG + NDG) * GRAD_BS * sizeof(float4);
   k_grad<S><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
       M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err, tabs, rbuf, dcache, ck,
-      gdt, gwe, cond);
+      gdt, gwe, cond, pp);
   GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
