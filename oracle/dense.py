@@ -19,6 +19,11 @@ alpha = sigma^2 (1 - i/(2 eta Q)), beta = omega0/(2Q) - i eta omega0, hence
 G(x) = Re(alpha (e^{-beta x} - 1 + beta x) / beta^2).
 Matern-3/2 / critically damped SHO (Q = 1/2): k(x) = sigma^2 (1 + lam x) e^{-lam x},
 G(x) = sigma^2 [2x/lam + (2/lam + x) e^{-lam x}/lam + e^{-lam x}/lam^2 - 3/lam^2].
+Overdamped SHO (Q < 1/2; Eq. sho_kernel with eta = i sqrt(1/(4Q^2) - 1), so
+cos and sin become cosh and sinh): with a = omega0/(2Q), b = omega0 sqrt(1/(4Q^2) - 1),
+k(x) = sigma^2 e^{-a x} (cosh(b x) + (a/b) sinh(b x)), a sum of two real
+exponentials c_pm e^{-lam_pm x}, c_pm = sigma^2 (1 pm a/b)/2, lam_pm = a -+ b,
+each with G = c (e^{-lam x} - 1 + lam x) / lam^2.
 """
 from __future__ import annotations
 
@@ -44,13 +49,23 @@ def split_theta(terms, theta):
     return out, theta[j]
 
 
+def overdamped_modes(sigma, w0, q, dtype=np.float64):
+    """The two real exponentials (c, lam) of the overdamped SHO kernel; the slow
+    rate a - b is formed as omega0^2 / (a + b) (no cancellation)."""
+    sigma, w0, q = dtype(sigma), dtype(w0), dtype(q)
+    a = w0 / (2 * q)
+    b = w0 * np.sqrt(1 / (4 * q * q) - 1)
+    return [(sigma ** 2 * (1 + a / b) / 2, w0 * w0 / (a + b)),
+            (sigma ** 2 * (1 - a / b) / 2, a + b)]
+
+
 def kernel(x, sigma, w0, q):
-    """Stationary SHO kernel k(|x|) (Eq. sho_kernel), Q >= 1/2."""
+    """Stationary SHO kernel k(|x|) (Eq. sho_kernel), any Q > 0."""
     x = np.abs(x)
     if q == 0.5:
         return sigma ** 2 * (1 + w0 * x) * np.exp(-w0 * x)
     if q < 0.5:
-        raise ValueError("overdamped SHO (Q < 1/2) is not supported")
+        return sum(c * np.exp(-lam * x) for c, lam in overdamped_modes(sigma, w0, q))
     eta = math.sqrt(1 - 1 / (4 * q * q))
     return sigma ** 2 * np.exp(-w0 * x / (2 * q)) * (
         np.cos(eta * w0 * x) + np.sin(eta * w0 * x) / (2 * eta * q))
@@ -68,6 +83,9 @@ def G(x, sigma, w0, q):
         lam = w0
         e = np.exp(-lam * x)
         return sigma ** 2 * (2 * x / lam + (2 / lam + x) * e / lam + e / lam ** 2 - 3 / lam ** 2)
+    if q < 0.5:
+        return sum(c * (np.exp(-lam * x) - 1 + lam * x) / lam ** 2
+                   for c, lam in overdamped_modes(sigma, w0, q, LD))
     eta = np.sqrt(1 - 1 / (4 * q * q))
     alpha = sigma ** 2 * (1 - np.clongdouble(1j) / (2 * eta * q))
     beta = w0 / (2 * q) - np.clongdouble(1j) * eta * w0
@@ -138,6 +156,8 @@ def F1(x, sigma, w0, q):
     if q == 0.5:
         lam = w0
         v = sigma ** 2 * (2 / lam - np.exp(-lam * a) * (2 / lam + a))
+    elif q < 0.5:
+        v = sum(c * -np.expm1(-lam * a) / lam for c, lam in overdamped_modes(sigma, w0, q))
     else:
         eta = math.sqrt(1 - 1 / (4 * q * q))
         alpha = sigma ** 2 * (1 - 1j / (2 * eta * q))
