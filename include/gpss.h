@@ -29,9 +29,11 @@
  *    (cudaMallocAsync) on the caller's stream and released before the call
  *    returns, so calls on different streams may share one model.
  *  - Hyperparameters are natural parameters, one row of n_params floats per
- *    set: per term (sigma, omega0, Q) for GP_SS_TERM_SHO (Q >= 1/2) or
- *    (sigma, ell) for GP_SS_TERM_MATERN32, in the order of the kernel spec,
- *    then the white-noise sd s.  n_params = 3*#SHO + 2*#Matern + 1.
+ *    set: per term (sigma, omega0, Q) for GP_SS_TERM_SHO (any Q > 0: the
+ *    overdamped oscillator Q < 1/2 of Appendix B included) or (sigma, ell)
+ *    for GP_SS_TERM_MATERN32, in the order of the kernel spec, then the
+ *    white-noise sd s.  n_params = 3*#SHO + 2*#Matern + 1.  Non-finite or
+ *    non-positive values surface as GP_SS_ENUMERIC (gp_ss_last_error_series).
  */
 #ifndef GPSS_H
 #define GPSS_H
@@ -49,7 +51,7 @@ typedef enum {
   GP_SS_EINVAL = 1,        /* bad argument: non-positive or non-finite exposure, NULL pointer, ... */
   GP_SS_EUNSORTED = 2,     /* series offsets not non-decreasing */
   GP_SS_ESELFOVERLAP = 3,  /* one instrument's exposures overlap each other */
-  GP_SS_EUNSUPPORTED = 4,  /* model shape not compiled (too many terms/slots), Q < 1/2 */
+  GP_SS_EUNSUPPORTED = 4,  /* model shape not compiled (too many terms/slots) */
   GP_SS_ENOMEM = 5,        /* device or host allocation failed */
   GP_SS_ECUDA = 6,         /* a CUDA runtime call failed */
   GP_SS_ENUMERIC = 7,      /* S <= 0 or non-finite value met on the device */

@@ -30,6 +30,18 @@
 //   w2^2 I_FF = t + I_pp + 4a^2 I_ff - 2f - 4a F1 + 2a f^2
 // (integrals of the oscillator equation multiplied by f', f and of F1^2),
 // which stay accurate once the exponential has decayed.
+//
+// Overdamped oscillator (Q < 1/2, beta < 0; the cosh/sinh transition of
+// Appendix B): f = e^{-a t} sinh(b t)/b, b = sqrt(-beta), decays with the two
+// rates l1 = w2/(a + b) (slow) and a + b (fast).  The Taylor branch then
+// covers (a + b) t <= 1.2 (its convergence is set by the fast rate) and the
+// identities above need the slow mode to have decayed (l1 t >= 1.2: below
+// that they cancel like (a + b)^4 / w2^2).  In between, the step is halved
+// into the Taylor range and the integrals doubled back with the semigroup
+// identities of the augmented model, Phi~(2t) = Phi~(t)^2 and Q~(2t) =
+// Phi~(t) Q~(t) Phi~(t)^T + Q~(t), written on the six scalars
+// (disc_double_integrals), with f and f' evaluated directly from the two
+// decaying modes at every level.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -39,6 +51,7 @@
 #include <stdint.h>
 
 #define GPSS_HD __host__ __device__ __forceinline__
+#define GPSS_HDNI static __host__ __device__ __noinline__
 #define GPSS_D __device__ __forceinline__
 
 namespace gpss {
@@ -121,9 +134,16 @@ template <class F> GPSS_HD Dual2<F> gexp(Dual2<F> x) {
   F e = gexp(x.v);
   return mk(e, e * x.da, e * x.db);
 }
+GPSS_HD float gsqrt(float x) { return sqrtf(x); }
+GPSS_HD double gsqrt(double x) { return sqrt(x); }
+template <class F> GPSS_HD Dual2<F> gsqrt(Dual2<F> x) {
+  F r = gsqrt(x.v), h = F(0.5) / r;
+  return mk(r, h * x.da, h * x.db);
+}
 
 // S(beta, t) = sin(sqrt(beta) t) / sqrt(beta)  (= t at beta = 0),
-// C(beta, t) = cos(sqrt(beta) t), for beta >= 0.
+// C(beta, t) = cos(sqrt(beta) t), for beta >= 0 (the overdamped case is
+// evaluated by disc_overdamped).
 GPSS_HD void sinc_pair(float beta, float t, float &S, float &C) {
   float b = sqrtf(beta);
   float tau = b * t;
@@ -225,14 +245,13 @@ GPSS_HD Disc<T> disc_taylor(F t, T a, T w2) {
   return d;
 }
 
+// Closed-form branch from f and f' through the integral identities of the
+// header comment.
 template <class T, class F>
-GPSS_HD Disc<T> disc_closed(F t, T a, T beta, T w2) {
-  T E = gexp(-a * t);
-  T S, C;
-  sinc_pair(beta, t, S, C);
+GPSS_HD Disc<T> disc_from_ffp(F t, T a, T w2, T f, T fp) {
   Disc<T> d;
-  d.f = E * S;
-  d.fp = E * (C - a * S);
+  d.f = f;
+  d.fp = fp;
   const T rw2 = cst<T>(F(1)) / w2;
   d.F1 = (F(1) - d.fp - F(2) * a * d.f) * rw2;
   d.Ipp = (F(1) - d.fp * d.fp - w2 * d.f * d.f) / (F(4) * a);
@@ -243,8 +262,112 @@ GPSS_HD Disc<T> disc_closed(F t, T a, T beta, T w2) {
   return d;
 }
 
-// All six per-term scalars for a step of length t >= 0.
 template <class T, class F>
+GPSS_HD Disc<T> disc_closed(F t, T a, T beta, T w2) {
+  T E = gexp(-a * t);
+  T S, C;
+  sinc_pair(beta, t, S, C);
+  return disc_from_ffp<T, F>(t, a, w2, E * S, E * (C - a * S));
+}
+
+// The integrals at 2t from the six scalars at t (Phi~(2t) = Phi~(t)^2,
+// Q~(2t) = Phi~(t) Q~(t) Phi~(t)^T + Q~(t) on the blocks of one term; p =
+// Phi_00, (p0, F1) = Phibar).  f and f' at 2t are left to the caller: formed
+// by the same squaring their relative error would double with every step.
+template <class T, class F>
+GPSS_HD void disc_double_integrals(Disc<T> &d, T a, T w2) {
+  const T f = d.f, fp = d.fp, F1 = d.F1, Iff = d.Iff, Ipp = d.Ipp;
+  const T ff = f * f, f3 = ff * f;
+  const T p = fp + F(2) * a * f;
+  const T p0 = f + F(2) * a * F1;
+  d.F1 = F1 * (F(1) + p) + ff;
+  d.Iff = Iff * (F(1) + p * p) + p * f3 + ff * Ipp;
+  d.Ipp = Ipp * (F(1) + fp * fp) + w2 * w2 * ff * Iff - w2 * fp * f3;
+  d.IFF = F(2) * d.IFF + p0 * p0 * Iff + p0 * F1 * ff + F1 * F1 * Ipp + p0 * F1 * F1 +
+          F(2) * F1 * (f * F1 - Iff);
+}
+
+// Number of halvings that bring a step t into the Taylor range r2 h^2 <= XT2
+// (h = t / 2^k exactly; at most 64).
+template <class F>
+GPSS_HD int halvings(F t, F r2, F xt2, F &h) {
+  int k = 0;
+  h = t;
+  while (r2 * h * h > xt2 && k < 64) {
+    h *= F(0.5);
+    ++k;
+  }
+  return k;
+}
+
+// e^{-a t} (sinh(b t)/b, cosh(b t)) for b t < 1/2 by their series in
+// x = (b t)^2 = -beta t^2 (truncation below 1e-17 of each).
+template <class T, class F>
+GPSS_HD void sinhc_pair(T x, F t, T &S, T &C) {
+  S = (F(1) + x * (F(1.0 / 6) + x * (F(1.0 / 120) + x * (F(1.0 / 5040) + x * (F(1.0 / 362880) +
+        x * (F(1.0 / 39916800) + x * F(1.0 / 6227020800.0))))))) * t;
+  C = F(1) + x * (F(0.5) + x * (F(1.0 / 24) + x * (F(1.0 / 720) + x * (F(1.0 / 40320) +
+        x * (F(1.0 / 3628800) + x * (F(1.0 / 479001600) + x * F(1.0 / 87178291200.0)))))));
+}
+
+// f = e^{-a t} sinh(b t)/b and f' of the overdamped oscillator (b =
+// sqrt(-beta)) without cancellation: the series below b t = 1/2, else the two
+// decaying modes, f = (e^{-l1 t} - e^{-l2 t}) / (2b), f' = (l2 e^{-l2 t} -
+// l1 e^{-l1 t}) / (2b), l2 = a + b, l1 = w2 / l2 (= a - b).
+template <class T, class F>
+GPSS_HD void od_f_fp(F t, T a, T beta, T b, T w2, T &f, T &fp) {
+  if (val(b) * t < F(0.5)) {
+    T S, C;
+    sinhc_pair<T, F>(-beta * (t * t), t, S, C);
+    const T E = gexp(-a * t);
+    f = E * S;
+    fp = E * (C - a * S);
+  } else {
+    const T l2 = a + b, l1 = w2 / l2;
+    const T e1 = gexp(-l1 * t), e2 = gexp(-l2 * t);
+    const T r = cst<T>(F(0.5)) / b;
+    f = (e1 - e2) * r;
+    fp = (l2 * e2 - l1 * e1) * r;
+  }
+}
+
+// Overdamped step above the Taylor range (beta < 0).  While the slow mode
+// has not decayed (l1 t < sqrt(XT2)) the step is halved into the Taylor
+// range and the integrals doubled back, with f and f' evaluated directly at
+// every level; after that the identities from f and f'.
+template <class T, class F>
+GPSS_HD Disc<T> disc_overdamped(F t, T a, T beta, T w2, F r2) {
+  const F xt2 = TaylorOrder<F>::XT2;
+  const F l1 = val(w2) / sqrt(r2);
+  const T b = gsqrt(-beta);
+  if (l1 * t * l1 * t < xt2) {
+    F h;
+    const int k = halvings<F>(t, r2, xt2, h);
+    Disc<T> d = disc_taylor<T, F>(h, a, w2);
+    for (int i = 0; i < k; ++i) {
+      disc_double_integrals<T, F>(d, a, w2);
+      h *= F(2);
+      od_f_fp<T, F>(h, a, beta, b, w2, d.f, d.fp);
+    }
+    return d;
+  }
+  T f, fp;
+  od_f_fp<T, F>(t, a, beta, b, w2, f, fp);
+  return disc_from_ffp<T, F>(t, a, w2, f, fp);
+}
+
+// Square of the fastest rate of the impulse response: w2 (beta >= 0) or
+// (a + b)^2 (beta < 0); the Taylor branch serves r2 t^2 <= XT2.
+template <class F>
+GPSS_HD F rate2(F a, F beta) {
+  if (beta >= F(0)) return beta + a * a;
+  const F r = a + sqrt(-beta);
+  return r * r;
+}
+
+// All six per-term scalars for a step of length t >= 0.  OD = false drops
+// the overdamped branches (for hyperparameter rows without a Q < 1/2 term).
+template <class T, class F, bool OD = true>
 GPSS_HD Disc<T> discretize(F t, T a, T beta) {
   T w2 = beta + a * a;
   if (t == F(0)) {
@@ -257,35 +380,42 @@ GPSS_HD Disc<T> discretize(F t, T a, T beta) {
     d.IFF = d.f;
     return d;
   }
-  if (val(w2) * t * t <= TaylorOrder<F>::XT2) return disc_taylor<T, F>(t, a, w2);
+  if constexpr (!OD) {
+    if (val(w2) * t * t <= TaylorOrder<F>::XT2) return disc_taylor<T, F>(t, a, w2);
+  } else {
+    const F r2 = rate2<F>(val(a), val(beta));
+    if (r2 * t * t <= TaylorOrder<F>::XT2) return disc_taylor<T, F>(t, a, w2);
+    if (val(beta) < F(0)) return disc_overdamped<T, F>(t, a, beta, w2, r2);
+  }
   return disc_closed<T, F>(t, a, beta, w2);
 }
 
 // Per-term constants from natural parameters, with the reciprocals and the
 // oscillation frequency the closed-form branch needs precomputed:
-// b = sqrt(beta), rb = 1/b (0 when b = 0), rw2 = 1/w2, r4a = 1/(4a).
+// b = sqrt(|beta|), rb = 1/b (0 when b = 0), rw2 = 1/w2, r4a = 1/(4a),
+// r2 = rate2(a, beta) (the Taylor branch's bound).
 template <class F>
 struct TermC {
   F a, beta, w2, qc, var;
-  F b, rb, rw2, r4a;
+  F b, rb, rw2, r4a, r2;
 };
 
 template <class F>
 GPSS_HD void finish_termc(TermC<F> &c) {
-  c.b = sqrt(c.beta);
+  c.b = sqrt(fabs(c.beta));
   c.rb = c.b > F(0) ? F(1) / c.b : F(0);
   c.rw2 = F(1) / c.w2;
   c.r4a = F(1) / (F(4) * c.a);
+  c.r2 = rate2<F>(c.a, c.beta);
 }
 
 // Closed-form branch with the per-term constants precomputed (no division,
 // no square root per step).  S = sin(b t)/b, C = cos(b t) as in sinc_pair.
 template <class T, class F>
-GPSS_HD Disc<T> disc_closed_k(F t, T a, T w2, T rw2, T r4a, T S, T C) {
-  T E = gexp(-a * t);
+GPSS_HD Disc<T> disc_closed_ffp(F t, T a, T w2, T rw2, T r4a, T f, T fp) {
   Disc<T> d;
-  d.f = E * S;
-  d.fp = E * (C - a * S);
+  d.f = f;
+  d.fp = fp;
   const T a2 = a * F(2);
   d.F1 = (F(1) - d.fp - a2 * d.f) * rw2;
   const T ff = d.f * d.f;
@@ -294,6 +424,12 @@ GPSS_HD Disc<T> disc_closed_k(F t, T a, T w2, T rw2, T r4a, T S, T C) {
   d.IFF = (cst<T>(t) + d.Ipp + a2 * a2 * d.Iff - F(2) * d.f - a2 * F(2) * d.F1 + a2 * ff) *
           (rw2 * rw2);
   return d;
+}
+
+template <class T, class F>
+GPSS_HD Disc<T> disc_closed_k(F t, T a, T w2, T rw2, T r4a, T S, T C) {
+  const T E = gexp(-a * t);
+  return disc_closed_ffp<T, F>(t, a, w2, rw2, r4a, E * S, E * (C - a * S));
 }
 
 GPSS_HD void sinc_pair_k(float t, float b, float rb, float &S, float &C) {
@@ -319,7 +455,7 @@ GPSS_HD void sinc_pair_k(float t, float b, float rb, float &S, float &C) {
 // c_{n+2} = -(2a (n+1) c_{n+1} + w2 c_n) / ((n+2)(n+1))).
 //
 // The table holds the Chebyshev economisation of these series on the range
-// the table serves, [0, T] with w2 T^2 = XT2 (1% margin): TAB_NTAY Taylor
+// the table serves, [0, T] with r2 T^2 = XT2 (1% margin): TAB_NTAY Taylor
 // terms (truncation ~1e-13 there), then each power u^n (u = t/T) from the
 // top down to TAB_NC is traded for the lower powers of the shifted Chebyshev
 // polynomial T*_n(u) = T_n(2u - 1), whose leading coefficient is 2^(2n-1)
@@ -402,9 +538,9 @@ GPSS_HD void taylor_coeff_pre(const T *c, const T *e, const T *p, const double *
   g[5] = s3 * rcp[k + 5];
 }
 
-// Range of the table: t in [0, T], T = 1.01 sqrt(XT2 / w2).
-GPSS_HD double table_range(double w2) {
-  return 1.01 * sqrt((double)TaylorOrder<float>::XT2 / w2);
+// Range of the table: t in [0, T], T = 1.01 sqrt(XT2 / r2), r2 = rate2(a, beta).
+GPSS_HD double table_range(double r2) {
+  return 1.01 * sqrt((double)TaylorOrder<float>::XT2 / r2);
 }
 
 // The economisation as a fixed linear map in u = t / T: coefficient k < NC of
@@ -455,7 +591,7 @@ template <class T>
 GPSS_HD void table_coeffs(const EconMap &E, T a, T beta, T (&e)[6][TAB_NC]) {
   T g[6][TAB_NTAY];
   taylor_coeffs<T>(a, beta, g);
-  const double rng = table_range(val(beta + a * a));
+  const double rng = table_range(rate2<double>(val(a), val(beta)));
   for (int j = 0; j < 6; ++j)
     for (int k = 0; k < TAB_NC; ++k) e[j][k] = econ_apply<T>(E, k, rng, g[j], 1);
 }
@@ -517,7 +653,45 @@ GPSS_HD Disc<Dual2<float>> disc_tab_dual(float t, const float4 *__restrict__ tab
   return d;
 }
 
-// Discretisation with the Taylor branch read from a table.
+// Overdamped step above the table's range (beta < 0), FP32 values or (a,
+// beta) duals (T = Dual2<float>: the forward-mode arithmetic differentiates
+// the same steps), as disc_overdamped with the Taylor branch read from the
+// table.  The dual version is kept out of line (it serves only the
+// gradient's tangents; inlined, its registers would spill in the reverse walk).
+GPSS_HD void tab_eval(float h, const float4 *tab, Disc<float> &d) { d = disc_tab(h, tab); }
+GPSS_HD void tab_eval(float h, const float4 *tab, Disc<Dual2<float>> &d) { d = disc_tab_dual(h, tab); }
+
+template <class T>
+GPSS_HD Disc<T> disc_od_tab_t(float t, const TermC<float> &c, T a, T beta, T b, T w2,
+                              const float4 *tab) {
+  const float xt2 = TaylorOrder<float>::XT2;
+  const float l1t = c.w2 * t / sqrtf(c.r2);
+  if (l1t * l1t < xt2) {
+    float h;
+    const int k = halvings<float>(t, c.r2, xt2, h);
+    Disc<T> d;
+    tab_eval(h, tab, d);
+    for (int i = 0; i < k; ++i) {
+      disc_double_integrals<T, float>(d, a, w2);
+      h *= 2.f;
+      od_f_fp<T, float>(h, a, beta, b, w2, d.f, d.fp);
+    }
+    return d;
+  }
+  T f, fp;
+  od_f_fp<T, float>(t, a, beta, b, w2, f, fp);
+  return disc_from_ffp<T, float>(t, a, w2, f, fp);
+}
+
+GPSS_HDNI Disc<Dual2<float>> disc_od_tab_dual(float t, const TermC<float> &c, const float4 *tab) {
+  // b = sqrt(-beta): db/dbeta = -1/(2b); w2 = beta + a^2
+  return disc_od_tab_t<Dual2<float>>(t, c, mk(c.a, 1.f, 0.f), mk(c.beta, 0.f, 1.f),
+                                     mk(c.b, 0.f, -0.5f * c.rb), mk(c.w2, 2.f * c.a, 1.f), tab);
+}
+
+// Discretisation with the Taylor branch read from a table.  OD = false
+// drops the overdamped branches (rows without a Q < 1/2 term).
+template <bool OD = true>
 GPSS_HD Disc<float> discretize_tab(float t, const TermC<float> &c, const float4 *tab) {
   if (t == 0.f) {
     Disc<float> d;
@@ -526,13 +700,49 @@ GPSS_HD Disc<float> discretize_tab(float t, const TermC<float> &c, const float4 
     d.F1 = d.Iff = d.Ipp = d.IFF = 0.f;
     return d;
   }
-  if (c.w2 * t * t <= TaylorOrder<float>::XT2) return disc_tab(t, tab);
-  float S, C;
-  sinc_pair_k(t, c.b, c.rb, S, C);
-  return disc_closed_k<float, float>(t, c.a, c.w2, c.rw2, c.r4a, S, C);
+  if constexpr (!OD) {
+    if (c.w2 * t * t <= TaylorOrder<float>::XT2) return disc_tab(t, tab);
+    float S, C;
+    sinc_pair_k(t, c.b, c.rb, S, C);
+    return disc_closed_k<float, float>(t, c.a, c.w2, c.rw2, c.r4a, S, C);
+  }
+  constexpr float xt2 = TaylorOrder<float>::XT2;
+  float h = t;
+  int k = 0;
+  bool in_tab = c.r2 * t * t <= xt2;
+  if (!in_tab && c.beta < 0.f) {
+    // overdamped with the slow mode not yet decayed: halve into the table's
+    // range, double the integrals back (f, f' direct at every level)
+    const float l1t = c.w2 * t * rsqrtf(c.r2);
+    if (l1t * l1t < xt2) {
+      k = halvings<float>(t, c.r2, xt2, h);
+      in_tab = true;
+    }
+  }
+  if (in_tab) {
+    Disc<float> d = disc_tab(h, tab);
+    for (int i = 0; i < k; ++i) {
+      disc_double_integrals<float, float>(d, c.a, c.w2);
+      h *= 2.f;
+      od_f_fp<float, float>(h, c.a, c.beta, c.b, c.w2, d.f, d.fp);
+    }
+    return d;
+  }
+  float f, fp;
+  if (c.beta < 0.f) {
+    od_f_fp<float, float>(t, c.a, c.beta, c.b, c.w2, f, fp);
+  } else {
+    float S, C;
+    sinc_pair_k(t, c.b, c.rb, S, C);
+    const float E = gexp(-c.a * t);
+    f = E * S;
+    fp = E * (C - c.a * S);
+  }
+  return disc_closed_ffp<float, float>(t, c.a, c.w2, c.rw2, c.r4a, f, fp);
 }
 
 // Same with forward-mode derivatives in (a, beta).
+template <bool OD = true>
 GPSS_HD Disc<Dual2<float>> discretize_tab_dual(float t, const TermC<float> &c, const float4 *tab) {
   if (t == 0.f) {
     Disc<Dual2<float>> d;
@@ -541,7 +751,12 @@ GPSS_HD Disc<Dual2<float>> discretize_tab_dual(float t, const TermC<float> &c, c
     d.F1 = d.Iff = d.Ipp = d.IFF = d.f;
     return d;
   }
-  if (c.w2 * t * t <= TaylorOrder<float>::XT2) return disc_tab_dual(t, tab);
+  if constexpr (!OD) {
+    if (c.w2 * t * t <= TaylorOrder<float>::XT2) return disc_tab_dual(t, tab);
+  } else {
+    if (c.r2 * t * t <= TaylorOrder<float>::XT2) return disc_tab_dual(t, tab);
+    if (c.beta < 0.f) return disc_od_tab_dual(t, c, tab);
+  }
   float s, co;
   sinc_pair_k(t, c.b, c.rb, s, co);
   // dS/dbeta = (t C - S) / (2 beta) (series for small beta t^2); dC/dbeta = -t S / 2
@@ -632,6 +847,7 @@ GPSS_HD void disc_closed_tangents(float t, const TermC<float> &c, const Disc<flo
 
 // Tangents for a step of length t, either branch (same branch rule as
 // discretize_tab).
+template <bool OD = true>
 GPSS_HD void disc_tangents(float t, const TermC<float> &c, const float4 *tab, const Disc<float> &d,
                            float (&da)[6], float (&db)[6]) {
   if (t == 0.f) {
@@ -639,10 +855,26 @@ GPSS_HD void disc_tangents(float t, const TermC<float> &c, const float4 *tab, co
     for (int i = 0; i < 6; ++i) da[i] = db[i] = 0.f;
     return;
   }
-  if (c.w2 * t * t <= TaylorOrder<float>::XT2)
+  if constexpr (!OD) {
+    if (c.w2 * t * t <= TaylorOrder<float>::XT2)
+      disc_tab_tangents(t, tab, da, db);
+    else
+      disc_closed_tangents(t, c, d, da, db);
+    return;
+  }
+  if (c.r2 * t * t <= TaylorOrder<float>::XT2) {
     disc_tab_tangents(t, tab, da, db);
-  else
+  } else if (c.beta < 0.f) {
+    const Disc<Dual2<float>> e = disc_od_tab_dual(t, c, tab);
+    const Dual2<float> v[6] = {e.f, e.fp, e.F1, e.Iff, e.Ipp, e.IFF};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      da[i] = v[i].da;
+      db[i] = v[i].db;
+    }
+  } else {
     disc_closed_tangents(t, c, d, da, db);
+  }
 }
 
 // Blocks of Phi~ and Q~ for one term (see header comment).
@@ -825,6 +1057,16 @@ GPSS_HD void load_terms(const float *th, const int *kinds, TermC<F> *tc, F &s2) 
   }
   F s = F(th[j]);
   s2 = s * s;
+}
+
+// True when some term of the row is an overdamped oscillator (beta < 0);
+// rows without one run the kernels' specialisation without those branches.
+template <int NT, class F>
+GPSS_HD bool any_overdamped(const TermC<F> *tc) {
+  bool od = false;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) od |= tc[t].beta < F(0);
+  return od;
 }
 
 // P0 = blkdiag(P_inf, I) (Section 3.2.3); m0 = 0.

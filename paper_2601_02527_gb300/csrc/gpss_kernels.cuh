@@ -134,18 +134,24 @@ template <> GPSS_D void load_meas<double>(const DevModel &M, int64_t i, double &
   w = __ldg(M.meas64 + 3 * i + 2);
 }
 
+// Compile-time tag selecting a kernel body with (true) or without (false) the
+// overdamped-oscillator branches of the discretisation; the kernels test the
+// row's terms once and run the matching body.
+template <bool V>
+struct OdTag {
+  static constexpr bool value = V;
+};
+
 // One event of the sequential filter on (m, P); returns true for an end
 // event, with S and v of its innovation.
 // Per-step scalars of term t: from the warp's Taylor table when one is given
 // (FP32 chunk kernels), else from the on-the-fly series (per-series kernels).
-template <class F>
+template <class F, bool OD>
 GPSS_D Disc<F> disc_step(F dt, const TermC<F> &c, const float4 *tab) {
-  return discretize<F, F>(dt, c.a, c.beta);
-}
-template <>
-GPSS_D Disc<float> disc_step<float>(float dt, const TermC<float> &c, const float4 *tab) {
-  if (tab) return discretize_tab(dt, c, tab);
-  return discretize<float, float>(dt, c.a, c.beta);
+  if constexpr (sizeof(F) == sizeof(float)) {
+    if (tab) return discretize_tab<OD>(dt, c, tab);
+  }
+  return discretize<F, F, OD>(dt, c.a, c.beta);
 }
 
 // One event of the sequential filter on (m, P) given its gap, tag and (for an
@@ -155,13 +161,13 @@ template <class S, class F>
 GPSS_D bool filter_blocks(const Blocks<F> *B, uint8_t tag, F y, F r0, F w, F s2, F *m, F *P,
                           F &Sv, F &v);
 
-template <class S, class F>
+template <class S, class F, bool OD = true>
 GPSS_D bool filter_step(F dt, uint8_t tag, F y, F r0, F w, const TermC<F> *tc, F s2, F *m, F *P,
                         F &Sv, F &v, const float4 *tab) {
   Blocks<F> B[S::NT];
 #pragma unroll
   for (int t = 0; t < S::NT; ++t)
-    B[t] = make_blocks(disc_step<F>(dt, tc[t], tab ? tab + t * (TAB_TERM / 4) : nullptr), tc[t]);
+    B[t] = make_blocks(disc_step<F, OD>(dt, tc[t], tab ? tab + t * (TAB_TERM / 4) : nullptr), tc[t]);
   return filter_blocks<S, F>(B, tag, y, r0, w, s2, m, P, Sv, v);
 }
 
@@ -195,7 +201,7 @@ GPSS_D bool filter_blocks(const Blocks<F> *B, uint8_t tag, F y, F r0, F w, F s2,
 }
 
 // Same, loading the event's data itself (per-series kernels).
-template <class S, class F>
+template <class S, class F, bool OD = true>
 GPSS_D bool filter_event(const DevModel &M, int64_t k, int64_t &mi, const TermC<F> *tc, F s2, F *m,
                          F *P, F &Sv, F &v, const float4 *tab = nullptr) {
   const F dt = load_dt<F>(M, k);
@@ -205,7 +211,7 @@ GPSS_D bool filter_event(const DevModel &M, int64_t k, int64_t &mi, const TermC<
     load_meas<F>(M, mi, y, r0, w);
     ++mi;
   }
-  return filter_step<S, F>(dt, tag, y, r0, w, tc, s2, m, P, Sv, v, tab);
+  return filter_step<S, F, OD>(dt, tag, y, r0, w, tc, s2, m, P, Sv, v, tab);
 }
 
 // Event reader for the FP32 chunk kernels: the gap and tag of the next event
@@ -320,7 +326,7 @@ __global__ void __launch_bounds__(32 * TABLE_WARPS) k_tables(const float *__rest
     for (int j = 0; j < 6; ++j) sg[w][j][lane] = g[j];
   }
   __syncwarp();
-  const double rng = table_range(tc[t].w2);
+  const double rng = table_range(tc[t].r2);
   float *base = tab + (size_t)rt * TAB_NC * TAB_W;
   for (int o = lane; o < 6 * TAB_NC; o += 32) {
     const int j = o / TAB_NC, k = o % TAB_NC;
@@ -365,26 +371,33 @@ __global__ void __launch_bounds__(128) k_plain(DevModel M, const float *__restri
   TermC<F> tc[S::NT];
   F s2;
   load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tc, s2);
-  F m[S::D], P[S::NP];
-  init_state<S>(tc, m, P);
-  double sum_logS = 0.0, sum_q = 0.0;
-  int64_t n_end = 0;
-  bool bad = false;
-  int64_t mi = M.meas_off[s];
-  const int64_t e1 = M.ev_off[s + 1];
-  for (int64_t k = M.ev_off[s]; k < e1; ++k) {
-    F Sv, vv;
-    if (filter_event<S, F>(M, k, mi, tc, s2, m, P, Sv, vv)) {
-      bad |= !(Sv > F(0));
-      sum_logS += glog(Sv);
-      sum_q += (double)(vv * vv / Sv);
-      ++n_end;
+  auto body = [&](auto od_tag) {
+    constexpr bool OD = decltype(od_tag)::value;
+    F m[S::D], P[S::NP];
+    init_state<S>(tc, m, P);
+    double sum_logS = 0.0, sum_q = 0.0;
+    int64_t n_end = 0;
+    bool bad = false;
+    int64_t mi = M.meas_off[s];
+    const int64_t e1 = M.ev_off[s + 1];
+    for (int64_t k = M.ev_off[s]; k < e1; ++k) {
+      F Sv, vv;
+      if (filter_event<S, F, OD>(M, k, mi, tc, s2, m, P, Sv, vv)) {
+        bad |= !(Sv > F(0));
+        sum_logS += glog(Sv);
+        sum_q += (double)(vv * vv / Sv);
+        ++n_end;
+      }
     }
-  }
-  const double ll = -0.5 * ((double)n_end * LOG_2PI + sum_logS + sum_q);
-  bad |= !isfinite(ll);
-  ll_out[v] = ll;
-  if (bad) flag_error(err, v, 7);
+    const double ll = -0.5 * ((double)n_end * LOG_2PI + sum_logS + sum_q);
+    bad |= !isfinite(ll);
+    ll_out[v] = ll;
+    if (bad) flag_error(err, v, 7);
+  };
+  if (any_overdamped<S::NT>(tc))
+    body(OdTag<true>{});
+  else
+    body(OdTag<false>{});
 }
 
 // ---------------------------------------------------------------------------
@@ -423,7 +436,7 @@ GPSS_D void store_elem(float *dst, int n_vch, int vc, const float (&A)[S::D][S::
 // fields as above plus the number of measurements before that point.  With
 // dcache set, every step's six scalars per term go to the step-scalar cache
 // (for the gradient's forward replay).
-template <class S>
+template <class S, bool OD>
 __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restrict__ theta, int n_vch,
                                               int per_series, float *__restrict__ ef,
                                               double *__restrict__ ed, int *__restrict__ err,
@@ -444,6 +457,9 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
   TermC<F> tc[S::NT];
   F s2;
   load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tc, s2);
+  // rows with an overdamped term run in the OD = true launch, the others in
+  // the OD = false one (whole warps: a warp's chunks share one row)
+  if (any_overdamped<S::NT>(tc) != OD) return;
   const float4 *tab =
       stage_table<S::NT>(tabs, row, smem_tab + (threadIdx.x >> 5) * (S::NT * TAB_TERM / 4));
   const bool first = M.ch_flags[c] & 1;
@@ -493,7 +509,7 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
       float x[W];
 #pragma unroll
       for (int t = 0; t < S::NT; ++t) {
-        const Disc<F> d = discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4));
+        const Disc<F> d = discretize_tab<OD>(dt, tc[t], tab + t * (TAB_TERM / 4));
         x[6 * t] = d.f;
         x[6 * t + 1] = d.fp;
         x[6 * t + 2] = d.F1;
@@ -932,15 +948,15 @@ struct TermGrad {
 // 2 Lambda*) P*.  With h_x selecting the latent components and u = P* h_x,
 // v = Phi2 u:  mean = h_x.m* + v.lp,  var = h_x.u + 2 v^T Lp v - (v.lp)^2.
 // Retrodiction: (m, P) the prior and d1 = 0; extrapolation: zero adjoint.
-template <class S>
+template <class S, bool OD = true>
 GPSS_D float2 predict_point(float d1, float d2, const TermC<float> *tc, const float4 *tab,
                             const float *m, const float *P, const float *lp, const float *Lp) {
   constexpr int D = S::D;
   Blocks<float> B1[S::NT], B2[S::NT];
 #pragma unroll
   for (int t = 0; t < S::NT; ++t) {
-    B1[t] = make_blocks(discretize_tab(d1, tc[t], tab + t * (TAB_TERM / 4)), tc[t]);
-    B2[t] = make_blocks(discretize_tab(d2, tc[t], tab + t * (TAB_TERM / 4)), tc[t]);
+    B1[t] = make_blocks(discretize_tab<OD>(d1, tc[t], tab + t * (TAB_TERM / 4)), tc[t]);
+    B2[t] = make_blocks(discretize_tab<OD>(d2, tc[t], tab + t * (TAB_TERM / 4)), tc[t]);
   }
   float ms[D], Ps[S::NP];
   apply_phi<S>(B1, m, ms);
@@ -1021,7 +1037,7 @@ struct NoHook {
   GPSS_D void operator()(const float *, const float *) const {}
 };
 
-template <class S, class Hook = NoHook>
+template <class S, bool OD = true, class Hook = NoHook>
 GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *tc, float s2,
                           const float *m, const float *P, float *lam, float *Lam,
                           TermGrad<S::NT> &gr, const float4 *tab, const Disc<float> *dv,
@@ -1159,7 +1175,7 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
                 (f * F1 - Iff) * q_z1 + IFF * q_zz;
     // through the discretisation: (a, beta) tangents of the six scalars
     F da[6], db[6];
-    disc_tangents(dt, c, tab + t * (TAB_TERM / 4), dv[t], da, db);
+    disc_tangents<OD>(dt, c, tab + t * (TAB_TERM / 4), dv[t], da, db);
     gr.a[t] += bf * da[0] + bfp * da[1] + bF1 * da[2] + bIff * da[3] + bIpp * da[4] + bIFF * da[5];
     gr.beta[t] += bf * db[0] + bfp * db[1] + bF1 * db[2] + bIff * db[3] + bIpp * db[4] + bIFF * db[5];
     if (want_exp) {
@@ -1293,261 +1309,274 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   const int bs = blockDim.x;
   float4 *stg = tab_slots + (bs / 32) * (S::NT * TAB_TERM / 4) + threadIdx.x;
   const float4 *tab = stage_table<S::NT>(tabs, row, tab_slots + (threadIdx.x >> 5) * (S::NT * TAB_TERM / 4));
-  const uint8_t flags = M.ch_flags[c];
-  const bool first = flags & 1, last = flags & 2;
-  F m[D], P[S::NP];
-  const int64_t e0 = M.ch_ev0[c];
-  const int len = M.ch_len[c];
-  const int nseg = (len + ck - 1) / ck;
-  const int f0 = len - (nseg - 1) * ck;
-  F lam[D], Lam[S::NP];
-  if (last) {
-#pragma unroll
-    for (int i = 0; i < D; ++i) lam[i] = F(0);
-#pragma unroll
-    for (int i = 0; i < S::NP; ++i) Lam[i] = F(0);
-  } else {
-    load_rec<S>(adj_end, n_vch, vc, lam, Lam);
-  }
-  TermGrad<S::NT> gr;
-#pragma unroll
-  for (int t = 0; t < S::NT; ++t) gr.a[t] = gr.beta[t] = gr.w2[t] = gr.qc[t] = gr.var[t] = F(0);
-  gr.s2 = F(0);
-  const int64_t m0 = M.ch_meas0[c];
-  // per-event exposure adjoints of this chunk (theta set `set`)
-  const int64_t eo = (int64_t)set * M.n_events + e0;
-  float4 *my = reinterpret_cast<float4 *>(rbuf) + vc;  // group v of slot k at (k SG + v) n_vch
-  const size_t rs = (size_t)n_vch;
-  const float4 *dc = dcache_col<S::NT>(M, const_cast<float *>(dcache), vc);
-  bool bad = false;
-  for (int seg = nseg - 1; seg >= 0; --seg) {
-    const int k0 = seg == 0 ? 0 : f0 + (seg - 1) * ck;
-    const int k1 = seg == 0 ? f0 : k0 + ck;
-    int mrel = 0;
-    if (seg == 0) {
-      if (first)
-        init_state<S>(tc, m, P);
-      else
-        load_rec<S>(state_end, n_vch, vc - 1, m, P);
+  // EX: conditioned outputs, predictions or exposure gradients requested
+  auto body = [&](auto od_tag, auto ex_tag) {
+    constexpr bool OD = decltype(od_tag)::value;
+    constexpr bool EX = decltype(ex_tag)::value;
+    const uint8_t flags = M.ch_flags[c];
+    const bool first = flags & 1, last = flags & 2;
+    F m[D], P[S::NP];
+    const int64_t e0 = M.ch_ev0[c];
+    const int len = M.ch_len[c];
+    const int nseg = (len + ck - 1) / ck;
+    const int f0 = len - (nseg - 1) * ck;
+    F lam[D], Lam[S::NP];
+    if (last) {
+  #pragma unroll
+      for (int i = 0; i < D; ++i) lam[i] = F(0);
+  #pragma unroll
+      for (int i = 0; i < S::NP; ++i) Lam[i] = F(0);
     } else {
-      F mi[D], Pi[S::NP];
-      if (first) {
-        // the first chunk's element already starts from the prior (A = 0)
-#pragma unroll
-        for (int i = 0; i < D; ++i) mi[i] = F(0);
-#pragma unroll
-        for (int i = 0; i < S::NP; ++i) Pi[i] = F(0);
+      load_rec<S>(adj_end, n_vch, vc, lam, Lam);
+    }
+    TermGrad<S::NT> gr;
+  #pragma unroll
+    for (int t = 0; t < S::NT; ++t) gr.a[t] = gr.beta[t] = gr.w2[t] = gr.qc[t] = gr.var[t] = F(0);
+    gr.s2 = F(0);
+    const int64_t m0 = M.ch_meas0[c];
+    // per-event exposure adjoints of this chunk (theta set `set`)
+    const int64_t eo = (int64_t)set * M.n_events + e0;
+    float4 *my = reinterpret_cast<float4 *>(rbuf) + vc;  // group v of slot k at (k SG + v) n_vch
+    const size_t rs = (size_t)n_vch;
+    const float4 *dc = dcache_col<S::NT>(M, const_cast<float *>(dcache), vc);
+    bool bad = false;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+      const int k0 = seg == 0 ? 0 : f0 + (seg - 1) * ck;
+      const int k1 = seg == 0 ? f0 : k0 + ck;
+      int mrel = 0;
+      if (seg == 0) {
+        if (first)
+          init_state<S>(tc, m, P);
+        else
+          load_rec<S>(state_end, n_vch, vc - 1, m, P);
       } else {
-        load_rec<S>(state_end, n_vch, vc - 1, mi, Pi);
-      }
-      const float *src = pck + (size_t)(seg - 1) * (NF + 1) * n_vch;
-      apply_partial<S>(src, n_vch, vc, mi, Pi, m, P);
-      mrel = __float_as_int(src[(size_t)NF * n_vch + vc]);
-    }
-    // forward replay of the segment (step scalars from the cache, the next
-    // step's loaded one ahead, or recomputed)
-    EventReader rd;
-    rd.start(M, e0 + k0, e0 + k1, m0 + mrel);
-    const float4 *dcr = dc ? dc + (size_t)k0 * (32 * NDG) : nullptr;
-    float nx[NDC];
-    if (dcr) dcache_load<S::NT>(dcr, nx);
-    for (int kk = k0; kk < k1; ++kk) {
-      const int slot = kk - k0;
-      {
-        float r[4 * SG];
-#pragma unroll
-        for (int i = 0; i < D; ++i) r[i] = m[i];
-#pragma unroll
-        for (int i = 0; i < S::NP; ++i) r[D + i] = P[i];
-#pragma unroll
-        for (int i = SD; i < 4 * SG; ++i) r[i] = 0.f;
-#pragma unroll
-        for (int v = 0; v < SG; ++v)
-          my[(size_t)(slot * SG + v) * rs] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
-      }
-      F dt, Sv, vv;
-      uint8_t tag;
-      float4 q;
-      rd.next(dt, tag, q);
-      Blocks<F> B[S::NT];
-      if (dcr) {
-#pragma unroll
-        for (int t = 0; t < S::NT; ++t) B[t] = make_blocks(dcache_term<S::NT>(nx, t), tc[t]);
-        dcr += 32 * NDG;
-        if (kk + 1 < k1) dcache_load<S::NT>(dcr, nx);
-      } else {
-#pragma unroll
-        for (int t = 0; t < S::NT; ++t)
-          B[t] = make_blocks(discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4)), tc[t]);
-      }
-      if (filter_blocks<S, F>(B, tag, q.x, q.y, q.z, s2, m, P, Sv, vv)) bad |= !(Sv > F(0));
-    }
-    // conditioned mean and variance of the chunk's last event, if it ends an
-    // exposure: the chunk's end state and its boundary adjoint
-    if (cond && seg == nseg - 1 && (__ldg(M.tag + e0 + k1 - 1) & 1)) {
-      const uint8_t tl = __ldg(M.tag + e0 + k1 - 1);
-      const float4 ql = __ldg(M.meas + rd.mi - 1);
-      F mb[D], Pb[S::NP];
-      load_rec<S>(state_end, n_vch, vc, mb, Pb);
-      cond[eo + k1 - 1] = conditioned<S>((tl >> 1) & 7, ql.z, mb, Pb, lam, Lam);
-    }
-    // test times after the series' last event: predicted from its filtered
-    // state (which all the data already conditions)
-    if (pp.off && last && seg == nseg - 1) {
-      F mb[D], Pb[S::NP], z[D], Z[S::NP];
-      load_rec<S>(state_end, n_vch, vc, mb, Pb);
-#pragma unroll
-      for (int i = 0; i < D; ++i) z[i] = F(0);
-#pragma unroll
-      for (int i = 0; i < S::NP; ++i) Z[i] = F(0);
-      for (int jj = pp.xoff[s]; jj < pp.xoff[s + 1]; ++jj) {
-        const float2 r = predict_point<S>(pp.d[jj].x, 0.f, tc, tab, mb, Pb, z, Z);
-        float *o = pp.out + ((int64_t)set * pp.n_star + pp.idx[jj]) * 2;
-        o[0] = r.x;
-        o[1] = r.y;
-      }
-    }
-    // backward walk.  The earlier step's replayed state and cached scalars
-    // are staged into shared memory by cp.async while the current step is
-    // processed; its gap, tag and measurement record are loaded one ahead.
-    // The measurement index of event k (relative to m0) is the count of end
-    // events before k, tracked downwards from the replay's end.
-    auto stage = [&](int buf, int slot, int kk) {
-      float4 *dst = stg + (size_t)buf * (SG + NDG) * bs;
-#pragma unroll
-      for (int v = 0; v < SG; ++v) cp_async16(dst + v * bs, my + (size_t)(slot * SG + v) * rs);
-      if (dc) {
-        const float4 *src = dc + (size_t)kk * (32 * NDG);
-#pragma unroll
-        for (int v = 0; v < NDG; ++v) cp_async16(dst + (SG + v) * bs, src + 32 * v);
-      }
-      cp_async_commit();
-    };
-    int k2 = k1 - 1;
-    F dt_n = __ldg(M.dt + e0 + k2);
-    uint8_t tag_n = __ldg(M.tag + e0 + k2);
-    int mr = (int)(rd.mi - m0) - (tag_n & 1);
-    float4 q_n = __ldg(M.meas + m0 + mr);
-    stage(0, k2 - k0, k2);
-    for (; k2 >= k0; --k2) {
-      const int slot = k2 - k0, buf = (k1 - 1 - k2) & 1;
-      const F dt = dt_n;
-      const uint8_t tag = tag_n;
-      const float4 q = q_n;
-      if (k2 > k0) {
-        dt_n = __ldg(M.dt + e0 + k2 - 1);
-        tag_n = __ldg(M.tag + e0 + k2 - 1);
-        mr -= tag_n & 1;
-        q_n = __ldg(M.meas + m0 + mr);
-        stage(buf ^ 1, slot - 1, k2 - 1);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      const float4 *sb = stg + (size_t)buf * (SG + NDG) * bs;
-      {
-        float r[4 * SG];
-#pragma unroll
-        for (int v = 0; v < SG; ++v) {
-          const float4 g4 = sb[v * bs];
-          r[4 * v] = g4.x;
-          r[4 * v + 1] = g4.y;
-          r[4 * v + 2] = g4.z;
-          r[4 * v + 3] = g4.w;
+        F mi[D], Pi[S::NP];
+        if (first) {
+          // the first chunk's element already starts from the prior (A = 0)
+  #pragma unroll
+          for (int i = 0; i < D; ++i) mi[i] = F(0);
+  #pragma unroll
+          for (int i = 0; i < S::NP; ++i) Pi[i] = F(0);
+        } else {
+          load_rec<S>(state_end, n_vch, vc - 1, mi, Pi);
         }
-#pragma unroll
-        for (int i = 0; i < D; ++i) m[i] = r[i];
-#pragma unroll
-        for (int i = 0; i < S::NP; ++i) P[i] = r[D + i];
+        const float *src = pck + (size_t)(seg - 1) * (NF + 1) * n_vch;
+        apply_partial<S>(src, n_vch, vc, mi, Pi, m, P);
+        mrel = __float_as_int(src[(size_t)NF * n_vch + vc]);
       }
-      Disc<F> dv[S::NT];
-      if (dc) {
-#pragma unroll
-        for (int v = 0; v < NDG; ++v) {
-          const float4 g4 = sb[(SG + v) * bs];
-          nx[4 * v] = g4.x;
-          nx[4 * v + 1] = g4.y;
-          nx[4 * v + 2] = g4.z;
-          nx[4 * v + 3] = g4.w;
+      // forward replay of the segment (step scalars from the cache, the next
+      // step's loaded one ahead, or recomputed)
+      EventReader rd;
+      rd.start(M, e0 + k0, e0 + k1, m0 + mrel);
+      const float4 *dcr = dc ? dc + (size_t)k0 * (32 * NDG) : nullptr;
+      float nx[NDC];
+      if (dcr) dcache_load<S::NT>(dcr, nx);
+      for (int kk = k0; kk < k1; ++kk) {
+        const int slot = kk - k0;
+        {
+          float r[4 * SG];
+  #pragma unroll
+          for (int i = 0; i < D; ++i) r[i] = m[i];
+  #pragma unroll
+          for (int i = 0; i < S::NP; ++i) r[D + i] = P[i];
+  #pragma unroll
+          for (int i = SD; i < 4 * SG; ++i) r[i] = 0.f;
+  #pragma unroll
+          for (int v = 0; v < SG; ++v)
+            my[(size_t)(slot * SG + v) * rs] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
         }
-#pragma unroll
-        for (int t = 0; t < S::NT; ++t) dv[t] = dcache_term<S::NT>(nx, t);
-      } else {
-#pragma unroll
-        for (int t = 0; t < S::NT; ++t) dv[t] = discretize_tab(dt, tc[t], tab + t * (TAB_TERM / 4));
+        F dt, Sv, vv;
+        uint8_t tag;
+        float4 q;
+        rd.next(dt, tag, q);
+        Blocks<F> B[S::NT];
+        if (dcr) {
+  #pragma unroll
+          for (int t = 0; t < S::NT; ++t) B[t] = make_blocks(dcache_term<S::NT>(nx, t), tc[t]);
+          dcr += 32 * NDG;
+          if (kk + 1 < k1) dcache_load<S::NT>(dcr, nx);
+        } else {
+  #pragma unroll
+          for (int t = 0; t < S::NT; ++t)
+            B[t] = make_blocks(discretize_tab<OD>(dt, tc[t], tab + t * (TAB_TERM / 4)), tc[t]);
+        }
+        if (filter_blocks<S, F>(B, tag, q.x, q.y, q.z, s2, m, P, Sv, vv)) bad |= !(Sv > F(0));
       }
-      F g_dt, g_w;
-      // test times in (t_{k2-1}, t_{k2}] (before the data for the series'
-      // first event): predicted from (m, P), smoothed from this event's adjoint
-      auto hook = [&](const float *lp, const float *Lp) {
-        if (!pp.off) return;
-        const int64_t e = e0 + k2;
-        for (int jj = pp.off[e]; jj < pp.off[e + 1]; ++jj) {
-          const float2 d = pp.d[jj];
-          const float2 r = predict_point<S>(d.x, d.y, tc, tab, m, P, lp, Lp);
+      // conditioned mean and variance of the chunk's last event, if it ends an
+      // exposure: the chunk's end state and its boundary adjoint
+      if (EX && cond && seg == nseg - 1 && (__ldg(M.tag + e0 + k1 - 1) & 1)) {
+        const uint8_t tl = __ldg(M.tag + e0 + k1 - 1);
+        const float4 ql = __ldg(M.meas + rd.mi - 1);
+        F mb[D], Pb[S::NP];
+        load_rec<S>(state_end, n_vch, vc, mb, Pb);
+        cond[eo + k1 - 1] = conditioned<S>((tl >> 1) & 7, ql.z, mb, Pb, lam, Lam);
+      }
+      // test times after the series' last event: predicted from its filtered
+      // state (which all the data already conditions)
+      if (EX && pp.off && last && seg == nseg - 1) {
+        F mb[D], Pb[S::NP], z[D], Z[S::NP];
+        load_rec<S>(state_end, n_vch, vc, mb, Pb);
+  #pragma unroll
+        for (int i = 0; i < D; ++i) z[i] = F(0);
+  #pragma unroll
+        for (int i = 0; i < S::NP; ++i) Z[i] = F(0);
+        for (int jj = pp.xoff[s]; jj < pp.xoff[s + 1]; ++jj) {
+          const float2 r = predict_point<S, OD>(pp.d[jj].x, 0.f, tc, tab, mb, Pb, z, Z);
           float *o = pp.out + ((int64_t)set * pp.n_star + pp.idx[jj]) * 2;
           o[0] = r.x;
           o[1] = r.y;
         }
-      };
-      reverse_event<S>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab, dv, gdt != nullptr, g_dt, g_w,
-                       hook);
-      if (gdt) {
-        gdt[eo + k2] = g_dt;
-        if (tag & 1) gwe[eo + k2] = q.z * q.z * g_w;
       }
-      // (m, P) is the filtered state after event k2 - 1 and (lam, Lam) now its
-      // adjoint: the conditioned values of that event's measurement
-      if (cond && k2 > 0) {
-        const uint8_t tp = k2 > k0 ? tag_n : __ldg(M.tag + e0 + k2 - 1);
-        if (tp & 1) {
-          const float4 qp = k2 > k0 ? q_n : __ldg(M.meas + m0 + mr - 1);
-          cond[eo + k2 - 1] = conditioned<S>((tp >> 1) & 7, qp.z, m, P, lam, Lam);
+      // backward walk.  The earlier step's replayed state and cached scalars
+      // are staged into shared memory by cp.async while the current step is
+      // processed; its gap, tag and measurement record are loaded one ahead.
+      // The measurement index of event k (relative to m0) is the count of end
+      // events before k, tracked downwards from the replay's end.
+      auto stage = [&](int buf, int slot, int kk) {
+        float4 *dst = stg + (size_t)buf * (SG + NDG) * bs;
+  #pragma unroll
+        for (int v = 0; v < SG; ++v) cp_async16(dst + v * bs, my + (size_t)(slot * SG + v) * rs);
+        if (dc) {
+          const float4 *src = dc + (size_t)kk * (32 * NDG);
+  #pragma unroll
+          for (int v = 0; v < NDG; ++v) cp_async16(dst + (SG + v) * bs, src + 32 * v);
+        }
+        cp_async_commit();
+      };
+      int k2 = k1 - 1;
+      F dt_n = __ldg(M.dt + e0 + k2);
+      uint8_t tag_n = __ldg(M.tag + e0 + k2);
+      int mr = (int)(rd.mi - m0) - (tag_n & 1);
+      float4 q_n = __ldg(M.meas + m0 + mr);
+      stage(0, k2 - k0, k2);
+      for (; k2 >= k0; --k2) {
+        const int slot = k2 - k0, buf = (k1 - 1 - k2) & 1;
+        const F dt = dt_n;
+        const uint8_t tag = tag_n;
+        const float4 q = q_n;
+        if (k2 > k0) {
+          dt_n = __ldg(M.dt + e0 + k2 - 1);
+          tag_n = __ldg(M.tag + e0 + k2 - 1);
+          mr -= tag_n & 1;
+          q_n = __ldg(M.meas + m0 + mr);
+          stage(buf ^ 1, slot - 1, k2 - 1);
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
+        }
+        const float4 *sb = stg + (size_t)buf * (SG + NDG) * bs;
+        {
+          float r[4 * SG];
+  #pragma unroll
+          for (int v = 0; v < SG; ++v) {
+            const float4 g4 = sb[v * bs];
+            r[4 * v] = g4.x;
+            r[4 * v + 1] = g4.y;
+            r[4 * v + 2] = g4.z;
+            r[4 * v + 3] = g4.w;
+          }
+  #pragma unroll
+          for (int i = 0; i < D; ++i) m[i] = r[i];
+  #pragma unroll
+          for (int i = 0; i < S::NP; ++i) P[i] = r[D + i];
+        }
+        Disc<F> dv[S::NT];
+        if (dc) {
+  #pragma unroll
+          for (int v = 0; v < NDG; ++v) {
+            const float4 g4 = sb[(SG + v) * bs];
+            nx[4 * v] = g4.x;
+            nx[4 * v + 1] = g4.y;
+            nx[4 * v + 2] = g4.z;
+            nx[4 * v + 3] = g4.w;
+          }
+  #pragma unroll
+          for (int t = 0; t < S::NT; ++t) dv[t] = dcache_term<S::NT>(nx, t);
+        } else {
+  #pragma unroll
+          for (int t = 0; t < S::NT; ++t) dv[t] = discretize_tab<OD>(dt, tc[t], tab + t * (TAB_TERM / 4));
+        }
+        F g_dt, g_w;
+        // test times in (t_{k2-1}, t_{k2}] (before the data for the series'
+        // first event): predicted from (m, P), smoothed from this event's adjoint
+        auto hook = [&](const float *lp, const float *Lp) {
+          if (!EX || !pp.off) return;
+          const int64_t e = e0 + k2;
+          for (int jj = pp.off[e]; jj < pp.off[e + 1]; ++jj) {
+            const float2 d = pp.d[jj];
+            const float2 r = predict_point<S, OD>(d.x, d.y, tc, tab, m, P, lp, Lp);
+            float *o = pp.out + ((int64_t)set * pp.n_star + pp.idx[jj]) * 2;
+            o[0] = r.x;
+            o[1] = r.y;
+          }
+        };
+        reverse_event<S, OD>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab, dv, EX && gdt != nullptr, g_dt, g_w,
+                         hook);
+        if (EX && gdt) {
+          gdt[eo + k2] = g_dt;
+          if (tag & 1) gwe[eo + k2] = q.z * q.z * g_w;
+        }
+        // (m, P) is the filtered state after event k2 - 1 and (lam, Lam) now its
+        // adjoint: the conditioned values of that event's measurement
+        if (EX && cond && k2 > 0) {
+          const uint8_t tp = k2 > k0 ? tag_n : __ldg(M.tag + e0 + k2 - 1);
+          if (tp & 1) {
+            const float4 qp = k2 > k0 ? q_n : __ldg(M.meas + m0 + mr - 1);
+            cond[eo + k2 - 1] = conditioned<S>((tp >> 1) & 7, qp.z, m, P, lam, Lam);
+          }
         }
       }
     }
-  }
-  if (first) {
-    // P0 = blkdiag(var diag(1, w2), I)
-#pragma unroll
+    if (first) {
+      // P0 = blkdiag(var diag(1, w2), I)
+  #pragma unroll
+      for (int t = 0; t < S::NT; ++t) {
+        gr.var[t] += Lam[S::pk(2 * t, 2 * t)] + tc[t].w2 * Lam[S::pk(2 * t + 1, 2 * t + 1)];
+        gr.w2[t] += tc[t].var * Lam[S::pk(2 * t + 1, 2 * t + 1)];
+      }
+    }
+    // chain to natural parameters
+    const float *th = theta + (size_t)row * M.n_params;
+    float *g = gpart + vc;
+    const size_t gs = (size_t)n_vch;
+    int p = 0;
+  #pragma unroll
     for (int t = 0; t < S::NT; ++t) {
-      gr.var[t] += Lam[S::pk(2 * t, 2 * t)] + tc[t].w2 * Lam[S::pk(2 * t + 1, 2 * t + 1)];
-      gr.w2[t] += tc[t].var * Lam[S::pk(2 * t + 1, 2 * t + 1)];
+      const F ga = gr.a[t] + F(2) * tc[t].a * gr.w2[t];
+      const F gb = gr.beta[t] + gr.w2[t];
+      if (M.kinds[t] == 1) {
+        const F sig = th[p], w0 = th[p + 1], q = th[p + 2];
+        const F dsig = gr.qc[t] * F(4) * w0 * w0 * w0 * sig / q + gr.var[t] * F(2) * sig;
+        const F dw0 = ga / (F(2) * q) + gb * F(2) * w0 * (F(1) - F(1) / (F(4) * q * q)) +
+                      gr.qc[t] * F(6) * w0 * w0 * sig * sig / q;
+        const F dq = -ga * w0 / (F(2) * q * q) + gb * w0 * w0 / (F(2) * q * q * q) -
+                     gr.qc[t] * F(2) * w0 * w0 * w0 * sig * sig / (q * q);
+        g[p * gs] = dsig;
+        g[(p + 1) * gs] = dw0;
+        g[(p + 2) * gs] = dq;
+        p += 3;
+      } else {
+        const F sig = th[p], ell = th[p + 1];
+        const F w0 = F(1.7320508075688772) / ell;
+        const F dsig = gr.qc[t] * F(8) * w0 * w0 * w0 * sig + gr.var[t] * F(2) * sig;
+        // a = w0, w2 = w0^2 (through ga), qc = 4 w0^3 sig^2 ; beta = 0 along this family
+        const F dw0 = gr.a[t] + F(2) * w0 * gr.w2[t] + gr.qc[t] * F(12) * w0 * w0 * sig * sig;
+        g[p * gs] = dsig;
+        g[(p + 1) * gs] = dw0 * (-w0 / ell);
+        p += 2;
+      }
     }
-  }
-  // chain to natural parameters
-  const float *th = theta + (size_t)row * M.n_params;
-  float *g = gpart + vc;
-  const size_t gs = (size_t)n_vch;
-  int p = 0;
-#pragma unroll
-  for (int t = 0; t < S::NT; ++t) {
-    const F ga = gr.a[t] + F(2) * tc[t].a * gr.w2[t];
-    const F gb = gr.beta[t] + gr.w2[t];
-    if (M.kinds[t] == 1) {
-      const F sig = th[p], w0 = th[p + 1], q = th[p + 2];
-      const F dsig = gr.qc[t] * F(4) * w0 * w0 * w0 * sig / q + gr.var[t] * F(2) * sig;
-      const F dw0 = ga / (F(2) * q) + gb * F(2) * w0 * (F(1) - F(1) / (F(4) * q * q)) +
-                    gr.qc[t] * F(6) * w0 * w0 * sig * sig / q;
-      const F dq = -ga * w0 / (F(2) * q * q) + gb * w0 * w0 / (F(2) * q * q * q) -
-                   gr.qc[t] * F(2) * w0 * w0 * w0 * sig * sig / (q * q);
-      g[p * gs] = dsig;
-      g[(p + 1) * gs] = dw0;
-      g[(p + 2) * gs] = dq;
-      p += 3;
-    } else {
-      const F sig = th[p], ell = th[p + 1];
-      const F w0 = F(1.7320508075688772) / ell;
-      const F dsig = gr.qc[t] * F(8) * w0 * w0 * w0 * sig + gr.var[t] * F(2) * sig;
-      // a = w0, w2 = w0^2 (through ga), qc = 4 w0^3 sig^2 ; beta = 0 along this family
-      const F dw0 = gr.a[t] + F(2) * w0 * gr.w2[t] + gr.qc[t] * F(12) * w0 * w0 * sig * sig;
-      g[p * gs] = dsig;
-      g[(p + 1) * gs] = dw0 * (-w0 / ell);
-      p += 2;
-    }
-  }
-  g[p * gs] = gr.s2 * F(2) * th[p];
-  if (bad) flag_error(err, orow, 7);
+    g[p * gs] = gr.s2 * F(2) * th[p];
+    if (bad) flag_error(err, orow, 7);
+  };
+  // rows with an overdamped term take the general body (rare); the others
+  // the lean one unless extra outputs are requested
+  if (any_overdamped<S::NT>(tc))
+    body(OdTag<true>{}, OdTag<true>{});
+  else if (cond || pp.off || gdt)
+    body(OdTag<false>{}, OdTag<true>{});
+  else
+    body(OdTag<false>{}, OdTag<false>{});
 }
 
 // Ordered per-series sums over chunks (deterministic): log-likelihood parts
@@ -1660,8 +1689,14 @@ cudaError_t launch_elem(const DevModel &M, const float *theta, int n_vch, int pe
   if (pck && (ck < 2 || ck > 64 || (ck & 1))) return cudaErrorInvalidValue;
   const int bs = 128;
   const size_t smem = (size_t)(bs / 32) * S::NT * TAB_TERM * sizeof(float);
-  k_elem<S><<<(n_vch + bs - 1) / bs, bs, smem, st>>>(M, theta, n_vch, per_series, ef, ed, err,
-                                                    tabs, pck, pck ? ck : 1, dcache);
+  // two launches: rows without an overdamped term (the lean body), then rows
+  // with one; each skips the other's rows
+  const int nb = (n_vch + bs - 1) / bs;
+  k_elem<S, false><<<nb, bs, smem, st>>>(M, theta, n_vch, per_series, ef, ed, err, tabs, pck,
+                                         pck ? ck : 1, dcache);
+  GPSS_COUNT_LAUNCH();
+  k_elem<S, true><<<nb, bs, smem, st>>>(M, theta, n_vch, per_series, ef, ed, err, tabs, pck,
+                                        pck ? ck : 1, dcache);
   GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }

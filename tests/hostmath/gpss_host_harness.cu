@@ -140,7 +140,7 @@ double hh_table_check(double a, double beta, int which) {
   Dual2<double> g[6][TAB_NTAY], e[6][TAB_NC];
   taylor_coeffs<Dual2<double>>(mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), g);
   table_coeffs<Dual2<double>>(E, mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), e);
-  const double T = table_range(beta + a * a);
+  const double T = table_range(rate2<double>(a, beta));
   double worst = 0.0;
   for (int j = 0; j < 6; ++j)
     for (int q = which ? 1 : 0; q < (which ? 3 : 1); ++q) {

@@ -54,8 +54,11 @@ def test_two_sho_layout1(gp, chunk, ck, cache):
     th = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
     ll, g, dexp = m.loglik_grad(th, exposure=True)
     ll2, g2 = m.loglik_grad(th)
+    # the call with exposure gradients runs a separately compiled kernel body:
+    # the same arithmetic up to FP32 rounding order
     np.testing.assert_array_equal(ll.cpu().numpy(), ll2.cpu().numpy())
-    np.testing.assert_array_equal(g.cpu().numpy(), g2.cpu().numpy())
+    np.testing.assert_allclose(g.cpu().numpy(), g2.cpu().numpy(), rtol=1e-5,
+                               atol=1e-6 * np.abs(g2.cpu().numpy()).max())
     dexp = dexp.cpu().numpy()[0]
     for s in range(wl.n_series):
         a, b = wl.offsets[s], wl.offsets[s + 1]

@@ -1,0 +1,154 @@
+"""GPU parity for overdamped SHO terms (Q < 1/2) against the FP64 oracle.
+
+The device discretisation of an overdamped term has three branches (Taylor
+table for (a + b) t <= 1.2; halving into the table and doubling back while the
+slow mode has not decayed; the integral identities from the two decaying
+modes after that).  Checked here with the tolerances of the other parity
+tests: the discretisation entries on a grid of step lengths through all three
+branches, the FP64 plain filter, the FP32 log-likelihood under every
+schedule, the hyperparameter gradient, the exposure gradient, the
+conditioned measurements and the prediction, on workloads where some series
+have one or both terms overdamped (0.05 <= Q < 1/2).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SHO, M32 = 1, 2
+QS = [0.05, 0.2, 0.3, 0.45, 0.499]
+
+
+@pytest.fixture(scope="module")
+def gp():
+    from paper_2601_02527_gb300 import build as gbuild
+    gbuild.build()
+    import paper_2601_02527_gb300 as g
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    oracle.build()
+    return g
+
+
+def _overdamped(wl, both_every=3):
+    """Q of the first term < 1/2 in every series; of the second too in every
+    `both_every`-th series (two-SHO workloads); FP32-rounded parameters."""
+    th = wl.theta.copy()
+    for s in range(th.shape[0]):
+        th[s, 2] = QS[s % len(QS)]
+        if th.shape[1] == 7 and s % both_every == 0:
+            th[s, 5] = QS[(s + 2) % len(QS)]
+    wl.theta = th.astype(np.float32).astype(np.float64)
+    return wl
+
+
+def _check_ll(got, ref, counts):
+    for a, b, n in zip(got, ref, counts):
+        assert abs(a - b) <= 1e-4 * max(abs(b), 0.1 * n), (a, b, n)
+
+
+def _check_rows(got, ref):
+    for a, b in zip(np.asarray(got, float), np.asarray(ref, float)):
+        scale = np.max(np.abs(b))
+        bad = np.abs(a - b) > 1e-3 * np.abs(b) + 1e-4 * scale
+        assert not bad.any(), (a, b)
+
+
+def _dev(th):
+    return torch.tensor(th, dtype=torch.float32, device="cuda")
+
+
+@pytest.mark.parametrize("terms,theta", [([SHO], [1.0, 0.8, 0.05, 0.1]),
+                                         ([SHO], [0.7, 3.1, 0.3, 0.1]),
+                                         ([SHO, M32], [1.0, 2.0, 0.45, 0.5, 2.0, 0.1]),
+                                         ([SHO], [1.0, 1.0, 0.499, 0.1])])
+def test_discretization_grid(gp, terms, theta):
+    th32 = np.asarray(theta, np.float32)
+    dts = np.concatenate([[0.0], np.logspace(-6, np.log10(3000.0), 401)]).astype(np.float32)
+    phi, q = gp.discretize(terms, 0, 1, _dev(th32), _dev(dts))
+    phi, q = phi.cpu().numpy(), q.cpu().numpy()
+    for k, dt in enumerate(dts):
+        P, Q, _ = oracle.discretize(terms, 0, 1, th32.astype(np.float64), float(dt))
+        for got, ref in ((phi[k], P), (q[k], Q)):
+            scale = np.max(np.abs(ref))
+            ok = np.abs(got - ref) <= 2e-5 * np.abs(ref) + 2e-6 * scale
+            assert ok.all(), (dt, got, ref)
+
+
+def test_plain_fp64(gp):
+    wl = _overdamped(synth.c2(n_series=5, scale=0.05))
+    m = gp.Model.from_workload(wl, precision=64)
+    ll = m.loglik(_dev(wl.theta)).cpu().numpy()
+    ref = oracle.loglik_workload(wl, processes=4)
+    for a, b in zip(ll, ref):
+        assert abs(a - b) <= 1e-9 * abs(b), (a, b)
+
+
+@pytest.mark.parametrize("schedule,chunk", [(1, 0), (2, 64), (0, 0), (3, 0)])
+def test_fp32_loglik(gp, schedule, chunk):
+    wl = _overdamped(synth.c2(n_series=10, scale=0.08))
+    m = gp.Model.from_workload(wl, schedule=schedule, chunk_len=chunk)
+    ll = m.loglik(_dev(wl.theta)).cpu().numpy()
+    _check_ll(ll, oracle.loglik_workload(wl, processes=4), np.diff(wl.offsets))
+    assert m.last_error() == (-1, 0)
+
+
+@pytest.mark.parametrize("chunk,ck,cache", [(48, 8, 0), (0, 32, 1), (64, 64, 0)])
+def test_gradient(gp, chunk, ck, cache):
+    wl = _overdamped(synth.c4(n_series=6, scale=0.05))
+    m = gp.Model.from_workload(wl, chunk_len=chunk, ckpt_interval=ck, step_cache=cache)
+    ll, g = m.loglik_grad(_dev(wl.theta))
+    ref_ll, ref_g = oracle.loglik_workload(wl, grad=True, processes=4)
+    _check_ll(ll.cpu().numpy(), ref_ll, np.diff(wl.offsets))
+    _check_rows(g.cpu().numpy(), ref_g)
+
+
+def test_exposure_gradient(gp):
+    wl = _overdamped(synth.c4(n_series=3, scale=0.012), both_every=2)
+    m = gp.Model.from_workload(wl, chunk_len=32, ckpt_interval=8)
+    _, _, dexp = m.loglik_grad(_dev(wl.theta), exposure=True)
+    dexp = dexp.cpu().numpy()[0]
+    for s in range(wl.n_series):
+        ts, te, y, ye, inst = wl.series(s)
+        r_ts, r_te = oracle.exposure_grad(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s],
+                                          instrument=inst)
+        ref = np.stack([r_ts, r_te], axis=1)
+        got = dexp[wl.offsets[s]:wl.offsets[s + 1]]
+        bad = np.abs(got - ref) > 1e-3 * np.abs(ref) + 1e-4 * np.abs(ref).max()
+        assert not bad.any(), (s, got[bad][:5], ref[bad][:5])
+
+
+def test_condition_and_predict(gp):
+    wl = _overdamped(synth.c4(n_series=4, scale=0.04), both_every=2)
+    m = gp.Model.from_workload(wl, chunk_len=48, ckpt_interval=16)
+    th = _dev(wl.theta)
+    _, cond = m.condition(th)
+    cond = cond.cpu().numpy()[0]
+    rng = np.random.default_rng(71)
+    tq, offs = [], [0]
+    for s in range(wl.n_series):
+        ts, te, _, _, _ = wl.series(s)
+        q = np.concatenate([[ts.min() - 1.5], ts[::7], te[::5],
+                            np.sort(rng.uniform(ts.min(), te.max(), 60)), [te.max() + 0.4]])
+        tq.append(q)
+        offs.append(offs[-1] + len(q))
+    tq, offs = np.concatenate(tq), np.array(offs, np.int64)
+    _, pred = m.predict(th, tq, offs)
+    pred = pred.cpu().numpy()[0]
+    for s in range(wl.n_series):
+        ts, te, y, ye, inst = wl.series(s)
+        for got, (mu, va) in (
+                (cond[wl.offsets[s]:wl.offsets[s + 1]],
+                 oracle.condition(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s], instrument=inst)),
+                (pred[offs[s]:offs[s + 1]],
+                 oracle.predict(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s],
+                                tq[offs[s]:offs[s + 1]], instrument=inst))):
+            gm, gv = got[:, 0].astype(np.float64), got[:, 1].astype(np.float64)
+            assert np.all(np.abs(gm - mu) <= 1e-3 * np.abs(mu).max() + 1e-5 * np.abs(mu))
+            bad = np.abs(gv - va) > 2e-3 * np.abs(va) + 1e-5 * va.max()
+            assert not bad.any(), (s, gv[bad][:5], va[bad][:5])

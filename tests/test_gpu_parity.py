@@ -260,7 +260,7 @@ def test_numeric_failure_is_reported(gp):
     wl = f32_theta(synth.c4(n_series=4, scale=0.02))
     m = gp.Model.from_workload(wl)
     th = theta_dev(wl)
-    th[2, 2] = 0.3  # Q < 1/2 is outside the supported regime -> non-finite values
+    th[2, 2] = float("nan")  # a non-finite parameter -> non-finite innovation variances
     m.loglik(th)
     torch.cuda.synchronize()
     row, code = m.last_error()

@@ -71,16 +71,19 @@ def oracle_scalars(w0, q, t):
 
 
 CASES = [(2 * math.pi / 10, 3.0), (math.sqrt(3) / 5, 0.5), (2.0, 0.55), (1.0, 9.5), (8.0, 1.0)]
+# overdamped oscillator (Q < 1/2): halving/doubling and two-exponential branches
+OVERDAMPED = [(1.0, 0.3), (0.5, 0.05), (2.0, 0.45), (1.0, 0.15), (0.3, 0.499)]
 
 
 def ab(w0, q):
     return w0 / (2 * q), (w0 * w0 * (1 - 1 / (4 * q * q)) if q != 0.5 else 0.0)
 
 
-@pytest.mark.parametrize("w0,q", CASES)
+@pytest.mark.parametrize("w0,q", CASES + OVERDAMPED)
 def test_step_scalars_match_oracle(oracle_lib, hh, w0, q):
     a, beta = ab(w0, q)
-    ts = np.logspace(-5, math.log10(40.0), 120) / w0
+    # up to 40 decay times of the slowest mode (rate ~ omega0 Q for Q << 1/2)
+    ts = np.logspace(-5, math.log10(40.0 / min(1.0, 2 * q)), 160) / w0
     refs = np.array([oracle_scalars(w0, q, t) for t in ts])
     floor = np.max(np.abs(refs), axis=0)
     out = np.zeros(6)
@@ -93,12 +96,15 @@ def test_step_scalars_match_oracle(oracle_lib, hh, w0, q):
 
 @pytest.mark.parametrize("path", ["dual", "tangents"])
 @pytest.mark.parametrize("w0,q", [(2 * math.pi / 10, 3.0), (2.0, 0.55), (1.0, 9.5),
-                                  (0.7, 0.52), (5.0, 30.0)])
+                                  (0.7, 0.52), (5.0, 30.0), (1.0, 0.3), (0.5, 0.05), (2.0, 0.45)])
 def test_step_scalar_derivatives(oracle_lib, hh, w0, q, path):
     a, beta = ab(w0, q)
     out = np.zeros(18)
     fn = hh.hh_discretize_dual if path == "dual" else hh.hh_discretize_tangents
-    for x in (0.01, 0.3, 0.9, 1.1, 1.3, 2.5, 8.0, 30.0):
+    xs = (0.01, 0.3, 0.9, 1.1, 1.3, 2.5, 8.0, 30.0)
+    if q < 0.5:
+        xs = xs + (0.05, 0.15, 90.0, 400.0)
+    for x in xs:
         t = x / w0
         fn(t, a, beta, _p(out, ctypes.c_double))
         da, db = out[6:12], out[12:18]
@@ -112,7 +118,8 @@ def test_step_scalar_derivatives(oracle_lib, hh, w0, q, path):
             assert np.all(np.abs(got - ref) <= 1e-4 * np.abs(ref) + 1e-5 * np.max(np.abs(ref))), (x, got, ref)
 
 
-@pytest.mark.parametrize("w0,q", CASES + [(0.2, 0.55), (9.9, 10.0), (0.05, 30.0), (30.0, 0.5)])
+@pytest.mark.parametrize("w0,q", CASES + OVERDAMPED + [(0.2, 0.55), (9.9, 10.0), (0.05, 30.0),
+                                                    (30.0, 0.5), (1.0, 0.02)])
 def test_economised_tables_match_taylor(hh, w0, q):
     # the ten economised coefficients reproduce the 22-term Taylor series on
     # the table's range: the six values to 1e-8 of each series' size (FP32
@@ -123,7 +130,7 @@ def test_economised_tables_match_taylor(hh, w0, q):
     assert hh.hh_table_check(a, beta, 1) <= 1e-6
 
 
-@pytest.mark.parametrize("w0,q", CASES)
+@pytest.mark.parametrize("w0,q", CASES + OVERDAMPED)
 def test_taylor_generators_agree(hh, w0, q):
     a, beta = ab(w0, q)
     assert hh.hh_taylor_k_check(a, beta) <= 1e-14
