@@ -35,12 +35,12 @@ UNIT = "measurements/s"
 # executes (fadd + fmul + 2 ffma, thread-level, predicated-on; the segment
 # replay included), counted by ncu on the c4 shape -- 512 of the 1024 series,
 # chunk length 256, segments of 64 (workload c4h; profiles/k_grad_c4_ncu.md).
-ALG_FLOPS_PER_EVENT = {"c4": 1576.0}
+ALG_FLOPS_PER_EVENT = {"c4": 1560.0}
 # DRAM bytes (read + write) per event of that k_grad launch, same capture;
 # the traffic grows with the events (replay records, cached step scalars,
 # partial elements, event stream), so a full launch is this x its events.
 # Valid for the captured configuration only (chunk length 256, segments of 64).
-TRAFFIC_PER_EVENT = {"c4": (346.8, 256, 64)}
+TRAFFIC_PER_EVENT = {"c4": (347.1, 256, 64)}
 FP32_LANES_PER_SM = 128
 N_SMS = 152
 
