@@ -108,9 +108,10 @@ def events(t_start, t_end, y, yerr, instrument=None):
     """Build the labelled event sequence of one series (Section 3.2.3).
 
     Returns a dict with per-event arrays ``t`` (float64), ``kind`` (0 start,
-    1 end), ``slot``, ``meas``, and for end events ``y``, ``r0`` (= yerr^2)
-    and ``invd`` (= 1/delta, delta = t_end - t_start in FP64), plus
-    ``n_slots``.
+    1 end, 2 instantaneous measurement: t_start == t_end), ``slot`` (-1 for
+    instantaneous), ``meas``, and for measurement events ``y``, ``r0`` (=
+    yerr^2) and, at ends, ``invd`` (= 1/delta, delta = t_end - t_start in
+    FP64), plus ``n_slots`` and ``n_meas``.
 
     Ordering: by time; at equal times every end comes before any start, so a
     reset never wipes an integral before it is read; then by measurement.
@@ -122,22 +123,25 @@ def events(t_start, t_end, y, yerr, instrument=None):
     t_end = np.asarray(t_end, np.float64)
     n = len(t_start)
     delta = t_end - t_start
-    if np.any(~np.isfinite(delta)) or np.any(delta <= 0):
-        raise ValueError("exposure lengths must be positive and finite")
+    if np.any(~np.isfinite(delta)) or np.any(delta < 0):
+        raise ValueError("exposure lengths must be non-negative and finite")
+    inst = delta == 0          # instantaneous measurements: one event, no slot
+    integ = np.nonzero(~inst)[0]
+    slot_of = np.full(n, -1, np.int64)
     if instrument is not None:
-        slot_of = np.asarray(instrument, np.int64)
-        if np.any(slot_of < 0):
+        lab = np.asarray(instrument, np.int64)
+        if np.any(lab < 0):
             raise ValueError("instrument labels must be >= 0")
-        n_slots = int(slot_of.max()) + 1 if n else 1
+        slot_of[integ] = lab[integ]
+        n_slots = int(lab[integ].max()) + 1 if len(integ) else 0
         for s in range(n_slots):
-            idx = np.nonzero(slot_of == s)[0]
+            idx = integ[lab[integ] == s]
             o = idx[np.argsort(t_start[idx], kind="stable")]
             if np.any(t_end[o[:-1]] > t_start[o[1:]]):
                 raise SelfOverlapError(f"instrument {s} overlaps itself")
     else:
-        slot_of = np.empty(n, np.int64)
         last_end = []
-        for i in np.argsort(t_start, kind="stable"):
+        for i in integ[np.argsort(t_start[integ], kind="stable")]:
             for s, e in enumerate(last_end):
                 if e <= t_start[i]:
                     slot_of[i] = s
@@ -146,19 +150,26 @@ def events(t_start, t_end, y, yerr, instrument=None):
             else:
                 slot_of[i] = len(last_end)
                 last_end.append(t_end[i])
-        n_slots = max(len(last_end), 1)
-    t = np.concatenate([t_start, t_end])
-    kind = np.concatenate([np.zeros(n, np.int32), np.ones(n, np.int32)])
-    meas = np.concatenate([np.arange(n), np.arange(n)])
-    # lexsort: last key is primary -> (time, kind with end=0 first, measurement)
-    order = np.lexsort((meas, 1 - kind, t))
+        n_slots = len(last_end)
+    ni = len(integ)
+    ii = np.nonzero(inst)[0]
+    t = np.concatenate([t_start[integ], t_end[integ], t_start[ii]])
+    kind = np.concatenate([np.zeros(ni, np.int32), np.ones(ni, np.int32),
+                           np.full(len(ii), 2, np.int32)])
+    meas = np.concatenate([integ, integ, ii])
+    # lexsort: last key is primary -> (time, ends then instants then starts,
+    # measurement); same-time updates commute, a reset must follow the read
+    korder = np.array([2, 0, 1])[kind]
+    order = np.lexsort((meas, korder, t))
     t, kind, meas = t[order], kind[order], meas[order]
     y64 = np.asarray(y, np.float64)[meas]
     r0 = np.asarray(yerr, np.float64)[meas] ** 2
-    invd = 1.0 / delta[meas]
+    with np.errstate(divide="ignore"):
+        invd = np.where(kind == 1, 1.0 / np.where(kind == 1, delta[meas], 1.0), 0.0)
+    obs = kind != 0
     return dict(t=t, kind=kind.astype(np.int32), slot=slot_of[meas].astype(np.int32), meas=meas,
-                y=np.where(kind == 1, y64, 0.0), r0=np.where(kind == 1, r0, 0.0),
-                invd=np.where(kind == 1, invd, 0.0), n_slots=n_slots)
+                y=np.where(obs, y64, 0.0), r0=np.where(obs, r0, 0.0),
+                invd=invd, n_slots=n_slots, n_meas=n)
 
 
 def loglik_events(terms, layout, ev, theta, grad=False, n_slots=None, dump=False):
@@ -174,7 +185,7 @@ def loglik_events(terms, layout, ev, theta, grad=False, n_slots=None, dump=False
         raise ValueError("unsupported model specification")
     n_ev = len(ev["t"])
     dP = np.zeros((n_ev, D, D)) if dump else None
-    dS = np.zeros(int(np.sum(ev["kind"]))) if dump else None
+    dS = np.zeros(int(np.sum(ev["kind"] != 0))) if dump else None
     arr = {k: np.ascontiguousarray(ev[k]) for k in ("t", "kind", "slot", "y", "r0", "invd")}
     rc = lib.gpss_oracle_loglik(
         _ptr(spec, ctypes.c_int32), n_ev, _ptr(arr["t"], ctypes.c_double),
@@ -226,12 +237,14 @@ def exposure_grad_events(terms, layout, ev, theta, n_slots=None):
     spec = spec_array(terms, layout, n_slots)
     theta = np.ascontiguousarray(theta, np.float64)
     n_ev = len(ev["t"])
-    n = n_ev // 2
+    n = ev["n_meas"]
     ks = np.zeros(n, np.int64)
     ke = np.zeros(n, np.int64)
     idx = np.arange(n_ev, dtype=np.int64)
     ks[ev["meas"][ev["kind"] == 0]] = idx[ev["kind"] == 0]
     ke[ev["meas"][ev["kind"] == 1]] = idx[ev["kind"] == 1]
+    ks[ev["meas"][ev["kind"] == 2]] = idx[ev["kind"] == 2]
+    ke[ev["meas"][ev["kind"] == 2]] = idx[ev["kind"] == 2]
     d_ts = np.zeros(n)
     d_te = np.zeros(n)
     arr = {k: np.ascontiguousarray(ev[k]) for k in ("t", "kind", "slot", "y", "r0", "invd")}
@@ -267,10 +280,10 @@ def condition_events(terms, layout, ev, theta, n_slots=None):
         _ptr(me, ctypes.c_double), _ptr(ve, ctypes.c_double))
     if rc != 0:
         raise RuntimeError(f"oracle smoother failed with code {rc}")
-    n = n_ev // 2
+    n = ev["n_meas"]
     mean = np.zeros(n)
     var = np.zeros(n)
-    end = ev["kind"] == 1
+    end = ev["kind"] != 0
     mean[ev["meas"][end]] = me[end]
     var[ev["meas"][end]] = ve[end]
     return mean, var

@@ -93,16 +93,38 @@ def G(x, sigma, w0, q):
 
 
 def integrated_cov(terms, theta, t_start, t_end):
-    """K_ij of exposure-averaged values for a sum of SHO / Matern-3/2 terms."""
+    """K_ij of exposure-averaged values for a sum of SHO / Matern-3/2 terms.
+
+    A measurement with t_start == t_end is instantaneous (the limit delta -> 0
+    of the exposure average, Section 3.2: z / delta -> f): its covariance with
+    another instantaneous one is k(|t_i - t_j|), with an exposure [a, b] of
+    length delta it is (F1(t - a) - F1(t - b)) / delta."""
     a = np.asarray(t_start, np.longdouble)
     b = np.asarray(t_end, np.longdouble)
     d = b - a
+    inst = d == 0
     pars, _ = split_theta(terms, theta)
-    K = np.zeros((len(a), len(a)), np.longdouble)
+    n = len(a)
+    K = np.zeros((n, n), np.longdouble)
     for sigma, w0, q in pars:
         K += (G(b[:, None] - a[None, :], sigma, w0, q) - G(a[:, None] - a[None, :], sigma, w0, q)
               - G(b[:, None] - b[None, :], sigma, w0, q) + G(a[:, None] - b[None, :], sigma, w0, q))
-    return (K / (d[:, None] * d[None, :])).astype(np.float64)
+    dd = np.where(inst, 1, d)
+    K = (K / (dd[:, None] * dd[None, :])).astype(np.float64)
+    if inst.any():
+        t = np.asarray(t_start, np.float64)
+        ta, tb, dl = t, np.asarray(t_end, np.float64), np.where(inst, 1.0, np.asarray(d, np.float64))
+        ki = np.nonzero(inst)[0]
+        cross = np.zeros((len(ki), n))
+        kk = np.zeros((len(ki), len(ki)))
+        for sigma, w0, q in pars:
+            cross += (F1(t[ki, None] - ta[None, :], sigma, w0, q) -
+                      F1(t[ki, None] - tb[None, :], sigma, w0, q)) / dl[None, :]
+            kk += kernel(t[ki, None] - t[None, ki], sigma, w0, q)
+        K[ki, :] = cross
+        K[:, ki] = cross.T
+        K[np.ix_(ki, ki)] = kk
+    return K
 
 
 def instantaneous_cov(terms, theta, t):
@@ -178,9 +200,12 @@ def predict(terms, theta, t_start, t_end, y, yerr, t_star):
     t_star = np.asarray(t_star, np.float64)
     ks = np.zeros((len(t_star), len(ts_)))
     k0 = 0.0
+    inst = d == 0
+    dl = np.where(inst, 1.0, d)
     for sig, w0, q in pars:
-        ks += (F1(t_star[:, None] - ts_[None, :], sig, w0, q) -
-               F1(t_star[:, None] - te_[None, :], sig, w0, q)) / d[None, :]
+        ks += np.where(inst[None, :], kernel(t_star[:, None] - ts_[None, :], sig, w0, q),
+                       (F1(t_star[:, None] - ts_[None, :], sig, w0, q) -
+                        F1(t_star[:, None] - te_[None, :], sig, w0, q)) / dl[None, :])
         k0 += sig ** 2
     sol = np.linalg.solve(A, np.c_[np.asarray(y, np.float64), ks.T])
     mean = ks @ sol[:, 0]

@@ -45,11 +45,24 @@ static int zindex(const model_t *M, int slot, int t) {
   return 2 * M->n_terms + slot * M->n_terms + t;
 }
 
+/* Observation vector of a measurement event (Eq. H_aug): an exposure end
+ * (kind 1) reads its slot's integral state(s) times 1/delta; an
+ * instantaneous measurement (kind 2, Section 2: t_start = t_end) reads the
+ * latent f = H x = sum_t x_t directly. */
+static void obs_vector(const model_t *M, int kind, int slot, double invd, double *h) {
+  for (int i = 0; i < M->dim; ++i) h[i] = 0.0;
+  if (kind == 2) {
+    for (int t = 0; t < M->n_terms; ++t) h[2 * t] = 1.0;
+  } else {
+    for (int t = 0; t < M->n_zper; ++t) h[zindex(M, slot, t)] = invd;
+  }
+}
+
 static int parse_spec(const int32_t *spec, model_t *M) {
   M->n_terms = spec[0];
   M->layout = spec[1];
   M->n_slots = spec[2];
-  if (M->n_terms < 1 || M->n_terms > MAXT || M->n_slots < 1) return 1;
+  if (M->n_terms < 1 || M->n_terms > MAXT || M->n_slots < 0) return 1;
   if (M->layout != 0 && M->layout != 1) return 1;
   for (int t = 0; t < M->n_terms; ++t) {
     M->kind[t] = spec[3 + t];
@@ -119,7 +132,8 @@ int gpss_oracle_discretize(const int32_t *spec, const double *theta, double dt, 
 
 /* Log-likelihood of one series (and, if grad != NULL, its gradient with
  * respect to the natural parameters by the complex-step method).
- * Per event k (time-sorted): t_ev, kind (0 start, 1 end), slot, and for end
+ * Per event k (time-sorted): t_ev, kind (0 start, 1 end, 2 instantaneous
+ * measurement), slot, and for measurement
  * events y, r0 = yerr^2 and 1/delta.  dumpP (n_ev * dim * dim) receives the
  * filtered covariance after each event and dumpS (n_end) the innovation
  * variances; both may be NULL.  Returns 0 on success. */
@@ -190,6 +204,20 @@ int gpss_oracle_exposure_grad(const int32_t *spec, int64_t n_ev, const double *t
   int rc = 0;
   for (int64_t n = 0; n < n_meas && !rc; ++n) {
     const int64_t ks = ev_start[n], ke = ev_end[n];
+    if (ks == ke) {
+      /* instantaneous measurement (one event): moving its time moves both
+       * "edges"; each column holds half of d loglik / d t */
+      for (int64_t k = 0; k < n_ev; ++k) {
+        tc[k] = t_ev[k];
+        ic[k] = invd_ev[k];
+      }
+      const double hstep = 1e-20 * (fabs(t_ev[ke]) > 1.0 ? fabs(t_ev[ke]) : 1.0);
+      tc[ke] += I * hstep;
+      double complex llc;
+      rc = filter_c(&M, thc, n_ev, tc, kind, slot, y_ev, r0_ev, ic, &llc, NULL, NULL);
+      if (!rc) d_ts[n] = d_te[n] = 0.5 * cimag(llc) / hstep;
+      continue;
+    }
     const double delta = 1.0 / invd_ev[ke];
     for (int edge = 0; edge < 2 && !rc; ++edge) {
       for (int64_t k = 0; k < n_ev; ++k) {
@@ -272,7 +300,8 @@ static int gain_solve(int n, double *S, double *X) {
  *   m^_k = base + G (m^_{k+1} - m-_{k+1}),
  *   P^_k = base + G (P^_{k+1} - P-_{k+1}) G^T,
  * with A_k the transition from event k to k+1.  At each end event (output
- * in event order) mean = H m^, var = H P^ H^T, H = e_z / delta.  P-_{k+1}
+ * in event order) mean = H m^, var = H P^ H^T, H = e_z / delta (the latent
+ * sum for an instantaneous measurement).  P-_{k+1}
  * is inverted as in gain_solve.  Returns 0, or 5 if it is singular beyond
  * zeroed integral states. */
 static int smooth_all(const model_t *Mp, int64_t n_ev, const double *t_ev, const int32_t *kind,
@@ -325,8 +354,7 @@ static int smooth_all(const model_t *Mp, int64_t n_ev, const double *t_ev, const
         for (int i = 0; i < D; ++i) P[z * D + i] = P[i * D + z] = 0;
       }
     } else {
-      for (int i = 0; i < D; ++i) h[i] = 0;
-      for (int t = 0; t < M.n_zper; ++t) h[zindex(&M, sj, t)] = invd_ev[k];
+      obs_vector(&M, kind[k], sj, invd_ev[k], h);
       const double r = r0_ev[k] + s2;
       double Sv = r, hm = 0;
       for (int i = 0; i < D; ++i) {
@@ -410,9 +438,8 @@ static int smooth_all(const model_t *Mp, int64_t n_ev, const double *t_ev, const
     memcpy(msa + k * D, ms, sizeof(double) * D);
     memcpy(Psa + k * DD, Ps, sizeof(double) * DD);
     if (!mean_ev) continue;
-    if (kind[k] == 1) {
-      for (int i = 0; i < D; ++i) h[i] = 0;
-      for (int t = 0; t < M.n_zper; ++t) h[zindex(&M, slot[k], t)] = invd_ev[k];
+    if (kind[k] != 0) {
+      obs_vector(&M, kind[k], slot[k], invd_ev[k], h);
       double mu = 0, va = 0;
       for (int i = 0; i < D; ++i) {
         mu += h[i] * ms[i];

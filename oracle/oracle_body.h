@@ -225,7 +225,7 @@ static int SFX(filter)(const model_t *M, const SCALAR *th, int64_t n_ev, const S
         P[j * D + i] = P[i * D + j];
       }
     const int sj = slot[k];
-    if (sj < 0 || sj >= M->n_slots) return 3;
+    if (kind[k] != 2 && (sj < 0 || sj >= M->n_slots)) return 3;
     if (kind[k] == 0) {
       /* exposure start: zero this slot's integral state(s) */
       for (int t = 0; t < M->n_zper; ++t) {
@@ -238,7 +238,10 @@ static int SFX(filter)(const model_t *M, const SCALAR *th, int64_t n_ev, const S
       }
     } else {
       for (int i = 0; i < D; ++i) h[i] = 0;
-      for (int t = 0; t < M->n_zper; ++t) h[zindex(M, sj, t)] = invd_ev[k];
+      if (kind[k] == 2)
+        for (int t = 0; t < M->n_terms; ++t) h[2 * t] = 1.0; /* instantaneous: f = H x */
+      else
+        for (int t = 0; t < M->n_zper; ++t) h[zindex(M, sj, t)] = invd_ev[k];
       SCALAR Sv = r0_ev[k] + s2, hm = 0;
       for (int i = 0; i < D; ++i) {
         SCALAR acc = 0;
