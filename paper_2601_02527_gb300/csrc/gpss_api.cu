@@ -23,6 +23,8 @@ OpTable ops_2_1_0();
 OpTable ops_2_2_0();
 OpTable ops_2_3_0();
 OpTable ops_2_1_1();
+OpTable ops_1_0_0();
+OpTable ops_2_0_0();
 
 __global__ void k_series_sum(int n_out, int per_series, int n_series, int n_chunks,
                              const int32_t *__restrict__ ch_first,
@@ -78,6 +80,12 @@ __global__ void k_exposure_grad(int n_rows, int n_series, const int64_t *__restr
   auto gt = [&](int64_t k) {
     return (k == kb ? 0.f : g[k]) - (k + 1 < kend ? g[k + 1] : 0.f);
   };
+  if (p.x == p.y) {
+    // instantaneous measurement: moving its time moves both "edges"; each
+    // column holds half of d loglik / d t
+    out[2 * idx] = out[2 * idx + 1] = 0.5f * gt(ks);
+    return;
+  }
   const float wpart = gwe[row * n_events + ke];
   out[2 * idx] = gt(ks) + wpart;
   out[2 * idx + 1] = gt(ke) - wpart;
@@ -195,6 +203,12 @@ struct DeviceGuard {
 };
 
 bool pick_ops(int n_terms, int n_slots, int layout, OpTable *o) {
+  if (n_slots == 0) {  // instantaneous measurements only
+    if (n_terms == 1) *o = gpss::ops_1_0_0();
+    else if (n_terms == 2) *o = gpss::ops_2_0_0();
+    else return false;
+    return true;
+  }
   if (n_terms == 1) {
     if (n_slots == 1) *o = gpss::ops_1_1_0();
     else if (n_slots == 2) *o = gpss::ops_1_2_0();
@@ -261,19 +275,62 @@ struct SeriesOut {
   int n_slots = 1;
 };
 
-void build_series(int64_t a, int64_t b, const double *ts, const double *te, const float *y,
-                  const float *yerr, const int32_t *inst, float *dt, uint8_t *tag, float4 *meas,
-                  double *dt64, double *meas64, int2 *mev, double *tev, SeriesOut *out) {
+// Per measurement: 0 = exposure (t_end > t_start), 1 = instantaneous
+// (t_end == t_start, Section 2), -1 = invalid input.
+inline int meas_kind(double ts, double te, float y, float yerr) {
+  const double d = te - ts;
+  if (!std::isfinite(d) || !std::isfinite(ts) || !std::isfinite(y) || !std::isfinite(yerr) ||
+      d < 0)
+    return -1;
+  return d == 0 ? 1 : 0;
+}
+
+// Events of series [a, b) at event offset e0: two per exposure (start, end),
+// one per instantaneous measurement (a measurement event observing the
+// latent; a model holds one kind only, checked by the caller).
+void build_series(int64_t a, int64_t b, int64_t e0, const double *ts, const double *te,
+                  const float *y, const float *yerr, const int32_t *inst, float *dt, uint8_t *tag,
+                  float4 *meas, double *dt64, double *meas64, int2 *mev, double *tev,
+                  SeriesOut *out) {
   const int64_t n = b - a;
   std::vector<int> slot(n);
   int n_slots = 1;
+  int64_t n_inst = 0;
   for (int64_t i = 0; i < n; ++i) {
-    const double d = te[a + i] - ts[a + i];
-    if (!(d > 0) || !std::isfinite(d) || !std::isfinite(ts[a + i]) || !std::isfinite(y[a + i]) ||
-        !std::isfinite(yerr[a + i])) {
+    const int kd = meas_kind(ts[a + i], te[a + i], y[a + i], yerr[a + i]);
+    if (kd < 0) {
       out->st = GP_SS_EINVAL;
       return;
     }
+    n_inst += kd;
+  }
+  if (n_inst > 0) {
+    // instantaneous series: one measurement event each, in time order (ties
+    // by input order; simultaneous updates commute)
+    out->n_slots = 0;
+    std::vector<int64_t> ord(n);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int64_t p, int64_t q) { return ts[a + p] < ts[a + q]; });
+    double tprev = n > 0 ? ts[a + ord[0]] : 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+      const int64_t i = ord[k];
+      const double gap = ts[a + i] - tprev;
+      tprev = ts[a + i];
+      dt[e0 + k] = (float)gap;
+      if (dt64) dt64[e0 + k] = gap;
+      tev[e0 + k] = ts[a + i];
+      tag[e0 + k] = 1;
+      mev[a + i] = make_int2((int)k, (int)k);
+      const double r0 = (double)yerr[a + i] * (double)yerr[a + i];
+      meas[a + k] = make_float4(y[a + i], (float)r0, 1.0f, 0.0f);
+      if (meas64) {
+        meas64[3 * (a + k)] = (double)y[a + i];
+        meas64[3 * (a + k) + 1] = r0;
+        meas64[3 * (a + k) + 2] = 1.0;
+      }
+    }
+    return;
   }
   std::vector<int64_t> order(n);
   std::iota(order.begin(), order.end(), 0);
@@ -326,7 +383,6 @@ void build_series(int64_t a, int64_t b, const double *ts, const double *te, cons
     if (p.kind != q.kind) return p.kind < q.kind;
     return p.i < q.i;
   });
-  const int64_t e0 = 2 * a;
   int64_t mi = a;
   double tprev = n > 0 ? ev[0].t : 0.0;
   for (int64_t k = 0; k < 2 * n; ++k) {
@@ -808,16 +864,34 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
     m->n_params += spec->terms[t] == GP_SS_TERM_SHO ? 3 : 2;
   }
   m->n_meas = N;
-  m->n_events = 2 * N;
   m->ev_off.resize(n_series + 1);
   m->meas_off.resize(n_series + 1);
+  // events per series: two per exposure, one per instantaneous measurement;
+  // a model holds one kind (mixing them needs a shape with both observation
+  // forms, which is not compiled)
+  int64_t n_inst = 0, n_bad = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    const int kd = meas_kind(t_start[i], t_end[i], y[i], yerr[i]);
+    n_bad += kd < 0;
+    n_inst += kd > 0;
+  }
+  if (n_bad) {
+    delete m;
+    return GP_SS_EINVAL;
+  }
+  if (n_inst > 0 && n_inst < N) {
+    delete m;
+    return GP_SS_EUNSUPPORTED;
+  }
+  const int64_t per_meas = n_inst > 0 ? 1 : 2;
   for (int s = 0; s <= n_series; ++s) {
     m->meas_off[s] = series_offsets[s];
-    m->ev_off[s] = 2 * series_offsets[s];
+    m->ev_off[s] = per_meas * series_offsets[s];
   }
+  m->n_events = per_meas * N;
   // one record past the last measurement: the chunk kernels prefetch the
   // next measurement record before they know whether another one follows
-  const size_t nE = std::max<int64_t>(2 * N, 1), nM = (size_t)N + 1;
+  const size_t nE = std::max<int64_t>(m->n_events, 1), nM = (size_t)N + 1;
   // host copies: pinned for fast re-upload when a device is present, plain
   // otherwise (validation then still runs and reports before any device work)
   m->pinned = cudaMallocHost((void **)&m->h_dt, nE * sizeof(float)) == cudaSuccess &&
@@ -841,7 +915,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   }
   m->h_meas[N] = make_float4(0.f, 0.f, 0.f, 0.f);
   std::vector<int2> mev(std::max<int64_t>(N, 1));
-  m->tev.assign(std::max<int64_t>(2 * N, 1), 0.0);
+  m->tev.assign(nE, 0.0);
   std::vector<double> dt64, meas64;
   if (o.precision == 64) {
     dt64.resize(nE);
@@ -856,15 +930,15 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
     for (unsigned w = 0; w < nthr; ++w)
       pool.emplace_back([&, w]() {
         for (int s = (int)w; s < n_series; s += (int)nthr)
-          build_series(series_offsets[s], series_offsets[s + 1], t_start, t_end, y, yerr,
-                       instrument, m->h_dt, m->h_tag, m->h_meas,
+          build_series(series_offsets[s], series_offsets[s + 1], m->ev_off[s], t_start, t_end,
+                       y, yerr, instrument, m->h_dt, m->h_tag, m->h_meas,
                        dt64.empty() ? nullptr : dt64.data(),
                        meas64.empty() ? nullptr : meas64.data(), mev.data(), m->tev.data(),
                        &so[s]);
       });
     for (auto &t : pool) t.join();
   }
-  int n_slots = 1;
+  int n_slots = n_inst > 0 ? 0 : 1;
   for (int s = 0; s < n_series; ++s) {
     if (so[s].st != GP_SS_OK) {
       gp_ss_status st = so[s].st;
@@ -880,7 +954,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
     delete m;
     return GP_SS_EUNSUPPORTED;
   }
-  m->tag.assign(m->h_tag, m->h_tag + 2 * N);
+  m->tag.assign(m->h_tag, m->h_tag + m->n_events);
   gp_ss_status st = GP_SS_OK;
   if (!st) st = dev_upload(&m->d_ev_off, m->ev_off.data(), m->ev_off.size());
   if (!st) st = dev_upload(&m->d_meas_off, m->meas_off.data(), m->meas_off.size());

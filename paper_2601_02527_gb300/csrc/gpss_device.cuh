@@ -1009,9 +1009,30 @@ GPSS_HD void reset_slot(int j, F *m, F *P) {
 }
 
 // Shared pieces of the measurement update with H~ = w * sum_{z in slot j} e_z
-// (Eq. H_aug; w = 1/delta):  u = P H~^T, S = H~ u + r, hm = H~ m.
+// (Eq. H_aug; w = 1/delta):  u = P H~^T, S = H~ u + r, hm = H~ m.  Shapes
+// without integral states (NS = 0) observe the latent instead.
 template <class S, class F>
 GPSS_HD void obs_project(int j, F w, const F *m, const F *P, F *u, F &hu, F &hm) {
+  if constexpr (S::NS == 0) {
+    // no integral states: an instantaneous measurement (Section 2), h = H =
+    // (1 0 1 0 ...) reads the latent f = sum_t x_t directly (w unused)
+#pragma unroll
+    for (int i = 0; i < S::D; ++i) {
+      F acc = F(0);
+#pragma unroll
+      for (int t = 0; t < S::NT; ++t) acc += P[S::pk(i, 2 * t)];
+      u[i] = acc;
+    }
+    F a1 = F(0), a2 = F(0);
+#pragma unroll
+    for (int t = 0; t < S::NT; ++t) {
+      a1 += u[2 * t];
+      a2 += m[2 * t];
+    }
+    hu = a1;
+    hm = a2;
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < S::D; ++i) {
     F acc = F(0);

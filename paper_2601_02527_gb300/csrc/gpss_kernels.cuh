@@ -559,13 +559,19 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
       obs_project<S>(j, w, b, C, u, hu, hb);
       const F Sv = hu + r0 + s2;
       const F cc = y - hb;
-      F g[D];
+      F g[D];  // h^T A
 #pragma unroll
       for (int col = 0; col < D; ++col) {
         F acc = F(0);
+        if constexpr (S::NS == 0) {
 #pragma unroll
-        for (int zi = 2 * S::NT; zi < D; ++zi) acc += (S::zslot(zi) == j) ? A[zi][col] : F(0);
-        g[col] = acc * w;
+          for (int t = 0; t < S::NT; ++t) acc += A[2 * t][col];
+          g[col] = acc;
+        } else {
+#pragma unroll
+          for (int zi = 2 * S::NT; zi < D; ++zi) acc += (S::zslot(zi) == j) ? A[zi][col] : F(0);
+          g[col] = acc * w;
+        }
       }
       bad |= !(Sv > F(0));
       const F iS = F(1) / Sv;
@@ -1002,6 +1008,32 @@ template <class S>
 GPSS_HD float2 conditioned(int j, float w, const float *m, const float *P, const float *lam,
                            const float *Lam) {
   constexpr int D = S::D;
+  if constexpr (S::NS == 0) {
+    // instantaneous measurement: h selects the latent components
+    float u[D], hm = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      float acc = 0.f;
+#pragma unroll
+      for (int t = 0; t < S::NT; ++t) acc += P[S::pk(i, 2 * t)];
+      u[i] = acc;
+    }
+    float ul = 0.f, hu = 0.f, uLu = 0.f;
+#pragma unroll
+    for (int t = 0; t < S::NT; ++t) {
+      hm += m[2 * t];
+      hu += u[2 * t];
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      ul += u[i] * lam[i];
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += Lam[S::pk(i, k)] * u[k];
+      uLu += u[i] * acc;
+    }
+    return make_float2(hm + ul, hu + 2.f * uLu - ul * ul);
+  }
   float u[D], hm = 0.f;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -1081,8 +1113,13 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
     const F vb = lu * iS - v * iS;
     F h[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) h[i] = (i >= 2 * S::NT && S::zslot(i) == j) ? w : F(0);
-    if (want_exp) {
+    for (int i = 0; i < D; ++i) {
+      if constexpr (S::NS == 0)
+        h[i] = (i % 2 == 0) ? F(1) : F(0);  // instantaneous: the latent
+      else
+        h[i] = (i >= 2 * S::NT && S::zslot(i) == j) ? w : F(0);
+    }
+    if (S::NS > 0 && want_exp) {
       // h = w e (e selects the slot's integral states): d/dh = Pp ub + 2 Sb u - vb mp
       F gw = F(0);
 #pragma unroll

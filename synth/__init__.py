@@ -257,6 +257,27 @@ def c2(seed=1002, n_series=4096, scale=1.0, nmin=500, nmax=20000):
     return _finish("c2", [SHO, MATERN32], 0, series, theta, True, rng)
 
 
+def c2i(seed=1006, n_series=4096, scale=1.0, nmin=500, nmax=20000, gap_mean=1.0):
+    """The c2 recipe (SHO + Matern-3/2, per-series parameters log-uniform over
+    a factor 10) on instantaneous measurements: times with Exponential(gap_mean)
+    gaps, t_start == t_end, observing the latent itself (Section 2)."""
+    rng = np.random.default_rng(seed)
+    ns = np.rint(np.exp(rng.uniform(math.log(nmin), math.log(nmax), n_series)) * scale)
+    ns = np.maximum(ns, 2).astype(np.int64)
+    theta = np.empty((n_series, 6))
+    theta[:, 0] = _loguniform(rng, 1.0, 10, n_series)
+    theta[:, 1] = _loguniform(rng, TWO_PI / 10, 10, n_series)
+    theta[:, 2] = _loguniform(rng, 3.0, 10, n_series)
+    theta[:, 3] = _loguniform(rng, 0.5, 10, n_series)
+    theta[:, 4] = _loguniform(rng, 5.0, 10, n_series)
+    theta[:, 5] = 0.1
+    series = []
+    for n in ns:
+        t = np.cumsum(rng.exponential(gap_mean, int(n)))
+        series.append((t, t.copy()))
+    return _finish("c2i", [SHO, MATERN32], 0, series, theta, True, rng)
+
+
 def c3(seed=1003, n=1 << 22):
     """One long series with up to 3 concurrently open exposures."""
     rng = np.random.default_rng(seed)

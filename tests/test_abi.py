@@ -63,8 +63,10 @@ def _build(lib, t_start, t_end, inst=None, offsets=None, terms=(1,), layout=0, o
 def test_host_validation_without_gpu(lib):
     # unsorted offsets
     assert _build(lib, [0.0, 1.0], [0.5, 1.5], offsets=[0, 2, 1]) == 2
-    # non-positive exposure
-    assert _build(lib, [0.0, 1.0], [0.5, 1.0]) == 1
+    # negative exposure
+    assert _build(lib, [0.0, 1.0], [0.5, 0.9]) == 1
+    # instantaneous (zero-length) and integrated measurements in one model: not compiled
+    assert _build(lib, [0.0, 1.0], [0.5, 1.0]) == 4
     # one instrument overlapping itself
     assert _build(lib, [0.0, 0.4], [0.5, 0.9], inst=[0, 0]) == 3
     # more than 3 concurrently open exposures (greedy slots) is not compiled
