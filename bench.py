@@ -74,6 +74,8 @@ def workload(name):
         return synth.c3()
     if name == "c5":
         return synth.c5()
+    if name == "c2i":  # the c2 recipe on instantaneous measurements
+        return synth.c2i()
     if name == "c4h":  # 512 series of the c4 recipe (profiling captures)
         return synth.c4(n_series=512)
     if name == "c4s":  # small variant for quick checks

@@ -29,24 +29,54 @@ from __future__ import annotations
 
 import math
 import numpy as np
+import scipy.integrate
 import scipy.linalg
 
 SHO = 1
 MATERN32 = 2
+SHO_PRODUCT = 3
 
 
 def split_theta(terms, theta):
-    """Per-term (sigma, omega0, Q) and white-noise sd from natural parameters."""
+    """Per-term (sigma, omega0, Q) and white-noise sd from natural parameters;
+    a product of two SHOs gives (sigma, omega_a, Q_a, omega_b, Q_b)."""
     out = []
     j = 0
     for k in terms:
         if k == SHO:
             out.append((theta[j], theta[j + 1], theta[j + 2]))
             j += 3
+        elif k == SHO_PRODUCT:
+            out.append(tuple(theta[j:j + 5]))
+            j += 5
         else:
             out.append((theta[j], math.sqrt(3.0) / theta[j + 1], 0.5))
             j += 2
     return out, theta[j]
+
+
+def term_kernel(x, p):
+    """k(|x|) of one term: an SHO / Matern-3/2 (sigma, omega0, Q), or a product
+    of two SHOs sigma^2 k_a k_b with unit-variance factors (Appendix C.2)."""
+    if len(p) == 3:
+        return kernel(x, *p)
+    sig, wa, qa, wb, qb = p
+    return sig ** 2 * kernel(x, 1.0, wa, qa) * kernel(x, 1.0, wb, qb)
+
+
+def _quad_window(kfun, t, a, b):
+    """int_a^b k(t - s) ds by adaptive quadrature (split at s = t)."""
+    pts = [t] if a < t < b else None
+    v, _ = scipy.integrate.quad(lambda u: kfun(t - u), a, b, points=pts, epsabs=1e-14,
+                                epsrel=1e-12, limit=200)
+    return v
+
+
+def _quad_pair(kfun, a1, b1, a2, b2):
+    """int_{a1}^{b1} int_{a2}^{b2} k(t - t') by nested quadrature."""
+    return scipy.integrate.quad(lambda t: _quad_window(kfun, t, a2, b2), a1, b1,
+                                points=[p for p in (a2, b2) if a1 < p < b1] or None,
+                                epsabs=1e-13, epsrel=1e-11, limit=200)[0]
 
 
 def overdamped_modes(sigma, w0, q, dtype=np.float64):
@@ -103,7 +133,9 @@ def integrated_cov(terms, theta, t_start, t_end):
     b = np.asarray(t_end, np.longdouble)
     d = b - a
     inst = d == 0
-    pars, _ = split_theta(terms, theta)
+    pars_all, _ = split_theta(terms, theta)
+    pars = [p for p in pars_all if len(p) == 3]
+    prods = [p for p in pars_all if len(p) == 5]
     n = len(a)
     K = np.zeros((n, n), np.longdouble)
     for sigma, w0, q in pars:
@@ -124,6 +156,24 @@ def integrated_cov(terms, theta, t_start, t_end):
         K[ki, :] = cross
         K[:, ki] = cross.T
         K[np.ix_(ki, ki)] = kk
+    if prods:
+        # products (no closed form here): quadrature of the kernel, for small N
+        ta, tb = np.asarray(t_start, np.float64), np.asarray(t_end, np.float64)
+        kfun = lambda x: sum(term_kernel(x, p) for p in prods)
+        for i in range(n):
+            for j in range(i, n):
+                if inst[i] and inst[j]:
+                    v = kfun(ta[i] - ta[j])
+                elif inst[i]:
+                    v = _quad_window(kfun, ta[i], ta[j], tb[j]) / (tb[j] - ta[j])
+                elif inst[j]:
+                    v = _quad_window(kfun, ta[j], ta[i], tb[i]) / (tb[i] - ta[i])
+                else:
+                    v = _quad_pair(kfun, ta[i], tb[i], ta[j], tb[j]) / (
+                        (tb[i] - ta[i]) * (tb[j] - ta[j]))
+                K[i, j] += v
+                if j != i:
+                    K[j, i] += v
     return K
 
 
@@ -131,8 +181,8 @@ def instantaneous_cov(terms, theta, t):
     t = np.asarray(t, np.float64)
     pars, _ = split_theta(terms, theta)
     K = np.zeros((len(t), len(t)))
-    for sigma, w0, q in pars:
-        K += kernel(t[:, None] - t[None, :], sigma, w0, q)
+    for p in pars:
+        K += term_kernel(t[:, None] - t[None, :], p)
     return K
 
 
@@ -202,11 +252,18 @@ def predict(terms, theta, t_start, t_end, y, yerr, t_star):
     k0 = 0.0
     inst = d == 0
     dl = np.where(inst, 1.0, d)
-    for sig, w0, q in pars:
+    for p in pars:
+        k0 += p[0] ** 2
+        if len(p) == 5:  # product: quadrature over each window (small cases)
+            for i, tq in enumerate(t_star):
+                for n in range(len(ts_)):
+                    ks[i, n] += (term_kernel(tq - ts_[n], p) if inst[n] else
+                                 _quad_window(lambda x: term_kernel(x, p), tq, ts_[n], te_[n]) / d[n])
+            continue
+        sig, w0, q = p
         ks += np.where(inst[None, :], kernel(t_star[:, None] - ts_[None, :], sig, w0, q),
                        (F1(t_star[:, None] - ts_[None, :], sig, w0, q) -
                         F1(t_star[:, None] - te_[None, :], sig, w0, q)) / dl[None, :])
-        k0 += sig ** 2
     sol = np.linalg.solve(A, np.c_[np.asarray(y, np.float64), ks.T])
     mean = ks @ sol[:, 0]
     var = k0 - np.einsum("ij,ji->i", ks, sol[:, 1:])

@@ -33,7 +33,10 @@
 
 typedef struct {
   int n_terms;
-  int kind[MAXT]; /* 1 = SHO, 2 = Matern-3/2 */
+  int kind[MAXT]; /* 1 = SHO, 2 = Matern-3/2, 3 = product of two SHOs */
+  int toff[MAXT]; /* first state index of each term */
+  int tdim[MAXT]; /* its state dimension: 2, or 4 for a product */
+  int nx;         /* latent (non-integral) state dimension, sum of tdim */
   int layout;     /* 0: one z per slot; 1: one z per term per slot */
   int n_slots;
   int dim;    /* augmented state dimension */
@@ -41,8 +44,8 @@ typedef struct {
 } model_t;
 
 static int zindex(const model_t *M, int slot, int t) {
-  if (M->layout == 0) return 2 * M->n_terms + slot;
-  return 2 * M->n_terms + slot * M->n_terms + t;
+  if (M->layout == 0) return M->nx + slot;
+  return M->nx + slot * M->n_terms + t;
 }
 
 /* Observation vector of a measurement event (Eq. H_aug): an exposure end
@@ -52,7 +55,7 @@ static int zindex(const model_t *M, int slot, int t) {
 static void obs_vector(const model_t *M, int kind, int slot, double invd, double *h) {
   for (int i = 0; i < M->dim; ++i) h[i] = 0.0;
   if (kind == 2) {
-    for (int t = 0; t < M->n_terms; ++t) h[2 * t] = 1.0;
+    for (int t = 0; t < M->n_terms; ++t) h[M->toff[t]] = 1.0;
   } else {
     for (int t = 0; t < M->n_zper; ++t) h[zindex(M, slot, t)] = invd;
   }
@@ -64,19 +67,23 @@ static int parse_spec(const int32_t *spec, model_t *M) {
   M->n_slots = spec[2];
   if (M->n_terms < 1 || M->n_terms > MAXT || M->n_slots < 0) return 1;
   if (M->layout != 0 && M->layout != 1) return 1;
+  M->nx = 0;
   for (int t = 0; t < M->n_terms; ++t) {
     M->kind[t] = spec[3 + t];
-    if (M->kind[t] != 1 && M->kind[t] != 2) return 1;
+    if (M->kind[t] < 1 || M->kind[t] > 3) return 1;
+    M->toff[t] = M->nx;
+    M->tdim[t] = M->kind[t] == 3 ? 4 : 2;
+    M->nx += M->tdim[t];
   }
   M->n_zper = M->layout == 0 ? 1 : M->n_terms;
-  M->dim = 2 * M->n_terms + M->n_slots * M->n_zper;
+  M->dim = M->nx + M->n_slots * M->n_zper;
   if (M->dim > MAXD) return 1;
   return 0;
 }
 
 static int n_params(const model_t *M) {
   int n = 1;
-  for (int t = 0; t < M->n_terms; ++t) n += (M->kind[t] == 1) ? 3 : 2;
+  for (int t = 0; t < M->n_terms; ++t) n += (M->kind[t] == 1) ? 3 : (M->kind[t] == 2 ? 2 : 5);
   return n;
 }
 
@@ -121,7 +128,7 @@ int gpss_oracle_discretize(const int32_t *spec, const double *theta, double dt, 
                            double *Q, double *P0) {
   model_t M;
   if (parse_spec(spec, &M)) return 1;
-  double w0[MAXT], q[MAXT], var[MAXT], s2;
+  double w0[2 * MAXT], q[2 * MAXT], var[MAXT], s2;
   double F[MAXD * MAXD], LQL[MAXD * MAXD];
   term_params_r(&M, theta, w0, q, var, &s2);
   build_F_r(&M, w0, q, var, F, LQL);
@@ -311,7 +318,7 @@ static int smooth_all(const model_t *Mp, int64_t n_ev, const double *t_ev, const
                       double *var_ev) {
   const model_t M = *Mp;
   const int D = M.dim, DD = D * D;
-  double w0[MAXT], q[MAXT], var[MAXT], s2;
+  double w0[2 * MAXT], q[2 * MAXT], var[MAXT], s2;
   double F[MAXD * MAXD], LQL[MAXD * MAXD], Phi[MAXD * MAXD], Qd[MAXD * MAXD];
   term_params_r(&M, theta, w0, q, var, &s2);
   build_F_r(&M, w0, q, var, F, LQL);
@@ -515,13 +522,13 @@ int gpss_oracle_predict(const int32_t *spec, int64_t n_ev, const double *t_ev, c
                         const double *t_star, double *mean_out, double *var_out) {
   model_t M;
   if (parse_spec(spec, &M)) return 1;
-  const int D = M.dim, DD = D * D, NX = 2 * M.n_terms;
+  const int D = M.dim, DD = D * D, NX = M.nx;
   states_t S;
   int rc = states_alloc(&S, n_ev, D);
   if (!rc)
     rc = smooth_all(&M, n_ev, t_ev, kind, slot, y_ev, r0_ev, invd_ev, theta, S.mp, S.Pp, S.mf,
                     S.Pf, S.ms, S.Ps, NULL, NULL);
-  double w0[MAXT], q[MAXT], var[MAXT], s2;
+  double w0[2 * MAXT], q[2 * MAXT], var[MAXT], s2;
   double F[MAXD * MAXD], LQL[MAXD * MAXD], A[MAXD * MAXD], Qd[MAXD * MAXD], P0[MAXD * MAXD];
   term_params_r(&M, theta, w0, q, var, &s2);
   build_F_r(&M, w0, q, var, F, LQL);
@@ -660,8 +667,8 @@ int gpss_oracle_predict(const int32_t *spec, int64_t n_ev, const double *t_ev, c
     }
     double mu = 0, va = 0;
     for (int t = 0; t < M.n_terms; ++t) {
-      mu += mh[2 * t];
-      for (int u = 0; u < M.n_terms; ++u) va += Ph[2 * t * D + 2 * u];
+      mu += mh[M.toff[t]];
+      for (int u = 0; u < M.n_terms; ++u) va += Ph[M.toff[t] * D + M.toff[u]];
     }
     mean_out[j] = mu;
     var_out[j] = va;

@@ -10,7 +10,11 @@
  * SHO (Appendix B, Eqs. sho_kernel, sho_Qc_Pinf): (sigma, omega0, Q),
  *   Q_c = 2 omega0^3 sigma^2 / Q, P_inf = sigma^2 diag(1, omega0^2).
  * Matern-3/2 is the critically damped SHO: Q = 1/2, omega0 = sqrt(3)/ell
- * (Eq. sho_kernel, Q = 1/2 case).  Last parameter: white-noise sd s. */
+ * (Eq. sho_kernel, Q = 1/2 case).
+ * Product of two SHOs (Appendix C.2): (sigma, omega_a, Q_a, omega_b, Q_b),
+ *   k = sigma^2 k_a k_b with unit-variance factors; factor b's (omega, Q)
+ *   are stored at index MAXT + t of w0 and q.
+ * Last parameter: white-noise sd s. */
 static void SFX(term_params)(const model_t *M, const SCALAR *th, SCALAR *w0, SCALAR *q,
                              SCALAR *var, SCALAR *s2) {
   int j = 0;
@@ -21,11 +25,18 @@ static void SFX(term_params)(const model_t *M, const SCALAR *th, SCALAR *w0, SCA
       w0[t] = th[j + 1];
       q[t] = th[j + 2];
       j += 3;
-    } else {
+    } else if (M->kind[t] == 2) {
       sig = th[j];
       w0[t] = S_SQRT(3.0) / th[j + 1];
       q[t] = 0.5;
       j += 2;
+    } else {
+      sig = th[j];
+      w0[t] = th[j + 1];
+      q[t] = th[j + 2];
+      w0[MAXT + t] = th[j + 3];
+      q[MAXT + t] = th[j + 4];
+      j += 5;
     }
     var[t] = sig * sig;
   }
@@ -45,16 +56,39 @@ static void SFX(build_F)(const model_t *M, const SCALAR *w0, const SCALAR *q, co
     LQL[i] = 0;
   }
   for (int t = 0; t < M->n_terms; ++t) {
-    int i = 2 * t;
-    F[i * D + i + 1] = 1.0;
-    F[(i + 1) * D + i] = -w0[t] * w0[t];
-    F[(i + 1) * D + i + 1] = -w0[t] / q[t];
-    LQL[(i + 1) * D + i + 1] = 2.0 * w0[t] * w0[t] * w0[t] * var[t] / q[t];
+    const int i = M->toff[t];
+    if (M->kind[t] != 3) {
+      F[i * D + i + 1] = 1.0;
+      F[(i + 1) * D + i] = -w0[t] * w0[t];
+      F[(i + 1) * D + i + 1] = -w0[t] / q[t];
+      LQL[(i + 1) * D + i + 1] = 2.0 * w0[t] * w0[t] * w0[t] * var[t] / q[t];
+      continue;
+    }
+    /* product (Appendix C.2): F = F_a (x) I + I (x) F_b and
+     * L Q_c L^T = (L Q_c L^T)_a (x) P_inf,b + P_inf,a (x) (L Q_c L^T)_b,
+     * factor a of unit variance, factor b of variance sigma^2; index of
+     * (row of a, row of b) = 2 r_a + r_b. */
+    const SCALAR wa = w0[t], qa = q[t], wb = w0[MAXT + t], qb = q[MAXT + t];
+    const SCALAR Fa[4] = {0.0, 1.0, -wa * wa, -wa / qa}, Fb[4] = {0.0, 1.0, -wb * wb, -wb / qb};
+    const SCALAR Pa[2] = {1.0, wa * wa}, Pb[2] = {var[t], var[t] * wb * wb};
+    const SCALAR La = 2.0 * wa * wa * wa / qa, Lb = 2.0 * wb * wb * wb * var[t] / qb;
+    for (int ra = 0; ra < 2; ++ra)
+      for (int rb = 0; rb < 2; ++rb)
+        for (int ca = 0; ca < 2; ++ca)
+          for (int cb = 0; cb < 2; ++cb) {
+            const int r = i + 2 * ra + rb, c = i + 2 * ca + cb;
+            F[r * D + c] = (rb == cb ? Fa[2 * ra + ca] : 0.0) + (ra == ca ? Fb[2 * rb + cb] : 0.0);
+          }
+    for (int ra = 0; ra < 2; ++ra)
+      for (int rb = 0; rb < 2; ++rb) {
+        const int r = i + 2 * ra + rb;
+        LQL[r * D + r] = (ra == 1 ? La : 0.0) * Pb[rb] + Pa[ra] * (rb == 1 ? Lb : 0.0);
+      }
   }
   for (int j = 0; j < M->n_slots; ++j) {
     for (int t = 0; t < M->n_terms; ++t) {
       int zi = zindex(M, j, t);
-      F[zi * D + 2 * t] = 1.0;
+      F[zi * D + M->toff[t]] = 1.0;
     }
   }
 }
@@ -176,10 +210,18 @@ static void SFX(initial_cov)(const model_t *M, const SCALAR *w0, const SCALAR *v
   const int D = M->dim;
   for (int i = 0; i < D * D; ++i) P[i] = 0;
   for (int t = 0; t < M->n_terms; ++t) {
-    P[(2 * t) * D + 2 * t] = var[t];
-    P[(2 * t + 1) * D + 2 * t + 1] = var[t] * w0[t] * w0[t];
+    const int i = M->toff[t];
+    if (M->kind[t] != 3) {
+      P[i * D + i] = var[t];
+      P[(i + 1) * D + i + 1] = var[t] * w0[t] * w0[t];
+      continue;
+    }
+    /* P_inf = P_inf,a (x) P_inf,b (Appendix C.2) */
+    const SCALAR Pa[2] = {1.0, w0[t] * w0[t]}, Pb[2] = {var[t], var[t] * w0[MAXT + t] * w0[MAXT + t]};
+    for (int ra = 0; ra < 2; ++ra)
+      for (int rb = 0; rb < 2; ++rb) P[(i + 2 * ra + rb) * D + i + 2 * ra + rb] = Pa[ra] * Pb[rb];
   }
-  for (int i = 2 * M->n_terms; i < D; ++i) P[i * D + i] = 1.0;
+  for (int i = M->nx; i < D; ++i) P[i * D + i] = 1.0;
 }
 
 /* Sequential integrated Kalman filter and log-likelihood.
@@ -194,7 +236,7 @@ static int SFX(filter)(const model_t *M, const SCALAR *th, int64_t n_ev, const S
                        const double *r0_ev, const SCALAR *invd_ev, SCALAR *ll_out, double *dumpP,
                        double *dumpS) {
   const int D = M->dim;
-  SCALAR w0[MAXT], q[MAXT], var[MAXT], s2;
+  SCALAR w0[2 * MAXT], q[2 * MAXT], var[MAXT], s2;
   SCALAR F[MAXD * MAXD], LQL[MAXD * MAXD], Phi[MAXD * MAXD], Qd[MAXD * MAXD];
   SCALAR P[MAXD * MAXD], T[MAXD * MAXD], A[MAXD * MAXD];
   SCALAR m[MAXD], mt[MAXD], h[MAXD], u[MAXD], K[MAXD];
@@ -239,7 +281,7 @@ static int SFX(filter)(const model_t *M, const SCALAR *th, int64_t n_ev, const S
     } else {
       for (int i = 0; i < D; ++i) h[i] = 0;
       if (kind[k] == 2)
-        for (int t = 0; t < M->n_terms; ++t) h[2 * t] = 1.0; /* instantaneous: f = H x */
+        for (int t = 0; t < M->n_terms; ++t) h[M->toff[t]] = 1.0; /* instantaneous: f = H x */
       else
         for (int t = 0; t < M->n_zper; ++t) h[zindex(M, sj, t)] = invd_ev[k];
       SCALAR Sv = r0_ev[k] + s2, hm = 0;
