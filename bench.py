@@ -62,6 +62,32 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def product_extra(gp, stream):
+    """Log-likelihood throughput of the product-kernel path (quasi-periodic
+    SHO x SHO + Matern-3/2 on instantaneous measurements, 410 series of the
+    c2p recipe, one thread per series), FP32 and FP64."""
+    import synth
+    import torch
+    wl = synth.c2p(n_series=410)
+    theta = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
+    out = {"workload": "c2p, 410 series", "n_meas": int(wl.n_meas), "unit": UNIT,
+           "work": "loglik only (plain per-series filter)"}
+    for prec in (32, 64):
+        m = gp.Model.from_workload(wl, precision=prec)
+        ll = torch.empty(wl.n_series, dtype=torch.float64, device="cuda")
+        m.loglik(theta, out=ll)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            m.loglik(theta, out=ll)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[f"fp{prec}"] = wl.n_meas / (a.elapsed_time(b) / 3 / 1e3)
+        del m
+    return out
+
+
 def workload(name):
     import synth
     if name == "c1":
@@ -76,6 +102,8 @@ def workload(name):
         return synth.c5()
     if name == "c2i":  # the c2 recipe on instantaneous measurements
         return synth.c2i()
+    if name == "c2p":  # product kernel on instantaneous measurements (loglik only)
+        return synth.c2p()
     if name == "c4h":  # 512 series of the c4 recipe (profiling captures)
         return synth.c4(n_series=512)
     if name == "c4s":  # small variant for quick checks
@@ -338,7 +366,7 @@ def run_ours(args):
         for _ in range(k2):
             model.loglik_grad_host(th_host, reupload_events=True)
         el = (time.perf_counter() - t1) / k2
-        h2d = 2 * wl.n_meas * 5 + wl.n_meas * 16 + th_host.nbytes
+        h2d = model.info["n_events"] * 5 + wl.n_meas * 16 + th_host.nbytes
         d2h = n_out * 8 + n_out * model.n_params * 4
         e2e = {"value": total_meas / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": el * 1e3}
@@ -385,11 +413,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     extra["fp32_condition"] = {"value": wl.n_meas / (a.elapsed_time(b) / 3 / 1e3), "unit": UNIT,
                                "work": "loglik + conditioned mean/variance per measurement"}
+    if not args.no_product:
+        extra["product_kernel_loglik"] = product_extra(gp, stream)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "n_series": int(wl_full.n_series),
-                       "n_meas": total_meas, "n_events": 2 * total_meas,
+                       "n_meas": total_meas, "n_events": int(model.info["n_events"]) * world,
                        "state_dim": model.info["state_dim"], "n_params": model.n_params,
                        "chunk_len": (tuned or {}).get("chunk_len", args.chunk_len), "n_chunks": model.info["n_chunks"],
                        "autotuned": tuned,
@@ -471,6 +501,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-product", action="store_true")
     ap.add_argument("--accuracy", action="store_true",
                     help="print FP32-vs-FP64 errors per workload instead of timing")
     ap.add_argument("--accuracy-workloads", default="c1,c2,c3,c4,c5")

@@ -30,9 +30,14 @@
  *    returns, so calls on different streams may share one model.
  *  - Hyperparameters are natural parameters, one row of n_params floats per
  *    set: per term (sigma, omega0, Q) for GP_SS_TERM_SHO (any Q > 0: the
- *    overdamped oscillator Q < 1/2 of Appendix B included) or (sigma, ell)
- *    for GP_SS_TERM_MATERN32, in the order of the kernel spec, then the
- *    white-noise sd s.  n_params = 3*#SHO + 2*#Matern + 1.  Non-finite or
+ *    overdamped oscillator Q < 1/2 of Appendix B included), (sigma, ell)
+ *    for GP_SS_TERM_MATERN32 or (sigma, omega_a, Q_a, omega_b, Q_b) for
+ *    GP_SS_TERM_SHO_PRODUCT, in the order of the kernel spec, then the
+ *    white-noise sd s.  n_params = 3*#SHO + 2*#Matern + 5*#product + 1.
+ *  - A measurement with t_end == t_start is instantaneous: it observes the
+ *    latent f(t) itself (Section 2).  A model holds either instantaneous
+ *    measurements only or exposure averages only (GP_SS_EUNSUPPORTED
+ *    otherwise); instantaneous models have no integral states.  Non-finite or
  *    non-positive values surface as GP_SS_ENUMERIC (gp_ss_last_error_series).
  */
 #ifndef GPSS_H
@@ -61,7 +66,13 @@ typedef enum {
 
 typedef enum {
   GP_SS_TERM_SHO = 1,      /* (sigma, omega0, Q): Appendix B, Eq. sho_kernel */
-  GP_SS_TERM_MATERN32 = 2  /* (sigma, ell) == SHO with Q = 1/2, omega0 = sqrt(3)/ell */
+  GP_SS_TERM_MATERN32 = 2, /* (sigma, ell) == SHO with Q = 1/2, omega0 = sqrt(3)/ell */
+  GP_SS_TERM_SHO_PRODUCT = 3 /* (sigma, omega_a, Q_a, omega_b, Q_b): sigma^2 k_a k_b, two
+                                unit-variance SHO factors (Appendix C.2, Kronecker state of
+                                dimension 4).  First term only, at most one plain term after
+                                it, instantaneous measurements only; gp_ss_loglik (the plain
+                                per-series filter, FP32 or FP64) only, other calls return
+                                GP_SS_EUNSUPPORTED. */
 } gp_ss_term;
 
 typedef struct {

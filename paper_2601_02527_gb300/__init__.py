@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libgpss.so")
 
 SHO = 1
 MATERN32 = 2
+SHO_PRODUCT = 3
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "series offsets not sorted",
           3: "an instrument's exposures overlap each other",
@@ -122,7 +123,7 @@ def _spec(terms, layout):
 
 
 def n_params_for(terms) -> int:
-    return sum(3 if int(t) == SHO else 2 for t in terms) + 1
+    return sum({SHO: 3, SHO_PRODUCT: 5}.get(int(t), 2) for t in terms) + 1
 
 
 class Model:

@@ -20,7 +20,7 @@ OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgpss.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["gpss_api.cu", "gpss_inst_t1.cu", "gpss_inst_t2.cu", "gpss_inst_t2s3.cu",
-           "gpss_inst_t2l1.cu", "gpss_inst_i.cu"]
+           "gpss_inst_t2l1.cu", "gpss_inst_i.cu", "gpss_inst_p.cu"]
 
 
 def nvcc_path() -> str:

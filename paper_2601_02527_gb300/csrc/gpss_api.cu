@@ -25,6 +25,8 @@ OpTable ops_2_3_0();
 OpTable ops_2_1_1();
 OpTable ops_1_0_0();
 OpTable ops_2_0_0();
+OpTable ops_prod1();
+OpTable ops_prod2();
 
 __global__ void k_series_sum(int n_out, int per_series, int n_series, int n_chunks,
                              const int32_t *__restrict__ ch_first,
@@ -144,6 +146,7 @@ struct GraphKey {
 struct gp_ss_model {
   int device = 0;
   int n_series = 0, n_terms = 0, kinds[4] = {0, 0, 0, 0}, layout = 0, n_slots = 1;
+  bool product = false;  // a product term: plain log-likelihood filters only
   int n_params = 0, precision = 32, schedule = 0;
   int64_t n_meas = 0, n_events = 0;
   OpTable ops{};
@@ -590,6 +593,15 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
   if (s0) return s0;
   const gpss::DevModel dm = dev_view(m);
   const OpTable &o = m->ops;
+  if (m->product) {
+    // product kernels: the plain filters (log-likelihood only)
+    if (grad || dexp || cond_out || pred) return GP_SS_EUNSUPPORTED;
+    if (m->precision == 64 && !m->d_dt64) return GP_SS_EINVAL;
+    PhaseTimer pt(m, st, 4);
+    GPSS_CK((m->precision == 64 ? o.plain64 : o.plain32)(dm, theta, n_out, per_series, ll,
+                                                         m->d_err, st));
+    return GP_SS_OK;
+  }
   if (m->precision == 64) {
     if (grad) return GP_SS_EUNSUPPORTED;
     if (!m->d_dt64) return GP_SS_EINVAL;
@@ -825,8 +837,12 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   if (spec->n_terms < 1 || spec->n_terms > 2) return GP_SS_EUNSUPPORTED;
   if (spec->integral_layout != 0 && spec->integral_layout != 1) return GP_SS_EINVAL;
   for (int t = 0; t < spec->n_terms; ++t)
-    if (spec->terms[t] != GP_SS_TERM_SHO && spec->terms[t] != GP_SS_TERM_MATERN32)
+    if (spec->terms[t] != GP_SS_TERM_SHO && spec->terms[t] != GP_SS_TERM_MATERN32 &&
+        spec->terms[t] != GP_SS_TERM_SHO_PRODUCT)
       return GP_SS_EINVAL;
+  // a product term is compiled as the first term, with at most one plain term
+  for (int t = 1; t < spec->n_terms; ++t)
+    if (spec->terms[t] == GP_SS_TERM_SHO_PRODUCT) return GP_SS_EUNSUPPORTED;
   gp_ss_options o{};
   o.precision = 32;
   if (opts) o = *opts;
@@ -861,8 +877,10 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   m->n_params = 1;
   for (int t = 0; t < spec->n_terms; ++t) {
     m->kinds[t] = spec->terms[t];
-    m->n_params += spec->terms[t] == GP_SS_TERM_SHO ? 3 : 2;
+    m->n_params += spec->terms[t] == GP_SS_TERM_SHO ? 3
+                   : spec->terms[t] == GP_SS_TERM_MATERN32 ? 2 : 5;
   }
+  m->product = spec->terms[0] == GP_SS_TERM_SHO_PRODUCT;
   m->n_meas = N;
   m->ev_off.resize(n_series + 1);
   m->meas_off.resize(n_series + 1);
@@ -879,7 +897,8 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
     delete m;
     return GP_SS_EINVAL;
   }
-  if (n_inst > 0 && n_inst < N) {
+  if ((n_inst > 0 && n_inst < N) || (m->product && n_inst < N)) {
+    // mixed kinds, or a product kernel on exposure averages: not compiled
     delete m;
     return GP_SS_EUNSUPPORTED;
   }
@@ -949,7 +968,9 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
     n_slots = std::max(n_slots, so[s].n_slots);
   }
   m->n_slots = n_slots;
-  if (n_slots > kMaxSlots || !pick_ops(m->n_terms, n_slots, m->layout, &m->ops)) {
+  if (m->product) {
+    m->ops = m->n_terms == 1 ? gpss::ops_prod1() : gpss::ops_prod2();
+  } else if (n_slots > kMaxSlots || !pick_ops(m->n_terms, n_slots, m->layout, &m->ops)) {
     free_model_buffers(m);
     delete m;
     return GP_SS_EUNSUPPORTED;
@@ -1004,8 +1025,12 @@ gp_ss_status gp_ss_discretize(const gp_ss_kernel_spec *spec, int n_slots, const 
   if (!spec || !spec->terms || !theta || !dt || !phi_out || !q_out || n < 0) return GP_SS_EINVAL;
   if (spec->n_terms < 1 || spec->n_terms > 2 || n_slots < 1) return GP_SS_EUNSUPPORTED;
   for (int t = 0; t < spec->n_terms; ++t)
-    if (spec->terms[t] != GP_SS_TERM_SHO && spec->terms[t] != GP_SS_TERM_MATERN32)
+    if (spec->terms[t] != GP_SS_TERM_SHO && spec->terms[t] != GP_SS_TERM_MATERN32 &&
+        spec->terms[t] != GP_SS_TERM_SHO_PRODUCT)
       return GP_SS_EINVAL;
+  // a product term is compiled as the first term, with at most one plain term
+  for (int t = 1; t < spec->n_terms; ++t)
+    if (spec->terms[t] == GP_SS_TERM_SHO_PRODUCT) return GP_SS_EUNSUPPORTED;
   OpTable o;
   const int layout = spec->n_terms == 1 ? 0 : spec->integral_layout;
   if (!pick_ops(spec->n_terms, n_slots, layout, &o)) return GP_SS_EUNSUPPORTED;
@@ -1263,6 +1288,7 @@ gp_ss_status gp_ss_autotune(gp_ss_model *m, const float *theta, int n_sets,
   gp_ss_status s = check_call(m, theta, n_sets, theta_per_series, best);
   if (s) return s;
   if (m->precision != 32 || reps < 1 || reps > 100) return GP_SS_EINVAL;
+  if (m->product) return GP_SS_EUNSUPPORTED;  // one schedule: nothing to tune
   DeviceGuard g(m->device);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   if (cudaDeviceSynchronize() != cudaSuccess) return GP_SS_ECUDA;
@@ -1441,7 +1467,7 @@ extern "C" gp_ss_status gp_ss_loglik_noalloc(const gp_ss_model *m, const float *
                                              double *loglik_out, void *cuda_stream) {
   gp_ss_status s = check_call(m, theta, n_sets, theta_per_series, loglik_out);
   if (s) return s;
-  if (m->precision != 32) return GP_SS_EUNSUPPORTED;
+  if (m->precision != 32 || m->product) return GP_SS_EUNSUPPORTED;
   const int n_out = theta_per_series ? m->n_series : n_sets * m->n_series;
   const int64_t n_vch64 = (int64_t)(theta_per_series ? 1 : n_sets) * m->n_chunks;
   const OpTable &o = m->ops;

@@ -1,0 +1,208 @@
+// Product kernels (Appendix C.2) on instantaneous measurements.
+//
+// A product of two SHO terms, k = sigma^2 k_a k_b with unit-variance factors
+// (parameters sigma, omega_a, Q_a, omega_b, Q_b), is the state-space model
+// with F = F_a (x) I + I (x) F_b, P_inf = P_inf,a (x) P_inf,b and observation
+// H = H_a (x) H_b = e_0; its transition is Phi_a (x) Phi_b and its process
+// noise Q = P_inf,a (x) Q_b + Q_a (x) P_inf,b - Q_a (x) Q_b (Eq. product_Q),
+// all from the two factors' per-step scalars (f, f', I_ff, I_pp; see
+// gpss_device.cuh).  Optionally a second, plain SHO / Matern-3/2 term is
+// added (state 4 + 2).  The state dimension grows as the product of the
+// factors' (Section C.2), so this path runs the sequential filter with one
+// thread per series and the full covariance in registers: log-likelihood
+// only, FP32 (FP64 sums) or FP64.
+#pragma once
+
+#include "gpss_kernels.cuh"
+
+namespace gpss {
+
+// The 2 x 2 transition and process noise of one oscillator factor of
+// variance var from its six per-step scalars (Eqs. sho_phi, Q).
+template <class F>
+struct Osc2 {
+  F p[2][2], q[2][2];
+};
+
+template <class F>
+GPSS_D Osc2<F> osc2(F dt, F w0, F Q, F var) {
+  const F a = w0 / (F(2) * Q);
+  const F beta = (Q == F(0.5)) ? F(0) : w0 * w0 * (F(1) - F(1) / (F(4) * Q * Q));
+  const Disc<F> d = discretize<F, F, true>(dt, a, beta);
+  const F qc = F(2) * w0 * w0 * w0 * var / Q;
+  Osc2<F> o;
+  o.p[0][0] = d.fp + F(2) * a * d.f;
+  o.p[0][1] = d.f;
+  o.p[1][0] = -w0 * w0 * d.f;
+  o.p[1][1] = d.fp;
+  o.q[0][0] = qc * d.Iff;
+  o.q[0][1] = o.q[1][0] = qc * d.f * d.f * F(0.5);
+  o.q[1][1] = qc * d.Ipp;
+  return o;
+}
+
+// One thread per (parameter set, series).  Parameter row: (sigma, omega_a,
+// Q_a, omega_b, Q_b) of the product, then (sigma, omega0, Q) or (sigma, ell)
+// of the plain term when SUM, then the white-noise sd.
+template <bool SUM, class F>
+__global__ void __launch_bounds__(128) k_plain_prod(DevModel M, const float *__restrict__ theta,
+                                                    int n_out, int per_series,
+                                                    double *__restrict__ ll_out,
+                                                    int *__restrict__ err) {
+  constexpr int D = SUM ? 6 : 4;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n_out) return;
+  const int s = per_series ? v : v % M.n_series;
+  const int row = per_series ? v : v / M.n_series;
+  const float *th = theta + (size_t)row * M.n_params;
+  const F sig = th[0], wa = th[1], qa = th[2], wb = th[3], qb = th[4];
+  const F var = sig * sig;
+  const F Pa[2] = {F(1), wa * wa}, Pb[2] = {var, var * wb * wb};
+  F sc = F(0), wc = F(1), qcq = F(0.5);
+  int j = 5;
+  if constexpr (SUM) {
+    sc = th[5];
+    if (M.kinds[1] == 1) {
+      wc = th[6];
+      qcq = th[7];
+      j = 8;
+    } else {
+      wc = F(1.7320508075688772) / F(th[6]);
+      j = 7;
+    }
+  }
+  const F s2 = F(th[j]) * F(th[j]);
+  // P0 = blkdiag(P_inf,a (x) P_inf,b, P_inf,c); m0 = 0
+  F m[D], P[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    m[i] = F(0);
+#pragma unroll
+    for (int c = 0; c < D; ++c) P[i][c] = F(0);
+  }
+#pragma unroll
+  for (int ra = 0; ra < 2; ++ra)
+#pragma unroll
+    for (int rb = 0; rb < 2; ++rb) P[2 * ra + rb][2 * ra + rb] = Pa[ra] * Pb[rb];
+  if constexpr (SUM) {
+    P[4][4] = sc * sc;
+    P[5][5] = sc * sc * wc * wc;
+  }
+  double sum_logS = 0.0, sum_q = 0.0;
+  int64_t n_end = 0;
+  bool bad = false;
+  int64_t mi = M.meas_off[s];
+  const int64_t e1 = M.ev_off[s + 1];
+  for (int64_t k = M.ev_off[s]; k < e1; ++k) {
+    const F dt = load_dt<F>(M, k);
+    F y, r0, w;
+    load_meas<F>(M, mi, y, r0, w);
+    ++mi;
+    const Osc2<F> A = osc2<F>(dt, wa, qa, F(1));
+    const Osc2<F> B = osc2<F>(dt, wb, qb, var);
+    // Phi (block-diagonal: the product's Kronecker block, then the plain term)
+    F Phi[D][D], Qd[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) Phi[r][c] = Qd[r][c] = F(0);
+#pragma unroll
+    for (int ra = 0; ra < 2; ++ra)
+#pragma unroll
+      for (int rb = 0; rb < 2; ++rb)
+#pragma unroll
+        for (int ca = 0; ca < 2; ++ca)
+#pragma unroll
+          for (int cb = 0; cb < 2; ++cb) {
+            const int r = 2 * ra + rb, c = 2 * ca + cb;
+            Phi[r][c] = A.p[ra][ca] * B.p[rb][cb];
+            // Eq. product_Q: P_inf,a (x) Q_b + Q_a (x) P_inf,b - Q_a (x) Q_b
+            Qd[r][c] = (ra == ca ? Pa[ra] * B.q[rb][cb] : F(0)) +
+                       (rb == cb ? A.q[ra][ca] * Pb[rb] : F(0)) - A.q[ra][ca] * B.q[rb][cb];
+          }
+    if constexpr (SUM) {
+      const Osc2<F> C = osc2<F>(dt, wc, qcq, sc * sc);
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          Phi[4 + r][4 + c] = C.p[r][c];
+          Qd[4 + r][4 + c] = C.q[r][c];
+        }
+    }
+    // predict: m <- Phi m, P <- Phi P Phi^T + Q
+    F mt[D], T[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      F acc = F(0);
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc += Phi[r][c] * m[c];
+      mt[r] = acc;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        F a2 = F(0);
+#pragma unroll
+        for (int e = 0; e < D; ++e) a2 += Phi[r][e] * P[e][c];
+        T[r][c] = a2;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      m[r] = mt[r];
+#pragma unroll
+      for (int c = r; c < D; ++c) {
+        F a2 = Qd[r][c];
+#pragma unroll
+        for (int e = 0; e < D; ++e) a2 += T[r][e] * Phi[c][e];
+        P[r][c] = a2;
+        P[c][r] = a2;
+      }
+    }
+    // update with h = e_0 (+ e_4): the latent f(t) of the product (and term)
+    F u[D], hu = F(0), hm = m[0] + (SUM ? m[4] : F(0));
+#pragma unroll
+    for (int r = 0; r < D; ++r) u[r] = P[r][0] + (SUM ? P[r][4] : F(0));
+    hu = u[0] + (SUM ? u[4] : F(0));
+    const F Sv = hu + r0 + s2;
+    const F vv = y - hm;
+    bad |= !(Sv > F(0));
+    const F iS = F(1) / Sv;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      m[r] += u[r] * vv * iS;
+#pragma unroll
+      for (int c = 0; c < D; ++c) P[r][c] -= u[r] * u[c] * iS;
+    }
+    sum_logS += glog(Sv);
+    sum_q += (double)(vv * vv / Sv);
+    ++n_end;
+  }
+  const double ll = -0.5 * ((double)n_end * LOG_2PI + sum_logS + sum_q);
+  bad |= !isfinite(ll);
+  ll_out[v] = ll;
+  if (bad) flag_error(err, v, 7);
+}
+
+template <bool SUM, class F>
+cudaError_t launch_plain_prod(const DevModel &M, const float *theta, int n_out, int per_series,
+                              double *ll, int *err, cudaStream_t st) {
+  if (n_out <= 0) return cudaSuccess;
+  const int bs = 128;
+  k_plain_prod<SUM, F><<<(n_out + bs - 1) / bs, bs, 0, st>>>(M, theta, n_out, per_series, ll, err);
+  GPSS_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+// Operation table of a product model: the plain filters only.
+template <bool SUM>
+OpTable make_prod_ops() {
+  OpTable o{};
+  o.D = SUM ? 6 : 4;
+  o.NP = o.D * (o.D + 1) / 2;
+  o.NT = SUM ? 2 : 1;
+  o.plain32 = &launch_plain_prod<SUM, float>;
+  o.plain64 = &launch_plain_prod<SUM, double>;
+  return o;
+}
+
+}  // namespace gpss

@@ -43,6 +43,7 @@ TWO_PI = 2.0 * math.pi
 # kernel term kinds (match the C ABI enum values)
 SHO = 1
 MATERN32 = 2
+SHO_PRODUCT = 3
 
 
 @dataclasses.dataclass
@@ -101,20 +102,37 @@ class Workload:
 
 
 def n_params_for(terms) -> int:
-    return sum(3 if k == SHO else 2 for k in terms) + 1
+    return sum({SHO: 3, SHO_PRODUCT: 5}.get(k, 2) for k in terms) + 1
 
 
 def _term_spectra(terms, theta_row):
-    """(sigma, omega0, Q) of each term; Matern-3/2 is the Q = 1/2 oscillator."""
+    """(sigma, omega0, Q) of each term; Matern-3/2 is the Q = 1/2 oscillator;
+    a product of two SHOs gives (sigma, omega_a, Q_a, omega_b, Q_b)."""
     out = []
     j = 0
     for k in terms:
         if k == SHO:
             out.append(tuple(theta_row[j:j + 3]))
             j += 3
+        elif k == SHO_PRODUCT:
+            out.append(tuple(theta_row[j:j + 5]))
+            j += 5
         else:
             out.append((theta_row[j], math.sqrt(3.0) / theta_row[j + 1], 0.5))
             j += 2
+    return out
+
+
+def _rff(rng, t, sig, w0, q, n_feat):
+    """Random-Fourier-feature draw with the oscillator's covariance at times t."""
+    w = _sample_psd(rng, w0, q, n_feat)
+    ph = rng.uniform(0, TWO_PI, n_feat)
+    amp = sig * math.sqrt(2.0 / n_feat)
+    out = np.zeros_like(t)
+    for a in range(0, len(t), 16384):
+        sl = slice(a, a + 16384)
+        arg = np.mod(np.outer(t[sl], w) + ph, TWO_PI)
+        out[sl] = amp * np.sum(np.cos(arg), axis=1)
     return out
 
 
@@ -142,7 +160,16 @@ def exposure_average_signal(rng, t_start, t_end, terms, theta_row, n_feat=16):
     tm = 0.5 * (t_start + t_end)
     half = 0.5 * (t_end - t_start)
     f = np.zeros_like(tm)
-    for sig, w0, q in _term_spectra(terms, theta_row):
+    for par in _term_spectra(terms, theta_row):
+        if len(par) == 5:
+            # product of two independent draws: covariance sigma^2 k_a k_b
+            # (instantaneous measurements only)
+            if np.any(half != 0):
+                raise NotImplementedError("product terms: instantaneous measurements only")
+            sig, wa, qa, wb, qb = par
+            f += _rff(rng, tm, 1.0, wa, qa, n_feat) * _rff(rng, tm, sig, wb, qb, n_feat)
+            continue
+        sig, w0, q = par
         w = _sample_psd(rng, w0, q, n_feat)
         ph = rng.uniform(0, TWO_PI, n_feat)
         amp = sig * math.sqrt(2.0 / n_feat)
@@ -276,6 +303,31 @@ def c2i(seed=1006, n_series=4096, scale=1.0, nmin=500, nmax=20000, gap_mean=1.0)
         t = np.cumsum(rng.exponential(gap_mean, int(n)))
         series.append((t, t.copy()))
     return _finish("c2i", [SHO, MATERN32], 0, series, theta, True, rng)
+
+
+def c2p(seed=1007, n_series=4096, scale=1.0, nmin=500, nmax=20000, gap_mean=1.0):
+    """Quasi-periodic batch on instantaneous measurements: a product of two SHO
+    terms (a slow envelope omega_a = 2 pi / 50, Q_a = 1 times a resonance
+    omega_b = 2 pi / 5, Q_b = 10, Appendix C.2) plus a Matern-3/2 term, each
+    parameter log-uniform over a factor 10 per series (Q_a truncated >= 0.55);
+    times with Exponential(gap_mean) gaps."""
+    rng = np.random.default_rng(seed)
+    ns = np.rint(np.exp(rng.uniform(math.log(nmin), math.log(nmax), n_series)) * scale)
+    ns = np.maximum(ns, 2).astype(np.int64)
+    theta = np.empty((n_series, 8))
+    theta[:, 0] = _loguniform(rng, 1.0, 10, n_series)
+    theta[:, 1] = _loguniform(rng, TWO_PI / 50, 10, n_series)
+    theta[:, 2] = np.maximum(_loguniform(rng, 1.0, 10, n_series), 0.55)
+    theta[:, 3] = _loguniform(rng, TWO_PI / 5, 10, n_series)
+    theta[:, 4] = _loguniform(rng, 10.0, 10, n_series)
+    theta[:, 5] = _loguniform(rng, 0.5, 10, n_series)
+    theta[:, 6] = _loguniform(rng, 5.0, 10, n_series)
+    theta[:, 7] = 0.1
+    series = []
+    for n in ns:
+        t = np.cumsum(rng.exponential(gap_mean, int(n)))
+        series.append((t, t.copy()))
+    return _finish("c2p", [SHO_PRODUCT, MATERN32], 0, series, theta, True, rng)
 
 
 def c3(seed=1003, n=1 << 22):

@@ -1,0 +1,93 @@
+"""GPU parity for product kernels (Appendix C.2) on instantaneous measurements
+against the FP64 oracle: the plain per-series filter in FP32 (FP64 sums;
+|L_gpu - L_or| <= 1e-4 max(|L_or|, 0.1 N)) and in FP64 (1e-9 relative).
+Calls the product path does not provide report GP_SS_EUNSUPPORTED.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SHO, M32, PROD = 1, 2, 3
+
+
+@pytest.fixture(scope="module")
+def gp():
+    from paper_2601_02527_gb300 import build as gbuild
+    gbuild.build()
+    import paper_2601_02527_gb300 as g
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    oracle.build()
+    return g
+
+
+def _f32(wl):
+    wl.theta = wl.theta.astype(np.float32).astype(np.float64)
+    return wl
+
+
+def _dev(th):
+    return torch.tensor(th, dtype=torch.float32, device="cuda")
+
+
+def _check(ll, ref, counts, rel=None):
+    for a, b, n in zip(ll, ref, counts):
+        tol = rel * abs(b) if rel else 1e-4 * max(abs(b), 0.1 * n)
+        assert abs(a - b) <= tol, (a, b, n)
+
+
+def _series_wl(terms, theta, n=600, seed=111):
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(0.8, n))
+    return _f32(synth._finish("p", terms, 0, [(t, t.copy())], np.asarray([theta]), True, rng))
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_batch_product_plus_matern(gp, precision):
+    wl = _f32(synth.c2p(n_series=8, scale=0.05))
+    m = gp.Model.from_workload(wl, precision=precision)
+    ll = m.loglik(_dev(wl.theta)).cpu().numpy()
+    ref = oracle.loglik_workload(wl, processes=4)
+    _check(ll, ref, np.diff(wl.offsets), rel=1e-9 if precision == 64 else None)
+    assert m.last_error() == (-1, 0)
+
+
+@pytest.mark.parametrize("terms,theta", [
+    ([PROD], [1.2, 0.2, 1.5, 2.0, 8.0, 0.1]),
+    ([PROD, SHO], [1.0, 0.3, 0.8, 1.3, 4.0, 0.6, 3.0, 0.3, 0.1]),   # overdamped plain term
+    ([PROD], [0.9, 0.5, 0.3, 1.1, 2.0, 0.05])])                     # overdamped factor
+def test_single_series(gp, terms, theta):
+    wl = _series_wl(terms, theta)
+    for precision in (32, 64):
+        m = gp.Model.from_workload(wl, precision=precision)
+        ll = m.loglik(_dev(wl.theta)).cpu().numpy()
+        _check(ll, oracle.loglik_workload(wl), [wl.n_meas], rel=1e-9 if precision == 64 else None)
+
+
+def test_shared_theta_sets(gp):
+    wl = _series_wl([PROD, M32], [1.0, 0.3, 1.0, 1.3, 5.0, 0.5, 3.0, 0.1], n=400)
+    th = np.array([wl.theta[0], wl.theta[0] * [1, 1.2, 1, 0.9, 1, 1, 1, 1]], np.float64)
+    th = th.astype(np.float32).astype(np.float64)
+    m = gp.Model.from_workload(wl)
+    ll = m.loglik(_dev(th), per_series=False).cpu().numpy().ravel()
+    ref = [oracle.loglik(wl.terms, 0, *wl.series(0)[:4], th[k]) for k in range(2)]
+    _check(ll, ref, [wl.n_meas] * 2)
+
+
+def test_unsupported_calls(gp):
+    wl = _series_wl([PROD], [1.2, 0.2, 1.5, 2.0, 8.0, 0.1], n=100)
+    m = gp.Model.from_workload(wl)
+    th = _dev(wl.theta)
+    with pytest.raises(Exception):
+        m.loglik_grad(th)
+    with pytest.raises(Exception):
+        m.condition(th)
+    t = wl.t_start
+    with pytest.raises(Exception):  # exposure averages with a product kernel
+        gp.Model(wl.terms, wl.offsets, t, t + 0.1, wl.y, wl.yerr, None, layout=0)
