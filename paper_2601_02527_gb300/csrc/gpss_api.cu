@@ -172,6 +172,7 @@ struct gp_ss_model {
   int step_cache = 0;      // 0 auto, 1 never keep the gradient's step scalars
   int64_t *d_ch_ev0 = nullptr, *d_ch_meas0 = nullptr;
   int32_t *d_ch_len = nullptr, *d_ch_series = nullptr, *d_ch_first = nullptr;
+  std::vector<int32_t> ch_first;  // host copy: first chunk of each series
   uint8_t *d_ch_flags = nullptr;
   // step-scalar cache of the gradient: per warp of chunks, 32 x (its longest
   // chunk) lane-steps; d_w_doff[w] = lane-steps before warp w, [n_w] = total
@@ -479,6 +480,7 @@ gp_ss_status make_plan(gp_ss_model *m, int chunk_len) {
   if ((st = dev_upload(&m->d_ch_len, len.data(), len.size()))) return st;
   if ((st = dev_upload(&m->d_ch_series, ser.data(), ser.size()))) return st;
   if ((st = dev_upload(&m->d_ch_first, first.data(), first.size()))) return st;
+  m->ch_first = first;
   if ((st = dev_upload(&m->d_ch_flags, flags.data(), flags.size()))) return st;
   if ((st = dev_upload(&m->d_w_doff, doff.data(), doff.size()))) return st;
   m->dcache_steps = doff[n_w];
@@ -584,10 +586,19 @@ gp_ss_status check_call(const gp_ss_model *m, const float *theta, int n_sets, in
   return GP_SS_OK;
 }
 
+// Series groups whose event streams arrive separately: the element pass of
+// group g (chunks [c0[g], c0[g+1])) waits for event ready[g].
+struct ElemSlices {
+  int n;
+  const int *c0;
+  const cudaEvent_t *ready;
+};
+
 // Enqueue the log-likelihood (and optionally gradient) computation.
 gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int per_series,
                      double *ll, float *grad, cudaStream_t st, float *dexp = nullptr,
-                     float *cond_out = nullptr, const gpss::PredPlan *pred = nullptr) {
+                     float *cond_out = nullptr, const gpss::PredPlan *pred = nullptr,
+                     const ElemSlices *slices = nullptr) {
   const int n_out = per_series ? m->n_series : n_sets * m->n_series;
   gp_ss_status s0 = prepare_err(m, n_out, st);
   if (s0) return s0;
@@ -660,12 +671,21 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
     }
     {
       PhaseTimer pt(m, st, 0);
-      if (o.tables(theta, n_sets, m->n_params, m->kinds[0], m->kinds[1], tabs, st) ||
-          o.elem(dm, theta, n_vch, per_series, ef, ed, m->d_err, tabs, grad ? ckpt : nullptr, ck,
-                 dcache, st)) {
+      if (o.tables(theta, n_sets, m->n_params, m->kinds[0], m->kinds[1], tabs, st)) {
         res = GP_SS_ECUDA;
         break;
       }
+      // whole model, or series groups as their event streams arrive
+      const int ng = slices ? slices->n : 1;
+      for (int g = 0; g < ng && !res; ++g) {
+        const int c0 = slices ? slices->c0[g] : 0;
+        const int cn = slices ? slices->c0[g + 1] - c0 : m->n_chunks;
+        if (slices && cudaStreamWaitEvent(st, slices->ready[g], 0) != cudaSuccess) res = GP_SS_ECUDA;
+        if (!res && o.elem(dm, theta, n_vch, per_series, ef, ed, m->d_err, tabs,
+                           grad ? ckpt : nullptr, ck, dcache, c0, cn, st))
+          res = GP_SS_ECUDA;
+      }
+      if (res) break;
     }
     if ((grad || tree) && !grab((void **)&state_end, (size_t)SD * n_vch * sizeof(float))) {
       res = GP_SS_ENOMEM;
@@ -1232,7 +1252,47 @@ gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *m, const float *theta_hos
       scratch_alloc(m, (void **)&d_grad, (size_t)n_out * m->n_params * sizeof(float), st))
     return GP_SS_ENOMEM;
   gp_ss_status res = GP_SS_OK;
-  if (reupload_events) {
+  // A re-sent event stream goes up in series groups on a second stream, and
+  // each group's element pass starts as soon as its events are in (the copy
+  // of the rest overlaps it).  The copy stream first waits for earlier work
+  // on st, which may still read the device copy.
+  constexpr int kGroups = 4;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t start_ev = nullptr, ready[kGroups] = {};
+  int c0[kGroups + 1] = {};
+  ElemSlices slices{0, c0, ready};
+  const bool pipe = reupload_events && !m->product && m->precision == 32 && m->n_series >= 2 &&
+                    m->ch_first.size() == (size_t)m->n_series + 1;
+  if (pipe) {
+    std::vector<int> sb{0};
+    for (int g = 1; g < kGroups; ++g) {
+      const int64_t target = m->ev_off[m->n_series] * g / kGroups;
+      const int sp = (int)(std::lower_bound(m->ev_off.begin(), m->ev_off.end(), target) -
+                           m->ev_off.begin());
+      if (sp > sb.back() && sp < m->n_series) sb.push_back(sp);
+    }
+    sb.push_back(m->n_series);
+    slices.n = (int)sb.size() - 1;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) ||
+        cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming) ||
+        cudaEventRecord(start_ev, st) || cudaStreamWaitEvent(cs, start_ev, 0))
+      res = GP_SS_ECUDA;
+    for (int g = 0; g < slices.n && !res; ++g) {
+      const int64_t e0 = m->ev_off[sb[g]], e1 = m->ev_off[sb[g + 1]];
+      const int64_t q0 = m->meas_off[sb[g]], q1 = m->meas_off[sb[g + 1]];
+      c0[g] = m->ch_first[sb[g]];
+      if (cudaEventCreateWithFlags(&ready[g], cudaEventDisableTiming) ||
+          cudaMemcpyAsync(m->d_dt + e0, m->h_dt + e0, (size_t)(e1 - e0) * sizeof(float),
+                          cudaMemcpyHostToDevice, cs) ||
+          cudaMemcpyAsync(m->d_tag + e0, m->h_tag + e0, (size_t)(e1 - e0),
+                          cudaMemcpyHostToDevice, cs) ||
+          cudaMemcpyAsync(m->d_meas + q0, m->h_meas + q0, (size_t)(q1 - q0) * sizeof(float4),
+                          cudaMemcpyHostToDevice, cs) ||
+          cudaEventRecord(ready[g], cs))
+        res = GP_SS_ECUDA;
+    }
+    c0[slices.n] = m->ch_first[m->n_series];
+  } else if (reupload_events) {
     if (cudaMemcpyAsync(m->d_dt, m->h_dt, (size_t)m->n_events * sizeof(float),
                         cudaMemcpyHostToDevice, st) ||
         cudaMemcpyAsync(m->d_tag, m->h_tag, (size_t)m->n_events, cudaMemcpyHostToDevice, st) ||
@@ -1242,7 +1302,9 @@ gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *m, const float *theta_hos
   }
   if (!res && cudaMemcpyAsync(d_theta, theta_host, nth * sizeof(float), cudaMemcpyHostToDevice, st))
     res = GP_SS_ECUDA;
-  if (!res) res = enqueue(m, d_theta, n_sets, theta_per_series, d_ll, d_grad, st);
+  if (!res)
+    res = enqueue(m, d_theta, n_sets, theta_per_series, d_ll, d_grad, st, nullptr, nullptr,
+                  nullptr, pipe ? &slices : nullptr);
   if (!res && (cudaMemcpyAsync(loglik_host, d_ll, (size_t)n_out * sizeof(double),
                                cudaMemcpyDeviceToHost, st) ||
                cudaMemcpyAsync(grad_host, d_grad, (size_t)n_out * m->n_params * sizeof(float),
@@ -1252,6 +1314,13 @@ gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *m, const float *theta_hos
   cudaFreeAsync(d_ll, st);
   cudaFreeAsync(d_grad, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !res) res = GP_SS_ECUDA;
+  if (cs) {
+    if (cudaStreamSynchronize(cs) != cudaSuccess && !res) res = GP_SS_ECUDA;
+    cudaStreamDestroy(cs);
+  }
+  if (start_ev) cudaEventDestroy(start_ev);
+  for (cudaEvent_t e : ready)
+    if (e) cudaEventDestroy(e);
   return res;
 }
 
@@ -1491,7 +1560,8 @@ extern "C" gp_ss_status gp_ss_loglik_noalloc(const gp_ss_model *m, const float *
   // every field the combination reads is written by the element pass first,
   // so nothing in the shared array needs clearing between calls
   if (o.tables(theta, n_sets, m->n_params, m->kinds[0], m->kinds[1], tabs, st) != cudaSuccess ||
-      o.elem(dm, theta, n_vch, theta_per_series, ef, ed, nullptr, tabs, nullptr, 0, nullptr, st) !=
+      o.elem(dm, theta, n_vch, theta_per_series, ef, ed, nullptr, tabs, nullptr, 0, nullptr, 0,
+             m->n_chunks, st) !=
           cudaSuccess)
     return GP_SS_ECUDA;
   if (o.scan(dm, n_out, theta_per_series, ef, ed, n_vch, nullptr, nullptr, loglik_out, 0,

@@ -442,15 +442,19 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
                                               double *__restrict__ ed, int *__restrict__ err,
                                               const float *__restrict__ tabs,
                                               float *__restrict__ pck, int ck,
-                                              float *__restrict__ dcache) {
+                                              float *__restrict__ dcache, int c_begin,
+                                              int c_count) {
   using F = float;
   constexpr int D = S::D;
   using L = ElemLayout<S>;
   extern __shared__ float4 smem_tab[];
-  const int vc = blockIdx.x * blockDim.x + threadIdx.x;
-  if (vc >= n_vch) return;
-  const int c = vc % M.n_chunks;
-  const int set = vc / M.n_chunks;
+  // chunks [c_begin, c_begin + c_count) of every parameter set (a multiple of
+  // 32 chunks per series keeps each warp in one series)
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= (n_vch / M.n_chunks) * c_count) return;
+  const int set = l / c_count;
+  const int c = c_begin + l % c_count;
+  const int vc = set * M.n_chunks + c;
   const int s = M.ch_series[c];
   const int row = per_series ? s : set;
   const int orow = per_series ? s : set * M.n_series + s;
@@ -1686,7 +1690,7 @@ struct OpTable {
   cudaError_t (*plain32)(const DevModel &, const float *, int, int, double *, int *, cudaStream_t);
   cudaError_t (*plain64)(const DevModel &, const float *, int, int, double *, int *, cudaStream_t);
   cudaError_t (*elem)(const DevModel &, const float *, int, int, float *, double *, int *,
-                      const float *, float *, int, float *, cudaStream_t);
+                      const float *, float *, int, float *, int, int, cudaStream_t);
   cudaError_t (*scan)(const DevModel &, int, int, const float *, const double *, int, float *,
                       float *, double *, int, int *, cudaStream_t);
   cudaError_t (*grad)(const DevModel &, const float *, int, int, const float *, const float *,
@@ -1721,19 +1725,21 @@ cudaError_t launch_plain(const DevModel &M, const float *theta, int n_out, int p
 template <class S>
 cudaError_t launch_elem(const DevModel &M, const float *theta, int n_vch, int per_series,
                         float *ef, double *ed, int *err, const float *tabs, float *pck, int ck,
-                        float *dcache, cudaStream_t st) {
-  if (n_vch <= 0) return cudaSuccess;
+                        float *dcache, int c_begin, int c_count, cudaStream_t st) {
+  if (n_vch <= 0 || c_count <= 0) return cudaSuccess;
+  if (c_begin < 0 || c_begin + c_count > M.n_chunks) return cudaErrorInvalidValue;
   if (pck && (ck < 2 || ck > 64 || (ck & 1))) return cudaErrorInvalidValue;
   const int bs = 128;
   const size_t smem = (size_t)(bs / 32) * S::NT * TAB_TERM * sizeof(float);
   // two launches: rows without an overdamped term (the lean body), then rows
   // with one; each skips the other's rows
-  const int nb = (n_vch + bs - 1) / bs;
+  const int64_t nt = (int64_t)(n_vch / M.n_chunks) * c_count;
+  const int nb = (int)((nt + bs - 1) / bs);
   k_elem<S, false><<<nb, bs, smem, st>>>(M, theta, n_vch, per_series, ef, ed, err, tabs, pck,
-                                         pck ? ck : 1, dcache);
+                                         pck ? ck : 1, dcache, c_begin, c_count);
   GPSS_COUNT_LAUNCH();
   k_elem<S, true><<<nb, bs, smem, st>>>(M, theta, n_vch, per_series, ef, ed, err, tabs, pck,
-                                        pck ? ck : 1, dcache);
+                                        pck ? ck : 1, dcache, c_begin, c_count);
   GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }

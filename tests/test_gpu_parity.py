@@ -243,6 +243,13 @@ def test_graph_and_host_paths_agree(gp):
     ll_h, g_h = m.loglik_grad_host(wl.theta, reupload_events=True)
     np.testing.assert_array_equal(ll.cpu().numpy(), ll_h)
     np.testing.assert_array_equal(g.cpu().numpy(), g_h)
+    # shared parameter sets: the event stream re-sent in series groups whose
+    # element passes start as each group arrives gives the same bits
+    th2 = th[:3]
+    ll_s, g_s = m.loglik_grad(th2, per_series=False)
+    ll_hs, g_hs = m.loglik_grad_host(wl.theta[:3], per_series=False, reupload_events=True)
+    np.testing.assert_array_equal(ll_s.cpu().numpy().ravel(), ll_hs.ravel())
+    np.testing.assert_array_equal(g_s.cpu().numpy().reshape(g_hs.shape), g_hs)
 
 
 def test_autograd_function(gp):
