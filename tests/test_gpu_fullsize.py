@@ -105,6 +105,43 @@ def test_c2_full_loglik(gp):
     _check_ll(ll[idx], ref, counts[idx])
 
 
+def test_c2i_full_instantaneous(gp):
+    # 4096 series of instantaneous measurements (22.2M): loglik + gradient in
+    # the bench's configuration (autotuned), sampled series against the
+    # oracle, every series against the FP64 plain filter
+    wl = _f32(synth.c2i())
+    m = gp.Model.from_workload(wl)
+    th = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
+    m.autotune(th, grad=True, reps=1)
+    ll, g = m.loglik_grad(th)
+    torch.cuda.synchronize()
+    assert m.last_error() == (-1, 0)
+    ll, g = ll.cpu().numpy(), g.cpu().numpy()
+    counts = np.diff(wl.offsets)
+    assert np.isfinite(ll).all() and np.isfinite(g).all()
+    ll64 = gp.Model.from_workload(wl, precision=64).loglik(th).cpu().numpy()
+    _check_ll(ll, ll64, counts)
+    idx = _sample(counts, 8)
+    ref_ll, ref_g = oracle.loglik_workload(wl, series_idx=idx, grad=True, processes=8)
+    assert np.all(np.abs(ll64[idx] - ref_ll) <= 1e-9 * np.abs(ref_ll))
+    _check_ll(ll[idx], ref_ll, counts[idx])
+    _check_grad(g[idx], ref_g)
+
+
+def test_c2p_product_loglik(gp):
+    # the product-kernel batch (1024 series of the c2p recipe): FP32 and FP64
+    # plain filters against each other everywhere, against the oracle sampled
+    wl = _f32(synth.c2p(n_series=1024))
+    th = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
+    ll = gp.Model.from_workload(wl).loglik(th).cpu().numpy()
+    ll64 = gp.Model.from_workload(wl, precision=64).loglik(th).cpu().numpy()
+    counts = np.diff(wl.offsets)
+    _check_ll(ll, ll64, counts)
+    idx = _sample(counts, 6)
+    ref = oracle.loglik_workload(wl, series_idx=idx, processes=6)
+    assert np.all(np.abs(ll64[idx] - ref) <= 1e-9 * np.abs(ref))
+
+
 def test_c3_full_scan(gp):
     wl = _f32(synth.c3())
     m = gp.Model.from_workload(wl)
