@@ -366,7 +366,8 @@ def run_ours(args):
         for _ in range(k2):
             model.loglik_grad_host(th_host, reupload_events=True)
         el = (time.perf_counter() - t1) / k2
-        h2d = model.info["n_events"] * 5 + wl.n_meas * 16 + th_host.nbytes
+        # gaps (4 B) and tags (1 B) per event, (y, r0, w) per measurement, theta
+        h2d = model.info["n_events"] * 5 + wl.n_meas * 12 + th_host.nbytes
         d2h = n_out * 8 + n_out * model.n_params * 4
         e2e = {"value": total_meas / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": el * 1e3}

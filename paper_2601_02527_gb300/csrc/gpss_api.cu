@@ -93,6 +93,13 @@ __global__ void k_exposure_grad(int n_rows, int n_series, const int64_t *__restr
   out[2 * idx + 1] = gt(ke) - wpart;
 }
 
+// Measurement records (y, r0, w) -> the float4 layout the chunk kernels read.
+__global__ void k_pack_meas(const float *__restrict__ in3, float4 *__restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = make_float4(in3[3 * i], in3[3 * i + 1], in3[3 * i + 2], 0.f);
+}
+
 __global__ void k_gather_cond(int n_rows, int n_series, const int64_t *__restrict__ ev_off,
                               const int64_t *__restrict__ meas_off, const int2 *__restrict__ mev,
                               int64_t n_meas, int64_t n_events, const float2 *__restrict__ cond,
@@ -156,6 +163,7 @@ struct gp_ss_model {
   float *h_dt = nullptr;  // host copies of the event stream (pinned when possible)
   uint8_t *h_tag = nullptr;
   float4 *h_meas = nullptr;
+  float *h_meas3 = nullptr;  // pinned (y, r0, w) per measurement: the host-buffer call sends these
   bool pinned = false;
   // device event stream
   int64_t *d_ev_off = nullptr, *d_meas_off = nullptr;
@@ -255,6 +263,8 @@ void free_model_buffers(gp_ss_model *m) {
     cudaMemPoolDestroy(m->pool);
     m->pool = nullptr;
   }
+  if (m->h_meas3) cudaFreeHost(m->h_meas3);
+  m->h_meas3 = nullptr;
   void *hst[] = {m->h_dt, m->h_tag, m->h_meas};
   for (void *p : hst)
     if (p) {
@@ -297,6 +307,10 @@ void build_series(int64_t a, int64_t b, int64_t e0, const double *ts, const doub
                   float4 *meas, double *dt64, double *meas64, int2 *mev, double *tev,
                   SeriesOut *out) {
   const int64_t n = b - a;
+  if (n == 0) {  // an empty series asks for no integral state
+    out->n_slots = 0;
+    return;
+  }
   std::vector<int> slot(n);
   int n_slots = 1;
   int64_t n_inst = 0;
@@ -1002,6 +1016,18 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   if (!st) st = dev_upload(&m->d_dt, m->h_dt, nE);
   if (!st) st = dev_upload(&m->d_tag, m->h_tag, nE);
   if (!st) st = dev_upload(&m->d_meas, m->h_meas, nM);
+  // the 12-byte records the host-buffer call sends (pinned hosts only)
+  if (!st && m->pinned && cudaMallocHost((void **)&m->h_meas3, (size_t)nM * 3 * sizeof(float)) ==
+                              cudaSuccess) {
+    for (int64_t i = 0; i < N; ++i) {
+      m->h_meas3[3 * i] = m->h_meas[i].x;
+      m->h_meas3[3 * i + 1] = m->h_meas[i].y;
+      m->h_meas3[3 * i + 2] = m->h_meas[i].z;
+    }
+  } else {
+    m->h_meas3 = nullptr;
+    cudaGetLastError();
+  }
   if (!st) st = dev_upload(&m->d_mev, mev.data(), mev.size());
   if (!st && o.precision == 64) {
     st = dev_upload(&m->d_dt64, dt64.data(), nE);
@@ -1262,7 +1288,8 @@ gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *m, const float *theta_hos
   int c0[kGroups + 1] = {};
   ElemSlices slices{0, c0, ready};
   const bool pipe = reupload_events && !m->product && m->precision == 32 && m->n_series >= 2 &&
-                    m->ch_first.size() == (size_t)m->n_series + 1;
+                    m->ch_first.size() == (size_t)m->n_series + 1 && m->h_meas3;
+  float *d_meas3 = nullptr;
   if (pipe) {
     std::vector<int> sb{0};
     for (int g = 1; g < kGroups; ++g) {
@@ -1273,24 +1300,36 @@ gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *m, const float *theta_hos
     }
     sb.push_back(m->n_series);
     slices.n = (int)sb.size() - 1;
+    // measurement records go up as 12-byte (y, r0, w) and are widened to the
+    // kernels' float4 on the device (a quarter fewer bytes than the float4s)
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) ||
         cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming) ||
-        cudaEventRecord(start_ev, st) || cudaStreamWaitEvent(cs, start_ev, 0))
+        cudaEventRecord(start_ev, st) || cudaStreamWaitEvent(cs, start_ev, 0) ||
+        scratch_alloc(m, (void **)&d_meas3, (size_t)std::max<int64_t>(m->n_meas, 1) * 3 *
+                                                sizeof(float), cs))
       res = GP_SS_ECUDA;
     for (int g = 0; g < slices.n && !res; ++g) {
       const int64_t e0 = m->ev_off[sb[g]], e1 = m->ev_off[sb[g + 1]];
       const int64_t q0 = m->meas_off[sb[g]], q1 = m->meas_off[sb[g + 1]];
       c0[g] = m->ch_first[sb[g]];
       if (cudaEventCreateWithFlags(&ready[g], cudaEventDisableTiming) ||
+          cudaMemcpyAsync(d_meas3 + 3 * q0, m->h_meas3 + 3 * q0, (size_t)(q1 - q0) * 3 * sizeof(float),
+                          cudaMemcpyHostToDevice, cs) ||
           cudaMemcpyAsync(m->d_dt + e0, m->h_dt + e0, (size_t)(e1 - e0) * sizeof(float),
                           cudaMemcpyHostToDevice, cs) ||
           cudaMemcpyAsync(m->d_tag + e0, m->h_tag + e0, (size_t)(e1 - e0),
-                          cudaMemcpyHostToDevice, cs) ||
-          cudaMemcpyAsync(m->d_meas + q0, m->h_meas + q0, (size_t)(q1 - q0) * sizeof(float4),
-                          cudaMemcpyHostToDevice, cs) ||
-          cudaEventRecord(ready[g], cs))
+                          cudaMemcpyHostToDevice, cs)) {
         res = GP_SS_ECUDA;
+        break;
+      }
+      if (q1 > q0) {
+        gpss::k_pack_meas<<<(unsigned)((q1 - q0 + 255) / 256), 256, 0, cs>>>(
+            d_meas3 + 3 * q0, m->d_meas + q0, q1 - q0);
+        GPSS_COUNT_LAUNCH();
+      }
+      if (cudaGetLastError() != cudaSuccess || cudaEventRecord(ready[g], cs)) res = GP_SS_ECUDA;
     }
+    if (d_meas3) cudaFreeAsync(d_meas3, cs);
     c0[slices.n] = m->ch_first[m->n_series];
   } else if (reupload_events) {
     if (cudaMemcpyAsync(m->d_dt, m->h_dt, (size_t)m->n_events * sizeof(float),

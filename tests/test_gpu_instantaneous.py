@@ -149,3 +149,28 @@ def test_single_term_and_mixing_rejected(gp):
     te[::2] += 0.1  # half of them exposures: not compiled
     with pytest.raises(Exception):
         gp.Model(wl.terms, wl.offsets, t, te, wl.y, wl.yerr, None, layout=0)
+
+
+def test_edge_cases(gp):
+    rng = np.random.default_rng(93)
+    series = []
+    series.append(np.array([3.0]))                                   # single measurement
+    t = np.cumsum(rng.exponential(1.0, 50))
+    t[10:14] = t[10]                                                 # repeated times
+    t[30:] += 500.0                                                  # one very long gap
+    series.append(np.sort(t))
+    series.append(np.zeros(0))                                       # empty series
+    series.append(np.cumsum(rng.exponential(0.3, 333)))              # ragged length
+    theta = np.array([[1.0, 2 * math.pi / 10, 3.0, 0.1]] * len(series))
+    wl = synth._finish("iedge", [SHO], 0, [(s, s.copy()) for s in series], theta, True, rng)
+    wl.theta = wl.theta.astype(np.float32).astype(np.float64)
+    keep = [0, 1, 3]
+    ref_ll, ref_g = oracle.loglik_workload(wl.subset(keep), grad=True)
+    for chunk in (0, 7, 64):
+        m = gp.Model.from_workload(wl, chunk_len=chunk)
+        assert m.info["n_slots"] == 0  # the empty series asks for no integral state
+        ll, g = m.loglik_grad(_dev(wl.theta))
+        ll, g = ll.cpu().numpy(), g.cpu().numpy()
+        assert ll[2] == 0.0 and np.all(g[2] == 0)
+        _check_ll(ll[keep], ref_ll, np.diff(wl.offsets)[keep])
+        _check_rows(g[keep], ref_g)

@@ -91,3 +91,17 @@ def test_unsupported_calls(gp):
     t = wl.t_start
     with pytest.raises(Exception):  # exposure averages with a product kernel
         gp.Model(wl.terms, wl.offsets, t, t + 0.1, wl.y, wl.yerr, None, layout=0)
+
+
+def test_edge_cases(gp):
+    rng = np.random.default_rng(112)
+    t = np.cumsum(rng.exponential(1.0, 80))
+    t[5:9] = t[5]          # repeated times
+    t[40:] += 300.0        # one very long gap
+    series = [np.array([1.5]), np.sort(t)]
+    theta = np.array([[1.2, 0.2, 1.5, 2.0, 8.0, 0.1]] * 2)
+    wl = _f32(synth._finish("pedge", [PROD], 0, [(s, s.copy()) for s in series], theta, True, rng))
+    ref = oracle.loglik_workload(wl)
+    for precision in (32, 64):
+        ll = gp.Model.from_workload(wl, precision=precision).loglik(_dev(wl.theta)).cpu().numpy()
+        _check(ll, ref, np.diff(wl.offsets), rel=1e-9 if precision == 64 else None)
