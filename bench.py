@@ -467,9 +467,10 @@ def run_accuracy(args):
             out["fp64_vs_oracle_max_rel"] = float(np.max(np.abs(l64 - ref) / np.abs(ref)))
         else:
             m = gp.Model.from_workload(wl)
-            grad = name in ("c4", "c5")
-            tuned = m.autotune(th, per_series=per, grad=grad, reps=1)
-            out["autotuned"] = {k: tuned[k] for k in ("schedule", "chunk_len", "ckpt_interval")}
+            grad = name in ("c4", "c5", "c2i")
+            if name != "c2p":  # the product path has one schedule
+                tuned = m.autotune(th, per_series=per, grad=grad, reps=1)
+                out["autotuned"] = {k: tuned[k] for k in ("schedule", "chunk_len", "ckpt_interval")}
             l32 = (m.loglik_grad(th, per_series=per)[0] if grad else
                    m.loglik(th, per_series=per)).cpu().numpy()
             nrow = np.tile(counts, len(l32) // len(counts))
@@ -505,7 +506,7 @@ def main():
     ap.add_argument("--no-product", action="store_true")
     ap.add_argument("--accuracy", action="store_true",
                     help="print FP32-vs-FP64 errors per workload instead of timing")
-    ap.add_argument("--accuracy-workloads", default="c1,c2,c3,c4,c5")
+    ap.add_argument("--accuracy-workloads", default="c1,c2,c3,c4,c5,c2i,c2p")
     args = ap.parse_args()
     if args.accuracy:
         run_accuracy(args)
