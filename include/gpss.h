@@ -71,8 +71,9 @@ typedef enum {
                                 unit-variance SHO factors (Appendix C.2, Kronecker state of
                                 dimension 4).  First term only, at most one plain term after
                                 it, instantaneous measurements only; gp_ss_loglik (the plain
-                                per-series filter, FP32 or FP64) only, other calls return
-                                GP_SS_EUNSUPPORTED. */
+                                per-series filter, FP32 or FP64) and gp_ss_loglik_grad
+                                (hyperparameter gradient by forward-mode tangents, FP32);
+                                other calls return GP_SS_EUNSUPPORTED. */
 } gp_ss_term;
 
 typedef struct {

@@ -619,8 +619,15 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
   const gpss::DevModel dm = dev_view(m);
   const OpTable &o = m->ops;
   if (m->product) {
-    // product kernels: the plain filters (log-likelihood only)
-    if (grad || dexp || cond_out || pred) return GP_SS_EUNSUPPORTED;
+    // product kernels: the plain filters; the hyperparameter gradient by
+    // forward-mode tangents (FP32)
+    if (dexp || cond_out || pred) return GP_SS_EUNSUPPORTED;
+    if (grad) {
+      if (m->precision == 64) return GP_SS_EUNSUPPORTED;
+      PhaseTimer pt(m, st, 2);
+      GPSS_CK(o.prod_grad(dm, theta, n_out, per_series, ll, grad, m->d_err, st));
+      return GP_SS_OK;
+    }
     if (m->precision == 64 && !m->d_dt64) return GP_SS_EINVAL;
     PhaseTimer pt(m, st, 4);
     GPSS_CK((m->precision == 64 ? o.plain64 : o.plain32)(dm, theta, n_out, per_series, ll,

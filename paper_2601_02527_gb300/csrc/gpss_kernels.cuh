@@ -1708,6 +1708,9 @@ struct OpTable {
                         const float *, float *, double *, int *, cudaStream_t);
   cudaError_t (*disc)(const float *, const float *, int, int, const float *, int, float *, float *,
                       cudaStream_t);
+  // product models: log-likelihood and hyperparameter gradient (else null)
+  cudaError_t (*prod_grad)(const DevModel &, const float *, int, int, double *, float *, int *,
+                           cudaStream_t);
 };
 
 constexpr int GRAD_BS = 64;
@@ -1901,6 +1904,7 @@ OpTable make_ops() {
   o.warp_combine = &launch_warp_combine<S>;
   o.warp_scratch = &warp_scratch_count<S>;
   o.NT = S::NT;
+  o.prod_grad = nullptr;
   return o;
 }
 

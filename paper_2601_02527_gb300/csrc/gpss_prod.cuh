@@ -10,7 +10,8 @@
 // added (state 4 + 2).  The state dimension grows as the product of the
 // factors' (Section C.2), so this path runs the sequential filter with one
 // thread per series and the full covariance in registers: log-likelihood
-// only, FP32 (FP64 sums) or FP64.
+// in FP32 (FP64 sums) or FP64, and its hyperparameter gradient by forward-mode
+// tangents (one thread per series and parameter).
 #pragma once
 
 #include "gpss_kernels.cuh"
@@ -18,22 +19,24 @@
 namespace gpss {
 
 // The 2 x 2 transition and process noise of one oscillator factor of
-// variance var from its six per-step scalars (Eqs. sho_phi, Q).
-template <class F>
+// variance var from its six per-step scalars (Eqs. sho_phi, Q).  T is F, or
+// Dual2<F> carrying one parameter tangent in .da (forward-mode gradient).
+template <class T>
 struct Osc2 {
-  F p[2][2], q[2][2];
+  T p[2][2], q[2][2];
 };
 
-template <class F>
-GPSS_D Osc2<F> osc2(F dt, F w0, F Q, F var) {
-  const F a = w0 / (F(2) * Q);
-  const F beta = (Q == F(0.5)) ? F(0) : w0 * w0 * (F(1) - F(1) / (F(4) * Q * Q));
-  const Disc<F> d = discretize<F, F, true>(dt, a, beta);
-  const F qc = F(2) * w0 * w0 * w0 * var / Q;
-  Osc2<F> o;
+template <class T, class F>
+GPSS_D Osc2<T> osc2(F dt, T w0, T Q, T var) {
+  const T a = w0 / (F(2) * Q);
+  const T beta = (val(Q) == F(0.5)) ? cst<T>(F(0))
+                                    : w0 * w0 * (F(1) - cst<T>(F(1)) / (F(4) * Q * Q));
+  const Disc<T> d = discretize<T, F, true>(dt, a, beta);
+  const T qc = F(2) * w0 * w0 * w0 * var / Q;
+  Osc2<T> o;
   o.p[0][0] = d.fp + F(2) * a * d.f;
   o.p[0][1] = d.f;
-  o.p[1][0] = -w0 * w0 * d.f;
+  o.p[1][0] = -(w0 * w0 * d.f);
   o.p[1][1] = d.fp;
   o.q[0][0] = qc * d.Iff;
   o.q[0][1] = o.q[1][0] = qc * d.f * d.f * F(0.5);
@@ -98,8 +101,8 @@ __global__ void __launch_bounds__(128) k_plain_prod(DevModel M, const float *__r
     F y, r0, w;
     load_meas<F>(M, mi, y, r0, w);
     ++mi;
-    const Osc2<F> A = osc2<F>(dt, wa, qa, F(1));
-    const Osc2<F> B = osc2<F>(dt, wb, qb, var);
+    const Osc2<F> A = osc2<F, F>(dt, wa, qa, F(1));
+    const Osc2<F> B = osc2<F, F>(dt, wb, qb, var);
     // Phi (block-diagonal: the product's Kronecker block, then the plain term)
     F Phi[D][D], Qd[D][D];
 #pragma unroll
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(128) k_plain_prod(DevModel M, const float *__r
                        (rb == cb ? A.q[ra][ca] * Pb[rb] : F(0)) - A.q[ra][ca] * B.q[rb][cb];
           }
     if constexpr (SUM) {
-      const Osc2<F> C = osc2<F>(dt, wc, qcq, sc * sc);
+      const Osc2<F> C = osc2<F, F>(dt, wc, qcq, sc * sc);
 #pragma unroll
       for (int r = 0; r < 2; ++r)
 #pragma unroll
@@ -183,6 +186,175 @@ __global__ void __launch_bounds__(128) k_plain_prod(DevModel M, const float *__r
   if (bad) flag_error(err, v, 7);
 }
 
+// Forward-mode gradient of the product filter: one thread per (output row,
+// parameter i) runs the filter in Dual2<float> with d/d theta_i in .da and
+// accumulates d loglik / d theta_i = -1/2 sum (dS/S + 2 v dv / S - v^2 dS / S^2)
+// in FP64; the i = 0 thread also writes the log-likelihood.
+template <class T>
+GPSS_D T seed(float v, bool on);
+template <>
+GPSS_D Dual2<float> seed<Dual2<float>>(float v, bool on) { return mk(v, on ? 1.f : 0.f, 0.f); }
+
+template <bool SUM>
+__global__ void __launch_bounds__(64) k_prod_grad(DevModel M, const float *__restrict__ theta,
+                                                  int n_out, int per_series,
+                                                  double *__restrict__ ll_out,
+                                                  float *__restrict__ grad_out,
+                                                  int *__restrict__ err) {
+  using F = float;
+  using T = Dual2<F>;
+  constexpr int D = SUM ? 6 : 4;
+  const int np = M.n_params;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)n_out * np) return;
+  const int v = (int)(tid / np), ip = (int)(tid % np);
+  const int s = per_series ? v : v % M.n_series;
+  const int row = per_series ? v : v / M.n_series;
+  const float *th = theta + (size_t)row * np;
+  auto par = [&](int i) { return seed<T>(th[i], i == ip); };
+  const T sig = par(0), wa = par(1), qa = par(2), wb = par(3), qb = par(4);
+  const T var = sig * sig;
+  const T one = cst<T>(F(1));
+  const T Pa[2] = {one, wa * wa}, Pb[2] = {var, var * wb * wb};
+  T sc = cst<T>(F(0)), wc = one, qcq = cst<T>(F(0.5));
+  int j = 5;
+  if constexpr (SUM) {
+    sc = par(5);
+    if (M.kinds[1] == 1) {
+      wc = par(6);
+      qcq = par(7);
+      j = 8;
+    } else {
+      wc = cst<T>(F(1.7320508075688772)) / par(6);
+      j = 7;
+    }
+  }
+  const T sw = par(j);
+  const T s2 = sw * sw;
+  T m[D], P[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    m[i] = cst<T>(F(0));
+#pragma unroll
+    for (int c = 0; c < D; ++c) P[i][c] = cst<T>(F(0));
+  }
+#pragma unroll
+  for (int ra = 0; ra < 2; ++ra)
+#pragma unroll
+    for (int rb = 0; rb < 2; ++rb) P[2 * ra + rb][2 * ra + rb] = Pa[ra] * Pb[rb];
+  if constexpr (SUM) {
+    P[4][4] = sc * sc;
+    P[5][5] = sc * sc * wc * wc;
+  }
+  double sum_ll = 0.0, sum_d = 0.0;
+  int64_t n_end = 0;
+  bool bad = false;
+  int64_t mi = M.meas_off[s];
+  const int64_t e1 = M.ev_off[s + 1];
+  for (int64_t k = M.ev_off[s]; k < e1; ++k) {
+    const F dt = load_dt<F>(M, k);
+    F y, r0, w;
+    load_meas<F>(M, mi, y, r0, w);
+    ++mi;
+    const Osc2<T> A = osc2<T, F>(dt, wa, qa, one);
+    const Osc2<T> B = osc2<T, F>(dt, wb, qb, var);
+    T Phi[D][D], Qd[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) Phi[r][c] = Qd[r][c] = cst<T>(F(0));
+#pragma unroll
+    for (int ra = 0; ra < 2; ++ra)
+#pragma unroll
+      for (int rb = 0; rb < 2; ++rb)
+#pragma unroll
+        for (int ca = 0; ca < 2; ++ca)
+#pragma unroll
+          for (int cb = 0; cb < 2; ++cb) {
+            const int r = 2 * ra + rb, c = 2 * ca + cb;
+            Phi[r][c] = A.p[ra][ca] * B.p[rb][cb];
+            T q = -(A.q[ra][ca] * B.q[rb][cb]);  // Eq. product_Q
+            if (ra == ca) q = q + Pa[ra] * B.q[rb][cb];
+            if (rb == cb) q = q + A.q[ra][ca] * Pb[rb];
+            Qd[r][c] = q;
+          }
+    if constexpr (SUM) {
+      const Osc2<T> C = osc2<T, F>(dt, wc, qcq, sc * sc);
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          Phi[4 + r][4 + c] = C.p[r][c];
+          Qd[4 + r][4 + c] = C.q[r][c];
+        }
+    }
+    T mt[D], Tm[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      T acc = cst<T>(F(0));
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc = acc + Phi[r][c] * m[c];
+      mt[r] = acc;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        T a2 = cst<T>(F(0));
+#pragma unroll
+        for (int e = 0; e < D; ++e) a2 = a2 + Phi[r][e] * P[e][c];
+        Tm[r][c] = a2;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      m[r] = mt[r];
+#pragma unroll
+      for (int c = r; c < D; ++c) {
+        T a2 = Qd[r][c];
+#pragma unroll
+        for (int e = 0; e < D; ++e) a2 = a2 + Tm[r][e] * Phi[c][e];
+        P[r][c] = a2;
+        P[c][r] = a2;
+      }
+    }
+    T u[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) u[r] = SUM ? P[r][0] + P[r][4] : P[r][0];
+    const T hu = SUM ? u[0] + u[4] : u[0];
+    const T hm = SUM ? m[0] + m[4] : m[0];
+    const T Sv = hu + s2 + r0;
+    const T vv = y - hm;
+    bad |= !(Sv.v > F(0));
+    const T iS = one / Sv;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      m[r] = m[r] + u[r] * vv * iS;
+#pragma unroll
+      for (int c = 0; c < D; ++c) P[r][c] = P[r][c] - u[r] * u[c] * iS;
+    }
+    const double S = Sv.v, dS = Sv.da, e = vv.v, de = vv.da;
+    sum_ll += log(S) + e * e / S;
+    sum_d += dS / S + 2.0 * e * de / S - e * e * dS / (S * S);
+    ++n_end;
+  }
+  const double ll = -0.5 * ((double)n_end * LOG_2PI + sum_ll);
+  const double g = -0.5 * sum_d;
+  bad |= !isfinite(ll) || !isfinite(g);
+  grad_out[(size_t)v * np + ip] = (float)g;
+  if (ip == 0) ll_out[v] = ll;
+  if (bad) flag_error(err, v, 7);
+}
+
+template <bool SUM>
+cudaError_t launch_prod_grad(const DevModel &M, const float *theta, int n_out, int per_series,
+                             double *ll, float *grad, int *err, cudaStream_t st) {
+  if (n_out <= 0) return cudaSuccess;
+  const int bs = 64;
+  const int64_t nt = (int64_t)n_out * M.n_params;
+  k_prod_grad<SUM><<<(unsigned)((nt + bs - 1) / bs), bs, 0, st>>>(M, theta, n_out, per_series, ll,
+                                                                 grad, err);
+  GPSS_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
 template <bool SUM, class F>
 cudaError_t launch_plain_prod(const DevModel &M, const float *theta, int n_out, int per_series,
                               double *ll, int *err, cudaStream_t st) {
@@ -202,6 +374,7 @@ OpTable make_prod_ops() {
   o.NT = SUM ? 2 : 1;
   o.plain32 = &launch_plain_prod<SUM, float>;
   o.plain64 = &launch_plain_prod<SUM, double>;
+  o.prod_grad = &launch_prod_grad<SUM>;
   return o;
 }
 
