@@ -34,11 +34,12 @@
  *    for GP_SS_TERM_MATERN32 or (sigma, omega_a, Q_a, omega_b, Q_b) for
  *    GP_SS_TERM_SHO_PRODUCT, in the order of the kernel spec, then the
  *    white-noise sd s.  n_params = 3*#SHO + 2*#Matern + 5*#product + 1.
+ *    Non-finite or non-positive hyperparameters surface as GP_SS_ENUMERIC
+ *    (gp_ss_last_error_series).
  *  - A measurement with t_end == t_start is instantaneous: it observes the
  *    latent f(t) itself (Section 2).  A model holds either instantaneous
  *    measurements only or exposure averages only (GP_SS_EUNSUPPORTED
- *    otherwise); instantaneous models have no integral states.  Non-finite or
- *    non-positive values surface as GP_SS_ENUMERIC (gp_ss_last_error_series).
+ *    otherwise); instantaneous models have no integral states.
  */
 #ifndef GPSS_H
 #define GPSS_H
@@ -53,7 +54,7 @@ typedef struct gp_ss_model gp_ss_model; /* opaque; immutable after build */
 
 typedef enum {
   GP_SS_OK = 0,
-  GP_SS_EINVAL = 1,        /* bad argument: non-positive or non-finite exposure, NULL pointer, ... */
+  GP_SS_EINVAL = 1,        /* bad argument: negative or non-finite exposure length, NULL pointer, ... */
   GP_SS_EUNSORTED = 2,     /* series offsets not non-decreasing */
   GP_SS_ESELFOVERLAP = 3,  /* one instrument's exposures overlap each other */
   GP_SS_EUNSUPPORTED = 4,  /* model shape not compiled (too many terms/slots) */
