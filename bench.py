@@ -360,8 +360,9 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         th_host = wl.theta.astype(np.float32)
-        model.loglik_grad_host(th_host, reupload_events=True)
-        k2 = max(2, min(args.steps, 5))
+        for _ in range(3):
+            model.loglik_grad_host(th_host, reupload_events=True)
+        k2 = max(2, min(args.steps, 20))
         t1 = time.perf_counter()
         for _ in range(k2):
             model.loglik_grad_host(th_host, reupload_events=True)
