@@ -576,14 +576,18 @@ GPSS_HD void econ_map(EconMap &E) {
 // Table coefficient k (in t) from the Taylor coefficients g[j][n] (all n):
 // e_k = sum_n m[k][n] T^(n-k) g_n.
 template <class T>
-GPSS_HD T econ_apply(const EconMap &E, int k, double rng, const T *g, int stride) {
+GPSS_HD T econ_apply(const double (*m)[TAB_NTAY], int k, double rng, const T *g, int stride) {
   T acc = g[0] * 0.0;
   double p = 1.0;  // T^(n-k)
   for (int n = k; n < TAB_NTAY; ++n) {
-    acc = acc + g[(size_t)n * stride] * (E.m[k][n] * p);
+    acc = acc + g[(size_t)n * stride] * (m[k][n] * p);
     p *= rng;
   }
   return acc;
+}
+template <class T>
+GPSS_HD T econ_apply(const EconMap &E, int k, double rng, const T *g, int stride) {
+  return econ_apply<T>(E.m, k, rng, g, stride);
 }
 
 // Economised table coefficients e[j][k], k < TAB_NC, on [0, T] (FP64).

@@ -302,6 +302,14 @@ __global__ void __launch_bounds__(32 * TABLE_WARPS) k_tables(const float *__rest
   constexpr int NCF = TAB_NCF;  // c_0 .. c_NCF
   __shared__ DD sc[TABLE_WARPS][NCF + 1], se[TABLE_WARPS][NCF + 1], sf[TABLE_WARPS][NCF + 1];
   __shared__ DD sg[TABLE_WARPS][6][TAB_NTAY];
+  // the economisation map and reciprocals in shared memory: the lanes index
+  // them with different k, which the parameter (constant) bank would serialise
+  __shared__ double sm_m[TAB_NC][TAB_NTAY];
+  __shared__ double sm_rcp[2 * TAB_NTAY + 8];
+  for (int i = threadIdx.x; i < TAB_NC * TAB_NTAY; i += blockDim.x)
+    sm_m[i / TAB_NTAY][i % TAB_NTAY] = E.m[i / TAB_NTAY][i % TAB_NTAY];
+  for (int i = threadIdx.x; i < 2 * TAB_NTAY + 8; i += blockDim.x) sm_rcp[i] = E.rcp[i];
+  __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rt = blockIdx.x * TABLE_WARPS + w;
   if (rt >= n_rows * NT) return;  // whole warps leave together
@@ -311,17 +319,17 @@ __global__ void __launch_bounds__(32 * TABLE_WARPS) k_tables(const float *__rest
   double s2;
   load_terms<NT, double>(theta + (size_t)row * n_params, kinds, tc, s2);
   const DD a = mk(tc[t].a, 1.0, 0.0), beta = mk(tc[t].beta, 0.0, 1.0);
-  if (lane == 0) taylor_c<DD>(a, beta, E.rcp, &sc[w][0]);
+  if (lane == 0) taylor_c<DD>(a, beta, sm_rcp, &sc[w][0]);
   __syncwarp();
   for (int n = lane; n <= NCF; n += 32) {
     const DD c = sc[w][n];
-    se[w][n] = c * E.rcp[n + 1];
+    se[w][n] = c * sm_rcp[n + 1];
     sf[w][n] = c * (double)n;
   }
   __syncwarp();
   if (lane < TAB_NTAY) {
     DD g[6];
-    taylor_coeff_pre<DD>(&sc[w][0], &se[w][0], &sf[w][0], E.rcp, lane, g);
+    taylor_coeff_pre<DD>(&sc[w][0], &se[w][0], &sf[w][0], sm_rcp, lane, g);
 #pragma unroll
     for (int j = 0; j < 6; ++j) sg[w][j][lane] = g[j];
   }
@@ -330,7 +338,7 @@ __global__ void __launch_bounds__(32 * TABLE_WARPS) k_tables(const float *__rest
   float *base = tab + (size_t)rt * TAB_NC * TAB_W;
   for (int o = lane; o < 6 * TAB_NC; o += 32) {
     const int j = o / TAB_NC, k = o % TAB_NC;
-    const DD e = econ_apply<DD>(E, k, rng, &sg[w][j][0], 1);
+    const DD e = econ_apply<DD>(sm_m, k, rng, &sg[w][j][0], 1);
     float *r = base + (size_t)k * TAB_W;
     r[j] = (float)e.v;
     r[8 + j] = (float)e.da;
