@@ -73,6 +73,11 @@ def test_host_validation_without_gpu(lib):
     assert _build(lib, [0.0, 0.1, 0.2, 0.3], [5.0, 5.0, 5.0, 5.0]) == 4
     # more than two terms
     assert _build(lib, [0.0], [1.0], terms=(1, 1, 1)) == 4
+    # a product term: compiled first only, and on instantaneous measurements only
+    assert _build(lib, [0.0, 1.0], [0.0, 1.0], terms=(1, 3)) == 4
+    assert _build(lib, [0.0, 1.0], [0.5, 1.5], terms=(3,)) == 4
+    # an unknown term kind
+    assert _build(lib, [0.0], [1.0], terms=(4,)) == 1
     # option values outside their ranges
     for bad in (gp._Options(32, 0, 0, 0, 12, 0, 0, 0), gp._Options(32, 0, 0, 0, 0, 0, 0, 2),
                 gp._Options(16, 0, 0, 0, 0, 0, 0, 0), gp._Options(32, 4, 0, 0, 0, 0, 0, 0),
