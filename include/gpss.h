@@ -207,7 +207,11 @@ gp_ss_status gp_ss_loglik_grad_batched(const gp_ss_model *model, const float *th
 /* Host-buffer variant of gp_ss_loglik_grad for end-to-end use: copies theta
  * (host f32) to the device, optionally re-uploads the model's event stream
  * from its pinned host copy (reupload_events != 0), computes, and copies the
- * results back into host buffers before returning (synchronous). */
+ * results back into host buffers before returning (synchronous).  The
+ * re-upload goes in series groups on an internal copy stream (it first waits
+ * for the work already queued on cuda_stream), each group's element pass
+ * starting once its events are in; it rewrites the model's device copy, so
+ * it must not run concurrently with other calls on the same model. */
 gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *model, const float *theta_host,
                                     int n_sets, int theta_per_series, double *loglik_host,
                                     float *grad_host, int reupload_events, void *cuda_stream);
