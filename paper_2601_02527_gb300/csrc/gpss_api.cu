@@ -629,10 +629,13 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       return GP_SS_OK;
     }
     if (m->precision == 64 && !m->d_dt64) return GP_SS_EINVAL;
-    PhaseTimer pt(m, st, 4);
-    GPSS_CK((m->precision == 64 ? o.plain64 : o.plain32)(dm, theta, n_out, per_series, ll,
-                                                         m->d_err, st));
-    return GP_SS_OK;
+    if (m->precision == 64 || m->schedule == 3) {
+      PhaseTimer pt(m, st, 4);
+      GPSS_CK((m->precision == 64 ? o.plain64 : o.plain32)(dm, theta, n_out, per_series, ll,
+                                                           m->d_err, st));
+      return GP_SS_OK;
+    }
+    // else the chunked log-likelihood below (product elements, shared combination)
   }
   if (m->precision == 64) {
     if (grad) return GP_SS_EUNSUPPORTED;

@@ -14,6 +14,8 @@
 // tangents (one thread per series and parameter).
 #pragma once
 
+#include <type_traits>
+
 #include "gpss_kernels.cuh"
 
 namespace gpss {
@@ -365,16 +367,238 @@ cudaError_t launch_plain_prod(const DevModel &M, const float *theta, int n_out, 
   return cudaGetLastError();
 }
 
-// Operation table of a product model: the plain filters only.
+// Chunk elements of a product model (the parallel-in-time log-likelihood,
+// Section 3.2.5 with the SG21 elements): as k_elem, with the dense
+// Kronecker-structured transition and noise of the product (and the plain
+// term).  The combination, the chunk log-likelihoods and the per-series sums
+// depend on the state dimension only, so the kernels of a shape with the
+// same dimension (ES) serve them.
+template <bool SUM, class ES>
+__global__ void __launch_bounds__(128) k_elem_prod(DevModel M, const float *__restrict__ theta,
+                                                   int n_vch, int per_series,
+                                                   float *__restrict__ ef, double *__restrict__ ed,
+                                                   int *__restrict__ err, int c_begin,
+                                                   int c_count) {
+  using F = float;
+  constexpr int D = SUM ? 6 : 4;
+  static_assert(ES::D == D, "element shape of the product state");
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= (n_vch / M.n_chunks) * c_count) return;
+  const int set = l / c_count;
+  const int c = c_begin + l % c_count;
+  const int vc = set * M.n_chunks + c;
+  const int s = M.ch_series[c];
+  const int row = per_series ? s : set;
+  const int orow = per_series ? s : set * M.n_series + s;
+  const float *th = theta + (size_t)row * M.n_params;
+  const F sig = th[0], wa = th[1], qa = th[2], wb = th[3], qb = th[4];
+  const F var = sig * sig;
+  const F Pa[2] = {F(1), wa * wa}, Pb[2] = {var, var * wb * wb};
+  F sc = F(0), wc = F(1), qcq = F(0.5);
+  int j = 5;
+  if constexpr (SUM) {
+    sc = th[5];
+    if (M.kinds[1] == 1) {
+      wc = th[6];
+      qcq = th[7];
+      j = 8;
+    } else {
+      wc = F(1.7320508075688772) / F(th[6]);
+      j = 7;
+    }
+  }
+  const F s2 = F(th[j]) * F(th[j]);
+  const bool first = M.ch_flags[c] & 1;
+  // element: A (D x D), b, C (full here, packed on store), eta, J (full)
+  F A[D][D], b[D], C[D][D], eta[D], J[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    b[i] = F(0);
+    eta[i] = F(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      A[i][k] = (!first && i == k) ? F(1) : F(0);
+      C[i][k] = F(0);
+      J[i][k] = F(0);
+    }
+  }
+  if (first) {  // the series' first chunk starts from the prior
+#pragma unroll
+    for (int ra = 0; ra < 2; ++ra)
+#pragma unroll
+      for (int rb = 0; rb < 2; ++rb) C[2 * ra + rb][2 * ra + rb] = Pa[ra] * Pb[rb];
+    if constexpr (SUM) {
+      C[4][4] = sc * sc;
+      C[5][5] = sc * sc * wc * wc;
+    }
+  }
+  double gam = 0.0, ld = 0.0;
+  int n_end = 0;
+  bool bad = false;
+  const int64_t e0 = M.ch_ev0[c];
+  const int len = M.ch_len[c];
+  int64_t mi = M.ch_meas0[c];
+  for (int kk = 0; kk < len; ++kk) {
+    const F dt = __ldg(M.dt + e0 + kk);
+    const float4 q = __ldg(M.meas + mi);
+    ++mi;
+    const Osc2<F> Ao = osc2<F, F>(dt, wa, qa, F(1));
+    const Osc2<F> Bo = osc2<F, F>(dt, wb, qb, var);
+    F Phi[D][D], Qd[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int cc = 0; cc < D; ++cc) Phi[r][cc] = Qd[r][cc] = F(0);
+#pragma unroll
+    for (int ra = 0; ra < 2; ++ra)
+#pragma unroll
+      for (int rb = 0; rb < 2; ++rb)
+#pragma unroll
+        for (int ca = 0; ca < 2; ++ca)
+#pragma unroll
+          for (int cb = 0; cb < 2; ++cb) {
+            const int r = 2 * ra + rb, cc = 2 * ca + cb;
+            Phi[r][cc] = Ao.p[ra][ca] * Bo.p[rb][cb];
+            Qd[r][cc] = (ra == ca ? Pa[ra] * Bo.q[rb][cb] : F(0)) +
+                        (rb == cb ? Ao.q[ra][ca] * Pb[rb] : F(0)) - Ao.q[ra][ca] * Bo.q[rb][cb];
+          }
+    if constexpr (SUM) {
+      const Osc2<F> Co = osc2<F, F>(dt, wc, qcq, sc * sc);
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          Phi[4 + r][4 + cc] = Co.p[r][cc];
+          Qd[4 + r][4 + cc] = Co.q[r][cc];
+        }
+    }
+    // A <- Phi A, b <- Phi b, C <- Phi C Phi^T + Q
+    F T1[D][D], T2[D][D], bt[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      F acc = F(0);
+#pragma unroll
+      for (int e = 0; e < D; ++e) acc += Phi[r][e] * b[e];
+      bt[r] = acc;
+#pragma unroll
+      for (int cc = 0; cc < D; ++cc) {
+        F a1 = F(0), a2 = F(0);
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+          a1 += Phi[r][e] * A[e][cc];
+          a2 += Phi[r][e] * C[e][cc];
+        }
+        T1[r][cc] = a1;
+        T2[r][cc] = a2;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      b[r] = bt[r];
+#pragma unroll
+      for (int cc = 0; cc < D; ++cc) A[r][cc] = T1[r][cc];
+#pragma unroll
+      for (int cc = r; cc < D; ++cc) {
+        F a2 = Qd[r][cc];
+#pragma unroll
+        for (int e = 0; e < D; ++e) a2 += T2[r][e] * Phi[cc][e];
+        C[r][cc] = a2;
+        C[cc][r] = a2;
+      }
+    }
+    // update with h = e_0 (+ e_4): the latent of the product (and term)
+    const F y = q.x, r0 = q.y;
+    F u[D], g[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      u[r] = C[r][0] + (SUM ? C[r][4] : F(0));
+      g[r] = A[0][r] + (SUM ? A[4][r] : F(0));  // h^T A
+    }
+    const F hu = u[0] + (SUM ? u[4] : F(0));
+    const F hb = b[0] + (SUM ? b[4] : F(0));
+    const F Sv = hu + r0 + s2;
+    const F cc = y - hb;
+    bad |= !(Sv > F(0));
+    const F iS = F(1) / Sv;
+    const F ci = cc * iS;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      eta[r] += g[r] * ci;
+#pragma unroll
+      for (int k = 0; k < D; ++k) J[r][k] += g[r] * g[k] * iS;
+    }
+    gam += (double)(cc * ci);
+    ld += glog(Sv);
+    ++n_end;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      const F Kr = u[r] * iS;
+#pragma unroll
+      for (int k = 0; k < D; ++k) A[r][k] -= Kr * g[k];
+      b[r] += Kr * cc;
+#pragma unroll
+      for (int k = 0; k < D; ++k) C[r][k] -= u[r] * u[k] * iS;
+    }
+  }
+  F Cp[ES::NP], Jp[ES::NP];
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int k = r; k < D; ++k) {
+      Cp[ES::pk(r, k)] = C[r][k];
+      Jp[ES::pk(r, k)] = J[r][k];
+    }
+  store_elem<ES>(ef, n_vch, vc, A, b, Cp, eta, Jp);
+  ed[vc] = gam;
+  ed[(size_t)n_vch + vc] = ld;
+  ed[(size_t)2 * n_vch + vc] = (double)n_end;
+  if (bad) flag_error(err, orow, 7);
+}
+
+template <bool SUM, class ES>
+cudaError_t launch_elem_prod(const DevModel &M, const float *theta, int n_vch, int per_series,
+                             float *ef, double *ed, int *err, const float *, float *, int, float *,
+                             int c_begin, int c_count, cudaStream_t st) {
+  if (n_vch <= 0 || c_count <= 0) return cudaSuccess;
+  if (c_begin < 0 || c_begin + c_count > M.n_chunks) return cudaErrorInvalidValue;
+  const int bs = 128;
+  const int64_t nt = (int64_t)(n_vch / M.n_chunks) * c_count;
+  k_elem_prod<SUM, ES><<<(unsigned)((nt + bs - 1) / bs), bs, 0, st>>>(
+      M, theta, n_vch, per_series, ef, ed, err, c_begin, c_count);
+  GPSS_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+// A product model has no step-scalar tables (its factors are discretised on
+// the fly).
+inline cudaError_t no_tables(const float *, int, int, int, int, float *, cudaStream_t) {
+  return cudaSuccess;
+}
+
+// Operation table of a product model: the plain filters, the forward-mode
+// gradient, and the chunked log-likelihood (dense product elements, then the
+// combination and chunk log-likelihoods of the shape ES of the same state
+// dimension).
 template <bool SUM>
 OpTable make_prod_ops() {
+  using ES = typename std::conditional<SUM, Shape<3, 0, 0>, Shape<2, 0, 0>>::type;
   OpTable o{};
-  o.D = SUM ? 6 : 4;
-  o.NP = o.D * (o.D + 1) / 2;
-  o.NT = SUM ? 2 : 1;
+  o.D = ES::D;
+  o.NP = ES::NP;
+  o.NF = ElemLayout<ES>::NF;
+  o.ND = ElemLayout<ES>::ND;
+  o.NT = 1;  // tables unused; keeps the table scratch small
   o.plain32 = &launch_plain_prod<SUM, float>;
   o.plain64 = &launch_plain_prod<SUM, double>;
   o.prod_grad = &launch_prod_grad<SUM>;
+  o.tables = &no_tables;
+  o.elem = &launch_elem_prod<SUM, ES>;
+  o.scan = &launch_scan<ES>;
+  o.scan_tree = &launch_scan_tree<ES>;
+  o.scan_scratch = &scan_scratch_count<ES>;
+  o.finish = &launch_finish<ES>;
+  o.warp_combine = &launch_warp_combine<ES>;
+  o.warp_scratch = &warp_scratch_count<ES>;
   return o;
 }
 

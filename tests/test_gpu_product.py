@@ -49,10 +49,13 @@ def _series_wl(terms, theta, n=600, seed=111):
     return _f32(synth._finish("p", terms, 0, [(t, t.copy())], np.asarray([theta]), True, rng))
 
 
-@pytest.mark.parametrize("precision", [32, 64])
-def test_batch_product_plus_matern(gp, precision):
+@pytest.mark.parametrize("precision,schedule,chunk", [(32, 0, 0), (32, 2, 16), (32, 3, 0),
+                                                     (64, 0, 0)])
+def test_batch_product_plus_matern(gp, precision, schedule, chunk):
+    # FP32: the chunked parallel-in-time path (product elements, shared
+    # combination) at two chunk lengths, and the plain per-series filter
     wl = _f32(synth.c2p(n_series=8, scale=0.05))
-    m = gp.Model.from_workload(wl, precision=precision)
+    m = gp.Model.from_workload(wl, precision=precision, schedule=schedule, chunk_len=chunk)
     ll = m.loglik(_dev(wl.theta)).cpu().numpy()
     ref = oracle.loglik_workload(wl, processes=4)
     _check(ll, ref, np.diff(wl.offsets), rel=1e-9 if precision == 64 else None)
@@ -65,8 +68,8 @@ def test_batch_product_plus_matern(gp, precision):
     ([PROD], [0.9, 0.5, 0.3, 1.1, 2.0, 0.05])])                     # overdamped factor
 def test_single_series(gp, terms, theta):
     wl = _series_wl(terms, theta)
-    for precision in (32, 64):
-        m = gp.Model.from_workload(wl, precision=precision)
+    for precision, schedule, chunk in ((32, 0, 0), (32, 2, 8), (32, 3, 0), (64, 0, 0)):
+        m = gp.Model.from_workload(wl, precision=precision, schedule=schedule, chunk_len=chunk)
         ll = m.loglik(_dev(wl.theta)).cpu().numpy()
         _check(ll, oracle.loglik_workload(wl), [wl.n_meas], rel=1e-9 if precision == 64 else None)
 
