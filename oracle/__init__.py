@@ -6,12 +6,14 @@ the CUDA path (``paper_2601_02527_gb300``) and neither imports the other.
 
 Parts:
   * :func:`events` -- the event sequence of Section 3.2 (two events per
-    exposure, time-sorted; ties resolved end-before-start) and the slot of
-    each exposure (instrument labels, or greedy interval colouring when none
-    are given; footnote to Section 3.2.3).
+    exposure, one per instantaneous measurement, time-sorted; ties resolved
+    end-before-start) and the slot of each exposure (instrument labels, or
+    greedy interval colouring when none are given; footnote to Section
+    3.2.3).
   * :func:`loglik` -- the sequential integrated Kalman filter in plain C,
     FP64, Van Loan discretisation (``gpss_oracle.c``), with complex-step
-    gradients.
+    gradients; :func:`exposure_grad`, :func:`condition` (integrated RTS
+    smoother) and :func:`predict` (Algorithm 1) on the same model.
   * :mod:`oracle.dense` -- the dense integrated-GP log-likelihood
     (Section 2.1 with the integrated kernel of Section 3.1), used to pin the
     filter on small N.

@@ -9,7 +9,8 @@
  * CUDA path, and the CUDA path never calls it.
  *
  * What it computes, in the paper's order:
- *   - model matrices from natural parameters (Appendix B, C.1);
+ *   - model matrices from natural parameters (Appendix B, C.1; products of
+ *     two SHO terms as the Kronecker model of Appendix C.2);
  *   - discretisation by the Van Loan matrix exponential (Eq. Q_from_vanloan)
  *     with exact semigroup doubling for long steps;
  *   - the integrated Kalman filter with resets (Eqs. integrated_kalman_pred,
@@ -18,8 +19,10 @@
  *   - gradients by the complex-step method: the filter is compiled a second
  *     time over double complex, theta_i is perturbed by i*h, and
  *     d loglik / d theta_i = Im(loglik) / h, exact up to rounding.
- * Events arrive already sorted and labelled (start/end, slot) by the Python
- * side of the oracle.
+ *   - the integrated RTS smoother (Eqs. rts, integrated_rts) and prediction
+ *     at arbitrary times (Algorithm 1).
+ * Events arrive already sorted and labelled (start / end / instantaneous
+ * measurement, slot) by the Python side of the oracle.
  */
 #include <complex.h>
 #include <math.h>
