@@ -72,6 +72,28 @@ float solve_d(const float *A, const float *B, float *X, int R) {
   return ld;
 }
 
+// Observation of a measurement event and its conditioned (mean, variance)
+// from full symmetric P and Lam (row-major D x D), for shape ids
+// 3 = (2 terms, no slot: instantaneous), 4 = (2 terms, 2 slots), 1 = (2 terms,
+// 1 slot, layout 1).  out4 = (hu, hm, cond mean, cond var); u receives P h.
+template <class S>
+void observe_s(int j, float w, const float *m, const float *Pf, const float *lam,
+               const float *Lf, float *u, float *out4) {
+  constexpr int D = S::D;
+  float P[S::NP], L[S::NP];
+  for (int i = 0; i < D; ++i)
+    for (int k = i; k < D; ++k) {
+      P[S::pk(i, k)] = Pf[i * D + k];
+      L[S::pk(i, k)] = Lf[i * D + k];
+    }
+  float hu, hm;
+  obs_project<S>(j, w, m, P, u, hu, hm);
+  const float2 c = conditioned<S>(j, w, m, P, lam, L);
+  out4[0] = hu;
+  out4[1] = hm;
+  out4[2] = c.x;
+  out4[3] = c.y;
+}
 }  // namespace
 
 extern "C" {
@@ -189,6 +211,16 @@ void hh_boundary_adjoint(int shape, const float *m, const float *P, const float 
   if (shape == 0) adj_s<Shape<1, 1, 0>>(m, P, eta, J, lam, Lam);
   else if (shape == 1) adj_s<Shape<2, 1, 1>>(m, P, eta, J, lam, Lam);
   else adj_s<Shape<2, 3, 0>>(m, P, eta, J, lam, Lam);
+}
+
+int hh_obs_dim(int shape) {
+  return shape == 3 ? Shape<2, 0, 0>::D : shape == 4 ? Shape<2, 2, 0>::D : Shape<2, 1, 1>::D;
+}
+void hh_observe(int shape, int j, float w, const float *m, const float *Pf, const float *lam,
+                const float *Lf, float *u, float *out4) {
+  if (shape == 3) observe_s<Shape<2, 0, 0>>(j, w, m, Pf, lam, Lf, u, out4);
+  else if (shape == 4) observe_s<Shape<2, 2, 0>>(j, w, m, Pf, lam, Lf, u, out4);
+  else observe_s<Shape<2, 1, 1>>(j, w, m, Pf, lam, Lf, u, out4);
 }
 
 // coefficient k of the six Taylor series: the division-free per-lane form

@@ -9,7 +9,9 @@ kernels inline (nvcc, host code only).  Checked here:
     of the oracle;
   * the economised step-scalar tables against the Taylor series they replace;
   * the pivoted dense solver, the element combination, the closed-form chunk
-    log-likelihood and the boundary adjoint against numpy.
+    log-likelihood and the boundary adjoint against numpy;
+  * the observation vector of the update and the conditioned value for
+    shapes with and without integral states (instantaneous measurements).
 """
 import ctypes
 import math
@@ -56,6 +58,8 @@ def hh():
     lib.hh_chunk_loglik.argtypes = [ctypes.c_int, P(f), P(f), P(f), P(f), d, d, d]
     lib.hh_chunk_loglik.restype = d
     lib.hh_boundary_adjoint.argtypes = [ctypes.c_int, P(f), P(f), P(f), P(f), P(f), P(f)]
+    lib.hh_obs_dim.argtypes = [ctypes.c_int]
+    lib.hh_observe.argtypes = [ctypes.c_int, ctypes.c_int, f, P(f), P(f), P(f), P(f), P(f), P(f)]
     return lib
 
 
@@ -235,3 +239,38 @@ def test_chunk_loglik_and_adjoint(hh, shape):
         Lref = 0.5 * (np.outer(lref, lref) - np.linalg.solve(Y, J))
         assert np.allclose(lam, lref, rtol=1e-4, atol=1e-4 * np.abs(lref).max())
         assert np.allclose(_unpack(Lam, D), Lref, rtol=1e-3, atol=1e-4 * np.abs(Lref).max())
+
+
+@pytest.mark.parametrize("shape,j,w", [(3, 0, 1.0), (4, 0, 2.5), (4, 1, 0.4), (1, 0, 1.7)])
+def test_observation_vector(hh, shape, j, w):
+    # the update's h: the latent sum for a shape without integral states
+    # (instantaneous measurements), else w on the measurement slot's integral
+    # state(s) (one per slot, or one per term under layout 1)
+    D = hh.hh_obs_dim(shape)
+    h = np.zeros(D)
+    if shape == 3:
+        h[[0, 2]] = 1.0
+    elif shape == 4:
+        h[4 + j] = w
+    else:
+        h[[4, 5]] = w
+    rng = np.random.default_rng(30 + shape)
+    X = rng.standard_normal((D, D))
+    Pm = (X @ X.T + D * np.eye(D)).astype(np.float32)
+    Y = rng.standard_normal((D, D))
+    Lm = (0.1 * (Y + Y.T)).astype(np.float32)
+    m = rng.standard_normal(D).astype(np.float32)
+    lam = rng.standard_normal(D).astype(np.float32)
+    u = np.zeros(D, np.float32)
+    out = np.zeros(4, np.float32)
+    hh.hh_observe(shape, j, w, _p(m, ctypes.c_float), _p(Pm, ctypes.c_float),
+                  _p(lam, ctypes.c_float), _p(Lm, ctypes.c_float), _p(u, ctypes.c_float),
+                  _p(out, ctypes.c_float))
+    P64, L64 = Pm.astype(float), Lm.astype(float)
+    uref = P64 @ h
+    np.testing.assert_allclose(u, uref, rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(out[:2], [h @ uref, h @ m], rtol=1e-5, atol=1e-5)
+    # conditioned value: smoothed state m + P lam, P - P (lam lam^T - 2 Lam) P
+    ms = m + P64 @ lam
+    Ps = P64 - P64 @ (np.outer(lam, lam) - 2 * L64) @ P64
+    np.testing.assert_allclose(out[2:], [h @ ms, h @ Ps @ h], rtol=1e-4, atol=1e-4)
