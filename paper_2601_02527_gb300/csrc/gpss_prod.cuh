@@ -8,10 +8,12 @@
 // all from the two factors' per-step scalars (f, f', I_ff, I_pp; see
 // gpss_device.cuh).  Optionally a second, plain SHO / Matern-3/2 term is
 // added (state 4 + 2).  The state dimension grows as the product of the
-// factors' (Section C.2), so this path runs the sequential filter with one
-// thread per series and the full covariance in registers: log-likelihood
-// in FP32 (FP64 sums) or FP64, and its hyperparameter gradient by forward-mode
-// tangents (one thread per series and parameter).
+// factors' (Section C.2), so the covariance is kept dense: the FP32
+// log-likelihood runs in parallel in time (k_elem_prod forms dense chunk
+// elements, the dimension-generic combination of a same-size shape does the
+// rest), the plain sequential filter (one thread per series) serves FP64 and
+// schedule 3, and the hyperparameter gradient comes from forward-mode tangents
+// (one thread per series and parameter).
 #pragma once
 
 #include <type_traits>
