@@ -174,3 +174,21 @@ def test_edge_cases(gp):
         assert ll[2] == 0.0 and np.all(g[2] == 0)
         _check_ll(ll[keep], ref_ll, np.diff(wl.offsets)[keep])
         _check_rows(g[keep], ref_g)
+
+
+def test_host_buffer_and_shared_sets(gp):
+    # the host-buffer call (grouped re-upload of the event stream) gives the
+    # device call's bits; shared parameter sets against the oracle
+    wl = _wl(n_series=6, scale=0.05)
+    m = gp.Model.from_workload(wl, chunk_len=32)
+    th = _dev(wl.theta)
+    ll, g = m.loglik_grad(th)
+    ll_h, g_h = m.loglik_grad_host(wl.theta, reupload_events=True)
+    np.testing.assert_array_equal(ll.cpu().numpy(), ll_h)
+    np.testing.assert_array_equal(g.cpu().numpy(), g_h)
+    ll_s, g_s = m.loglik_grad(th[:2], per_series=False)
+    ll_s = ll_s.cpu().numpy().reshape(2, wl.n_series)
+    for k in range(2):
+        ref_ll = [oracle.loglik(wl.terms, 0, *wl.series(i)[:4], wl.theta[k])
+                  for i in range(wl.n_series)]
+        _check_ll(ll_s[k], ref_ll, np.diff(wl.offsets))

@@ -137,3 +137,20 @@ def test_edge_cases(gp):
     for precision in (32, 64):
         ll = gp.Model.from_workload(wl, precision=precision).loglik(_dev(wl.theta)).cpu().numpy()
         _check(ll, ref, np.diff(wl.offsets), rel=1e-9 if precision == 64 else None)
+
+
+def test_gradient_shared_sets_and_host_buffer(gp):
+    wl = _series_wl([PROD, M32], [1.0, 0.3, 1.0, 1.3, 5.0, 0.5, 3.0, 0.1], n=300)
+    th = np.array([wl.theta[0], wl.theta[0] * [1, 1.2, 1, 0.9, 1, 1, 1, 1]], np.float64)
+    th = th.astype(np.float32).astype(np.float64)
+    m = gp.Model.from_workload(wl)
+    ll, g = m.loglik_grad(_dev(th), per_series=False)
+    ll, g = ll.cpu().numpy().ravel(), g.cpu().numpy().reshape(2, -1)
+    for k in range(2):
+        r_ll, r_g = oracle.loglik(wl.terms, 0, *wl.series(0)[:4], th[k], grad=True)
+        _check([ll[k]], [r_ll], [wl.n_meas])
+        assert np.all(np.abs(g[k] - r_g) <= 1e-3 * np.abs(r_g) + 1e-4 * np.abs(r_g).max())
+    ll_h, g_h = m.loglik_grad_host(wl.theta, reupload_events=True)
+    ll_d, g_d = m.loglik_grad(_dev(wl.theta))
+    np.testing.assert_array_equal(ll_d.cpu().numpy(), ll_h)
+    np.testing.assert_array_equal(g_d.cpu().numpy(), g_h)
