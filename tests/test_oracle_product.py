@@ -98,3 +98,28 @@ def test_smoother_and_prediction(oracle_lib):
     mu_d, va_d = dense.predict(terms, th, t, t, y, ye, tq)
     assert np.max(np.abs(mu - mu_d)) <= 1e-9 * np.abs(mu_d).max()
     assert np.all(np.abs(va - va_d) <= 1e-7 * va_d + 1e-12)
+
+
+def test_integrated_smoother_and_prediction(oracle_lib):
+    # exposure averages with a product kernel (two overlapping instruments):
+    # the oracle's integrated RTS smoother and Algorithm 1 prediction against
+    # the dense posterior and prediction (kernel integrals by quadrature)
+    th = [1.0, 0.5, 3.0, 1.9, 2.0, 0.1]
+    ts = np.array([0.0, 0.8, 1.9, 3.1, 4.0])
+    te = ts + np.array([0.5, 0.6, 0.9, 0.4, 1.0])
+    t2 = np.array([0.3, 2.2])
+    a = np.concatenate([ts, t2])
+    b = np.concatenate([te, t2 + 1.5])
+    inst = np.array([0] * 5 + [1] * 2, np.int32)
+    rng = np.random.default_rng(105)
+    y = rng.standard_normal(len(a))
+    ye = np.full(len(a), 0.1)
+    mu, va = oracle.condition([PROD], 0, a, b, y, ye, th, instrument=inst)
+    mu_d, va_d = dense.posterior([PROD], th, a, b, y, ye)
+    assert np.max(np.abs(mu - mu_d)) <= 1e-8 * np.abs(mu_d).max()
+    assert np.all(np.abs(va - va_d) <= 1e-7 * va_d + 1e-11)
+    tq = np.array([-0.5, 0.2, 1.0, 2.5, 4.6, 6.0])
+    mu, va = oracle.predict([PROD], 0, a, b, y, ye, th, tq, instrument=inst)
+    mu_d, va_d = dense.predict([PROD], th, a, b, y, ye, tq)
+    assert np.max(np.abs(mu - mu_d)) <= 1e-8 * np.abs(mu_d).max()
+    assert np.all(np.abs(va - va_d) <= 1e-7 * va_d + 1e-11)
