@@ -6,6 +6,13 @@ This package is a thin binding over ``libgpss.so`` (CUDA, sm_103a; C ABI in
 computation runs in the library's kernels.  PyTorch supplies device memory and
 streams.  There is no CPU fallback: if the library is missing or no CUDA
 device is present, calls raise.
+
+``Model`` holds one event stream (exposure averages, or instantaneous
+measurements with t_end == t_start) and offers the log-likelihood, its
+gradient with respect to the hyperparameters and the exposure windows, the
+conditioned value of every measurement, predictions at arbitrary times and an
+autotuner; ``loglik`` wraps the gradient in a ``torch.autograd.Function``.
+Kernel terms: SHO (any Q > 0), Matern-3/2, and a product of two SHOs.
 """
 from __future__ import annotations
 
