@@ -334,7 +334,7 @@ def run_ours(args):
     peaks, src = load_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
-    n_events = 2 * wl.n_meas
+    n_events = int(model.info["n_events"])
     # the gradient phase is k_grad alone; its per-launch time from the
     # phase events recorded on the launching stream inside the timed region
     fpe = ALG_FLOPS_PER_EVENT.get(args.workload)

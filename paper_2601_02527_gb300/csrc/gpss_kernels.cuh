@@ -1,9 +1,10 @@
 // Kernels of the integrated-measurement GP log-likelihood (arXiv 2601.02527).
 //
 // Event stream (built on the host, Section 3.2): per series 2N events in time
-// order; per event a gap dt (FP32, formed in FP64) and a tag byte
-// (bit 0: exposure end, bits 1-3: slot); per measurement, in end order, a
-// float4 (y, yerr^2, 1/delta, 0).
+// order (N for a series of instantaneous measurements, which observe the
+// latent and need no integral state); per event a gap dt (FP32, formed in
+// FP64) and a tag byte (bit 0: measurement, bits 1-3: slot); per measurement,
+// in event order, a float4 (y, yerr^2, 1/delta, 0).
 //
 // Schedules
 //  * k_plain  -- one thread per series runs the whole sequential filter
