@@ -31,7 +31,7 @@ struct Osc2 {
 };
 
 template <class T, class F>
-GPSS_D Osc2<T> osc2(F dt, T w0, T Q, T var) {
+GPSS_HD Osc2<T> osc2(F dt, T w0, T Q, T var) {
   const T a = w0 / (F(2) * Q);
   const T beta = (val(Q) == F(0.5)) ? cst<T>(F(0))
                                     : w0 * w0 * (F(1) - cst<T>(F(1)) / (F(4) * Q * Q));

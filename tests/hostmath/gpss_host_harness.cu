@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "gpss_kernels.cuh"
+#include "gpss_prod.cuh"
 
 using namespace gpss;
 
@@ -93,6 +94,27 @@ void observe_s(int j, float w, const float *m, const float *Pf, const float *lam
   out4[1] = hm;
   out4[2] = c.x;
   out4[3] = c.y;
+}
+// The product term's transition and noise (row-major 4 x 4) for a step dt
+// and parameters (sigma, omega_a, Q_a, omega_b, Q_b), built as the kernels
+// build them: Phi_a (x) Phi_b and Eq. product_Q from the two factors' 2 x 2
+// blocks (osc2), in FP64 (prec 64) or FP32 (prec 32).
+template <class F>
+void prod_disc_t(double dt, const double *th, double *Phi, double *Q) {
+  const F var = F(th[0]) * F(th[0]);
+  const Osc2<F> A = osc2<F, F>(F(dt), F(th[1]), F(th[2]), F(1));
+  const Osc2<F> B = osc2<F, F>(F(dt), F(th[3]), F(th[4]), var);
+  const F Pa[2] = {F(1), F(th[1]) * F(th[1])}, Pb[2] = {var, var * F(th[3]) * F(th[3])};
+  for (int ra = 0; ra < 2; ++ra)
+    for (int rb = 0; rb < 2; ++rb)
+      for (int ca = 0; ca < 2; ++ca)
+        for (int cb = 0; cb < 2; ++cb) {
+          const int r = 2 * ra + rb, c = 2 * ca + cb;
+          Phi[4 * r + c] = (double)(A.p[ra][ca] * B.p[rb][cb]);
+          Q[4 * r + c] = (double)((ra == ca ? Pa[ra] * B.q[rb][cb] : F(0)) +
+                                  (rb == cb ? A.q[ra][ca] * Pb[rb] : F(0)) -
+                                  A.q[ra][ca] * B.q[rb][cb]);
+        }
 }
 }  // namespace
 
@@ -221,6 +243,13 @@ void hh_observe(int shape, int j, float w, const float *m, const float *Pf, cons
   if (shape == 3) observe_s<Shape<2, 0, 0>>(j, w, m, Pf, lam, Lf, u, out4);
   else if (shape == 4) observe_s<Shape<2, 2, 0>>(j, w, m, Pf, lam, Lf, u, out4);
   else observe_s<Shape<2, 1, 1>>(j, w, m, Pf, lam, Lf, u, out4);
+}
+
+void hh_prod_disc(int prec, double dt, const double *th, double *Phi, double *Q) {
+  if (prec == 64)
+    prod_disc_t<double>(dt, th, Phi, Q);
+  else
+    prod_disc_t<float>(dt, th, Phi, Q);
 }
 
 // coefficient k of the six Taylor series: the division-free per-lane form

@@ -11,7 +11,9 @@ kernels inline (nvcc, host code only).  Checked here:
   * the pivoted dense solver, the element combination, the closed-form chunk
     log-likelihood and the boundary adjoint against numpy;
   * the observation vector of the update and the conditioned value for
-    shapes with and without integral states (instantaneous measurements).
+    shapes with and without integral states (instantaneous measurements);
+  * the product term's transition and noise (Kronecker of the factors'
+    blocks, Eq. product_Q), FP64 and FP32, against the oracle's Van Loan.
 """
 import ctypes
 import math
@@ -59,6 +61,7 @@ def hh():
     lib.hh_chunk_loglik.restype = d
     lib.hh_boundary_adjoint.argtypes = [ctypes.c_int, P(f), P(f), P(f), P(f), P(f), P(f)]
     lib.hh_obs_dim.argtypes = [ctypes.c_int]
+    lib.hh_prod_disc.argtypes = [ctypes.c_int, d, P(d), P(d), P(d)]
     lib.hh_observe.argtypes = [ctypes.c_int, ctypes.c_int, f, P(f), P(f), P(f), P(f), P(f), P(f)]
     return lib
 
@@ -274,3 +277,21 @@ def test_observation_vector(hh, shape, j, w):
     ms = m + P64 @ lam
     Ps = P64 - P64 @ (np.outer(lam, lam) - 2 * L64) @ P64
     np.testing.assert_allclose(out[2:], [h @ ms, h @ Ps @ h], rtol=1e-4, atol=1e-4)
+
+
+@pytest.mark.parametrize("theta", [(1.3, 0.4, 5.0, 2.1, 0.8), (0.9, 1.1, 0.3, 0.5, 3.0),
+                                   (1.0, 2.0, 0.5, 0.7, 0.5)])
+def test_product_discretisation(oracle_lib, hh, theta):
+    # the kernels' product transition and noise (Kronecker of the factors'
+    # blocks, Eq. product_Q) against the oracle's Van Loan of the product model
+    th = np.array(list(theta) + [0.1])
+    for dt in (0.0, 1e-3, 0.05, 0.7, 3.0, 25.0):
+        P_ref, Q_ref, P0 = oracle.discretize([3], 0, 0, th, dt)
+        scale = np.abs(P0).max()
+        for prec, tol in ((64, 1e-10), (32, 3e-6)):
+            Phi = np.zeros(16)
+            Q = np.zeros(16)
+            hh.hh_prod_disc(prec, dt, _p(th, ctypes.c_double), _p(Phi, ctypes.c_double),
+                            _p(Q, ctypes.c_double))
+            assert np.all(np.abs(Phi.reshape(4, 4) - P_ref) <= tol * (np.abs(P_ref) + 1)), (prec, dt)
+            assert np.all(np.abs(Q.reshape(4, 4) - Q_ref) <= tol * (np.abs(Q_ref) + scale)), (prec, dt)
