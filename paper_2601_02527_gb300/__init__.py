@@ -207,10 +207,31 @@ class Model:
         import torch
         if not (isinstance(theta, torch.Tensor) and theta.is_cuda):
             raise TypeError("theta must be a CUDA tensor")
+        if theta.device.index != self.device:
+            raise ValueError(f"theta is on cuda:{theta.device.index}, the model on "
+                             f"cuda:{self.device}")
         th = theta.detach().to(torch.float32).contiguous()
         if th.dim() != 2 or th.shape[1] != self.n_params:
             raise ValueError(f"theta must be [n_sets, {self.n_params}]")
         return th
+
+    def _check_out(self, t, what, dtype, numel):
+        """A caller-supplied output buffer must be a contiguous tensor of the
+        given dtype on the model's device with at least ``numel`` elements:
+        the kernels write that many values through its pointer."""
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{what} must be a CUDA tensor")
+        if t.device.index != self.device:
+            raise ValueError(f"{what} is on cuda:{t.device.index}, the model on "
+                             f"cuda:{self.device}")
+        if t.dtype != dtype:
+            raise ValueError(f"{what} must be {dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{what} must be contiguous")
+        if t.numel() < numel:
+            raise ValueError(f"{what} holds {t.numel()} elements, {numel} needed")
+        return t
 
     def loglik(self, theta, per_series=True, out=None, stream=None, batched=False):
         """Log-likelihood per output row (float64 CUDA tensor)."""
@@ -219,6 +240,7 @@ class Model:
         n = self.n_out(th, per_series)
         if out is None:
             out = torch.empty(n, dtype=torch.float64, device=th.device)
+        self._check_out(out, "out", torch.float64, n)
         f = self._lib.gp_ss_loglik_batched if batched else self._lib.gp_ss_loglik
         _check(f(self._h, th.data_ptr(), th.shape[0], int(bool(per_series)), out.data_ptr(),
                  _stream_ptr(stream)), "gp_ss_loglik")
@@ -243,6 +265,7 @@ class Model:
         n = self.n_out(th, per_series)
         if out is None:
             out = torch.empty(n, dtype=torch.float64, device=th.device)
+        self._check_out(out, "out", torch.float64, n)
         _check(self._lib.gp_ss_loglik_noalloc(self._h, th.data_ptr(), th.shape[0],
                                               int(bool(per_series)), out.data_ptr(),
                                               _stream_ptr(stream)), "gp_ss_loglik_noalloc")
@@ -263,10 +286,14 @@ class Model:
             grad = torch.empty(n, self.n_params, dtype=torch.float32, device=th.device)
         if exposure and batched:
             raise ValueError("the exposure gradient is computed by the direct call only")
-        if exposure and dexp is None:
+        self._check_out(out, "out", torch.float64, n)
+        self._check_out(grad, "grad", torch.float32, n * self.n_params)
+        if exposure:
             rows = 1 if per_series else th.shape[0]
-            dexp = torch.empty(rows, self.info["n_meas"], 2, dtype=torch.float32,
-                               device=th.device)
+            if dexp is None:
+                dexp = torch.empty(rows, self.info["n_meas"], 2, dtype=torch.float32,
+                                   device=th.device)
+            self._check_out(dexp, "dexp", torch.float32, rows * self.info["n_meas"] * 2)
         if batched:
             rc = self._lib.gp_ss_loglik_grad_batched(self._h, th.data_ptr(), th.shape[0],
                                                      int(bool(per_series)), out.data_ptr(),

@@ -242,13 +242,19 @@ bool pick_ops(int n_terms, int n_slots, int layout, OpTable *o) {
   return false;
 }
 
+// Allocate *dst and copy n elements of src into it.  On failure *dst is
+// null and nothing stays allocated.
 template <class T>
 gp_ss_status dev_upload(T **dst, const T *src, size_t n) {
   *dst = nullptr;
   if (n == 0) n = 1;
-  if (cudaMalloc((void **)dst, n * sizeof(T)) != cudaSuccess) return GP_SS_ENOMEM;
-  if (src && cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+  T *p = nullptr;
+  if (cudaMalloc((void **)&p, n * sizeof(T)) != cudaSuccess) return GP_SS_ENOMEM;
+  if (src && cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(p);
     return GP_SS_ECUDA;
+  }
+  *dst = p;
   return GP_SS_OK;
 }
 
@@ -484,19 +490,43 @@ gp_ss_status make_plan(gp_ss_model *m, int chunk_len) {
     for (int l = 0; l < 32; ++l) ml = std::max(ml, len[w * 32 + l]);
     doff[w + 1] = doff[w] + 32 * (int64_t)ml;
   }
+  // upload the new plan into fresh buffers first: the model keeps its old
+  // plan, untouched, unless every upload succeeds
+  int64_t *n_ev0 = nullptr, *n_meas0 = nullptr, *n_doff = nullptr;
+  int32_t *n_len = nullptr, *n_ser = nullptr, *n_first = nullptr;
+  uint8_t *n_flags = nullptr;
+  gp_ss_status st = GP_SS_OK;
+  if (!st) st = dev_upload(&n_ev0, ev0.data(), ev0.size());
+  if (!st) st = dev_upload(&n_meas0, meas0.data(), meas0.size());
+  if (!st) st = dev_upload(&n_len, len.data(), len.size());
+  if (!st) st = dev_upload(&n_ser, ser.data(), ser.size());
+  if (!st) st = dev_upload(&n_first, first.data(), first.size());
+  if (!st) st = dev_upload(&n_flags, flags.data(), flags.size());
+  if (!st) st = dev_upload(&n_doff, doff.data(), doff.size());
+  if (st) {
+    void *fresh[] = {n_ev0, n_meas0, n_len, n_ser, n_first, n_flags, n_doff};
+    for (void *p : fresh)
+      if (p) cudaFree(p);
+    return st;
+  }
+  // kernels queued earlier may still read the old plan
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    void *fresh[] = {n_ev0, n_meas0, n_len, n_ser, n_first, n_flags, n_doff};
+    for (void *p : fresh) cudaFree(p);
+    return GP_SS_ECUDA;
+  }
   void *old[] = {m->d_ch_ev0, m->d_ch_meas0, m->d_ch_len, m->d_ch_series, m->d_ch_first,
                  m->d_ch_flags, m->d_w_doff};
   for (void *p : old)
     if (p) cudaFree(p);
-  gp_ss_status st;
-  if ((st = dev_upload(&m->d_ch_ev0, ev0.data(), ev0.size()))) return st;
-  if ((st = dev_upload(&m->d_ch_meas0, meas0.data(), meas0.size()))) return st;
-  if ((st = dev_upload(&m->d_ch_len, len.data(), len.size()))) return st;
-  if ((st = dev_upload(&m->d_ch_series, ser.data(), ser.size()))) return st;
-  if ((st = dev_upload(&m->d_ch_first, first.data(), first.size()))) return st;
+  m->d_ch_ev0 = n_ev0;
+  m->d_ch_meas0 = n_meas0;
+  m->d_ch_len = n_len;
+  m->d_ch_series = n_ser;
+  m->d_ch_first = n_first;
+  m->d_ch_flags = n_flags;
+  m->d_w_doff = n_doff;
   m->ch_first = first;
-  if ((st = dev_upload(&m->d_ch_flags, flags.data(), flags.size()))) return st;
-  if ((st = dev_upload(&m->d_w_doff, doff.data(), doff.size()))) return st;
   m->dcache_steps = doff[n_w];
   m->chunk_len = L;
   m->n_chunks = (int)len.size();
@@ -585,12 +615,17 @@ struct PhaseTimer {
 // Scratch from the model's pool; the default pool while the stream is
 // being captured into a graph (graph allocations have their own pool) or
 // when the model has no pool.
+// On failure *p is null.
 cudaError_t scratch_alloc(const gp_ss_model *m, void **p, size_t bytes, cudaStream_t st) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e;
   if (m->pool && cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
       cs == cudaStreamCaptureStatusNone)
-    return cudaMallocFromPoolAsync(p, bytes, m->pool, st);
-  return cudaMallocAsync(p, bytes, st);
+    e = cudaMallocFromPoolAsync(p, bytes, m->pool, st);
+  else
+    e = cudaMallocAsync(p, bytes, st);
+  if (e != cudaSuccess) *p = nullptr;
+  return e;
 }
 
 gp_ss_status check_call(const gp_ss_model *m, const float *theta, int n_sets, int per_series,
@@ -1283,10 +1318,16 @@ gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *m, const float *theta_hos
   float *d_theta = nullptr, *d_grad = nullptr;
   double *d_ll = nullptr;
   const size_t nth = (size_t)n_sets * m->n_params;
-  if (scratch_alloc(m, (void **)&d_theta, nth * sizeof(float), st) ||
-      scratch_alloc(m, (void **)&d_ll, (size_t)n_out * sizeof(double), st) ||
-      scratch_alloc(m, (void **)&d_grad, (size_t)n_out * m->n_params * sizeof(float), st))
+  if (scratch_alloc(m, (void **)&d_theta, nth * sizeof(float), st) != cudaSuccess ||
+      scratch_alloc(m, (void **)&d_ll, (size_t)n_out * sizeof(double), st) != cudaSuccess ||
+      scratch_alloc(m, (void **)&d_grad, (size_t)n_out * m->n_params * sizeof(float), st) !=
+          cudaSuccess) {
+    // give back whichever of the three was taken
+    void *taken[] = {d_theta, d_ll, d_grad};
+    for (void *p : taken)
+      if (p) cudaFreeAsync(p, st);
     return GP_SS_ENOMEM;
+  }
   gp_ss_status res = GP_SS_OK;
   // A re-sent event stream goes up in series groups on a second stream, and
   // each group's element pass starts as soon as its events are in (the copy

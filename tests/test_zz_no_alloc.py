@@ -26,9 +26,17 @@ def gp():
     return g
 
 
-def test_noalloc_matches_loglik_two_calls(gp):
-    wl = synth.c2(n_series=24, scale=0.1)
-    m = gp.Model.from_workload(wl, chunk_len=128)
+def _overdamped(wl):
+    """Q of the first term below 1/2 in every other series (those rows run
+    the element pass's second launch, the one with the overdamped branches)."""
+    th = wl.theta.copy()
+    th[::2, 2] = 0.3
+    wl.theta = th
+    return wl
+
+
+def _two_calls(gp, wl, chunk_len):
+    m = gp.Model.from_workload(wl, chunk_len=chunk_len)
     th = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
     ref = m.loglik(th).cpu().numpy()
     n = np.diff(wl.offsets)
@@ -41,6 +49,35 @@ def test_noalloc_matches_loglik_two_calls(gp):
     for got in outs:
         assert np.all(np.isfinite(got))
         assert np.all(np.abs(got - ref) <= 1e-4 * np.maximum(np.abs(ref), 0.1 * n))
+    return m
+
+
+@pytest.mark.parametrize("kind", ["sho_m32", "overdamped", "instantaneous"])
+def test_noalloc_matches_loglik_two_calls(gp, kind):
+    if kind == "sho_m32":
+        wl = synth.c2(n_series=24, scale=0.1)
+    elif kind == "overdamped":
+        wl = _overdamped(synth.c2(n_series=24, scale=0.1))
+    else:
+        wl = synth.c2i(n_series=24, scale=0.1)
+    m = _two_calls(gp, wl, 128)
+    if kind == "instantaneous":
+        assert m.info["n_slots"] == 0
+
+
+def _need_bytes(m, n_rows):
+    d, nc = m.info["state_dim"], m.info["n_chunks"]
+    need = ((2 * d * d + 3 * d) * 4 * nc + 255) // 256 * 256 + 24 * nc
+    return need + (960 * 2 * n_rows + 255) // 256 * 256
+
+
+def test_noalloc_just_under_the_limit(gp):
+    # a plan sized to fill most of the fixed array: accepted, same values
+    wl = synth.c2(n_series=64, scale=1.0)
+    m = gp.Model.from_workload(wl, chunk_len=10)
+    need = _need_bytes(m, wl.n_series)
+    assert (12 << 20) < need <= (16 << 20), need
+    _two_calls(gp, wl, 10)
 
 
 def test_noalloc_shared_sets(gp):
@@ -56,10 +93,7 @@ def test_noalloc_shared_sets(gp):
 def test_noalloc_rejects_too_large(gp):
     wl = synth.c2(n_series=64, scale=1.5)
     m = gp.Model.from_workload(wl, chunk_len=12)
-    d = m.info["state_dim"]
-    need = ((2 * d * d + 3 * d) * 4 * m.info["n_chunks"] + 255) // 256 * 256 + 24 * m.info["n_chunks"]
-    need += (960 * 2 * wl.n_series + 255) // 256 * 256
-    assert need > 16 << 20
+    assert _need_bytes(m, wl.n_series) > 16 << 20
     th = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
     with pytest.raises(gp.GPSSError) as e:
         m.loglik_noalloc(th)
