@@ -48,7 +48,7 @@ def _build(lib, t_start, t_end, inst=None, offsets=None, terms=(1,), layout=0, o
     y = np.zeros(n, np.float32)
     ye = np.zeros(n, np.float32)
     spec, keep = gp._spec(terms, layout)
-    opts = opts if opts is not None else gp._Options(32, 0, 0, 0, 0, 0, 0, 0)
+    opts = opts if opts is not None else gp._Options(32, 0, 0, 0, 0, 0, 0, 0, 0)
     h = ctypes.c_void_p()
     ii = None if inst is None else np.ascontiguousarray(inst, np.int32)
     rc = lib.gp_ss_build_model(ctypes.byref(spec), len(offs) - 1, offs.ctypes.data,
@@ -79,7 +79,7 @@ def test_host_validation_without_gpu(lib):
     # an unknown term kind
     assert _build(lib, [0.0], [1.0], terms=(4,)) == 1
     # option values outside their ranges
-    for bad in (gp._Options(32, 0, 0, 0, 12, 0, 0, 0), gp._Options(32, 0, 0, 0, 0, 0, 0, 2),
-                gp._Options(16, 0, 0, 0, 0, 0, 0, 0), gp._Options(32, 4, 0, 0, 0, 0, 0, 0),
-                gp._Options(32, 0, 0, 0, 0, 0, 3, 0)):
+    for bad in (gp._Options(32, 0, 0, 0, 12, 0, 0, 0, 0), gp._Options(32, 0, 0, 0, 0, 0, 0, 2),
+                gp._Options(16, 0, 0, 0, 0, 0, 0, 0, 0), gp._Options(32, 4, 0, 0, 0, 0, 0, 0),
+                gp._Options(32, 0, 0, 0, 0, 0, 3, 0), gp._Options(32, 0, 0, 0, 0, 0, 0, 0, 16)):
         assert _build(lib, [0.0], [1.0], opts=bad) == 1

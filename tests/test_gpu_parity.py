@@ -301,3 +301,42 @@ def test_autotune_loglik(gp):
     # a gradient call after a log-likelihood tuning still works
     _, g = m.loglik_grad(th)
     assert np.isfinite(g.cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("combine,chunk", [(1, 24), (2, 24), (2, 8)])
+def test_combination_precision(gp, prec, combine, chunk):
+    # the cross-chunk combination in FP32 or FP64 (sequential fold or warp
+    # scans + fold/scan of warp totals): log-likelihood and gradient against
+    # the oracle, per-series and shared-set modes
+    wl = f32_theta(synth.c4(n_series=5, scale=0.04))
+    m = gp.Model.from_workload(wl, chunk_len=chunk, combine=combine, combine_precision=prec)
+    ll, g = m.loglik_grad(theta_dev(wl))
+    ref_ll, ref_g = oracle_ll(wl, grad=True)
+    check_ll(ll.cpu().numpy(), ref_ll, counts_of(wl))
+    check_grad(g.cpu().numpy(), ref_g)
+    np.testing.assert_allclose(m.loglik(theta_dev(wl)).cpu().numpy(), ll.cpu().numpy(),
+                               rtol=1e-12)
+    ws = f32_theta(synth.c5(n=900, n_sets=3))
+    ms = gp.Model.from_workload(ws, chunk_len=chunk, combine=combine, combine_precision=prec)
+    lls, gs = ms.loglik_grad(theta_dev(ws), per_series=False)
+    ref_ll, ref_g = oracle_ll(ws, grad=True)
+    check_ll(lls.cpu().numpy(), ref_ll, [ws.n_meas] * len(ref_ll))
+    check_grad(gs.cpu().numpy(), ref_g)
+    # the no-allocation path follows the model's combination precision
+    lln = ms.loglik_noalloc(theta_dev(ws), per_series=False).cpu().numpy()
+    check_ll(lln, ref_ll, [ws.n_meas] * len(ref_ll))
+
+
+def test_output_buffers_are_checked(gp):
+    wl = f32_theta(synth.c4(n_series=3, scale=0.02))
+    m = gp.Model.from_workload(wl)
+    th = theta_dev(wl)
+    with pytest.raises(ValueError):
+        m.loglik(th, out=torch.empty(3, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        m.loglik(th, out=torch.empty(2, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        m.loglik_grad(th, grad=torch.empty(3, m.n_params, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        m.loglik(th, out=torch.empty(6, dtype=torch.float64, device="cuda")[::2])
