@@ -108,6 +108,11 @@ typedef struct {
                              memory for the reverse sweep while they take at most 8 GiB
                              (24 bytes per event and term per theta set), else the sweep
                              recomputes them; 1 always recompute */
+  int combine_precision;  /* arithmetic of the combination of chunk elements across a series
+                             (every level of the scan of Section 3.2.5, the closed-form chunk
+                             log-likelihoods and the adjoints at chunk ends): 0 auto (= 32),
+                             64 FP64, 32 FP32.  The chunk elements themselves are always
+                             FP32; the log-likelihood sums are always FP64. */
 } gp_ss_options;
 
 /* Build a model from exposures (Section 3.2: two events per exposure, reset
@@ -234,7 +239,8 @@ gp_ss_status gp_ss_discretize(const gp_ss_kernel_spec *spec, int n_slots, const 
  * loop that must not pay for or synchronise on an allocation, a process whose
  * allocator is disabled or capped -- can call this instead.  It computes the
  * same log-likelihood (FP32 models only; element pass plus sequential
- * per-series combination) with its scratch in one array of 16 MiB compiled
+ * per-series combination in the model's combination_precision) with its
+ * scratch in one array of 16 MiB compiled
  * into the library: every GPU that loads libgpss holds that array until the
  * process exits.  It calls no allocation routine of CUDA or of any library.
  *   - Arguments and result as gp_ss_loglik; theta and loglik_out are
@@ -310,6 +316,63 @@ gp_ss_status gp_ss_autotune(gp_ss_model *model, const float *theta, int n_sets,
  * (the _batched calls after their first capture) are not included.
  *   out  host int64, written.  GP_SS_EINVAL if NULL. */
 gp_ss_status gp_ss_launch_count(int64_t *out);
+
+/* A single long series split in time across devices (Section 3.2.5: the
+ * associative combination of the elements of Sarkka & Garcia-Fernandez 2021,
+ * applied to contiguous ranges of the model's chunks).  Every device builds
+ * the same one-series model; device r calls gp_ss_span_element on its chunk
+ * range, the spans' elements are exchanged (an all-gather of a few hundred
+ * bytes per span and row), and gp_ss_span_loglik folds them in time order.
+ *
+ * gp_ss_span_element: the element of chunks [c_begin, c_end) of a model with
+ * one series (FP32 models only), for every row (theta_per_series = 1: one
+ * set, one row; 0: n_sets rows), combined in FP64:
+ *   elem_out  device f64 [rows * (NF + 1)], per row the fields A (d x d,
+ *             row-major), b (d), C (d(d+1)/2, packed upper triangle), eta (d),
+ *             J (packed), then the log-normaliser c; NF = 2d^2 + 3d.  The data
+ *             of the range have likelihood exp(c + eta^T x - x^T J x / 2)
+ *             given the state x entering it, which then leaves it as
+ *             N(A x + b, C); the range starting at chunk 0 has A = 0 and c its
+ *             own log-likelihood.
+ * Returns EUNSUPPORTED for models with more than one series, EINVAL for an
+ * empty or out-of-range chunk range.  Numeric failures as gp_ss_loglik. */
+gp_ss_status gp_ss_span_element(const gp_ss_model *model, const float *theta, int n_sets,
+                                int theta_per_series, int c_begin, int c_end, double *elem_out,
+                                void *cuda_stream);
+
+/* gp_ss_span_loglik: the series' log-likelihood per row from the elements of
+ * n_spans consecutive chunk ranges covering the series in time order, the
+ * first starting at chunk 0.
+ *   span_elems  device f64 [n_spans * n_rows * (NF + 1)], span-major
+ *   loglik_out  device f64 [n_rows] */
+gp_ss_status gp_ss_span_loglik(const gp_ss_model *model, const double *span_elems, int n_spans,
+                               int n_rows, double *loglik_out, void *cuda_stream);
+
+/* Host-only event build of one series, as gp_ss_build_model builds each
+ * series (no CUDA call; for host-side checks and tools).
+ *   n                       measurements; inputs as gp_ss_build_model
+ *   n_events                host, receives 2n (exposures) or n (instantaneous)
+ *   dt_out                  host f64 [2n], gaps between consecutive events
+ *   tag_out                 host u8 [2n], bit 0 measurement event, bits 1-3 slot
+ *   meas_out                host f64 [3n], (y, yerr^2, 1/delta) of each
+ *                           measurement in the order its event comes
+ *                           (1/delta = 1 for an instantaneous measurement)
+ *   n_slots                 host, receives the number of integral-state slots
+ * Returns EINVAL, ESELFOVERLAP or EUNSUPPORTED as gp_ss_build_model. */
+gp_ss_status gp_ss_build_events(int64_t n, const double *t_start, const double *t_end,
+                                const float *y, const float *yerr, const int32_t *instrument,
+                                int64_t *n_events, double *dt_out, uint8_t *tag_out,
+                                double *meas_out, int *n_slots);
+
+/* FP32 FMA throughput of the current device (no counterpart in the paper; a
+ * measurement aid for the roofline of the FP32-bound kernels): a kernel of
+ * independent FMA chains on 8 blocks of 256 threads per SM, timed with CUDA
+ * events on the stream, best of five launches after one warm-up.
+ *   tflops  host, receives 2 x FMAs / second / 1e12
+ *   n_sms   host, receives the device's multiprocessor count
+ * Synchronises the stream.  Allocates (and frees) a few bytes of device
+ * memory. */
+gp_ss_status gp_ss_measure_fp32_peak(double *tflops, int *n_sms, void *cuda_stream);
 
 void gp_ss_free_model(gp_ss_model *model);
 const char *gp_ss_status_string(gp_ss_status status);

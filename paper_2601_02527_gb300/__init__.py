@@ -41,7 +41,8 @@ EXPORTS = ["gp_ss_build_model", "gp_ss_loglik", "gp_ss_loglik_grad", "gp_ss_logl
            "gp_ss_set_chunk_len", "gp_ss_last_error_series", "gp_ss_free_model",
            "gp_ss_status_string", "gp_ss_discretize", "gp_ss_set_timing", "gp_ss_get_timing",
            "gp_ss_loglik_noalloc", "gp_ss_launch_count", "gp_ss_autotune", "gp_ss_condition",
-           "gp_ss_predict"]
+           "gp_ss_predict", "gp_ss_measure_fp32_peak", "gp_ss_span_element",
+           "gp_ss_span_loglik", "gp_ss_build_events"]
 
 PHASES = ["elem", "scan", "grad", "convert", "plain"]
 
@@ -68,7 +69,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("threads_per_series", ctypes.c_int), ("chunk_len", ctypes.c_int),
                 ("ckpt_interval", ctypes.c_int), ("debug_checks", ctypes.c_int),
-                ("chunk_combine", ctypes.c_int), ("step_cache", ctypes.c_int)]
+                ("chunk_combine", ctypes.c_int), ("step_cache", ctypes.c_int),
+                ("combine_precision", ctypes.c_int)]
 
 
 _lib = None
@@ -108,6 +110,10 @@ def load_library(path: str | None = None):
     lib.gp_ss_set_timing.argtypes = [vp, i32]
     lib.gp_ss_loglik_noalloc.argtypes = [vp, vp, i32, i32, vp, vp]
     lib.gp_ss_get_timing.argtypes = [vp, vp, vp]
+    lib.gp_ss_measure_fp32_peak.argtypes = [P(ctypes.c_double), P(i32), vp]
+    lib.gp_ss_span_element.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp]
+    lib.gp_ss_span_loglik.argtypes = [vp, vp, i32, i32, vp, vp]
+    lib.gp_ss_build_events.argtypes = [i64, vp, vp, vp, vp, vp, P(i64), vp, vp, vp, P(i32)]
     _lib = lib
     return lib
 
@@ -143,7 +149,7 @@ class Model:
 
     def __init__(self, terms, offsets, t_start, t_end, y, yerr, instrument=None, layout=0,
                  precision=32, schedule=0, chunk_len=0, combine=0, ckpt_interval=0,
-                 step_cache=0):
+                 step_cache=0, combine_precision=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -161,7 +167,7 @@ class Model:
         inst = None if instrument is None else np.ascontiguousarray(instrument, np.int32)
         spec, self._spec_arr = _spec(self.terms, self.layout)
         opts = _Options(int(precision), int(schedule), 0, int(chunk_len), int(ckpt_interval), 0,
-                        int(combine), int(step_cache))
+                        int(combine), int(step_cache), int(combine_precision))
         h = ctypes.c_void_p()
         self.device = torch.cuda.current_device()
         rc = lib.gp_ss_build_model(ctypes.byref(spec), len(offs) - 1, offs.ctypes.data,
@@ -360,6 +366,35 @@ class Model:
         self.info = self._info()
         return {f: getattr(t, f) for f, _ in _Tuning._fields_}
 
+    def span_element(self, theta, c_begin, c_end, per_series=True, stream=None):
+        """Element of chunks [c_begin, c_end) of this one-series model
+        (gp_ss_span_element): float64 CUDA tensor [rows, 2d^2 + 3d + 1]."""
+        import torch
+        th = self._theta(theta)
+        rows = 1 if per_series else th.shape[0]
+        d = self.info["state_dim"]
+        out = torch.empty(rows, 2 * d * d + 3 * d + 1, dtype=torch.float64, device=th.device)
+        _check(self._lib.gp_ss_span_element(self._h, th.data_ptr(), th.shape[0],
+                                            int(bool(per_series)), int(c_begin), int(c_end),
+                                            out.data_ptr(), _stream_ptr(stream)),
+               "gp_ss_span_element")
+        return out
+
+    def span_loglik(self, span_elems, stream=None):
+        """Log-likelihood per row from the elements of consecutive chunk ranges
+        covering the series ([n_spans, rows, NC] float64 CUDA tensor)."""
+        import torch
+        e = span_elems.contiguous()
+        d = self.info["state_dim"]
+        if e.dim() != 3 or e.shape[2] != 2 * d * d + 3 * d + 1:
+            raise ValueError("span elements must be [n_spans, rows, 2d^2 + 3d + 1]")
+        self._check_out(e, "span_elems", torch.float64, e.numel())
+        out = torch.empty(e.shape[1], dtype=torch.float64, device=e.device)
+        _check(self._lib.gp_ss_span_loglik(self._h, e.data_ptr(), e.shape[0], e.shape[1],
+                                           out.data_ptr(), _stream_ptr(stream)),
+               "gp_ss_span_loglik")
+        return out
+
     def set_chunk_len(self, chunk_len: int):
         _check(self._lib.gp_ss_set_chunk_len(self._h, int(chunk_len)), "gp_ss_set_chunk_len")
         self.info = self._info()
@@ -390,6 +425,36 @@ def launch_count() -> int:
     out = ctypes.c_int64()
     _check(lib.gp_ss_launch_count(ctypes.byref(out)), "gp_ss_launch_count")
     return int(out.value)
+
+
+def measure_fp32_peak(stream=None):
+    """(FP32 FMA TFLOP/s measured on the current device, its SM count)."""
+    lib = load_library()
+    tf, n = ctypes.c_double(), ctypes.c_int()
+    _check(lib.gp_ss_measure_fp32_peak(ctypes.byref(tf), ctypes.byref(n), _stream_ptr(stream)),
+           "gp_ss_measure_fp32_peak")
+    return float(tf.value), int(n.value)
+
+
+def build_events(t_start, t_end, y, yerr, instrument=None):
+    """Host-only event build of one series (gp_ss_build_events): (dt float64,
+    tag uint8, meas float64 [n, 3] in event order, n_slots)."""
+    lib = load_library()
+    ts = np.ascontiguousarray(t_start, np.float64)
+    te = np.ascontiguousarray(t_end, np.float64)
+    yy = np.ascontiguousarray(y, np.float32)
+    ye = np.ascontiguousarray(yerr, np.float32)
+    inst = None if instrument is None else np.ascontiguousarray(instrument, np.int32)
+    n = len(ts)
+    dt = np.empty(max(2 * n, 1), np.float64)
+    tag = np.empty(max(2 * n, 1), np.uint8)
+    meas = np.empty((max(n, 1), 3), np.float64)
+    ne, ns = ctypes.c_int64(), ctypes.c_int()
+    _check(lib.gp_ss_build_events(n, ts.ctypes.data, te.ctypes.data, yy.ctypes.data,
+                                  ye.ctypes.data, None if inst is None else inst.ctypes.data,
+                                  ctypes.byref(ne), dt.ctypes.data, tag.ctypes.data,
+                                  meas.ctypes.data, ctypes.byref(ns)), "gp_ss_build_events")
+    return dt[:ne.value], tag[:ne.value], meas[:n], ns.value
 
 
 def discretize(terms, layout, n_slots, theta_row, dt, stream=None):

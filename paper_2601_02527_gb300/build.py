@@ -20,7 +20,8 @@ OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgpss.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["gpss_api.cu", "gpss_inst_t1.cu", "gpss_inst_t2.cu", "gpss_inst_t2s3.cu",
-           "gpss_inst_t2l1.cu", "gpss_inst_i.cu", "gpss_inst_p.cu"]
+           "gpss_inst_t2l1.cu", "gpss_inst_i.cu", "gpss_inst_p.cu", "gpss_c64_t1.cu",
+           "gpss_c64_t2.cu", "gpss_c64_t3.cu"]
 
 
 def nvcc_path() -> str:
@@ -35,8 +36,8 @@ def _flags(extra=()):
             *ARCH, *extra]
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(OBJDIR, os.path.splitext(src)[0] + ".o")
+def _compile(src: str, extra, objdir=OBJDIR) -> str:
+    obj = os.path.join(objdir, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc_path(), "-c", os.path.join(CSRC, src), "-o", obj, *_flags(extra)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -53,22 +54,26 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile every CUDA translation unit and link libgpss.so; returns its path."""
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, extra=(), out: str = LIB) -> str:
+    """Compile every CUDA translation unit and link libgpss.so (or ``out``,
+    with its objects beside it, e.g. a build with extra -D flags); returns
+    its path."""
+    if out == LIB and not force and not _stale():
         return LIB
-    os.makedirs(OBJDIR, exist_ok=True)
+    objdir = OBJDIR if out == LIB else os.path.join(os.path.dirname(os.path.abspath(out)),
+                                                    "_objs")
+    os.makedirs(objdir, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, extra, objdir), SOURCES))
+    tmp = out + f".tmp{os.getpid()}"
     cmd = [nvcc_path(), "-shared", "-o", tmp, *objs, *ARCH, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, out)
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", out)
+    return out
 
 
 if __name__ == "__main__":

@@ -27,6 +27,16 @@ OpTable ops_1_0_0();
 OpTable ops_2_0_0();
 OpTable ops_prod1();
 OpTable ops_prod2();
+CombineOps comb64_1_0_0();
+CombineOps comb64_1_1_0();
+CombineOps comb64_1_2_0();
+CombineOps comb64_1_3_0();
+CombineOps comb64_2_0_0();
+CombineOps comb64_3_0_0();
+CombineOps comb64_2_1_0();
+CombineOps comb64_2_2_0();
+CombineOps comb64_2_1_1();
+CombineOps comb64_2_3_0();
 
 __global__ void k_series_sum(int n_out, int per_series, int n_series, int n_chunks,
                              const int32_t *__restrict__ ch_first,
@@ -93,6 +103,28 @@ __global__ void k_exposure_grad(int n_rows, int n_series, const int64_t *__restr
   out[2 * idx + 1] = gt(ke) - wpart;
 }
 
+// FP32 FMA throughput probe: eight independent FMA chains per thread, iters
+// steps each (2 FLOP per FMA).  The result is stored only when it equals a
+// value the chains never reach, which keeps the compiler from removing them.
+__global__ void __launch_bounds__(256) k_fma_peak(float *__restrict__ sink, int iters, float b,
+                                                  float c) {
+  float a0 = threadIdx.x * 1e-7f, a1 = a0 + 1e-7f, a2 = a0 + 2e-7f, a3 = a0 + 3e-7f;
+  float a4 = a0 + 4e-7f, a5 = a0 + 5e-7f, a6 = a0 + 6e-7f, a7 = a0 + 7e-7f;
+#pragma unroll 4
+  for (int i = 0; i < iters; ++i) {
+    a0 = fmaf(a0, b, c);
+    a1 = fmaf(a1, b, c);
+    a2 = fmaf(a2, b, c);
+    a3 = fmaf(a3, b, c);
+    a4 = fmaf(a4, b, c);
+    a5 = fmaf(a5, b, c);
+    a6 = fmaf(a6, b, c);
+    a7 = fmaf(a7, b, c);
+  }
+  const float r = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+  if (r == -12345.0f) sink[blockIdx.x] = r;
+}
+
 // Measurement records (y, r0, w) -> the float4 layout the chunk kernels read.
 __global__ void k_pack_meas(const float *__restrict__ in3, float4 *__restrict__ out, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,6 +159,8 @@ namespace {
 
 constexpr int kMaxSlots = 3;
 constexpr int kDefaultChunk = 256;
+// arithmetic of the cross-chunk combination when the options leave it open
+constexpr int kDefaultCombPrec = 32;
 // largest step-scalar cache a gradient call allocates (bytes)
 constexpr size_t kDcacheMax = (size_t)8 << 30;
 
@@ -178,6 +212,7 @@ struct gp_ss_model {
   int combine = 0;  // cross-chunk combination: 0 auto, 1 sequential per series, 2 tree
   int ckpt_interval = 32;  // events per recomputation segment of the gradient
   int step_cache = 0;      // 0 auto, 1 never keep the gradient's step scalars
+  int comb_prec = 32;      // arithmetic of the cross-chunk combination: 32 or 64
   int64_t *d_ch_ev0 = nullptr, *d_ch_meas0 = nullptr;
   int32_t *d_ch_len = nullptr, *d_ch_series = nullptr, *d_ch_first = nullptr;
   std::vector<int32_t> ch_first;  // host copy: first chunk of each series
@@ -216,27 +251,50 @@ struct DeviceGuard {
 
 bool pick_ops(int n_terms, int n_slots, int layout, OpTable *o) {
   if (n_slots == 0) {  // instantaneous measurements only
-    if (n_terms == 1) *o = gpss::ops_1_0_0();
-    else if (n_terms == 2) *o = gpss::ops_2_0_0();
-    else return false;
+    if (n_terms == 1) {
+      *o = gpss::ops_1_0_0();
+      o->comb64 = gpss::comb64_1_0_0();
+    } else if (n_terms == 2) {
+      *o = gpss::ops_2_0_0();
+      o->comb64 = gpss::comb64_2_0_0();
+    } else {
+      return false;
+    }
     return true;
   }
   if (n_terms == 1) {
-    if (n_slots == 1) *o = gpss::ops_1_1_0();
-    else if (n_slots == 2) *o = gpss::ops_1_2_0();
-    else if (n_slots == 3) *o = gpss::ops_1_3_0();
-    else return false;
+    if (n_slots == 1) {
+      *o = gpss::ops_1_1_0();
+      o->comb64 = gpss::comb64_1_1_0();
+    } else if (n_slots == 2) {
+      *o = gpss::ops_1_2_0();
+      o->comb64 = gpss::comb64_1_2_0();
+    } else if (n_slots == 3) {
+      *o = gpss::ops_1_3_0();
+      o->comb64 = gpss::comb64_1_3_0();
+    } else {
+      return false;
+    }
     return true;
   }
   if (n_terms == 2 && layout == 0) {
-    if (n_slots == 1) *o = gpss::ops_2_1_0();
-    else if (n_slots == 2) *o = gpss::ops_2_2_0();
-    else if (n_slots == 3) *o = gpss::ops_2_3_0();
-    else return false;
+    if (n_slots == 1) {
+      *o = gpss::ops_2_1_0();
+      o->comb64 = gpss::comb64_2_1_0();
+    } else if (n_slots == 2) {
+      *o = gpss::ops_2_2_0();
+      o->comb64 = gpss::comb64_2_2_0();
+    } else if (n_slots == 3) {
+      *o = gpss::ops_2_3_0();
+      o->comb64 = gpss::comb64_2_3_0();
+    } else {
+      return false;
+    }
     return true;
   }
   if (n_terms == 2 && layout == 1 && n_slots == 1) {
     *o = gpss::ops_2_1_1();
+    o->comb64 = gpss::comb64_2_1_1();
     return true;
   }
   return false;
@@ -689,6 +747,10 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
   if (n_vch64 > INT32_MAX / 8) return GP_SS_EUNSUPPORTED;
   const int n_vch = (int)n_vch64;
   const int SD = o.D + o.NP;
+  // the cross-chunk combination's arithmetic (its state, information and
+  // partial-combination buffers hold eb bytes per value)
+  const gpss::CombineOps &cb = m->comb_prec == 64 ? o.comb64 : o.comb32;
+  const size_t eb = (size_t)cb.elem_bytes;
   // cross-chunk combination: warp-level scans plus a scan of warp totals
   // (default), or the sequential fold with one thread per series
   bool tree = m->combine != 1;
@@ -701,8 +763,8 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
     bufs.push_back(*p);
     return true;
   };
-  float *ef = nullptr, *state_end = nullptr, *info = nullptr, *adj = nullptr, *ckpt = nullptr,
-        *scratch = nullptr, *gpart = nullptr, *tabs = nullptr;
+  float *ef = nullptr, *adj = nullptr, *ckpt = nullptr, *gpart = nullptr, *tabs = nullptr;
+  void *state_end = nullptr, *info = nullptr, *scratch = nullptr;
   double *ed = nullptr, *ll_part = nullptr;
   gp_ss_status res = GP_SS_OK;
   do {
@@ -746,7 +808,7 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       }
       if (res) break;
     }
-    if ((grad || tree) && !grab((void **)&state_end, (size_t)SD * n_vch * sizeof(float))) {
+    if ((grad || tree) && !grab(&state_end, (size_t)SD * n_vch * eb)) {
       res = GP_SS_ENOMEM;
       break;
     }
@@ -755,17 +817,16 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       break;
     }
     // warp-level combination buffers
-    float *pre_local = nullptr, *suf_local = nullptr, *wtot = nullptr, *wpre = nullptr,
-          *wsuf = nullptr;
+    void *pre_local = nullptr, *suf_local = nullptr, *wtot = nullptr, *wpre = nullptr,
+         *wsuf = nullptr;
     const int n_w = n_vch / 32;
     if (tree && (!grab((void **)&ll_part, (size_t)n_vch * sizeof(double)) ||
-                 !grab((void **)&pre_local, (size_t)o.NF * n_vch * sizeof(float)) ||
-                 !grab((void **)&wtot, (size_t)o.NF * n_w * sizeof(float)) ||
-                 !grab((void **)&wpre, (size_t)o.NF * n_w * sizeof(float)) ||
-                 !grab((void **)&scratch, o.warp_scratch(n_vch) * sizeof(float)) ||
-                 (grad && (!grab((void **)&info, (size_t)SD * n_vch * sizeof(float)) ||
-                           !grab((void **)&suf_local, (size_t)o.NF * n_vch * sizeof(float)) ||
-                           !grab((void **)&wsuf, (size_t)o.NF * n_w * sizeof(float)))))) {
+                 !grab(&pre_local, (size_t)o.NF * n_vch * eb) ||
+                 !grab(&wtot, (size_t)o.NF * n_w * eb) || !grab(&wpre, (size_t)o.NF * n_w * eb) ||
+                 !grab(&scratch, cb.warp_scratch(n_vch) * eb) ||
+                 (grad && (!grab(&info, (size_t)SD * n_vch * eb) ||
+                           !grab(&suf_local, (size_t)o.NF * n_vch * eb) ||
+                           !grab(&wsuf, (size_t)o.NF * n_w * eb))))) {
       res = GP_SS_ENOMEM;
       break;
     }
@@ -773,15 +834,16 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       PhaseTimer pt(m, st, 1);
       cudaError_t e;
       if (!tree) {
-        e = o.scan(dm, n_out, per_series, ef, ed, n_vch, state_end, adj, ll, grad ? 1 : 0,
-                   m->d_err, st);
+        e = cb.scan(dm, n_out, per_series, ef, ed, n_vch, state_end, adj, ll, grad ? 1 : 0,
+                    m->d_err, st);
       } else {
         // few warps per series: fold warp totals sequentially; else scan them
         const int fold = m->max_chunks_per_series <= 16 * 32 ? 1 : 0;
-        e = o.warp_combine(dm, ef, n_vch, pre_local, suf_local, wtot, wpre, wsuf, scratch,
-                           state_end, info, grad ? 1 : 0, fold, n_out, per_series, st);
+        e = cb.warp_combine(dm, ef, n_vch, pre_local, suf_local, wtot, wpre, wsuf, scratch,
+                            state_end, info, grad ? 1 : 0, fold, n_out, per_series, st);
         if (e == cudaSuccess)
-          e = o.finish(dm, n_vch, per_series, ef, ed, state_end, info, adj, ll_part, m->d_err, st);
+          e = cb.finish(dm, n_vch, per_series, ef, ed, state_end, info, adj, ll_part, m->d_err,
+                        st);
       }
       if (e != cudaSuccess) {
         res = GP_SS_ECUDA;
@@ -805,8 +867,8 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
       }
       PhaseTimer pt(m, st, 2);
       const gpss::PredPlan none;
-      if (o.grad(dm, theta, n_vch, per_series, state_end, adj, ckpt, gpart, m->d_err, tabs, rbuf,
-                 dcache, ck, gdt, gwe, cond, pred ? *pred : none, st)) {
+      if (o.grad(dm, theta, n_vch, per_series, state_end, eb == 8 ? 1 : 0, adj, ckpt, gpart,
+                 m->d_err, tabs, rbuf, dcache, ck, gdt, gwe, cond, pred ? *pred : none, st)) {
         res = GP_SS_ECUDA;
         break;
       }
@@ -933,6 +995,8 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
       o.ckpt_interval != 32 && o.ckpt_interval != 64)
     return GP_SS_EINVAL;
   if (o.step_cache != 0 && o.step_cache != 1) return GP_SS_EINVAL;
+  if (o.combine_precision != 0 && o.combine_precision != 32 && o.combine_precision != 64)
+    return GP_SS_EINVAL;
   if (o.schedule < 0 || o.schedule > 3 || o.chunk_combine < 0 || o.chunk_combine > 2)
     return GP_SS_EINVAL;
   if (series_offsets[0] != 0) return GP_SS_EINVAL;
@@ -953,6 +1017,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   m->combine = o.chunk_combine;
   m->ckpt_interval = o.ckpt_interval == 0 ? 32 : o.ckpt_interval;
   m->step_cache = o.step_cache;
+  m->comb_prec = o.combine_precision == 0 ? kDefaultCombPrec : o.combine_precision;
   m->n_params = 1;
   for (int t = 0; t < spec->n_terms; ++t) {
     m->kinds[t] = spec->terms[t];
@@ -1049,6 +1114,7 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   m->n_slots = n_slots;
   if (m->product) {
     m->ops = m->n_terms == 1 ? gpss::ops_prod1() : gpss::ops_prod2();
+    m->ops.comb64 = m->n_terms == 1 ? gpss::comb64_2_0_0() : gpss::comb64_3_0_0();
   } else if (n_slots > kMaxSlots || !pick_ops(m->n_terms, n_slots, m->layout, &m->ops)) {
     free_model_buffers(m);
     delete m;
@@ -1414,6 +1480,93 @@ gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *m, const float *theta_hos
   return res;
 }
 
+gp_ss_status gp_ss_span_element(const gp_ss_model *m, const float *theta, int n_sets,
+                                int theta_per_series, int c_begin, int c_end, double *elem_out,
+                                void *cuda_stream) {
+  gp_ss_status s = check_call(m, theta, n_sets, theta_per_series, elem_out);
+  if (s) return s;
+  if (m->n_series != 1 || m->precision != 32) return GP_SS_EUNSUPPORTED;
+  if (c_begin < 0 || c_end > m->n_chunks || c_begin >= c_end) return GP_SS_EINVAL;
+  DeviceGuard g(m->device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const OpTable &o = m->ops;
+  const int rows = theta_per_series ? 1 : n_sets;
+  const int64_t n_vch64 = (int64_t)rows * m->n_chunks;
+  if (n_vch64 > INT32_MAX / 8) return GP_SS_EUNSUPPORTED;
+  const int n_vch = (int)n_vch64;
+  if ((s = prepare_err(m, rows, st))) return s;
+  const gpss::DevModel dm = dev_view(m);
+  float *ef = nullptr, *tabs = nullptr;
+  double *ed = nullptr, *scratch = nullptr;
+  gp_ss_status res = GP_SS_OK;
+  if (scratch_alloc(m, (void **)&ef, (size_t)o.NF * n_vch * sizeof(float), st) ||
+      scratch_alloc(m, (void **)&ed, (size_t)o.ND * n_vch * sizeof(double), st) ||
+      scratch_alloc(m, (void **)&tabs, (size_t)n_sets * o.NT * gpss::TAB_TERM * sizeof(float),
+                    st) ||
+      scratch_alloc(m, (void **)&scratch, o.span_scratch(c_end - c_begin, rows) * sizeof(double),
+                    st)) {
+    res = GP_SS_ENOMEM;
+  } else if (o.tables(theta, n_sets, m->n_params, m->kinds[0], m->kinds[1], tabs, st) ||
+             o.elem(dm, theta, n_vch, theta_per_series, ef, ed, m->d_err, tabs, nullptr, 0,
+                    nullptr, c_begin, c_end - c_begin, st) ||
+             o.span_element(ef, ed, n_vch, m->n_chunks, c_begin, c_end, rows, scratch, elem_out,
+                            st)) {
+    res = GP_SS_ECUDA;
+  }
+  void *bufs[] = {ef, ed, tabs, scratch};
+  for (void *p : bufs)
+    if (p) cudaFreeAsync(p, st);
+  return res;
+}
+
+gp_ss_status gp_ss_span_loglik(const gp_ss_model *m, const double *span_elems, int n_spans,
+                               int n_rows, double *loglik_out, void *cuda_stream) {
+  if (!m || !span_elems || !loglik_out || n_spans < 1 || n_rows < 1) return GP_SS_EINVAL;
+  if (m->n_series != 1 || m->precision != 32) return GP_SS_EUNSUPPORTED;
+  DeviceGuard g(m->device);
+  if (m->ops.span_fold(span_elems, n_spans, n_rows, loglik_out, (cudaStream_t)cuda_stream))
+    return GP_SS_ECUDA;
+  return GP_SS_OK;
+}
+
+gp_ss_status gp_ss_build_events(int64_t n, const double *t_start, const double *t_end,
+                                const float *y, const float *yerr, const int32_t *instrument,
+                                int64_t *n_events, double *dt_out, uint8_t *tag_out,
+                                double *meas_out, int *n_slots) {
+  if (n < 0 || !n_events || !n_slots || (n > 0 && (!t_start || !t_end || !y || !yerr ||
+                                                  !dt_out || !tag_out || !meas_out)))
+    return GP_SS_EINVAL;
+  if (n == 0) {
+    *n_events = 0;
+    *n_slots = 0;
+    return GP_SS_OK;
+  }
+  int64_t n_inst = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int kd = meas_kind(t_start[i], t_end[i], y[i], yerr[i]);
+    if (kd < 0) return GP_SS_EINVAL;
+    n_inst += kd;
+  }
+  if (n_inst != 0 && n_inst != n) return GP_SS_EUNSUPPORTED;
+  const int64_t ne = n_inst ? n : 2 * n;
+  std::vector<float> dt(ne);
+  std::vector<uint8_t> tag(ne);
+  std::vector<float4> meas(n + 1);
+  std::vector<double> dt64(ne), meas64(3 * n), tev(ne);
+  std::vector<int2> mev(n);
+  SeriesOut so;
+  build_series(0, n, 0, t_start, t_end, y, yerr, instrument, dt.data(), tag.data(), meas.data(),
+               dt64.data(), meas64.data(), mev.data(), tev.data(), &so);
+  if (so.st) return so.st;
+  if (so.n_slots > kMaxSlots) return GP_SS_EUNSUPPORTED;
+  *n_events = ne;
+  *n_slots = so.n_slots;
+  std::memcpy(dt_out, dt64.data(), ne * sizeof(double));
+  std::memcpy(tag_out, tag.data(), ne);
+  std::memcpy(meas_out, meas64.data(), 3 * n * sizeof(double));
+  return GP_SS_OK;
+}
+
 gp_ss_status gp_ss_last_error_series(const gp_ss_model *m, int64_t *first_bad_series,
                                      gp_ss_status *code) {
   if (!m || !first_bad_series || !code) return GP_SS_EINVAL;
@@ -1433,6 +1586,44 @@ gp_ss_status gp_ss_last_error_series(const gp_ss_model *m, int64_t *first_bad_se
       break;
     }
   return GP_SS_OK;
+}
+
+gp_ss_status gp_ss_measure_fp32_peak(double *tflops, int *n_sms, void *cuda_stream) {
+  if (!tflops || !n_sms) return GP_SS_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return GP_SS_ECUDA;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  float *sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int blocks = sms * 8, threads = 256, iters = 1 << 16;
+  gp_ss_status res = GP_SS_OK;
+  if (cudaMalloc((void **)&sink, (size_t)blocks * sizeof(float)) != cudaSuccess)
+    return GP_SS_ENOMEM;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    res = GP_SS_ECUDA;
+  } else {
+    float best = 1e30f;
+    for (int r = 0; r < 6 && !res; ++r) {
+      cudaEventRecord(e0, st);
+      gpss::k_fma_peak<<<blocks, threads, 0, st>>>(sink, iters, 0.999999f, 1e-7f);
+      GPSS_COUNT_LAUNCH();
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        res = GP_SS_ECUDA;
+      else if (r > 0)
+        best = std::min(best, ms);  // the first launch warms up
+    }
+    if (!res) *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+    *n_sms = sms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(sink);
+  return res;
 }
 
 gp_ss_status gp_ss_launch_count(int64_t *out) {
@@ -1654,8 +1845,9 @@ extern "C" gp_ss_status gp_ss_loglik_noalloc(const gp_ss_model *m, const float *
              m->n_chunks, st) !=
           cudaSuccess)
     return GP_SS_ECUDA;
-  if (o.scan(dm, n_out, theta_per_series, ef, ed, n_vch, nullptr, nullptr, loglik_out, 0,
-             nullptr, st) != cudaSuccess)
+  const gpss::CombineOps &cb = m->comb_prec == 64 ? o.comb64 : o.comb32;
+  if (cb.scan(dm, n_out, theta_per_series, ef, ed, n_vch, nullptr, nullptr, loglik_out, 0,
+              nullptr, st) != cudaSuccess)
     return GP_SS_ECUDA;
   return GP_SS_OK;
 }

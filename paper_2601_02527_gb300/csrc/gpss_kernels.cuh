@@ -115,8 +115,8 @@ GPSS_D Disc<float> dcache_term(const float (&x)[DcW<NT>::W], int t) {
 }
 
 // log of an innovation variance: computed at the filter's precision, summed in FP64
-GPSS_D double glog(float x) { return (double)logf(x); }
-GPSS_D double glog(double x) { return log(x); }
+GPSS_HD double glog(float x) { return (double)logf(x); }
+GPSS_HD double glog(double x) { return log(x); }
 
 template <class F> GPSS_D F load_dt(const DevModel &M, int64_t k);
 template <> GPSS_D float load_dt<float>(const DevModel &M, int64_t k) { return __ldg(M.dt + k); }
@@ -439,6 +439,86 @@ GPSS_D void store_elem(float *dst, int n_vch, int vc, const float (&A)[S::D][S::
   }
 }
 
+// One event of a chunk element: the filter run from an unknown incoming state
+// x, with mean A x + b, covariance C, information (eta, J) about x from the
+// chunk's measurements so far, gamma = sum c^2/S and sum log S (the element
+// of Sarkka & Garcia-Fernandez 2021 for a stretch of events, Section 3.2.5).
+// Predict with the step's blocks (A <- Phi~ A, b <- Phi~ b, C <- Phi~ C
+// Phi~^T + Q~), then reset the slot at an exposure start or update with the
+// measurement (y, r0, w) at an end.
+template <class S, class F>
+GPSS_HD void elem_event(const Blocks<F> *B, uint8_t tag, F y, F r0, F w, F s2,
+                        F (&A)[S::D][S::D], F *b, F *C, F *eta, F *J, double &gam, double &ld,
+                        int &n_end, bool &bad) {
+  constexpr int D = S::D;
+#pragma unroll
+  for (int col = 0; col < D; ++col) {
+    F v[D], o[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = A[i][col];
+    apply_phi<S>(B, v, o);
+#pragma unroll
+    for (int i = 0; i < D; ++i) A[i][col] = o[i];
+  }
+  {
+    F o[D];
+    apply_phi<S>(B, b, o);
+#pragma unroll
+    for (int i = 0; i < D; ++i) b[i] = o[i];
+  }
+  predict_cov<S>(B, C);
+  const int j = (tag >> 1) & 7;
+  if (!(tag & 1)) {
+    reset_slot<S>(j, b, C);
+#pragma unroll
+    for (int zi = 2 * S::NT; zi < D; ++zi) {
+      const bool hit = (S::zslot(zi) == j);
+#pragma unroll
+      for (int col = 0; col < D; ++col) A[zi][col] = hit ? F(0) : A[zi][col];
+    }
+    return;
+  }
+  F u[D], hu, hb;
+  obs_project<S>(j, w, b, C, u, hu, hb);
+  const F Sv = hu + r0 + s2;
+  const F cc = y - hb;
+  F g[D];  // h^T A
+#pragma unroll
+  for (int col = 0; col < D; ++col) {
+    F acc = F(0);
+    if constexpr (S::NS == 0) {
+#pragma unroll
+      for (int t = 0; t < S::NT; ++t) acc += A[2 * t][col];
+      g[col] = acc;
+    } else {
+#pragma unroll
+      for (int zi = 2 * S::NT; zi < D; ++zi) acc += (S::zslot(zi) == j) ? A[zi][col] : F(0);
+      g[col] = acc * w;
+    }
+  }
+  bad |= !(Sv > F(0));
+  const F iS = F(1) / Sv;
+  const F ci = cc * iS;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    eta[i] += g[i] * ci;
+#pragma unroll
+    for (int jj = i; jj < D; ++jj) J[S::pk(i, jj)] += g[i] * g[jj] * iS;
+  }
+  gam += (double)(cc * ci);
+  ld += glog(Sv);
+  ++n_end;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const F Ki = u[i] * iS;
+#pragma unroll
+    for (int col = 0; col < D; ++col) A[i][col] -= Ki * g[col];
+    b[i] += Ki * cc;
+#pragma unroll
+    for (int jj = i; jj < D; ++jj) C[S::pk(i, jj)] -= u[i] * u[jj] * iS;
+  }
+}
+
 // With pck set, the partial element of the chunk's first events is also saved
 // at the start of every gradient segment but the first (segments of ck
 // events, aligned to the chunk's end): record j at pck + j (NF + 1) n_vch,
@@ -540,74 +620,7 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
           r[32 * v] = make_float4(x[4 * v], x[4 * v + 1], x[4 * v + 2], x[4 * v + 3]);
       }
     }
-    // A <- Phi~ A (column by column), b <- Phi~ b, C <- Phi~ C Phi~^T + Q~
-#pragma unroll
-    for (int col = 0; col < D; ++col) {
-      F v[D], o[D];
-#pragma unroll
-      for (int i = 0; i < D; ++i) v[i] = A[i][col];
-      apply_phi<S>(B, v, o);
-#pragma unroll
-      for (int i = 0; i < D; ++i) A[i][col] = o[i];
-    }
-    {
-      F o[D];
-      apply_phi<S>(B, b, o);
-#pragma unroll
-      for (int i = 0; i < D; ++i) b[i] = o[i];
-    }
-    predict_cov<S>(B, C);
-    const int j = (tag >> 1) & 7;
-    if (!(tag & 1)) {
-      reset_slot<S>(j, b, C);
-#pragma unroll
-      for (int zi = 2 * S::NT; zi < D; ++zi) {
-        const bool hit = (S::zslot(zi) == j);
-#pragma unroll
-        for (int col = 0; col < D; ++col) A[zi][col] = hit ? F(0) : A[zi][col];
-      }
-    } else {
-      const F y = q.x, r0 = q.y, w = q.z;
-      F u[D], hu, hb;
-      obs_project<S>(j, w, b, C, u, hu, hb);
-      const F Sv = hu + r0 + s2;
-      const F cc = y - hb;
-      F g[D];  // h^T A
-#pragma unroll
-      for (int col = 0; col < D; ++col) {
-        F acc = F(0);
-        if constexpr (S::NS == 0) {
-#pragma unroll
-          for (int t = 0; t < S::NT; ++t) acc += A[2 * t][col];
-          g[col] = acc;
-        } else {
-#pragma unroll
-          for (int zi = 2 * S::NT; zi < D; ++zi) acc += (S::zslot(zi) == j) ? A[zi][col] : F(0);
-          g[col] = acc * w;
-        }
-      }
-      bad |= !(Sv > F(0));
-      const F iS = F(1) / Sv;
-      const F ci = cc * iS;
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        eta[i] += g[i] * ci;
-#pragma unroll
-        for (int jj = i; jj < D; ++jj) J[S::pk(i, jj)] += g[i] * g[jj] * iS;
-      }
-      gam += (double)(cc * ci);
-      ld += glog(Sv);
-      ++n_end;
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        const F Ki = u[i] * iS;
-#pragma unroll
-        for (int col = 0; col < D; ++col) A[i][col] -= Ki * g[col];
-        b[i] += Ki * cc;
-#pragma unroll
-        for (int jj = i; jj < D; ++jj) C[S::pk(i, jj)] -= u[i] * u[jj] * iS;
-      }
-    }
+    elem_event<S, F>(B, tag, q.x, q.y, q.z, s2, A, b, C, eta, J, gam, ld, n_end, bad);
   }
   store_elem<S>(ef, n_vch, vc, A, b, C, eta, J);
   ed[vc] = gam;
@@ -634,34 +647,34 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
 // ---------------------------------------------------------------------------
 // Marginal log-likelihood of a chunk's data given N(m, P) for the state
 // entering it, from the chunk's information (eta, J), gamma = sum c^2/S and
-// sum log S over its n_end measurements.
-template <class S>
-GPSS_HD double chunk_loglik(const float *m, const float *P, const float *eta, const float *J,
-                           double gam, double ld, double ne) {
+// sum log S over its n_end measurements; arithmetic of T.
+template <class S, class T = float>
+GPSS_HD double chunk_loglik(const T *m, const T *P, const T *eta, const T *J, double gam,
+                            double ld, double ne) {
   constexpr int D = S::D;
-  float X[D][D], R[D][D];
-  float u[D];
+  T X[D][D], R[D][D];
+  T u[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    float jm = 0.f;
+    T jm = T(0);
 #pragma unroll
     for (int k = 0; k < D; ++k) jm += J[S::pk(i, k)] * m[k];
     u[i] = eta[i] - jm;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      float acc = (i == j) ? 1.f : 0.f;
+      T acc = (i == j) ? T(1) : T(0);
 #pragma unroll
       for (int k = 0; k < D; ++k) acc += P[S::pk(i, k)] * J[S::pk(k, j)];
       X[i][j] = acc;
       R[i][j] = P[S::pk(i, j)];
     }
   }
-  const float logdet = solve_inplace<D, D, float>(X, R);  // R = (I + P J)^{-1} P
-  float etam = 0.f, mJm = 0.f, uWu = 0.f;
+  const T logdet = solve_inplace<D, D, T>(X, R);  // R = (I + P J)^{-1} P
+  T etam = T(0), mJm = T(0), uWu = T(0);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     etam += eta[i] * m[i];
-    float jm = 0.f, wu = 0.f;
+    T jm = T(0), wu = T(0);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       jm += J[S::pk(i, k)] * m[k];
@@ -670,91 +683,90 @@ GPSS_HD double chunk_loglik(const float *m, const float *P, const float *eta, co
     mJm += m[i] * jm;
     uWu += u[i] * wu;
   }
-  const double quad = gam + (double)(-2.f * etam + mJm - uWu);
+  const double quad = gam + (double)(T(-2) * etam + mJm - uWu);
   return -0.5 * (ld + ne * LOG_2PI + (double)logdet + quad);
 }
 
 // Adjoint of the log-likelihood of all later data with respect to the
 // filtered state (m, P), given their information (eta, J) about it:
 // lambda = (I + J P)^{-1} (eta - J m), Lambda = (lambda lambda^T - (I + J P)^{-1} J) / 2.
-template <class S>
-GPSS_HD void boundary_adjoint(const float *m, const float *P, const float *eta, const float *J,
-                             float *lam, float *Lam) {
+template <class S, class T = float>
+GPSS_HD void boundary_adjoint(const T *m, const T *P, const T *eta, const T *J, float *lam,
+                              float *Lam) {
   constexpr int D = S::D;
-  float X[D][D], R[D][D + 1];
+  T X[D][D], R[D][D + 1];
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    float jm = 0.f;
+    T jm = T(0);
 #pragma unroll
     for (int k = 0; k < D; ++k) jm += J[S::pk(i, k)] * m[k];
     R[i][D] = eta[i] - jm;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      float acc = (i == j) ? 1.f : 0.f;
+      T acc = (i == j) ? T(1) : T(0);
 #pragma unroll
       for (int k = 0; k < D; ++k) acc += J[S::pk(i, k)] * P[S::pk(k, j)];
       X[i][j] = acc;
       R[i][j] = J[S::pk(i, j)];
     }
   }
-  solve_inplace<D, D + 1, float>(X, R);
+  solve_inplace<D, D + 1, T>(X, R);
 #pragma unroll
-  for (int i = 0; i < D; ++i) lam[i] = R[i][D];
+  for (int i = 0; i < D; ++i) lam[i] = (float)R[i][D];
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = i; j < D; ++j)
-      Lam[S::pk(i, j)] = 0.5f * (lam[i] * lam[j] - 0.5f * (R[i][j] + R[j][i]));
+      Lam[S::pk(i, j)] = (float)(T(0.5) * (R[i][D] * R[j][D] - T(0.5) * (R[i][j] + R[j][i])));
 }
 
 template <class S>
 GPSS_D void load_elem(const float *ef, int n_vch, int vc, float (&A)[S::D][S::D], float *b, float *C,
                       float *eta, float *J) {
-  using L = ElemLayout<S>;
-  constexpr int D = S::D;
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-#pragma unroll
-    for (int j = 0; j < D; ++j) A[i][j] = ef[(size_t)(L::A + i * D + j) * n_vch + vc];
-    b[i] = ef[(size_t)(L::B + i) * n_vch + vc];
-    eta[i] = ef[(size_t)(L::ETA + i) * n_vch + vc];
-  }
-#pragma unroll
-  for (int i = 0; i < S::NP; ++i) {
-    C[i] = ef[(size_t)(L::C + i) * n_vch + vc];
-    J[i] = ef[(size_t)(L::J + i) * n_vch + vc];
-  }
+  load_elem_t<S, float, float>(ef, (size_t)n_vch, (size_t)vc, A, b, C, eta, J);
 }
 
-template <class S>
-GPSS_D void store_rec(float *dst, int n_vch, int vc, const float *v, const float *P) {
+// State / adjoint records (vector D | packed NP), stride n_vch, stored as U
+// and held as T.
+template <class S, class U, class T>
+GPSS_D void store_rec(U *dst, int n_vch, int vc, const T *v, const T *P) {
 #pragma unroll
-  for (int i = 0; i < S::D; ++i) dst[(size_t)i * n_vch + vc] = v[i];
+  for (int i = 0; i < S::D; ++i) dst[(size_t)i * n_vch + vc] = (U)v[i];
 #pragma unroll
-  for (int i = 0; i < S::NP; ++i) dst[(size_t)(S::D + i) * n_vch + vc] = P[i];
+  for (int i = 0; i < S::NP; ++i) dst[(size_t)(S::D + i) * n_vch + vc] = (U)P[i];
 }
 
+template <class S, class U, class T>
+GPSS_D void load_rec(const U *src, int n_vch, int vc, T *v, T *P) {
+#pragma unroll
+  for (int i = 0; i < S::D; ++i) v[i] = (T)src[(size_t)i * n_vch + vc];
+#pragma unroll
+  for (int i = 0; i < S::NP; ++i) P[i] = (T)src[(size_t)(S::D + i) * n_vch + vc];
+}
+
+// A filtered-state record that is FP32 or FP64 (the combination's
+// precision), read as FP32.
 template <class S>
-GPSS_D void load_rec(const float *src, int n_vch, int vc, float *v, float *P) {
-#pragma unroll
-  for (int i = 0; i < S::D; ++i) v[i] = src[(size_t)i * n_vch + vc];
-#pragma unroll
-  for (int i = 0; i < S::NP; ++i) P[i] = src[(size_t)(S::D + i) * n_vch + vc];
+GPSS_D void load_state_f(const void *src, int se64, int n_vch, int vc, float *v, float *P) {
+  if (se64)
+    load_rec<S>(static_cast<const double *>(src), n_vch, vc, v, P);
+  else
+    load_rec<S>(static_cast<const float *>(src), n_vch, vc, v, P);
 }
 
 // Sequential schedule of the cross-chunk combination: one thread per
-// (virtual) series folds its chunks in time order.  Writes the filtered state
-// at the end of every chunk (state_end), the series log-likelihood, and for
-// the gradient the adjoint of each chunk's end state (adj_end).
-template <class S>
+// (virtual) series folds its chunks in time order, in the arithmetic of T.
+// Writes the filtered state at the end of every chunk (state_end, records of
+// T), the series log-likelihood, and for the gradient the adjoint of each
+// chunk's end state (adj_end, FP32).
+template <class S, class T>
 __global__ void __launch_bounds__(64) k_scan_seq(DevModel M, int n_out, int per_series,
                                                  const float *__restrict__ ef,
                                                  const double *__restrict__ ed, int n_vch,
-                                                 float *__restrict__ state_end,
+                                                 T *__restrict__ state_end,
                                                  float *__restrict__ adj_end,
                                                  double *__restrict__ ll_out, int want_grad,
                                                  int *__restrict__ err) {
-  using F = float;
   constexpr int D = S::D;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n_out) return;
@@ -762,12 +774,12 @@ __global__ void __launch_bounds__(64) k_scan_seq(DevModel M, int n_out, int per_
   const int set = per_series ? 0 : v / M.n_series;
   const int c0 = M.ch_first[s], c1 = M.ch_first[s + 1];
   const int base = set * M.n_chunks;
-  F m[D], P[S::NP];
+  T m[D], P[S::NP];
   double ll = 0.0;
   for (int c = c0; c < c1; ++c) {
     const int vc = base + c;
-    F A[D][D], b[D], C[S::NP], eta[D], J[S::NP];
-    load_elem<S>(ef, n_vch, vc, A, b, C, eta, J);
+    T A[D][D], b[D], C[S::NP], eta[D], J[S::NP];
+    load_elem_t<S, T, float>(ef, (size_t)n_vch, (size_t)vc, A, b, C, eta, J);
     const double gam = ed[vc], ld = ed[(size_t)n_vch + vc], ne = ed[(size_t)2 * n_vch + vc];
     if (c == c0) {
       ll += -0.5 * (ld + gam + ne * LOG_2PI);
@@ -776,49 +788,8 @@ __global__ void __launch_bounds__(64) k_scan_seq(DevModel M, int n_out, int per_
 #pragma unroll
       for (int i = 0; i < S::NP; ++i) P[i] = C[i];
     } else {
-      ll += chunk_loglik<S>(m, P, eta, J, gam, ld, ne);
-      // outgoing state: m' = A (I + P J)^{-1} (m + P eta) + b, P' = A (I + P J)^{-1} P A^T + C
-      F X[D][D], R[D][D + 1];
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        F pe = F(0);
-#pragma unroll
-        for (int k = 0; k < D; ++k) pe += P[S::pk(i, k)] * eta[k];
-        R[i][D] = m[i] + pe;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-          F acc = (i == j) ? F(1) : F(0);
-#pragma unroll
-          for (int k = 0; k < D; ++k) acc += P[S::pk(i, k)] * J[S::pk(k, j)];
-          X[i][j] = acc;
-          R[i][j] = P[S::pk(i, j)];
-        }
-      }
-      solve_inplace<D, D + 1, F>(X, R);
-      F T[D][D];
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        F acc = b[i];
-#pragma unroll
-        for (int k = 0; k < D; ++k) acc += A[i][k] * R[k][D];
-        m[i] = acc;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-          F a2 = F(0);
-#pragma unroll
-          for (int k = 0; k < D; ++k) a2 += A[i][k] * R[k][j];
-          T[i][j] = a2;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = i; j < D; ++j) {
-          F acc = C[S::pk(i, j)];
-#pragma unroll
-          for (int k = 0; k < D; ++k) acc += T[i][k] * A[j][k];
-          P[S::pk(i, j)] = acc;
-        }
+      ll += chunk_loglik<S, T>(m, P, eta, J, gam, ld, ne);
+      state_through<S, T>(A, b, C, eta, J, m, P);
     }
     if (want_grad) store_rec<S>(state_end, n_vch, vc, m, P);
   }
@@ -826,69 +797,30 @@ __global__ void __launch_bounds__(64) k_scan_seq(DevModel M, int n_out, int per_
   if (!isfinite(ll)) flag_error(err, v, 7);
   if (!want_grad) return;
   // backward information and end-of-chunk adjoints
-  F ie[D], iJ[S::NP];
+  T ie[D], iJ[S::NP];
 #pragma unroll
-  for (int i = 0; i < D; ++i) ie[i] = F(0);
+  for (int i = 0; i < D; ++i) ie[i] = T(0);
 #pragma unroll
-  for (int i = 0; i < S::NP; ++i) iJ[i] = F(0);
+  for (int i = 0; i < S::NP; ++i) iJ[i] = T(0);
   for (int c = c1 - 1; c >= c0; --c) {
     const int vc = base + c;
-    F lam[D], Lam[S::NP];
+    float lam[D], Lam[S::NP];
     if (c == c1 - 1) {
 #pragma unroll
-      for (int i = 0; i < D; ++i) lam[i] = F(0);
+      for (int i = 0; i < D; ++i) lam[i] = 0.f;
 #pragma unroll
-      for (int i = 0; i < S::NP; ++i) Lam[i] = F(0);
+      for (int i = 0; i < S::NP; ++i) Lam[i] = 0.f;
     } else {
-      F mb[D], Pb[S::NP];
+      T mb[D], Pb[S::NP];
       load_rec<S>(state_end, n_vch, vc, mb, Pb);
-      boundary_adjoint<S>(mb, Pb, ie, iJ, lam, Lam);
+      boundary_adjoint<S, T>(mb, Pb, ie, iJ, lam, Lam);
     }
     store_rec<S>(adj_end, n_vch, vc, lam, Lam);
     if (c == c0) break;
-    // fold chunk c into the backward information:
-    // eta <- A^T (I + J_n C)^{-1} (eta_n - J_n b) + eta, J <- A^T (I + J_n C)^{-1} J_n A + J
-    F A[D][D], b[D], C[S::NP], eta[D], J[S::NP];
-    load_elem<S>(ef, n_vch, vc, A, b, C, eta, J);
-    F X[D][D], R[D][D + 1];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      F jb = F(0);
-#pragma unroll
-      for (int k = 0; k < D; ++k) jb += iJ[S::pk(i, k)] * b[k];
-      R[i][D] = ie[i] - jb;
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        F acc = (i == j) ? F(1) : F(0), ja = F(0);
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          acc += iJ[S::pk(i, k)] * C[S::pk(k, j)];
-          ja += iJ[S::pk(i, k)] * A[k][j];
-        }
-        X[i][j] = acc;
-        R[i][j] = ja;
-      }
-    }
-    solve_inplace<D, D + 1, F>(X, R);
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      F acc = eta[i];
-#pragma unroll
-      for (int k = 0; k < D; ++k) acc += A[k][i] * R[k][D];
-      ie[i] = acc;
-    }
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-      for (int j = i; j < D; ++j) {
-        F acc = F(0), acc2 = F(0);
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          acc += A[k][i] * R[k][j];
-          acc2 += A[k][j] * R[k][i];
-        }
-        iJ[S::pk(i, j)] = J[S::pk(i, j)] + F(0.5) * (acc + acc2);
-      }
+    // fold chunk c into the backward information
+    T A[D][D], b[D], C[S::NP], eta[D], J[S::NP];
+    load_elem_t<S, T, float>(ef, (size_t)n_vch, (size_t)vc, A, b, C, eta, J);
+    info_through<S, T>(A, b, C, eta, J, ie, iJ);
   }
 }
 
@@ -898,16 +830,17 @@ __global__ void __launch_bounds__(64) k_scan_seq(DevModel M, int n_out, int per_
 //   state_end  (b, C) of the inclusive prefix scan   (filtered end state)
 //   info_incl  (eta, J) of the inclusive suffix scan (information about the
 //              state entering the chunk from it and all later chunks)
-template <class S>
+// Both are records of T (the combination's arithmetic), which is also the
+// arithmetic of the closed-form chunk log-likelihood and of the adjoint.
+template <class S, class T>
 __global__ void __launch_bounds__(128) k_finish(DevModel M, int n_vch, int per_series,
                                                 const float *__restrict__ ef,
                                                 const double *__restrict__ ed,
-                                                const float *__restrict__ state_end,
-                                                const float *__restrict__ info_incl,
+                                                const T *__restrict__ state_end,
+                                                const T *__restrict__ info_incl,
                                                 float *__restrict__ adj_end,
                                                 double *__restrict__ ll_part,
                                                 int *__restrict__ err) {
-  using F = float;
   constexpr int D = S::D;
   using L = ElemLayout<S>;
   const int vc = blockIdx.x * blockDim.x + threadIdx.x;
@@ -922,28 +855,28 @@ __global__ void __launch_bounds__(128) k_finish(DevModel M, int n_vch, int per_s
   if (flags & 1) {
     ll = -0.5 * (ld + gam + ne * LOG_2PI);
   } else {
-    F m[D], P[S::NP], eta[D], J[S::NP];
+    T m[D], P[S::NP], eta[D], J[S::NP];
     load_rec<S>(state_end, n_vch, vc - 1, m, P);
 #pragma unroll
-    for (int i = 0; i < D; ++i) eta[i] = ef[(size_t)(L::ETA + i) * n_vch + vc];
+    for (int i = 0; i < D; ++i) eta[i] = T(ef[(size_t)(L::ETA + i) * n_vch + vc]);
 #pragma unroll
-    for (int i = 0; i < S::NP; ++i) J[i] = ef[(size_t)(L::J + i) * n_vch + vc];
-    ll = chunk_loglik<S>(m, P, eta, J, gam, ld, ne);
+    for (int i = 0; i < S::NP; ++i) J[i] = T(ef[(size_t)(L::J + i) * n_vch + vc]);
+    ll = chunk_loglik<S, T>(m, P, eta, J, gam, ld, ne);
   }
   ll_part[vc] = ll;
   if (!isfinite(ll)) flag_error(err, orow, 7);
   if (!adj_end) return;
-  F lam[D], Lam[S::NP];
+  float lam[D], Lam[S::NP];
   if (flags & 2) {
 #pragma unroll
-    for (int i = 0; i < D; ++i) lam[i] = F(0);
+    for (int i = 0; i < D; ++i) lam[i] = 0.f;
 #pragma unroll
-    for (int i = 0; i < S::NP; ++i) Lam[i] = F(0);
+    for (int i = 0; i < S::NP; ++i) Lam[i] = 0.f;
   } else {
-    F mb[D], Pb[S::NP], ie[D], iJ[S::NP];
+    T mb[D], Pb[S::NP], ie[D], iJ[S::NP];
     load_rec<S>(state_end, n_vch, vc, mb, Pb);
     load_rec<S>(info_incl, n_vch, vc + 1, ie, iJ);
-    boundary_adjoint<S>(mb, Pb, ie, iJ, lam, Lam);
+    boundary_adjoint<S, T>(mb, Pb, ie, iJ, lam, Lam);
   }
   store_rec<S>(adj_end, n_vch, vc, lam, Lam);
 }
@@ -951,6 +884,7 @@ __global__ void __launch_bounds__(128) k_finish(DevModel M, int n_vch, int per_s
 // ---------------------------------------------------------------------------
 // Reverse-time gradient, one thread per chunk.
 // ---------------------------------------------------------------------------
+constexpr int GRAD_BS = 64;
 template <int NT>
 struct TermGrad {
   float a[NT], beta[NT], w2[NT], qc[NT], var[NT];
@@ -1326,8 +1260,8 @@ GPSS_HD void apply_partial(const float *src, int n_vch, int vc, const float *m_i
 // (w = 1/delta of its measurement; dw/dt_start = w^2 = -dw/dt_end).
 template <class S>
 __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restrict__ theta, int n_vch,
-                                             int per_series, const float *__restrict__ state_end,
-                                             const float *__restrict__ adj_end,
+                                             int per_series, const void *__restrict__ state_end,
+                                             int se64, const float *__restrict__ adj_end,
                                              const float *__restrict__ pck, float *__restrict__ gpart,
                                              int *__restrict__ err,
                                              const float *__restrict__ tabs,
@@ -1350,9 +1284,20 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   const int s = M.ch_series[c];
   const int row = per_series ? s : set;
   const int orow = per_series ? s : set * M.n_series + s;
-  TermC<F> tc[S::NT];
+  // Per-term constants of the row (one row per warp: a warp's 32 chunks lie
+  // in one series and one parameter set) and the gradient accumulators live
+  // in shared memory, which frees registers for the filter state.
+  __shared__ TermC<F> s_tc[GRAD_BS / 32][S::NT];
+  __shared__ TermGrad<S::NT> s_gr[GRAD_BS];
+  TermC<F> *tc = s_tc[threadIdx.x >> 5];
   F s2;
-  load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tc, s2);
+  {
+    TermC<F> tl[S::NT];
+    load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tl, s2);
+    if ((threadIdx.x & 31) == 0)
+      for (int t = 0; t < S::NT; ++t) tc[t] = tl[t];
+    __syncwarp();
+  }
   // shared memory: the warps' tables, then two staging buffers per thread
   // for the backward walk, stg[(buf (SG + NDG) + group) bs + thread] (float4)
   float4 *tab_slots = reinterpret_cast<float4 *>(sm);
@@ -1379,7 +1324,7 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
     } else {
       load_rec<S>(adj_end, n_vch, vc, lam, Lam);
     }
-    TermGrad<S::NT> gr;
+    TermGrad<S::NT> &gr = s_gr[threadIdx.x];
   #pragma unroll
     for (int t = 0; t < S::NT; ++t) gr.a[t] = gr.beta[t] = gr.w2[t] = gr.qc[t] = gr.var[t] = F(0);
     gr.s2 = F(0);
@@ -1398,7 +1343,7 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
         if (first)
           init_state<S>(tc, m, P);
         else
-          load_rec<S>(state_end, n_vch, vc - 1, m, P);
+          load_state_f<S>(state_end, se64, n_vch, vc - 1, m, P);
       } else {
         F mi[D], Pi[S::NP];
         if (first) {
@@ -1408,7 +1353,7 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   #pragma unroll
           for (int i = 0; i < S::NP; ++i) Pi[i] = F(0);
         } else {
-          load_rec<S>(state_end, n_vch, vc - 1, mi, Pi);
+          load_state_f<S>(state_end, se64, n_vch, vc - 1, mi, Pi);
         }
         const float *src = pck + (size_t)(seg - 1) * (NF + 1) * n_vch;
         apply_partial<S>(src, n_vch, vc, mi, Pi, m, P);
@@ -1458,14 +1403,14 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
         const uint8_t tl = __ldg(M.tag + e0 + k1 - 1);
         const float4 ql = __ldg(M.meas + rd.mi - 1);
         F mb[D], Pb[S::NP];
-        load_rec<S>(state_end, n_vch, vc, mb, Pb);
+        load_state_f<S>(state_end, se64, n_vch, vc, mb, Pb);
         cond[eo + k1 - 1] = conditioned<S>((tl >> 1) & 7, ql.z, mb, Pb, lam, Lam);
       }
       // test times after the series' last event: predicted from its filtered
       // state (which all the data already conditions)
       if (EX && pp.off && last && seg == nseg - 1) {
         F mb[D], Pb[S::NP], z[D], Z[S::NP];
-        load_rec<S>(state_end, n_vch, vc, mb, Pb);
+        load_state_f<S>(state_end, se64, n_vch, vc, mb, Pb);
   #pragma unroll
         for (int i = 0; i < D; ++i) z[i] = F(0);
   #pragma unroll
@@ -1692,37 +1637,184 @@ __global__ void k_disc(const float *__restrict__ theta, const float *__restrict_
 }
 
 // ---------------------------------------------------------------------------
+// A series split in time (Section 3.2.5 across devices): the chunks
+// [c_begin, c_end) of every row combined into one element with its
+// log-normaliser c (Elem fields, then c; NC = NF + 1 values, FP64).  Each
+// level reduces tiles of SPAN_T items by a tree of combinations in shared
+// memory; the first level reads the chunk elements, later ones the tile
+// totals ([row][item][field]).  Folding the spans' elements in time order
+// gives the series' log-likelihood in c (the first span starts from the
+// prior, A = 0).
+// ---------------------------------------------------------------------------
+constexpr int SPAN_T = 64;
+
+template <class S>
+constexpr size_t span_smem_bytes() {
+  return (size_t)SPAN_T * (Elem<S>::NF + 1) * sizeof(double);
+}
+
+template <class S, bool FROM_CHUNKS>
+__global__ void __launch_bounds__(SPAN_T) k_span_reduce(const float *__restrict__ ef,
+                                                        const double *__restrict__ ed,
+                                                        int n_vch, int n_chunks, int c_begin,
+                                                        const double *__restrict__ src, int n,
+                                                        double *__restrict__ dst,
+                                                        int n_out_tiles) {
+  constexpr int NF = Elem<S>::NF, NC = NF + 1;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  double *sm = reinterpret_cast<double *>(sm_raw);
+  const int tile = blockIdx.x, row = blockIdx.y, tid = threadIdx.x;
+  const int i0 = tile * SPAN_T;
+  const int len = min(SPAN_T, n - i0);
+  EViewT<double> mine{sm + tid, SPAN_T};
+  if (tid < len) {
+    const int i = i0 + tid;
+    if (FROM_CHUNKS) {
+      const size_t vc = (size_t)row * n_chunks + c_begin + i;
+      for (int f = 0; f < NF; ++f) mine[f] = (double)ef[(size_t)f * n_vch + vc];
+      const double gam = ed[vc], ld = ed[(size_t)n_vch + vc], ne = ed[(size_t)2 * n_vch + vc];
+      mine[NF] = -0.5 * (ld + gam + ne * LOG_2PI);
+    } else {
+      for (int f = 0; f < NC; ++f) mine[f] = src[((size_t)row * n + i) * NC + f];
+    }
+  }
+  __syncthreads();
+  for (int s = 1; s < SPAN_T; s <<= 1) {
+    if ((tid % (2 * s)) == 0 && tid + s < len)
+      combine<S, double, true>(mine, EViewT<double>{sm + tid + s, SPAN_T}, mine);
+    __syncthreads();
+  }
+  if (tid == 0)
+    for (int f = 0; f < NC; ++f) dst[((size_t)row * n_out_tiles + tile) * NC + f] = mine[f];
+}
+
+// Fold the spans' elements [span][row][NC] in time order, one thread per
+// row; the log-normaliser of the whole is the series' log-likelihood.
+template <class S>
+__global__ void k_span_fold(const double *__restrict__ elems, int n_spans, int n_rows,
+                            double *__restrict__ ll_out) {
+  constexpr int NC = Elem<S>::NF + 1;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n_rows) return;
+  double acc[NC], nxt[NC], out[NC];
+  for (int f = 0; f < NC; ++f) acc[f] = elems[(size_t)row * NC + f];
+  for (int sp = 1; sp < n_spans; ++sp) {
+    for (int f = 0; f < NC; ++f) nxt[f] = elems[((size_t)sp * n_rows + row) * NC + f];
+    combine<S, double, true>(EViewT<double>{acc, 1}, EViewT<double>{nxt, 1},
+                             EViewT<double>{out, 1});
+    for (int f = 0; f < NC; ++f) acc[f] = out[f];
+  }
+  ll_out[row] = acc[NC - 1];
+}
+
+// Element of chunks [c_begin, c_end) of each of n_rows rows (the chunk
+// elements already in ef / ed) -> elem_out [n_rows][NC].  scratch: at least
+// span_scratch_count(c_end - c_begin, n_rows) doubles.
+template <class S>
+size_t span_scratch_count(int n, int n_rows) {
+  size_t tot = 0;
+  while (n > 1) {
+    n = (n + SPAN_T - 1) / SPAN_T;
+    tot += (size_t)n * n_rows * (Elem<S>::NF + 1);
+  }
+  return tot + 1;
+}
+
+template <class S>
+cudaError_t launch_span_element(const float *ef, const double *ed, int n_vch, int n_chunks,
+                                int c_begin, int c_end, int n_rows, double *scratch,
+                                double *elem_out, cudaStream_t st) {
+  constexpr int NC = Elem<S>::NF + 1;
+  const size_t smem = span_smem_bytes<S>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_span_reduce<S, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_span_reduce<S, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int n = c_end - c_begin;
+  if (n <= 0 || n_rows <= 0) return cudaErrorInvalidValue;
+  const double *src = nullptr;
+  double *buf = scratch;
+  bool first = true;
+  do {
+    const int nt = (n + SPAN_T - 1) / SPAN_T;
+    double *dst = nt == 1 ? elem_out : buf;
+    if (first)
+      k_span_reduce<S, true><<<dim3(nt, n_rows), SPAN_T, smem, st>>>(
+          ef, ed, n_vch, n_chunks, c_begin, nullptr, n, dst, nt);
+    else
+      k_span_reduce<S, false><<<dim3(nt, n_rows), SPAN_T, smem, st>>>(
+          nullptr, nullptr, 0, 0, 0, src, n, dst, nt);
+    GPSS_COUNT_LAUNCH();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    src = dst;
+    buf += (size_t)nt * n_rows * NC;
+    n = nt;
+    first = false;
+  } while (n > 1);
+  return cudaSuccess;
+}
+
+template <class S>
+cudaError_t launch_span_fold(const double *elems, int n_spans, int n_rows, double *ll,
+                             cudaStream_t st) {
+  if (n_spans <= 0 || n_rows <= 0) return cudaErrorInvalidValue;
+  k_span_fold<S><<<(n_rows + 63) / 64, 64, 0, st>>>(elems, n_spans, n_rows, ll);
+  GPSS_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers, one table per compiled shape.
 // ---------------------------------------------------------------------------
+// Cross-chunk combination in one arithmetic (FP32 or FP64): the sequential
+// fold per series, the warp-level scans with the scan or fold of warp totals
+// and the per-chunk join, and the chunk log-likelihoods with the boundary
+// adjoints.  Buffers other than the chunk elements (FP32) and the adjoints
+// (FP32) hold elem_bytes per value.
+struct CombineOps {
+  int elem_bytes;
+  cudaError_t (*scan)(const DevModel &, int, int, const float *, const double *, int, void *,
+                      float *, double *, int, int *, cudaStream_t);
+  cudaError_t (*warp_combine)(const DevModel &, const float *, int, void *, void *, void *,
+                              void *, void *, void *, void *, void *, int, int, int, int,
+                              cudaStream_t);
+  size_t (*warp_scratch)(int);  // values of the scan of warp totals
+  cudaError_t (*finish)(const DevModel &, int, int, const float *, const double *, const void *,
+                        const void *, float *, double *, int *, cudaStream_t);
+};
+
 struct OpTable {
   int D, NP, NF, ND;
   cudaError_t (*plain32)(const DevModel &, const float *, int, int, double *, int *, cudaStream_t);
   cudaError_t (*plain64)(const DevModel &, const float *, int, int, double *, int *, cudaStream_t);
   cudaError_t (*elem)(const DevModel &, const float *, int, int, float *, double *, int *,
                       const float *, float *, int, float *, int, int, cudaStream_t);
-  cudaError_t (*scan)(const DevModel &, int, int, const float *, const double *, int, float *,
-                      float *, double *, int, int *, cudaStream_t);
-  cudaError_t (*grad)(const DevModel &, const float *, int, int, const float *, const float *,
-                      const float *, float *, int *, const float *, float *, const float *, int,
-                      float *, float *, float2 *, const PredPlan &, cudaStream_t);
+  cudaError_t (*grad)(const DevModel &, const float *, int, int, const void *, int,
+                      const float *, const float *, float *, int *, const float *, float *,
+                      const float *, int, float *, float *, float2 *, const PredPlan &,
+                      cudaStream_t);
   cudaError_t (*tables)(const float *, int, int, int, int, float *, cudaStream_t);
-  cudaError_t (*warp_combine)(const DevModel &, const float *, int, float *, float *, float *,
-                              float *, float *, float *, float *, float *, int, int, int, int,
-                              cudaStream_t);
-  size_t (*warp_scratch)(int);
+  CombineOps comb32, comb64;  // the combination in FP32 / FP64
   int NT;
-  cudaError_t (*scan_tree)(const float *, int, float *, int, int, float *, cudaStream_t);
-  size_t (*scan_scratch)(int);
-  cudaError_t (*finish)(const DevModel &, int, int, const float *, const double *, const float *,
-                        const float *, float *, double *, int *, cudaStream_t);
   cudaError_t (*disc)(const float *, const float *, int, int, const float *, int, float *, float *,
                       cudaStream_t);
   // product models: log-likelihood and hyperparameter gradient (else null)
   cudaError_t (*prod_grad)(const DevModel &, const float *, int, int, double *, float *, int *,
                            cudaStream_t);
+  // a series split in time: element of a chunk range, fold of span elements
+  cudaError_t (*span_element)(const float *, const double *, int, int, int, int, int, double *,
+                              double *, cudaStream_t);
+  size_t (*span_scratch)(int, int);
+  cudaError_t (*span_fold)(const double *, int, int, double *, cudaStream_t);
 };
 
-constexpr int GRAD_BS = 64;
 
 template <class S, class F>
 cudaError_t launch_plain(const DevModel &M, const float *theta, int n_out, int per_series,
@@ -1772,91 +1864,97 @@ cudaError_t launch_tables(const float *theta, int n_rows, int n_params, int k0, 
   return cudaGetLastError();
 }
 
-template <class S>
+template <class S, class T>
 cudaError_t launch_scan(const DevModel &M, int n_out, int per_series, const float *ef,
-                        const double *ed, int n_vch, float *state_end, float *adj_end, double *ll,
+                        const double *ed, int n_vch, void *state_end, float *adj_end, double *ll,
                         int want_grad, int *err, cudaStream_t st) {
   if (n_out <= 0) return cudaSuccess;
   const int bs = 64;
-  k_scan_seq<S><<<(n_out + bs - 1) / bs, bs, 0, st>>>(M, n_out, per_series, ef, ed, n_vch,
-                                                     state_end, adj_end, ll, want_grad, err);
+  k_scan_seq<S, T><<<(n_out + bs - 1) / bs, bs, 0, st>>>(M, n_out, per_series, ef, ed, n_vch,
+                                                        static_cast<T *>(state_end), adj_end, ll,
+                                                        want_grad, err);
   GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
-// Tree schedule: inclusive scan of the n chunk elements, mode 1 -> state
-// records in time order, mode 2 (suffix) -> information records.
-template <class S>
-cudaError_t launch_scan_tree(const float *ef, int n, float *dst, int mode, int rev,
-                             float *scratch, cudaStream_t st) {
-  return scan_elems<S>(ef, n, dst, mode, rev, rev, scratch, st);
-}
-
-template <class S>
-size_t scan_scratch_count(int n) {
-  return scan_scratch_floats<S>(n);
-}
-
 // Warp-level combination (k_warp_scan, scan of warp totals, k_join): writes
-// state_end (and info_incl when want_info).  Buffers: pre_local, suf_local
-// [NF * n_vch]; wtot, wpre, wsuf [NF * n_vch/32]; scratch [warp_scratch].
-template <class S>
-cudaError_t launch_warp_combine(const DevModel &M, const float *ef, int n_vch, float *pre_local,
-                                float *suf_local, float *wtot, float *wpre, float *wsuf,
-                                float *scratch, float *state_end, float *info_incl, int want_info,
-                                int fold, int n_out, int per_series, cudaStream_t st) {
+// state_end (and info_incl when want_info), records of T.  Buffers of T:
+// pre_local, suf_local [NF * n_vch]; wtot, wpre, wsuf [NF * n_vch/32];
+// scratch [warp_scratch values].
+template <class S, class T>
+cudaError_t launch_warp_combine(const DevModel &M, const float *ef, int n_vch, void *pre_local_v,
+                                void *suf_local_v, void *wtot_v, void *wpre_v, void *wsuf_v,
+                                void *scratch_v, void *state_end_v, void *info_incl_v,
+                                int want_info, int fold, int n_out, int per_series,
+                                cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
+  T *pre_local = static_cast<T *>(pre_local_v), *suf_local = static_cast<T *>(suf_local_v);
+  T *wtot = static_cast<T *>(wtot_v), *wpre = static_cast<T *>(wpre_v),
+    *wsuf = static_cast<T *>(wsuf_v), *scratch = static_cast<T *>(scratch_v);
+  T *state_end = static_cast<T *>(state_end_v), *info_incl = static_cast<T *>(info_incl_v);
   const int n_w = n_vch / 32;
-  const size_t smem = warp_scan_smem_bytes<S>(2);
+  const size_t smem = warp_scan_smem_bytes<S, T>(2);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_warp_scan<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_warp_scan<S, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_warp_scan<S><<<(n_vch + 63) / 64, 64, smem, st>>>(ef, n_vch, pre_local, suf_local, wtot,
-                                                      want_info);
+  k_warp_scan<S, T><<<(n_vch + 63) / 64, 64, smem, st>>>(ef, n_vch, pre_local, suf_local, wtot,
+                                                         want_info);
   GPSS_COUNT_LAUNCH();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (fold) {
     // few warps per series: sequential fold of the warp totals per series
-    k_warp_fold<S><<<(n_out + 63) / 64, 64, 0, st>>>(n_out, per_series, M.n_series, M.n_chunks,
-                                                     M.ch_first, wtot, n_w, wpre, wsuf,
-                                                     want_info);
+    k_warp_fold<S, T><<<(n_out + 63) / 64, 64, 0, st>>>(n_out, per_series, M.n_series,
+                                                        M.n_chunks, M.ch_first, wtot, n_w, wpre,
+                                                        wsuf, want_info);
     GPSS_COUNT_LAUNCH();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   } else {
-    e = scan_elems<S>(wtot, n_w, wpre, 0, 0, 0, scratch, st);
+    e = scan_elems<S, T>(wtot, n_w, wpre, 0, 0, 0, scratch, st);
     if (e != cudaSuccess) return e;
     if (want_info) {
-      e = scan_elems<S>(wtot, n_w, wsuf, 3, 1, 1, scratch, st);
+      e = scan_elems<S, T>(wtot, n_w, wsuf, 3, 1, 1, scratch, st);
       if (e != cudaSuccess) return e;
     }
   }
-  k_join<S><<<(n_vch + 127) / 128, 128, 0, st>>>(n_vch, M.n_chunks, M.ch_flags, pre_local,
-                                                 suf_local, wpre, wsuf, state_end,
-                                                 want_info ? info_incl : nullptr);
+  k_join<S, T><<<(n_vch + 127) / 128, 128, 0, st>>>(n_vch, M.n_chunks, M.ch_flags, pre_local,
+                                                    suf_local, wpre, wsuf, state_end,
+                                                    want_info ? info_incl : nullptr);
   GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
 template <class S>
 size_t warp_scratch_count(int n_vch) {
-  return scan_scratch_floats<S>(n_vch / 32);
+  return scan_scratch_count<S>(n_vch / 32);
 }
 
-template <class S>
+template <class S, class T>
 cudaError_t launch_finish(const DevModel &M, int n_vch, int per_series, const float *ef,
-                          const double *ed, const float *state_end, const float *info_incl,
+                          const double *ed, const void *state_end, const void *info_incl,
                           float *adj_end, double *ll_part, int *err, cudaStream_t st) {
   if (n_vch <= 0) return cudaSuccess;
-  k_finish<S><<<(n_vch + 127) / 128, 128, 0, st>>>(M, n_vch, per_series, ef, ed, state_end,
-                                                   info_incl, adj_end, ll_part, err);
+  k_finish<S, T><<<(n_vch + 127) / 128, 128, 0, st>>>(
+      M, n_vch, per_series, ef, ed, static_cast<const T *>(state_end),
+      static_cast<const T *>(info_incl), adj_end, ll_part, err);
   GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
+}
+
+template <class S, class T>
+CombineOps make_combine() {
+  CombineOps c;
+  c.elem_bytes = (int)sizeof(T);
+  c.scan = &launch_scan<S, T>;
+  c.warp_combine = &launch_warp_combine<S, T>;
+  c.warp_scratch = &warp_scratch_count<S>;
+  c.finish = &launch_finish<S, T>;
+  return c;
 }
 
 // ck: events per recomputation segment (even, 2..64), the value k_elem saved
@@ -1868,7 +1966,7 @@ cudaError_t launch_finish(const DevModel &M, int n_vch, int per_series, const fl
 // (mean, variance) of end events [rows * n_events], or null.
 template <class S>
 cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int per_series,
-                        const float *state_end, const float *adj_end, const float *pck,
+                        const void *state_end, int se64, const float *adj_end, const float *pck,
                         float *gpart, int *err, const float *tabs, float *rbuf,
                         const float *dcache, int ck, float *gdt, float *gwe, float2 *cond,
                         const PredPlan &pp, cudaStream_t st) {
@@ -1878,8 +1976,8 @@ cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int pe
   const size_t smem = (size_t)(GRAD_BS / 32) * S::NT * TAB_TERM * sizeof(float) +
                       (size_t)2 * (SG + NDG) * GRAD_BS * sizeof(float4);
   k_grad<S><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
-      M, theta, n_vch, per_series, state_end, adj_end, pck, gpart, err, tabs, rbuf, dcache, ck,
-      gdt, gwe, cond, pp);
+      M, theta, n_vch, per_series, state_end, se64, adj_end, pck, gpart, err, tabs, rbuf, dcache,
+      ck, gdt, gwe, cond, pp);
   GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
@@ -1893,9 +1991,11 @@ cudaError_t launch_disc(const float *theta, const float *tabs, int k0, int k1, c
   return cudaGetLastError();
 }
 
+// The operation table of a shape; the FP64 combination (comb64) is filled
+// by make_ops_c64, compiled in its own translation unit.
 template <class S>
 OpTable make_ops() {
-  OpTable o;
+  OpTable o{};
   o.D = S::D;
   o.NP = S::NP;
   o.NF = ElemLayout<S>::NF;
@@ -1903,17 +2003,15 @@ OpTable make_ops() {
   o.plain32 = &launch_plain<S, float>;
   o.plain64 = &launch_plain<S, double>;
   o.elem = &launch_elem<S>;
-  o.scan = &launch_scan<S>;
   o.grad = &launch_grad<S>;
   o.disc = &launch_disc<S>;
-  o.scan_tree = &launch_scan_tree<S>;
-  o.scan_scratch = &scan_scratch_count<S>;
-  o.finish = &launch_finish<S>;
+  o.comb32 = make_combine<S, float>();
   o.tables = &launch_tables<S>;
-  o.warp_combine = &launch_warp_combine<S>;
-  o.warp_scratch = &warp_scratch_count<S>;
   o.NT = S::NT;
   o.prod_grad = nullptr;
+  o.span_element = &launch_span_element<S>;
+  o.span_scratch = &span_scratch_count<S>;
+  o.span_fold = &launch_span_fold<S>;
   return o;
 }
 

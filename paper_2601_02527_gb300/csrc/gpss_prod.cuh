@@ -580,7 +580,7 @@ inline cudaError_t no_tables(const float *, int, int, int, int, float *, cudaStr
 // Operation table of a product model: the plain filters, the forward-mode
 // gradient, and the chunked log-likelihood (dense product elements, then the
 // combination and chunk log-likelihoods of the shape ES of the same state
-// dimension).
+// dimension; its FP64 combination is filled by make_ops_c64 like the others).
 template <bool SUM>
 OpTable make_prod_ops() {
   using ES = typename std::conditional<SUM, Shape<3, 0, 0>, Shape<2, 0, 0>>::type;
@@ -595,12 +595,10 @@ OpTable make_prod_ops() {
   o.prod_grad = &launch_prod_grad<SUM>;
   o.tables = &no_tables;
   o.elem = &launch_elem_prod<SUM, ES>;
-  o.scan = &launch_scan<ES>;
-  o.scan_tree = &launch_scan_tree<ES>;
-  o.scan_scratch = &scan_scratch_count<ES>;
-  o.finish = &launch_finish<ES>;
-  o.warp_combine = &launch_warp_combine<ES>;
-  o.warp_scratch = &warp_scratch_count<ES>;
+  o.comb32 = make_combine<ES, float>();
+  o.span_element = &launch_span_element<ES>;
+  o.span_scratch = &span_scratch_count<ES>;
+  o.span_fold = &launch_span_fold<ES>;
   return o;
 }
 

@@ -87,6 +87,10 @@ class Workload:
         inst = None if self.instrument is None else self.instrument[a:b]
         return self.t_start[a:b], self.t_end[a:b], self.y[a:b], self.yerr[a:b], inst
 
+    def with_theta(self, theta) -> "Workload":
+        """The same series with other parameter sets (shared-set mode kept)."""
+        return dataclasses.replace(self, theta=np.array(theta, dtype=np.float64, copy=True))
+
     def subset(self, idx) -> "Workload":
         """Workload restricted to the given series indices (theta follows)."""
         idx = np.asarray(idx, dtype=np.int64)

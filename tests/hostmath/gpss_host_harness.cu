@@ -1,6 +1,7 @@
 // Host build of the CUDA path's device arithmetic, for CPU tests: the same
 // header functions the kernels inline, called from ordinary host code.
 // Compiled by tests/test_host_math.py with nvcc into a shared library.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -116,6 +117,99 @@ void prod_disc_t(double dt, const double *th, double *Phi, double *Q) {
                                   A.q[ra][ca] * B.q[rb][cb]);
         }
 }
+}  // namespace
+
+namespace {
+
+// Element of events [k_begin, k_end) of one series, as the chunk kernels
+// form it but in FP64 with the on-the-fly discretisation: chunks of
+// chunk_len events from k_begin, each run by elem_event from an unknown
+// incoming state (from the prior for the series' first chunk), then combined
+// in time order with their log-normalisers.  dt, tag: the series' events;
+// meas3: (y, r0, w) per measurement in event order; theta: one row.
+// out: NF + 1 doubles (fields of Elem, then c).
+template <class S>
+void span_elem_s(const double *dt, const uint8_t *tag, const double *meas3, const float *theta,
+                 const int *kinds, int64_t k_begin, int64_t k_end, int chunk_len, double *out) {
+  constexpr int D = S::D, NF = Elem<S>::NF, NC = NF + 1;
+  TermC<double> tc[S::NT];
+  double s2;
+  load_terms<S::NT, double>(theta, kinds, tc, s2);
+  int64_t mi = 0;
+  for (int64_t k = 0; k < k_begin; ++k) mi += tag[k] & 1;
+  double acc[NC], cur[NC], tmp[NC];
+  bool have = false;
+  for (int64_t c0 = k_begin; c0 < k_end; c0 += chunk_len) {
+    const int64_t c1 = std::min<int64_t>(k_end, c0 + chunk_len);
+    double A[D][D], b[D], C[S::NP], eta[D], J[S::NP];
+    const bool first = c0 == 0;
+    if (first) {
+      init_state<S>(tc, b, C);
+    } else {
+      for (int i = 0; i < D; ++i) b[i] = 0.0;
+      for (int i = 0; i < S::NP; ++i) C[i] = 0.0;
+    }
+    for (int i = 0; i < D; ++i) {
+      eta[i] = 0.0;
+      for (int j = 0; j < D; ++j) A[i][j] = (!first && i == j) ? 1.0 : 0.0;
+    }
+    for (int i = 0; i < S::NP; ++i) J[i] = 0.0;
+    double gam = 0.0, ld = 0.0;
+    int n_end = 0;
+    bool bad = false;
+    for (int64_t k = c0; k < c1; ++k) {
+      Blocks<double> B[S::NT];
+      for (int t = 0; t < S::NT; ++t)
+        B[t] = make_blocks(discretize<double, double, true>(dt[k], tc[t].a, tc[t].beta), tc[t]);
+      double y = 0.0, r0 = 0.0, w = 0.0;
+      if (tag[k] & 1) {
+        y = meas3[3 * mi];
+        r0 = meas3[3 * mi + 1];
+        w = meas3[3 * mi + 2];
+        ++mi;
+      }
+      elem_event<S, double>(B, tag[k], y, r0, w, s2, A, b, C, eta, J, gam, ld, n_end, bad);
+    }
+    using L = Elem<S>;
+    for (int i = 0; i < D; ++i) {
+      for (int j = 0; j < D; ++j) cur[L::A + i * D + j] = A[i][j];
+      cur[L::B + i] = b[i];
+      cur[L::ETA + i] = eta[i];
+    }
+    for (int i = 0; i < S::NP; ++i) {
+      cur[L::C + i] = C[i];
+      cur[L::J + i] = J[i];
+    }
+    cur[NF] = -0.5 * (ld + gam + n_end * LOG_2PI);
+    if (!have) {
+      std::memcpy(acc, cur, sizeof acc);
+      have = true;
+    } else {
+      combine<S, double, true>(EViewT<double>{acc, 1}, EViewT<double>{cur, 1},
+                               EViewT<double>{tmp, 1});
+      std::memcpy(acc, tmp, sizeof acc);
+    }
+  }
+  std::memcpy(out, acc, sizeof acc);
+}
+
+// The log-likelihood of a series from its spans' elements (n_spans x NC,
+// time order), folded as the device does.
+template <class S>
+double span_fold_s(const double *elems, int n_spans) {
+  constexpr int NC = Elem<S>::NF + 1;
+  double acc[NC], tmp[NC];
+  std::memcpy(acc, elems, sizeof acc);
+  for (int sp = 1; sp < n_spans; ++sp) {
+    double nxt[NC];
+    std::memcpy(nxt, elems + (size_t)sp * NC, sizeof nxt);
+    combine<S, double, true>(EViewT<double>{acc, 1}, EViewT<double>{nxt, 1},
+                             EViewT<double>{tmp, 1});
+    std::memcpy(acc, tmp, sizeof acc);
+  }
+  return acc[NC - 1];
+}
+
 }  // namespace
 
 extern "C" {
@@ -285,6 +379,35 @@ double hh_taylor_k_check(double a, double beta) {
     }
   }
   return worst;
+}
+
+// span shape ids: 0 = (1 term, 1 slot), 1 = (1 term, 3 slots), 2 = (2 terms,
+// 3 slots), 3 = (2 terms, 1 slot, layout 1)
+int hh_span_nc(int shape) {
+  switch (shape) {
+    case 0: return Elem<Shape<1, 1, 0>>::NF + 1;
+    case 1: return Elem<Shape<1, 3, 0>>::NF + 1;
+    case 2: return Elem<Shape<2, 3, 0>>::NF + 1;
+  }
+  return Elem<Shape<2, 1, 1>>::NF + 1;
+}
+void hh_span_element(int shape, const double *dt, const uint8_t *tag, const double *meas3,
+                     const float *theta, const int *kinds, int64_t k_begin, int64_t k_end,
+                     int chunk_len, double *out) {
+  switch (shape) {
+    case 0: span_elem_s<Shape<1, 1, 0>>(dt, tag, meas3, theta, kinds, k_begin, k_end, chunk_len, out); break;
+    case 1: span_elem_s<Shape<1, 3, 0>>(dt, tag, meas3, theta, kinds, k_begin, k_end, chunk_len, out); break;
+    case 2: span_elem_s<Shape<2, 3, 0>>(dt, tag, meas3, theta, kinds, k_begin, k_end, chunk_len, out); break;
+    default: span_elem_s<Shape<2, 1, 1>>(dt, tag, meas3, theta, kinds, k_begin, k_end, chunk_len, out);
+  }
+}
+double hh_span_fold(int shape, const double *elems, int n_spans) {
+  switch (shape) {
+    case 0: return span_fold_s<Shape<1, 1, 0>>(elems, n_spans);
+    case 1: return span_fold_s<Shape<1, 3, 0>>(elems, n_spans);
+    case 2: return span_fold_s<Shape<2, 3, 0>>(elems, n_spans);
+  }
+  return span_fold_s<Shape<2, 1, 1>>(elems, n_spans);
 }
 
 }  // extern "C"

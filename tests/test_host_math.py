@@ -17,53 +17,17 @@ kernels inline (nvcc, host code only).  Checked here:
 """
 import ctypes
 import math
-import os
-import subprocess
 
 import numpy as np
 import pytest
 
 import oracle
 
-HERE = os.path.dirname(os.path.abspath(__file__))
-ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "hostmath", "gpss_host_harness.cu")
-OUT = os.path.join(HERE, "hostmath", "_build", "libgpss_hostmath.so")
-
 
 @pytest.fixture(scope="module")
 def hh():
-    os.makedirs(os.path.dirname(OUT), exist_ok=True)
-    deps = [SRC] + [os.path.join(ROOT, "paper_2601_02527_gb300", "csrc", f)
-                    for f in ("gpss_device.cuh", "gpss_kernels.cuh", "gpss_scan.cuh")]
-    if not os.path.exists(OUT) or os.path.getmtime(OUT) < max(map(os.path.getmtime, deps)):
-        nvcc = "/usr/local/cuda/bin/nvcc"
-        subprocess.check_call([nvcc, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-                               "-I", os.path.join(ROOT, "include"),
-                               "-I", os.path.join(ROOT, "paper_2601_02527_gb300", "csrc"),
-                               SRC, "-o", OUT + ".tmp"])
-        os.replace(OUT + ".tmp", OUT)
-    lib = ctypes.CDLL(OUT)
-    P = ctypes.POINTER
-    d, f = ctypes.c_double, ctypes.c_float
-    lib.hh_discretize.argtypes = [ctypes.c_int, d, d, d, P(d)]
-    lib.hh_discretize_dual.argtypes = [d, d, d, P(d)]
-    lib.hh_discretize_tangents.argtypes = [d, d, d, P(d)]
-    lib.hh_solve.argtypes = [ctypes.c_int, P(f), P(f), P(f), ctypes.c_int]
-    lib.hh_solve.restype = f
-    lib.hh_dim.argtypes = [ctypes.c_int]
-    lib.hh_table_check.argtypes = [d, d, ctypes.c_int]
-    lib.hh_table_check.restype = d
-    lib.hh_taylor_k_check.argtypes = [d, d]
-    lib.hh_taylor_k_check.restype = d
-    lib.hh_combine.argtypes = [ctypes.c_int, P(f), P(f), P(f)]
-    lib.hh_chunk_loglik.argtypes = [ctypes.c_int, P(f), P(f), P(f), P(f), d, d, d]
-    lib.hh_chunk_loglik.restype = d
-    lib.hh_boundary_adjoint.argtypes = [ctypes.c_int, P(f), P(f), P(f), P(f), P(f), P(f)]
-    lib.hh_obs_dim.argtypes = [ctypes.c_int]
-    lib.hh_prod_disc.argtypes = [ctypes.c_int, d, P(d), P(d), P(d)]
-    lib.hh_observe.argtypes = [ctypes.c_int, ctypes.c_int, f, P(f), P(f), P(f), P(f), P(f), P(f)]
-    return lib
+    from hostmath import harness
+    return harness.load()
 
 
 def _p(a, t):
