@@ -474,7 +474,7 @@ def run_ours(args):
                "d2h_bytes_per_step": int(d2h), "ms_per_step": el * 1e3}
     # the plain FP64 per-series filter and the FP32 path's error against it
     extra = {"fp32_peak_tflops_measured": fp32_peak, "n_sms": n_sms,
-             "combine_precision": args.combine_precision or 64}
+             "combine_precision": args.combine_precision or 32}
     if not args.no_fp64:
         m64 = gp.Model.from_workload(wl, precision=64)
         # shared sets on one long series: four sets (one FP64 thread each)

@@ -125,6 +125,29 @@ __global__ void __launch_bounds__(256) k_fma_peak(float *__restrict__ sink, int 
   if (r == -12345.0f) sink[blockIdx.x] = r;
 }
 
+__global__ void k_interleave(DevModel M, int c_begin, int c_count, float4 *__restrict__ ilv,
+                             uint8_t *__restrict__ ilv_tag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c_count) return;
+  const int c = c_begin + i;
+  const int64_t e0 = M.ch_ev0[c];
+  const int len = M.ch_len[c];
+  int64_t mi = M.ch_meas0[c];
+  int64_t idx = lane_step(M, c, 0);
+  for (int k = 0; k < len; ++k, idx += 32) {
+    const uint8_t t = M.tag[e0 + k];
+    float4 r = make_float4(M.dt[e0 + k], 0.f, 0.f, 0.f);
+    if (t & 1) {
+      const float4 q = M.meas[mi++];
+      r.y = q.x;
+      r.z = q.y;
+      r.w = q.z;
+    }
+    ilv[idx] = r;
+    ilv_tag[idx] = t;
+  }
+}
+
 // Measurement records (y, r0, w) -> the float4 layout the chunk kernels read.
 __global__ void k_pack_meas(const float *__restrict__ in3, float4 *__restrict__ out, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -221,6 +244,9 @@ struct gp_ss_model {
   // chunk) lane-steps; d_w_doff[w] = lane-steps before warp w, [n_w] = total
   int64_t *d_w_doff = nullptr;
   int64_t dcache_steps = 0;
+  // the event stream in lane-step order (k_interleave), for the chunk plan
+  float4 *d_ilv = nullptr;
+  uint8_t *d_ilv_tag = nullptr;
   // per-call scratch comes from this model's stream-ordered pool, which keeps
   // freed memory reserved (no unmapping and re-mapping at every synchronise)
   cudaMemPool_t pool = nullptr;
@@ -320,7 +346,7 @@ void free_model_buffers(gp_ss_model *m) {
   void *dev[] = {m->d_ev_off, m->d_meas_off, m->d_dt, m->d_tag, m->d_meas, m->d_dt64, m->d_meas64,
                  m->d_mev,
                  m->d_ch_ev0, m->d_ch_meas0, m->d_ch_len, m->d_ch_series, m->d_ch_first,
-                 m->d_ch_flags, m->d_w_doff, m->d_err};
+                 m->d_ch_flags, m->d_w_doff, m->d_err, m->d_ilv, m->d_ilv_tag};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (m->pool) {
@@ -496,6 +522,18 @@ void build_series(int64_t a, int64_t b, int64_t e0, const double *ts, const doub
   }
 }
 
+gpss::DevModel dev_view(const gp_ss_model *m);
+
+// Re-lay the event stream of chunks [c0, c0 + cn) in the plan's lane-step
+// order (after a new plan, or after the event stream was re-sent).
+cudaError_t interleave_events(const gp_ss_model *m, int c0, int cn, cudaStream_t st) {
+  if (cn <= 0 || !m->d_ilv) return cudaSuccess;
+  gpss::k_interleave<<<(cn + 127) / 128, 128, 0, st>>>(dev_view(m), c0, cn, m->d_ilv,
+                                                        m->d_ilv_tag);
+  GPSS_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
 gp_ss_status make_plan(gp_ss_model *m, int chunk_len) {
   const int n = m->n_series;
   int L = chunk_len;
@@ -561,22 +599,29 @@ gp_ss_status make_plan(gp_ss_model *m, int chunk_len) {
   if (!st) st = dev_upload(&n_first, first.data(), first.size());
   if (!st) st = dev_upload(&n_flags, flags.data(), flags.size());
   if (!st) st = dev_upload(&n_doff, doff.data(), doff.size());
+  // the event stream in this plan's lane-step order
+  float4 *n_ilv = nullptr;
+  uint8_t *n_ilv_tag = nullptr;
+  if (!st) st = dev_upload<float4>(&n_ilv, nullptr, (size_t)doff[n_w]);
+  if (!st) st = dev_upload<uint8_t>(&n_ilv_tag, nullptr, (size_t)doff[n_w]);
   if (st) {
-    void *fresh[] = {n_ev0, n_meas0, n_len, n_ser, n_first, n_flags, n_doff};
+    void *fresh[] = {n_ev0, n_meas0, n_len, n_ser, n_first, n_flags, n_doff, n_ilv, n_ilv_tag};
     for (void *p : fresh)
       if (p) cudaFree(p);
     return st;
   }
   // kernels queued earlier may still read the old plan
   if (cudaDeviceSynchronize() != cudaSuccess) {
-    void *fresh[] = {n_ev0, n_meas0, n_len, n_ser, n_first, n_flags, n_doff};
+    void *fresh[] = {n_ev0, n_meas0, n_len, n_ser, n_first, n_flags, n_doff, n_ilv, n_ilv_tag};
     for (void *p : fresh) cudaFree(p);
     return GP_SS_ECUDA;
   }
   void *old[] = {m->d_ch_ev0, m->d_ch_meas0, m->d_ch_len, m->d_ch_series, m->d_ch_first,
-                 m->d_ch_flags, m->d_w_doff};
+                 m->d_ch_flags, m->d_w_doff, m->d_ilv, m->d_ilv_tag};
   for (void *p : old)
     if (p) cudaFree(p);
+  m->d_ilv = n_ilv;
+  m->d_ilv_tag = n_ilv_tag;
   m->d_ch_ev0 = n_ev0;
   m->d_ch_meas0 = n_meas0;
   m->d_ch_len = n_len;
@@ -592,6 +637,9 @@ gp_ss_status make_plan(gp_ss_model *m, int chunk_len) {
   m->max_chunks_per_series = 0;
   for (int s = 0; s < n; ++s)
     m->max_chunks_per_series = std::max(m->max_chunks_per_series, first[s + 1] - first[s]);
+  if (interleave_events(m, 0, m->n_chunks, nullptr) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess)
+    return GP_SS_ECUDA;
   for (auto &kv : m->graphs) cudaGraphExecDestroy(kv.second);
   m->graphs.clear();
   return GP_SS_OK;
@@ -620,6 +668,8 @@ gpss::DevModel dev_view(const gp_ss_model *m) {
   d.n_events = m->n_events;
   d.w_doff = m->d_w_doff;
   d.dcache_steps = m->dcache_steps;
+  d.ilv = m->d_ilv;
+  d.ilv_tag = m->d_ilv_tag;
   return d;
 }
 
@@ -1444,6 +1494,10 @@ gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *m, const float *theta_hos
             d_meas3 + 3 * q0, m->d_meas + q0, q1 - q0);
         GPSS_COUNT_LAUNCH();
       }
+      if (interleave_events(m, c0[g], m->ch_first[sb[g + 1]] - c0[g], cs) != cudaSuccess) {
+        res = GP_SS_ECUDA;
+        break;
+      }
       if (cudaGetLastError() != cudaSuccess || cudaEventRecord(ready[g], cs)) res = GP_SS_ECUDA;
     }
     if (d_meas3) cudaFreeAsync(d_meas3, cs);
@@ -1453,7 +1507,8 @@ gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *m, const float *theta_hos
                         cudaMemcpyHostToDevice, st) ||
         cudaMemcpyAsync(m->d_tag, m->h_tag, (size_t)m->n_events, cudaMemcpyHostToDevice, st) ||
         cudaMemcpyAsync(m->d_meas, m->h_meas, (size_t)m->n_meas * sizeof(float4),
-                        cudaMemcpyHostToDevice, st))
+                        cudaMemcpyHostToDevice, st) ||
+        interleave_events(m, 0, m->n_chunks, st))
       res = GP_SS_ECUDA;
   }
   if (!res && cudaMemcpyAsync(d_theta, theta_host, nth * sizeof(float), cudaMemcpyHostToDevice, st))
@@ -1659,13 +1714,17 @@ gp_ss_status gp_ss_autotune(gp_ss_model *m, const float *theta, int n_sets,
     int schedule, L, combine, ck;
   };
   std::vector<Cand> cands;
-  const int Ls[] = {64, 128, 192, 256, 384, 512, 1024};
+  // chunk lengths: besides the work per thread, the length sets how many
+  // waves of blocks a launch takes, so lengths between the round ones let the
+  // last wave come out fuller
+  const int Ls[] = {64, 128, 160, 192, 224, 256, 288, 320, 384, 448, 512, 1024};
   if (want_grad) {
-    for (int ck : {16, 32, 64}) {
+    for (int ck : {32, 64}) {
       cands.push_back({1, 0, 2, ck});
       for (int L : Ls)
         if (L >= 128 && L <= 512) cands.push_back({2, L, 2, ck});
     }
+    cands.push_back({2, 256, 2, 16});
     cands.push_back({2, 256, 1, 32});
   } else {
     cands.push_back({3, 0, 2, 32});

@@ -63,7 +63,19 @@ struct DevModel {
   // dcache_steps; the record of step k is DcW<NT>::G float4 groups x 32 lanes
   const int64_t *w_doff;
   int64_t dcache_steps;
+  // the event stream re-laid out for the chunk kernels, in the lane-step
+  // order of the step-scalar cache: step k of the chunk on lane l of warp w
+  // at w_doff[w] + 32 k + l; record (dt, y, yerr^2, 1/delta) (zeros but dt
+  // at an exposure start) and its tag byte.  A warp's loads of one step are
+  // one 512-byte and one 32-byte contiguous access.
+  const float4 *ilv;
+  const uint8_t *ilv_tag;
 };
+
+// Lane-step index of step k of chunk c.
+GPSS_D int64_t lane_step(const DevModel &M, int c, int k) {
+  return M.w_doff[c >> 5] + (int64_t)k * 32 + (c & 31);
+}
 
 // Test times of a prediction call, grouped by the event that closes their
 // interval: points [off[e], off[e+1]) lie in (t_{e-1}, t_e] of event e's
@@ -215,46 +227,49 @@ GPSS_D bool filter_event(const DevModel &M, int64_t k, int64_t &mi, const TermC<
   return filter_step<S, F, OD>(dt, tag, y, r0, w, tc, s2, m, P, Sv, v, tab);
 }
 
-// Event reader for the FP32 chunk kernels: the gap and tag of the next event
-// and the next measurement record are loaded one step ahead of their use, so
-// their latency overlaps the arithmetic of the current event.
+// Event reader for the FP32 chunk kernels over the lane-step records: the
+// next step's record and tag are loaded one step ahead of their use, so
+// their latency overlaps the arithmetic of the current event.  The lanes of
+// a warp read consecutive records (coalesced).
 struct EventReader {
-  const float *dt;
-  const uint8_t *tag;
-  const float4 *meas;
-  int64_t k, kend, mi;
-  float dt_n;
+  const float4 *rec;
+  const uint8_t *tg;
+  int64_t idx;
+  int k, kend;
+  float4 r_n;
   uint8_t tag_n;
-  float4 q_n;
-  GPSS_D void start(const DevModel &M, int64_t k0, int64_t k1, int64_t m0) {
-    dt = M.dt;
-    tag = M.tag;
-    meas = M.meas;
+  // steps [k0, k1) of chunk c
+  GPSS_D void start(const DevModel &M, int c, int k0, int k1) {
+    rec = M.ilv;
+    tg = M.ilv_tag;
+    idx = lane_step(M, c, k0);
     k = k0;
     kend = k1;
-    mi = m0;
     if (k < kend) {
-      dt_n = __ldg(dt + k);
-      tag_n = __ldg(tag + k);
+      r_n = __ldg(rec + idx);
+      tag_n = __ldg(tg + idx);
     }
-    q_n = __ldg(meas + mi);
   }
-  // current event's data; prefetches the following one
+  // current event's gap, tag and measurement record (y, yerr^2, 1/delta, 0);
+  // prefetches the following one
   GPSS_D void next(float &d, uint8_t &t, float4 &q) {
-    d = dt_n;
+    d = r_n.x;
     t = tag_n;
-    q = q_n;
+    q = make_float4(r_n.y, r_n.z, r_n.w, 0.f);
     ++k;
+    idx += 32;
     if (k < kend) {
-      dt_n = __ldg(dt + k);
-      tag_n = __ldg(tag + k);
-    }
-    if (t & 1) {
-      ++mi;
-      q_n = __ldg(meas + mi);
+      r_n = __ldg(rec + idx);
+      tag_n = __ldg(tg + idx);
     }
   }
 };
+
+// Lay the event stream out in lane-step order (one thread per chunk, after
+// every change of the chunk plan or of the event stream): chunks
+// [c_begin, c_begin + c_count).
+__global__ void k_interleave(DevModel M, int c_begin, int c_count, float4 *__restrict__ ilv,
+                             uint8_t *__restrict__ ilv_tag);
 
 GPSS_D void flag_error(int *err, int row, int code) {
   if (err) atomicMax(err + row, code);
@@ -576,11 +591,10 @@ __global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restric
   double gam = 0.0, ld = 0.0;
   int n_end = 0;
   bool bad = false;
-  const int64_t e0 = M.ch_ev0[c];
   const int len = M.ch_len[c];
   float4 *dc = dcache_col<S::NT>(M, dcache, vc);
   EventReader rd;
-  rd.start(M, e0, e0 + len, M.ch_meas0[c]);
+  rd.start(M, c, 0, len);
   // gradient segments end at len - j ck (the first one is the short one);
   // at each later segment's start the partial element is saved
   const int f0 = len - ((len - 1) / ck) * ck;
@@ -1284,20 +1298,9 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   const int s = M.ch_series[c];
   const int row = per_series ? s : set;
   const int orow = per_series ? s : set * M.n_series + s;
-  // Per-term constants of the row (one row per warp: a warp's 32 chunks lie
-  // in one series and one parameter set) and the gradient accumulators live
-  // in shared memory, which frees registers for the filter state.
-  __shared__ TermC<F> s_tc[GRAD_BS / 32][S::NT];
-  __shared__ TermGrad<S::NT> s_gr[GRAD_BS];
-  TermC<F> *tc = s_tc[threadIdx.x >> 5];
+  TermC<F> tc[S::NT];
   F s2;
-  {
-    TermC<F> tl[S::NT];
-    load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tl, s2);
-    if ((threadIdx.x & 31) == 0)
-      for (int t = 0; t < S::NT; ++t) tc[t] = tl[t];
-    __syncwarp();
-  }
+  load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tc, s2);
   // shared memory: the warps' tables, then two staging buffers per thread
   // for the backward walk, stg[(buf (SG + NDG) + group) bs + thread] (float4)
   float4 *tab_slots = reinterpret_cast<float4 *>(sm);
@@ -1324,11 +1327,10 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
     } else {
       load_rec<S>(adj_end, n_vch, vc, lam, Lam);
     }
-    TermGrad<S::NT> &gr = s_gr[threadIdx.x];
+    TermGrad<S::NT> gr;
   #pragma unroll
     for (int t = 0; t < S::NT; ++t) gr.a[t] = gr.beta[t] = gr.w2[t] = gr.qc[t] = gr.var[t] = F(0);
     gr.s2 = F(0);
-    const int64_t m0 = M.ch_meas0[c];
     // per-event exposure adjoints of this chunk (theta set `set`)
     const int64_t eo = (int64_t)set * M.n_events + e0;
     float4 *my = reinterpret_cast<float4 *>(rbuf) + vc;  // group v of slot k at (k SG + v) n_vch
@@ -1338,7 +1340,6 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
     for (int seg = nseg - 1; seg >= 0; --seg) {
       const int k0 = seg == 0 ? 0 : f0 + (seg - 1) * ck;
       const int k1 = seg == 0 ? f0 : k0 + ck;
-      int mrel = 0;
       if (seg == 0) {
         if (first)
           init_state<S>(tc, m, P);
@@ -1357,12 +1358,11 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
         }
         const float *src = pck + (size_t)(seg - 1) * (NF + 1) * n_vch;
         apply_partial<S>(src, n_vch, vc, mi, Pi, m, P);
-        mrel = __float_as_int(src[(size_t)NF * n_vch + vc]);
       }
       // forward replay of the segment (step scalars from the cache, the next
       // step's loaded one ahead, or recomputed)
       EventReader rd;
-      rd.start(M, e0 + k0, e0 + k1, m0 + mrel);
+      rd.start(M, c, k0, k1);
       const float4 *dcr = dc ? dc + (size_t)k0 * (32 * NDG) : nullptr;
       float nx[NDC];
       if (dcr) dcache_load<S::NT>(dcr, nx);
@@ -1399,12 +1399,13 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       }
       // conditioned mean and variance of the chunk's last event, if it ends an
       // exposure: the chunk's end state and its boundary adjoint
-      if (EX && cond && seg == nseg - 1 && (__ldg(M.tag + e0 + k1 - 1) & 1)) {
-        const uint8_t tl = __ldg(M.tag + e0 + k1 - 1);
-        const float4 ql = __ldg(M.meas + rd.mi - 1);
+      if (EX && cond && seg == nseg - 1 && (__ldg(M.ilv_tag + lane_step(M, c, k1 - 1)) & 1)) {
+        const int64_t il = lane_step(M, c, k1 - 1);
+        const uint8_t tl = __ldg(M.ilv_tag + il);
+        const float4 rl = __ldg(M.ilv + il);
         F mb[D], Pb[S::NP];
         load_state_f<S>(state_end, se64, n_vch, vc, mb, Pb);
-        cond[eo + k1 - 1] = conditioned<S>((tl >> 1) & 7, ql.z, mb, Pb, lam, Lam);
+        cond[eo + k1 - 1] = conditioned<S>((tl >> 1) & 7, rl.w, mb, Pb, lam, Lam);
       }
       // test times after the series' last event: predicted from its filtered
       // state (which all the data already conditions)
@@ -1424,9 +1425,7 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       }
       // backward walk.  The earlier step's replayed state and cached scalars
       // are staged into shared memory by cp.async while the current step is
-      // processed; its gap, tag and measurement record are loaded one ahead.
-      // The measurement index of event k (relative to m0) is the count of end
-      // events before k, tracked downwards from the replay's end.
+      // processed; its lane-step record and tag are loaded one ahead.
       auto stage = [&](int buf, int slot, int kk) {
         float4 *dst = stg + (size_t)buf * (SG + NDG) * bs;
   #pragma unroll
@@ -1439,21 +1438,19 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
         cp_async_commit();
       };
       int k2 = k1 - 1;
-      F dt_n = __ldg(M.dt + e0 + k2);
-      uint8_t tag_n = __ldg(M.tag + e0 + k2);
-      int mr = (int)(rd.mi - m0) - (tag_n & 1);
-      float4 q_n = __ldg(M.meas + m0 + mr);
+      int64_t li = lane_step(M, c, k2);
+      float4 r_n = __ldg(M.ilv + li);
+      uint8_t tag_n = __ldg(M.ilv_tag + li);
       stage(0, k2 - k0, k2);
       for (; k2 >= k0; --k2) {
         const int slot = k2 - k0, buf = (k1 - 1 - k2) & 1;
-        const F dt = dt_n;
+        const F dt = r_n.x;
         const uint8_t tag = tag_n;
-        const float4 q = q_n;
+        const float4 q = make_float4(r_n.y, r_n.z, r_n.w, 0.f);
         if (k2 > k0) {
-          dt_n = __ldg(M.dt + e0 + k2 - 1);
-          tag_n = __ldg(M.tag + e0 + k2 - 1);
-          mr -= tag_n & 1;
-          q_n = __ldg(M.meas + m0 + mr);
+          li -= 32;
+          r_n = __ldg(M.ilv + li);
+          tag_n = __ldg(M.ilv_tag + li);
           stage(buf ^ 1, slot - 1, k2 - 1);
           cp_async_wait<1>();
         } else {
@@ -1514,10 +1511,11 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
         // (m, P) is the filtered state after event k2 - 1 and (lam, Lam) now its
         // adjoint: the conditioned values of that event's measurement
         if (EX && cond && k2 > 0) {
-          const uint8_t tp = k2 > k0 ? tag_n : __ldg(M.tag + e0 + k2 - 1);
+          const int64_t lp = lane_step(M, c, k2 - 1);
+          const uint8_t tp = k2 > k0 ? tag_n : __ldg(M.ilv_tag + lp);
           if (tp & 1) {
-            const float4 qp = k2 > k0 ? q_n : __ldg(M.meas + m0 + mr - 1);
-            cond[eo + k2 - 1] = conditioned<S>((tp >> 1) & 7, qp.z, m, P, lam, Lam);
+            const float wp = k2 > k0 ? r_n.w : __ldg(M.ilv + lp).w;
+            cond[eo + k2 - 1] = conditioned<S>((tp >> 1) & 7, wp, m, P, lam, Lam);
           }
         }
       }
