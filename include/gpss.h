@@ -245,7 +245,7 @@ gp_ss_status gp_ss_discretize(const gp_ss_kernel_spec *spec, int n_slots, const 
  * process exits.  It calls no allocation routine of CUDA or of any library.
  *   - Arguments and result as gp_ss_loglik; theta and loglik_out are
  *     caller-owned device buffers.
- *   - Scratch needed: 960*n_terms*n_sets bytes of step-scalar tables and
+ *   - Scratch needed: 800*n_terms*n_sets bytes of step-scalar tables and
  *     NF*n_chunks*4 bytes (each rounded up to 256) + 24*n_chunks bytes,
  *     NF = 2d^2 + 3d (d = augmented dimension; 90 at d = 6), n_chunks the
  *     model's chunk count times n_sets when theta_per_series = 0.

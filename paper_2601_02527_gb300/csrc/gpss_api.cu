@@ -134,17 +134,31 @@ __global__ void k_interleave(DevModel M, int c_begin, int c_count, float4 *__res
   const int len = M.ch_len[c];
   int64_t mi = M.ch_meas0[c];
   int64_t idx = lane_step(M, c, 0);
-  for (int k = 0; k < len; ++k, idx += 32) {
-    const uint8_t t = M.tag[e0 + k];
-    float4 r = make_float4(M.dt[e0 + k], 0.f, 0.f, 0.f);
-    if (t & 1) {
-      const float4 q = M.meas[mi++];
-      r.y = q.x;
-      r.z = q.y;
-      r.w = q.z;
+  // eight steps at a time: their loads are independent, so they are in
+  // flight together
+  constexpr int U = 8;
+  for (int k0 = 0; k0 < len; k0 += U, idx += 32 * U) {
+    uint8_t t[U];
+    float dt[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      t[u] = k0 + u < len ? M.tag[e0 + k0 + u] : 0;
+      dt[u] = k0 + u < len ? M.dt[e0 + k0 + u] : 0.f;
     }
-    ilv[idx] = r;
-    ilv_tag[idx] = t;
+    float4 q[U];
+    int64_t mu = mi;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      q[u] = (t[u] & 1) ? M.meas[mu] : make_float4(0.f, 0.f, 0.f, 0.f);
+      mu += t[u] & 1;
+    }
+    mi = mu;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k0 + u < len) {
+        ilv[idx + 32 * u] = make_float4(dt[u], q[u].x, q[u].y, q[u].z);
+        ilv_tag[idx + 32 * u] = t[u];
+      }
   }
 }
 
@@ -744,7 +758,8 @@ gp_ss_status check_call(const gp_ss_model *m, const float *theta, int n_sets, in
 }
 
 // Series groups whose event streams arrive separately: the element pass of
-// group g (chunks [c0[g], c0[g+1])) waits for event ready[g].
+// group g (chunks [c0[g], c0[g+1])) waits for event ready[g] and first lays
+// the group's new events out in lane-step order.
 struct ElemSlices {
   int n;
   const int *c0;
@@ -852,6 +867,9 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
         const int c0 = slices ? slices->c0[g] : 0;
         const int cn = slices ? slices->c0[g + 1] - c0 : m->n_chunks;
         if (slices && cudaStreamWaitEvent(st, slices->ready[g], 0) != cudaSuccess) res = GP_SS_ECUDA;
+        // a re-sent group's events are laid out for the chunk kernels here,
+        // on the compute stream, while the copy stream sends the next group
+        if (!res && slices && interleave_events(m, c0, cn, st) != cudaSuccess) res = GP_SS_ECUDA;
         if (!res && o.elem(dm, theta, n_vch, per_series, ef, ed, m->d_err, tabs,
                            grad ? ckpt : nullptr, ck, dcache, c0, cn, st))
           res = GP_SS_ECUDA;
@@ -1494,10 +1512,7 @@ gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *m, const float *theta_hos
             d_meas3 + 3 * q0, m->d_meas + q0, q1 - q0);
         GPSS_COUNT_LAUNCH();
       }
-      if (interleave_events(m, c0[g], m->ch_first[sb[g + 1]] - c0[g], cs) != cudaSuccess) {
-        res = GP_SS_ECUDA;
-        break;
-      }
+
       if (cudaGetLastError() != cudaSuccess || cudaEventRecord(ready[g], cs)) res = GP_SS_ECUDA;
     }
     if (d_meas3) cudaFreeAsync(d_meas3, cs);

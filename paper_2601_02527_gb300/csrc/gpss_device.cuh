@@ -468,11 +468,12 @@ GPSS_HD void sinc_pair_k(float t, float b, float rb, float &S, float &C) {
 // the tangent series are economised like the values.
 //
 // Table layout per (row, term): for k = 0..NC-1 one record of TAB_W floats:
-// [6 values, 2 pad, 6 d/da, 2 pad, 6 d/dbeta, 2 pad].
+// [6 values, 2 pad, 6 d/da, 6 d/dbeta] (five float4: the values are read as
+// two, the twelve tangents as three).
 // ---------------------------------------------------------------------------
 constexpr int TAB_NC = 10;
 constexpr int TAB_NTAY = 22;
-constexpr int TAB_W = 24;
+constexpr int TAB_W = 20;
 constexpr int TAB_TERM = TAB_NC * TAB_W;
 
 // Taylor coefficients g[j][k], k < TAB_NTAY, of the six series.
@@ -590,6 +591,138 @@ GPSS_HD T econ_apply(const EconMap &E, int k, double rng, const T *g, int stride
   return econ_apply<T>(E.m, k, rng, g, stride);
 }
 
+// ---------------------------------------------------------------------------
+// Double-float numbers for the table generation: the unevaluated sum hi + lo
+// of two floats (about 48 significant bits), built on the error-free
+// transformations TwoSum (Knuth) and TwoProduct by fused multiply-add
+// (Dekker's product with an FMA), with the accurate addition of the
+// double-double literature (both parts' errors carried).  They run on the
+// FP32 pipe, which on this GPU is many times wider than the FP64 one.
+// ---------------------------------------------------------------------------
+struct DF {
+  float hi, lo;
+};
+GPSS_HD DF df_of(double x) {
+  const float h = (float)x;
+  return DF{h, (float)(x - (double)h)};
+}
+GPSS_HD double df_val(DF x) { return (double)x.hi + (double)x.lo; }
+GPSS_HD DF df_fast(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = a + b;
+  return DF{s, b - (s - a)};
+}
+GPSS_HD DF df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return DF{s, (a - (s - bb)) + (b - bb)};
+}
+GPSS_HD DF operator+(DF x, DF y) {
+  DF s = df_two_sum(x.hi, y.hi);
+  const DF t = df_two_sum(x.lo, y.lo);
+  s.lo += t.hi;
+  s = df_fast(s.hi, s.lo);
+  s.lo += t.lo;
+  return df_fast(s.hi, s.lo);
+}
+GPSS_HD DF operator-(DF x) { return DF{-x.hi, -x.lo}; }
+GPSS_HD DF operator-(DF x, DF y) { return x + (-y); }
+GPSS_HD DF operator*(DF x, DF y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+  return df_fast(p, e);
+}
+GPSS_HD Dual2<DF> mkdf(DF v, DF da, DF db) { return Dual2<DF>{v, da, db}; }
+GPSS_HD Dual2<DF> operator*(Dual2<DF> x, DF c) { return mkdf(x.v * c, x.da * c, x.db * c); }
+
+// Table coefficients with the scale of the table's range T taken out, in
+// double-float (the form the table kernel computes; FP64 inputs, FP32 pipe).
+// With c~_n = c_n T^n the oscillator recurrence reads
+//   c~_{n+2} = -(2 a T (n+1) c~_{n+1} + w2 T^2 c~_n) / ((n+2)(n+1)),
+// c~_0 = 0, c~_1 = T, c~_2 = -a T^2, and every coefficient stays of order one
+// however large or small omega0 is (omega0 T is about 1.2).  Coefficient n of
+// series j times T^(n + q_j) (q = 1 for f, f', F1; 2 for I_ff, I_pp, I_FF)
+// then follows from the c~ alone, and the economisation, linear with T fixed,
+// maps these to the table's coefficients times T^(k + q_j).
+// taylor_c_scaled: the recurrence into c (NCF + 1 entries).
+GPSS_HD void taylor_c_scaled(Dual2<DF> aT, Dual2<DF> w2T2, const DF *rcp, Dual2<DF> *c,
+                             DF T) {
+  const DF z = df_of(0.0);
+  c[0] = mkdf(z, z, z);
+  c[1] = mkdf(T, z, z);
+  c[2] = -(aT * T);
+  for (int n = 1; n + 2 <= TAB_NCF; ++n) {
+    const DF two_n1 = df_of(2.0 * (n + 1));
+    c[n + 2] = -((aT * two_n1) * c[n + 1] + w2T2 * c[n]) * (rcp[n + 2] * rcp[n + 1]);
+  }
+}
+
+// Coefficient k of the six scaled series from c~ (e_n = c~_n / (n+1) and
+// p_n = n c~_n precomputed), as taylor_coeff_pre with the T factors out.
+GPSS_HD void taylor_coeff_scaled(const Dual2<DF> *c, const Dual2<DF> *e, const Dual2<DF> *p,
+                                 const DF *rcp, int k, Dual2<DF> (&g)[6]) {
+  const DF z = df_of(0.0);
+  Dual2<DF> s1 = mkdf(z, z, z), s2 = s1, s3 = s1;
+  for (int n = 1; n <= k + 1; ++n) {
+    const int m = k + 2 - n;
+    s1 = s1 + c[n] * c[m];
+    s2 = s2 + p[n] * p[m];
+    s3 = s3 + e[n] * e[m];
+  }
+  g[0] = c[k + 1];
+  g[1] = c[k + 1] * df_of((double)(k + 1));
+  g[2] = c[k + 1] * rcp[k + 2];
+  g[3] = s1 * rcp[k + 3];
+  g[4] = s2 * rcp[k + 1];
+  g[5] = s3 * rcp[k + 5];
+}
+
+// Economised coefficient k of one scaled series: sum_n m[k][n] g~_n.
+GPSS_HD Dual2<DF> econ_apply_scaled(const DF (*m)[TAB_NTAY], int k, const Dual2<DF> *g) {
+  const DF z = df_of(0.0);
+  Dual2<DF> acc = mkdf(z, z, z);
+  for (int n = k; n < TAB_NTAY; ++n) acc = acc + g[n] * m[k][n];
+  return acc;
+}
+
+// Power of T that scales series j's coefficients (beyond T^k).
+GPSS_HD int table_q(int j) { return j < 3 ? 1 : 2; }
+
+// One term's table by the double-float path, sequentially (the table kernel
+// computes the same quantities, one coefficient per lane): values and (a,
+// beta) tangents of e[j][k] = table coefficient k of series j, in t.
+GPSS_HD void table_coeffs_df(const EconMap &E, double a, double beta, double (&v)[6][TAB_NC],
+                             double (&da)[6][TAB_NC], double (&db)[6][TAB_NC]) {
+  DF rcp[2 * TAB_NTAY + 8];
+  for (int i = 0; i < 2 * TAB_NTAY + 8; ++i) rcp[i] = df_of(E.rcp[i]);
+  const double T = table_range(rate2<double>(a, beta));
+  const DF one = df_of(1.0), zero = df_of(0.0);
+  const Dual2<DF> ad = mkdf(df_of(a), one, zero), bd = mkdf(df_of(beta), zero, one);
+  const Dual2<DF> w2 = bd + ad * ad;
+  Dual2<DF> c[TAB_NCF + 1], e[TAB_NCF + 1], p[TAB_NCF + 1], g[6][TAB_NTAY];
+  taylor_c_scaled(ad * df_of(T), w2 * df_of(T * T), rcp, c, df_of(T));
+  for (int n = 0; n <= TAB_NCF; ++n) {
+    e[n] = c[n] * rcp[n + 1];
+    p[n] = c[n] * df_of((double)n);
+  }
+  for (int k = 0; k < TAB_NTAY; ++k) {
+    Dual2<DF> h[6];
+    taylor_coeff_scaled(c, e, p, rcp, k, h);
+    for (int j = 0; j < 6; ++j) g[j][k] = h[j];
+  }
+  DF m[TAB_NC][TAB_NTAY];
+  for (int k = 0; k < TAB_NC; ++k)
+    for (int n = 0; n < TAB_NTAY; ++n) m[k][n] = df_of(E.m[k][n]);
+  for (int j = 0; j < 6; ++j)
+    for (int k = 0; k < TAB_NC; ++k) {
+      const Dual2<DF> r = econ_apply_scaled(m, k, g[j]);
+      const double sc = pow(T, -(double)(k + table_q(j)));
+      v[j][k] = df_val(r.v) * sc;
+      da[j][k] = df_val(r.da) * sc;
+      db[j][k] = df_val(r.db) * sc;
+    }
+}
+
 // Economised table coefficients e[j][k], k < TAB_NC, on [0, T] (FP64).
 template <class T>
 GPSS_HD void table_coeffs(const EconMap &E, T a, T beta, T (&e)[6][TAB_NC]) {
@@ -632,21 +765,21 @@ GPSS_HD Disc<Dual2<float>> disc_tab_dual(float t, const float4 *__restrict__ tab
   float v[6], da[6], db[6];
   {
     const float4 *r = tab + (TAB_NC - 1) * (TAB_W / 4);
-    const float4 q0 = r[0], q1 = r[1], q2 = r[2], q3 = r[3], q4 = r[4], q5 = r[5];
+    const float4 q0 = r[0], q1 = r[1], q2 = r[2], q3 = r[3], q4 = r[4];
     v[0] = q0.x; v[1] = q0.y; v[2] = q0.z; v[3] = q0.w; v[4] = q1.x; v[5] = q1.y;
     da[0] = q2.x; da[1] = q2.y; da[2] = q2.z; da[3] = q2.w; da[4] = q3.x; da[5] = q3.y;
-    db[0] = q4.x; db[1] = q4.y; db[2] = q4.z; db[3] = q4.w; db[4] = q5.x; db[5] = q5.y;
+    db[0] = q3.z; db[1] = q3.w; db[2] = q4.x; db[3] = q4.y; db[4] = q4.z; db[5] = q4.w;
   }
 #pragma unroll 3
   for (int k = TAB_NC - 2; k >= 0; --k) {
     const float4 *r = tab + k * (TAB_W / 4);
-    const float4 q0 = r[0], q1 = r[1], q2 = r[2], q3 = r[3], q4 = r[4], q5 = r[5];
+    const float4 q0 = r[0], q1 = r[1], q2 = r[2], q3 = r[3], q4 = r[4];
     v[0] = fmaf(v[0], t, q0.x); v[1] = fmaf(v[1], t, q0.y); v[2] = fmaf(v[2], t, q0.z);
     v[3] = fmaf(v[3], t, q0.w); v[4] = fmaf(v[4], t, q1.x); v[5] = fmaf(v[5], t, q1.y);
     da[0] = fmaf(da[0], t, q2.x); da[1] = fmaf(da[1], t, q2.y); da[2] = fmaf(da[2], t, q2.z);
     da[3] = fmaf(da[3], t, q2.w); da[4] = fmaf(da[4], t, q3.x); da[5] = fmaf(da[5], t, q3.y);
-    db[0] = fmaf(db[0], t, q4.x); db[1] = fmaf(db[1], t, q4.y); db[2] = fmaf(db[2], t, q4.z);
-    db[3] = fmaf(db[3], t, q4.w); db[4] = fmaf(db[4], t, q5.x); db[5] = fmaf(db[5], t, q5.y);
+    db[0] = fmaf(db[0], t, q3.z); db[1] = fmaf(db[1], t, q3.w); db[2] = fmaf(db[2], t, q4.x);
+    db[3] = fmaf(db[3], t, q4.y); db[4] = fmaf(db[4], t, q4.z); db[5] = fmaf(db[5], t, q4.w);
   }
   const float t2 = t * t, t3 = t2 * t;
   const float sc[6] = {t, 1.f, t2, t3, t, t3 * t2};
@@ -789,18 +922,18 @@ GPSS_HD void disc_tab_tangents(float t, const float4 *__restrict__ tab, float (&
                                float (&db)[6]) {
   {
     const float4 *r = tab + (TAB_NC - 1) * (TAB_W / 4);
-    const float4 q2 = r[2], q3 = r[3], q4 = r[4], q5 = r[5];
+    const float4 q2 = r[2], q3 = r[3], q4 = r[4];
     da[0] = q2.x; da[1] = q2.y; da[2] = q2.z; da[3] = q2.w; da[4] = q3.x; da[5] = q3.y;
-    db[0] = q4.x; db[1] = q4.y; db[2] = q4.z; db[3] = q4.w; db[4] = q5.x; db[5] = q5.y;
+    db[0] = q3.z; db[1] = q3.w; db[2] = q4.x; db[3] = q4.y; db[4] = q4.z; db[5] = q4.w;
   }
 #pragma unroll 3
   for (int k = TAB_NC - 2; k >= 0; --k) {
     const float4 *r = tab + k * (TAB_W / 4);
-    const float4 q2 = r[2], q3 = r[3], q4 = r[4], q5 = r[5];
+    const float4 q2 = r[2], q3 = r[3], q4 = r[4];
     da[0] = fmaf(da[0], t, q2.x); da[1] = fmaf(da[1], t, q2.y); da[2] = fmaf(da[2], t, q2.z);
     da[3] = fmaf(da[3], t, q2.w); da[4] = fmaf(da[4], t, q3.x); da[5] = fmaf(da[5], t, q3.y);
-    db[0] = fmaf(db[0], t, q4.x); db[1] = fmaf(db[1], t, q4.y); db[2] = fmaf(db[2], t, q4.z);
-    db[3] = fmaf(db[3], t, q4.w); db[4] = fmaf(db[4], t, q5.x); db[5] = fmaf(db[5], t, q5.y);
+    db[0] = fmaf(db[0], t, q3.z); db[1] = fmaf(db[1], t, q3.w); db[2] = fmaf(db[2], t, q4.x);
+    db[3] = fmaf(db[3], t, q4.y); db[4] = fmaf(db[4], t, q4.z); db[5] = fmaf(db[5], t, q4.w);
   }
   const float t2 = t * t, t3 = t2 * t;
   const float sc[6] = {t, 1.f, t2, t3, t, t3 * t2};

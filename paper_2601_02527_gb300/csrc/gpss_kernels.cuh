@@ -300,12 +300,13 @@ GPSS_D void cp_async_wait() {
 }
 
 // ---------------------------------------------------------------------------
-// Step-scalar tables, one warp per (hyperparameter row, term), FP64 with
-// (a, beta) tangents.  Lane 0 runs the recurrence of f's Taylor coefficients
-// c_n; lanes form the pre-scaled c_n/(n+1) and n c_n; lane k sums the
-// products giving Taylor coefficient k of the six series (definitions as in
-// taylor_coeffs); all lanes then share the outputs of the economisation map.
-// Divisions by integers use the reciprocal table of E (FP64 division is slow).
+// Step-scalar tables, one warp per (hyperparameter row, term), with (a, beta)
+// tangents, in double-float arithmetic on the FP32 pipe (table_coeffs_df is
+// the same computation written sequentially).  Lane 0 runs the scaled
+// recurrence of f's Taylor coefficients c~_n = c_n T^n; lanes form c~_n/(n+1)
+// and n c~_n; lane k sums the products giving coefficient k of the six
+// series; all lanes then share the outputs of the economisation map, each
+// scaled back by T^-(k+q) in FP64 and rounded once to FP32.
 // ---------------------------------------------------------------------------
 constexpr int TABLE_WARPS = 4;
 
@@ -314,17 +315,17 @@ __global__ void __launch_bounds__(32 * TABLE_WARPS) k_tables(const float *__rest
                                                             int n_rows, int n_params, int kind0,
                                                             int kind1, float *__restrict__ tab,
                                                             EconMap E) {
-  using DD = Dual2<double>;
+  using DD = Dual2<DF>;
   constexpr int NCF = TAB_NCF;  // c_0 .. c_NCF
   __shared__ DD sc[TABLE_WARPS][NCF + 1], se[TABLE_WARPS][NCF + 1], sf[TABLE_WARPS][NCF + 1];
   __shared__ DD sg[TABLE_WARPS][6][TAB_NTAY];
   // the economisation map and reciprocals in shared memory: the lanes index
   // them with different k, which the parameter (constant) bank would serialise
-  __shared__ double sm_m[TAB_NC][TAB_NTAY];
-  __shared__ double sm_rcp[2 * TAB_NTAY + 8];
+  __shared__ DF sm_m[TAB_NC][TAB_NTAY];
+  __shared__ DF sm_rcp[2 * TAB_NTAY + 8];
   for (int i = threadIdx.x; i < TAB_NC * TAB_NTAY; i += blockDim.x)
-    sm_m[i / TAB_NTAY][i % TAB_NTAY] = E.m[i / TAB_NTAY][i % TAB_NTAY];
-  for (int i = threadIdx.x; i < 2 * TAB_NTAY + 8; i += blockDim.x) sm_rcp[i] = E.rcp[i];
+    sm_m[i / TAB_NTAY][i % TAB_NTAY] = df_of(E.m[i / TAB_NTAY][i % TAB_NTAY]);
+  for (int i = threadIdx.x; i < 2 * TAB_NTAY + 8; i += blockDim.x) sm_rcp[i] = df_of(E.rcp[i]);
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rt = blockIdx.x * TABLE_WARPS + w;
@@ -334,38 +335,41 @@ __global__ void __launch_bounds__(32 * TABLE_WARPS) k_tables(const float *__rest
   TermC<double> tc[NT];
   double s2;
   load_terms<NT, double>(theta + (size_t)row * n_params, kinds, tc, s2);
-  const DD a = mk(tc[t].a, 1.0, 0.0), beta = mk(tc[t].beta, 0.0, 1.0);
-  if (lane == 0) taylor_c<DD>(a, beta, sm_rcp, &sc[w][0]);
+  const double T = table_range(tc[t].r2);
+  const DF one = df_of(1.0), zero = df_of(0.0);
+  const DD a = mkdf(df_of(tc[t].a), one, zero), beta = mkdf(df_of(tc[t].beta), zero, one);
+  const DD w2 = beta + a * a;
+  if (lane == 0) taylor_c_scaled(a * df_of(T), w2 * df_of(T * T), sm_rcp, &sc[w][0], df_of(T));
   __syncwarp();
   for (int n = lane; n <= NCF; n += 32) {
     const DD c = sc[w][n];
     se[w][n] = c * sm_rcp[n + 1];
-    sf[w][n] = c * (double)n;
+    sf[w][n] = c * df_of((double)n);
   }
   __syncwarp();
   if (lane < TAB_NTAY) {
     DD g[6];
-    taylor_coeff_pre<DD>(&sc[w][0], &se[w][0], &sf[w][0], sm_rcp, lane, g);
+    taylor_coeff_scaled(&sc[w][0], &se[w][0], &sf[w][0], sm_rcp, lane, g);
 #pragma unroll
     for (int j = 0; j < 6; ++j) sg[w][j][lane] = g[j];
   }
   __syncwarp();
-  const double rng = table_range(tc[t].r2);
   float *base = tab + (size_t)rt * TAB_NC * TAB_W;
   for (int o = lane; o < 6 * TAB_NC; o += 32) {
     const int j = o / TAB_NC, k = o % TAB_NC;
-    const DD e = econ_apply<DD>(sm_m, k, rng, &sg[w][j][0], 1);
+    const DD e = econ_apply_scaled(sm_m, k, &sg[w][j][0]);
+    double sT = 1.0;
+    const double iT = 1.0 / T;
+    for (int i = 0; i < k + table_q(j); ++i) sT *= iT;
     float *r = base + (size_t)k * TAB_W;
-    r[j] = (float)e.v;
-    r[8 + j] = (float)e.da;
-    r[16 + j] = (float)e.db;
+    r[j] = (float)(df_val(e.v) * sT);
+    r[8 + j] = (float)(df_val(e.da) * sT);
+    r[14 + j] = (float)(df_val(e.db) * sT);
   }
-  for (int o = lane; o < TAB_NC * 6; o += 32) {
-    const int k = o / 6, p = o % 6;  // the pads: columns 6, 7 of each block of 8
-    float *r = base + (size_t)k * TAB_W;
-    if (p < 2) r[6 + p] = 0.f;
-    else if (p < 4) r[14 + p - 2] = 0.f;
-    else r[22 + p - 4] = 0.f;
+  for (int o = lane; o < TAB_NC * 2; o += 32) {
+    // the pads: columns 6, 7 of each record
+    float *r = base + (size_t)(o >> 1) * TAB_W;
+    r[6 + (o & 1)] = 0.f;
   }
 }
 
@@ -454,6 +458,12 @@ GPSS_D void store_elem(float *dst, int n_vch, int vc, const float (&A)[S::D][S::
   }
 }
 
+// resident 128-thread blocks per SM the register budget of k_elem is sized for
+#ifndef GPSS_ELEM_MIN_BLOCKS
+#define GPSS_ELEM_MIN_BLOCKS 3
+#endif
+constexpr int ELEM_MIN_BLOCKS = GPSS_ELEM_MIN_BLOCKS;
+
 // One event of a chunk element: the filter run from an unknown incoming state
 // x, with mean A x + b, covariance C, information (eta, J) about x from the
 // chunk's measurements so far, gamma = sum c^2/S and sum log S (the element
@@ -541,7 +551,7 @@ GPSS_HD void elem_event(const Blocks<F> *B, uint8_t tag, F y, F r0, F w, F s2,
 // dcache set, every step's six scalars per term go to the step-scalar cache
 // (for the gradient's forward replay).
 template <class S, bool OD>
-__global__ void __launch_bounds__(128) k_elem(DevModel M, const float *__restrict__ theta, int n_vch,
+__global__ void __launch_bounds__(128, ELEM_MIN_BLOCKS) k_elem(DevModel M, const float *__restrict__ theta, int n_vch,
                                               int per_series, float *__restrict__ ef,
                                               double *__restrict__ ed, int *__restrict__ err,
                                               const float *__restrict__ tabs,
@@ -899,6 +909,17 @@ __global__ void __launch_bounds__(128) k_finish(DevModel M, int n_vch, int per_s
 // Reverse-time gradient, one thread per chunk.
 // ---------------------------------------------------------------------------
 constexpr int GRAD_BS = 64;
+// resident blocks per SM the register budget of k_grad is sized for
+#ifndef GPSS_GRAD_MIN_BLOCKS
+#define GPSS_GRAD_MIN_BLOCKS 6
+#endif
+constexpr int GRAD_MIN_BLOCKS = GPSS_GRAD_MIN_BLOCKS;
+// cp.async stages of the backward walk's staging (replay record and cached
+// step scalars): the step GRAD_STAGES - 1 ahead is in flight
+#ifndef GPSS_GRAD_STAGES
+#define GPSS_GRAD_STAGES 2
+#endif
+constexpr int GRAD_STAGES = GPSS_GRAD_STAGES;
 template <int NT>
 struct TermGrad {
   float a[NT], beta[NT], w2[NT], qc[NT], var[NT];
@@ -1273,7 +1294,7 @@ GPSS_HD void apply_partial(const float *src, int n_vch, int vc, const float *m_i
 // (gap before k) and, at an end event, gwe[...] = w^2 d loglik / d w
 // (w = 1/delta of its measurement; dw/dt_start = w^2 = -dw/dt_end).
 template <class S>
-__global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restrict__ theta, int n_vch,
+__global__ void __launch_bounds__(GRAD_BS, GRAD_MIN_BLOCKS) k_grad(DevModel M, const float *__restrict__ theta, int n_vch,
                                              int per_series, const void *__restrict__ state_end,
                                              int se64, const float *__restrict__ adj_end,
                                              const float *__restrict__ pck, float *__restrict__ gpart,
@@ -1301,8 +1322,8 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
   TermC<F> tc[S::NT];
   F s2;
   load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tc, s2);
-  // shared memory: the warps' tables, then two staging buffers per thread
-  // for the backward walk, stg[(buf (SG + NDG) + group) bs + thread] (float4)
+  // shared memory: the warps' tables, then GRAD_STAGES staging buffers per
+  // thread for the backward walk, stg[(buf (SG + NDG) + group) bs + thread]
   float4 *tab_slots = reinterpret_cast<float4 *>(sm);
   const int bs = blockDim.x;
   float4 *stg = tab_slots + (bs / 32) * (S::NT * TAB_TERM / 4) + threadIdx.x;
@@ -1441,9 +1462,17 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
       int64_t li = lane_step(M, c, k2);
       float4 r_n = __ldg(M.ilv + li);
       uint8_t tag_n = __ldg(M.ilv_tag + li);
-      stage(0, k2 - k0, k2);
-      for (; k2 >= k0; --k2) {
-        const int slot = k2 - k0, buf = (k1 - 1 - k2) & 1;
+      // GRAD_STAGES - 1 steps are staged ahead (empty groups past the
+      // segment's start keep the group count uniform)
+#pragma unroll
+      for (int p = 0; p < GRAD_STAGES - 1; ++p) {
+        if (k2 - p >= k0)
+          stage(p, k2 - p - k0, k2 - p);
+        else
+          cp_async_commit();
+      }
+      for (int it = 0; k2 >= k0; --k2, ++it) {
+        const int buf = it % GRAD_STAGES;
         const F dt = r_n.x;
         const uint8_t tag = tag_n;
         const float4 q = make_float4(r_n.y, r_n.z, r_n.w, 0.f);
@@ -1451,10 +1480,14 @@ __global__ void __launch_bounds__(64, 6) k_grad(DevModel M, const float *__restr
           li -= 32;
           r_n = __ldg(M.ilv + li);
           tag_n = __ldg(M.ilv_tag + li);
-          stage(buf ^ 1, slot - 1, k2 - 1);
-          cp_async_wait<1>();
-        } else {
-          cp_async_wait<0>();
+        }
+        {
+          const int ka = k2 - (GRAD_STAGES - 1);
+          if (ka >= k0)
+            stage((it + GRAD_STAGES - 1) % GRAD_STAGES, ka - k0, ka);
+          else
+            cp_async_commit();
+          cp_async_wait<GRAD_STAGES - 1>();
         }
         const float4 *sb = stg + (size_t)buf * (SG + NDG) * bs;
         {
@@ -1972,7 +2005,7 @@ cudaError_t launch_grad(const DevModel &M, const float *theta, int n_vch, int pe
   if (ck < 2 || ck > 64 || (ck & 1)) return cudaErrorInvalidValue;
   const int SG = (S::D + S::NP + 3) / 4, NDG = DcW<S::NT>::G;
   const size_t smem = (size_t)(GRAD_BS / 32) * S::NT * TAB_TERM * sizeof(float) +
-                      (size_t)2 * (SG + NDG) * GRAD_BS * sizeof(float4);
+                      (size_t)GRAD_STAGES * (SG + NDG) * GRAD_BS * sizeof(float4);
   k_grad<S><<<(n_vch + GRAD_BS - 1) / GRAD_BS, GRAD_BS, smem, st>>>(
       M, theta, n_vch, per_series, state_end, se64, adj_end, pck, gpart, err, tabs, rbuf, dcache,
       ck, gdt, gwe, cond, pp);

@@ -23,7 +23,7 @@ void build_table(float a, float beta, float *tab) {
     for (int j = 0; j < 6; ++j) {
       r[j] = (float)g[j][k].v;
       r[8 + j] = (float)g[j][k].da;
-      r[16 + j] = (float)g[j][k].db;
+      r[14 + j] = (float)g[j][k].db;
     }
   }
 }
@@ -376,6 +376,33 @@ double hh_taylor_k_check(double a, double beta) {
       const double d[3] = {h[j].v - g[j][k].v, h[j].da - g[j][k].da, h[j].db - g[j][k].db};
       for (int q = 0; q < 3; ++q)
         if (mx[j][q] > 0.0) worst = std::fmax(worst, std::fabs(d[q]) / mx[j][q]);
+    }
+  }
+  return worst;
+}
+
+// The double-float table path the table kernel runs against the FP64 one:
+// the largest difference of a coefficient, relative to the largest
+// coefficient of the same series and component (values, d/da, d/dbeta).
+double hh_table_df_check(double a, double beta) {
+  EconMap E;
+  econ_map(E);
+  Dual2<double> g[6][TAB_NC];
+  table_coeffs<Dual2<double>>(E, mk(a, 1.0, 0.0), mk(beta, 0.0, 1.0), g);
+  static double v[6][TAB_NC], da[6][TAB_NC], db[6][TAB_NC];
+  table_coeffs_df(E, a, beta, v, da, db);
+  double worst = 0.0;
+  for (int j = 0; j < 6; ++j) {
+    double mx[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < TAB_NC; ++k) {
+      mx[0] = std::fmax(mx[0], std::fabs(g[j][k].v));
+      mx[1] = std::fmax(mx[1], std::fabs(g[j][k].da));
+      mx[2] = std::fmax(mx[2], std::fabs(g[j][k].db));
+    }
+    for (int k = 0; k < TAB_NC; ++k) {
+      const double d[3] = {v[j][k] - g[j][k].v, da[j][k] - g[j][k].da, db[j][k] - g[j][k].db};
+      for (int q = 0; q < 3; ++q)
+        if (mx[q] > 0.0) worst = std::fmax(worst, std::fabs(d[q]) / mx[q]);
     }
   }
   return worst;

@@ -42,6 +42,8 @@ def load():
     lib.hh_obs_dim.argtypes = [i32]
     lib.hh_prod_disc.argtypes = [i32, d, P(d), P(d), P(d)]
     lib.hh_observe.argtypes = [i32, i32, f, P(f), P(f), P(f), P(f), P(f), P(f)]
+    lib.hh_table_df_check.argtypes = [d, d]
+    lib.hh_table_df_check.restype = d
     lib.hh_span_nc.argtypes = [i32]
     lib.hh_span_element.argtypes = [i32, vp, vp, vp, vp, vp, i64, i64, i32, vp]
     lib.hh_span_fold.argtypes = [i32, vp, i32]

@@ -90,6 +90,18 @@ def test_step_scalar_derivatives(oracle_lib, hh, w0, q, path):
 
 
 @pytest.mark.parametrize("w0,q", CASES + OVERDAMPED + [(0.2, 0.55), (9.9, 10.0), (0.05, 30.0),
+                                                    (30.0, 0.5), (1.0, 0.02), (1e-3, 3.0),
+                                                    (300.0, 3.0)])
+def test_table_double_float_path_matches_fp64(hh, w0, q):
+    # the table kernel forms the coefficients in double-float arithmetic with
+    # the range's scale taken out; against the FP64 construction (same
+    # definitions) every coefficient agrees to 1e-12 of its series. size,
+    # far inside the FP32 rounding the table is stored with (6e-8)
+    a, beta = ab(w0, q)
+    assert hh.hh_table_df_check(a, beta) <= 1e-12
+
+
+@pytest.mark.parametrize("w0,q", CASES + OVERDAMPED + [(0.2, 0.55), (9.9, 10.0), (0.05, 30.0),
                                                     (30.0, 0.5), (1.0, 0.02)])
 def test_economised_tables_match_taylor(hh, w0, q):
     # the ten economised coefficients reproduce the 22-term Taylor series on

@@ -68,7 +68,7 @@ def test_noalloc_matches_loglik_two_calls(gp, kind):
 def _need_bytes(m, n_rows):
     d, nc = m.info["state_dim"], m.info["n_chunks"]
     need = ((2 * d * d + 3 * d) * 4 * nc + 255) // 256 * 256 + 24 * nc
-    return need + (960 * 2 * n_rows + 255) // 256 * 256
+    return need + (800 * 2 * n_rows + 255) // 256 * 256
 
 
 def test_noalloc_just_under_the_limit(gp):
