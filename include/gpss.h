@@ -37,9 +37,11 @@
  *    Non-finite or non-positive hyperparameters surface as GP_SS_ENUMERIC
  *    (gp_ss_last_error_series).
  *  - A measurement with t_end == t_start is instantaneous: it observes the
- *    latent f(t) itself (Section 2).  A model holds either instantaneous
- *    measurements only or exposure averages only (GP_SS_EUNSUPPORTED
- *    otherwise); instantaneous models have no integral states.
+ *    latent f(t) itself (Section 2), as one event.  A model of instantaneous
+ *    measurements only has no integral states; one that mixes them with
+ *    exposure averages keeps the exposures' integral states and orders
+ *    simultaneous events exposure ends, then instants, then starts.
+ *    (Product kernels: instantaneous measurements only.)
  */
 #ifndef GPSS_H
 #define GPSS_H

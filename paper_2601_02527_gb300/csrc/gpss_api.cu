@@ -225,6 +225,7 @@ struct gp_ss_model {
   int device = 0;
   int n_series = 0, n_terms = 0, kinds[4] = {0, 0, 0, 0}, layout = 0, n_slots = 1;
   bool product = false;  // a product term: plain log-likelihood filters only
+  bool mixed = false;    // instantaneous measurements among exposure averages
   int n_params = 0, precision = 32, schedule = 0;
   int64_t n_meas = 0, n_events = 0;
   OpTable ops{};
@@ -406,13 +407,23 @@ inline int meas_kind(double ts, double te, float y, float yerr) {
 // Events of series [a, b) at event offset e0: two per exposure (start, end),
 // one per instantaneous measurement (a measurement event observing the
 // latent; a model holds one kind only, checked by the caller).
+void build_series_mixed(int64_t a, int64_t b, int64_t e0, const double *ts, const double *te,
+                        const float *y, const float *yerr, const int32_t *inst, float *dt,
+                        uint8_t *tag, float4 *meas, double *dt64, double *meas64, int2 *mev,
+                        double *tev, SeriesOut *out);
+
 void build_series(int64_t a, int64_t b, int64_t e0, const double *ts, const double *te,
                   const float *y, const float *yerr, const int32_t *inst, float *dt, uint8_t *tag,
                   float4 *meas, double *dt64, double *meas64, int2 *mev, double *tev,
-                  SeriesOut *out) {
+                  SeriesOut *out, bool mixed = false) {
   const int64_t n = b - a;
   if (n == 0) {  // an empty series asks for no integral state
     out->n_slots = 0;
+    return;
+  }
+  if (mixed) {
+    build_series_mixed(a, b, e0, ts, te, y, yerr, inst, dt, tag, meas, dt64, meas64, mev, tev,
+                       out);
     return;
   }
   std::vector<int> slot(n);
@@ -533,6 +544,107 @@ void build_series(int64_t a, int64_t b, int64_t e0, const double *ts, const doub
       }
       ++mi;
     }
+  }
+}
+
+// A series of a model that mixes instantaneous measurements with exposure
+// averages: two events per exposure (reset at the start, read at the end,
+// slots as in build_series), one per instant (tagged TAG_INSTANT: it
+// observes the latent, Section 2).  Order: time, then exposure ends, then
+// instants, then starts (every read before a reset at the same time), then
+// measurement index.
+void build_series_mixed(int64_t a, int64_t b, int64_t e0, const double *ts, const double *te,
+                        const float *y, const float *yerr, const int32_t *inst, float *dt,
+                        uint8_t *tag, float4 *meas, double *dt64, double *meas64, int2 *mev,
+                        double *tev, SeriesOut *out) {
+  const int64_t n = b - a;
+  std::vector<int> slot(n, 0), kind(n);
+  for (int64_t i = 0; i < n; ++i) {
+    kind[i] = meas_kind(ts[a + i], te[a + i], y[a + i], yerr[a + i]);
+    if (kind[i] < 0) {
+      out->st = GP_SS_EINVAL;
+      return;
+    }
+  }
+  std::vector<int64_t> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t p, int64_t q) { return ts[a + p] < ts[a + q]; });
+  int n_slots = 0;
+  std::vector<double> last_end;
+  for (int64_t r = 0; r < n; ++r) {
+    const int64_t i = order[r];
+    if (kind[i] == 1) continue;  // instants take no slot
+    int s = 0;
+    if (inst) {
+      s = inst[a + i];
+      if (s < 0 || s >= 8) {
+        out->st = s < 0 ? GP_SS_EINVAL : GP_SS_EUNSUPPORTED;
+        return;
+      }
+      if ((int)last_end.size() <= s) last_end.resize(s + 1, -INFINITY);
+      if (last_end[s] > ts[a + i]) {
+        out->st = GP_SS_ESELFOVERLAP;
+        return;
+      }
+    } else {
+      while (s < (int)last_end.size() && last_end[s] > ts[a + i]) ++s;
+      if (s == (int)last_end.size()) last_end.push_back(0);
+    }
+    last_end[s] = te[a + i];
+    slot[i] = s;
+    n_slots = std::max(n_slots, s + 1);
+  }
+  out->n_slots = n_slots;
+  struct Ev {
+    double t;
+    int kind;  // 0 exposure end, 1 instant, 2 exposure start
+    int64_t i;
+  };
+  std::vector<Ev> ev;
+  ev.reserve(2 * n);
+  for (int64_t i = 0; i < n; ++i) {
+    if (kind[i] == 1) {
+      ev.push_back({ts[a + i], 1, i});
+    } else {
+      ev.push_back({ts[a + i], 2, i});
+      ev.push_back({te[a + i], 0, i});
+    }
+  }
+  std::sort(ev.begin(), ev.end(), [](const Ev &p, const Ev &q) {
+    if (p.t != q.t) return p.t < q.t;
+    if (p.kind != q.kind) return p.kind < q.kind;
+    return p.i < q.i;
+  });
+  int64_t mi = a;
+  double tprev = ev.empty() ? 0.0 : ev[0].t;
+  for (size_t k = 0; k < ev.size(); ++k) {
+    const double gap = ev[k].t - tprev;
+    tprev = ev[k].t;
+    dt[e0 + k] = (float)gap;
+    if (dt64) dt64[e0 + k] = gap;
+    tev[e0 + k] = ev[k].t;
+    const int64_t i = ev[k].i;
+    if (ev[k].kind == 2) {
+      tag[e0 + k] = (uint8_t)(slot[i] << 1);
+      mev[a + i].x = (int)k;
+      continue;
+    }
+    const bool instant = ev[k].kind == 1;
+    tag[e0 + k] = instant ? (uint8_t)(1 | gpss::TAG_INSTANT) : (uint8_t)(1 | (slot[i] << 1));
+    if (instant)
+      mev[a + i] = make_int2((int)k, (int)k);
+    else
+      mev[a + i].y = (int)k;
+    const double w = instant ? 1.0 : 1.0 / (te[a + i] - ts[a + i]);
+    const double r0 = (double)yerr[a + i] * (double)yerr[a + i];
+    meas[mi] = make_float4(y[a + i], (float)r0, (float)w, 0.0f);
+    if (meas64) {
+      meas64[3 * mi] = (double)y[a + i];
+      meas64[3 * mi + 1] = r0;
+      meas64[3 * mi + 2] = w;
+    }
+    ++mi;
   }
 }
 
@@ -684,6 +796,7 @@ gpss::DevModel dev_view(const gp_ss_model *m) {
   d.dcache_steps = m->dcache_steps;
   d.ilv = m->d_ilv;
   d.ilv_tag = m->d_ilv_tag;
+  d.mixed = m->mixed ? 1 : 0;
   return d;
 }
 
@@ -1096,9 +1209,9 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
   m->n_meas = N;
   m->ev_off.resize(n_series + 1);
   m->meas_off.resize(n_series + 1);
-  // events per series: two per exposure, one per instantaneous measurement;
-  // a model holds one kind (mixing them needs a shape with both observation
-  // forms, which is not compiled)
+  // events per series: two per exposure, one per instantaneous measurement.
+  // A model of instants only has no integral states; one that mixes instants
+  // with exposure averages marks its instants' events (TAG_INSTANT)
   int64_t n_inst = 0, n_bad = 0;
   for (int64_t i = 0; i < N; ++i) {
     const int kd = meas_kind(t_start[i], t_end[i], y[i], yerr[i]);
@@ -1109,17 +1222,22 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
     delete m;
     return GP_SS_EINVAL;
   }
-  if ((n_inst > 0 && n_inst < N) || (m->product && n_inst < N)) {
-    // mixed kinds, or a product kernel on exposure averages: not compiled
+  if (m->product && n_inst < N) {
+    // a product kernel on exposure averages: not compiled
     delete m;
     return GP_SS_EUNSUPPORTED;
   }
-  const int64_t per_meas = n_inst > 0 ? 1 : 2;
-  for (int s = 0; s <= n_series; ++s) {
+  m->mixed = n_inst > 0 && n_inst < N;
+  m->ev_off[0] = 0;
+  for (int s = 0; s < n_series; ++s) {
     m->meas_off[s] = series_offsets[s];
-    m->ev_off[s] = per_meas * series_offsets[s];
+    int64_t ne = 0;
+    for (int64_t i = series_offsets[s]; i < series_offsets[s + 1]; ++i)
+      ne += (t_end[i] == t_start[i]) ? 1 : 2;
+    m->ev_off[s + 1] = m->ev_off[s] + ne;
   }
-  m->n_events = per_meas * N;
+  m->meas_off[n_series] = series_offsets[n_series];
+  m->n_events = m->ev_off[n_series];
   // one record past the last measurement: the chunk kernels prefetch the
   // next measurement record before they know whether another one follows
   const size_t nE = std::max<int64_t>(m->n_events, 1), nM = (size_t)N + 1;
@@ -1165,11 +1283,11 @@ gp_ss_status gp_ss_build_model(const gp_ss_kernel_spec *spec, int n_series,
                        y, yerr, instrument, m->h_dt, m->h_tag, m->h_meas,
                        dt64.empty() ? nullptr : dt64.data(),
                        meas64.empty() ? nullptr : meas64.data(), mev.data(), m->tev.data(),
-                       &so[s]);
+                       &so[s], m->mixed);
       });
     for (auto &t : pool) t.join();
   }
-  int n_slots = n_inst > 0 ? 0 : 1;
+  int n_slots = (n_inst > 0 && !m->mixed) ? 0 : 1;
   for (int s = 0; s < n_series; ++s) {
     if (so[s].st != GP_SS_OK) {
       gp_ss_status st = so[s].st;
@@ -1617,8 +1735,8 @@ gp_ss_status gp_ss_build_events(int64_t n, const double *t_start, const double *
     if (kd < 0) return GP_SS_EINVAL;
     n_inst += kd;
   }
-  if (n_inst != 0 && n_inst != n) return GP_SS_EUNSUPPORTED;
-  const int64_t ne = n_inst ? n : 2 * n;
+  const bool mixed = n_inst != 0 && n_inst != n;
+  const int64_t ne = n_inst == n ? n : 2 * n - n_inst;
   std::vector<float> dt(ne);
   std::vector<uint8_t> tag(ne);
   std::vector<float4> meas(n + 1);
@@ -1626,8 +1744,9 @@ gp_ss_status gp_ss_build_events(int64_t n, const double *t_start, const double *
   std::vector<int2> mev(n);
   SeriesOut so;
   build_series(0, n, 0, t_start, t_end, y, yerr, instrument, dt.data(), tag.data(), meas.data(),
-               dt64.data(), meas64.data(), mev.data(), tev.data(), &so);
+               dt64.data(), meas64.data(), mev.data(), tev.data(), &so, mixed);
   if (so.st) return so.st;
+  if (mixed) so.n_slots = std::max(so.n_slots, 1);
   if (so.n_slots > kMaxSlots) return GP_SS_EUNSUPPORTED;
   *n_events = ne;
   *n_slots = so.n_slots;

@@ -1145,29 +1145,40 @@ GPSS_HD void reset_slot(int j, F *m, F *P) {
   }
 }
 
+// An instantaneous measurement (Section 2) observes the latent with h = H =
+// (1 0 1 0 ... 0): u = P h, hu = h.u, hm = h.m.
+template <class S, class F>
+GPSS_HD void obs_latent(const F *m, const F *P, F *u, F &hu, F &hm) {
+#pragma unroll
+  for (int i = 0; i < S::D; ++i) {
+    F acc = F(0);
+#pragma unroll
+    for (int t = 0; t < S::NT; ++t) acc += P[S::pk(i, 2 * t)];
+    u[i] = acc;
+  }
+  F a1 = F(0), a2 = F(0);
+#pragma unroll
+  for (int t = 0; t < S::NT; ++t) {
+    a1 += u[2 * t];
+    a2 += m[2 * t];
+  }
+  hu = a1;
+  hm = a2;
+}
+
+// Tag bit of an instantaneous measurement in a model whose shape has
+// integral states (exposure averages and instants in one model): the event
+// observes the latent instead of a slot's integral state.
+constexpr uint8_t TAG_INSTANT = 0x10;
+
 // Shared pieces of the measurement update with H~ = w * sum_{z in slot j} e_z
 // (Eq. H_aug; w = 1/delta):  u = P H~^T, S = H~ u + r, hm = H~ m.  Shapes
 // without integral states (NS = 0) observe the latent instead.
 template <class S, class F>
 GPSS_HD void obs_project(int j, F w, const F *m, const F *P, F *u, F &hu, F &hm) {
   if constexpr (S::NS == 0) {
-    // no integral states: an instantaneous measurement (Section 2), h = H =
-    // (1 0 1 0 ...) reads the latent f = sum_t x_t directly (w unused)
-#pragma unroll
-    for (int i = 0; i < S::D; ++i) {
-      F acc = F(0);
-#pragma unroll
-      for (int t = 0; t < S::NT; ++t) acc += P[S::pk(i, 2 * t)];
-      u[i] = acc;
-    }
-    F a1 = F(0), a2 = F(0);
-#pragma unroll
-    for (int t = 0; t < S::NT; ++t) {
-      a1 += u[2 * t];
-      a2 += m[2 * t];
-    }
-    hu = a1;
-    hm = a2;
+    // no integral states: every measurement is instantaneous (w unused)
+    obs_latent<S>(m, P, u, hu, hm);
     return;
   }
 #pragma unroll
@@ -1186,6 +1197,20 @@ GPSS_HD void obs_project(int j, F w, const F *m, const F *P, F *u, F &hu, F &hm)
   }
   hu = a1 * w;
   hm = a2 * w;
+}
+
+// The update's projections for a measurement event given its tag: with MIX
+// (a model mixing instants with exposure averages), an event tagged
+// TAG_INSTANT observes the latent; otherwise slot (tag >> 1) & 7.
+template <class S, class F, bool MIX>
+GPSS_HD void obs_project_tag(uint8_t tag, F w, const F *m, const F *P, F *u, F &hu, F &hm) {
+  if constexpr (MIX && S::NS > 0) {
+    if (tag & TAG_INSTANT) {
+      obs_latent<S>(m, P, u, hu, hm);
+      return;
+    }
+  }
+  obs_project<S>((tag >> 1) & 7, w, m, P, u, hu, hm);
 }
 
 // Load per-term constants and s^2 from a row of natural parameters.

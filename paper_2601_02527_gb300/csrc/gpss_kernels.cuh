@@ -70,6 +70,9 @@ struct DevModel {
   // one 512-byte and one 32-byte contiguous access.
   const float4 *ilv;
   const uint8_t *ilv_tag;
+  // nonzero: instantaneous measurements (TAG_INSTANT) among exposure averages;
+  // every row then runs the kernels' general bodies, which read that bit
+  int mixed;
 };
 
 // Lane-step index of step k of chunk c.
@@ -170,7 +173,7 @@ GPSS_D Disc<F> disc_step(F dt, const TermC<F> &c, const float4 *tab) {
 // One event of the sequential filter on (m, P) given its gap, tag and (for an
 // exposure end) its measurement record; returns true for an end event, with
 // S and v of its innovation.
-template <class S, class F>
+template <class S, class F, bool MIX = false>
 GPSS_D bool filter_blocks(const Blocks<F> *B, uint8_t tag, F y, F r0, F w, F s2, F *m, F *P,
                           F &Sv, F &v);
 
@@ -181,11 +184,12 @@ GPSS_D bool filter_step(F dt, uint8_t tag, F y, F r0, F w, const TermC<F> *tc, F
 #pragma unroll
   for (int t = 0; t < S::NT; ++t)
     B[t] = make_blocks(disc_step<F, OD>(dt, tc[t], tab ? tab + t * (TAB_TERM / 4) : nullptr), tc[t]);
-  return filter_blocks<S, F>(B, tag, y, r0, w, s2, m, P, Sv, v);
+  return filter_blocks<S, F, OD>(B, tag, y, r0, w, s2, m, P, Sv, v);
 }
 
-// The filter step given the step's blocks.
-template <class S, class F>
+// The filter step given the step's blocks.  MIX: the tag may mark an
+// instantaneous measurement among exposure averages.
+template <class S, class F, bool MIX>
 GPSS_D bool filter_blocks(const Blocks<F> *B, uint8_t tag, F y, F r0, F w, F s2, F *m, F *P,
                           F &Sv, F &v) {
   F mt[S::D];
@@ -199,7 +203,7 @@ GPSS_D bool filter_blocks(const Blocks<F> *B, uint8_t tag, F y, F r0, F w, F s2,
     return false;
   }
   F u[S::D], hu, hm;
-  obs_project<S>(j, w, m, P, u, hu, hm);
+  obs_project_tag<S, F, MIX>(tag, w, m, P, u, hu, hm);
   Sv = hu + r0 + s2;
   v = y - hm;
   const F iS = F(1) / Sv;
@@ -422,7 +426,7 @@ __global__ void __launch_bounds__(128) k_plain(DevModel M, const float *__restri
     ll_out[v] = ll;
     if (bad) flag_error(err, v, 7);
   };
-  if (any_overdamped<S::NT>(tc))
+  if (any_overdamped<S::NT>(tc) || M.mixed)
     body(OdTag<true>{});
   else
     body(OdTag<false>{});
@@ -471,7 +475,7 @@ constexpr int ELEM_MIN_BLOCKS = GPSS_ELEM_MIN_BLOCKS;
 // Predict with the step's blocks (A <- Phi~ A, b <- Phi~ b, C <- Phi~ C
 // Phi~^T + Q~), then reset the slot at an exposure start or update with the
 // measurement (y, r0, w) at an end.
-template <class S, class F>
+template <class S, class F, bool MIX = false>
 GPSS_HD void elem_event(const Blocks<F> *B, uint8_t tag, F y, F r0, F w, F s2,
                         F (&A)[S::D][S::D], F *b, F *C, F *eta, F *J, double &gam, double &ld,
                         int &n_end, bool &bad) {
@@ -504,22 +508,21 @@ GPSS_HD void elem_event(const Blocks<F> *B, uint8_t tag, F y, F r0, F w, F s2,
     return;
   }
   F u[D], hu, hb;
-  obs_project<S>(j, w, b, C, u, hu, hb);
+  obs_project_tag<S, F, MIX>(tag, w, b, C, u, hu, hb);
   const F Sv = hu + r0 + s2;
   const F cc = y - hb;
+  // an instantaneous measurement reads the latent (always in shapes without
+  // integral states; by its tag in a mixed model)
+  const bool inst = S::NS == 0 || (MIX && (tag & TAG_INSTANT));
   F g[D];  // h^T A
 #pragma unroll
   for (int col = 0; col < D; ++col) {
-    F acc = F(0);
-    if constexpr (S::NS == 0) {
+    F acc = F(0), lat = F(0);
 #pragma unroll
-      for (int t = 0; t < S::NT; ++t) acc += A[2 * t][col];
-      g[col] = acc;
-    } else {
+    for (int t = 0; t < S::NT; ++t) lat += A[2 * t][col];
 #pragma unroll
-      for (int zi = 2 * S::NT; zi < D; ++zi) acc += (S::zslot(zi) == j) ? A[zi][col] : F(0);
-      g[col] = acc * w;
-    }
+    for (int zi = 2 * S::NT; zi < D; ++zi) acc += (S::zslot(zi) == j) ? A[zi][col] : F(0);
+    g[col] = inst ? lat : acc * w;
   }
   bad |= !(Sv > F(0));
   const F iS = F(1) / Sv;
@@ -575,9 +578,10 @@ __global__ void __launch_bounds__(128, ELEM_MIN_BLOCKS) k_elem(DevModel M, const
   TermC<F> tc[S::NT];
   F s2;
   load_terms<S::NT, F>(theta + (size_t)row * M.n_params, M.kinds, tc, s2);
-  // rows with an overdamped term run in the OD = true launch, the others in
-  // the OD = false one (whole warps: a warp's chunks share one row)
-  if (any_overdamped<S::NT>(tc) != OD) return;
+  // rows with an overdamped term (and every row of a mixed model) run in the
+  // OD = true launch, the others in the OD = false one (whole warps: a warp's
+  // chunks share one row)
+  if ((any_overdamped<S::NT>(tc) || M.mixed) != OD) return;
   const float4 *tab =
       stage_table<S::NT>(tabs, row, smem_tab + (threadIdx.x >> 5) * (S::NT * TAB_TERM / 4));
   const bool first = M.ch_flags[c] & 1;
@@ -644,7 +648,7 @@ __global__ void __launch_bounds__(128, ELEM_MIN_BLOCKS) k_elem(DevModel M, const
           r[32 * v] = make_float4(x[4 * v], x[4 * v + 1], x[4 * v + 2], x[4 * v + 3]);
       }
     }
-    elem_event<S, F>(B, tag, q.x, q.y, q.z, s2, A, b, C, eta, J, gam, ld, n_end, bad);
+    elem_event<S, F, OD>(B, tag, q.x, q.y, q.z, s2, A, b, C, eta, J, gam, ld, n_end, bad);
   }
   store_elem<S>(ef, n_vch, vc, A, b, C, eta, J);
   ed[vc] = gam;
@@ -987,10 +991,10 @@ GPSS_D float2 predict_point(float d1, float d2, const TermC<float> *tc, const fl
 // so with h = w e_j and u = P h:  mean = h.m + u.lam,
 // var = h.u + u^T (2 Lam) u - (u.lam)^2.
 template <class S>
-GPSS_HD float2 conditioned(int j, float w, const float *m, const float *P, const float *lam,
-                           const float *Lam) {
+GPSS_HD float2 conditioned_latent(const float *m, const float *P, const float *lam,
+                                  const float *Lam) {
   constexpr int D = S::D;
-  if constexpr (S::NS == 0) {
+  {
     // instantaneous measurement: h selects the latent components
     float u[D], hm = 0.f;
 #pragma unroll
@@ -1016,6 +1020,13 @@ GPSS_HD float2 conditioned(int j, float w, const float *m, const float *P, const
     }
     return make_float2(hm + ul, hu + 2.f * uLu - ul * ul);
   }
+}
+
+template <class S>
+GPSS_HD float2 conditioned(int j, float w, const float *m, const float *P, const float *lam,
+                           const float *Lam) {
+  constexpr int D = S::D;
+  if constexpr (S::NS == 0) return conditioned_latent<S>(m, P, lam, Lam);
   float u[D], hm = 0.f;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -1037,6 +1048,17 @@ GPSS_HD float2 conditioned(int j, float w, const float *m, const float *P, const
     uLu += u[i] * acc;
   }
   return make_float2(w * hm + ul, w * hu + 2.f * uLu - ul * ul);
+}
+
+// The same for a measurement event given its tag (MIX: instants among
+// exposure averages, marked TAG_INSTANT).
+template <class S, bool MIX>
+GPSS_HD float2 conditioned_tag(uint8_t tag, float w, const float *m, const float *P,
+                               const float *lam, const float *Lam) {
+  if constexpr (MIX && S::NS > 0) {
+    if (tag & TAG_INSTANT) return conditioned_latent<S>(m, P, lam, Lam);
+  }
+  return conditioned<S>((tag >> 1) & 7, w, m, P, lam, Lam);
 }
 
 // Reverse of one event.  (m, P): filtered state before the event; dv: the
@@ -1072,8 +1094,11 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
   predict_cov<S>(B, Pp, G);
   if (tag & 1) {
     const F y = q.x, r0 = q.y, w = q.z;
+    // an instantaneous measurement reads the latent (always in shapes without
+    // integral states; by its tag in a mixed model, whose rows run OD bodies)
+    const bool inst = S::NS == 0 || (OD && (tag & TAG_INSTANT));
     F u[D], hu, hm;
-    obs_project<S>(j, w, mp, Pp, u, hu, hm);
+    obs_project_tag<S, F, OD>(tag, w, mp, Pp, u, hu, hm);
     const F Sv = hu + r0 + s2;
     const F v = y - hm;
     const F iS = F(1) / Sv;
@@ -1096,12 +1121,11 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
     F h[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      if constexpr (S::NS == 0)
-        h[i] = (i % 2 == 0) ? F(1) : F(0);  // instantaneous: the latent
-      else
-        h[i] = (i >= 2 * S::NT && S::zslot(i) == j) ? w : F(0);
+      const F hl = (i < 2 * S::NT && i % 2 == 0) ? F(1) : F(0);  // the latent
+      const F hz = (i >= 2 * S::NT && S::zslot(i) == j) ? w : F(0);
+      h[i] = inst ? hl : hz;
     }
-    if (S::NS > 0 && want_exp) {
+    if (S::NS > 0 && want_exp && !inst) {
       // h = w e (e selects the slot's integral states): d/dh = Pp ub + 2 Sb u - vb mp
       F gw = F(0);
 #pragma unroll
@@ -1416,7 +1440,7 @@ __global__ void __launch_bounds__(GRAD_BS, GRAD_MIN_BLOCKS) k_grad(DevModel M, c
           for (int t = 0; t < S::NT; ++t)
             B[t] = make_blocks(discretize_tab<OD>(dt, tc[t], tab + t * (TAB_TERM / 4)), tc[t]);
         }
-        if (filter_blocks<S, F>(B, tag, q.x, q.y, q.z, s2, m, P, Sv, vv)) bad |= !(Sv > F(0));
+        if (filter_blocks<S, F, OD>(B, tag, q.x, q.y, q.z, s2, m, P, Sv, vv)) bad |= !(Sv > F(0));
       }
       // conditioned mean and variance of the chunk's last event, if it ends an
       // exposure: the chunk's end state and its boundary adjoint
@@ -1426,7 +1450,7 @@ __global__ void __launch_bounds__(GRAD_BS, GRAD_MIN_BLOCKS) k_grad(DevModel M, c
         const float4 rl = __ldg(M.ilv + il);
         F mb[D], Pb[S::NP];
         load_state_f<S>(state_end, se64, n_vch, vc, mb, Pb);
-        cond[eo + k1 - 1] = conditioned<S>((tl >> 1) & 7, rl.w, mb, Pb, lam, Lam);
+        cond[eo + k1 - 1] = conditioned_tag<S, OD>(tl, rl.w, mb, Pb, lam, Lam);
       }
       // test times after the series' last event: predicted from its filtered
       // state (which all the data already conditions)
@@ -1548,7 +1572,7 @@ __global__ void __launch_bounds__(GRAD_BS, GRAD_MIN_BLOCKS) k_grad(DevModel M, c
           const uint8_t tp = k2 > k0 ? tag_n : __ldg(M.ilv_tag + lp);
           if (tp & 1) {
             const float wp = k2 > k0 ? r_n.w : __ldg(M.ilv + lp).w;
-            cond[eo + k2 - 1] = conditioned<S>((tp >> 1) & 7, wp, m, P, lam, Lam);
+            cond[eo + k2 - 1] = conditioned_tag<S, OD>(tp, wp, m, P, lam, Lam);
           }
         }
       }
@@ -1595,9 +1619,9 @@ __global__ void __launch_bounds__(GRAD_BS, GRAD_MIN_BLOCKS) k_grad(DevModel M, c
     g[p * gs] = gr.s2 * F(2) * th[p];
     if (bad) flag_error(err, orow, 7);
   };
-  // rows with an overdamped term take the general body (rare); the others
-  // the lean one unless extra outputs are requested
-  if (any_overdamped<S::NT>(tc))
+  // rows with an overdamped term, and every row of a mixed model, take the
+  // general body; the others the lean one unless extra outputs are requested
+  if (any_overdamped<S::NT>(tc) || M.mixed)
     body(OdTag<true>{}, OdTag<true>{});
   else if (cond || pp.off || gdt)
     body(OdTag<false>{}, OdTag<true>{});

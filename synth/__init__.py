@@ -387,6 +387,24 @@ def c5(seed=1005, n=1_000_000, n_sets=256):
                    with_instrument=True)
 
 
+def mixed(seed, n_series, n, terms, theta_row, layout=0, frac_instant=0.5):
+    """Series mixing exposure averages with instantaneous measurements (t_end
+    == t_start): ``n`` exposures of the c1 recipe per series and about
+    ``frac_instant * n`` instants drawn uniformly over the series' span, three
+    of them placed on an exposure's start or end (simultaneous events)."""
+    rng = np.random.default_rng(seed)
+    series = []
+    for _ in range(n_series):
+        ts, te = single_instrument_exposures(rng, n, 1.0, 0.05, 0.5)
+        ti = np.sort(rng.uniform(ts[0] - 1.0, te[-1] + 1.0, max(3, int(frac_instant * n))))
+        ti[:3] = [ts[min(5, n - 1)], te[min(7, n - 1)], ts[min(9, n - 1)]]
+        a = np.concatenate([ts, ti])
+        b = np.concatenate([te, ti])
+        series.append((a, b))
+    theta = np.array([theta_row] * n_series, dtype=np.float64)
+    return _finish("mixed", list(terms), layout, series, theta, True, rng)
+
+
 def small_single(seed, n, terms, theta_row, gap_mean=1.0, dmin=0.05, dmax=0.5, s_white=0.1):
     """A one-series workload of the c1 exposure recipe with a given kernel."""
     rng = np.random.default_rng(seed)

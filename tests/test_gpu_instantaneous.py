@@ -134,7 +134,7 @@ def test_condition_and_predict(gp):
             assert not bad.any(), (s, gv[bad][:5], va[bad][:5])
 
 
-def test_single_term_and_mixing_rejected(gp):
+def test_single_term(gp):
     rng = np.random.default_rng(92)
     t = np.cumsum(rng.exponential(0.5, 700))
     th = np.array([[1.0, 2 * math.pi / 10, 3.0, 0.1]])
@@ -145,10 +145,6 @@ def test_single_term_and_mixing_rejected(gp):
     ref_ll, ref_g = oracle.loglik_workload(wl, grad=True)
     _check_ll(ll.cpu().numpy(), ref_ll, [len(t)])
     _check_rows(g.cpu().numpy(), ref_g)
-    te = t.copy()
-    te[::2] += 0.1  # half of them exposures: not compiled
-    with pytest.raises(Exception):
-        gp.Model(wl.terms, wl.offsets, t, te, wl.y, wl.yerr, None, layout=0)
 
 
 def test_edge_cases(gp):
