@@ -36,12 +36,12 @@ UNIT = "measurements/s"
 # replay included), from ncu's FP32 instruction counters of one k_grad launch
 # on 512 series of the c4 recipe (chunk length 256, segments of 64), captured
 # with --clock-control none.
-ALG_FLOPS_PER_EVENT = {"c4": 1560.0}
+ALG_FLOPS_PER_EVENT = {"c4": 1578.8}
 # DRAM bytes (read + write) per event of that k_grad launch, same capture;
 # the traffic grows with the events (replay records, cached step scalars,
 # partial elements, event stream), so a full launch is this x its events.
 # Valid for the captured configuration only (chunk length 256, segments of 64).
-TRAFFIC_PER_EVENT = {"c4": (347.1, 256, 64)}
+TRAFFIC_PER_EVENT = {"c4": (346.9, 256, 64)}
 FP32_LANES_PER_SM = 128
 
 # Per workload: whether a step includes the gradient, and whether the
@@ -143,10 +143,27 @@ class ClockSampler:
                 stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        # nvidia-smi takes a while to start: wait (bounded) for its first sample
+        # so that a short timed region still has samples around it
+        self._wait_lines(1, 10.0)
+
+    def _n_lines(self):
+        try:
+            with open(self.path) as f:
+                return sum(1 for _ in f)
+        except Exception:
+            return 0
+
+    def _wait_lines(self, n, limit_s):
+        t_end = time.time() + limit_s
+        while self.proc is not None and self._n_lines() < n and time.time() < t_end:
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
             return None
+        # one more sample after the timed window closed (bounded wait)
+        self._wait_lines(self._n_lines() + 2, 3.0)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)

@@ -467,6 +467,11 @@ GPSS_HD void sinc_pair_k(float t, float b, float rb, float &S, float &C) {
 // worst case is critical damping.  The map is linear with T held fixed, so
 // the tangent series are economised like the values.
 //
+// Unrolling of the Horner loops over the table's records (sm_103a: three)
+#ifndef GPSS_HORNER_UNROLL
+#define GPSS_HORNER_UNROLL _Pragma("unroll 3")
+#endif
+
 // Table layout per (row, term): for k = 0..NC-1 one record of TAB_W floats:
 // [6 values, 2 pad, 6 d/da, 6 d/dbeta] (five float4: the values are read as
 // two, the twelve tangents as three).
@@ -740,7 +745,7 @@ GPSS_HD Disc<float> disc_tab(float t, const float4 *__restrict__ tab) {
     const float4 q0 = tab[(TAB_NC - 1) * (TAB_W / 4)], q1 = tab[(TAB_NC - 1) * (TAB_W / 4) + 1];
     acc[0] = q0.x; acc[1] = q0.y; acc[2] = q0.z; acc[3] = q0.w; acc[4] = q1.x; acc[5] = q1.y;
   }
-#pragma unroll 3
+GPSS_HORNER_UNROLL
   for (int k = TAB_NC - 2; k >= 0; --k) {
     const float4 q0 = tab[k * (TAB_W / 4)], q1 = tab[k * (TAB_W / 4) + 1];
     acc[0] = fmaf(acc[0], t, q0.x);
@@ -770,7 +775,7 @@ GPSS_HD Disc<Dual2<float>> disc_tab_dual(float t, const float4 *__restrict__ tab
     da[0] = q2.x; da[1] = q2.y; da[2] = q2.z; da[3] = q2.w; da[4] = q3.x; da[5] = q3.y;
     db[0] = q3.z; db[1] = q3.w; db[2] = q4.x; db[3] = q4.y; db[4] = q4.z; db[5] = q4.w;
   }
-#pragma unroll 3
+GPSS_HORNER_UNROLL
   for (int k = TAB_NC - 2; k >= 0; --k) {
     const float4 *r = tab + k * (TAB_W / 4);
     const float4 q0 = r[0], q1 = r[1], q2 = r[2], q3 = r[3], q4 = r[4];
@@ -926,7 +931,7 @@ GPSS_HD void disc_tab_tangents(float t, const float4 *__restrict__ tab, float (&
     da[0] = q2.x; da[1] = q2.y; da[2] = q2.z; da[3] = q2.w; da[4] = q3.x; da[5] = q3.y;
     db[0] = q3.z; db[1] = q3.w; db[2] = q4.x; db[3] = q4.y; db[4] = q4.z; db[5] = q4.w;
   }
-#pragma unroll 3
+GPSS_HORNER_UNROLL
   for (int k = TAB_NC - 2; k >= 0; --k) {
     const float4 *r = tab + k * (TAB_W / 4);
     const float4 q2 = r[2], q3 = r[3], q4 = r[4];
@@ -1103,32 +1108,63 @@ GPSS_HD void add_q(const Blocks<F> *B, F *P) {
     }
 }
 
-// P <- Phi~ P Phi~^T + Q~ on packed storage; G (optional) receives Phi~ P.
+// P <- Phi~ P Phi~^T + Q~ on packed storage, in place, one term at a time.
+// Phi~ is the product of commuting factors Phi_t, each the identity except
+// on term t's pair a = (2t, 2t+1), which it maps by its 2x2 block, and on the
+// integral states z of that term, which gain pb0 x_a0 + pb1 x_a1.  The
+// congruence P <- Phi_t P Phi_t^T changes only the rows and columns of a and
+// of the z: with W = P Phi_t^T (columns j in a and z),
+//   W[k][a_r] = A[r][0] P[k][a0] + A[r][1] P[k][a1],
+//   W[k][z]   = P[k][z] + pb0 P[k][a0] + pb1 P[k][a1],
+// the new entries are W[k][j] for k outside a and z, and, for i, j in a and
+// z, Phi_t[i,:] W[:, j] (a row of Phi_t has two or three nonzeros).
 template <class S, class F>
-GPSS_HD void predict_cov(const Blocks<F> *B, F *P, F (*G)[S::D] = nullptr) {
+GPSS_HD void predict_cov(const Blocks<F> *B, F *P) {
   constexpr int D = S::D;
-  F T1[D][D];
 #pragma unroll
-  for (int j = 0; j < D; ++j) {
-    F col[D], o[D];
+  for (int t = 0; t < S::NT; ++t) {
+    const int a0 = 2 * t, a1 = 2 * t + 1;
+    const F p00 = B[t].p00, p01 = B[t].p01, p10 = B[t].p10, p11 = B[t].p11;
+    const F pb0 = B[t].pb0, pb1 = B[t].pb1;
+    // W = P Phi_t^T at the changed columns, every row
+    F W[D][D];  // only columns a0, a1 and term t's z are formed
 #pragma unroll
-    for (int i = 0; i < D; ++i) col[i] = P[S::pk(i, j)];
-    apply_phi<S>(B, col, o);
+    for (int k = 0; k < D; ++k) {
+      const F x0 = P[S::pk(k, a0)], x1 = P[S::pk(k, a1)];
+      W[k][a0] = p00 * x0 + p01 * x1;
+      W[k][a1] = p10 * x0 + p11 * x1;
 #pragma unroll
-    for (int i = 0; i < D; ++i) T1[i][j] = o[i];
-  }
-  if (G) {
+      for (int z = 2 * S::NT; z < D; ++z)
+        if (S::zint(z, t)) W[k][z] = P[S::pk(k, z)] + pb0 * x0 + pb1 * x1;
+    }
+    // rows outside the changed set keep W; the changed block is Phi_t W
 #pragma unroll
-    for (int i = 0; i < D; ++i)
+    for (int k = 0; k < D; ++k) {
+      const bool kc = (k == a0 || k == a1 || (k >= 2 * S::NT && S::zint(k, t)));
+      if (kc) continue;
+      P[S::pk(k, a0)] = W[k][a0];
+      P[S::pk(k, a1)] = W[k][a1];
 #pragma unroll
-      for (int j = 0; j < D; ++j) G[i][j] = T1[i][j];
-  }
+      for (int z = 2 * S::NT; z < D; ++z)
+        if (S::zint(z, t)) P[S::pk(k, z)] = W[k][z];
+    }
+    auto row = [&](int i, int j) -> F {  // (Phi_t W)[i][j], i and j changed
+      if (i == a0) return p00 * W[a0][j] + p01 * W[a1][j];
+      if (i == a1) return p10 * W[a0][j] + p11 * W[a1][j];
+      return W[i][j] + pb0 * W[a0][j] + pb1 * W[a1][j];
+    };
+    P[S::pk(a0, a0)] = row(a0, a0);
+    P[S::pk(a0, a1)] = row(a0, a1);
+    P[S::pk(a1, a1)] = row(a1, a1);
 #pragma unroll
-  for (int i = 0; i < D; ++i) {
-    F o[D];
-    apply_phi<S>(B, T1[i], o);
+    for (int z = 2 * S::NT; z < D; ++z) {
+      if (!S::zint(z, t)) continue;
+      P[S::pk(a0, z)] = row(a0, z);
+      P[S::pk(a1, z)] = row(a1, z);
 #pragma unroll
-    for (int j = i; j < D; ++j) P[S::pk(i, j)] = o[j];
+      for (int z2 = 2 * S::NT; z2 <= z; ++z2)
+        if (S::zint(z2, t)) P[S::pk(z2, z)] = row(z2, z);
+    }
   }
   add_q<S>(B, P);
 }

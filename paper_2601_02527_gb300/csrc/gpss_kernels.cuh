@@ -1073,9 +1073,24 @@ struct NoHook {
   GPSS_D void operator()(const float *, const float *) const {}
 };
 
-template <class S, bool OD = true, class Hook = NoHook>
+// Value i of a staged replay record (m first, then packed P) in shared
+// memory: float4 group g of this thread's slot at sb[g bs].
+struct StagedRec {
+  const float4 *sb;
+  int bs, off;
+  GPSS_D float operator[](int i) const {
+    const int k = i + off;
+    return reinterpret_cast<const float *>(sb + (size_t)(k >> 2) * bs)[k & 3];
+  }
+};
+
+//
+// m and P are read through operator[] (register arrays, or the staged replay
+// record in shared memory, which the walk then reads where it needs them
+// instead of holding them in registers across the event).
+template <class S, bool OD = true, class Hook = NoHook, class V = const float *>
 GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *tc, float s2,
-                          const float *m, const float *P, float *lam, float *Lam,
+                          const V &m, const V &P, float *lam, float *Lam,
                           TermGrad<S::NT> &gr, const float4 *tab, const Disc<float> *dv,
                           bool want_exp, float &g_dt, float &g_w, const Hook &hook = Hook()) {
   using F = float;
@@ -1087,11 +1102,16 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
 #pragma unroll
   for (int t = 0; t < S::NT; ++t) B[t] = make_blocks(dv[t], tc[t]);
   // recompute the prediction
-  F mp[D], Pp[S::NP], G[D][D];
-  apply_phi<S>(B, m, mp);
+  F mp[D], Pp[S::NP];
+  {
+    F mv[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) mv[i] = m[i];
+    apply_phi<S>(B, mv, mp);
+  }
 #pragma unroll
   for (int i = 0; i < S::NP; ++i) Pp[i] = P[i];
-  predict_cov<S>(B, Pp, G);
+  predict_cov<S>(B, Pp);
   if (tag & 1) {
     const F y = q.x, r0 = q.y, w = q.z;
     // an instantaneous measurement reads the latent (always in shapes without
@@ -1150,16 +1170,27 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
     reset_slot<S>(j, lam, Lam);
   }
   hook(lam, Lam);
-  // reverse of the prediction: (lam, Lam) are now adjoints of (m-, P-)
-  // d/dPhi~ = lam m^T + 2 Lam G, G = Phi~ P; d/dQ~ = Lam.
-  F zl = F(0);
-  F zL[D];
+  // reverse of the prediction: (lam, Lam) are now adjoints of (m-, P-).
+  // d/dPhi~ = lam m^T + 2 Lam Phi~ P and d/dQ~ = Lam.  With T2 = Lam Phi~ the
+  // middle term is T2 P and the adjoint of P is Phi~^T T2, so Phi~ P need not
+  // be kept from the prediction; P is read again here.
+  F T2[D][D];  // row i = (Phi~^T Lam[i,:])^T
 #pragma unroll
-  for (int kk = 0; kk < D; ++kk) zL[kk] = F(0);
+  for (int i = 0; i < D; ++i) {
+    F row[D], o[D];
+#pragma unroll
+    for (int kk = 0; kk < D; ++kk) row[kk] = Lam[S::pk(i, kk)];
+    apply_phi_t<S>(B, row, o);
+#pragma unroll
+    for (int kk = 0; kk < D; ++kk) T2[i][kk] = o[kk];
+  }
+  // adjoints of the six step scalars per term, (f, f', F1, I_ff, I_pp, I_FF)
+  F bX[S::NT][6];
 #pragma unroll
   for (int t = 0; t < S::NT; ++t) {
     const int i0 = 2 * t, i1 = 2 * t + 1;
-    // structured adjoints of Phi_t
+    // structured adjoints of Phi_t: LG = (lam m^T + 2 T2 P) at rows and
+    // columns (i0, i1)
     F LG[2][2];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
@@ -1167,37 +1198,34 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
       for (int cc = 0; cc < 2; ++cc) {
         F acc = F(0);
 #pragma unroll
-        for (int kk = 0; kk < D; ++kk) acc += Lam[S::pk(i0 + r, kk)] * G[kk][i0 + cc];
+        for (int kk = 0; kk < D; ++kk) acc += T2[i0 + r][kk] * P[S::pk(kk, i0 + cc)];
         LG[r][cc] = lam[i0 + r] * m[i0 + cc] + F(2) * acc;
       }
-    // z rows integrating this term
-    F zlam = F(0), zrow[D];
-#pragma unroll
-    for (int kk = 0; kk < D; ++kk) zrow[kk] = F(0);
+    // z rows integrating this term: their summed rows of lam m^T + 2 T2 P at
+    // columns (i0, i1), and the Q blocks' adjoints
+    F pb0 = F(0), pb1 = F(0);
     F q_z0 = F(0), q_z1 = F(0), q_zz = F(0);
 #pragma unroll
     for (int zi = 2 * S::NT; zi < D; ++zi) {
       if (!S::zint(zi, t)) continue;
-      zlam += lam[zi];
+      F a0 = F(0), a1 = F(0);
 #pragma unroll
-      for (int kk = 0; kk < D; ++kk) zrow[kk] += Lam[S::pk(zi, kk)];
+      for (int kk = 0; kk < D; ++kk) {
+        a0 += T2[zi][kk] * P[S::pk(kk, i0)];
+        a1 += T2[zi][kk] * P[S::pk(kk, i1)];
+      }
+      pb0 += lam[zi] * m[i0] + F(2) * a0;
+      pb1 += lam[zi] * m[i1] + F(2) * a1;
       q_z0 += F(2) * Lam[S::pk(i0, zi)];
       q_z1 += F(2) * Lam[S::pk(i1, zi)];
 #pragma unroll
       for (int zj = 2 * S::NT; zj < D; ++zj)
         if (S::zint(zj, t)) q_zz += Lam[S::pk(zi, zj)];
     }
-    F pb0 = zlam * m[i0], pb1 = zlam * m[i1];
-#pragma unroll
-    for (int kk = 0; kk < D; ++kk) {
-      pb0 += F(2) * zrow[kk] * G[kk][i0];
-      pb1 += F(2) * zrow[kk] * G[kk][i1];
-    }
     const F q00 = Lam[S::pk(i0, i0)], q01 = F(2) * Lam[S::pk(i0, i1)], q11 = Lam[S::pk(i1, i1)];
     // blocks -> (f, f', F1, I_ff, I_pp, I_FF) adjoints and explicit (a, w2, Qc)
     const TermC<F> &c = tc[t];
-    const F f = dv[t].f, fp = dv[t].fp, F1 = dv[t].F1, Iff = dv[t].Iff, Ipp = dv[t].Ipp,
-            IFF = dv[t].IFF;
+    const F f = dv[t].f, F1 = dv[t].F1, Iff = dv[t].Iff, Ipp = dv[t].Ipp, IFF = dv[t].IFF;
     F bf = F(0), bfp = F(0), bF1 = F(0), bIff = F(0), bIpp = F(0), bIFF = F(0);
     // p00 = fp + 2a f ; p01 = f ; p10 = -w2 f ; p11 = fp
     bfp += LG[0][0] + LG[1][1];
@@ -1216,35 +1244,19 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
     bIFF += c.qc * q_zz;
     gr.qc[t] += Iff * q00 + F(0.5) * f * f * q01 + Ipp * q11 + F(0.5) * F1 * F1 * q_z0 +
                 (f * F1 - Iff) * q_z1 + IFF * q_zz;
-    // through the discretisation: (a, beta) tangents of the six scalars
-    F da[6], db[6];
-    disc_tangents<OD>(dt, c, tab + t * (TAB_TERM / 4), dv[t], da, db);
-    gr.a[t] += bf * da[0] + bfp * da[1] + bF1 * da[2] + bIff * da[3] + bIpp * da[4] + bIFF * da[5];
-    gr.beta[t] += bf * db[0] + bfp * db[1] + bF1 * db[2] + bIff * db[3] + bIpp * db[4] + bIFF * db[5];
-    if (want_exp) {
-      // d/dt of the six scalars: f', f'' = -2a f' - w2 f, f, f^2, f'^2, F1^2
-      g_dt += bf * fp + bfp * (F(-2) * c.a * fp - c.w2 * f) + bF1 * f + bIff * f * f +
-              bIpp * fp * fp + bIFF * F1 * F1;
-    }
+    bX[t][0] = bf;
+    bX[t][1] = bfp;
+    bX[t][2] = bF1;
+    bX[t][3] = bIff;
+    bX[t][4] = bIpp;
+    bX[t][5] = bIFF;
   }
-  (void)zl;
-  (void)zL;
-  // lam <- Phi~^T lam ; Lam <- Phi~^T Lam Phi~
+  // lam <- Phi~^T lam ; Lam <- Phi~^T T2 = Phi~^T Lam Phi~
   {
     F o[D];
     apply_phi_t<S>(B, lam, o);
 #pragma unroll
     for (int i = 0; i < D; ++i) lam[i] = o[i];
-  }
-  F T2[D][D];  // T2 = Lam Phi~ : row i = (Phi~^T Lam[i,:])^T
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    F row[D], o[D];
-#pragma unroll
-    for (int kk = 0; kk < D; ++kk) row[kk] = Lam[S::pk(i, kk)];
-    apply_phi_t<S>(B, row, o);
-#pragma unroll
-    for (int kk = 0; kk < D; ++kk) T2[i][kk] = o[kk];
   }
 #pragma unroll
   for (int cc = 0; cc < D; ++cc) {
@@ -1254,6 +1266,23 @@ GPSS_D void reverse_event(float dt, uint8_t tag, float4 q, const TermC<float> *t
     apply_phi_t<S>(B, col, o);
 #pragma unroll
     for (int i = 0; i <= cc; ++i) Lam[S::pk(i, cc)] = o[i];
+  }
+  // through the discretisation: (a, beta) tangents of the six scalars
+#pragma unroll
+  for (int t = 0; t < S::NT; ++t) {
+    const TermC<F> &c = tc[t];
+    F da[6], db[6];
+    disc_tangents<OD>(dt, c, tab + t * (TAB_TERM / 4), dv[t], da, db);
+    gr.a[t] += bX[t][0] * da[0] + bX[t][1] * da[1] + bX[t][2] * da[2] + bX[t][3] * da[3] +
+               bX[t][4] * da[4] + bX[t][5] * da[5];
+    gr.beta[t] += bX[t][0] * db[0] + bX[t][1] * db[1] + bX[t][2] * db[2] + bX[t][3] * db[3] +
+                  bX[t][4] * db[4] + bX[t][5] * db[5];
+    if (want_exp) {
+      // d/dt of the six scalars: f', f'' = -2a f' - w2 f, f, f^2, f'^2, F1^2
+      const F f = dv[t].f, fp = dv[t].fp, F1 = dv[t].F1;
+      g_dt += bX[t][0] * fp + bX[t][1] * (F(-2) * c.a * fp - c.w2 * f) + bX[t][2] * f +
+              bX[t][3] * f * f + bX[t][4] * fp * fp + bX[t][5] * F1 * F1;
+    }
   }
 }
 
@@ -1514,7 +1543,8 @@ __global__ void __launch_bounds__(GRAD_BS, GRAD_MIN_BLOCKS) k_grad(DevModel M, c
           cp_async_wait<GRAD_STAGES - 1>();
         }
         const float4 *sb = stg + (size_t)buf * (SG + NDG) * bs;
-        {
+        if constexpr (EX) {
+          // the extra outputs read (m, P) as arrays
           float r[4 * SG];
   #pragma unroll
           for (int v = 0; v < SG; ++v) {
@@ -1559,8 +1589,13 @@ __global__ void __launch_bounds__(GRAD_BS, GRAD_MIN_BLOCKS) k_grad(DevModel M, c
             o[1] = r.y;
           }
         };
-        reverse_event<S, OD>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab, dv, EX && gdt != nullptr, g_dt, g_w,
-                         hook);
+        if constexpr (EX)
+          reverse_event<S, OD, decltype(hook), const float *>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab,
+                                                              dv, gdt != nullptr, g_dt, g_w, hook);
+        else
+          reverse_event<S, OD, NoHook, StagedRec>(dt, tag, q, tc, s2, StagedRec{sb, bs, 0},
+                                                  StagedRec{sb, bs, D}, lam, Lam, gr, tab, dv, false,
+                                                  g_dt, g_w);
         if (EX && gdt) {
           gdt[eo + k2] = g_dt;
           if (tag & 1) gwe[eo + k2] = q.z * q.z * g_w;

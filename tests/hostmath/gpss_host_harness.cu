@@ -437,4 +437,29 @@ double hh_span_fold(int shape, const double *elems, int n_spans) {
   return span_fold_s<Shape<2, 1, 1>>(elems, n_spans);
 }
 
+// Covariance prediction in FP64: P (packed upper triangle of the shape's
+// state) <- Phi~ P Phi~^T + Q~ with the blocks of each term given as 12
+// doubles (p00 p01 p10 p11 pb0 pb1 q00 q01 q11 qz0 qz1 qzz).  Shape ids: 0 =
+// (1 term, 1 slot), 1 = (1 term, 3 slots), 2 = (2 terms, 1 slot, layout 1),
+// 3 = (2 terms, 3 slots), 4 = (2 terms, 2 slots), 5 = (2 terms, no slot).
+void hh_predict_cov(int shape, const double *blocks, double *P) {
+  auto run = [&](auto tag) {
+    using S = decltype(tag);
+    Blocks<double> B[S::NT];
+    for (int t = 0; t < S::NT; ++t) {
+      const double *b = blocks + 12 * t;
+      B[t] = Blocks<double>{b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7], b[8], b[9], b[10], b[11]};
+    }
+    predict_cov<S, double>(B, P);
+  };
+  switch (shape) {
+    case 0: run(Shape<1, 1, 0>{}); break;
+    case 1: run(Shape<1, 3, 0>{}); break;
+    case 2: run(Shape<2, 1, 1>{}); break;
+    case 3: run(Shape<2, 3, 0>{}); break;
+    case 4: run(Shape<2, 2, 0>{}); break;
+    case 5: run(Shape<2, 0, 0>{}); break;
+  }
+}
+
 }  // extern "C"

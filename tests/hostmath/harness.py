@@ -48,4 +48,5 @@ def load():
     lib.hh_span_element.argtypes = [i32, vp, vp, vp, vp, vp, i64, i64, i32, vp]
     lib.hh_span_fold.argtypes = [i32, vp, i32]
     lib.hh_span_fold.restype = d
+    lib.hh_predict_cov.argtypes = [i32, vp, vp]
     return lib

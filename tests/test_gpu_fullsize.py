@@ -22,6 +22,7 @@ import pytest
 
 import oracle
 import synth
+from gpu_checks import check_mean_var, prior_var
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -82,9 +83,8 @@ def test_c4_full_autotuned(gp):
     for i in idx[:4]:
         a, b = wl.offsets[i], wl.offsets[i + 1]
         ts, te, y, ye, inst = wl.series(i)
-        mu, va = oracle.condition(wl.terms, wl.layout, ts, te, y, ye, wl.theta[i])
-        assert np.all(np.abs(cond[a:b, 0] - mu) <= 1e-3 * np.abs(mu).max() + 1e-5 * np.abs(mu))
-        assert np.all(np.abs(cond[a:b, 1] - va) <= 2e-3 * va + 1e-5 * va.max())
+        check_mean_var(cond[a:b], *oracle.condition(wl.terms, wl.layout, ts, te, y, ye, wl.theta[i]),
+                       prior_var(wl.terms, wl.layout, ts, te, y, ye, wl.theta[i]))
     # time-shift invariance of the exposure gradient, every series
     for s in range(wl.n_series):
         a, b = wl.offsets[s], wl.offsets[s + 1]

@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 import synth
+from gpu_checks import check_mean_var, prior_var
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -122,16 +123,14 @@ def test_condition_and_predict(gp):
     pred = pred.cpu().numpy()[0]
     for s in range(wl.n_series):
         ts, te, y, ye, _ = wl.series(s)
+        v0 = prior_var(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s])
         for got, (mu, va) in (
                 (cond[wl.offsets[s]:wl.offsets[s + 1]],
                  oracle.condition(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s])),
                 (pred[offs[s]:offs[s + 1]],
                  oracle.predict(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s],
                                 tq[offs[s]:offs[s + 1]]))):
-            gm, gv = got[:, 0].astype(np.float64), got[:, 1].astype(np.float64)
-            assert np.all(np.abs(gm - mu) <= 1e-3 * np.abs(mu).max() + 1e-5 * np.abs(mu))
-            bad = np.abs(gv - va) > 2e-3 * np.abs(va) + 1e-5 * va.max()
-            assert not bad.any(), (s, gv[bad][:5], va[bad][:5])
+            check_mean_var(got, mu, va, v0)
 
 
 def test_single_term(gp):

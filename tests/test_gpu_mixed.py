@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 import synth
+from gpu_checks import check_mean_var, prior_var
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -101,14 +102,12 @@ def test_mixed_condition_predict_exposure(gp):
     for s in range(wl.n_series):
         a, b = wl.offsets[s], wl.offsets[s + 1]
         ts, te, y, ye, _ = wl.series(s)
-        mu, va = oracle.condition(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s])
-        assert np.all(np.abs(cond[a:b, 0] - mu) <= 1e-3 * np.abs(mu).max() + 1e-5 * np.abs(mu))
-        assert np.all(np.abs(cond[a:b, 1] - va) <= 2e-3 * va + 1e-5 * va.max())
-        pm, pv = oracle.predict(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s],
-                                tq[offs[s]:offs[s + 1]])
-        got = pred[offs[s]:offs[s + 1]]
-        assert np.all(np.abs(got[:, 0] - pm) <= 1e-3 * np.abs(pm).max() + 1e-5 * np.abs(pm))
-        assert np.all(np.abs(got[:, 1] - pv) <= 2e-3 * pv + 1e-5 * pv.max())
+        v0 = prior_var(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s])
+        check_mean_var(cond[a:b], *oracle.condition(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s]),
+                       v0)
+        check_mean_var(pred[offs[s]:offs[s + 1]],
+                       *oracle.predict(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s],
+                                       tq[offs[s]:offs[s + 1]]), v0)
         r_ts, r_te = oracle.exposure_grad(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s])
         ref = np.stack([r_ts, r_te], axis=1)
         bad = np.abs(dexp[a:b] - ref) > 1e-3 * np.abs(ref) + 1e-4 * np.abs(ref).max()

@@ -271,3 +271,52 @@ def test_product_discretisation(oracle_lib, hh, theta):
                             _p(Q, ctypes.c_double))
             assert np.all(np.abs(Phi.reshape(4, 4) - P_ref) <= tol * (np.abs(P_ref) + 1)), (prec, dt)
             assert np.all(np.abs(Q.reshape(4, 4) - Q_ref) <= tol * (np.abs(Q_ref) + scale)), (prec, dt)
+
+
+# (terms, slots, layout) of the harness's covariance-prediction shape ids
+_PRED_SHAPES = {0: (1, 1, 0), 1: (1, 3, 0), 2: (2, 1, 1), 3: (2, 3, 0), 4: (2, 2, 0), 5: (2, 0, 0)}
+
+
+@pytest.mark.parametrize("shape", sorted(_PRED_SHAPES))
+def test_covariance_prediction_in_place(hh, shape):
+    # the kernels' in-place, one-term-at-a-time P <- Phi P Phi^T + Q against
+    # the dense product of the transition and noise the blocks define
+    # (Section 3.2: Phi~ maps each term's pair by its 2x2 block; an integral
+    # state adds pb0 x + pb1 xdot of the terms it integrates)
+    nt, ns, layout = _PRED_SHAPES[shape]
+    nz = ns * (1 if layout == 0 or nt == 1 else nt)
+    D = 2 * nt + nz
+    zs = list(range(2 * nt, D))
+
+    def integrates(z, t):
+        return True if (layout == 0 or nt == 1) else (z - 2 * nt) % nt == t
+
+    rng = np.random.default_rng(40 + shape)
+    for _ in range(20):
+        G = rng.normal(size=(D, D))
+        P = G @ G.T
+        blk = rng.normal(size=(nt, 12))
+        Phi, Q = np.eye(D), np.zeros((D, D))
+        for t in range(nt):
+            p00, p01, p10, p11, pb0, pb1, q00, q01, q11, qz0, qz1, qzz = blk[t]
+            a0, a1 = 2 * t, 2 * t + 1
+            Phi[a0, a0], Phi[a0, a1], Phi[a1, a0], Phi[a1, a1] = p00, p01, p10, p11
+            Q[a0, a0] += q00
+            Q[a0, a1] += q01
+            Q[a1, a0] += q01
+            Q[a1, a1] += q11
+            for z in zs:
+                if not integrates(z, t):
+                    continue
+                Phi[z, a0], Phi[z, a1] = pb0, pb1
+                for (i, v) in ((a0, qz0), (a1, qz1)):
+                    Q[i, z] += v
+                    Q[z, i] += v
+                for z2 in zs:
+                    if integrates(z2, t):
+                        Q[z, z2] += qzz
+        ref = Phi @ P @ Phi.T + Q
+        v = np.array([P[i, j] for i in range(D) for j in range(i, D)], np.float64)
+        b = np.ascontiguousarray(blk.ravel(), np.float64)
+        hh.hh_predict_cov(shape, b.ctypes.data, v.ctypes.data)
+        np.testing.assert_allclose(_unpack(v, D), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
