@@ -36,12 +36,12 @@ UNIT = "measurements/s"
 # replay included), from ncu's FP32 instruction counters of one k_grad launch
 # on 512 series of the c4 recipe (chunk length 256, segments of 64), captured
 # with --clock-control none.
-ALG_FLOPS_PER_EVENT = {"c4": 1578.8}
+ALG_FLOPS_PER_EVENT = {"c4": 1440.2}
 # DRAM bytes (read + write) per event of that k_grad launch, same capture;
 # the traffic grows with the events (replay records, cached step scalars,
 # partial elements, event stream), so a full launch is this x its events.
 # Valid for the captured configuration only (chunk length 256, segments of 64).
-TRAFFIC_PER_EVENT = {"c4": (346.9, 256, 64)}
+TRAFFIC_PER_EVENT = {"c4": (347.1, 256, 64)}
 FP32_LANES_PER_SM = 128
 
 # Per workload: whether a step includes the gradient, and whether the

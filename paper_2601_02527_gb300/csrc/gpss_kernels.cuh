@@ -1543,8 +1543,11 @@ __global__ void __launch_bounds__(GRAD_BS, GRAD_MIN_BLOCKS) k_grad(DevModel M, c
           cp_async_wait<GRAD_STAGES - 1>();
         }
         const float4 *sb = stg + (size_t)buf * (SG + NDG) * bs;
-        if constexpr (EX) {
-          // the extra outputs read (m, P) as arrays
+        // the extra outputs read (m, P) as arrays; so does the lean body of a
+        // shape without integral states, whose smaller state fits in registers
+        // (reading it from shared memory there measured slower)
+        constexpr bool ARR = EX || S::NS == 0;
+        if constexpr (ARR) {
           float r[4 * SG];
   #pragma unroll
           for (int v = 0; v < SG; ++v) {
@@ -1589,7 +1592,7 @@ __global__ void __launch_bounds__(GRAD_BS, GRAD_MIN_BLOCKS) k_grad(DevModel M, c
             o[1] = r.y;
           }
         };
-        if constexpr (EX)
+        if constexpr (ARR)
           reverse_event<S, OD, decltype(hook), const float *>(dt, tag, q, tc, s2, m, P, lam, Lam, gr, tab,
                                                               dv, gdt != nullptr, g_dt, g_w, hook);
         else

@@ -12,10 +12,13 @@ import numpy as np
 import oracle
 
 
-def prior_var(terms, layout, ts, te, y, ye, theta):
-    """The latent's stationary prior variance: the oracle's prediction at a
-    time long before the data, where they no longer inform it."""
-    _, v = oracle.predict(terms, layout, ts, te, y, ye, theta, np.array([ts.min() - 1e4]))
+def prior_var(terms, layout, theta):
+    """The latent's stationary prior variance: the oracle's prediction long
+    before a single, uninformative exposure (the series' own data may hold
+    coincident resets that the oracle's smoother does not take)."""
+    one = np.array([0.0])
+    _, v = oracle.predict(terms, layout, one, one + 1.0, one, np.array([1e6]), theta,
+                          np.array([-1e4]))
     return float(v[0])
 
 

@@ -46,7 +46,7 @@ def _oracle_cond(wl, s, theta):
     # (mean, variance, the latent's prior variance)
     ts, te, y, ye, inst = wl.series(s)
     mu, va = oracle.condition(wl.terms, wl.layout, ts, te, y, ye, theta, instrument=inst)
-    return mu, va, prior_var(wl.terms, wl.layout, ts, te, y, ye, theta)
+    return mu, va, prior_var(wl.terms, wl.layout, theta)
 
 
 @pytest.mark.parametrize("chunk,ck", [(48, 8), (64, 16), (0, 32), (0, 64)])
@@ -88,7 +88,7 @@ def test_shared_series_theta_sets(gp):
     ts, te, y, ye, _ = wl.series(0)
     for k in range(3):
         _check(cond[k], *dense.posterior(wl.terms, wl.theta[k], ts, te, y, ye),
-               prior_var(wl.terms, wl.layout, ts, te, y, ye, wl.theta[k]))
+               prior_var(wl.terms, wl.layout, wl.theta[k]))
 
 
 def test_edge_cases(gp):

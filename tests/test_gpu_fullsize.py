@@ -84,7 +84,7 @@ def test_c4_full_autotuned(gp):
         a, b = wl.offsets[i], wl.offsets[i + 1]
         ts, te, y, ye, inst = wl.series(i)
         check_mean_var(cond[a:b], *oracle.condition(wl.terms, wl.layout, ts, te, y, ye, wl.theta[i]),
-                       prior_var(wl.terms, wl.layout, ts, te, y, ye, wl.theta[i]))
+                       prior_var(wl.terms, wl.layout, wl.theta[i]))
     # time-shift invariance of the exposure gradient, every series
     for s in range(wl.n_series):
         a, b = wl.offsets[s], wl.offsets[s + 1]

@@ -123,7 +123,7 @@ def test_condition_and_predict(gp):
     pred = pred.cpu().numpy()[0]
     for s in range(wl.n_series):
         ts, te, y, ye, _ = wl.series(s)
-        v0 = prior_var(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s])
+        v0 = prior_var(wl.terms, wl.layout, wl.theta[s])
         for got, (mu, va) in (
                 (cond[wl.offsets[s]:wl.offsets[s + 1]],
                  oracle.condition(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s])),

@@ -102,7 +102,7 @@ def test_mixed_condition_predict_exposure(gp):
     for s in range(wl.n_series):
         a, b = wl.offsets[s], wl.offsets[s + 1]
         ts, te, y, ye, _ = wl.series(s)
-        v0 = prior_var(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s])
+        v0 = prior_var(wl.terms, wl.layout, wl.theta[s])
         check_mean_var(cond[a:b], *oracle.condition(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s]),
                        v0)
         check_mean_var(pred[offs[s]:offs[s + 1]],

@@ -67,7 +67,7 @@ def test_two_sho_layout1(gp, chunk, ck):
         q = tq[offs[s]:offs[s + 1]]
         mu, va = oracle.predict(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s], q)
         _check(pred[offs[s]:offs[s + 1]], mu, va,
-               prior_var(wl.terms, wl.layout, ts, te, y, ye, wl.theta[s]))
+               prior_var(wl.terms, wl.layout, wl.theta[s]))
 
 
 def test_sho_plus_matern_overlap(gp):
@@ -87,7 +87,7 @@ def test_sho_plus_matern_overlap(gp):
     t0, t1, y, ye, ins = wl.series(0)
     _check(pred.cpu().numpy()[0], *oracle.predict(wl.terms, wl.layout, t0, t1, y, ye,
                                                   wl.theta[0], tq, instrument=ins),
-           prior_var(wl.terms, wl.layout, t0, t1, y, ye, wl.theta[0]))
+           prior_var(wl.terms, wl.layout, wl.theta[0]))
 
 
 def test_shared_series_sets(gp):
@@ -103,4 +103,4 @@ def test_shared_series_sets(gp):
     for k in range(2):
         # coincident resets at t = 0: the dense prediction is the reference
         _check(pred[k], *dense.predict(wl.terms, wl.theta[k], t0, t1, y, ye, tq),
-               prior_var(wl.terms, wl.layout, t0, t1, y, ye, wl.theta[k]))
+               prior_var(wl.terms, wl.layout, wl.theta[k]))
