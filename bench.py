@@ -70,13 +70,15 @@ def load_peaks():
 def product_extra(gp, stream):
     """Log-likelihood throughput of the product-kernel path (quasi-periodic
     SHO x SHO + Matern-3/2 on instantaneous measurements, 410 series of the
-    c2p recipe): FP32 chunked parallel-in-time, and the plain FP64 filter."""
+    c2p recipe): FP32 chunked parallel-in-time, and the plain FP64 filter;
+    and of its FP32 log-likelihood + gradient, chunked and per series."""
     import synth
     import torch
     wl = synth.c2p(n_series=410)
     theta = torch.tensor(wl.theta, dtype=torch.float32, device="cuda")
     out = {"workload": "c2p, 410 series", "n_meas": int(wl.n_meas), "unit": UNIT,
-           "work": "loglik only; fp32: chunked parallel-in-time, fp64: plain per-series filter"}
+           "work": "fp32, fp64: loglik (chunked parallel-in-time; plain per-series filter); "
+                   "fp32_grad_*: loglik + gradient, per chunk or per series"}
     for prec in (32, 64):
         m = gp.Model.from_workload(wl, precision=prec)
         ll = torch.empty(wl.n_series, dtype=torch.float64, device="cuda")
@@ -89,6 +91,22 @@ def product_extra(gp, stream):
         b.record(stream)
         torch.cuda.synchronize()
         out[f"fp{prec}"] = wl.n_meas / (a.elapsed_time(b) / 3 / 1e3)
+        del m
+    # loglik + gradient (FP32 forward-mode tangents): per chunk and parameter
+    # against the combination's boundary adjoints, and per series and parameter
+    for key, sched in (("fp32_grad_chunked", 0), ("fp32_grad_per_series", 3)):
+        m = gp.Model.from_workload(wl, schedule=sched)
+        ll = torch.empty(wl.n_series, dtype=torch.float64, device="cuda")
+        g = torch.empty(wl.n_series, m.n_params, dtype=torch.float32, device="cuda")
+        m.loglik_grad(theta, out=ll, grad=g)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            m.loglik_grad(theta, out=ll, grad=g)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[key] = wl.n_meas / (a.elapsed_time(b) / 3 / 1e3)
         del m
     return out
 

@@ -224,7 +224,7 @@ struct GraphKey {
 struct gp_ss_model {
   int device = 0;
   int n_series = 0, n_terms = 0, kinds[4] = {0, 0, 0, 0}, layout = 0, n_slots = 1;
-  bool product = false;  // a product term: plain log-likelihood filters only
+  bool product = false;  // a product term (instantaneous measurements only)
   bool mixed = false;    // instantaneous measurements among exposure averages
   int n_params = 0, precision = 32, schedule = 0;
   int64_t n_meas = 0, n_events = 0;
@@ -890,14 +890,19 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
   const gpss::DevModel dm = dev_view(m);
   const OpTable &o = m->ops;
   if (m->product) {
-    // product kernels: the plain filters; the hyperparameter gradient by
-    // forward-mode tangents (FP32)
+    // product kernels: the plain filters (FP64, schedule 3), or the chunked
+    // log-likelihood below; the hyperparameter gradient by forward-mode
+    // tangents (FP32), per series (schedule 3) or per chunk
     if (dexp || cond_out || pred) return GP_SS_EUNSUPPORTED;
     if (grad) {
       if (m->precision == 64) return GP_SS_EUNSUPPORTED;
-      PhaseTimer pt(m, st, 2);
-      GPSS_CK(o.prod_grad(dm, theta, n_out, per_series, ll, grad, m->d_err, st));
-      return GP_SS_OK;
+      // the plain schedule: one thread per series and parameter over the
+      // whole series; otherwise the chunked path below
+      if (m->schedule == 3 || !o.prod_grad_chunk) {
+        PhaseTimer pt(m, st, 2);
+        GPSS_CK(o.prod_grad(dm, theta, n_out, per_series, ll, grad, m->d_err, st));
+        return GP_SS_OK;
+      }
     }
     if (m->precision == 64 && !m->d_dt64) return GP_SS_EINVAL;
     if (m->precision == 64 || m->schedule == 3) {
@@ -953,14 +958,15 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
     if (!grab((void **)&ef, (size_t)o.NF * n_vch * sizeof(float)) ||
         !grab((void **)&ed, (size_t)o.ND * n_vch * sizeof(double)) ||
         !grab((void **)&tabs, (size_t)n_sets * o.NT * gpss::TAB_TERM * sizeof(float)) ||
-        (grad && !grab((void **)&ckpt, (size_t)n_pck * (o.NF + 1) * n_vch * sizeof(float)))) {
+        (grad && !m->product &&
+         !grab((void **)&ckpt, (size_t)n_pck * (o.NF + 1) * n_vch * sizeof(float)))) {
       res = GP_SS_ENOMEM;
       break;
     }
     // the element pass keeps every step's scalars for the gradient's replay
     // while that takes at most kDcacheMax bytes (else the replay recomputes them)
     float *dcache = nullptr;
-    if (grad) {
+    if (grad && !m->product) {
       const size_t dbytes = (size_t)(n_vch / m->n_chunks) * (size_t)m->dcache_steps *
                             (4 * ((6 * o.NT + 3) / 4)) * sizeof(float);
       if (m->step_cache == 0 && dbytes <= kDcacheMax && !grab((void **)&dcache, dbytes)) {
@@ -1041,38 +1047,47 @@ gp_ss_status enqueue(const gp_ss_model *m, const float *theta, int n_sets, int p
         res = GP_SS_ENOMEM;
         break;
       }
-      if (!grab((void **)&rbuf, (size_t)ck * (4 * ((SD + 3) / 4)) * n_vch * sizeof(float)) ||
+      if ((!m->product &&
+           !grab((void **)&rbuf, (size_t)ck * (4 * ((SD + 3) / 4)) * n_vch * sizeof(float))) ||
           !grab((void **)&gpart, (size_t)m->n_params * n_vch * sizeof(float))) {
         res = GP_SS_ENOMEM;
         break;
       }
       PhaseTimer pt(m, st, 2);
-      const gpss::PredPlan none;
-      if (o.grad(dm, theta, n_vch, per_series, state_end, eb == 8 ? 1 : 0, adj, ckpt, gpart,
-                 m->d_err, tabs, rbuf, dcache, ck, gdt, gwe, cond, pred ? *pred : none, st)) {
-        res = GP_SS_ECUDA;
-        break;
-      }
-      if (cond_out && m->n_meas > 0) {
-        const int64_t nt = (int64_t)exp_rows * m->n_meas;
-        gpss::k_gather_cond<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(
-            exp_rows, m->n_series, m->d_ev_off, m->d_meas_off, m->d_mev, m->n_meas, m->n_events,
-            cond, cond_out);
-        GPSS_COUNT_LAUNCH();
-        if (cudaGetLastError() != cudaSuccess) {
+      if (m->product) {
+        // chunked forward-mode tangents against the boundary adjoints
+        if (o.prod_grad_chunk(dm, theta, n_vch, per_series, state_end, eb == 8 ? 1 : 0, adj, gpart,
+                              m->d_err, st))
+          res = GP_SS_ECUDA;
+        if (res) break;
+      } else {
+        const gpss::PredPlan none;
+        if (o.grad(dm, theta, n_vch, per_series, state_end, eb == 8 ? 1 : 0, adj, ckpt, gpart,
+                   m->d_err, tabs, rbuf, dcache, ck, gdt, gwe, cond, pred ? *pred : none, st)) {
           res = GP_SS_ECUDA;
           break;
         }
-      }
-      if (dexp && m->n_meas > 0) {
-        const int64_t nt = (int64_t)exp_rows * m->n_meas;
-        gpss::k_exposure_grad<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(
-            exp_rows, m->n_series, m->d_ev_off, m->d_meas_off, m->d_mev, m->n_meas, m->n_events,
-            gdt, gwe, dexp);
-        GPSS_COUNT_LAUNCH();
-        if (cudaGetLastError() != cudaSuccess) {
-          res = GP_SS_ECUDA;
-          break;
+        if (cond_out && m->n_meas > 0) {
+          const int64_t nt = (int64_t)exp_rows * m->n_meas;
+          gpss::k_gather_cond<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(
+              exp_rows, m->n_series, m->d_ev_off, m->d_meas_off, m->d_mev, m->n_meas, m->n_events,
+              cond, cond_out);
+          GPSS_COUNT_LAUNCH();
+          if (cudaGetLastError() != cudaSuccess) {
+            res = GP_SS_ECUDA;
+            break;
+          }
+        }
+        if (dexp && m->n_meas > 0) {
+          const int64_t nt = (int64_t)exp_rows * m->n_meas;
+          gpss::k_exposure_grad<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(
+              exp_rows, m->n_series, m->d_ev_off, m->d_meas_off, m->d_mev, m->n_meas, m->n_events,
+              gdt, gwe, dexp);
+          GPSS_COUNT_LAUNCH();
+          if (cudaGetLastError() != cudaSuccess) {
+            res = GP_SS_ECUDA;
+            break;
+          }
         }
       }
     }
@@ -1827,7 +1842,7 @@ gp_ss_status gp_ss_autotune(gp_ss_model *m, const float *theta, int n_sets,
   gp_ss_status s = check_call(m, theta, n_sets, theta_per_series, best);
   if (s) return s;
   if (m->precision != 32 || reps < 1 || reps > 100) return GP_SS_EINVAL;
-  if (m->product) return GP_SS_EUNSUPPORTED;  // one schedule: nothing to tune
+  if (m->product) return GP_SS_EUNSUPPORTED;  // product models are not tuned
   DeviceGuard g(m->device);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   if (cudaDeviceSynchronize() != cudaSuccess) return GP_SS_ECUDA;

@@ -1901,6 +1901,10 @@ struct OpTable {
   // product models: log-likelihood and hyperparameter gradient (else null)
   cudaError_t (*prod_grad)(const DevModel &, const float *, int, int, double *, float *, int *,
                            cudaStream_t);
+  // product models, chunked schedule: gradient parts per (chunk, parameter)
+  // from the combination's incoming states and boundary adjoints (else null)
+  cudaError_t (*prod_grad_chunk)(const DevModel &, const float *, int, int, const void *, int,
+                                 const float *, float *, int *, cudaStream_t);
   // a series split in time: element of a chunk range, fold of span elements
   cudaError_t (*span_element)(const float *, const double *, int, int, int, int, int, double *,
                               double *, cudaStream_t);

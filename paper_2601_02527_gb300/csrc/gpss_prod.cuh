@@ -12,8 +12,10 @@
 // log-likelihood runs in parallel in time (k_elem_prod forms dense chunk
 // elements, the dimension-generic combination of a same-size shape does the
 // rest), the plain sequential filter (one thread per series) serves FP64 and
-// schedule 3, and the hyperparameter gradient comes from forward-mode tangents
-// (one thread per series and parameter).
+// schedule 3, and the hyperparameter gradient comes from forward-mode tangents:
+// per chunk and parameter against the combination's boundary adjoints
+// (k_prod_grad_chunk, the chunked schedule), or per series and parameter
+// (k_prod_grad, schedule 3).
 #pragma once
 
 #include <type_traits>
@@ -190,15 +192,170 @@ __global__ void __launch_bounds__(128) k_plain_prod(DevModel M, const float *__r
   if (bad) flag_error(err, v, 7);
 }
 
-// Forward-mode gradient of the product filter: one thread per (output row,
-// parameter i) runs the filter in Dual2<float> with d/d theta_i in .da and
-// accumulates d loglik / d theta_i = -1/2 sum (dS/S + 2 v dv / S - v^2 dS / S^2)
-// in FP64; the i = 0 thread also writes the log-likelihood.
+// Forward-mode gradient of the product filter: the filter runs in
+// Dual2<float> with d/d theta_i in .da, and d loglik / d theta_i accumulates
+// -1/2 sum (dS/S + 2 v dv / S - v^2 dS / S^2) in FP64.
 template <class T>
 GPSS_D T seed(float v, bool on);
 template <>
 GPSS_D Dual2<float> seed<Dual2<float>>(float v, bool on) { return mk(v, on ? 1.f : 0.f, 0.f); }
 
+// The product model's parameters as duals, parameter ip seeded (row layout as
+// for k_plain_prod).
+template <bool SUM>
+struct ProdPar {
+  using T = Dual2<float>;
+  T wa, qa, wb, qb, var, sc, wc, qcq, s2;
+};
+
+template <bool SUM>
+GPSS_D ProdPar<SUM> prod_par(const DevModel &M, const float *th, int ip) {
+  using F = float;
+  using T = Dual2<F>;
+  auto par = [&](int i) { return seed<T>(th[i], i == ip); };
+  ProdPar<SUM> p;
+  const T sig = par(0);
+  p.wa = par(1);
+  p.qa = par(2);
+  p.wb = par(3);
+  p.qb = par(4);
+  p.var = sig * sig;
+  p.sc = cst<T>(F(0));
+  p.wc = cst<T>(F(1));
+  p.qcq = cst<T>(F(0.5));
+  int j = 5;
+  if constexpr (SUM) {
+    p.sc = par(5);
+    if (M.kinds[1] == 1) {
+      p.wc = par(6);
+      p.qcq = par(7);
+      j = 8;
+    } else {
+      p.wc = cst<T>(F(1.7320508075688772)) / par(6);
+      j = 7;
+    }
+  }
+  const T sw = par(j);
+  p.s2 = sw * sw;
+  return p;
+}
+
+// Stationary prior of the product state (P_inf,a (x) P_inf,b; the plain term's
+// block when SUM), zero mean.
+template <bool SUM>
+GPSS_D void prod_prior(const ProdPar<SUM> &p, Dual2<float> (*m), Dual2<float> (*P)[SUM ? 6 : 4]) {
+  using F = float;
+  using T = Dual2<F>;
+  constexpr int D = SUM ? 6 : 4;
+  const T one = cst<T>(F(1));
+  const T Pa[2] = {one, p.wa * p.wa}, Pb[2] = {p.var, p.var * p.wb * p.wb};
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    m[i] = cst<T>(F(0));
+#pragma unroll
+    for (int c = 0; c < D; ++c) P[i][c] = cst<T>(F(0));
+  }
+#pragma unroll
+  for (int ra = 0; ra < 2; ++ra)
+#pragma unroll
+    for (int rb = 0; rb < 2; ++rb) P[2 * ra + rb][2 * ra + rb] = Pa[ra] * Pb[rb];
+  if constexpr (SUM) {
+    P[4][4] = p.sc * p.sc;
+    P[5][5] = p.sc * p.sc * p.wc * p.wc;
+  }
+}
+
+// One event (instantaneous measurement y with variance r0) of the dual
+// product filter on the dense (m, P); adds log S + v^2/S and its tangent.
+template <bool SUM>
+GPSS_D void prod_event(const ProdPar<SUM> &p, float dt, float y, float r0, Dual2<float> *m,
+                       Dual2<float> (*P)[SUM ? 6 : 4], double &sum_ll, double &sum_d, bool &bad) {
+  using F = float;
+  using T = Dual2<F>;
+  constexpr int D = SUM ? 6 : 4;
+  const T one = cst<T>(F(1));
+  const T Pa[2] = {one, p.wa * p.wa}, Pb[2] = {p.var, p.var * p.wb * p.wb};
+  const Osc2<T> A = osc2<T, F>(dt, p.wa, p.qa, one);
+  const Osc2<T> B = osc2<T, F>(dt, p.wb, p.qb, p.var);
+  T Phi[D][D], Qd[D][D];
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int c = 0; c < D; ++c) Phi[r][c] = Qd[r][c] = cst<T>(F(0));
+#pragma unroll
+  for (int ra = 0; ra < 2; ++ra)
+#pragma unroll
+    for (int rb = 0; rb < 2; ++rb)
+#pragma unroll
+      for (int ca = 0; ca < 2; ++ca)
+#pragma unroll
+        for (int cb = 0; cb < 2; ++cb) {
+          const int r = 2 * ra + rb, c = 2 * ca + cb;
+          Phi[r][c] = A.p[ra][ca] * B.p[rb][cb];
+          T q = -(A.q[ra][ca] * B.q[rb][cb]);  // Eq. product_Q
+          if (ra == ca) q = q + Pa[ra] * B.q[rb][cb];
+          if (rb == cb) q = q + A.q[ra][ca] * Pb[rb];
+          Qd[r][c] = q;
+        }
+  if constexpr (SUM) {
+    const Osc2<T> C = osc2<T, F>(dt, p.wc, p.qcq, p.sc * p.sc);
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        Phi[4 + r][4 + c] = C.p[r][c];
+        Qd[4 + r][4 + c] = C.q[r][c];
+      }
+  }
+  T mt[D], Tm[D][D];
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    T acc = cst<T>(F(0));
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc = acc + Phi[r][c] * m[c];
+    mt[r] = acc;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      T a2 = cst<T>(F(0));
+#pragma unroll
+      for (int e = 0; e < D; ++e) a2 = a2 + Phi[r][e] * P[e][c];
+      Tm[r][c] = a2;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    m[r] = mt[r];
+#pragma unroll
+    for (int c = r; c < D; ++c) {
+      T a2 = Qd[r][c];
+#pragma unroll
+      for (int e = 0; e < D; ++e) a2 = a2 + Tm[r][e] * Phi[c][e];
+      P[r][c] = a2;
+      P[c][r] = a2;
+    }
+  }
+  T u[D];
+#pragma unroll
+  for (int r = 0; r < D; ++r) u[r] = SUM ? P[r][0] + P[r][4] : P[r][0];
+  const T hu = SUM ? u[0] + u[4] : u[0];
+  const T hm = SUM ? m[0] + m[4] : m[0];
+  const T Sv = hu + p.s2 + r0;
+  const T vv = y - hm;
+  bad |= !(Sv.v > F(0));
+  const T iS = one / Sv;
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    m[r] = m[r] + u[r] * vv * iS;
+#pragma unroll
+    for (int c = 0; c < D; ++c) P[r][c] = P[r][c] - u[r] * u[c] * iS;
+  }
+  const double S = Sv.v, dS = Sv.da, e = vv.v, de = vv.da;
+  sum_ll += log(S) + e * e / S;
+  sum_d += dS / S + 2.0 * e * de / S - e * e * dS / (S * S);
+}
+
+// One thread per (output row, parameter i) over the whole series (the plain
+// schedule); the i = 0 thread also writes the log-likelihood.
 template <bool SUM>
 __global__ void __launch_bounds__(64) k_prod_grad(DevModel M, const float *__restrict__ theta,
                                                   int n_out, int per_series,
@@ -214,129 +371,19 @@ __global__ void __launch_bounds__(64) k_prod_grad(DevModel M, const float *__res
   const int v = (int)(tid / np), ip = (int)(tid % np);
   const int s = per_series ? v : v % M.n_series;
   const int row = per_series ? v : v / M.n_series;
-  const float *th = theta + (size_t)row * np;
-  auto par = [&](int i) { return seed<T>(th[i], i == ip); };
-  const T sig = par(0), wa = par(1), qa = par(2), wb = par(3), qb = par(4);
-  const T var = sig * sig;
-  const T one = cst<T>(F(1));
-  const T Pa[2] = {one, wa * wa}, Pb[2] = {var, var * wb * wb};
-  T sc = cst<T>(F(0)), wc = one, qcq = cst<T>(F(0.5));
-  int j = 5;
-  if constexpr (SUM) {
-    sc = par(5);
-    if (M.kinds[1] == 1) {
-      wc = par(6);
-      qcq = par(7);
-      j = 8;
-    } else {
-      wc = cst<T>(F(1.7320508075688772)) / par(6);
-      j = 7;
-    }
-  }
-  const T sw = par(j);
-  const T s2 = sw * sw;
+  const ProdPar<SUM> p = prod_par<SUM>(M, theta + (size_t)row * np, ip);
   T m[D], P[D][D];
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    m[i] = cst<T>(F(0));
-#pragma unroll
-    for (int c = 0; c < D; ++c) P[i][c] = cst<T>(F(0));
-  }
-#pragma unroll
-  for (int ra = 0; ra < 2; ++ra)
-#pragma unroll
-    for (int rb = 0; rb < 2; ++rb) P[2 * ra + rb][2 * ra + rb] = Pa[ra] * Pb[rb];
-  if constexpr (SUM) {
-    P[4][4] = sc * sc;
-    P[5][5] = sc * sc * wc * wc;
-  }
+  prod_prior<SUM>(p, m, P);
   double sum_ll = 0.0, sum_d = 0.0;
   int64_t n_end = 0;
   bool bad = false;
   int64_t mi = M.meas_off[s];
   const int64_t e1 = M.ev_off[s + 1];
   for (int64_t k = M.ev_off[s]; k < e1; ++k) {
-    const F dt = load_dt<F>(M, k);
     F y, r0, w;
     load_meas<F>(M, mi, y, r0, w);
     ++mi;
-    const Osc2<T> A = osc2<T, F>(dt, wa, qa, one);
-    const Osc2<T> B = osc2<T, F>(dt, wb, qb, var);
-    T Phi[D][D], Qd[D][D];
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int c = 0; c < D; ++c) Phi[r][c] = Qd[r][c] = cst<T>(F(0));
-#pragma unroll
-    for (int ra = 0; ra < 2; ++ra)
-#pragma unroll
-      for (int rb = 0; rb < 2; ++rb)
-#pragma unroll
-        for (int ca = 0; ca < 2; ++ca)
-#pragma unroll
-          for (int cb = 0; cb < 2; ++cb) {
-            const int r = 2 * ra + rb, c = 2 * ca + cb;
-            Phi[r][c] = A.p[ra][ca] * B.p[rb][cb];
-            T q = -(A.q[ra][ca] * B.q[rb][cb]);  // Eq. product_Q
-            if (ra == ca) q = q + Pa[ra] * B.q[rb][cb];
-            if (rb == cb) q = q + A.q[ra][ca] * Pb[rb];
-            Qd[r][c] = q;
-          }
-    if constexpr (SUM) {
-      const Osc2<T> C = osc2<T, F>(dt, wc, qcq, sc * sc);
-#pragma unroll
-      for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          Phi[4 + r][4 + c] = C.p[r][c];
-          Qd[4 + r][4 + c] = C.q[r][c];
-        }
-    }
-    T mt[D], Tm[D][D];
-#pragma unroll
-    for (int r = 0; r < D; ++r) {
-      T acc = cst<T>(F(0));
-#pragma unroll
-      for (int c = 0; c < D; ++c) acc = acc + Phi[r][c] * m[c];
-      mt[r] = acc;
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        T a2 = cst<T>(F(0));
-#pragma unroll
-        for (int e = 0; e < D; ++e) a2 = a2 + Phi[r][e] * P[e][c];
-        Tm[r][c] = a2;
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < D; ++r) {
-      m[r] = mt[r];
-#pragma unroll
-      for (int c = r; c < D; ++c) {
-        T a2 = Qd[r][c];
-#pragma unroll
-        for (int e = 0; e < D; ++e) a2 = a2 + Tm[r][e] * Phi[c][e];
-        P[r][c] = a2;
-        P[c][r] = a2;
-      }
-    }
-    T u[D];
-#pragma unroll
-    for (int r = 0; r < D; ++r) u[r] = SUM ? P[r][0] + P[r][4] : P[r][0];
-    const T hu = SUM ? u[0] + u[4] : u[0];
-    const T hm = SUM ? m[0] + m[4] : m[0];
-    const T Sv = hu + s2 + r0;
-    const T vv = y - hm;
-    bad |= !(Sv.v > F(0));
-    const T iS = one / Sv;
-#pragma unroll
-    for (int r = 0; r < D; ++r) {
-      m[r] = m[r] + u[r] * vv * iS;
-#pragma unroll
-      for (int c = 0; c < D; ++c) P[r][c] = P[r][c] - u[r] * u[c] * iS;
-    }
-    const double S = Sv.v, dS = Sv.da, e = vv.v, de = vv.da;
-    sum_ll += log(S) + e * e / S;
-    sum_d += dS / S + 2.0 * e * de / S - e * e * dS / (S * S);
+    prod_event<SUM>(p, load_dt<F>(M, k), y, r0, m, P, sum_ll, sum_d, bad);
     ++n_end;
   }
   const double ll = -0.5 * ((double)n_end * LOG_2PI + sum_ll);
@@ -347,6 +394,80 @@ __global__ void __launch_bounds__(64) k_prod_grad(DevModel M, const float *__res
   if (bad) flag_error(err, v, 7);
 }
 
+// Chunked gradient of a product model: one thread per (chunk, parameter i).
+// With the chunk's incoming filtered state s_in (from the parallel-in-time
+// combination) held fixed, the log-likelihood splits as 𝓛 = sum_c 𝓛_c(s_in,c,
+// theta), and by the chain rule over chunks
+//   d𝓛/dtheta_i = sum_c [ d𝓛_c/dtheta_i + lam_c . dm_end,c/dtheta_i
+//                         + sum_jk Lam_c[j,k] dP_end,c[j,k]/dtheta_i ],
+// the derivatives taken through chunk c's own steps only, (lam_c, Lam_c) the
+// adjoint of all later data's log-likelihood with respect to chunk c's end
+// state (the combination's boundary adjoint; full-matrix convention).  The
+// thread runs its chunk's filter in Dual2 from s_in (zero tangent; the prior,
+// with its tangent, for a series' first chunk) and writes its part of
+// d𝓛/dtheta_i; the per-series sums add the parts in chunk order.
+template <bool SUM, class ES>
+__global__ void __launch_bounds__(64) k_prod_grad_chunk(DevModel M, const float *__restrict__ theta,
+                                                        int n_vch, int per_series,
+                                                        const void *__restrict__ state_end, int se64,
+                                                        const float *__restrict__ adj_end,
+                                                        float *__restrict__ gpart,
+                                                        int *__restrict__ err) {
+  using F = float;
+  using T = Dual2<F>;
+  constexpr int D = SUM ? 6 : 4;
+  static_assert(ES::D == D, "combination shape of the product's state size");
+  const int np = M.n_params;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)n_vch * np) return;
+  // the threads of one chunk are adjacent and read the same events
+  const int vc = (int)(tid / np), ip = (int)(tid % np);
+  const int c = vc % M.n_chunks, set = vc / M.n_chunks;
+  const int s = M.ch_series[c];
+  const int row = per_series ? s : set;
+  const int orow = per_series ? s : set * M.n_series + s;
+  const uint8_t flags = M.ch_flags[c];
+  const ProdPar<SUM> p = prod_par<SUM>(M, theta + (size_t)row * np, ip);
+  T m[D], P[D][D];
+  if (flags & 1) {
+    prod_prior<SUM>(p, m, P);
+  } else {
+    F mf[D], Pf[ES::NP];
+    load_state_f<ES>(state_end, se64, n_vch, vc - 1, mf, Pf);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      m[i] = cst<T>(mf[i]);
+#pragma unroll
+      for (int j = 0; j < D; ++j) P[i][j] = cst<T>(Pf[ES::pk(i, j)]);
+    }
+  }
+  double sum_ll = 0.0, sum_d = 0.0;
+  bool bad = false;
+  int64_t mi = M.ch_meas0[c];
+  const int64_t k0 = M.ch_ev0[c], k1 = k0 + M.ch_len[c];
+  for (int64_t k = k0; k < k1; ++k) {
+    F y, r0, w;
+    load_meas<F>(M, mi, y, r0, w);
+    ++mi;
+    prod_event<SUM>(p, load_dt<F>(M, k), y, r0, m, P, sum_ll, sum_d, bad);
+  }
+  double g = -0.5 * sum_d;
+  if (!(flags & 2)) {
+    F lam[D], Lam[ES::NP];
+    load_rec<ES>(adj_end, n_vch, vc, lam, Lam);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      g += (double)lam[i] * (double)m[i].da;
+#pragma unroll
+      for (int j = i; j < D; ++j)
+        g += (i == j ? 1.0 : 2.0) * (double)Lam[ES::pk(i, j)] * (double)P[i][j].da;
+    }
+  }
+  bad |= !isfinite(g);
+  gpart[(size_t)ip * n_vch + vc] = (float)g;
+  if (bad) flag_error(err, orow, 7);
+}
+
 template <bool SUM>
 cudaError_t launch_prod_grad(const DevModel &M, const float *theta, int n_out, int per_series,
                              double *ll, float *grad, int *err, cudaStream_t st) {
@@ -355,6 +476,19 @@ cudaError_t launch_prod_grad(const DevModel &M, const float *theta, int n_out, i
   const int64_t nt = (int64_t)n_out * M.n_params;
   k_prod_grad<SUM><<<(unsigned)((nt + bs - 1) / bs), bs, 0, st>>>(M, theta, n_out, per_series, ll,
                                                                  grad, err);
+  GPSS_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+template <bool SUM, class ES>
+cudaError_t launch_prod_grad_chunk(const DevModel &M, const float *theta, int n_vch, int per_series,
+                                   const void *state_end, int se64, const float *adj_end,
+                                   float *gpart, int *err, cudaStream_t st) {
+  if (n_vch <= 0) return cudaSuccess;
+  const int bs = 64;
+  const int64_t nt = (int64_t)n_vch * M.n_params;
+  k_prod_grad_chunk<SUM, ES><<<(unsigned)((nt + bs - 1) / bs), bs, 0, st>>>(
+      M, theta, n_vch, per_series, state_end, se64, adj_end, gpart, err);
   GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }
@@ -593,6 +727,7 @@ OpTable make_prod_ops() {
   o.plain32 = &launch_plain_prod<SUM, float>;
   o.plain64 = &launch_plain_prod<SUM, double>;
   o.prod_grad = &launch_prod_grad<SUM>;
+  o.prod_grad_chunk = &launch_prod_grad_chunk<SUM, ES>;
   o.tables = &no_tables;
   o.elem = &launch_elem_prod<SUM, ES>;
   o.comb32 = make_combine<ES, float>();

@@ -1,7 +1,8 @@
 """GPU parity for product kernels (Appendix C.2) on instantaneous measurements
 against the FP64 oracle: the plain per-series filter in FP32 (FP64 sums;
 |L_gpu - L_or| <= 1e-4 max(|L_or|, 0.1 N)) and in FP64 (1e-9 relative), and
-the forward-mode hyperparameter gradient (1e-3 |g| + 1e-4 max|g| per component).
+the forward-mode hyperparameter gradient, chunked and per series (1e-3 |g| +
+1e-4 max|g| per component).
 Calls the product path does not provide report GP_SS_EUNSUPPORTED.
 """
 import math
@@ -74,32 +75,46 @@ def test_single_series(gp, terms, theta):
         _check(ll, oracle.loglik_workload(wl), [wl.n_meas], rel=1e-9 if precision == 64 else None)
 
 
+def _check_grad(g, ref_g):
+    for a, b in zip(np.asarray(g, float), ref_g):
+        bad = np.abs(a - b) > 1e-3 * np.abs(b) + 1e-4 * np.abs(b).max()
+        assert not bad.any(), (a, b)
+
+
+# (schedule, chunk length): the chunked forward-mode gradient (one thread per
+# chunk and parameter, boundary adjoints from the combination) at the default
+# and at a short chunk length, and the plain one (per series and parameter)
+_GRAD_SCHEDULES = [(0, 0), (2, 8), (3, 0)]
+
+
 @pytest.mark.parametrize("terms,theta", [
     ([PROD], [1.2, 0.2, 1.5, 2.0, 8.0, 0.1]),
     ([PROD, SHO], [1.0, 0.3, 0.8, 1.3, 4.0, 0.6, 3.0, 0.3, 0.1]),
     ([PROD, M32], [0.9, 0.5, 0.3, 1.1, 2.0, 0.5, 3.0, 0.05])])
 def test_gradient(gp, terms, theta):
-    # forward-mode tangents (one thread per series and parameter) against the
-    # oracle's complex-step gradient
+    # forward-mode tangents against the oracle's complex-step gradient
     wl = _series_wl(terms, theta, n=500)
-    m = gp.Model.from_workload(wl)
-    ll, g = m.loglik_grad(_dev(wl.theta))
     ref_ll, ref_g = oracle.loglik_workload(wl, grad=True)
-    _check(ll.cpu().numpy(), ref_ll, [wl.n_meas])
-    for a, b in zip(g.cpu().numpy().astype(float), ref_g):
-        bad = np.abs(a - b) > 1e-3 * np.abs(b) + 1e-4 * np.abs(b).max()
-        assert not bad.any(), (a, b)
+    for schedule, chunk in _GRAD_SCHEDULES:
+        m = gp.Model.from_workload(wl, schedule=schedule, chunk_len=chunk)
+        ll, g = m.loglik_grad(_dev(wl.theta))
+        _check(ll.cpu().numpy(), ref_ll, [wl.n_meas])
+        _check_grad(g.cpu().numpy(), ref_g)
+        assert m.last_error() == (-1, 0)
 
 
 def test_gradient_batch(gp):
     wl = _f32(synth.c2p(n_series=12, scale=0.03))
-    m = gp.Model.from_workload(wl)
-    ll, g = m.loglik_grad(_dev(wl.theta))
     ref_ll, ref_g = oracle.loglik_workload(wl, grad=True, processes=4)
-    _check(ll.cpu().numpy(), ref_ll, np.diff(wl.offsets))
-    for a, b in zip(g.cpu().numpy().astype(float), ref_g):
-        bad = np.abs(a - b) > 1e-3 * np.abs(b) + 1e-4 * np.abs(b).max()
-        assert not bad.any(), (a, b)
+    got = {}
+    for schedule, chunk in _GRAD_SCHEDULES:
+        m = gp.Model.from_workload(wl, schedule=schedule, chunk_len=chunk)
+        ll, g = m.loglik_grad(_dev(wl.theta))
+        _check(ll.cpu().numpy(), ref_ll, np.diff(wl.offsets))
+        _check_grad(g.cpu().numpy(), ref_g)
+        got[schedule] = g.cpu().numpy().astype(float)
+    # the chunked and the per-series tangents agree to FP32 rounding
+    np.testing.assert_allclose(got[0], got[3], rtol=2e-4, atol=2e-5 * np.abs(got[3]).max())
 
 
 def test_shared_theta_sets(gp):
@@ -139,11 +154,12 @@ def test_edge_cases(gp):
         _check(ll, ref, np.diff(wl.offsets), rel=1e-9 if precision == 64 else None)
 
 
-def test_gradient_shared_sets_and_host_buffer(gp):
+@pytest.mark.parametrize("schedule,chunk", _GRAD_SCHEDULES)
+def test_gradient_shared_sets_and_host_buffer(gp, schedule, chunk):
     wl = _series_wl([PROD, M32], [1.0, 0.3, 1.0, 1.3, 5.0, 0.5, 3.0, 0.1], n=300)
     th = np.array([wl.theta[0], wl.theta[0] * [1, 1.2, 1, 0.9, 1, 1, 1, 1]], np.float64)
     th = th.astype(np.float32).astype(np.float64)
-    m = gp.Model.from_workload(wl)
+    m = gp.Model.from_workload(wl, schedule=schedule, chunk_len=chunk)
     ll, g = m.loglik_grad(_dev(th), per_series=False)
     ll, g = ll.cpu().numpy().ravel(), g.cpu().numpy().reshape(2, -1)
     for k in range(2):
