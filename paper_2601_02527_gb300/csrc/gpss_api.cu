@@ -125,40 +125,54 @@ __global__ void __launch_bounds__(256) k_fma_peak(float *__restrict__ sink, int 
   if (r == -12345.0f) sink[blockIdx.x] = r;
 }
 
-__global__ void k_interleave(DevModel M, int c_begin, int c_count, float4 *__restrict__ ilv,
-                             uint8_t *__restrict__ ilv_tag) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= c_count) return;
-  const int c = c_begin + i;
+// One warp per chunk, so that a series group's share (a quarter of the chunks
+// or less) still fills the GPU.  A tile of 32 x ILV_RUN steps: lane j takes
+// the run of steps [j ILV_RUN, (j + 1) ILV_RUN) of the tile, counts its end
+// events, and an exclusive warp scan of the counts gives the run's first
+// measurement; each lane then writes its run's lane-step records.
+constexpr int ILV_RUN = 8;
+
+__global__ void __launch_bounds__(128) k_interleave(DevModel M, int c_begin, int c_count,
+                                                    float4 *__restrict__ ilv,
+                                                    uint8_t *__restrict__ ilv_tag) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= c_count) return;  // whole warps
+  const int c = c_begin + (int)w;
   const int64_t e0 = M.ch_ev0[c];
   const int len = M.ch_len[c];
   int64_t mi = M.ch_meas0[c];
-  int64_t idx = lane_step(M, c, 0);
-  // eight steps at a time: their loads are independent, so they are in
-  // flight together
-  constexpr int U = 8;
-  for (int k0 = 0; k0 < len; k0 += U, idx += 32 * U) {
-    uint8_t t[U];
-    float dt[U];
+  const int64_t idx0 = lane_step(M, c, 0);
+  for (int k0 = 0; k0 < len; k0 += 32 * ILV_RUN) {  // len is the same on every lane
+    const int ks = k0 + lane * ILV_RUN;
+    uint8_t t[ILV_RUN];
+    float dt[ILV_RUN];
+    int cnt = 0;
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      t[u] = k0 + u < len ? M.tag[e0 + k0 + u] : 0;
-      dt[u] = k0 + u < len ? M.dt[e0 + k0 + u] : 0.f;
+    for (int u = 0; u < ILV_RUN; ++u) {
+      const bool in = ks + u < len;
+      t[u] = in ? M.tag[e0 + ks + u] : 0;
+      dt[u] = in ? M.dt[e0 + ks + u] : 0.f;
+      cnt += t[u] & 1;
     }
-    float4 q[U];
-    int64_t mu = mi;
+    int incl = cnt;
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      q[u] = (t[u] & 1) ? M.meas[mu] : make_float4(0.f, 0.f, 0.f, 0.f);
-      mu += t[u] & 1;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
     }
-    mi = mu;
+    int64_t mu = mi + (incl - cnt);
+    mi += __shfl_sync(0xffffffffu, incl, 31);
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (k0 + u < len) {
-        ilv[idx + 32 * u] = make_float4(dt[u], q[u].x, q[u].y, q[u].z);
-        ilv_tag[idx + 32 * u] = t[u];
+    for (int u = 0; u < ILV_RUN; ++u) {
+      if (ks + u < len) {
+        const float4 q = (t[u] & 1) ? M.meas[mu] : make_float4(0.f, 0.f, 0.f, 0.f);
+        mu += t[u] & 1;
+        const int64_t o = idx0 + (int64_t)32 * (ks + u);
+        ilv[o] = make_float4(dt[u], q.x, q.y, q.z);
+        ilv_tag[o] = t[u];
       }
+    }
   }
 }
 
@@ -654,8 +668,9 @@ gpss::DevModel dev_view(const gp_ss_model *m);
 // order (after a new plan, or after the event stream was re-sent).
 cudaError_t interleave_events(const gp_ss_model *m, int c0, int cn, cudaStream_t st) {
   if (cn <= 0 || !m->d_ilv) return cudaSuccess;
-  gpss::k_interleave<<<(cn + 127) / 128, 128, 0, st>>>(dev_view(m), c0, cn, m->d_ilv,
-                                                        m->d_ilv_tag);
+  const int64_t threads = (int64_t)cn * 32;  // one warp per chunk
+  gpss::k_interleave<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(dev_view(m), c0, cn,
+                                                                       m->d_ilv, m->d_ilv_tag);
   GPSS_COUNT_LAUNCH();
   return cudaGetLastError();
 }

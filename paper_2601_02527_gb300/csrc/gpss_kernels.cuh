@@ -269,11 +269,12 @@ struct EventReader {
   }
 };
 
-// Lay the event stream out in lane-step order (one thread per chunk, after
-// every change of the chunk plan or of the event stream): chunks
-// [c_begin, c_begin + c_count).
-__global__ void k_interleave(DevModel M, int c_begin, int c_count, float4 *__restrict__ ilv,
-                             uint8_t *__restrict__ ilv_tag);
+// Lay the event stream out in lane-step order (one warp per chunk, 128-thread
+// blocks, after every change of the chunk plan or of the event stream):
+// chunks [c_begin, c_begin + c_count).
+__global__ void __launch_bounds__(128) k_interleave(DevModel M, int c_begin, int c_count,
+                                                    float4 *__restrict__ ilv,
+                                                    uint8_t *__restrict__ ilv_tag);
 
 GPSS_D void flag_error(int *err, int row, int code) {
   if (err) atomicMax(err + row, code);

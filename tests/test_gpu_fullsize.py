@@ -129,7 +129,7 @@ def test_c2i_full_instantaneous(gp):
     _check_grad(g[idx], ref_g)
 
 
-def test_c2p_product_loglik(gp):
+def test_c2p_product_loglik_and_grad(gp):
     # the product-kernel batch (1024 series of the c2p recipe): FP32 and FP64
     # plain filters against each other everywhere, against the oracle sampled
     wl = _f32(synth.c2p(n_series=1024))
@@ -141,6 +141,17 @@ def test_c2p_product_loglik(gp):
     idx = _sample(counts, 6)
     ref = oracle.loglik_workload(wl, series_idx=idx, processes=6)
     assert np.all(np.abs(ll64[idx] - ref) <= 1e-9 * np.abs(ref))
+    # loglik + gradient at full size: the chunked forward-mode gradient against
+    # the per-series one everywhere, and against the oracle's complex-step
+    # gradient on sampled series
+    llg, g = gp.Model.from_workload(wl).loglik_grad(th)
+    _, g3 = gp.Model.from_workload(wl, schedule=3).loglik_grad(th)
+    g, g3 = g.cpu().numpy(), g3.cpu().numpy()
+    _check_ll(llg.cpu().numpy(), ll64, counts)
+    _check_grad(g, g3)
+    idx = _sample(counts, 4)
+    _, ref_g = oracle.loglik_workload(wl, series_idx=idx, grad=True, processes=4)
+    _check_grad(g[idx], ref_g)
 
 
 def test_c3_full_scan(gp):
