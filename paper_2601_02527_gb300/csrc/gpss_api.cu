@@ -1614,7 +1614,9 @@ gp_ss_status gp_ss_loglik_grad_host(const gp_ss_model *m, const float *theta_hos
   // A re-sent event stream goes up in series groups on a second stream, and
   // each group's element pass starts as soon as its events are in (the copy
   // of the rest overlaps it).  The copy stream first waits for earlier work
-  // on st, which may still read the device copy.
+  // on st, which may still read the device copy.  Four groups (c4 element
+  // phase with the upload: 1.84 ms with four, 1.90 ms with two; 0.80 ms
+  // without the upload, 1.18 ms for the upload alone).
   constexpr int kGroups = 4;
   cudaStream_t cs = nullptr;
   cudaEvent_t start_ev = nullptr, ready[kGroups] = {};
