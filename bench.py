@@ -223,9 +223,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sel), "samples_from": where}
 
 
-def oracle_sample_rate(wl, budget_s, n_proc, prefix_meas, grad=True):
-    """The FP64 oracle (Van Loan discretisation; log-likelihood, with ``grad``
-    also its complex-step gradient) on host cores.
+def oracle_sample_rate(wl, budget_s, n_proc, prefix_meas, grad=True, closed_form=True):
+    """The FP64 oracle (log-likelihood, with ``grad`` also its complex-step
+    gradient) on host cores.  ``closed_form``: its timing mode, Appendix B's
+    closed forms for the discretisation where every term is an underdamped SHO
+    (Van Loan otherwise); else the Van Loan discretisation the parity tests use.
 
     Sample: the first ``prefix_meas`` measurements of consecutive series (or,
     for one series shared by parameter sets, of the series under consecutive
@@ -246,7 +248,7 @@ def oracle_sample_rate(wl, budget_s, n_proc, prefix_meas, grad=True):
         k = min(prefix_meas, len(ts))
         jobs.append((wl.terms, wl.layout, (ts[:k], te[:k], y[:k], ye[:k],
                                            None if inst is None else inst[:k]), wl.theta[i],
-                     grad))
+                     grad, closed_form))
     done = 0
     t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(n_proc) as pool:
@@ -259,7 +261,11 @@ def oracle_sample_rate(wl, budget_s, n_proc, prefix_meas, grad=True):
     el = time.perf_counter() - t0
     what = "loglik + complex-step gradient" if grad else "loglik"
     unit = "series" if wl.theta_per_series else "parameter sets of the one series"
-    return done / el, n_proc, (f"oracle {what}, FP64 (Van Loan), first {prefix_meas} "
+    all_sho = all(t == 1 for t in wl.terms)
+    disc = ("closed forms of Appendix B" if closed_form and all_sho else
+            "Van Loan" + (" (no closed forms printed for its Matern-3/2 term)"
+                          if closed_form else ""))
+    return done / el, n_proc, (f"oracle {what}, FP64 ({disc}), first {prefix_meas} "
                                f"measurements of {j} {unit}, {n_proc} processes, {el:.1f} s")
 
 
@@ -385,6 +391,11 @@ def run_ours(args):
             r2, c2, d2 = oracle_sample_rate(wl, max(2.0, args.cpu_budget / 3), ncore, prefix,
                                             grad=False)
             cpu["loglik_only"] = {"value": r2, "unit": UNIT, "cores": c2, "sample": d2}
+        if all(t == 1 for t in wl.terms):
+            # the Van Loan discretisation (the parity reference), timed apart
+            r3, c3, d3 = oracle_sample_rate(wl, max(2.0, args.cpu_budget / 3), ncore, prefix,
+                                            grad=want_grad, closed_form=False)
+            cpu["van_loan"] = {"value": r3, "unit": UNIT, "cores": c3, "sample": d3}
     fp32_peak, n_sms = gp.measure_fp32_peak()
     t0 = time.perf_counter()
     model = gp.Model.from_workload(wl, chunk_len=args.chunk_len, ckpt_interval=args.ckpt_interval,

@@ -94,8 +94,11 @@ def _ptr(a, ctype):
     return a.ctypes.data_as(ctypes.POINTER(ctype))
 
 
-def spec_array(terms, layout, n_slots):
-    return np.asarray([len(terms), layout, n_slots] + list(terms), dtype=np.int32)
+def spec_array(terms, layout, n_slots, closed_form=False):
+    """Model specification; ``closed_form`` selects the filter's timing mode
+    (Appendix B closed forms for underdamped SHO terms, Van Loan otherwise)."""
+    return np.asarray([len(terms), layout | (256 if closed_form else 0), n_slots] + list(terms),
+                      dtype=np.int32)
 
 
 def dim(terms, layout, n_slots) -> int:
@@ -174,11 +177,14 @@ def events(t_start, t_end, y, yerr, instrument=None):
                 invd=invd, n_slots=n_slots, n_meas=n)
 
 
-def loglik_events(terms, layout, ev, theta, grad=False, n_slots=None, dump=False):
-    """Oracle log-likelihood (and complex-step gradient) from built events."""
+def loglik_events(terms, layout, ev, theta, grad=False, n_slots=None, dump=False,
+                  closed_form=False):
+    """Oracle log-likelihood (and complex-step gradient) from built events.
+    ``closed_form``: the timing mode (see spec_array); the parity reference is
+    the default Van Loan discretisation."""
     lib = _load()
     n_slots = ev["n_slots"] if n_slots is None else n_slots
-    spec = spec_array(terms, layout, n_slots)
+    spec = spec_array(terms, layout, n_slots, closed_form)
     theta = np.ascontiguousarray(theta, np.float64)
     out = np.zeros(1)
     g = np.zeros(len(theta)) if grad else None
@@ -305,17 +311,19 @@ def exposure_grad(terms, layout, t_start, t_end, y, yerr, theta, instrument=None
 
 
 def loglik(terms, layout, t_start, t_end, y, yerr, theta, instrument=None, grad=False,
-           n_slots=None):
+           n_slots=None, closed_form=False):
     """Oracle log-likelihood of one series; returns float or (float, grad)."""
     ev = events(t_start, t_end, y, yerr, instrument)
-    r = loglik_events(terms, layout, ev, theta, grad=grad, n_slots=n_slots)
+    r = loglik_events(terms, layout, ev, theta, grad=grad, n_slots=n_slots,
+                      closed_form=closed_form)
     return (r["loglik"], r["grad"]) if grad else r["loglik"]
 
 
-def discretize(terms, layout, n_slots, theta, dt):
-    """Phi~(dt), Q~(dt) and P0 of the augmented model (Van Loan + doubling)."""
+def discretize(terms, layout, n_slots, theta, dt, closed_form=False):
+    """Phi~(dt), Q~(dt) and P0 of the augmented model (Van Loan + doubling, or
+    with ``closed_form`` the Appendix B closed forms where they apply)."""
     lib = _load()
-    spec = spec_array(terms, layout, n_slots)
+    spec = spec_array(terms, layout, n_slots, closed_form)
     D = lib.gpss_oracle_dim(_ptr(spec, ctypes.c_int32))
     Phi = np.zeros((D, D))
     Q = np.zeros((D, D))
@@ -330,9 +338,11 @@ def discretize(terms, layout, n_slots, theta, dt):
 
 
 def _series_job(args):
-    terms, layout, ser, th, grad = args
+    terms, layout, ser, th, grad = args[:5]
+    closed_form = args[5] if len(args) > 5 else False
     ts, te, y, ye, inst = ser
-    r = loglik(terms, layout, ts, te, y, ye, th, instrument=inst, grad=grad)
+    r = loglik(terms, layout, ts, te, y, ye, th, instrument=inst, grad=grad,
+               closed_form=closed_form)
     return r
 
 

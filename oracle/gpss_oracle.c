@@ -44,6 +44,7 @@ typedef struct {
   int n_slots;
   int dim;    /* augmented state dimension */
   int n_zper; /* integral states per slot */
+  int closed; /* 1: the filter's timing mode (Appendix B closed forms where they apply) */
 } model_t;
 
 static int zindex(const model_t *M, int slot, int t) {
@@ -64,9 +65,12 @@ static void obs_vector(const model_t *M, int kind, int slot, double invd, double
   }
 }
 
+/* spec: n_terms, layout (bit 8: closed-form timing mode), n_slots, kinds. */
 static int parse_spec(const int32_t *spec, model_t *M) {
   M->n_terms = spec[0];
-  M->layout = spec[1];
+  M->layout = spec[1] & 0xff;
+  M->closed = (spec[1] >> 8) & 1;
+  if (spec[1] & ~0x1ff) return 1;
   M->n_slots = spec[2];
   if (M->n_terms < 1 || M->n_terms > MAXT || M->n_slots < 0) return 1;
   if (M->layout != 0 && M->layout != 1) return 1;
@@ -97,6 +101,9 @@ static int n_params(const model_t *M) {
 #define S_LOG log
 #define S_ABS fabs
 #define S_RE(x) (x)
+#define S_EXP exp
+#define S_SIN sin
+#define S_COS cos
 #include "oracle_body.h"
 #undef SCALAR
 #undef SFX
@@ -104,6 +111,9 @@ static int n_params(const model_t *M) {
 #undef S_LOG
 #undef S_ABS
 #undef S_RE
+#undef S_EXP
+#undef S_SIN
+#undef S_COS
 
 /* ---- complex instantiation (complex-step derivatives) ---- */
 #define SCALAR double complex
@@ -112,6 +122,9 @@ static int n_params(const model_t *M) {
 #define S_LOG clog
 #define S_ABS cabs
 #define S_RE(x) creal(x)
+#define S_EXP cexp
+#define S_SIN csin
+#define S_COS ccos
 #include "oracle_body.h"
 #undef SCALAR
 #undef SFX
@@ -119,6 +132,9 @@ static int n_params(const model_t *M) {
 #undef S_LOG
 #undef S_ABS
 #undef S_RE
+#undef S_EXP
+#undef S_SIN
+#undef S_COS
 
 int gpss_oracle_dim(const int32_t *spec) {
   model_t M;
@@ -126,7 +142,8 @@ int gpss_oracle_dim(const int32_t *spec) {
   return M.dim;
 }
 
-/* Phi~, Q~ and P0 (row-major dim x dim) for one step dt of the augmented model. */
+/* Phi~, Q~ and P0 (row-major dim x dim) for one step dt of the augmented model
+ * (Van Loan, or the closed forms in the timing mode where they apply). */
 int gpss_oracle_discretize(const int32_t *spec, const double *theta, double dt, double *Phi,
                            double *Q, double *P0) {
   model_t M;
@@ -135,7 +152,8 @@ int gpss_oracle_discretize(const int32_t *spec, const double *theta, double dt, 
   double F[MAXD * MAXD], LQL[MAXD * MAXD];
   term_params_r(&M, theta, w0, q, var, &s2);
   build_F_r(&M, w0, q, var, F, LQL);
-  discretize_r(&M, F, LQL, dt, Phi, Q);
+  if (!M.closed || discretize_closed_r(&M, w0, q, var, dt, Phi, Q))
+    discretize_r(&M, F, LQL, dt, Phi, Q);
   if (P0) initial_cov_r(&M, w0, var, P0);
   return 0;
 }

@@ -205,6 +205,86 @@ static void SFX(discretize)(const model_t *M, const SCALAR *F, const SCALAR *LQL
   }
 }
 
+/* Timing mode of the CPU baseline: Phi~ and Q~ of a model whose terms are
+ * all underdamped SHOs (Q > 1/2) from the closed forms printed in Appendix B,
+ * per term: Phi (Eq. sho_phi), Q (Eq. sho_Q), the first row of
+ * Phibar = int_0^dt Phi (Eq. sho_phibar), Q~12 (Eq. analytic_Qaug12) and
+ * Q~22 (Eq. analytic_Qaug22).  The terms are independent, so an integral
+ * state z gets Phibar's row and Q~12 of every term it integrates, and two
+ * integral states share Q~22 of every term both integrate (each integrates
+ * the same function over the same step).  sigma^2 e^{-w0 dt/Q} (e^{w0 dt/Q}
+ * - 1 - ...) of Eq. sho_Q is written (1 - e^{-w0 dt/Q}) - e^{-w0 dt/Q}(...)
+ * so that long steps do not overflow.  Returns 0, or 1 when a term is not an
+ * underdamped SHO (the caller then uses Van Loan). */
+static int SFX(discretize_closed)(const model_t *M, const SCALAR *w0v, const SCALAR *qv,
+                                  const SCALAR *var, SCALAR dt, SCALAR *Phi, SCALAR *Q) {
+  const int D = M->dim;
+  for (int t = 0; t < M->n_terms; ++t)
+    if (M->kind[t] != 1 || !(S_RE(qv[t]) > 0.5)) return 1;
+  for (int i = 0; i < D * D; ++i) {
+    Phi[i] = (i % (D + 1) == 0) ? 1.0 : 0.0;
+    Q[i] = 0;
+  }
+  if (dt == 0.0) return 0;
+  SCALAR pb[MAXT][2], q12[MAXT][2], q22[MAXT];
+  for (int t = 0; t < M->n_terms; ++t) {
+    const int i = M->toff[t];
+    const SCALAR w0 = w0v[t], q = qv[t], v = var[t];
+    const SCALAR eta = S_SQRT(1.0 - 1.0 / (4.0 * q * q));
+    const SCALAR tau = eta * w0 * dt, A = 1.0 / (2.0 * eta * q);
+    const SCALAR e1 = S_EXP(-w0 * dt / (2.0 * q)), e2 = e1 * e1;
+    const SCALAR sn = S_SIN(tau), cs = S_COS(tau), s2t = S_SIN(2.0 * tau), c2t = S_COS(2.0 * tau);
+    const SCALAR ss = sn * sn;
+    /* Eq. sho_phi, Q > 1/2 */
+    Phi[i * D + i] = e1 * (cs + A * sn);
+    Phi[i * D + i + 1] = e1 * sn / (eta * w0);
+    Phi[(i + 1) * D + i] = -e1 * w0 * sn / eta;
+    Phi[(i + 1) * D + i + 1] = e1 * (cs - A * sn);
+    /* Eq. sho_Q */
+    const SCALAR k2 = 1.0 / (2.0 * eta * eta * q * q);
+    Q[i * D + i] = v * ((1.0 - e2) - e2 * (A * s2t + k2 * ss));
+    Q[i * D + i + 1] = Q[(i + 1) * D + i] = v * e2 * w0 / (eta * eta * q) * ss;
+    Q[(i + 1) * D + i + 1] = v * w0 * w0 * ((1.0 - e2) + e2 * (A * s2t - k2 * ss));
+    /* Eq. sho_phibar, first row: e^{a t}/(a^2 + b^2) (Ic + A Is, B Is) from 0 to dt */
+    const SCALAR a = -w0 / (2.0 * q), b = eta * w0, B = 1.0 / (eta * w0);
+    const SCALAR n1 = S_EXP(a * dt) / (a * a + b * b), n0 = 1.0 / (a * a + b * b);
+    const SCALAR Is1 = a * sn - b * cs, Ic1 = a * cs + b * sn; /* at t = dt (b dt = tau) */
+    const SCALAR Is0 = -b, Ic0 = a;                            /* at t = 0 */
+    pb[t][0] = n1 * (Ic1 + A * Is1) - n0 * (Ic0 + A * Is0);
+    pb[t][1] = n1 * (B * Is1) - n0 * (B * Is0);
+    /* Eq. analytic_Qaug12 */
+    const SCALAR r = e1 * (cs + A * sn) - 1.0;
+    q12[t][0] = v / (q * w0) * r * r;
+    q12[t][1] = v * (A * e1 * (4.0 * sn - e1 * s2t) - 2.0 * A * A * e2 * ss + e2 - 1.0);
+    /* Eq. analytic_Qaug22 */
+    q22[t] = v / (4.0 * q * q * w0 * w0) *
+             (8.0 * q * w0 * dt + 4.0 * q * q - 12.0 + A * A * e2 * (c2t - 16.0 * q * q * q * q) +
+              16.0 * e1 * (cs + (1.0 - 2.0 * q * q) * A * sn) +
+              e2 * ((1.0 - 3.0 * A * A) / A * s2t - 3.0 * c2t));
+  }
+  for (int z = M->nx; z < D; ++z) {
+    const int zs = z - M->nx;
+    for (int t = 0; t < M->n_terms; ++t) {
+      if (M->layout == 1 && zs % M->n_terms != t) continue; /* z_{t,j} integrates x_t only */
+      const int i = M->toff[t];
+      Phi[z * D + i] = pb[t][0];
+      Phi[z * D + i + 1] = pb[t][1];
+      Q[i * D + z] = Q[z * D + i] = q12[t][0];
+      Q[(i + 1) * D + z] = Q[z * D + i + 1] = q12[t][1];
+    }
+    for (int z2 = M->nx; z2 < D; ++z2) {
+      const int zs2 = z2 - M->nx;
+      SCALAR acc = 0;
+      for (int t = 0; t < M->n_terms; ++t) {
+        if (M->layout == 1 && (zs % M->n_terms != t || zs2 % M->n_terms != t)) continue;
+        acc += q22[t];
+      }
+      Q[z * D + z2] = acc;
+    }
+  }
+  return 0;
+}
+
 /* Initial covariance P0 = blkdiag(P_inf, I) (Section 3.2.3, final paragraph). */
 static void SFX(initial_cov)(const model_t *M, const SCALAR *w0, const SCALAR *var, SCALAR *P) {
   const int D = M->dim;
@@ -251,7 +331,8 @@ static int SFX(filter)(const model_t *M, const SCALAR *th, int64_t n_ev, const S
     SCALAR dt = t_ev[k] - tprev;
     tprev = t_ev[k];
     if (S_RE(dt) < 0) return 2;
-    SFX(discretize)(M, F, LQL, dt, Phi, Qd);
+    if (!M->closed || SFX(discretize_closed)(M, w0, q, var, dt, Phi, Qd))
+      SFX(discretize)(M, F, LQL, dt, Phi, Qd);
     for (int i = 0; i < D; ++i) {
       SCALAR acc = 0;
       for (int j = 0; j < D; ++j) acc += Phi[i * D + j] * m[j];

@@ -190,3 +190,41 @@ def test_multi_slot_and_sum_block_structure(oracle_lib):
     np.testing.assert_allclose(P1l[4, 2:4], 0, atol=1e-15)
     np.testing.assert_allclose(Q1l[5, 5], Qm[2, 2], rtol=1e-12)
     assert abs(Q1l[4, 5]) <= 1e-15
+
+
+@pytest.mark.parametrize("q", [0.55, 3.0, 10.0])
+@pytest.mark.parametrize("dt", [0.05, 0.7, 4.0, 40.0, 400.0])
+@pytest.mark.parametrize("layout,n_slots", [(0, 1), (0, 3), (1, 2)])
+def test_closed_form_timing_mode_matches_van_loan(oracle_lib, q, dt, layout, n_slots):
+    # the timing mode's per-term closed forms (Appendix B), assembled for a sum
+    # of two SHO terms and several integral states, against Van Loan of the
+    # whole augmented model
+    theta = [1.3, 0.9, q, 0.6, 2.5, 1.7, 0.1]
+    Pv, Qv, _ = oracle.discretize([SHO, SHO], layout, n_slots, theta, dt)
+    Pc, Qc, _ = oracle.discretize([SHO, SHO], layout, n_slots, theta, dt, closed_form=True)
+    assert close(Pc, Pv, rtol=1e-9, ntol=1e-12)
+    assert close(Qc, Qv, rtol=1e-9, ntol=1e-12)
+
+
+def test_closed_form_timing_mode_falls_back():
+    # a Matern-3/2 term has no printed closed forms for Q~: Van Loan is used
+    theta = [1.0, 2.0, 3.0, 0.5, 4.0, 0.1]
+    Pv, Qv, _ = oracle.discretize([SHO, M32], 0, 1, theta, 0.3)
+    Pc, Qc, _ = oracle.discretize([SHO, M32], 0, 1, theta, 0.3, closed_form=True)
+    assert np.array_equal(Pc, Pv) and np.array_equal(Qc, Qv)
+
+
+def test_closed_form_timing_mode_loglik_and_gradient(oracle_lib):
+    # the filter in the timing mode gives the Van Loan log-likelihood and
+    # complex-step gradient to within 1e-9 per measurement (c1 and c4 recipes)
+    import synth
+    for wl in (synth.c1(), synth.c4(n_series=2, scale=0.1)):
+        for i in range(wl.n_series):
+            ts, te, y, ye, _ = wl.series(i)
+            k = min(len(ts), 800)
+            a, ga = oracle.loglik(wl.terms, wl.layout, ts[:k], te[:k], y[:k], ye[:k],
+                                  wl.theta[i], grad=True)
+            b, gb = oracle.loglik(wl.terms, wl.layout, ts[:k], te[:k], y[:k], ye[:k],
+                                  wl.theta[i], grad=True, closed_form=True)
+            assert abs(a - b) <= 1e-9 * k
+            assert np.all(np.abs(ga - gb) <= 1e-7 * np.abs(ga) + 1e-9 * k)
