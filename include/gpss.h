@@ -73,10 +73,13 @@ typedef enum {
   GP_SS_TERM_SHO_PRODUCT = 3 /* (sigma, omega_a, Q_a, omega_b, Q_b): sigma^2 k_a k_b, two
                                 unit-variance SHO factors (Appendix C.2, Kronecker state of
                                 dimension 4).  First term only, at most one plain term after
-                                it, instantaneous measurements only; gp_ss_loglik (the plain
-                                per-series filter, FP32 or FP64) and gp_ss_loglik_grad
-                                (hyperparameter gradient by forward-mode tangents, FP32);
-                                other calls return GP_SS_EUNSUPPORTED. */
+                                it, instantaneous measurements only; gp_ss_loglik (FP32
+                                parallel in time, or the plain per-series filter: FP64 and
+                                schedule 3) and gp_ss_loglik_grad (hyperparameter gradient
+                                by forward-mode tangents in FP32: per chunk and parameter
+                                against the combination's boundary adjoints, or per series
+                                and parameter under schedule 3); other calls return
+                                GP_SS_EUNSUPPORTED. */
 } gp_ss_term;
 
 typedef struct {
