@@ -225,9 +225,10 @@ class ClockSampler:
 
 def oracle_sample_rate(wl, budget_s, n_proc, prefix_meas, grad=True, closed_form=True):
     """The FP64 oracle (log-likelihood, with ``grad`` also its complex-step
-    gradient) on host cores.  ``closed_form``: its timing mode, Appendix B's
-    closed forms for the discretisation where every term is an underdamped SHO
-    (Van Loan otherwise); else the Van Loan discretisation the parity tests use.
+    gradient) on host cores.  ``closed_form``: its timing mode, closed forms for
+    the discretisation (Appendix B's for underdamped SHO terms, the defining
+    integrals worked out for critically damped ones; Van Loan for overdamped
+    and product terms); else the Van Loan discretisation the parity tests use.
 
     Sample: the first ``prefix_meas`` measurements of consecutive series (or,
     for one series shared by parameter sets, of the series under consecutive
@@ -265,10 +266,9 @@ def oracle_sample_rate(wl, budget_s, n_proc, prefix_meas, grad=True, closed_form
     el = time.perf_counter() - t0
     what = "loglik + complex-step gradient" if grad else "loglik"
     unit = "series" if wl.theta_per_series else "parameter sets of the one series"
-    all_sho = all(t == 1 for t in wl.terms)
-    disc = ("closed forms of Appendix B" if closed_form and all_sho else
-            "Van Loan" + (" (no closed forms printed for its Matern-3/2 term)"
-                          if closed_form else ""))
+    plain = all(t in (1, 2) for t in wl.terms)
+    disc = ("closed forms (Appendix B; Van Loan for any overdamped row)" if closed_form and plain
+            else "Van Loan" + (" (product terms have no closed forms here)" if closed_form else ""))
     return done / el, n_proc, (f"oracle {what}, FP64 ({disc}), first {prefix_meas} "
                                f"measurements of {min(j, rows)} {unit}"
                                f"{' (cycled: ' + str(j) + ' jobs)' if j > rows else ''}, "
@@ -397,7 +397,7 @@ def run_ours(args):
             r2, c2, d2 = oracle_sample_rate(wl, max(2.0, args.cpu_budget / 3), ncore, prefix,
                                             grad=False)
             cpu["loglik_only"] = {"value": r2, "unit": UNIT, "cores": c2, "sample": d2}
-        if all(t == 1 for t in wl.terms):
+        if all(t in (1, 2) for t in wl.terms):
             # the Van Loan discretisation (the parity reference), timed apart
             r3, c3, d3 = oracle_sample_rate(wl, max(2.0, args.cpu_budget / 3), ncore, prefix,
                                             grad=want_grad, closed_form=False)

@@ -206,21 +206,31 @@ static void SFX(discretize)(const model_t *M, const SCALAR *F, const SCALAR *LQL
 }
 
 /* Timing mode of the CPU baseline: Phi~ and Q~ of a model whose terms are
- * all underdamped SHOs (Q > 1/2) from the closed forms printed in Appendix B,
- * per term: Phi (Eq. sho_phi), Q (Eq. sho_Q), the first row of
+ * all SHOs with Q >= 1/2 (Matern-3/2 included) in closed form.  Underdamped
+ * terms (Q > 1/2) take the closed forms printed in Appendix B, per term: Phi (Eq. sho_phi), Q (Eq. sho_Q), the first row of
  * Phibar = int_0^dt Phi (Eq. sho_phibar), Q~12 (Eq. analytic_Qaug12) and
  * Q~22 (Eq. analytic_Qaug22).  The terms are independent, so an integral
  * state z gets Phibar's row and Q~12 of every term it integrates, and two
  * integral states share Q~22 of every term both integrate (each integrates
  * the same function over the same step).  sigma^2 e^{-w0 dt/Q} (e^{w0 dt/Q}
  * - 1 - ...) of Eq. sho_Q is written (1 - e^{-w0 dt/Q}) - e^{-w0 dt/Q}(...)
- * so that long steps do not overflow.  Returns 0, or 1 when a term is not an
- * underdamped SHO (the caller then uses Van Loan). */
+ * so that long steps do not overflow.  A critically damped term (Matern-3/2,
+ * or an SHO with Q = 1/2) takes Phi of Eq. sho_phi (Q = 1/2), Q = P_inf -
+ * Phi P_inf Phi^T (Eq. Q), and Phibar, Q~12, Q~22 from their defining
+ * integrals (Eqs. phiaug, Q_aug: Q~12_i = Q_c int_0^dt (Phi(s) L)_i G(s) ds,
+ * Q~22 = Q_c int_0^dt G(s)^2 ds, G(s) = int_0^s Phi_01) worked out for
+ * Phi(s) L = e^{-w s} (s, 1 - w s); with x = w dt and E = e^{-x}:
+ *   Phibar = ((2 - (2 + x) E) / w, (1 - (1 + x) E) / w^2),
+ *   Q~12 = sigma^2 (2 (x^2 E^2 + 2 x E^2 - 2 (x + 1) E + 1 + E^2) / w,
+ *                   -2 x^2 E^2 + 4 x E - 2 x E^2 - 1 + E^2),
+ *   Q~22 = sigma^2 (4 x - 11 + 8 (x + 2) E - (2 x^2 + 6 x + 5) E^2) / w^2.
+ * Returns 0, or 1 when a term is overdamped or a product (the caller then
+ * uses Van Loan). */
 static int SFX(discretize_closed)(const model_t *M, const SCALAR *w0v, const SCALAR *qv,
                                   const SCALAR *var, SCALAR dt, SCALAR *Phi, SCALAR *Q) {
   const int D = M->dim;
   for (int t = 0; t < M->n_terms; ++t)
-    if (M->kind[t] != 1 || !(S_RE(qv[t]) > 0.5)) return 1;
+    if (M->kind[t] == 3 || !(S_RE(qv[t]) >= 0.5)) return 1;
   for (int i = 0; i < D * D; ++i) {
     Phi[i] = (i % (D + 1) == 0) ? 1.0 : 0.0;
     Q[i] = 0;
@@ -230,6 +240,24 @@ static int SFX(discretize_closed)(const model_t *M, const SCALAR *w0v, const SCA
   for (int t = 0; t < M->n_terms; ++t) {
     const int i = M->toff[t];
     const SCALAR w0 = w0v[t], q = qv[t], v = var[t];
+    if (S_RE(q) == 0.5) {
+      /* critically damped */
+      const SCALAR x = w0 * dt, E = S_EXP(-x), E2 = E * E;
+      Phi[i * D + i] = E * (1.0 + x);
+      Phi[i * D + i + 1] = E * dt;
+      Phi[(i + 1) * D + i] = -E * w0 * w0 * dt;
+      Phi[(i + 1) * D + i + 1] = E * (1.0 - x);
+      Q[i * D + i] = v * (1.0 - (x * x + (x + 1.0) * (x + 1.0)) * E2);
+      Q[i * D + i + 1] = Q[(i + 1) * D + i] = v * 2.0 * x * x * w0 * E2;
+      Q[(i + 1) * D + i + 1] = v * w0 * w0 * (1.0 - (x * x + (x - 1.0) * (x - 1.0)) * E2);
+      pb[t][0] = (2.0 - (2.0 + x) * E) / w0;
+      pb[t][1] = (1.0 - (1.0 + x) * E) / (w0 * w0);
+      q12[t][0] = v * 2.0 * (x * x * E2 + 2.0 * x * E2 - 2.0 * (x + 1.0) * E + 1.0 + E2) / w0;
+      q12[t][1] = v * (-2.0 * x * x * E2 + 4.0 * x * E - 2.0 * x * E2 - 1.0 + E2);
+      q22[t] = v * (4.0 * x - 11.0 + 8.0 * (x + 2.0) * E - (2.0 * x * x + 6.0 * x + 5.0) * E2) /
+               (w0 * w0);
+      continue;
+    }
     const SCALAR eta = S_SQRT(1.0 - 1.0 / (4.0 * q * q));
     const SCALAR tau = eta * w0 * dt, A = 1.0 / (2.0 * eta * q);
     const SCALAR e1 = S_EXP(-w0 * dt / (2.0 * q)), e2 = e1 * e1;
